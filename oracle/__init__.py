@@ -1,0 +1,22 @@
+"""HOMG CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Plain FP64 restatement of the high-occupancy multigrid of arXiv:1108.2045, in C
+(``homg_oracle.c``) behind thin numpy wrappers. Only ``tests/``, the package smoke check and the
+benchmark's CPU-baseline leg may import this package. The GPU library shares no code with it and
+never calls it.
+"""
+
+from .oracle import (  # noqa: F401
+    DIVERGED,
+    NOT_CONVERGED,
+    OK,
+    build,
+    cycle,
+    default_omega_j,
+    iteration,
+    mfmg_schedule,
+    norm_interior,
+    residual,
+    restrict,
+    solve,
+)

@@ -1,0 +1,408 @@
+/*
+ * HOMG CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 restatement of the high-occupancy multigrid (HOMG) of
+ * Becerra-Sagredo, Malaga and Mandujano, "A novel and scalable Multigrid algorithm for many-core
+ * architectures" (arXiv:1108.2045). Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this file; the GPU library neither links nor calls it and
+ * shares no code with it.
+ *
+ * Every function follows the paper's steps in the paper's order, one grid node at a time, with no
+ * blocking, fusion or reordering. The arithmetic order inside each formula is fixed and written
+ * out so a reader can check it by eye ("canonical order").
+ *
+ * Problem (Sec. 2, Eq. 1; Sec. 4, Eq. "poisson"): A u = f on the unit square (cube) with zero
+ * Dirichlet boundary, A = -Laplacian discretised with the 5-point (2-D) or 7-point (3-D) stencil
+ * on a node grid of (n+1)^d nodes, n = 2^K, h = 1/n. The paper writes the Poisson equation with
+ * the opposite sign; the positive-definite form is used here so that damped Jacobi is stable
+ * (reading A1 of the design notes).
+ *
+ * Layout: node (i, j[, k]) of a grid with n intervals per side lives at
+ *   2-D: j*(n+1) + i          3-D: (k*(n+1) + j)*(n+1) + i        (x fastest).
+ * Level m (Sec. 2, relaxation formula) is the lattice of interior nodes whose indexes are all
+ * multiples of l = 2^m, with spacing h_m = 2^m h. A "compact" level-m array stores one value per
+ * node of that lattice (boundary included) as an (n/2^m + 1)^d grid in the same layout.
+ *
+ * Parity pins (tests/test_oracle_*.py): closed-form discrete eigen-solutions, dense direct solves
+ * on tiny grids, the closed form of full weighting on a sine product, the adjoint relation between
+ * full weighting and bilinear interpolation, exact reproduction of (tri)linear fields by the
+ * interpolation, the damped-Jacobi amplification factor of a single-level cycle, the Fig. 3
+ * narrative (spike, stall, pyramid), O(h^2) discretisation error, the residual decrease per cycle,
+ * and the Fig. 4 error levels as an order-of-magnitude check. The schedule itself (Fig. 1 is
+ * missing) is pinned only by the MFMG rule stated in Sec. 2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define HOMG_ORACLE_OK 0
+#define HOMG_ORACLE_NOT_CONVERGED 1
+#define HOMG_ORACLE_DIVERGED 2
+#define HOMG_ORACLE_EINVAL (-1)
+#define HOMG_ORACLE_ENOMEM (-4)
+
+static int64_t ipow(int64_t b, int e) {
+    int64_t r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
+static int log2_exact(int64_t n) {
+    int k = 0;
+    if (n < 1) return -1;
+    while (((int64_t)1 << k) < n) ++k;
+    return (((int64_t)1 << k) == n) ? k : -1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Schedule (Sec. 2, MFMG paragraph and Fig. 1 caption): levels are visited from the coarsest   */
+/* M = levels-1 down to the finest 0; the coarsest gets two iterations and every finer level     */
+/* doubles the count until it reaches MaxI.                                                      */
+/* ------------------------------------------------------------------------------------------ */
+int homg_oracle_mfmg_schedule(int levels, int max_i, int *sched, int cap) {
+    int count = 0;
+    if (levels < 1 || max_i < 1) return HOMG_ORACLE_EINVAL;
+    int M = levels - 1;
+    for (int m = M; m >= 0; --m) {
+        int64_t nm = 2;
+        for (int s = 0; s < M - m && nm < max_i; ++s) nm *= 2;
+        if (nm > max_i) nm = max_i;
+        for (int64_t t = 0; t < nm; ++t) {
+            if (sched && count < cap) sched[count] = m;
+            ++count;
+        }
+    }
+    return count;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Residual r = f - A_h u (Sec. 2, step (b) of the two-grid scheme). Interior nodes only; the     */
+/* boundary of r is 0 and boundary values of u are taken as the homogeneous Dirichlet value 0.  */
+/* 2-D: A_h u = ((((4u - uW) - uE) - uS) - uN) / h^2                                              */
+/* 3-D: A_h u = ((((((6u - uW) - uE) - uS) - uN) - uB) - uT) / h^2                                */
+/* ------------------------------------------------------------------------------------------ */
+static double u_at2(const double *u, int64_t n, int64_t i, int64_t j) {
+    if (i <= 0 || j <= 0 || i >= n || j >= n) return 0.0;
+    return u[j * (n + 1) + i];
+}
+
+static double u_at3(const double *u, int64_t n, int64_t i, int64_t j, int64_t k) {
+    if (i <= 0 || j <= 0 || k <= 0 || i >= n || j >= n || k >= n) return 0.0;
+    return u[(k * (n + 1) + j) * (n + 1) + i];
+}
+
+void homg_oracle_residual(int ndim, int64_t n, const double *f, const double *u, double *r) {
+    const double h = 1.0 / (double)n;
+    const double h2 = h * h;
+    if (ndim == 2) {
+        for (int64_t j = 0; j <= n; ++j)
+            for (int64_t i = 0; i <= n; ++i) {
+                int64_t p = j * (n + 1) + i;
+                if (i == 0 || j == 0 || i == n || j == n) { r[p] = 0.0; continue; }
+                double lap = 4.0 * u_at2(u, n, i, j);
+                lap = lap - u_at2(u, n, i - 1, j);
+                lap = lap - u_at2(u, n, i + 1, j);
+                lap = lap - u_at2(u, n, i, j - 1);
+                lap = lap - u_at2(u, n, i, j + 1);
+                r[p] = f[p] - lap / h2;
+            }
+    } else {
+        for (int64_t k = 0; k <= n; ++k)
+            for (int64_t j = 0; j <= n; ++j)
+                for (int64_t i = 0; i <= n; ++i) {
+                    int64_t p = (k * (n + 1) + j) * (n + 1) + i;
+                    if (i == 0 || j == 0 || k == 0 || i == n || j == n || k == n) { r[p] = 0.0; continue; }
+                    double lap = 6.0 * u_at3(u, n, i, j, k);
+                    lap = lap - u_at3(u, n, i - 1, j, k);
+                    lap = lap - u_at3(u, n, i + 1, j, k);
+                    lap = lap - u_at3(u, n, i, j - 1, k);
+                    lap = lap - u_at3(u, n, i, j + 1, k);
+                    lap = lap - u_at3(u, n, i, j, k - 1);
+                    lap = lap - u_at3(u, n, i, j, k + 1);
+                    r[p] = f[p] - lap / h2;
+                }
+    }
+}
+
+/* Euclidean norm over the interior nodes, summed in layout order (reading A7: relative 2-norm). */
+double homg_oracle_norm_interior(int ndim, int64_t n, const double *v) {
+    double s = 0.0;
+    if (ndim == 2) {
+        for (int64_t j = 1; j < n; ++j)
+            for (int64_t i = 1; i < n; ++i) { double x = v[j * (n + 1) + i]; s += x * x; }
+    } else {
+        for (int64_t k = 1; k < n; ++k)
+            for (int64_t j = 1; j < n; ++j)
+                for (int64_t i = 1; i < n; ++i) { double x = v[(k * (n + 1) + j) * (n + 1) + i]; s += x * x; }
+    }
+    return sqrt(s);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Restriction P (Sec. 2: restrictions are linearly weighted averages of neighbouring sources,   */
+/* done once per cycle as nested reductions over the mesh; reading A4: full weighting, the       */
+/* adjoint of (bi/tri)linear interpolation). Compact level-m array (nf intervals per side) to    */
+/* compact level-(m+1) array (nf/2 intervals). Boundary of the coarse array is 0.               */
+/* 2-D: Fc = (4c + 2(((w+e)+s)+n) + (((sw+se)+nw)+ne)) / 16                                      */
+/* 3-D: Fc = (8c + 4*faces + 2*edges + corners) / 64, each group summed in a fixed order.         */
+/* ------------------------------------------------------------------------------------------ */
+void homg_oracle_restrict(int ndim, int64_t nf, const double *Ff, double *Fc) {
+    const int64_t nc = nf / 2;
+    if (ndim == 2) {
+#define FF(I, J) Ff[(J) * (nf + 1) + (I)]
+        for (int64_t J = 0; J <= nc; ++J)
+            for (int64_t I = 0; I <= nc; ++I) {
+                int64_t q = J * (nc + 1) + I;
+                if (I == 0 || J == 0 || I == nc || J == nc) { Fc[q] = 0.0; continue; }
+                int64_t i = 2 * I, j = 2 * J;
+                double c = FF(i, j);
+                double edges = ((FF(i - 1, j) + FF(i + 1, j)) + FF(i, j - 1)) + FF(i, j + 1);
+                double corners = ((FF(i - 1, j - 1) + FF(i + 1, j - 1)) + FF(i - 1, j + 1)) + FF(i + 1, j + 1);
+                Fc[q] = (4.0 * c + 2.0 * edges + corners) / 16.0;
+            }
+#undef FF
+    } else {
+#define FF(I, J, K) Ff[((K) * (nf + 1) + (J)) * (nf + 1) + (I)]
+        for (int64_t K = 0; K <= nc; ++K)
+            for (int64_t J = 0; J <= nc; ++J)
+                for (int64_t I = 0; I <= nc; ++I) {
+                    int64_t q = (K * (nc + 1) + J) * (nc + 1) + I;
+                    if (I == 0 || J == 0 || K == 0 || I == nc || J == nc || K == nc) { Fc[q] = 0.0; continue; }
+                    int64_t i = 2 * I, j = 2 * J, k = 2 * K;
+                    double c = FF(i, j, k);
+                    double faces = 0.0, edges = 0.0, corners = 0.0;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                int nz = (dx != 0) + (dy != 0) + (dz != 0);
+                                double v = FF(i + dx, j + dy, k + dz);
+                                if (nz == 1) faces = faces + v;
+                                else if (nz == 2) edges = edges + v;
+                                else if (nz == 3) corners = corners + v;
+                            }
+                    Fc[q] = (8.0 * c + 4.0 * faces + 2.0 * edges + corners) / 64.0;
+                }
+#undef FF
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Interpolation S (Sec. 2: linear interpolation; Sec. 4, Fig. 3 "pyramid"): the value at node   */
+/* (i,j[,k]) of the (bi/tri)linear interpolant of the compact level-mp array d (stride           */
+/* lp = 2^mp). Weights are the exact dyadic fractions (lp-a)/lp and a/lp per direction.          */
+/* 2-D order: (w00*d00 + w10*d10) + (w01*d01 + w11*d11)                                          */
+/* ------------------------------------------------------------------------------------------ */
+static double interp2(const double *d, int64_t n, int mp, int64_t i, int64_t j) {
+    const int64_t lp = (int64_t)1 << mp, nc = n >> mp;
+    int64_t I0 = i / lp, a = i - I0 * lp;
+    int64_t J0 = j / lp, b = j - J0 * lp;
+    int64_t I1 = (a == 0) ? I0 : I0 + 1, J1 = (b == 0) ? J0 : J0 + 1;
+    double wx0 = (double)(lp - a) / (double)lp, wx1 = (double)a / (double)lp;
+    double wy0 = (double)(lp - b) / (double)lp, wy1 = (double)b / (double)lp;
+    double d00 = d[J0 * (nc + 1) + I0], d10 = d[J0 * (nc + 1) + I1];
+    double d01 = d[J1 * (nc + 1) + I0], d11 = d[J1 * (nc + 1) + I1];
+    return ((wx0 * wy0) * d00 + (wx1 * wy0) * d10) + ((wx0 * wy1) * d01 + (wx1 * wy1) * d11);
+}
+
+/* 3-D order: ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), cXYZ = w*d. */
+static double interp3(const double *d, int64_t n, int mp, int64_t i, int64_t j, int64_t k) {
+    const int64_t lp = (int64_t)1 << mp, nc = n >> mp;
+    int64_t I0 = i / lp, a = i - I0 * lp;
+    int64_t J0 = j / lp, b = j - J0 * lp;
+    int64_t K0 = k / lp, c = k - K0 * lp;
+    int64_t I1 = (a == 0) ? I0 : I0 + 1, J1 = (b == 0) ? J0 : J0 + 1, K1 = (c == 0) ? K0 : K0 + 1;
+    double wx[2] = {(double)(lp - a) / (double)lp, (double)a / (double)lp};
+    double wy[2] = {(double)(lp - b) / (double)lp, (double)b / (double)lp};
+    double wz[2] = {(double)(lp - c) / (double)lp, (double)c / (double)lp};
+    int64_t Ix[2] = {I0, I1}, Jy[2] = {J0, J1}, Kz[2] = {K0, K1};
+    double t[2][2][2];
+    for (int z = 0; z < 2; ++z)
+        for (int y = 0; y < 2; ++y)
+            for (int x = 0; x < 2; ++x)
+                t[z][y][x] = ((wx[x] * wy[y]) * wz[z]) * d[(Kz[z] * (nc + 1) + Jy[y]) * (nc + 1) + Ix[x]];
+    return ((t[0][0][0] + t[0][0][1]) + (t[0][1][0] + t[0][1][1])) +
+           ((t[1][0][0] + t[1][0][1]) + (t[1][1][0] + t[1][1][1]));
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* One HOMG iteration (Sec. 2: relaxation on the level-m lattice fused with interpolation of the  */
+/* previous iteration's variations on the rest of the grid; Sec. 4: the interpolation is         */
+/* delayed by one iteration because both run in parallel).                                        */
+/*                                                                                              */
+/*   for p in L_m:   delta(p) = omega * (h_m^2 F_m(p) - lap_m(e_old)(p))                          */
+/*                   (damped Jacobi = explicit Euler of Eq. "heat" at level m, sign-consistent     */
+/*                    for A = -Laplacian; lap_m uses neighbours at distance l = 2^m)               */
+/*   e_new(p) = e_old(p) + [p in L_m] delta(p) + [p not in L_mprev] (S_mprev dprev)(p)            */
+/*                                                                                              */
+/* Every term reads only e_old (Jacobi). mprev < 0 means "no pending variation" (first iteration */
+/* of a cycle). F_m and d_new are compact level-m arrays; dprev is a compact level-mprev array.   */
+/* d_new receives delta on L_m and 0 on the lattice boundary.                                     */
+/* ------------------------------------------------------------------------------------------ */
+static void iteration2(int64_t n, int m, int mprev, double omega, const double *Fm, const double *dprev,
+                       const double *e_old, double *e_new, double *d_new) {
+    const int64_t l = (int64_t)1 << m, nm = n >> m, side = n + 1;
+    const int64_t lp = (mprev >= 0) ? ((int64_t)1 << mprev) : 1;
+    const double h = 1.0 / (double)n;
+    const double hm = h * (double)l;
+    const double hm2 = hm * hm;
+    for (int64_t q = 0; q < (nm + 1) * (nm + 1); ++q) d_new[q] = 0.0;
+    for (int64_t j = 0; j <= n; ++j)
+        for (int64_t i = 0; i <= n; ++i) {
+            int64_t p = j * side + i;
+            if (i == 0 || j == 0 || i == n || j == n) { e_new[p] = 0.0; continue; }
+            double v = e_old[p];
+            if (i % l == 0 && j % l == 0) {
+                double lap = 4.0 * v;
+                lap = lap - e_old[j * side + (i - l)];
+                lap = lap - e_old[j * side + (i + l)];
+                lap = lap - e_old[(j - l) * side + i];
+                lap = lap - e_old[(j + l) * side + i];
+                int64_t q = (j / l) * (nm + 1) + (i / l);
+                double delta = omega * (hm2 * Fm[q] - lap);
+                d_new[q] = delta;
+                v = v + delta;
+            }
+            if (mprev >= 0 && !(i % lp == 0 && j % lp == 0)) v = v + interp2(dprev, n, mprev, i, j);
+            e_new[p] = v;
+        }
+}
+
+static void iteration3(int64_t n, int m, int mprev, double omega, const double *Fm, const double *dprev,
+                       const double *e_old, double *e_new, double *d_new) {
+    const int64_t l = (int64_t)1 << m, nm = n >> m, side = n + 1;
+    const int64_t lp = (mprev >= 0) ? ((int64_t)1 << mprev) : 1;
+    const double h = 1.0 / (double)n;
+    const double hm = h * (double)l;
+    const double hm2 = hm * hm;
+    for (int64_t q = 0; q < (nm + 1) * (nm + 1) * (nm + 1); ++q) d_new[q] = 0.0;
+    for (int64_t k = 0; k <= n; ++k)
+        for (int64_t j = 0; j <= n; ++j)
+            for (int64_t i = 0; i <= n; ++i) {
+                int64_t p = (k * side + j) * side + i;
+                if (i == 0 || j == 0 || k == 0 || i == n || j == n || k == n) { e_new[p] = 0.0; continue; }
+                double v = e_old[p];
+                if (i % l == 0 && j % l == 0 && k % l == 0) {
+                    double lap = 6.0 * v;
+                    lap = lap - e_old[(k * side + j) * side + (i - l)];
+                    lap = lap - e_old[(k * side + j) * side + (i + l)];
+                    lap = lap - e_old[(k * side + (j - l)) * side + i];
+                    lap = lap - e_old[(k * side + (j + l)) * side + i];
+                    lap = lap - e_old[((k - l) * side + j) * side + i];
+                    lap = lap - e_old[((k + l) * side + j) * side + i];
+                    int64_t q = ((k / l) * (nm + 1) + (j / l)) * (nm + 1) + (i / l);
+                    double delta = omega * (hm2 * Fm[q] - lap);
+                    d_new[q] = delta;
+                    v = v + delta;
+                }
+                if (mprev >= 0 && !(i % lp == 0 && j % lp == 0 && k % lp == 0)) v = v + interp3(dprev, n, mprev, i, j, k);
+                e_new[p] = v;
+            }
+}
+
+void homg_oracle_iteration(int ndim, int64_t n, int m, int mprev, double omega, const double *Fm,
+                           const double *dprev, const double *e_old, double *e_new, double *d_new) {
+    if (ndim == 2) iteration2(n, m, mprev, omega, Fm, dprev, e_old, e_new, d_new);
+    else iteration3(n, m, mprev, omega, Fm, dprev, e_old, e_new, d_new);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* One HOMG cycle on the residual equation A e = F_0 starting from e = 0 (Sec. 2, steps (a)-(c)  */
+/* and the MFMG paragraph). F_0 is the fine residual; F_1..F_{L-1} are built once, before the     */
+/* cycle, by nested full-weighting reductions. The schedule lists the level of every iteration   */
+/* and must end on the finest level, where no variation is left pending.                         */
+/* omega = omega_J / (2 d) is the damped-Jacobi weight per iteration (reading A2).               */
+/* ------------------------------------------------------------------------------------------ */
+int homg_oracle_cycle(int ndim, int64_t n, int levels, const int *sched, int nsched, double omega_j,
+                      const double *F0, double *e) {
+    int K = log2_exact(n);
+    if ((ndim != 2 && ndim != 3) || K < 1 || levels < 1 || levels > K || nsched < 1) return HOMG_ORACLE_EINVAL;
+    for (int t = 0; t < nsched; ++t)
+        if (sched[t] < 0 || sched[t] >= levels) return HOMG_ORACLE_EINVAL;
+    if (sched[nsched - 1] != 0) return HOMG_ORACLE_EINVAL;
+    const double omega = omega_j / (2.0 * ndim);
+    const int64_t side = n + 1;
+    const int64_t total = ipow(side, ndim);
+
+    double **F = (double **)calloc((size_t)levels, sizeof(double *));
+    double *ebuf = (double *)malloc((size_t)total * sizeof(double));
+    double *dA = (double *)malloc((size_t)total * sizeof(double));
+    double *dB = (double *)malloc((size_t)total * sizeof(double));
+    int rc = HOMG_ORACLE_OK;
+    if (!F || !ebuf || !dA || !dB) { rc = HOMG_ORACLE_ENOMEM; goto done; }
+    F[0] = (double *)F0;
+    for (int m = 1; m < levels; ++m) {
+        F[m] = (double *)malloc((size_t)ipow((n >> m) + 1, ndim) * sizeof(double));
+        if (!F[m]) { rc = HOMG_ORACLE_ENOMEM; goto done; }
+        homg_oracle_restrict(ndim, n >> (m - 1), F[m - 1], F[m]);
+    }
+    for (int64_t p = 0; p < total; ++p) e[p] = 0.0;
+    {
+        double *e_old = e, *e_new = ebuf, *dprev = dA, *dnew = dB;
+        int mprev = -1;
+        for (int t = 0; t < nsched; ++t) {
+            int m = sched[t];
+            homg_oracle_iteration(ndim, n, m, mprev, omega, F[m], dprev, e_old, e_new, dnew);
+            double *tmp = e_old; e_old = e_new; e_new = tmp;
+            tmp = dprev; dprev = dnew; dnew = tmp;
+            mprev = m;
+        }
+        if (e_old != e) memcpy(e, e_old, (size_t)total * sizeof(double));
+    }
+done:
+    if (F) for (int m = 1; m < levels; ++m) free(F[m]);
+    free(F); free(ebuf); free(dA); free(dB);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Solver (Sec. 2, last paragraph; Sec. 4: after a cycle the residual equation restarts the      */
+/* cycles as often as needed). u is the initial guess and the result; only interior nodes are     */
+/* read or written. hist[k] (k = 0..cycles) receives ||r_k|| / ||f|| before cycle k+1.            */
+/* Stop when the relative residual <= tol (OK), when it is not finite or grows past              */
+/* div_factor * hist[0] (DIVERGED), or after max_cycles cycles (NOT_CONVERGED).                  */
+/* ||f|| = 0 gives u = 0 (interior), relres = 0, 0 cycles.                                        */
+/* ------------------------------------------------------------------------------------------ */
+int homg_oracle_solve(int ndim, int64_t n, int levels, const int *sched, int nsched, double omega_j,
+                      double div_factor, const double *f, double *u, double tol, int max_cycles,
+                      double *hist, int *cycles_out, double *relres_out) {
+    int K = log2_exact(n);
+    if ((ndim != 2 && ndim != 3) || K < 1 || levels < 1 || levels > K || max_cycles < 0) return HOMG_ORACLE_EINVAL;
+    const int64_t side = n + 1;
+    const int64_t total = ipow(side, ndim);
+    double fnorm = homg_oracle_norm_interior(ndim, n, f);
+    if (fnorm == 0.0) {
+        for (int64_t p = 0; p < total; ++p) {
+            int64_t i = p % side, j = (p / side) % side, k = (ndim == 3) ? p / (side * side) : 1;
+            if (i > 0 && j > 0 && k > 0 && i < n && j < n && k < n) u[p] = 0.0;
+        }
+        if (hist) hist[0] = 0.0;
+        if (cycles_out) *cycles_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        return HOMG_ORACLE_OK;
+    }
+    double *r = (double *)malloc((size_t)total * sizeof(double));
+    double *e = (double *)malloc((size_t)total * sizeof(double));
+    if (!r || !e) { free(r); free(e); return HOMG_ORACLE_ENOMEM; }
+    int status = HOMG_ORACLE_NOT_CONVERGED, k;
+    double rr = 0.0, rr0 = 0.0;
+    for (k = 0;; ++k) {
+        homg_oracle_residual(ndim, n, f, u, r);
+        rr = homg_oracle_norm_interior(ndim, n, r) / fnorm;
+        if (hist) hist[k] = rr;
+        if (k == 0) rr0 = rr;
+        if (rr <= tol) { status = HOMG_ORACLE_OK; break; }
+        if (!isfinite(rr) || rr > div_factor * rr0) { status = HOMG_ORACLE_DIVERGED; break; }
+        if (k == max_cycles) { status = HOMG_ORACLE_NOT_CONVERGED; break; }
+        int rc = homg_oracle_cycle(ndim, n, levels, sched, nsched, omega_j, r, e);
+        if (rc != HOMG_ORACLE_OK) { free(r); free(e); return rc; }
+        for (int64_t p = 0; p < total; ++p) {
+            int64_t i = p % side, j = (p / side) % side, kk = (ndim == 3) ? p / (side * side) : 1;
+            if (i > 0 && j > 0 && kk > 0 && i < n && j < n && kk < n) u[p] = u[p] + e[p];
+        }
+    }
+    free(r); free(e);
+    if (cycles_out) *cycles_out = k;
+    if (relres_out) *relres_out = rr;
+    return status;
+}

@@ -1,0 +1,165 @@
+"""numpy wrappers around the C oracle (``homg_oracle.c``) -- TEST INFRASTRUCTURE ONLY.
+
+Arrays are FP64, C-contiguous, node grids of shape (n+1, n+1) or (n+1, n+1, n+1) indexed
+[j, i] / [k, j, i] (x fastest), n = 2^K. Compact level-m arrays have side n/2^m + 1.
+"""
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "homg_oracle.c")
+_LIB = os.path.join(_HERE, "libhomg_oracle.so")
+_lib = None
+
+OK, NOT_CONVERGED, DIVERGED = 0, 1, 2
+
+
+def build(force=False):
+    """Compile the oracle with gcc into ``oracle/libhomg_oracle.so`` (plain -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load(path=None):
+    global _lib
+    if _lib is None or path is not None:
+        lib = ctypes.CDLL(path or build())
+        P = ctypes.POINTER(ctypes.c_double)
+        IP = ctypes.POINTER(ctypes.c_int)
+        i64 = ctypes.c_int64
+        lib.homg_oracle_mfmg_schedule.argtypes = [ctypes.c_int, ctypes.c_int, IP, ctypes.c_int]
+        lib.homg_oracle_residual.argtypes = [ctypes.c_int, i64, P, P, P]
+        lib.homg_oracle_norm_interior.argtypes = [ctypes.c_int, i64, P]
+        lib.homg_oracle_norm_interior.restype = ctypes.c_double
+        lib.homg_oracle_restrict.argtypes = [ctypes.c_int, i64, P, P]
+        lib.homg_oracle_iteration.argtypes = [ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              P, P, P, P, P]
+        lib.homg_oracle_cycle.argtypes = [ctypes.c_int, i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double, P, P]
+        lib.homg_oracle_solve.argtypes = [ctypes.c_int, i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, P, P, ctypes.c_double, ctypes.c_int, P, IP, P]
+        _lib = lib
+    return _lib
+
+
+class using_library:
+    """Context manager: route every wrapper through another build of ``homg_oracle.c`` (used by the
+    mutation test, which plants mistakes in copies of the oracle to show that the pins catch them)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _load(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _grid_n(a):
+    n = a.shape[0] - 1
+    assert all(s == n + 1 for s in a.shape) and a.ndim in (2, 3), a.shape
+    return a.ndim, n
+
+
+def default_omega_j(ndim):
+    """Reading A2: the classic optimal smoothing weight of damped Jacobi, 4/5 (2-D) or 6/7 (3-D)."""
+    return 4.0 / 5.0 if ndim == 2 else 6.0 / 7.0
+
+
+def mfmg_schedule(levels, max_i=32):
+    """Level of every iteration of one MFMG cycle (Sec. 2): coarsest first, 2 iterations, doubling, capped."""
+    lib = _load()
+    cnt = lib.homg_oracle_mfmg_schedule(levels, max_i, None, 0)
+    if cnt < 0:
+        raise ValueError("invalid levels/max_i")
+    out = (ctypes.c_int * cnt)()
+    lib.homg_oracle_mfmg_schedule(levels, max_i, out, cnt)
+    return list(out)
+
+
+def residual(f, u):
+    """r = f - A_h u on interior nodes, 0 on the boundary."""
+    ndim, n = _grid_n(f)
+    r = np.empty_like(f)
+    _load().homg_oracle_residual(ndim, n, _p(f), _p(u), _p(r))
+    return r
+
+
+def norm_interior(v):
+    ndim, n = _grid_n(v)
+    return _load().homg_oracle_norm_interior(ndim, n, _p(v))
+
+
+def restrict(Ff):
+    """Full weighting of a compact array with nf intervals per side onto nf/2 intervals."""
+    ndim, nf = _grid_n(Ff)
+    Fc = np.empty((nf // 2 + 1,) * ndim)
+    _load().homg_oracle_restrict(ndim, nf, _p(Ff), _p(Fc))
+    return Fc
+
+
+def iteration(n, m, mprev, omega, Fm, dprev, e_old):
+    """One HOMG iteration at level m with the pending variation of level mprev (None: none).
+
+    Returns (e_new, d_new) where d_new is the compact level-m variation.
+    """
+    ndim = e_old.ndim
+    e_new = np.empty_like(e_old)
+    d_new = np.empty(((n >> m) + 1,) * ndim)
+    if dprev is None:
+        dprev = np.zeros(1)
+        mprev = -1
+    _load().homg_oracle_iteration(ndim, n, m, mprev, omega, _p(Fm), _p(dprev), _p(e_old), _p(e_new), _p(d_new))
+    return e_new, d_new
+
+
+def cycle(F0, levels, schedule=None, max_i=32, omega_j=None):
+    """One HOMG cycle on A e = F0 from e = 0; returns e."""
+    ndim, n = _grid_n(F0)
+    if omega_j is None:
+        omega_j = default_omega_j(ndim)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    e = np.empty_like(F0)
+    rc = _load().homg_oracle_cycle(ndim, n, levels, cs, len(sched), omega_j, _p(np.ascontiguousarray(F0)), _p(e))
+    if rc != 0:
+        raise ValueError("oracle cycle rejected its arguments (rc=%d)" % rc)
+    return e
+
+
+def solve(f, levels, u0=None, tol=1e-10, max_cycles=100, schedule=None, max_i=32, omega_j=None,
+          div_factor=1e3):
+    """Restarted HOMG solve. Returns (u, status, cycles, hist) with hist[k] = ||r_k|| / ||f||."""
+    ndim, n = _grid_n(f)
+    if omega_j is None:
+        omega_j = default_omega_j(ndim)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    u = np.zeros_like(f) if u0 is None else np.array(u0, dtype=np.float64, order="C", copy=True)
+    hist = np.zeros(max_cycles + 1)
+    cyc = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    status = _load().homg_oracle_solve(ndim, n, levels, cs, len(sched), omega_j, div_factor,
+                                       _p(np.ascontiguousarray(f)), _p(u), tol, max_cycles, _p(hist),
+                                       ctypes.byref(cyc), ctypes.byref(rr))
+    if status < 0:
+        raise ValueError("oracle solve rejected its arguments (rc=%d)" % status)
+    return u, status, cyc.value, hist[: cyc.value + 1]

@@ -1,0 +1,76 @@
+"""Seeded synthetic inputs for the HOMG solver and its tests.
+
+This module holds no multigrid arithmetic: it only produces right-hand sides (and, for tests, the
+continuous solutions they come from) on node grids of (n+1)^d nodes, n = 2^K, h = 1/n, indexed
+[j, i] / [k, j, i] with x fastest. Boundary nodes are 0. Both the GPU path and the CPU oracle
+consume these arrays; neither produces them.
+
+Workloads (stand-ins for the paper's Poisson experiments of Sec. 4; the paper uses no dataset):
+* ``sine_rhs``     f = d pi^2 prod_k sin(pi x_k), whose continuous solution is prod_k sin(pi x_k).
+* ``uniform_rhs``  f iid uniform[-1, 1] over the interior nodes in layout order, numpy
+                   ``default_rng(seed)`` (seed 0 for the 4097^2 benchmark grid).
+* ``normal_rhs``   f iid N(0, 1), same ordering.
+* ``paper_poly_rhs`` / ``paper_poly_solution``: the polynomial test problem of Sec. 4, converted
+                   to A = -Laplacian (the paper states Laplacian(u) = f, so f here is minus the
+                   paper's source and the solution is the paper's u).
+"""
+
+import numpy as np
+
+
+def node_coords(n, ndim):
+    """Coordinates x_k of every node, as a list of ndim broadcastable arrays ([..., i] = x)."""
+    x = np.arange(n + 1, dtype=np.float64) / n
+    if ndim == 2:
+        return [x[None, :], x[:, None]]
+    return [x[None, None, :], x[None, :, None], x[:, None, None]]
+
+
+def _zero_boundary(a):
+    a[(0, -1), ...] = 0.0
+    a[:, (0, -1)] = 0.0
+    if a.ndim == 3:
+        a[:, :, (0, -1)] = 0.0
+    return a
+
+
+def sine_solution(n, ndim=2):
+    xs = node_coords(n, ndim)
+    u = np.ones((n + 1,) * ndim)
+    for x in xs:
+        u = u * np.sin(np.pi * x)
+    return _zero_boundary(np.ascontiguousarray(u))
+
+
+def sine_rhs(n, ndim=2):
+    """f = d pi^2 prod sin(pi x_k) (cfg: 129^2 with 7 levels; 513^3 with 9 levels)."""
+    return _zero_boundary(ndim * np.pi ** 2 * sine_solution(n, ndim))
+
+
+def uniform_rhs(n, ndim=2, seed=0):
+    """f iid uniform[-1, 1] on interior nodes in layout order from ``default_rng(seed)``."""
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n + 1,) * ndim)
+    f[(slice(1, -1),) * ndim] = rng.uniform(-1.0, 1.0, size=(n - 1,) * ndim)
+    return f
+
+
+def normal_rhs(n, ndim=2, seed=0):
+    """f iid N(0, 1) on interior nodes in layout order from ``default_rng(seed)``."""
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n + 1,) * ndim)
+    f[(slice(1, -1),) * ndim] = rng.standard_normal(size=(n - 1,) * ndim)
+    return f
+
+
+def paper_poly_solution(n):
+    """u = -x^2 y^2 (1 - x^2)(1 - y^2), the analytic solution of the paper's test problem (Sec. 4)."""
+    x, y = node_coords(n, 2)
+    return np.ascontiguousarray(-(x ** 2) * y ** 2 * (1 - x ** 2) * (1 - y ** 2))
+
+
+def paper_poly_rhs(n):
+    """Right-hand side for A = -Laplacian whose solution is ``paper_poly_solution`` (Sec. 4, Eq. for the source, sign flipped)."""
+    x, y = node_coords(n, 2)
+    f_paper = -2.0 * (y ** 2 * (1 - 6 * x ** 2) * (1 - y ** 2) + x ** 2 * (1 - 6 * y ** 2) * (1 - x ** 2))
+    return _zero_boundary(np.ascontiguousarray(-f_paper + 0.0 * x * y))

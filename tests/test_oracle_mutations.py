@@ -1,0 +1,84 @@
+"""Plant plausible mistakes in copies of the oracle (on the CPU) and check the pins catch each one.
+
+Every mutation below is a slip one could make when restating the paper: a sign, a stride, a
+weight, a transposed index, a dropped term, the one-iteration delay, the schedule rule. The test
+compiles the mutated C source into a temporary library, routes the oracle wrappers through it and
+runs a representative subset of the pins of ``test_oracle_pins.py``; at least one must fail.
+"""
+
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from oracle import oracle as oracle_impl
+
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "homg_oracle.c")
+
+MUTATIONS = {
+    "residual_sign": ("r[p] = f[p] - lap / h2;", "r[p] = f[p] + lap / h2;"),
+    "residual_dropped_neighbour": ("lap = lap - u_at2(u, n, i, j + 1);", ""),
+    "restrict_edge_weight": ("(4.0 * c + 2.0 * edges + corners) / 16.0", "(4.0 * c + 1.0 * edges + corners) / 16.0"),
+    "restrict_corner_index": ("FF(i - 1, j + 1)) + FF(i + 1, j + 1)", "FF(i - 1, j + 1)) + FF(i + 1, j)"),
+    "restrict3_face_weight": ("(8.0 * c + 4.0 * faces", "(8.0 * c + 2.0 * faces"),
+    "relax_stride": ("lap = lap - e_old[j * side + (i - l)];", "lap = lap - e_old[j * side + (i - 1)];"),
+    "relax_sign": ("double delta = omega * (hm2 * Fm[q] - lap);", "double delta = omega * (lap - hm2 * Fm[q]);"),
+    "relax_level_spacing": ("const double hm = h * (double)l;", "const double hm = h;"),
+    "interp_weight_transposed": ("(wx1 * wy0) * d10", "(wx0 * wy1) * d10"),
+    "interp_corner_swapped": ("d10 = d[J0 * (nc + 1) + I1]", "d10 = d[J1 * (nc + 1) + I0]"),
+    "no_interpolation_delay_mask": ("if (mprev >= 0 && !(i % lp == 0 && j % lp == 0))", "if (mprev >= 0)"),
+    "schedule_start_count": ("int64_t nm = 2;", "int64_t nm = 1;"),
+    "omega_per_dimension": ("const double omega = omega_j / (2.0 * ndim);", "const double omega = omega_j / 4.0;"),
+    "update_sign": ("u[p] = u[p] + e[p];", "u[p] = u[p] - e[p];"),
+    "norm_not_squared": ("double x = v[j * (n + 1) + i]; s += x * x;", "double x = v[j * (n + 1) + i]; s += fabs(x);"),
+}
+
+
+def run_pins():
+    """Run a representative subset of the pins; return the names of those that failed."""
+    checks = [
+        ("schedule", lambda: pins.test_mfmg_schedule_rule()),
+        ("residual_closed_form", lambda: pins.test_residual_closed_form(2, 16)),
+        ("residual_dense", lambda: pins.test_residual_matches_dense(2, 8)),
+        ("restrict_sine", lambda: pins.test_restrict_sine_closed_form(2, 32)),
+        ("restrict3_sine", lambda: pins.test_restrict_sine_closed_form(3, 16)),
+        ("adjoint", lambda: pins.test_restrict_is_adjoint_of_interpolation(2, 16)),
+        ("multilinear", lambda: pins.test_interpolation_reproduces_multilinear(2, 32, 3)),
+        ("relax_level", lambda: pins.test_level_relaxation_closed_form(2, 64, 2)),
+        ("relax3_level", lambda: pins.test_level_relaxation_closed_form(3, 16, 1)),
+        ("jacobi_cycle", lambda: pins.test_single_level_cycle_is_damped_jacobi(2, 32, 7)),
+        ("fig3", lambda: pins.test_fig3_spike_stall_pyramid()),
+        ("eigen_solution", lambda: pins.test_solution_matches_discrete_eigen_closed_form(2, 5)),
+        ("eigen_solution3", lambda: pins.test_solution_matches_discrete_eigen_closed_form(3, 4)),
+        ("dense_solve", lambda: pins.test_solution_matches_dense_direct_solve(2, 3)),
+        ("decrease", lambda: pins.test_residual_decreases_every_cycle("uniform")),
+    ]
+    failed = []
+    for name, fn in checks:
+        try:
+            fn()
+        except (AssertionError, ValueError):
+            failed.append(name)
+    return failed
+
+
+def test_unmutated_oracle_passes_the_subset():
+    assert run_pins() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutation anchor not found: " + old
+    mutated = src.replace(old, new, 1)
+    c = tmp_path / "mut.c"
+    so = tmp_path / "libmut.so"
+    c.write_text(mutated)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", str(so), str(c), "-lm"])
+    with oracle_impl.using_library(str(so)):
+        failed = run_pins()
+    assert failed, "no pin caught mutation " + name
