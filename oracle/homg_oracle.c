@@ -195,8 +195,9 @@ void homg_oracle_restrict(int ndim, int64_t nf, const double *Ff, double *Fc) {
 /* ------------------------------------------------------------------------------------------ */
 static double interp2(const double *d, int64_t n, int mp, int64_t i, int64_t j) {
     const int64_t lp = (int64_t)1 << mp, nc = n >> mp;
-    int64_t I0 = i / lp, a = i - I0 * lp;
-    int64_t J0 = j / lp, b = j - J0 * lp;
+    /* lp is a power of two: i / lp == i >> mp and i % lp == i & (lp - 1) */
+    int64_t I0 = i >> mp, a = i & (lp - 1);
+    int64_t J0 = j >> mp, b = j & (lp - 1);
     int64_t I1 = (a == 0) ? I0 : I0 + 1, J1 = (b == 0) ? J0 : J0 + 1;
     double wx0 = (double)(lp - a) / (double)lp, wx1 = (double)a / (double)lp;
     double wy0 = (double)(lp - b) / (double)lp, wy1 = (double)b / (double)lp;
@@ -208,9 +209,9 @@ static double interp2(const double *d, int64_t n, int mp, int64_t i, int64_t j) 
 /* 3-D order: ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), cXYZ = w*d. */
 static double interp3(const double *d, int64_t n, int mp, int64_t i, int64_t j, int64_t k) {
     const int64_t lp = (int64_t)1 << mp, nc = n >> mp;
-    int64_t I0 = i / lp, a = i - I0 * lp;
-    int64_t J0 = j / lp, b = j - J0 * lp;
-    int64_t K0 = k / lp, c = k - K0 * lp;
+    int64_t I0 = i >> mp, a = i & (lp - 1);
+    int64_t J0 = j >> mp, b = j & (lp - 1);
+    int64_t K0 = k >> mp, c = k & (lp - 1);
     int64_t I1 = (a == 0) ? I0 : I0 + 1, J1 = (b == 0) ? J0 : J0 + 1, K1 = (c == 0) ? K0 : K0 + 1;
     double wx[2] = {(double)(lp - a) / (double)lp, (double)a / (double)lp};
     double wy[2] = {(double)(lp - b) / (double)lp, (double)b / (double)lp};
@@ -252,18 +253,18 @@ static void iteration2(int64_t n, int m, int mprev, double omega, const double *
             int64_t p = j * side + i;
             if (i == 0 || j == 0 || i == n || j == n) { e_new[p] = 0.0; continue; }
             double v = e_old[p];
-            if (i % l == 0 && j % l == 0) {
+            if ((i & (l - 1)) == 0 && (j & (l - 1)) == 0) { /* p on the level-m lattice */
                 double lap = 4.0 * v;
                 lap = lap - e_old[j * side + (i - l)];
                 lap = lap - e_old[j * side + (i + l)];
                 lap = lap - e_old[(j - l) * side + i];
                 lap = lap - e_old[(j + l) * side + i];
-                int64_t q = (j / l) * (nm + 1) + (i / l);
+                int64_t q = (j >> m) * (nm + 1) + (i >> m);
                 double delta = omega * (hm2 * Fm[q] - lap);
                 d_new[q] = delta;
                 v = v + delta;
             }
-            if (mprev >= 0 && !(i % lp == 0 && j % lp == 0)) v = v + interp2(dprev, n, mprev, i, j);
+            if (mprev >= 0 && !((i & (lp - 1)) == 0 && (j & (lp - 1)) == 0)) v = v + interp2(dprev, n, mprev, i, j);
             e_new[p] = v;
         }
 }
@@ -282,7 +283,7 @@ static void iteration3(int64_t n, int m, int mprev, double omega, const double *
                 int64_t p = (k * side + j) * side + i;
                 if (i == 0 || j == 0 || k == 0 || i == n || j == n || k == n) { e_new[p] = 0.0; continue; }
                 double v = e_old[p];
-                if (i % l == 0 && j % l == 0 && k % l == 0) {
+                if ((i & (l - 1)) == 0 && (j & (l - 1)) == 0 && (k & (l - 1)) == 0) { /* p on the level-m lattice */
                     double lap = 6.0 * v;
                     lap = lap - e_old[(k * side + j) * side + (i - l)];
                     lap = lap - e_old[(k * side + j) * side + (i + l)];
@@ -290,12 +291,12 @@ static void iteration3(int64_t n, int m, int mprev, double omega, const double *
                     lap = lap - e_old[(k * side + (j + l)) * side + i];
                     lap = lap - e_old[((k - l) * side + j) * side + i];
                     lap = lap - e_old[((k + l) * side + j) * side + i];
-                    int64_t q = ((k / l) * (nm + 1) + (j / l)) * (nm + 1) + (i / l);
+                    int64_t q = ((k >> m) * (nm + 1) + (j >> m)) * (nm + 1) + (i >> m);
                     double delta = omega * (hm2 * Fm[q] - lap);
                     d_new[q] = delta;
                     v = v + delta;
                 }
-                if (mprev >= 0 && !(i % lp == 0 && j % lp == 0 && k % lp == 0)) v = v + interp3(dprev, n, mprev, i, j, k);
+                if (mprev >= 0 && !((i & (lp - 1)) == 0 && (j & (lp - 1)) == 0 && (k & (lp - 1)) == 0)) v = v + interp3(dprev, n, mprev, i, j, k);
                 e_new[p] = v;
             }
 }

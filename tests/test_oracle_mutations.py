@@ -29,7 +29,8 @@ MUTATIONS = {
     "relax_level_spacing": ("const double hm = h * (double)l;", "const double hm = h;"),
     "interp_weight_transposed": ("(wx1 * wy0) * d10", "(wx0 * wy1) * d10"),
     "interp_corner_swapped": ("d10 = d[J0 * (nc + 1) + I1]", "d10 = d[J1 * (nc + 1) + I0]"),
-    "no_interpolation_delay_mask": ("if (mprev >= 0 && !(i % lp == 0 && j % lp == 0))", "if (mprev >= 0)"),
+    "no_interpolation_delay_mask": ("if (mprev >= 0 && !((i & (lp - 1)) == 0 && (j & (lp - 1)) == 0))", "if (mprev >= 0)"),
+    "lattice_mask_wrong_stride": ("if ((i & (l - 1)) == 0 && (j & (l - 1)) == 0) {", "if ((i & (l - 1)) == 0 && (j & (lp - 1)) == 0) {"),
     "schedule_start_count": ("int64_t nm = 2;", "int64_t nm = 1;"),
     "omega_per_dimension": ("const double omega = omega_j / (2.0 * ndim);", "const double omega = omega_j / 4.0;"),
     "update_sign": ("u[p] = u[p] + e[p];", "u[p] = u[p] - e[p];"),
