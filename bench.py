@@ -1,0 +1,328 @@
+"""Benchmark: unknowns solved per second to relative residual 1e-10 with the GB300 HOMG solver.
+
+Workload: 2-D Poisson, 5-point stencil, 4097^2 nodes (h = 1/4096), 12 levels, FP64, f iid
+uniform[-1, 1] over the interior from numpy default_rng(0), u0 = 0, MFMG cycles with MaxI = 32,
+restarted until ||f - A u|| / ||f|| <= 1e-10. One step = one complete solve (zeroing u, then
+``homg_solve``). The working set (about 0.8 GB) exceeds the 126 MB L2, so no flush is needed.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle instead (the reference arm
+of this benchmark, since the paper publishes no code).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unknowns solved/sec to 1e-10 rel residual"
+UNIT = "unknowns/s"
+N_SIDE = 4096
+LEVELS = 12
+TOL = 1e-10
+MAX_I = 32
+MAX_CYCLES = 60
+WORKLOAD = ("2-D Poisson -Lap u = f, 5-point, 4097x4097 nodes, 12 levels, FP64, f iid uniform[-1,1] "
+            "(default_rng(0)), u0 = 0, HOMG MFMG MaxI=32, to relative residual 1e-10")
+
+# Peaks for the roofline (denominators).
+FALLBACK_HBM_GBS = 6800.0
+# FP64 issue rate: nominal 1.25 TFLOP/s (FMA = 2 flops) = 0.625e12 FP64 instructions/s,
+# i.e. 2 FP64 instructions per clock per SM x 152 SMs x 2.07 GHz.
+FP64_PEAK_OPS = 0.625e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_cpu_baseline(f_np, cycles):
+    """The oracle as it stands, single-threaded on a host core: one cycle on the benchmark grid
+    (residual + restriction + 286 HOMG iterations), scaled by the solve's cycle count."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.solve(f_np, LEVELS, tol=0.0, max_cycles=1, max_i=MAX_I)
+    dt = time.perf_counter() - t0
+    t_solve = dt * cycles
+    return {"value": (N_SIDE - 1) ** 2 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one oracle cycle on the 4097^2 grid (%.1f s), scaled by the %d cycles a solve takes" % (dt, cycles)}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1108_2045_gb300 import inputs
+
+    oracle.build()
+    f = inputs.uniform_rhs(N_SIDE, 2, seed=0)
+    # cycle count of the full solve (resolution-independent contraction): from the oracle at 1025^2
+    fs = inputs.uniform_rhs(1024, 2, seed=0)
+    _, _, cycles, _ = oracle.solve(fs, 10, tol=TOL, max_cycles=MAX_CYCLES, max_i=MAX_I)
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.solve(f, LEVELS, tol=0.0, max_cycles=1, max_i=MAX_I)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt * cycles)
+    total = sum(times)
+    value = (N_SIDE - 1) ** 2 * args.steps / total
+    sample = ("each step: one oracle cycle on the 4097^2 grid, scaled by the %d cycles the solve needs "
+              "(cycle count from the oracle's full solve at 1025^2)" % cycles)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1108_2045_gb300 import homg, inputs
+
+    dev = torch.device("cuda", local)
+    f_np = inputs.uniform_rhs(N_SIDE, 2, seed=0)
+    f = torch.from_numpy(f_np).to(dev)
+    u = torch.zeros_like(f)
+    stream = torch.cuda.current_stream(dev)
+    solver = homg.Solver(2, N_SIDE + 1, LEVELS, max_i=MAX_I, exec_mode=args.exec)
+    solver.set_stream(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step():
+        u.zero_()
+        status, cycles, relres = solver.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+        if status != homg.HOMG_OK:
+            raise RuntimeError("solve did not converge: status %d after %d cycles (relres %.3e)" % (status, cycles, relres))
+        return cycles, relres
+
+    for _ in range(args.warmup):
+        step()
+    # timed region: K device-resident solves
+    stats = []
+    barrier()
+    with ClockSampler(local) as clocks:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            cycles, relres = step()
+            stats.append(solver.stats())
+        t1.record(stream)
+        barrier()
+    elapsed_ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    unknowns = (N_SIDE - 1) ** 2
+    value = unknowns * args.steps * world / (elapsed_ms * 1e-3)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    f_host = torch.from_numpy(f_np).pin_memory()
+    u_host = torch.zeros_like(f_host).pin_memory()
+    solver.solve_host(f_host, u_host, tol=TOL, max_cycles=MAX_CYCLES)
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        u_host.zero_()
+        st, _, _ = solver.solve_host(f_host, u_host, tol=TOL, max_cycles=MAX_CYCLES)
+        if st != homg.HOMG_OK:
+            raise RuntimeError("host solve did not converge")
+    barrier()
+    e2e_s = time.perf_counter() - e0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    grid_bytes = f_np.nbytes
+
+    # whole-grid form of the same iterates (the paper's one-launch-per-iteration layout), for contrast
+    wg = None
+    if args.wholegrid_steps > 0:
+        with homg.Solver(2, N_SIDE + 1, LEVELS, max_i=MAX_I, exec_mode="wholegrid") as s2:
+            s2.set_stream(stream)
+            u.zero_()
+            s2.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+            ws = []
+            barrier()
+            w0 = torch.cuda.Event(enable_timing=True)
+            w1 = torch.cuda.Event(enable_timing=True)
+            w0.record(stream)
+            for _ in range(args.wholegrid_steps):
+                u.zero_()
+                s2.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+                ws.append(s2.stats())
+            w1.record(stream)
+            barrier()
+            wms = w0.elapsed_time(w1) / args.wholegrid_steps
+            iters = sum(s["cycles"] * (s["iterations_per_cycle"] - s["fine_iterations_per_cycle"]) for s in ws)
+            coarse_ms = sum(s["coarse_ms"] for s in ws)
+            wg = {"value": unknowns / (wms * 1e-3), "ms_per_step": wms,
+                  "coarse_iteration_us": 1e3 * coarse_ms / iters if iters else None}
+
+    peaks, peak_src = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
+    launches = sum(s["cycles"] * s["fine_iterations_per_cycle"] for s in stats)
+    fine_ms = sum(s["fine_ms"] for s in stats)
+    per_launch_s = fine_ms * 1e-3 / launches
+    ops = stats[0]["fine_fp64_ops_per_iteration"]
+    bts = stats[0]["fine_bytes_per_iteration"]
+    alu_achieved = ops / per_launch_s / 1e12
+    hbm_achieved = bts / per_launch_s / 1e9
+    clk = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL,
+                   "exec": args.exec, "exec_used": {1: "wholegrid", 2: "lattice"}[stats[0]["exec_mode"]],
+                   "cycles": stats[-1]["cycles"], "final_relres": relres,
+                   "iterations_per_cycle": stats[0]["iterations_per_cycle"],
+                   "l2": "working set ~0.8 GB > 126 MB L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_iterate (level-0 HOMG iteration: damped Jacobi on every interior node)",
+                     "bound": "alu", "achieved": alu_achieved, "peak": FP64_PEAK_OPS / 1e12,
+                     "unit": "TFP64op/s", "frac": alu_achieved / (FP64_PEAK_OPS / 1e12),
+                     "peak_source": "nominal FP64 rate (1.25 TFLOP/s = 0.625e12 FP64 instr/s)",
+                     "traffic": None, "launch_us": per_launch_s * 1e6, "launches": launches,
+                     "algorithmic_ops_per_launch": ops, "algorithmic_bytes_per_launch": bts,
+                     "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": hbm_achieved / hbm_peak, "hbm_peak_source": peak_src},
+        "e2e": {"value": unknowns * args.steps * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * grid_bytes, "d2h_bytes_per_step": grid_bytes},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "clocks": clk,
+        "time_split_ms_per_step": {k: sum(s[k] for s in stats) / len(stats)
+                                   for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms", "solve_ms")},
+    }
+    if wg:
+        line["wholegrid"] = wg
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_cpu_baseline(f_np, stats[-1]["cycles"])
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="homg", choices=["homg", "reference"])
+    p.add_argument("--exec", default="auto", choices=["auto", "lattice", "wholegrid"])
+    p.add_argument("--wholegrid-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args()
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

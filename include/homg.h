@@ -1,0 +1,177 @@
+/*
+ * homg.h -- C ABI of the GB300 (sm_103a) high-occupancy multigrid (HOMG) solver.
+ *
+ * Method: Becerra-Sagredo, Malaga and Mandujano, "A novel and scalable Multigrid algorithm for
+ * many-core architectures" (arXiv:1108.2045). The library solves A u = f (Sec. 2, Eq. 1) for the
+ * Poisson problem on the unit square or cube with zero Dirichlet boundary (Sec. 4, Eq. "poisson"),
+ * A = -Laplacian discretised by the 5-point (2-D) or 7-point (3-D) stencil on a node grid of
+ * (2^K + 1)^d nodes, h = 2^-K. The sign convention makes A positive definite (the paper writes
+ * Laplacian(u) = f; pass -f to solve the paper's form).
+ *
+ * One solve = restarted HOMG cycles on the residual equation (Sec. 2, last paragraph) until
+ *   ||f - A u||_2 / ||f||_2 <= tol      (2-norms over interior nodes)
+ * Each cycle: residual and full-weighting restriction to every level (Sec. 2, restriction
+ * paragraph), then the MFMG sequence of HOMG iterations from the coarsest level to the finest
+ * (Sec. 2, steps (a)-(c), MFMG paragraph), each iteration relaxing the level-m lattice with damped
+ * Jacobi (Sec. 2, relaxation formula) fused with the interpolation of the previous iteration's
+ * variations on the rest of the grid, then u += e. Everything runs on the GPU: the cycle loop and
+ * its convergence test are captured in one CUDA graph with device-side conditional nodes, and the
+ * host synchronises once per solve.
+ *
+ * Conventions shared by every entry point:
+ * - Return codes: 0 = HOMG_OK. Positive = soft outcome with valid outputs (HOMG_NOT_CONVERGED,
+ *   HOMG_DIVERGED). Negative = hard error, outputs untouched (HOMG_EINVAL, HOMG_ESHAPE, HOMG_ECUDA,
+ *   HOMG_ENOMEM); homg_last_error() then describes it. No C++ exception crosses this ABI and no
+ *   kernel traps.
+ * - Grid arrays are FP64, contiguous, row-major with x fastest: node (i, j[, k]) at
+ *   j*(n+1) + i (2-D) or (k*(n+1) + j)*(n+1) + i (3-D), n = 2^K, covering the whole node grid
+ *   including the boundary. Only interior nodes are read or written; the operator takes the
+ *   boundary value 0.
+ * - Device pointers are caller-owned CUDA device (or managed) memory on the handle's device.
+ *   They must stay valid until the call returns; the library keeps no reference to them.
+ * - A handle is not thread-safe: use one handle per host thread (or serialise calls).
+ */
+#ifndef HOMG_H
+#define HOMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------------------------- */
+#define HOMG_OK 0
+#define HOMG_NOT_CONVERGED 1 /* max_cycles cycles done, relative residual still above tol       */
+#define HOMG_DIVERGED 2      /* relative residual not finite, or above diverge_factor * initial   */
+#define HOMG_TIMEOUT 3       /* reserved for bounded device-side waits; no current kernel waits   */
+#define HOMG_EINVAL (-1)     /* invalid argument (null pointer, level count, stencil, options ...)  */
+#define HOMG_ESHAPE (-2)     /* grid sides not 2^K + 1, not all equal, or too large                 */
+#define HOMG_ECUDA (-3)      /* a CUDA runtime call failed                                          */
+#define HOMG_ENOMEM (-4)     /* device or pinned host allocation failed                             */
+
+/* ---- execution forms of the same iterates -------------------------------------------------- */
+/* HOMG_EXEC_WHOLEGRID: the paper's form (Sec. 2: "operations over the entire grid"): every HOMG
+ *   iteration is one launch over every fine-grid node, relaxing the level-m lattice and adding the
+ *   interpolated previous variation everywhere else (one working unit per iteration, Sec. 4).
+ * HOMG_EXEC_LATTICE: the same iterates up to rounding order, computed level by level on each
+ *   level's own lattice. The HOMG iterate restricted to the level-m lattice depends only on values
+ *   on that lattice, so the iterations of level m run on its compact (n/2^m + 1)^d copy; at each
+ *   level change one fused kernel interpolates the coarser lattice's iterate onto the finer one
+ *   with the one-iteration delay of Sec. 4 (Fig. 3 discussion). Requires a schedule whose levels
+ *   never increase (MFMG is such a schedule).
+ * HOMG_EXEC_AUTO: LATTICE when the schedule allows it, else WHOLEGRID. */
+#define HOMG_EXEC_AUTO 0
+#define HOMG_EXEC_WHOLEGRID 1
+#define HOMG_EXEC_LATTICE 2
+
+/* Largest max_cycles accepted by homg_solve (the cycle loop is unrolled into the solve graph). */
+#define HOMG_MAX_CYCLES 200
+/* Largest grid side exponent K accepted: 2-D n <= 2^15, 3-D n <= 2^10. */
+#define HOMG_MAX_K_2D 15
+#define HOMG_MAX_K_3D 10
+
+typedef struct homg_options {
+    /* Damped-Jacobi weight omega_J; each relaxation uses omega = omega_J / (2d) (Sec. 2,
+     * relaxation formula with the Jacobi diagonal 2d). 0 selects 4/5 (2-D) or 6/7 (3-D). */
+    double omega_j;
+    /* MaxI of the MFMG cycle (Sec. 2, MFMG paragraph): 2 iterations on the coarsest level,
+     * doubling per finer level, capped at max_i. 0 selects 32, the paper's timing setting (Sec. 4). */
+    int max_i;
+    /* Optional explicit schedule (Sec. 2 step (c): "a chosen pattern"): n_schedule level indexes in
+     * [0, levels), one per HOMG iteration, ending with 0. Copied by homg_create. 0/NULL = MFMG. */
+    int n_schedule;
+    const int* schedule;
+    /* HOMG_EXEC_* (see above). */
+    int exec_mode;
+    /* 1: evaluate every formula in the CPU oracle's canonical operation order with no fused
+     * multiply-add contraction (whole-grid form then reproduces the oracle's iterates bit for bit).
+     * 0: reassociated forms with fewer FP64 instructions (results equal up to rounding). */
+    int strict_fp;
+    /* Divergence threshold on the relative residual, as a multiple of the initial one. 0 = 1e3. */
+    double diverge_factor;
+} homg_options;
+
+/* Statistics of the last homg_solve on a handle (times from CUDA events recorded on the handle's
+ * stream inside the solve graph; zero when the last call failed). */
+typedef struct homg_stats {
+    int cycles;                  /* cycles performed                                            */
+    int status;                  /* return code of the last solve                               */
+    int exec_mode;               /* form actually used (HOMG_EXEC_WHOLEGRID / _LATTICE)          */
+    int iterations_per_cycle;    /* HOMG iterations (working units) per cycle                    */
+    int fine_iterations_per_cycle;   /* iterations on the finest level (level 0) per cycle      */
+    int kernels_per_cycle;       /* kernel launches per cycle                                    */
+    int kernels_fixed;           /* kernel launches per solve outside the cycles                 */
+    long long kernel_launches;   /* total kernel launches of the last solve                      */
+    double solve_ms;             /* whole solve graph, first node to last                        */
+    double coarse_ms;            /* sum over cycles: iterations on levels >= 1                   */
+    double fine_ms;              /* sum over cycles: iterations on level 0                       */
+    double residual_ms;          /* sum over cycles: update + residual + restriction + test     */
+    double setup_ms;             /* initial residual + final copy-out                            */
+    double fine_bytes_per_iteration;   /* algorithmic DRAM bytes of one level-0 iteration       */
+    double fine_fp64_ops_per_iteration; /* algorithmic FP64 instructions of one level-0 iteration */
+    double coarse_bytes_per_cycle;     /* algorithmic DRAM bytes of the levels >= 1 per cycle   */
+    double coarse_fp64_ops_per_cycle;  /* algorithmic FP64 instructions of levels >= 1 per cycle */
+} homg_stats;
+
+typedef struct homg_ctx* homg_handle;
+
+/* Fill *opt with the defaults described above. */
+void homg_default_options(homg_options* opt);
+
+/* Create a solver for a (2^K+1)^ndim node grid (Sec. 2: nested grids doubling the spacing).
+ *   ndim     2 or 3.
+ *   dims     ndim node counts, all equal to 2^K + 1 with K >= 1 (ESHAPE otherwise).
+ *   levels   number of levels L, 1 <= L <= K; level m has spacing 2^m h, the coarsest is L-1.
+ *   stencil  5 (ndim 2) or 7 (ndim 3).
+ *   opt      NULL for defaults.
+ *   out      receives the handle (NULL on failure).
+ * Allocates one device buffer holding every level (all compact level arrays, the fine iterates,
+ * the per-level restricted sources, norm partials and the cycle state) on the current device,
+ * and creates the handle's events and pinned host state. Returns 0 or a negative code. */
+int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const homg_options* opt, homg_handle* out);
+
+/* Use `stream` (a cudaStream_t, NULL = legacy default stream) for every later call on h. */
+int homg_set_stream(homg_handle h, void* stream);
+
+/* Restarted HOMG solve (Sec. 2 last paragraph; Sec. 4: "the residual equation is used to restart
+ * the cycles as many times as needed").
+ *   f           device pointer, right-hand side (interior nodes used).
+ *   u           device pointer, in: initial guess, out: solution (interior nodes only).
+ *   tol         stop when ||r||/||f|| <= tol (>= 0, finite).
+ *   max_cycles  0 .. HOMG_MAX_CYCLES; 0 only evaluates the initial residual.
+ *   cycles_out, relres_out  optional; receive the cycle count and the final relative residual.
+ * Returns HOMG_OK, HOMG_NOT_CONVERGED or HOMG_DIVERGED (u holds the last iterate), or a negative
+ * code. ||f|| = 0 gives u = 0 and relres 0 after 0 cycles. The call enqueues one graph launch on
+ * the handle's stream and synchronises that stream once, at the end. */
+int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cycles, int* cycles_out,
+               double* relres_out);
+
+/* Same as homg_solve with HOST arrays (pinned memory recommended): copies f and u to device
+ * buffers owned by the handle (allocated on first use), solves, copies u back. */
+int homg_solve_host(homg_handle h, const double* f_host, double* u_host, double tol, int max_cycles,
+                    int* cycles_out, double* relres_out);
+
+/* ||f - A u||_2 / ||f||_2 over interior nodes for device arrays f, u (relres_out required);
+ * 0 when ||f|| = 0 and u's interior is 0, +inf when ||f|| = 0 otherwise. Synchronises the stream. */
+int homg_residual_norm(homg_handle h, const double* f, const double* u, double* relres_out);
+
+/* Relative residual before every cycle of the last solve: hist[0] = initial, hist[k] after k
+ * cycles. Copies min(cap, cycles + 1) values; returns that count or a negative code. */
+int homg_get_history(homg_handle h, double* hist, int cap);
+
+/* Statistics of the last solve (see homg_stats). */
+int homg_get_stats(homg_handle h, homg_stats* out);
+
+/* Message for the last hard error on h (or of the last failed homg_create when h is NULL). */
+const char* homg_last_error(homg_handle h);
+
+/* Release every resource of h (no-op for NULL). */
+void homg_destroy(homg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOMG_H */

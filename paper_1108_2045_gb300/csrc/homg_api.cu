@@ -1,0 +1,681 @@
+// Host side of the HOMG C ABI (include/homg.h): validation, the single level buffer, the cycle
+// schedule and the solve graph.
+//
+// Solve graph (built once per handle and grown when a larger max_cycles is requested):
+//   [initial residual + test] E0
+//   for stage k = 1..S:  IF_A{restrict to every level; iterations on levels >= 1} E
+//                        IF_B{iterations on level 0}                          E
+//                        IF_C{u += e; residual; convergence test}            E
+//   [copy the final iterate out] E_end
+// The test kernel enables stage k+1's three conditional nodes only while the solve continues, so
+// the cycle loop never returns to the host. Event nodes between the stages time each part.
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/homg.h"
+#include "homg_internal.h"
+
+using namespace homg;
+
+namespace {
+
+thread_local char g_create_error[512] = "";
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int64_t grid_elems(int ndim, int n, int64_t pitch) {
+    return (ndim == 2) ? (int64_t)(n + 1) * pitch : (int64_t)(n + 1) * (n + 1) * pitch;
+}
+
+struct Level {
+    int n;                 // intervals per side of the compact lattice
+    int64_t pitch;
+    double* g = nullptr;   // pre-scaled restricted source
+    double* G[2] = {nullptr, nullptr};  // lattice iterates (lattice form; level 0 aliases e)
+    double* d[2] = {nullptr, nullptr};  // compact variations
+};
+
+struct Op {  // one kernel launch of a cycle part
+    enum Kind { ITER, PROLONG, RESTRICT } kind;
+    IterArgs it;
+    ProlongArgs pr;
+    RestrictArgs rs;
+};
+
+}  // namespace
+
+struct homg_ctx {
+    int ndim = 2, n = 0, K = 0, levels = 1, stencil = 5;
+    homg_options opt{};
+    std::vector<int> sched;
+    int exec = HOMG_EXEC_WHOLEGRID;
+    bool strict = false;
+    double omega = 0.2;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    int64_t pitch0 = 0;
+    std::vector<Level> L;
+    double* uint_[2] = {nullptr, nullptr};
+    double* e[2] = {nullptr, nullptr};
+    double* part_r = nullptr;
+    double* part_f = nullptr;
+    int nparts = 0;
+    State* dstate = nullptr;
+    double* dhist = nullptr;
+    cudaGraphConditionalHandle* dhandles = nullptr;
+
+    State* hstate = nullptr;  // pinned
+    double* hhist = nullptr;  // pinned
+
+    std::vector<Op> partA, partB;  // cycle parts (A: restriction + levels >= 1, B: level 0)
+    int e_final = 0;               // index of e[] holding the cycle's result (whole-grid form)
+    int fine_iters = 0, coarse_iters = 0;
+
+    cudaGraphExec_t exec_graph = nullptr;
+    int stages = 0;
+    std::vector<cudaEvent_t> ev;  // 3*stages + 2 events
+
+    double* stage_f = nullptr;  // homg_solve_host staging
+    double* stage_u = nullptr;
+
+    homg_stats stats{};
+    char err[512] = "";
+};
+
+namespace {
+
+int fail(homg_ctx* h, int code, const char* fmt, const char* what = "", const char* extra = "") {
+    char* dst = h ? h->err : g_create_error;
+    snprintf(dst, 512, fmt, what, extra);
+    return code;
+}
+
+int cuda_fail(homg_ctx* h, cudaError_t e, const char* where) {
+    cudaGetLastError();
+    return fail(h, e == cudaErrorMemoryAllocation ? HOMG_ENOMEM : HOMG_ECUDA, "CUDA error in %s: %s", where,
+                cudaGetErrorString(e));
+}
+
+#define CK(h, call, where)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+    } while (0)
+
+// Default MFMG schedule (Sec. 2, MFMG paragraph): coarsest first, 2 iterations, doubling, MaxI cap.
+std::vector<int> mfmg(int levels, int max_i) {
+    std::vector<int> s;
+    for (int m = levels - 1; m >= 0; --m) {
+        long long nm = 2;
+        for (int t = 0; t < levels - 1 - m && nm < max_i; ++t) nm *= 2;
+        nm = std::min<long long>(nm, max_i);
+        for (long long t = 0; t < nm; ++t) s.push_back(m);
+    }
+    return s;
+}
+
+CGrid cgrid(const double* p, int64_t pitch, int n) { return CGrid{p, pitch, n}; }
+Grid grid(double* p, int64_t pitch, int n) { return Grid{p, pitch, n}; }
+
+// Lay out every array in one buffer: returns bytes needed; assigns pointers when base != nullptr.
+size_t layout(homg_ctx* h, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> double* {
+        off = (size_t)round_up((int64_t)off, 256);
+        double* p = base ? (double*)(base + off) : nullptr;
+        off += bytes;
+        return p;
+    };
+    const int nd = h->ndim;
+    const bool lattice = (h->exec == HOMG_EXEC_LATTICE);
+    for (int m = 0; m < h->levels; ++m) {
+        Level& lv = h->L[m];
+        const size_t bytes = (size_t)grid_elems(nd, lv.n, lv.pitch) * sizeof(double);
+        lv.g = take(bytes);
+        if (m >= 1) {
+            if (lattice) {
+                lv.G[0] = take(bytes);
+                lv.G[1] = take(bytes);
+                lv.d[0] = take(bytes);
+            } else {
+                lv.d[0] = take(bytes);
+                lv.d[1] = take(bytes);
+            }
+        }
+    }
+    const size_t fine = (size_t)grid_elems(nd, h->n, h->pitch0) * sizeof(double);
+    h->e[0] = take(fine);
+    h->e[1] = take(fine);
+    h->uint_[0] = take(fine);
+    h->uint_[1] = take(fine);
+    h->L[0].G[0] = h->e[0];
+    h->L[0].G[1] = h->e[1];
+    h->part_r = take((size_t)h->nparts * sizeof(double));
+    h->part_f = take((size_t)h->nparts * sizeof(double));
+    h->dstate = (State*)take(sizeof(State));
+    h->dhist = take((HOMG_MAX_CYCLES + 1) * sizeof(double));
+    return (size_t)round_up((int64_t)off, 256);
+}
+
+// Kernel sequence of one cycle's parts A (restriction + levels >= 1) and B (level 0).
+void plan_cycle(homg_ctx* h) {
+    h->partA.clear();
+    h->partB.clear();
+    const int nd = h->ndim;
+    (void)nd;
+    for (int m = 1; m < h->levels; ++m) {
+        Op op{};
+        op.kind = Op::RESTRICT;
+        op.rs.gf = cgrid(h->L[m - 1].g, h->L[m - 1].pitch, h->L[m - 1].n);
+        op.rs.gc = grid(h->L[m].g, h->L[m].pitch, h->L[m].n);
+        h->partA.push_back(op);
+    }
+    const std::vector<int>& s = h->sched;
+    const int T = (int)s.size();
+    int tail = T;  // first index of the trailing run of level-0 iterations
+    while (tail > 0 && s[tail - 1] == 0) --tail;
+    h->fine_iters = T - tail;
+    h->coarse_iters = tail;
+    if (h->exec == HOMG_EXEC_WHOLEGRID) {
+        int cur = 0;  // e[cur] holds the current iterate
+        int mprev = -1;
+        int dpar[32] = {0};
+        for (int t = 0; t < T; ++t) {
+            const int m = s[t];
+            Op op{};
+            op.kind = Op::ITER;
+            IterArgs& a = op.it;
+            a.e_old = (t == 0) ? cgrid(nullptr, h->pitch0, h->n) : cgrid(h->e[cur], h->pitch0, h->n);
+            a.e_new = grid(h->e[cur ^ 1], h->pitch0, h->n);
+            a.g = cgrid(h->L[m].g, h->L[m].pitch, h->L[m].n);
+            a.m = m;
+            a.omega = h->omega;
+            a.mp = -1;
+            if (mprev >= 1) {
+                a.mp = mprev;
+                const Level& lp = h->L[mprev];
+                a.dprev = cgrid(lp.d[dpar[mprev] ^ 1], lp.pitch, lp.n);
+            }
+            a.dnew = grid(nullptr, 0, 0);
+            if (m >= 1) {
+                a.dnew = grid(h->L[m].d[dpar[m]], h->L[m].pitch, h->L[m].n);
+                dpar[m] ^= 1;
+            }
+            (t < tail ? h->partA : h->partB).push_back(op);
+            cur ^= 1;
+            mprev = m;
+        }
+        h->e_final = cur;
+    } else {
+        // Lattice form: runs of equal levels, never increasing.
+        int t = 0, mprev = -1;
+        int e_cur = 0;
+        while (t < T) {
+            const int m = s[t];
+            int c = 0;
+            while (t + c < T && s[t + c] == m) ++c;
+            Level& lv = h->L[m];
+            int cur = 0;
+            const bool first_run = (mprev < 0);
+            if (!first_run) {
+                const Level& lc = h->L[mprev];
+                Op op{};
+                op.kind = Op::PROLONG;
+                op.pr.G = grid(lv.G[0], lv.pitch, lv.n);
+                op.pr.Gc = cgrid(lc.G[e_cur], lc.pitch, lc.n);
+                op.pr.dl = cgrid(lc.d[0], lc.pitch, lc.n);
+                op.pr.s = mprev - m;
+                h->partA.push_back(op);
+            }
+            for (int q = 0; q < c; ++q) {
+                Op op{};
+                op.kind = Op::ITER;
+                IterArgs& a = op.it;
+                a.e_old = (first_run && q == 0) ? cgrid(nullptr, lv.pitch, lv.n) : cgrid(lv.G[cur], lv.pitch, lv.n);
+                a.e_new = grid(lv.G[cur ^ 1], lv.pitch, lv.n);
+                a.g = cgrid(lv.g, lv.pitch, lv.n);
+                a.m = 0;
+                a.omega = h->omega;
+                a.mp = -1;
+                if (q == 0 && !first_run) {
+                    const Level& lc = h->L[mprev];
+                    a.mp = mprev - m;
+                    a.dprev = cgrid(lc.d[0], lc.pitch, lc.n);
+                }
+                a.dnew = grid(nullptr, 0, 0);
+                if (q == c - 1 && m >= 1) a.dnew = grid(lv.d[0], lv.pitch, lv.n);
+                (m == 0 ? h->partB : h->partA).push_back(op);
+                cur ^= 1;
+            }
+            e_cur = cur;
+            mprev = m;
+            t += c;
+        }
+        h->e_final = e_cur;
+    }
+}
+
+cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s) {
+    for (const Op& op : ops) {
+        cudaError_t e = cudaSuccess;
+        switch (op.kind) {
+            case Op::ITER: e = launch_iterate(h->ndim, h->strict, op.it, s); break;
+            case Op::PROLONG: e = launch_prolong(h->ndim, h->strict, op.pr, s); break;
+            case Op::RESTRICT: e = launch_restrict(h->ndim, h->strict, op.rs, s); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+ResidArgs resid_args(homg_ctx* h, int stage) {
+    ResidArgs a{};
+    a.st = h->dstate;
+    const double hh = 1.0 / (double)h->n;
+    a.inv_h2 = (double)h->n * (double)h->n;
+    a.scale = hh * hh;
+    a.part_r = h->part_r;
+    a.part_f = nullptr;
+    a.g0 = grid(h->L[0].g, h->L[0].pitch, h->n);
+    if (stage == 0) {
+        a.u_in = cgrid(nullptr, 0, h->n);
+        a.e = cgrid(nullptr, 0, h->n);
+        a.u_out = grid(h->uint_[0], h->pitch0, h->n);
+        a.part_f = h->part_f;
+    } else {
+        a.u_in = cgrid(h->uint_[(stage - 1) & 1], h->pitch0, h->n);
+        a.e = cgrid(h->e[h->e_final], h->pitch0, h->n);
+        a.u_out = grid(h->uint_[stage & 1], h->pitch0, h->n);
+    }
+    return a;
+}
+
+FinalizeArgs fin_args(homg_ctx* h, int mode) {
+    FinalizeArgs f{};
+    f.st = h->dstate;
+    f.hist = h->dhist;
+    f.part_r = h->part_r;
+    f.part_f = (mode == FIN_CYCLE) ? nullptr : h->part_f;
+    f.nparts = h->nparts;
+    f.mode = mode;
+    f.handles = h->dhandles;
+    f.nstages = h->stages;
+    return f;
+}
+
+void destroy_graph(homg_ctx* h) {
+    if (h->exec_graph) cudaGraphExecDestroy(h->exec_graph);
+    h->exec_graph = nullptr;
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+    if (h->dhandles) cudaFree(h->dhandles);
+    h->dhandles = nullptr;
+    h->stages = 0;
+}
+
+// Capture `fn(stream)` into the body graph `body` (or a fresh graph when body == nullptr).
+template <typename Fn>
+cudaError_t capture_into(cudaGraph_t body, cudaStream_t cap, Fn fn, cudaGraph_t* out) {
+    cudaError_t e = body ? cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)
+                         : cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = fn(cap);
+    cudaGraph_t g = body;
+    e = cudaStreamEndCapture(cap, &g);
+    if (le != cudaSuccess) return le;
+    if (out) *out = g;
+    return e;
+}
+
+// Event layout: ev[0] before the initial residual, ev[1] after it (= start of stage 1); stage k
+// records ev[3k-1] after part A, ev[3k] after part B, ev[3k+1] after part C; ev[3S+2] at the end.
+int build_graph(homg_ctx* h, int stages) {
+    destroy_graph(h);
+    std::vector<cudaGraphConditionalHandle> handles(3 * (stages + 1), 0);
+    h->stages = stages;
+    h->ev.assign(3 * stages + 3, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& ev : h->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaMalloc(&h->dhandles, handles.size() * sizeof(cudaGraphConditionalHandle));
+    cudaStream_t cap = nullptr;
+    cudaGraph_t top = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&top, 0);
+    cudaGraphNode_t last = nullptr, node = nullptr;
+    auto add_event = [&](int idx) -> cudaError_t {
+        cudaError_t r = cudaGraphAddEventRecordNode(&node, top, last ? &last : nullptr, last ? 1 : 0, h->ev[idx]);
+        if (r == cudaSuccess) last = node;
+        return r;
+    };
+    // Append the kernels enqueued by fn directly to the top graph, after `last`.
+    auto add_seq = [&](auto fn) -> cudaError_t {
+        cudaError_t r = cudaStreamBeginCaptureToGraph(cap, top, last ? &last : nullptr, nullptr, last ? 1 : 0,
+                                                      cudaStreamCaptureModeThreadLocal);
+        if (r != cudaSuccess) return r;
+        cudaError_t le = fn(cap);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaError_t qe = cudaStreamGetCaptureInfo(cap, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+        cudaGraphNode_t tail = (qe == cudaSuccess && nd == 1) ? deps[0] : nullptr;
+        cudaGraph_t g = top;
+        r = cudaStreamEndCapture(cap, &g);
+        if (le != cudaSuccess) return le;
+        if (qe != cudaSuccess) return qe;
+        if (r != cudaSuccess) return r;
+        if (!tail) return cudaErrorInvalidValue;
+        last = tail;
+        return cudaSuccess;
+    };
+    auto add_if = [&](int k, int part, auto fn) -> cudaError_t {
+        cudaGraphConditionalHandle hd;
+        cudaError_t r = cudaGraphConditionalHandleCreate(&hd, top, 0, cudaGraphCondAssignDefault);
+        if (r != cudaSuccess) return r;
+        handles[3 * k + part] = hd;
+        cudaGraphNodeParams p{};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = hd;
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        r = cudaGraphAddNode(&node, top, &last, nullptr, 1, &p);
+        if (r != cudaSuccess) return r;
+        last = node;
+        return capture_into(p.conditional.phGraph_out[0], cap, fn, nullptr);
+    };
+    if (e == cudaSuccess) e = add_event(0);
+    if (e == cudaSuccess)
+        e = add_seq([&](cudaStream_t s) -> cudaError_t {
+            cudaError_t r = launch_residual(h->ndim, h->strict, resid_args(h, 0), h->n, s);
+            if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_INIT), s);
+            return r;
+        });
+    if (e == cudaSuccess) e = add_event(1);
+    for (int k = 1; k <= stages && e == cudaSuccess; ++k) {
+        e = add_if(k, 0, [&](cudaStream_t s) { return enqueue_ops(h, h->partA, s); });
+        if (e == cudaSuccess) e = add_event(3 * k - 1);
+        if (e == cudaSuccess) e = add_if(k, 1, [&](cudaStream_t s) { return enqueue_ops(h, h->partB, s); });
+        if (e == cudaSuccess) e = add_event(3 * k);
+        if (e == cudaSuccess)
+            e = add_if(k, 2, [&](cudaStream_t s) -> cudaError_t {
+                cudaError_t r = launch_residual(h->ndim, h->strict, resid_args(h, k), h->n, s);
+                if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_CYCLE), s);
+                return r;
+            });
+        if (e == cudaSuccess) e = add_event(3 * k + 1);
+    }
+    if (e == cudaSuccess)
+        e = add_seq([&](cudaStream_t s) -> cudaError_t {
+            CopyOutArgs c{};
+            c.st = h->dstate;
+            c.u0 = cgrid(h->uint_[0], h->pitch0, h->n);
+            c.u1 = cgrid(h->uint_[1], h->pitch0, h->n);
+            return launch_copy_out(h->ndim, c, h->n, s);
+        });
+    if (e == cudaSuccess) e = add_event(3 * stages + 2);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->dhandles, handles.data(), handles.size() * sizeof(handles[0]), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_graph, top, 0);
+    int rc = (e == cudaSuccess) ? HOMG_OK : cuda_fail(h, e, "building the solve graph");
+    if (top) cudaGraphDestroy(top);
+    if (cap) cudaStreamDestroy(cap);
+    if (rc != HOMG_OK) destroy_graph(h);
+    return rc;
+}
+
+bool schedule_monotone(const std::vector<int>& s) {
+    for (size_t t = 1; t < s.size(); ++t)
+        if (s[t] > s[t - 1]) return false;
+    return true;
+}
+
+double elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+void homg_default_options(homg_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->omega_j = 0.0;
+    opt->max_i = 32;
+    opt->exec_mode = HOMG_EXEC_AUTO;
+    opt->diverge_factor = 1e3;
+}
+
+int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const homg_options* opt, homg_handle* out) {
+    if (out) *out = nullptr;
+    g_create_error[0] = 0;
+    if (!out || !dims) return fail(nullptr, HOMG_EINVAL, "homg_create: null %s%s", !out ? "out" : "dims");
+    if (ndim != 2 && ndim != 3) return fail(nullptr, HOMG_EINVAL, "homg_create: ndim must be 2 or 3%s%s");
+    if ((ndim == 2 && stencil != 5) || (ndim == 3 && stencil != 7))
+        return fail(nullptr, HOMG_EINVAL, "homg_create: stencil must be 5 (2-D) or 7 (3-D)%s%s");
+    for (int d = 1; d < ndim; ++d)
+        if (dims[d] != dims[0]) return fail(nullptr, HOMG_ESHAPE, "homg_create: grid sides must be equal%s%s");
+    const int64_t n = dims[0] - 1;
+    int K = 0;
+    while (K < 62 && ((int64_t)1 << K) < n) ++K;
+    if (n < 2 || ((int64_t)1 << K) != n)
+        return fail(nullptr, HOMG_ESHAPE, "homg_create: grid side must be 2^K + 1 with K >= 1%s%s");
+    if (K > (ndim == 2 ? HOMG_MAX_K_2D : HOMG_MAX_K_3D))
+        return fail(nullptr, HOMG_ESHAPE, "homg_create: grid side above the supported maximum%s%s");
+    if (levels < 1 || levels > K) return fail(nullptr, HOMG_EINVAL, "homg_create: levels must be in [1, K]%s%s");
+    homg_options o;
+    homg_default_options(&o);
+    if (opt) o = *opt;
+    if (o.omega_j == 0.0) o.omega_j = (ndim == 2) ? 4.0 / 5.0 : 6.0 / 7.0;
+    if (o.max_i == 0) o.max_i = 32;
+    if (o.diverge_factor == 0.0) o.diverge_factor = 1e3;
+    if (!(o.omega_j > 0.0 && o.omega_j <= 2.0) || o.max_i < 1 || !(o.diverge_factor > 1.0) || o.n_schedule < 0 ||
+        (o.n_schedule > 0 && !o.schedule) || o.exec_mode < 0 || o.exec_mode > 2 || (o.strict_fp != 0 && o.strict_fp != 1))
+        return fail(nullptr, HOMG_EINVAL, "homg_create: invalid options%s%s");
+
+    homg_ctx* h = new (std::nothrow) homg_ctx();
+    if (!h) return fail(nullptr, HOMG_ENOMEM, "homg_create: out of host memory%s%s");
+    h->ndim = ndim;
+    h->n = (int)n;
+    h->K = K;
+    h->levels = levels;
+    h->stencil = stencil;
+    h->opt = o;
+    h->strict = (o.strict_fp == 1);
+    h->omega = o.omega_j / (2.0 * ndim);
+    if (o.n_schedule > 0) {
+        h->sched.assign(o.schedule, o.schedule + o.n_schedule);
+        for (int m : h->sched)
+            if (m < 0 || m >= levels) {
+                delete h;
+                return fail(nullptr, HOMG_EINVAL, "homg_create: schedule level out of range%s%s");
+            }
+        if (h->sched.back() != 0) {
+            delete h;
+            return fail(nullptr, HOMG_EINVAL, "homg_create: schedule must end on level 0%s%s");
+        }
+        h->opt.schedule = nullptr;
+    } else {
+        h->sched = mfmg(levels, o.max_i);
+    }
+    const bool mono = schedule_monotone(h->sched);
+    if (o.exec_mode == HOMG_EXEC_LATTICE && !mono) {
+        delete h;
+        return fail(nullptr, HOMG_EINVAL, "homg_create: the lattice form needs a schedule whose levels never increase%s%s");
+    }
+    h->exec = (o.exec_mode == HOMG_EXEC_WHOLEGRID || !mono) ? HOMG_EXEC_WHOLEGRID : HOMG_EXEC_LATTICE;
+
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce != cudaSuccess) {
+        int rc = cuda_fail(nullptr, ce, "cudaGetDevice");
+        delete h;
+        return rc;
+    }
+    h->pitch0 = round_up(n + 1, 16);
+    h->L.resize(levels);
+    for (int m = 0; m < levels; ++m) {
+        h->L[m].n = (int)(n >> m);
+        h->L[m].pitch = (m == 0) ? h->pitch0 : round_up(h->L[m].n + 1, 16);
+    }
+    h->nparts = residual_blocks(ndim, (int)n);
+    h->arena_bytes = layout(h, nullptr);
+    ce = cudaMalloc(&h->arena, h->arena_bytes);
+    if (ce == cudaSuccess) ce = cudaMemset(h->arena, 0, h->arena_bytes);
+    if (ce == cudaSuccess) ce = cudaMallocHost(&h->hstate, sizeof(State));
+    if (ce == cudaSuccess) ce = cudaMallocHost(&h->hhist, (HOMG_MAX_CYCLES + 1) * sizeof(double));
+    if (ce != cudaSuccess) {
+        int rc = cuda_fail(nullptr, ce, "allocating the level buffer");
+        homg_destroy(h);
+        return rc;
+    }
+    layout(h, h->arena);
+    plan_cycle(h);
+    *out = h;
+    return HOMG_OK;
+}
+
+int homg_set_stream(homg_handle h, void* stream) {
+    if (!h) return HOMG_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return HOMG_OK;
+}
+
+int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cycles, int* cycles_out, double* relres_out) {
+    if (!h) return HOMG_EINVAL;
+    memset(&h->stats, 0, sizeof(h->stats));
+    if (!f || !u) return fail(h, HOMG_EINVAL, "homg_solve: null %s%s", !f ? "f" : "u");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, HOMG_EINVAL, "homg_solve: tol must be finite and >= 0%s%s");
+    if (max_cycles < 0 || max_cycles > HOMG_MAX_CYCLES)
+        return fail(h, HOMG_EINVAL, "homg_solve: max_cycles must be in [0, HOMG_MAX_CYCLES]%s%s");
+    CK(h, cudaSetDevice(h->device), "cudaSetDevice");
+    const int want = std::max(max_cycles, 1);
+    if (!h->exec_graph || h->stages < want) {
+        int rc = build_graph(h, std::max(want, h->stages));
+        if (rc != HOMG_OK) return rc;
+    }
+    State* s = h->hstate;
+    memset(s, 0, sizeof(*s));
+    s->f = f;
+    s->u = u;
+    s->tol = tol;
+    s->div_factor = h->opt.diverge_factor;
+    s->max_cycles = max_cycles;
+    s->stages = h->stages;
+    s->status = -1;
+    CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(state)");
+    CK(h, cudaGraphLaunch(h->exec_graph, h->stream), "cudaGraphLaunch");
+    CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
+    CK(h, cudaMemcpyAsync(h->hhist, h->dhist, (max_cycles + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+       "cudaMemcpyAsync(hist)");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    const int cycles = s->cycle;
+    if (cycles_out) *cycles_out = cycles;
+    if (relres_out) *relres_out = s->relres;
+    homg_stats& st = h->stats;
+    st.cycles = cycles;
+    st.status = s->status;
+    st.exec_mode = h->exec;
+    st.iterations_per_cycle = (int)h->sched.size();
+    st.fine_iterations_per_cycle = h->fine_iters;
+    st.kernels_per_cycle = (int)(h->partA.size() + h->partB.size()) + 2;
+    st.kernels_fixed = 3;
+    st.kernel_launches = st.kernels_fixed + (long long)cycles * st.kernels_per_cycle;
+    st.solve_ms = elapsed(h->ev[0], h->ev[3 * h->stages + 2]);
+    for (int k = 1; k <= cycles; ++k) {
+        st.coarse_ms += elapsed(h->ev[3 * k - 2], h->ev[3 * k - 1]);
+        st.fine_ms += elapsed(h->ev[3 * k - 1], h->ev[3 * k]);
+        st.residual_ms += elapsed(h->ev[3 * k], h->ev[3 * k + 1]);
+    }
+    st.setup_ms = st.solve_ms - st.coarse_ms - st.fine_ms - st.residual_ms;
+    const double pts = (h->ndim == 2) ? (double)(h->n - 1) * (h->n - 1) : (double)(h->n - 1) * (h->n - 1) * (h->n - 1);
+    st.fine_bytes_per_iteration = 24.0 * pts;
+    st.fine_fp64_ops_per_iteration = (h->ndim == 2 ? 5.0 : 7.0) * pts;
+    return s->status;
+}
+
+int homg_solve_host(homg_handle h, const double* f_host, double* u_host, double tol, int max_cycles, int* cycles_out,
+                    double* relres_out) {
+    if (!h) return HOMG_EINVAL;
+    if (!f_host || !u_host) return fail(h, HOMG_EINVAL, "homg_solve_host: null %s%s", !f_host ? "f" : "u");
+    CK(h, cudaSetDevice(h->device), "cudaSetDevice");
+    const size_t bytes = (size_t)grid_elems(h->ndim, h->n, h->n + 1) * sizeof(double);
+    if (!h->stage_f) {
+        CK(h, cudaMalloc(&h->stage_f, bytes), "cudaMalloc(staging f)");
+        CK(h, cudaMalloc(&h->stage_u, bytes), "cudaMalloc(staging u)");
+    }
+    CK(h, cudaMemcpyAsync(h->stage_f, f_host, bytes, cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(f)");
+    CK(h, cudaMemcpyAsync(h->stage_u, u_host, bytes, cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(u)");
+    int rc = homg_solve(h, h->stage_f, h->stage_u, tol, max_cycles, cycles_out, relres_out);
+    if (rc < 0) return rc;
+    CK(h, cudaMemcpyAsync(u_host, h->stage_u, bytes, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(u)");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return rc;
+}
+
+int homg_residual_norm(homg_handle h, const double* f, const double* u, double* relres_out) {
+    if (!h) return HOMG_EINVAL;
+    if (!f || !u || !relres_out) return fail(h, HOMG_EINVAL, "homg_residual_norm: null argument%s%s");
+    CK(h, cudaSetDevice(h->device), "cudaSetDevice");
+    State* s = h->hstate;
+    memset(s, 0, sizeof(*s));
+    s->f = f;
+    s->u = (double*)u;
+    CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(state)");
+    ResidArgs a{};
+    a.st = h->dstate;
+    a.inv_h2 = (double)h->n * (double)h->n;
+    a.part_r = h->part_r;
+    a.part_f = h->part_f;
+    CK(h, launch_residual(h->ndim, h->strict, a, h->n, h->stream), "residual kernel");
+    FinalizeArgs fa = fin_args(h, FIN_NORM);
+    fa.part_f = h->part_f;
+    CK(h, launch_finalize(fa, h->stream), "finalize kernel");
+    CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    *relres_out = s->relres;
+    return HOMG_OK;
+}
+
+int homg_get_history(homg_handle h, double* hist, int cap) {
+    if (!h || !hist || cap < 0) return HOMG_EINVAL;
+    const int cnt = std::min(cap, h->stats.cycles + 1);
+    memcpy(hist, h->hhist, (size_t)cnt * sizeof(double));
+    return cnt;
+}
+
+int homg_get_stats(homg_handle h, homg_stats* out) {
+    if (!h || !out) return HOMG_EINVAL;
+    *out = h->stats;
+    return HOMG_OK;
+}
+
+const char* homg_last_error(homg_handle h) { return h ? h->err : g_create_error; }
+
+void homg_destroy(homg_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    destroy_graph(h);
+    if (h->arena) cudaFree(h->arena);
+    if (h->stage_f) cudaFree(h->stage_f);
+    if (h->stage_u) cudaFree(h->stage_u);
+    if (h->hstate) cudaFreeHost(h->hstate);
+    if (h->hhist) cudaFreeHost(h->hhist);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Private declarations shared by the HOMG kernels and the host-side C ABI implementation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace homg {
+
+// Cycle state kept on the device for one solve (written by the host before the graph launch,
+// updated by the convergence-test kernel, read back once at the end).
+struct State {
+    const double* f;   // caller right-hand side, unpadded (n+1)^d
+    double* u;         // caller solution, unpadded (n+1)^d
+    double tol;
+    double div_factor;
+    int max_cycles;
+    int stages;        // cycle stages unrolled in the solve graph
+    int cycle;         // cycles completed
+    int status;        // -1 running, else HOMG_OK / HOMG_NOT_CONVERGED / HOMG_DIVERGED
+    int done;
+    int zero_u;        // ||f|| == 0: the solution is u = 0
+    double fnorm;
+    double rr0;
+    double relres;
+};
+
+// A grid array: `n` intervals per side, rows of `pitch` doubles, (n+1) rows per plane.
+struct Grid {
+    double* p;
+    int64_t pitch;
+    int n;
+};
+
+struct CGrid {
+    const double* p;
+    int64_t pitch;
+    int n;
+};
+
+__host__ __device__ inline CGrid cg(Grid g) { return CGrid{g.p, g.pitch, g.n}; }
+
+// One HOMG iteration on a grid of n intervals per side (the fine grid in the whole-grid form, a
+// level's compact lattice in the lattice form):
+//   relax the stride-2^m lattice (source g = h_m^2 F_m, compact, one value per lattice node),
+//   add the interpolation of the pending variation dprev (compact at stride 2^mp) off its lattice.
+struct IterArgs {
+    CGrid e_old;
+    Grid e_new;
+    CGrid g;        // compact level-m source, pre-scaled: h_m^2 F_m (strict) or omega h_m^2 F_m
+    int m;          // relaxation stride exponent
+    int mp;         // pending stride exponent, -1: none
+    CGrid dprev;    // compact pending variation (level mp)
+    Grid dnew;      // compact variation output (p == nullptr: not stored)
+    double omega;
+};
+
+// Lattice form, level change: fine lattice G (stride 1) from the coarser lattice's final iterate
+// Gc and last variation dl (both compact at stride 2^s on G): lattice nodes copy Gc, the others
+// get the interpolant of (Gc - dl), the value the whole-grid iterate holds there before the
+// delayed interpolation of dl is applied.
+struct ProlongArgs {
+    Grid G;
+    CGrid Gc;
+    CGrid dl;
+    int s;
+};
+
+// Update + residual: u_out = u_in (+ e); r = f - A_h u_out; g0 = scale * r; partial sums of r^2
+// (and f^2) per block.
+struct ResidArgs {
+    State* st;
+    CGrid u_in;     // p == nullptr: read the caller's u (st->u, unpadded)
+    CGrid e;        // p == nullptr: no update
+    Grid u_out;     // p == nullptr: not written
+    Grid g0;        // p == nullptr: not written
+    double scale;   // h^2 (strict) or omega h^2
+    double inv_h2;
+    double* part_r;
+    double* part_f; // nullptr: not accumulated
+};
+
+// Full weighting g_c = 4 * FW(g_f) (the factor 4 = 2^2 keeps the source pre-scaled by h_m^2).
+struct RestrictArgs {
+    CGrid gf;
+    Grid gc;
+};
+
+// Convergence test (one block): sums the residual partials in a fixed order and decides.
+enum FinalizeMode { FIN_INIT = 0, FIN_CYCLE = 1, FIN_NORM = 2 };
+
+struct FinalizeArgs {
+    State* st;
+    double* hist;
+    const double* part_r;
+    const double* part_f;
+    int nparts;
+    int mode;
+    const cudaGraphConditionalHandle* handles;  // 3 per stage, stage k at [3k, 3k+3)
+    int nstages;
+};
+
+struct CopyOutArgs {
+    State* st;
+    CGrid u0;   // internal iterate after an even number of cycles
+    CGrid u1;   // ... after an odd number
+};
+
+// Launchers (enqueue on `s`; return the launch error).
+cudaError_t launch_iterate(int ndim, bool strict, const IterArgs& a, cudaStream_t s);
+cudaError_t launch_prolong(int ndim, bool strict, const ProlongArgs& a, cudaStream_t s);
+cudaError_t launch_residual(int ndim, bool strict, const ResidArgs& a, int n, cudaStream_t s);
+int residual_blocks(int ndim, int n);
+cudaError_t launch_restrict(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s);
+cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s);
+cudaError_t launch_zero(int ndim, Grid g, cudaStream_t s);
+
+}  // namespace homg

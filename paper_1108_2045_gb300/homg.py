@@ -1,0 +1,253 @@
+"""Python binding of the HOMG C ABI (``include/homg.h``): argument marshalling only.
+
+Every function has the name of the C entry point it calls. Grid arrays passed as device pointers
+are torch CUDA tensors (float64, contiguous, shape (n+1,)*ndim); host arrays are numpy arrays or
+CPU tensors. All arithmetic runs in ``lib/libhomg.so``; there is no fallback: if the library is
+missing, loading raises.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libhomg.so")
+
+HOMG_OK, HOMG_NOT_CONVERGED, HOMG_DIVERGED, HOMG_TIMEOUT = 0, 1, 2, 3
+HOMG_EINVAL, HOMG_ESHAPE, HOMG_ECUDA, HOMG_ENOMEM = -1, -2, -3, -4
+HOMG_EXEC_AUTO, HOMG_EXEC_WHOLEGRID, HOMG_EXEC_LATTICE = 0, 1, 2
+HOMG_MAX_CYCLES = 200
+
+EXEC_MODES = {"auto": HOMG_EXEC_AUTO, "wholegrid": HOMG_EXEC_WHOLEGRID, "lattice": HOMG_EXEC_LATTICE}
+
+# Every entry point declared in include/homg.h (checked by the symbol test).
+EXPORTS = [
+    "homg_default_options",
+    "homg_create",
+    "homg_set_stream",
+    "homg_solve",
+    "homg_solve_host",
+    "homg_residual_norm",
+    "homg_get_history",
+    "homg_get_stats",
+    "homg_last_error",
+    "homg_destroy",
+]
+
+
+class homg_options(ctypes.Structure):
+    _fields_ = [
+        ("omega_j", ctypes.c_double),
+        ("max_i", ctypes.c_int),
+        ("n_schedule", ctypes.c_int),
+        ("schedule", ctypes.POINTER(ctypes.c_int)),
+        ("exec_mode", ctypes.c_int),
+        ("strict_fp", ctypes.c_int),
+        ("diverge_factor", ctypes.c_double),
+    ]
+
+
+class homg_stats(ctypes.Structure):
+    _fields_ = [
+        ("cycles", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("exec_mode", ctypes.c_int),
+        ("iterations_per_cycle", ctypes.c_int),
+        ("fine_iterations_per_cycle", ctypes.c_int),
+        ("kernels_per_cycle", ctypes.c_int),
+        ("kernels_fixed", ctypes.c_int),
+        ("kernel_launches", ctypes.c_longlong),
+        ("solve_ms", ctypes.c_double),
+        ("coarse_ms", ctypes.c_double),
+        ("fine_ms", ctypes.c_double),
+        ("residual_ms", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+        ("fine_bytes_per_iteration", ctypes.c_double),
+        ("fine_fp64_ops_per_iteration", ctypes.c_double),
+        ("coarse_bytes_per_cycle", ctypes.c_double),
+        ("coarse_fp64_ops_per_cycle", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load ``libhomg.so`` (raises if it has not been built: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("HOMG CUDA library not built (%s missing): run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    lib.homg_default_options.argtypes = [ctypes.POINTER(homg_options)]
+    lib.homg_default_options.restype = None
+    lib.homg_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(homg_options), ctypes.POINTER(vp)]
+    lib.homg_set_stream.argtypes = [vp, vp]
+    lib.homg_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp]
+    lib.homg_solve_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp]
+    lib.homg_residual_norm.argtypes = [vp, vp, vp, dp]
+    lib.homg_get_history.argtypes = [vp, dp, ctypes.c_int]
+    lib.homg_get_stats.argtypes = [vp, ctypes.POINTER(homg_stats)]
+    lib.homg_last_error.argtypes = [vp]
+    lib.homg_last_error.restype = ctypes.c_char_p
+    lib.homg_destroy.argtypes = [vp]
+    lib.homg_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("homg_default_options", "homg_last_error", "homg_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class HomgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("HOMG error %d: %s" % (code, msg))
+        self.code = code
+
+
+def homg_last_error(handle=None):
+    return load().homg_last_error(handle).decode(errors="replace")
+
+
+def homg_default_options():
+    o = homg_options()
+    load().homg_default_options(ctypes.byref(o))
+    return o
+
+
+def _check(rc, handle):
+    if rc < 0:
+        raise HomgError(rc, homg_last_error(handle))
+    return rc
+
+
+def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, schedule=None, exec_mode="auto",
+                strict_fp=False, diverge_factor=0.0):
+    """Create a handle for an (n_nodes)^ndim grid; returns an opaque handle (int)."""
+    lib = load()
+    o = homg_default_options()
+    o.omega_j = omega_j
+    o.max_i = max_i
+    o.exec_mode = EXEC_MODES[exec_mode] if isinstance(exec_mode, str) else int(exec_mode)
+    o.strict_fp = 1 if strict_fp else 0
+    o.diverge_factor = diverge_factor
+    keep = None
+    if schedule is not None:
+        keep = (ctypes.c_int * len(schedule))(*schedule)
+        o.n_schedule = len(schedule)
+        o.schedule = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    dims = (ctypes.c_int64 * ndim)(*([n_nodes] * ndim))
+    h = ctypes.c_void_p()
+    stencil = stencil if stencil is not None else (5 if ndim == 2 else 7)
+    _check(lib.homg_create(ndim, dims, levels, stencil, ctypes.byref(o), ctypes.byref(h)), None)
+    return h.value
+
+
+def homg_set_stream(handle, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default stream)."""
+    raw = getattr(stream, "cuda_stream", stream) or 0
+    return _check(load().homg_set_stream(handle, ctypes.c_void_p(raw)), handle)
+
+
+def _devptr(t, name):
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if str(t.dtype) != "torch.float64" or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def homg_solve(handle, f, u, tol=1e-10, max_cycles=50):
+    """Solve in place on device tensors; returns (status, cycles, relres)."""
+    cyc, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = load().homg_solve(handle, _devptr(f, "f"), _devptr(u, "u"), tol, max_cycles, ctypes.byref(cyc), ctypes.byref(rr))
+    return _check(rc, handle), cyc.value, rr.value
+
+
+def _hostptr(a, name):
+    import numpy as np
+
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda or str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("%s must be a contiguous float64 CPU tensor" % name)
+        return ctypes.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("%s must be a contiguous float64 array" % name)
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def homg_solve_host(handle, f, u, tol=1e-10, max_cycles=50):
+    """Solve with host arrays (copies in and out inside the call); returns (status, cycles, relres)."""
+    cyc, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = load().homg_solve_host(handle, _hostptr(f, "f"), _hostptr(u, "u"), tol, max_cycles, ctypes.byref(cyc),
+                                ctypes.byref(rr))
+    return _check(rc, handle), cyc.value, rr.value
+
+
+def homg_residual_norm(handle, f, u):
+    rr = ctypes.c_double(0.0)
+    _check(load().homg_residual_norm(handle, _devptr(f, "f"), _devptr(u, "u"), ctypes.byref(rr)), handle)
+    return rr.value
+
+
+def homg_get_history(handle, cap=HOMG_MAX_CYCLES + 1):
+    buf = (ctypes.c_double * cap)()
+    cnt = _check(load().homg_get_history(handle, buf, cap), handle)
+    return list(buf[:cnt])
+
+
+def homg_get_stats(handle):
+    s = homg_stats()
+    _check(load().homg_get_stats(handle, ctypes.byref(s)), handle)
+    return {name: getattr(s, name) for name, _ in homg_stats._fields_}
+
+
+def homg_destroy(handle):
+    if handle:
+        load().homg_destroy(handle)
+
+
+class Solver:
+    """Convenience owner of a handle (same arguments as ``homg_create``)."""
+
+    def __init__(self, ndim, n_nodes, levels, **kw):
+        self.ndim, self.n_nodes, self.levels = ndim, n_nodes, levels
+        self.handle = homg_create(ndim, n_nodes, levels, **kw)
+
+    def set_stream(self, stream):
+        return homg_set_stream(self.handle, stream)
+
+    def solve(self, f, u, tol=1e-10, max_cycles=50):
+        return homg_solve(self.handle, f, u, tol, max_cycles)
+
+    def solve_host(self, f, u, tol=1e-10, max_cycles=50):
+        return homg_solve_host(self.handle, f, u, tol, max_cycles)
+
+    def residual_norm(self, f, u):
+        return homg_residual_norm(self.handle, f, u)
+
+    def history(self):
+        return homg_get_history(self.handle)
+
+    def stats(self):
+        return homg_get_stats(self.handle)
+
+    def close(self):
+        homg_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.close()
+        except Exception:
+            pass

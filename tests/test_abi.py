@@ -1,0 +1,98 @@
+"""The C ABI library loads and exports every entry point ``include/homg.h`` declares; host-side
+argument validation runs without a GPU (no compute call is made)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "homg.h")
+
+
+@pytest.fixture(scope="module")
+def homg():
+    import __graft_entry__
+
+    from paper_1108_2045_gb300 import build
+
+    build.build()
+    from paper_1108_2045_gb300 import homg as binding
+
+    binding.load()
+    return binding
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(homg_[a-z_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("homg_create", "homg_solve", "homg_residual_norm", "homg_destroy", "homg_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(homg):
+    lib = ctypes.CDLL(homg.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(homg.EXPORTS) == declared_functions()
+
+
+def test_default_options(homg):
+    o = homg.homg_default_options()
+    assert o.max_i == 32 and o.exec_mode == homg.HOMG_EXEC_AUTO and o.diverge_factor == 1e3 and o.n_schedule == 0
+
+
+@pytest.mark.parametrize(
+    "args,code",
+    [
+        ((1, 129, 7, 5), -1),          # ndim
+        ((2, 129, 7, 7), -1),          # stencil of the wrong dimension
+        ((3, 65, 6, 5), -1),
+        ((2, 128, 7, 5), -2),          # not 2^K + 1
+        ((2, 2, 1, 5), -2),            # K = 0
+        ((2, 129, 8, 5), -1),          # levels > K
+        ((2, 129, 0, 5), -1),          # levels < 1
+        ((2, (1 << 16) + 1, 3, 5), -2),  # beyond the 2-D maximum
+        ((3, (1 << 11) + 1, 3, 7), -2),  # beyond the 3-D maximum
+    ],
+)
+def test_create_rejects_invalid_arguments(homg, args, code):
+    with pytest.raises(homg.HomgError) as ei:
+        homg.homg_create(*args)
+    assert ei.value.code == code
+    assert homg.homg_last_error(None)
+
+
+def test_create_rejects_unequal_sides_and_bad_options(homg):
+    lib = homg.load()
+    dims = (ctypes.c_int64 * 2)(129, 65)
+    h = ctypes.c_void_p()
+    assert lib.homg_create(2, dims, 3, 5, None, ctypes.byref(h)) == homg.HOMG_ESHAPE
+    assert h.value is None
+    for kw in [dict(omega_j=-1.0), dict(max_i=-3), dict(exec_mode=7), dict(diverge_factor=0.5),
+               dict(schedule=[1, 2]), dict(schedule=[3, 0]), dict(schedule=[0, 1, 0], exec_mode="lattice")]:
+        with pytest.raises(homg.HomgError) as ei:
+            homg.homg_create(2, 33, 3, **kw)
+        assert ei.value.code == homg.HOMG_EINVAL, kw
+
+
+def test_null_handle_calls_are_rejected(homg):
+    lib = homg.load()
+    assert lib.homg_solve(None, None, None, 1e-10, 5, None, None) == homg.HOMG_EINVAL
+    assert lib.homg_residual_norm(None, None, None, None) == homg.HOMG_EINVAL
+    assert lib.homg_set_stream(None, None) == homg.HOMG_EINVAL
+    lib.homg_destroy(None)
+
+
+def test_binding_refuses_host_tensors_for_device_calls(homg):
+    import torch
+
+    with pytest.raises(TypeError):
+        homg._devptr(torch.zeros(3, dtype=torch.float64), "f")

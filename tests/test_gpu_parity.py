@@ -1,0 +1,253 @@
+"""GPU path vs the CPU oracle, element by element on the same seeded inputs (GB300 only).
+
+Bar (floating point): after every cycle, ||u_gpu - u_oracle||_2 / ||u_oracle||_2 <= 1e-12. The
+whole-grid form with strict_fp evaluates every formula in the oracle's order and must reproduce its
+iterates bit for bit. Grid sides are 2^K + 1, so every size has a ragged tail against the kernels'
+32 x 8 tiles.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1108_2045_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def homg():
+    import torch
+
+    import __graft_entry__
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    __graft_entry__.build()
+    from paper_1108_2045_gb300 import homg as binding
+
+    return binding
+
+
+def gpu_solve(homg, f_np, levels, u0=None, tol=0.0, max_cycles=1, **kw):
+    import torch
+
+    ndim = f_np.ndim
+    n1 = f_np.shape[0]
+    with homg.Solver(ndim, n1, levels, **kw) as s:
+        f = torch.from_numpy(np.ascontiguousarray(f_np)).cuda()
+        u = torch.zeros_like(f) if u0 is None else torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+        status, cycles, relres = s.solve(f, u, tol=tol, max_cycles=max_cycles)
+        hist = s.history()
+        stats = s.stats()
+        return u.cpu().numpy(), status, cycles, relres, hist, stats
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def oracle_kw(kw):
+    return {k: v for k, v in kw.items() if k in ("max_i", "omega_j", "schedule")}
+
+
+CASES_2D = [(3, 3), (5, 5), (7, 7), (8, 8), (8, 5), (10, 10), (10, 6)]
+
+
+@pytest.mark.parametrize("K,levels", CASES_2D)
+@pytest.mark.parametrize("mode", ["wholegrid", "lattice"])
+@pytest.mark.parametrize("strict", [True, False])
+def test_cycles_match_oracle_2d(homg, K, levels, mode, strict):
+    n = 2 ** K
+    f = inputs.uniform_rhs(n, 2, seed=K)
+    for k in (1, 2, 3) if K <= 8 else (1, 2):
+        ref, rst, rcyc, rhist = oracle.solve(f, levels, tol=0.0, max_cycles=k)
+        got, st, cyc, rr, hist, _ = gpu_solve(homg, f, levels, max_cycles=k, exec_mode=mode, strict_fp=strict)
+        assert st == homg.HOMG_NOT_CONVERGED and cyc == k
+        if strict and mode == "wholegrid":
+            np.testing.assert_array_equal(got, ref)
+        else:
+            assert rel(got, ref) <= TOL, (k, rel(got, ref))
+        np.testing.assert_allclose(hist, rhist, rtol=1e-9)
+
+
+@pytest.mark.parametrize("K,levels", [(3, 3), (4, 4), (5, 5), (6, 4)])
+@pytest.mark.parametrize("mode", ["wholegrid", "lattice"])
+@pytest.mark.parametrize("strict", [True, False])
+def test_cycles_match_oracle_3d(homg, K, levels, mode, strict):
+    n = 2 ** K
+    f = inputs.normal_rhs(n, 3, seed=K)
+    for k in (1, 2):
+        ref, _, _, _ = oracle.solve(f, levels, tol=0.0, max_cycles=k)
+        got, st, cyc, rr, hist, _ = gpu_solve(homg, f, levels, max_cycles=k, exec_mode=mode, strict_fp=strict)
+        assert cyc == k
+        if strict and mode == "wholegrid":
+            np.testing.assert_array_equal(got, ref)
+        else:
+            assert rel(got, ref) <= TOL, (k, rel(got, ref))
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [
+        dict(max_i=1),
+        dict(max_i=2),
+        dict(max_i=4),
+        dict(omega_j=1.0),
+        dict(omega_j=0.6),
+        dict(schedule=[6, 6, 4, 4, 4, 1, 0, 0]),              # levels skipped, never increasing
+        dict(schedule=[5, 3, 4, 2, 0, 1, 0, 0]),              # goes back to coarser levels
+        dict(schedule=[0, 0, 0]),
+        dict(schedule=[2, 0], exec_mode="lattice"),
+    ],
+)
+@pytest.mark.parametrize("strict", [True, False])
+def test_options_match_oracle(homg, kw, strict):
+    n, levels = 128, 7
+    f = inputs.uniform_rhs(n, 2, seed=3)
+    ref, _, _, _ = oracle.solve(f, levels, tol=0.0, max_cycles=2, **oracle_kw(kw))
+    got, st, cyc, rr, hist, stats = gpu_solve(homg, f, levels, max_cycles=2, strict_fp=strict, **kw)
+    assert cyc == 2
+    assert rel(got, ref) <= TOL, rel(got, ref)
+    if strict and stats["exec_mode"] == homg.HOMG_EXEC_WHOLEGRID:
+        np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("mode", ["wholegrid", "lattice"])
+def test_full_solve_cfg1(homg, mode):
+    # 129^2 nodes, 7 levels, f = 2 pi^2 sin sin, solve to 1e-10
+    n, K = 128, 7
+    f = inputs.sine_rhs(n)
+    ref, rst, rcyc, rhist = oracle.solve(f, K, tol=1e-10, max_cycles=50)
+    got, st, cyc, rr, hist, stats = gpu_solve(homg, f, K, tol=1e-10, max_cycles=50, exec_mode=mode)
+    assert st == homg.HOMG_OK and rst == oracle.OK
+    assert cyc == rcyc
+    assert rr <= 1e-10
+    assert rel(got, ref) <= TOL
+    # an independent check of the returned solution's residual
+    r = oracle.residual(f, got)
+    assert oracle.norm_interior(r) / oracle.norm_interior(f) <= 1e-10
+    # late entries sit near the FP64 floor of the residual itself (about 1e-16 * ||A|| ||u|| / ||f||)
+    np.testing.assert_allclose(hist, rhist, rtol=1e-6, atol=1e-14)
+    assert stats["iterations_per_cycle"] == 126 and stats["fine_iterations_per_cycle"] == 32
+
+
+def test_zero_rhs_gives_zero(homg):
+    n = 64
+    f = np.zeros((n + 1, n + 1))
+    u0 = inputs.uniform_rhs(n, 2, seed=1)
+    u0[0, :] = 7.0  # boundary content is never read or written
+    got, st, cyc, rr, hist, _ = gpu_solve(homg, f, 6, u0=u0, tol=1e-10, max_cycles=10)
+    assert st == homg.HOMG_OK and cyc == 0 and rr == 0.0
+    assert np.all(got[1:-1, 1:-1] == 0) and np.all(got[0, :] == 7.0)
+
+
+def test_max_cycles_zero_and_initial_guess(homg):
+    n, K = 64, 6
+    f = inputs.uniform_rhs(n, 2, seed=2)
+    u0 = np.zeros_like(f)
+    u0[1:-1, 1:-1] = inputs.normal_rhs(n, 2, seed=4)[1:-1, 1:-1] * 1e-3
+    got, st, cyc, rr, hist, _ = gpu_solve(homg, f, K, u0=u0, tol=1e-10, max_cycles=0)
+    assert st == homg.HOMG_NOT_CONVERGED and cyc == 0
+    np.testing.assert_array_equal(got, u0)
+    r0 = oracle.norm_interior(oracle.residual(f, u0)) / oracle.norm_interior(f)
+    assert rr == pytest.approx(r0, rel=1e-12)
+    ref, _, rcyc, _ = oracle.solve(f, K, u0=u0, tol=1e-10, max_cycles=40)
+    got, st, cyc, rr, hist, _ = gpu_solve(homg, f, K, u0=u0, tol=1e-10, max_cycles=40)
+    assert st == homg.HOMG_OK and cyc == rcyc and rel(got, ref) <= TOL
+
+
+def test_nan_rhs_diverges(homg):
+    n = 32
+    f = inputs.uniform_rhs(n, 2, seed=5)
+    f[4, 9] = np.nan
+    got, st, cyc, rr, hist, _ = gpu_solve(homg, f, 5, tol=1e-10, max_cycles=10)
+    assert st == homg.HOMG_DIVERGED
+
+
+def test_loose_tolerance_stops_early(homg):
+    n = 64
+    f = inputs.uniform_rhs(n, 2, seed=6)
+    got, st, cyc, rr, hist, _ = gpu_solve(homg, f, 6, tol=2.0, max_cycles=10)
+    assert st == homg.HOMG_OK and cyc == 0 and np.all(got == 0)
+    ref, _, rcyc, _ = oracle.solve(f, 6, tol=1e-3, max_cycles=10)
+    got, st, cyc, rr, hist, _ = gpu_solve(homg, f, 6, tol=1e-3, max_cycles=10)
+    assert cyc == rcyc and rr <= 1e-3
+
+
+def test_residual_norm_and_host_solve(homg):
+    import torch
+
+    n, K = 256, 8
+    f_np = inputs.uniform_rhs(n, 2, seed=7)
+    u_np = inputs.normal_rhs(n, 2, seed=8) * 1e-4
+    u_np[0, :] = u_np[-1, :] = u_np[:, 0] = u_np[:, -1] = 0
+    with homg.Solver(2, n + 1, K) as s:
+        f = torch.from_numpy(f_np).cuda()
+        u = torch.from_numpy(u_np).cuda()
+        rr = s.residual_norm(f, u)
+        expect = oracle.norm_interior(oracle.residual(f_np, u_np)) / oracle.norm_interior(f_np)
+        assert rr == pytest.approx(expect, rel=1e-12)
+        u_dev = torch.zeros_like(f)
+        st1, c1, r1 = s.solve(f, u_dev, tol=1e-10, max_cycles=30)
+        u_host = np.zeros_like(f_np)
+        st2, c2, r2 = s.solve_host(f_np, u_host, tol=1e-10, max_cycles=30)
+        assert (st1, c1) == (st2, c2) and r1 == r2
+        np.testing.assert_array_equal(u_dev.cpu().numpy(), u_host)
+        # a larger max_cycles grows the solve graph; a smaller one reuses it
+        st3, c3, r3 = s.solve(f, torch.zeros_like(f), tol=1e-10, max_cycles=60)
+        st4, c4, r4 = s.solve(f, torch.zeros_like(f), tol=1e-10, max_cycles=5)
+        assert (st3, c3) == (st1, c1) and st4 == homg.HOMG_NOT_CONVERGED and c4 == 5
+
+
+def test_solve_on_side_stream(homg):
+    import torch
+
+    n, K = 128, 7
+    f_np = inputs.uniform_rhs(n, 2, seed=9)
+    ref, _, _, _ = oracle.solve(f_np, K, tol=0.0, max_cycles=2)
+    stream = torch.cuda.Stream()
+    with homg.Solver(2, n + 1, K) as s, torch.cuda.stream(stream):
+        f = torch.from_numpy(f_np).cuda()
+        u = torch.zeros_like(f)
+        stream.wait_stream(torch.cuda.default_stream())
+        s.set_stream(stream)
+        s.solve(f, u, tol=0.0, max_cycles=2)
+        got = u.cpu().numpy()
+    assert rel(got, ref) <= TOL
+
+
+_BENCH_REF = {}
+
+
+def bench_reference():
+    """Oracle's first cycle on the benchmark grid (about half a minute of CPU; computed once)."""
+    if not _BENCH_REF:
+        f = inputs.uniform_rhs(4096, 2, seed=0)
+        ref, _, _, rhist = oracle.solve(f, 12, tol=0.0, max_cycles=1)
+        _BENCH_REF.update(f=f, ref=ref, hist=rhist)
+    return _BENCH_REF["f"], _BENCH_REF["ref"], _BENCH_REF["hist"]
+
+
+@pytest.mark.parametrize("mode", ["lattice", "wholegrid"])
+def test_benchmark_grid_first_cycle_matches_oracle(homg, mode):
+    # 4097^2 nodes, 12 levels, f iid uniform[-1, 1] (seed 0): the launch configuration the benchmark times
+    K = 12
+    f, ref, rhist = bench_reference()
+    got, st, cyc, rr, hist, _ = gpu_solve(homg, f, K, max_cycles=1, exec_mode=mode)
+    assert rel(got, ref) <= TOL, rel(got, ref)
+    np.testing.assert_allclose(hist, rhist, rtol=1e-9)
+
+
+def test_benchmark_grid_full_solve(homg):
+    # the benchmark's whole solve: converged result checked by the oracle's own residual
+    n, K = 4096, 12
+    f = inputs.uniform_rhs(n, 2, seed=0)
+    got, st, cyc, rr, hist, stats = gpu_solve(homg, f, K, tol=1e-10, max_cycles=50)
+    assert st == homg.HOMG_OK and rr <= 1e-10
+    r = oracle.residual(f, got)
+    assert oracle.norm_interior(r) / oracle.norm_interior(f) <= 1e-10
+    assert np.all(np.diff(hist) < 0)
+    assert stats["iterations_per_cycle"] == 286
