@@ -170,6 +170,29 @@ const char* homg_last_error(homg_handle h);
 /* Release every resource of h (no-op for NULL). */
 void homg_destroy(homg_handle h);
 
+/* Capacity of the static scratch used by homg_residual_norm_noalloc: one partial sum per thread
+ * block of the residual kernel, at most this many (2-D grids up to 4097^2, 3-D up to 257^3). */
+#define HOMG_NOALLOC_MAX_BLOCKS 65536
+
+/* Allocation-free relative residual ||f - A u||_2 / ||f||_2 (interior nodes) of device arrays f
+ * and u on a (dims[0])^ndim node grid, for callers that cannot call cudaMalloc (it synchronises the
+ * device, and fails when another allocator already holds the memory) and so cannot create a handle.
+ * The paper has no counterpart: this is a service entry point of the library, the same computation
+ * as homg_residual_norm without a handle.
+ *   dims       ndim equal node counts 2^K + 1; grids needing more than HOMG_NOALLOC_MAX_BLOCKS
+ *              partial sums are rejected with HOMG_ESHAPE and a message in homg_last_error(NULL).
+ *   stream     cudaStream_t to run on (NULL = legacy default stream); synchronised before return.
+ *   relres_out host pointer receiving the result (0 when f = 0 and u's interior is 0, +inf when
+ *              f = 0 otherwise).
+ * Scratch: a fixed 1 MiB file-scope device array, held by every GPU that loads the library until
+ * the process exits, shared by all calls and keeping the last call's contents (every value a call
+ * reads is written by that call first). Calls whose work overlaps on one GPU (other host threads,
+ * other streams) race on it: serialise them. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) once for that device; make that first call before any
+ * stream capture. Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+int homg_residual_norm_noalloc(int ndim, const int64_t* dims, const double* f, const double* u, double* relres_out,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

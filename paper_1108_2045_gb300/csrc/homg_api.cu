@@ -450,6 +450,10 @@ double elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 }  // namespace
 
+namespace homg {
+void set_null_handle_error(const char* msg) { snprintf(g_create_error, sizeof(g_create_error), "%s", msg); }
+}  // namespace homg
+
 extern "C" {
 
 void homg_default_options(homg_options* opt) {

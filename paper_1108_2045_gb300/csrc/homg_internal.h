@@ -113,6 +113,8 @@ int residual_blocks(int ndim, int n);
 cudaError_t launch_restrict(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s);
-cudaError_t launch_zero(int ndim, Grid g, cudaStream_t s);
+
+// Message reported by homg_last_error(NULL) (errors of calls made without a handle).
+void set_null_handle_error(const char* msg);
 
 }  // namespace homg

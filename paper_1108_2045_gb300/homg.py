@@ -31,6 +31,7 @@ EXPORTS = [
     "homg_get_stats",
     "homg_last_error",
     "homg_destroy",
+    "homg_residual_norm_noalloc",
 ]
 
 
@@ -92,6 +93,7 @@ def load(path=LIB_PATH):
     lib.homg_get_stats.argtypes = [vp, ctypes.POINTER(homg_stats)]
     lib.homg_last_error.argtypes = [vp]
     lib.homg_last_error.restype = ctypes.c_char_p
+    lib.homg_residual_norm_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), vp, vp, dp, vp]
     lib.homg_destroy.argtypes = [vp]
     lib.homg_destroy.restype = None
     for name in EXPORTS:
@@ -189,6 +191,18 @@ def homg_solve_host(handle, f, u, tol=1e-10, max_cycles=50):
 def homg_residual_norm(handle, f, u):
     rr = ctypes.c_double(0.0)
     _check(load().homg_residual_norm(handle, _devptr(f, "f"), _devptr(u, "u"), ctypes.byref(rr)), handle)
+    return rr.value
+
+
+def homg_residual_norm_noalloc(f, u, stream=None):
+    """||f - A u|| / ||f|| of device tensors without a handle; the library allocates nothing for it
+    (its scratch is a fixed static device array shared by all calls: do not overlap calls)."""
+    ndim = f.dim()
+    dims = (ctypes.c_int64 * ndim)(*f.shape)
+    rr = ctypes.c_double(0.0)
+    raw = getattr(stream, "cuda_stream", stream) or 0
+    _check(load().homg_residual_norm_noalloc(ndim, dims, _devptr(f, "f"), _devptr(u, "u"), ctypes.byref(rr),
+                                             ctypes.c_void_p(raw)), None)
     return rr.value
 
 
