@@ -179,7 +179,7 @@ def run(args):
     f = torch.from_numpy(f_np).to(dev)
     u = torch.zeros_like(f)
     stream = torch.cuda.current_stream(dev)
-    solver = homg.Solver(2, N_SIDE + 1, LEVELS, max_i=MAX_I, exec_mode=args.exec)
+    solver = homg.Solver(2, N_SIDE + 1, LEVELS, max_i=MAX_I, exec_mode=args.exec, launch_mode=args.launch)
     solver.set_stream(stream)
 
     def barrier():
@@ -279,7 +279,7 @@ def run(args):
                    "cycles": stats[-1]["cycles"], "final_relres": relres,
                    "iterations_per_cycle": stats[0]["iterations_per_cycle"],
                    "l2": "working set ~0.8 GB > 126 MB L2; no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "launch": args.launch},
         "roofline": {"kernel": "k_iterate (level-0 HOMG iteration: damped Jacobi on every interior node)",
                      "bound": "alu", "achieved": alu_achieved, "peak": FP64_PEAK_OPS / 1e12,
                      "unit": "TFP64op/s", "frac": alu_achieved / (FP64_PEAK_OPS / 1e12),
@@ -315,6 +315,8 @@ def main():
     p.add_argument("--impl", default="homg", choices=["homg", "reference"])
     p.add_argument("--exec", default="auto", choices=["auto", "lattice", "wholegrid"])
     p.add_argument("--wholegrid-steps", type=int, default=2)
+    p.add_argument("--launch", default="graph", choices=["graph", "stream"],
+                   help="stream: enqueue kernels directly (for profilers that cannot see inside conditional graphs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
     if args.warmup < 3:

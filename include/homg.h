@@ -91,7 +91,15 @@ typedef struct homg_options {
     int strict_fp;
     /* Divergence threshold on the relative residual, as a multiple of the initial one. 0 = 1e3. */
     double diverge_factor;
+    /* HOMG_LAUNCH_GRAPH (default): the whole solve is one CUDA graph launch with device-side
+     * conditional nodes. HOMG_LAUNCH_STREAM: the same kernels enqueued directly on the stream, the
+     * host reading the cycle state once per cycle; meant for profilers and debuggers that cannot
+     * look inside graphs with conditional nodes. Results are identical. */
+    int launch_mode;
 } homg_options;
+
+#define HOMG_LAUNCH_GRAPH 0
+#define HOMG_LAUNCH_STREAM 1
 
 /* Statistics of the last homg_solve on a handle (times from CUDA events recorded on the handle's
  * stream inside the solve graph; zero when the last call failed). */
@@ -171,7 +179,7 @@ const char* homg_last_error(homg_handle h);
 void homg_destroy(homg_handle h);
 
 /* Capacity of the static scratch used by homg_residual_norm_noalloc: one partial sum per thread
- * block of the residual kernel, at most this many (2-D grids up to 4097^2, 3-D up to 257^3). */
+ * block of the residual kernel, at most this many (2-D grids up to 8193^2, 3-D up to 257^3). */
 #define HOMG_NOALLOC_MAX_BLOCKS 65536
 
 /* Allocation-free relative residual ||f - A u||_2 / ||f||_2 (interior nodes) of device arrays f

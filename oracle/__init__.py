@@ -10,7 +10,9 @@ from .oracle import (  # noqa: F401
     DIVERGED,
     NOT_CONVERGED,
     OK,
+    bf16_round,
     build,
+    cycle_lp,
     cycle,
     default_omega_j,
     iteration,
@@ -19,4 +21,5 @@ from .oracle import (  # noqa: F401
     residual,
     restrict,
     solve,
+    solve_mixed,
 )

@@ -407,3 +407,244 @@ int homg_oracle_solve(int ndim, int64_t n, int levels, const int *sched, int nsc
     if (relres_out) *relres_out = rr;
     return status;
 }
+
+/* ========================================================================================== */
+/* Low-precision cycle for mixed-precision solves (Sec. 4: the paper's computations are all in  */
+/* single precision). The cycle's values -- restricted sources, iterates and variations -- are  */
+/* stored and computed in IEEE binary32 (prec = 1), or computed in binary32 and stored as       */
+/* bfloat16 (prec = 2), following exactly the steps and canonical operation order of the FP64   */
+/* functions above. The residual that feeds a cycle, the update u += e and the norms stay       */
+/* binary64 in homg_oracle_solve_mixed: the restart loop is then iterative refinement.          */
+/* ========================================================================================== */
+
+/* bfloat16 keeps the sign, the 8 exponent bits and the top 7 fraction bits of binary32; rounding */
+/* to it is round-to-nearest-even on the 16 dropped bits. NaN stays NaN (made quiet).            */
+static float bf16_round(float x) {
+    uint32_t b;
+    memcpy(&b, &x, sizeof(b));
+    if ((b & 0x7f800000u) == 0x7f800000u) {
+        if (b & 0x007fffffu) b |= 0x00400000u;
+        b &= 0xffff0000u;
+    } else {
+        uint32_t lsb = (b >> 16) & 1u;
+        b += 0x7fffu + lsb;
+        b &= 0xffff0000u;
+    }
+    memcpy(&x, &b, sizeof(x));
+    return x;
+}
+
+static float store_lp(float x, int prec) { return prec == 2 ? bf16_round(x) : x; }
+
+float homg_oracle_bf16_round(float x) { return bf16_round(x); }
+
+static float interp2f(const float *d, int64_t n, int mp, int64_t i, int64_t j) {
+    const int64_t lp = (int64_t)1 << mp, nc = n >> mp;
+    int64_t I0 = i >> mp, a = i & (lp - 1);
+    int64_t J0 = j >> mp, b = j & (lp - 1);
+    int64_t I1 = (a == 0) ? I0 : I0 + 1, J1 = (b == 0) ? J0 : J0 + 1;
+    float wx0 = (float)(lp - a) / (float)lp, wx1 = (float)a / (float)lp;
+    float wy0 = (float)(lp - b) / (float)lp, wy1 = (float)b / (float)lp;
+    float d00 = d[J0 * (nc + 1) + I0], d10 = d[J0 * (nc + 1) + I1];
+    float d01 = d[J1 * (nc + 1) + I0], d11 = d[J1 * (nc + 1) + I1];
+    return ((wx0 * wy0) * d00 + (wx1 * wy0) * d10) + ((wx0 * wy1) * d01 + (wx1 * wy1) * d11);
+}
+
+static float interp3f(const float *d, int64_t n, int mp, int64_t i, int64_t j, int64_t k) {
+    const int64_t lp = (int64_t)1 << mp, nc = n >> mp;
+    int64_t I0 = i >> mp, a = i & (lp - 1);
+    int64_t J0 = j >> mp, b = j & (lp - 1);
+    int64_t K0 = k >> mp, c = k & (lp - 1);
+    int64_t I1 = (a == 0) ? I0 : I0 + 1, J1 = (b == 0) ? J0 : J0 + 1, K1 = (c == 0) ? K0 : K0 + 1;
+    float wx[2] = {(float)(lp - a) / (float)lp, (float)a / (float)lp};
+    float wy[2] = {(float)(lp - b) / (float)lp, (float)b / (float)lp};
+    float wz[2] = {(float)(lp - c) / (float)lp, (float)c / (float)lp};
+    int64_t Ix[2] = {I0, I1}, Jy[2] = {J0, J1}, Kz[2] = {K0, K1};
+    float t[2][2][2];
+    for (int z = 0; z < 2; ++z)
+        for (int y = 0; y < 2; ++y)
+            for (int x = 0; x < 2; ++x)
+                t[z][y][x] = ((wx[x] * wy[y]) * wz[z]) * d[(Kz[z] * (nc + 1) + Jy[y]) * (nc + 1) + Ix[x]];
+    return ((t[0][0][0] + t[0][0][1]) + (t[0][1][0] + t[0][1][1])) +
+           ((t[1][0][0] + t[1][0][1]) + (t[1][1][0] + t[1][1][1]));
+}
+
+/* Full weighting (see homg_oracle_restrict), single precision, result stored at precision prec. */
+void homg_oracle_restrict_lp(int ndim, int64_t nf, const float *Ff, float *Fc, int prec) {
+    const int64_t nc = nf / 2;
+    if (ndim == 2) {
+#define FF(I, J) Ff[(J) * (nf + 1) + (I)]
+        for (int64_t J = 0; J <= nc; ++J)
+            for (int64_t I = 0; I <= nc; ++I) {
+                int64_t q = J * (nc + 1) + I;
+                if (I == 0 || J == 0 || I == nc || J == nc) { Fc[q] = 0.0f; continue; }
+                int64_t i = 2 * I, j = 2 * J;
+                float c = FF(i, j);
+                float edges = ((FF(i - 1, j) + FF(i + 1, j)) + FF(i, j - 1)) + FF(i, j + 1);
+                float corners = ((FF(i - 1, j - 1) + FF(i + 1, j - 1)) + FF(i - 1, j + 1)) + FF(i + 1, j + 1);
+                Fc[q] = store_lp((4.0f * c + 2.0f * edges + corners) / 16.0f, prec);
+            }
+#undef FF
+    } else {
+#define FF(I, J, K) Ff[((K) * (nf + 1) + (J)) * (nf + 1) + (I)]
+        for (int64_t K = 0; K <= nc; ++K)
+            for (int64_t J = 0; J <= nc; ++J)
+                for (int64_t I = 0; I <= nc; ++I) {
+                    int64_t q = (K * (nc + 1) + J) * (nc + 1) + I;
+                    if (I == 0 || J == 0 || K == 0 || I == nc || J == nc || K == nc) { Fc[q] = 0.0f; continue; }
+                    int64_t i = 2 * I, j = 2 * J, k = 2 * K;
+                    float c = FF(i, j, k);
+                    float faces = 0.0f, edges = 0.0f, corners = 0.0f;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                int nz = (dx != 0) + (dy != 0) + (dz != 0);
+                                float v = FF(i + dx, j + dy, k + dz);
+                                if (nz == 1) faces = faces + v;
+                                else if (nz == 2) edges = edges + v;
+                                else if (nz == 3) corners = corners + v;
+                            }
+                    Fc[q] = store_lp((8.0f * c + 4.0f * faces + 2.0f * edges + corners) / 64.0f, prec);
+                }
+#undef FF
+    }
+}
+
+/* One HOMG iteration (see homg_oracle_iteration), single precision; stored values at prec. */
+void homg_oracle_iteration_lp(int ndim, int64_t n, int m, int mprev, float omega, const float *Fm,
+                              const float *dprev, const float *e_old, float *e_new, float *d_new, int prec) {
+    const int64_t l = (int64_t)1 << m, nm = n >> m, side = n + 1;
+    const int64_t lp = (mprev >= 0) ? ((int64_t)1 << mprev) : 1;
+    const float h = 1.0f / (float)n;
+    const float hm = h * (float)l;
+    const float hm2 = hm * hm;
+    const int64_t dsize = (ndim == 2) ? (nm + 1) * (nm + 1) : (nm + 1) * (nm + 1) * (nm + 1);
+    for (int64_t q = 0; q < dsize; ++q) d_new[q] = 0.0f;
+    const int64_t kmax = (ndim == 2) ? 0 : n;
+    for (int64_t k = 0; k <= kmax; ++k)
+        for (int64_t j = 0; j <= n; ++j)
+            for (int64_t i = 0; i <= n; ++i) {
+                int64_t p = (k * side + j) * side + i;
+                int boundary = i == 0 || j == 0 || i == n || j == n || (ndim == 3 && (k == 0 || k == n));
+                if (boundary) { e_new[p] = 0.0f; continue; }
+                float v = e_old[p];
+                int on = (i & (l - 1)) == 0 && (j & (l - 1)) == 0 && (ndim == 2 || (k & (l - 1)) == 0);
+                if (on) { /* p on the level-m lattice */
+                    float lap;
+                    if (ndim == 2) {
+                        lap = 4.0f * v;
+                        lap = lap - e_old[j * side + (i - l)];
+                        lap = lap - e_old[j * side + (i + l)];
+                        lap = lap - e_old[(j - l) * side + i];
+                        lap = lap - e_old[(j + l) * side + i];
+                    } else {
+                        lap = 6.0f * v;
+                        lap = lap - e_old[(k * side + j) * side + (i - l)];
+                        lap = lap - e_old[(k * side + j) * side + (i + l)];
+                        lap = lap - e_old[(k * side + (j - l)) * side + i];
+                        lap = lap - e_old[(k * side + (j + l)) * side + i];
+                        lap = lap - e_old[((k - l) * side + j) * side + i];
+                        lap = lap - e_old[((k + l) * side + j) * side + i];
+                    }
+                    int64_t q = ((k >> m) * (nm + 1) + (j >> m)) * (nm + 1) + (i >> m);
+                    float delta = omega * (hm2 * Fm[q] - lap);
+                    d_new[q] = store_lp(delta, prec);
+                    v = v + delta;
+                }
+                if (mprev >= 0) {
+                    int on_prev = (i & (lp - 1)) == 0 && (j & (lp - 1)) == 0 && (ndim == 2 || (k & (lp - 1)) == 0);
+                    if (!on_prev) v = v + ((ndim == 2) ? interp2f(dprev, n, mprev, i, j) : interp3f(dprev, n, mprev, i, j, k));
+                }
+                e_new[p] = store_lp(v, prec);
+            }
+}
+
+/* One low-precision HOMG cycle on A e = F0 (see homg_oracle_cycle); F0 and e are binary64 arrays
+ * at the interface, rounded to / widened from the cycle's precision. */
+int homg_oracle_cycle_lp(int ndim, int64_t n, int levels, const int *sched, int nsched, double omega_j, int prec,
+                         const double *F0, double *e) {
+    int K = log2_exact(n);
+    if ((ndim != 2 && ndim != 3) || K < 1 || levels < 1 || levels > K || nsched < 1 || (prec != 1 && prec != 2))
+        return HOMG_ORACLE_EINVAL;
+    for (int t = 0; t < nsched; ++t)
+        if (sched[t] < 0 || sched[t] >= levels) return HOMG_ORACLE_EINVAL;
+    if (sched[nsched - 1] != 0) return HOMG_ORACLE_EINVAL;
+    const float omega = (float)(omega_j / (2.0 * ndim));
+    const int64_t total = ipow(n + 1, ndim);
+    float **F = (float **)calloc((size_t)levels, sizeof(float *));
+    float *ea = (float *)calloc((size_t)total, sizeof(float));
+    float *eb = (float *)malloc((size_t)total * sizeof(float));
+    float *dA = (float *)malloc((size_t)total * sizeof(float));
+    float *dB = (float *)malloc((size_t)total * sizeof(float));
+    int rc = HOMG_ORACLE_OK;
+    if (!F || !ea || !eb || !dA || !dB) { rc = HOMG_ORACLE_ENOMEM; goto done; }
+    for (int m = 0; m < levels; ++m) {
+        F[m] = (float *)malloc((size_t)ipow((n >> m) + 1, ndim) * sizeof(float));
+        if (!F[m]) { rc = HOMG_ORACLE_ENOMEM; goto done; }
+    }
+    for (int64_t p = 0; p < total; ++p) F[0][p] = store_lp((float)F0[p], prec);
+    for (int m = 1; m < levels; ++m) homg_oracle_restrict_lp(ndim, n >> (m - 1), F[m - 1], F[m], prec);
+    {
+        float *e_old = ea, *e_new = eb, *dprev = dA, *dnew = dB;
+        int mprev = -1;
+        for (int t = 0; t < nsched; ++t) {
+            int m = sched[t];
+            homg_oracle_iteration_lp(ndim, n, m, mprev, omega, F[m], dprev, e_old, e_new, dnew, prec);
+            float *tmp = e_old; e_old = e_new; e_new = tmp;
+            tmp = dprev; dprev = dnew; dnew = tmp;
+            mprev = m;
+        }
+        for (int64_t p = 0; p < total; ++p) e[p] = (double)e_old[p];
+    }
+done:
+    if (F) for (int m = 0; m < levels; ++m) free(F[m]);
+    free(F); free(ea); free(eb); free(dA); free(dB);
+    return rc;
+}
+
+/* Mixed-precision restarted solve: binary64 residual, update and norms around low-precision     */
+/* cycles (prec 1: binary32, prec 2: bfloat16 storage). Same stopping rules as homg_oracle_solve. */
+int homg_oracle_solve_mixed(int ndim, int64_t n, int levels, const int *sched, int nsched, double omega_j,
+                            double div_factor, int prec, const double *f, double *u, double tol, int max_cycles,
+                            double *hist, int *cycles_out, double *relres_out) {
+    int K = log2_exact(n);
+    if ((ndim != 2 && ndim != 3) || K < 1 || levels < 1 || levels > K || max_cycles < 0 || (prec != 1 && prec != 2))
+        return HOMG_ORACLE_EINVAL;
+    const int64_t side = n + 1;
+    const int64_t total = ipow(side, ndim);
+    double fnorm = homg_oracle_norm_interior(ndim, n, f);
+    if (fnorm == 0.0) {
+        for (int64_t p = 0; p < total; ++p) {
+            int64_t i = p % side, j = (p / side) % side, k = (ndim == 3) ? p / (side * side) : 1;
+            if (i > 0 && j > 0 && k > 0 && i < n && j < n && k < n) u[p] = 0.0;
+        }
+        if (hist) hist[0] = 0.0;
+        if (cycles_out) *cycles_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        return HOMG_ORACLE_OK;
+    }
+    double *r = (double *)malloc((size_t)total * sizeof(double));
+    double *e = (double *)malloc((size_t)total * sizeof(double));
+    if (!r || !e) { free(r); free(e); return HOMG_ORACLE_ENOMEM; }
+    int status = HOMG_ORACLE_NOT_CONVERGED, k;
+    double rr = 0.0, rr0 = 0.0;
+    for (k = 0;; ++k) {
+        homg_oracle_residual(ndim, n, f, u, r);
+        rr = homg_oracle_norm_interior(ndim, n, r) / fnorm;
+        if (hist) hist[k] = rr;
+        if (k == 0) rr0 = rr;
+        if (rr <= tol) { status = HOMG_ORACLE_OK; break; }
+        if (!isfinite(rr) || rr > div_factor * rr0) { status = HOMG_ORACLE_DIVERGED; break; }
+        if (k == max_cycles) { status = HOMG_ORACLE_NOT_CONVERGED; break; }
+        int rc = homg_oracle_cycle_lp(ndim, n, levels, sched, nsched, omega_j, prec, r, e);
+        if (rc != HOMG_ORACLE_OK) { free(r); free(e); return rc; }
+        for (int64_t p = 0; p < total; ++p) {
+            int64_t i = p % side, j = (p / side) % side, kk = (ndim == 3) ? p / (side * side) : 1;
+            if (i > 0 && j > 0 && kk > 0 && i < n && j < n && kk < n) u[p] = u[p] + e[p];
+        }
+    }
+    free(r); free(e);
+    if (cycles_out) *cycles_out = k;
+    if (relres_out) *relres_out = rr;
+    return status;
+}

@@ -45,6 +45,13 @@ def _load(path=None):
         lib.homg_oracle_cycle.argtypes = [ctypes.c_int, i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double, P, P]
         lib.homg_oracle_solve.argtypes = [ctypes.c_int, i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, P, P, ctypes.c_double, ctypes.c_int, P, IP, P]
+        lib.homg_oracle_cycle_lp.argtypes = [ctypes.c_int, i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, P, P]
+        lib.homg_oracle_solve_mixed.argtypes = [ctypes.c_int, i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int,
+                                                P, IP, P]
+        lib.homg_oracle_bf16_round.argtypes = [ctypes.c_float]
+        lib.homg_oracle_bf16_round.restype = ctypes.c_float
         _lib = lib
     return _lib
 
@@ -143,6 +150,49 @@ def cycle(F0, levels, schedule=None, max_i=32, omega_j=None):
     if rc != 0:
         raise ValueError("oracle cycle rejected its arguments (rc=%d)" % rc)
     return e
+
+
+PRECISIONS = {"fp32": 1, "bf16": 2}
+
+
+def bf16_round(x):
+    """Round a binary32 value to bfloat16 (round to nearest even), as the low-precision cycle stores."""
+    return _load().homg_oracle_bf16_round(float(x))
+
+
+def cycle_lp(F0, levels, precision="fp32", schedule=None, max_i=32, omega_j=None):
+    """One low-precision HOMG cycle (binary32 arithmetic; fp32 or bf16 storage) on A e = F0."""
+    ndim, n = _grid_n(F0)
+    if omega_j is None:
+        omega_j = default_omega_j(ndim)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    e = np.empty_like(F0)
+    rc = _load().homg_oracle_cycle_lp(ndim, n, levels, cs, len(sched), omega_j, PRECISIONS[precision],
+                                      _p(np.ascontiguousarray(F0)), _p(e))
+    if rc != 0:
+        raise ValueError("oracle cycle rejected its arguments (rc=%d)" % rc)
+    return e
+
+
+def solve_mixed(f, levels, precision="fp32", u0=None, tol=1e-10, max_cycles=100, schedule=None, max_i=32,
+                omega_j=None, div_factor=1e3):
+    """Restarted solve with binary64 residual/update/norms around low-precision cycles."""
+    ndim, n = _grid_n(f)
+    if omega_j is None:
+        omega_j = default_omega_j(ndim)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    u = np.zeros_like(f) if u0 is None else np.array(u0, dtype=np.float64, order="C", copy=True)
+    hist = np.zeros(max_cycles + 1)
+    cyc = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    status = _load().homg_oracle_solve_mixed(ndim, n, levels, cs, len(sched), omega_j, div_factor,
+                                             PRECISIONS[precision], _p(np.ascontiguousarray(f)), _p(u), tol,
+                                             max_cycles, _p(hist), ctypes.byref(cyc), ctypes.byref(rr))
+    if status < 0:
+        raise ValueError("oracle solve rejected its arguments (rc=%d)" % status)
+    return u, status, cyc.value, hist[: cyc.value + 1]
 
 
 def solve(f, levels, u0=None, tol=1e-10, max_cycles=100, schedule=None, max_i=32, omega_j=None,

@@ -83,7 +83,8 @@ struct homg_ctx {
 
     cudaGraphExec_t exec_graph = nullptr;
     int stages = 0;
-    std::vector<cudaEvent_t> ev;  // 3*stages + 2 events
+    std::vector<cudaEvent_t> ev;  // 3*stages + 3 events recorded by the solve graph
+    std::vector<cudaEvent_t> sev; // events of the stream launch mode
 
     double* stage_f = nullptr;  // homg_solve_host staging
     double* stage_u = nullptr;
@@ -283,7 +284,7 @@ ResidArgs resid_args(homg_ctx* h, int stage) {
     a.st = h->dstate;
     const double hh = 1.0 / (double)h->n;
     a.inv_h2 = (double)h->n * (double)h->n;
-    a.scale = hh * hh;
+    a.scale = h->strict ? hh * hh : h->omega * hh * hh;  // fast mode stores omega h^2 F
     a.part_r = h->part_r;
     a.part_f = nullptr;
     a.g0 = grid(h->L[0].g, h->L[0].pitch, h->n);
@@ -489,7 +490,8 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     if (o.max_i == 0) o.max_i = 32;
     if (o.diverge_factor == 0.0) o.diverge_factor = 1e3;
     if (!(o.omega_j > 0.0 && o.omega_j <= 2.0) || o.max_i < 1 || !(o.diverge_factor > 1.0) || o.n_schedule < 0 ||
-        (o.n_schedule > 0 && !o.schedule) || o.exec_mode < 0 || o.exec_mode > 2 || (o.strict_fp != 0 && o.strict_fp != 1))
+        (o.n_schedule > 0 && !o.schedule) || o.exec_mode < 0 || o.exec_mode > 2 || (o.strict_fp != 0 && o.strict_fp != 1) ||
+        (o.launch_mode != HOMG_LAUNCH_GRAPH && o.launch_mode != HOMG_LAUNCH_STREAM))
         return fail(nullptr, HOMG_EINVAL, "homg_create: invalid options%s%s");
 
     homg_ctx* h = new (std::nothrow) homg_ctx();
@@ -536,7 +538,7 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
         h->L[m].n = (int)(n >> m);
         h->L[m].pitch = (m == 0) ? h->pitch0 : round_up(h->L[m].n + 1, 16);
     }
-    h->nparts = residual_blocks(ndim, (int)n);
+    h->nparts = residual_blocks(ndim, h->strict, (int)n);
     h->arena_bytes = layout(h, nullptr);
     ce = cudaMalloc(&h->arena, h->arena_bytes);
     if (ce == cudaSuccess) ce = cudaMemset(h->arena, 0, h->arena_bytes);
@@ -567,11 +569,6 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     if (max_cycles < 0 || max_cycles > HOMG_MAX_CYCLES)
         return fail(h, HOMG_EINVAL, "homg_solve: max_cycles must be in [0, HOMG_MAX_CYCLES]%s%s");
     CK(h, cudaSetDevice(h->device), "cudaSetDevice");
-    const int want = std::max(max_cycles, 1);
-    if (!h->exec_graph || h->stages < want) {
-        int rc = build_graph(h, std::max(want, h->stages));
-        if (rc != HOMG_OK) return rc;
-    }
     State* s = h->hstate;
     memset(s, 0, sizeof(*s));
     s->f = f;
@@ -579,11 +576,63 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     s->tol = tol;
     s->div_factor = h->opt.diverge_factor;
     s->max_cycles = max_cycles;
-    s->stages = h->stages;
     s->status = -1;
-    CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(state)");
-    CK(h, cudaGraphLaunch(h->exec_graph, h->stream), "cudaGraphLaunch");
-    CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
+    const std::vector<cudaEvent_t>* ev = nullptr;
+    int end_ev = 0;
+    if (h->opt.launch_mode == HOMG_LAUNCH_GRAPH) {
+        const int want = std::max(max_cycles, 1);
+        if (!h->exec_graph || h->stages < want) {
+            int rc = build_graph(h, std::max(want, h->stages));
+            if (rc != HOMG_OK) return rc;
+        }
+        s->stages = h->stages;
+        CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(state)");
+        CK(h, cudaGraphLaunch(h->exec_graph, h->stream), "cudaGraphLaunch");
+        CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
+        ev = &h->ev;
+        end_ev = 3 * h->stages + 2;
+    } else {
+        // Stream launch mode: same kernels and event layout, the host reads the state once per cycle.
+        const size_t need = 3 * (size_t)max_cycles + 3;
+        while (h->sev.size() < need) {
+            cudaEvent_t e;
+            CK(h, cudaEventCreate(&e), "cudaEventCreate");
+            h->sev.push_back(e);
+        }
+        cudaStream_t st = h->stream;
+        CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(state)");
+        CK(h, cudaEventRecord(h->sev[0], st), "cudaEventRecord");
+        FinalizeArgs fi = fin_args(h, FIN_INIT);
+        fi.handles = nullptr;
+        fi.nstages = 0;
+        CK(h, launch_residual(h->ndim, h->strict, resid_args(h, 0), h->n, st), "residual kernel");
+        CK(h, launch_finalize(fi, st), "finalize kernel");
+        CK(h, cudaEventRecord(h->sev[1], st), "cudaEventRecord");
+        CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync(state)");
+        CK(h, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        for (int k = 1; !s->done && k <= max_cycles; ++k) {
+            CK(h, enqueue_ops(h, h->partA, st), "cycle kernels");
+            CK(h, cudaEventRecord(h->sev[3 * k - 1], st), "cudaEventRecord");
+            CK(h, enqueue_ops(h, h->partB, st), "cycle kernels");
+            CK(h, cudaEventRecord(h->sev[3 * k], st), "cudaEventRecord");
+            FinalizeArgs fc = fin_args(h, FIN_CYCLE);
+            fc.handles = nullptr;
+            fc.nstages = 0;
+            CK(h, launch_residual(h->ndim, h->strict, resid_args(h, k), h->n, st), "residual kernel");
+            CK(h, launch_finalize(fc, st), "finalize kernel");
+            CK(h, cudaEventRecord(h->sev[3 * k + 1], st), "cudaEventRecord");
+            CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync(state)");
+            CK(h, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        }
+        CopyOutArgs c{};
+        c.st = h->dstate;
+        c.u0 = cgrid(h->uint_[0], h->pitch0, h->n);
+        c.u1 = cgrid(h->uint_[1], h->pitch0, h->n);
+        CK(h, launch_copy_out(h->ndim, c, h->n, st), "copy-out kernel");
+        end_ev = 3 * s->cycle + 2;
+        CK(h, cudaEventRecord(h->sev[end_ev], st), "cudaEventRecord");
+        ev = &h->sev;
+    }
     CK(h, cudaMemcpyAsync(h->hhist, h->dhist, (max_cycles + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
        "cudaMemcpyAsync(hist)");
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -599,11 +648,12 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     st.kernels_per_cycle = (int)(h->partA.size() + h->partB.size()) + 2;
     st.kernels_fixed = 3;
     st.kernel_launches = st.kernels_fixed + (long long)cycles * st.kernels_per_cycle;
-    st.solve_ms = elapsed(h->ev[0], h->ev[3 * h->stages + 2]);
+    const std::vector<cudaEvent_t>& E = *ev;
+    st.solve_ms = elapsed(E[0], E[end_ev]);
     for (int k = 1; k <= cycles; ++k) {
-        st.coarse_ms += elapsed(h->ev[3 * k - 2], h->ev[3 * k - 1]);
-        st.fine_ms += elapsed(h->ev[3 * k - 1], h->ev[3 * k]);
-        st.residual_ms += elapsed(h->ev[3 * k], h->ev[3 * k + 1]);
+        st.coarse_ms += elapsed(E[3 * k - 2], E[3 * k - 1]);
+        st.fine_ms += elapsed(E[3 * k - 1], E[3 * k]);
+        st.residual_ms += elapsed(E[3 * k], E[3 * k + 1]);
     }
     st.setup_ms = st.solve_ms - st.coarse_ms - st.fine_ms - st.residual_ms;
     const double pts = (h->ndim == 2) ? (double)(h->n - 1) * (h->n - 1) : (double)(h->n - 1) * (h->n - 1) * (h->n - 1);
@@ -674,6 +724,7 @@ void homg_destroy(homg_handle h) {
     if (!h) return;
     cudaSetDevice(h->device);
     destroy_graph(h);
+    for (cudaEvent_t e : h->sev) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
     if (h->stage_f) cudaFree(h->stage_f);
     if (h->stage_u) cudaFree(h->stage_u);

@@ -109,7 +109,7 @@ struct CopyOutArgs {
 cudaError_t launch_iterate(int ndim, bool strict, const IterArgs& a, cudaStream_t s);
 cudaError_t launch_prolong(int ndim, bool strict, const ProlongArgs& a, cudaStream_t s);
 cudaError_t launch_residual(int ndim, bool strict, const ResidArgs& a, int n, cudaStream_t s);
-int residual_blocks(int ndim, int n);
+int residual_blocks(int ndim, bool strict, int n);  // partial sums written by launch_residual
 cudaError_t launch_restrict(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s);

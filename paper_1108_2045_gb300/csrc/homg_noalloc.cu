@@ -66,11 +66,11 @@ extern "C" int homg_residual_norm_noalloc(int ndim, const int64_t* dims, const d
         return fail(HOMG_ESHAPE, "homg_residual_norm_noalloc: grid side must be 2^K + 1 with K >= 1");
     if (K > (ndim == 2 ? HOMG_MAX_K_2D : HOMG_MAX_K_3D))
         return fail(HOMG_ESHAPE, "homg_residual_norm_noalloc: grid side above the supported maximum");
-    const int nblocks = residual_blocks(ndim, (int)n);
+    const int nblocks = residual_blocks(ndim, false, (int)n);
     if (nblocks > HOMG_NOALLOC_MAX_BLOCKS) {
         snprintf(msg, sizeof(msg),
                  "homg_residual_norm_noalloc: this grid needs %d partial sums, the static scratch holds %d "
-                 "(2-D grids up to 4097^2, 3-D grids up to 257^3)",
+                 "(2-D grids up to 8193^2, 3-D grids up to 257^3)",
                  nblocks, HOMG_NOALLOC_MAX_BLOCKS);
         return fail(HOMG_ESHAPE, msg);
     }

@@ -15,9 +15,11 @@ LIB_PATH = os.path.join(HERE, "lib", "libhomg.so")
 HOMG_OK, HOMG_NOT_CONVERGED, HOMG_DIVERGED, HOMG_TIMEOUT = 0, 1, 2, 3
 HOMG_EINVAL, HOMG_ESHAPE, HOMG_ECUDA, HOMG_ENOMEM = -1, -2, -3, -4
 HOMG_EXEC_AUTO, HOMG_EXEC_WHOLEGRID, HOMG_EXEC_LATTICE = 0, 1, 2
+HOMG_LAUNCH_GRAPH, HOMG_LAUNCH_STREAM = 0, 1
 HOMG_MAX_CYCLES = 200
 
 EXEC_MODES = {"auto": HOMG_EXEC_AUTO, "wholegrid": HOMG_EXEC_WHOLEGRID, "lattice": HOMG_EXEC_LATTICE}
+LAUNCH_MODES = {"graph": HOMG_LAUNCH_GRAPH, "stream": HOMG_LAUNCH_STREAM}
 
 # Every entry point declared in include/homg.h (checked by the symbol test).
 EXPORTS = [
@@ -44,6 +46,7 @@ class homg_options(ctypes.Structure):
         ("exec_mode", ctypes.c_int),
         ("strict_fp", ctypes.c_int),
         ("diverge_factor", ctypes.c_double),
+        ("launch_mode", ctypes.c_int),
     ]
 
 
@@ -126,7 +129,7 @@ def _check(rc, handle):
 
 
 def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, schedule=None, exec_mode="auto",
-                strict_fp=False, diverge_factor=0.0):
+                strict_fp=False, diverge_factor=0.0, launch_mode="graph"):
     """Create a handle for an (n_nodes)^ndim grid; returns an opaque handle (int)."""
     lib = load()
     o = homg_default_options()
@@ -135,6 +138,7 @@ def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, sche
     o.exec_mode = EXEC_MODES[exec_mode] if isinstance(exec_mode, str) else int(exec_mode)
     o.strict_fp = 1 if strict_fp else 0
     o.diverge_factor = diverge_factor
+    o.launch_mode = LAUNCH_MODES[launch_mode] if isinstance(launch_mode, str) else int(launch_mode)
     keep = None
     if schedule is not None:
         keep = (ctypes.c_int * len(schedule))(*schedule)

@@ -202,6 +202,23 @@ def test_residual_norm_and_host_solve(homg):
         assert (st3, c3) == (st1, c1) and st4 == homg.HOMG_NOT_CONVERGED and c4 == 5
 
 
+@pytest.mark.parametrize("mode", ["lattice", "wholegrid"])
+def test_stream_launch_mode_matches_graph(homg, mode):
+    n, K = 256, 8
+    f = inputs.uniform_rhs(n, 2, seed=10)
+    ug, sg, cg, rg, hg, _ = gpu_solve(homg, f, K, tol=1e-10, max_cycles=30, exec_mode=mode)
+    us, ss, cs, rs, hs, stats = gpu_solve(homg, f, K, tol=1e-10, max_cycles=30, exec_mode=mode, launch_mode="stream")
+    assert (sg, cg) == (ss, cs) and sg == homg.HOMG_OK
+    np.testing.assert_array_equal(ug, us)
+    assert hg == hs and rg == rs
+    assert stats["fine_ms"] > 0 and stats["solve_ms"] >= stats["fine_ms"]
+    # zero right-hand side and max_cycles = 0 through the same path
+    z, sz, cz, rz, _, _ = gpu_solve(homg, np.zeros_like(f), K, tol=1e-10, max_cycles=5, launch_mode="stream")
+    assert sz == homg.HOMG_OK and cz == 0 and rz == 0.0 and np.all(z == 0)
+    _, s0, c0, _, _, _ = gpu_solve(homg, f, K, tol=1e-10, max_cycles=0, launch_mode="stream")
+    assert s0 == homg.HOMG_NOT_CONVERGED and c0 == 0
+
+
 def test_solve_on_side_stream(homg):
     import torch
 

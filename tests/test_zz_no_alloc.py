@@ -49,7 +49,7 @@ def test_noalloc_rejects_grids_beyond_its_scratch(homg):
     import ctypes
 
     lib = homg.load()
-    dims = (ctypes.c_int64 * 2)(8193, 8193)
+    dims = (ctypes.c_int64 * 2)(16385, 16385)  # needs 131072 partial sums: rejected before any device access
     rr = ctypes.c_double(0.0)
     rc = lib.homg_residual_norm_noalloc(2, dims, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(rr), None)
     assert rc == homg.HOMG_ESHAPE
