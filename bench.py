@@ -179,7 +179,8 @@ def run(args):
     f = torch.from_numpy(f_np).to(dev)
     u = torch.zeros_like(f)
     stream = torch.cuda.current_stream(dev)
-    solver = homg.Solver(2, N_SIDE + 1, LEVELS, max_i=MAX_I, exec_mode=args.exec, launch_mode=args.launch)
+    solver = homg.Solver(2, N_SIDE + 1, LEVELS, max_i=MAX_I, exec_mode=args.exec, launch_mode=args.launch,
+                         precision=args.precision)
     solver.set_stream(stream)
 
     def barrier():
@@ -259,35 +260,75 @@ def run(args):
             wg = {"value": unknowns / (wms * 1e-3), "ms_per_step": wms,
                   "coarse_iteration_us": 1e3 * coarse_ms / iters if iters else None}
 
+    # mixed precision (FP32 / bfloat16 cycles inside the FP64 restart loop) on the same workload
+    mixed = {}
     peaks, peak_src = measured_peaks()
+    hbm_peak_mp = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    for prec in ([] if args.mixed_steps <= 0 else ["fp32", "bf16"]):
+        with homg.Solver(2, N_SIDE + 1, LEVELS, max_i=MAX_I, precision=prec) as s3:
+            s3.set_stream(stream)
+            for _ in range(3):
+                u.zero_()
+                s3.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+            ms_list, sts = [], []
+            barrier()
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            for _ in range(args.mixed_steps):
+                u.zero_()
+                st3, c3, r3 = s3.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+                if st3 != homg.HOMG_OK:
+                    raise RuntimeError("%s solve did not converge" % prec)
+                sts.append(s3.stats())
+            m1.record(stream)
+            barrier()
+            mms = m0.elapsed_time(m1) / args.mixed_steps
+            fl = sum(x["cycles"] * x["fine_iterations_per_cycle"] for x in sts)
+            fus = 1e3 * sum(x["fine_ms"] for x in sts) / fl
+            fb = sts[0]["fine_bytes_per_iteration"]
+            mixed[prec] = {"value": unknowns / (mms * 1e-3), "ms_per_step": mms, "cycles": c3, "final_relres": r3,
+                           "speedup_vs_fp64": (elapsed_ms / args.steps) / mms,
+                           "fine_launch_us": fus, "fine_hbm_gbs": fb / (fus * 1e-6) / 1e9,
+                           "fine_hbm_frac": fb / (fus * 1e-6) / 1e9 / hbm_peak_mp,
+                           "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
+                                                      for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
+
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
     launches = sum(s["cycles"] * s["fine_iterations_per_cycle"] for s in stats)
     fine_ms = sum(s["fine_ms"] for s in stats)
     per_launch_s = fine_ms * 1e-3 / launches
-    ops = stats[0]["fine_fp64_ops_per_iteration"]
+    ops = stats[0]["fine_flops_per_iteration"]
     bts = stats[0]["fine_bytes_per_iteration"]
     alu_achieved = ops / per_launch_s / 1e12
     hbm_achieved = bts / per_launch_s / 1e9
     clk = clocks.summary()
+    kname = "k_jacobi2 (level-0 HOMG iteration: damped Jacobi on every interior node)"
+    common = {"kernel": kname, "launch_us": per_launch_s * 1e6, "launches": launches,
+              "algorithmic_flops_per_launch": ops, "algorithmic_bytes_per_launch": bts, "traffic": None}
+    if args.precision == "fp64":
+        # FP64 pipe bound on GB300: 5 FP64 instructions per node against 0.625e12 instructions/s
+        roofline = dict(common, bound="alu", achieved=alu_achieved, peak=FP64_PEAK_OPS / 1e12, unit="TFP64op/s",
+                        frac=alu_achieved / (FP64_PEAK_OPS / 1e12),
+                        peak_source="nominal FP64 rate (1.25 TFLOP/s = 0.625e12 FP64 instr/s)",
+                        hbm_achieved_gbs=hbm_achieved, hbm_peak_gbs=hbm_peak, hbm_frac=hbm_achieved / hbm_peak,
+                        hbm_peak_source=peak_src)
+    else:
+        roofline = dict(common, bound="hbm", achieved=hbm_achieved, peak=hbm_peak, unit="GB/s",
+                        frac=hbm_achieved / hbm_peak, peak_source=peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL,
+        "dtype": {"fp64": "f64", "fp32": "f32 cycles, f64 residual/update", "bf16": "bf16 cycles, f64 residual/update"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL,
                    "exec": args.exec, "exec_used": {1: "wholegrid", 2: "lattice"}[stats[0]["exec_mode"]],
                    "cycles": stats[-1]["cycles"], "final_relres": relres,
                    "iterations_per_cycle": stats[0]["iterations_per_cycle"],
                    "l2": "working set ~0.8 GB > 126 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU", "launch": args.launch},
-        "roofline": {"kernel": "k_iterate (level-0 HOMG iteration: damped Jacobi on every interior node)",
-                     "bound": "alu", "achieved": alu_achieved, "peak": FP64_PEAK_OPS / 1e12,
-                     "unit": "TFP64op/s", "frac": alu_achieved / (FP64_PEAK_OPS / 1e12),
-                     "peak_source": "nominal FP64 rate (1.25 TFLOP/s = 0.625e12 FP64 instr/s)",
-                     "traffic": None, "launch_us": per_launch_s * 1e6, "launches": launches,
-                     "algorithmic_ops_per_launch": ops, "algorithmic_bytes_per_launch": bts,
-                     "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak,
-                     "hbm_frac": hbm_achieved / hbm_peak, "hbm_peak_source": peak_src},
+        "roofline": roofline,
         "e2e": {"value": unknowns * args.steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * grid_bytes, "d2h_bytes_per_step": grid_bytes},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
@@ -297,6 +338,8 @@ def run(args):
     }
     if wg:
         line["wholegrid"] = wg
+    if mixed:
+        line["mixed_precision"] = mixed
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_cpu_baseline(f_np, stats[-1]["cycles"])
     solver.close()
@@ -314,10 +357,13 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="homg", choices=["homg", "reference"])
     p.add_argument("--exec", default="auto", choices=["auto", "lattice", "wholegrid"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
+                   help="precision of the timed solver's cycles (the FP64 workload is the headline)")
     p.add_argument("--wholegrid-steps", type=int, default=2)
     p.add_argument("--launch", default="graph", choices=["graph", "stream"],
                    help="stream: enqueue kernels directly (for profilers that cannot see inside conditional graphs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mixed-steps", type=int, default=3, help="timed solves per mixed-precision variant (0: skip)")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")

@@ -96,7 +96,17 @@ typedef struct homg_options {
      * host reading the cycle state once per cycle; meant for profilers and debuggers that cannot
      * look inside graphs with conditional nodes. Results are identical. */
     int launch_mode;
+    /* Precision of each cycle's values (restricted sources, iterates, variations):
+     * HOMG_PREC_FP64 (default), HOMG_PREC_FP32 (binary32), HOMG_PREC_BF16 (bfloat16 storage,
+     * binary32 arithmetic). The residual, the update u += e and the norms are always FP64, so the
+     * restart loop is iterative refinement and reaches the same tolerance (Sec. 4 ran the method in
+     * single precision). */
+    int precision;
 } homg_options;
+
+#define HOMG_PREC_FP64 0
+#define HOMG_PREC_FP32 1
+#define HOMG_PREC_BF16 2
 
 #define HOMG_LAUNCH_GRAPH 0
 #define HOMG_LAUNCH_STREAM 1
@@ -107,6 +117,7 @@ typedef struct homg_stats {
     int cycles;                  /* cycles performed                                            */
     int status;                  /* return code of the last solve                               */
     int exec_mode;               /* form actually used (HOMG_EXEC_WHOLEGRID / _LATTICE)          */
+    int precision;               /* HOMG_PREC_* of the cycle arrays                              */
     int iterations_per_cycle;    /* HOMG iterations (working units) per cycle                    */
     int fine_iterations_per_cycle;   /* iterations on the finest level (level 0) per cycle      */
     int kernels_per_cycle;       /* kernel launches per cycle                                    */
@@ -118,7 +129,8 @@ typedef struct homg_stats {
     double residual_ms;          /* sum over cycles: update + residual + restriction + test     */
     double setup_ms;             /* initial residual + final copy-out                            */
     double fine_bytes_per_iteration;   /* algorithmic DRAM bytes of one level-0 iteration       */
-    double fine_fp64_ops_per_iteration; /* algorithmic FP64 instructions of one level-0 iteration */
+    double fine_flops_per_iteration;   /* algorithmic floating-point instructions (FP64 or FP32,
+                                        * by precision) of one level-0 iteration                  */
     double coarse_bytes_per_cycle;     /* algorithmic DRAM bytes of the levels >= 1 per cycle   */
     double coarse_fp64_ops_per_cycle;  /* algorithmic FP64 instructions of levels >= 1 per cycle */
 } homg_stats;

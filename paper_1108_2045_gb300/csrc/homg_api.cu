@@ -36,10 +36,10 @@ int64_t grid_elems(int ndim, int n, int64_t pitch) {
 
 struct Level {
     int n;                 // intervals per side of the compact lattice
-    int64_t pitch;
-    double* g = nullptr;   // pre-scaled restricted source
-    double* G[2] = {nullptr, nullptr};  // lattice iterates (lattice form; level 0 aliases e)
-    double* d[2] = {nullptr, nullptr};  // compact variations
+    int64_t pitch;         // elements per row
+    void* g = nullptr;     // pre-scaled restricted source
+    void* G[2] = {nullptr, nullptr};  // lattice iterates (lattice form; level 0 aliases e)
+    void* d[2] = {nullptr, nullptr};  // compact variations
 };
 
 struct Op {  // one kernel launch of a cycle part
@@ -65,8 +65,9 @@ struct homg_ctx {
     size_t arena_bytes = 0;
     int64_t pitch0 = 0;
     std::vector<Level> L;
+    int prec = PREC_FP64;     // storage precision of the cycle arrays
     double* uint_[2] = {nullptr, nullptr};
-    double* e[2] = {nullptr, nullptr};
+    void* e[2] = {nullptr, nullptr};
     double* part_r = nullptr;
     double* part_f = nullptr;
     int nparts = 0;
@@ -125,23 +126,26 @@ std::vector<int> mfmg(int levels, int max_i) {
     return s;
 }
 
-CGrid cgrid(const double* p, int64_t pitch, int n) { return CGrid{p, pitch, n}; }
-Grid grid(double* p, int64_t pitch, int n) { return Grid{p, pitch, n}; }
+CGrid cgrid(const void* p, int64_t pitch, int n) { return CGrid{p, pitch, n}; }
+Grid grid(void* p, int64_t pitch, int n) { return Grid{p, pitch, n}; }
+CDGrid cdgrid(const double* p, int64_t pitch, int n) { return CDGrid{p, pitch, n}; }
+DGrid dgrid(double* p, int64_t pitch, int n) { return DGrid{p, pitch, n}; }
 
 // Lay out every array in one buffer: returns bytes needed; assigns pointers when base != nullptr.
 size_t layout(homg_ctx* h, char* base) {
     size_t off = 0;
-    auto take = [&](size_t bytes) -> double* {
+    auto take = [&](size_t bytes) -> void* {
         off = (size_t)round_up((int64_t)off, 256);
-        double* p = base ? (double*)(base + off) : nullptr;
+        void* p = base ? (void*)(base + off) : nullptr;
         off += bytes;
         return p;
     };
     const int nd = h->ndim;
+    const size_t es = (size_t)prec_bytes(h->prec);
     const bool lattice = (h->exec == HOMG_EXEC_LATTICE);
     for (int m = 0; m < h->levels; ++m) {
         Level& lv = h->L[m];
-        const size_t bytes = (size_t)grid_elems(nd, lv.n, lv.pitch) * sizeof(double);
+        const size_t bytes = (size_t)grid_elems(nd, lv.n, lv.pitch) * es;
         lv.g = take(bytes);
         if (m >= 1) {
             if (lattice) {
@@ -154,17 +158,18 @@ size_t layout(homg_ctx* h, char* base) {
             }
         }
     }
-    const size_t fine = (size_t)grid_elems(nd, h->n, h->pitch0) * sizeof(double);
-    h->e[0] = take(fine);
-    h->e[1] = take(fine);
-    h->uint_[0] = take(fine);
-    h->uint_[1] = take(fine);
+    const size_t fine_lp = (size_t)grid_elems(nd, h->n, h->pitch0) * es;
+    const size_t fine64 = (size_t)grid_elems(nd, h->n, h->pitch0) * sizeof(double);
+    h->e[0] = take(fine_lp);
+    h->e[1] = take(fine_lp);
+    h->uint_[0] = (double*)take(fine64);
+    h->uint_[1] = (double*)take(fine64);
     h->L[0].G[0] = h->e[0];
     h->L[0].G[1] = h->e[1];
-    h->part_r = take((size_t)h->nparts * sizeof(double));
-    h->part_f = take((size_t)h->nparts * sizeof(double));
+    h->part_r = (double*)take((size_t)h->nparts * sizeof(double));
+    h->part_f = (double*)take((size_t)h->nparts * sizeof(double));
     h->dstate = (State*)take(sizeof(State));
-    h->dhist = take((HOMG_MAX_CYCLES + 1) * sizeof(double));
+    h->dhist = (double*)take((HOMG_MAX_CYCLES + 1) * sizeof(double));
     return (size_t)round_up((int64_t)off, 256);
 }
 
@@ -270,9 +275,9 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
     for (const Op& op : ops) {
         cudaError_t e = cudaSuccess;
         switch (op.kind) {
-            case Op::ITER: e = launch_iterate(h->ndim, h->strict, op.it, s); break;
-            case Op::PROLONG: e = launch_prolong(h->ndim, h->strict, op.pr, s); break;
-            case Op::RESTRICT: e = launch_restrict(h->ndim, h->strict, op.rs, s); break;
+            case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
+            case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
+            case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -289,14 +294,14 @@ ResidArgs resid_args(homg_ctx* h, int stage) {
     a.part_f = nullptr;
     a.g0 = grid(h->L[0].g, h->L[0].pitch, h->n);
     if (stage == 0) {
-        a.u_in = cgrid(nullptr, 0, h->n);
+        a.u_in = cdgrid(nullptr, 0, h->n);
         a.e = cgrid(nullptr, 0, h->n);
-        a.u_out = grid(h->uint_[0], h->pitch0, h->n);
+        a.u_out = dgrid(h->uint_[0], h->pitch0, h->n);
         a.part_f = h->part_f;
     } else {
-        a.u_in = cgrid(h->uint_[(stage - 1) & 1], h->pitch0, h->n);
+        a.u_in = cdgrid(h->uint_[(stage - 1) & 1], h->pitch0, h->n);
         a.e = cgrid(h->e[h->e_final], h->pitch0, h->n);
-        a.u_out = grid(h->uint_[stage & 1], h->pitch0, h->n);
+        a.u_out = dgrid(h->uint_[stage & 1], h->pitch0, h->n);
     }
     return a;
 }
@@ -397,7 +402,7 @@ int build_graph(homg_ctx* h, int stages) {
     if (e == cudaSuccess) e = add_event(0);
     if (e == cudaSuccess)
         e = add_seq([&](cudaStream_t s) -> cudaError_t {
-            cudaError_t r = launch_residual(h->ndim, h->strict, resid_args(h, 0), h->n, s);
+            cudaError_t r = launch_residual(h->ndim, h->prec, h->strict, resid_args(h, 0), h->n, s);
             if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_INIT), s);
             return r;
         });
@@ -409,7 +414,7 @@ int build_graph(homg_ctx* h, int stages) {
         if (e == cudaSuccess) e = add_event(3 * k);
         if (e == cudaSuccess)
             e = add_if(k, 2, [&](cudaStream_t s) -> cudaError_t {
-                cudaError_t r = launch_residual(h->ndim, h->strict, resid_args(h, k), h->n, s);
+                cudaError_t r = launch_residual(h->ndim, h->prec, h->strict, resid_args(h, k), h->n, s);
                 if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_CYCLE), s);
                 return r;
             });
@@ -419,8 +424,8 @@ int build_graph(homg_ctx* h, int stages) {
         e = add_seq([&](cudaStream_t s) -> cudaError_t {
             CopyOutArgs c{};
             c.st = h->dstate;
-            c.u0 = cgrid(h->uint_[0], h->pitch0, h->n);
-            c.u1 = cgrid(h->uint_[1], h->pitch0, h->n);
+            c.u0 = cdgrid(h->uint_[0], h->pitch0, h->n);
+            c.u1 = cdgrid(h->uint_[1], h->pitch0, h->n);
             return launch_copy_out(h->ndim, c, h->n, s);
         });
     if (e == cudaSuccess) e = add_event(3 * stages + 2);
@@ -491,7 +496,8 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     if (o.diverge_factor == 0.0) o.diverge_factor = 1e3;
     if (!(o.omega_j > 0.0 && o.omega_j <= 2.0) || o.max_i < 1 || !(o.diverge_factor > 1.0) || o.n_schedule < 0 ||
         (o.n_schedule > 0 && !o.schedule) || o.exec_mode < 0 || o.exec_mode > 2 || (o.strict_fp != 0 && o.strict_fp != 1) ||
-        (o.launch_mode != HOMG_LAUNCH_GRAPH && o.launch_mode != HOMG_LAUNCH_STREAM))
+        (o.launch_mode != HOMG_LAUNCH_GRAPH && o.launch_mode != HOMG_LAUNCH_STREAM) ||
+        (o.precision != HOMG_PREC_FP64 && o.precision != HOMG_PREC_FP32 && o.precision != HOMG_PREC_BF16))
         return fail(nullptr, HOMG_EINVAL, "homg_create: invalid options%s%s");
 
     homg_ctx* h = new (std::nothrow) homg_ctx();
@@ -503,6 +509,7 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     h->stencil = stencil;
     h->opt = o;
     h->strict = (o.strict_fp == 1);
+    h->prec = o.precision;
     h->omega = o.omega_j / (2.0 * ndim);
     if (o.n_schedule > 0) {
         h->sched.assign(o.schedule, o.schedule + o.n_schedule);
@@ -605,7 +612,7 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
         FinalizeArgs fi = fin_args(h, FIN_INIT);
         fi.handles = nullptr;
         fi.nstages = 0;
-        CK(h, launch_residual(h->ndim, h->strict, resid_args(h, 0), h->n, st), "residual kernel");
+        CK(h, launch_residual(h->ndim, h->prec, h->strict, resid_args(h, 0), h->n, st), "residual kernel");
         CK(h, launch_finalize(fi, st), "finalize kernel");
         CK(h, cudaEventRecord(h->sev[1], st), "cudaEventRecord");
         CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync(state)");
@@ -618,7 +625,7 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
             FinalizeArgs fc = fin_args(h, FIN_CYCLE);
             fc.handles = nullptr;
             fc.nstages = 0;
-            CK(h, launch_residual(h->ndim, h->strict, resid_args(h, k), h->n, st), "residual kernel");
+            CK(h, launch_residual(h->ndim, h->prec, h->strict, resid_args(h, k), h->n, st), "residual kernel");
             CK(h, launch_finalize(fc, st), "finalize kernel");
             CK(h, cudaEventRecord(h->sev[3 * k + 1], st), "cudaEventRecord");
             CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync(state)");
@@ -626,8 +633,8 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
         }
         CopyOutArgs c{};
         c.st = h->dstate;
-        c.u0 = cgrid(h->uint_[0], h->pitch0, h->n);
-        c.u1 = cgrid(h->uint_[1], h->pitch0, h->n);
+        c.u0 = cdgrid(h->uint_[0], h->pitch0, h->n);
+        c.u1 = cdgrid(h->uint_[1], h->pitch0, h->n);
         CK(h, launch_copy_out(h->ndim, c, h->n, st), "copy-out kernel");
         end_ev = 3 * s->cycle + 2;
         CK(h, cudaEventRecord(h->sev[end_ev], st), "cudaEventRecord");
@@ -657,8 +664,9 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     }
     st.setup_ms = st.solve_ms - st.coarse_ms - st.fine_ms - st.residual_ms;
     const double pts = (h->ndim == 2) ? (double)(h->n - 1) * (h->n - 1) : (double)(h->n - 1) * (h->n - 1) * (h->n - 1);
-    st.fine_bytes_per_iteration = 24.0 * pts;
-    st.fine_fp64_ops_per_iteration = (h->ndim == 2 ? 5.0 : 7.0) * pts;
+    st.precision = h->prec;
+    st.fine_bytes_per_iteration = 3.0 * prec_bytes(h->prec) * pts;
+    st.fine_flops_per_iteration = (h->ndim == 2 ? 5.0 : 7.0) * pts;
     return s->status;
 }
 
@@ -695,7 +703,7 @@ int homg_residual_norm(homg_handle h, const double* f, const double* u, double* 
     a.inv_h2 = (double)h->n * (double)h->n;
     a.part_r = h->part_r;
     a.part_f = h->part_f;
-    CK(h, launch_residual(h->ndim, h->strict, a, h->n, h->stream), "residual kernel");
+    CK(h, launch_residual(h->ndim, h->prec, h->strict, a, h->n, h->stream), "residual kernel");
     FinalizeArgs fa = fin_args(h, FIN_NORM);
     fa.part_f = h->part_f;
     CK(h, launch_finalize(fa, h->stream), "finalize kernel");

@@ -6,6 +6,12 @@
 
 namespace homg {
 
+// Storage precision of a cycle's arrays (restricted sources, iterates, variations). The residual,
+// the update u += e and the norms are always FP64.
+enum Prec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_BF16 = 2 };
+
+inline int prec_bytes(int prec) { return prec == PREC_FP64 ? 8 : (prec == PREC_FP32 ? 4 : 2); }
+
 // Cycle state kept on the device for one solve (written by the host before the graph launch,
 // updated by the convergence-test kernel, read back once at the end).
 struct State {
@@ -24,27 +30,39 @@ struct State {
     double relres;
 };
 
-// A grid array: `n` intervals per side, rows of `pitch` doubles, (n+1) rows per plane.
+// A grid array of the cycle's storage type: `n` intervals per side, rows of `pitch` elements,
+// (n+1) rows per plane.
 struct Grid {
-    double* p;
+    void* p;
     int64_t pitch;
     int n;
 };
 
 struct CGrid {
+    const void* p;
+    int64_t pitch;
+    int n;
+};
+
+// An FP64 grid (solution iterates).
+struct DGrid {
+    double* p;
+    int64_t pitch;
+    int n;
+};
+
+struct CDGrid {
     const double* p;
     int64_t pitch;
     int n;
 };
 
-__host__ __device__ inline CGrid cg(Grid g) { return CGrid{g.p, g.pitch, g.n}; }
-
 // One HOMG iteration on a grid of n intervals per side (the fine grid in the whole-grid form, a
 // level's compact lattice in the lattice form):
-//   relax the stride-2^m lattice (source g = h_m^2 F_m, compact, one value per lattice node),
+//   relax the stride-2^m lattice (source g, compact, one value per lattice node),
 //   add the interpolation of the pending variation dprev (compact at stride 2^mp) off its lattice.
 struct IterArgs {
-    CGrid e_old;
+    CGrid e_old;    // p == nullptr: e_old = 0
     Grid e_new;
     CGrid g;        // compact level-m source, pre-scaled: h_m^2 F_m (strict) or omega h_m^2 F_m
     int m;          // relaxation stride exponent
@@ -69,9 +87,9 @@ struct ProlongArgs {
 // (and f^2) per block.
 struct ResidArgs {
     State* st;
-    CGrid u_in;     // p == nullptr: read the caller's u (st->u, unpadded)
+    CDGrid u_in;    // p == nullptr: read the caller's u (st->u, unpadded)
     CGrid e;        // p == nullptr: no update
-    Grid u_out;     // p == nullptr: not written
+    DGrid u_out;    // p == nullptr: not written
     Grid g0;        // p == nullptr: not written
     double scale;   // h^2 (strict) or omega h^2
     double inv_h2;
@@ -101,16 +119,17 @@ struct FinalizeArgs {
 
 struct CopyOutArgs {
     State* st;
-    CGrid u0;   // internal iterate after an even number of cycles
-    CGrid u1;   // ... after an odd number
+    CDGrid u0;   // internal iterate after an even number of cycles
+    CDGrid u1;   // ... after an odd number
 };
 
-// Launchers (enqueue on `s`; return the launch error).
-cudaError_t launch_iterate(int ndim, bool strict, const IterArgs& a, cudaStream_t s);
-cudaError_t launch_prolong(int ndim, bool strict, const ProlongArgs& a, cudaStream_t s);
-cudaError_t launch_residual(int ndim, bool strict, const ResidArgs& a, int n, cudaStream_t s);
+// Launchers (enqueue on `s`; return the launch error). `prec` is the storage precision of the
+// cycle arrays (Prec); `strict` selects the oracle's canonical operation order.
+cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, cudaStream_t s);
+cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a, cudaStream_t s);
+cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a, int n, cudaStream_t s);
 int residual_blocks(int ndim, bool strict, int n);  // partial sums written by launch_residual
-cudaError_t launch_restrict(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s);
+cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s);
 

@@ -1,8 +1,14 @@
 // HOMG kernels for sm_103a: the fused relaxation+interpolation iteration, the lattice level change,
 // update+residual, full-weighting restriction, the convergence test and the copy-out.
 //
-// Arithmetic: with STRICT every formula is evaluated in the CPU oracle's canonical operation order
-// with round-to-nearest intrinsics (no FMA contraction); otherwise the compiler may contract.
+// Storage type T of a cycle's arrays: double (FP64 path), float (FP32 relaxation and transfers) or
+// __nv_bfloat16 (bfloat16 storage, FP32 arithmetic). Arithmetic type C is double for T = double,
+// float otherwise. The residual, the update and the norms always run in FP64.
+//
+// STRICT (S) kernels evaluate every formula in the CPU oracle's canonical operation order with
+// round-to-nearest intrinsics (no FMA contraction), storing through the same rounding as the
+// oracle. The fast kernels reassociate to issue fewer floating-point instructions.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "../../include/homg.h"
@@ -14,44 +20,79 @@ namespace {
 constexpr int BX = 32;
 constexpr int BY = 8;
 
+// ---- storage traits -------------------------------------------------------------------------
+template <typename T> struct St;
+template <> struct St<double> {
+    using C = double;
+    static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ double rd(const double* p) { return *p; }
+    static __device__ __forceinline__ double put(double x) { return x; }
+    static __device__ __forceinline__ double from_d(double x) { return x; }
+};
+template <> struct St<float> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float rd(const float* p) { return *p; }
+    static __device__ __forceinline__ float put(float x) { return x; }
+    static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
+};
+template <> struct St<__nv_bfloat16> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
+    }
+    static __device__ __forceinline__ float rd(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ __nv_bfloat16 put(float x) { return __float2bfloat16_rn(x); }
+    // double -> binary32 -> bfloat16, each round-to-nearest (the oracle's storage rounding)
+    static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
+};
+
+// ---- arithmetic in the canonical order (S) or freely contracted ------------------------------
 template <bool S> __device__ __forceinline__ double add(double a, double b) { return S ? __dadd_rn(a, b) : a + b; }
 template <bool S> __device__ __forceinline__ double sub(double a, double b) { return S ? __dsub_rn(a, b) : a - b; }
 template <bool S> __device__ __forceinline__ double mul(double a, double b) { return S ? __dmul_rn(a, b) : a * b; }
+template <bool S> __device__ __forceinline__ float add(float a, float b) { return S ? __fadd_rn(a, b) : a + b; }
+template <bool S> __device__ __forceinline__ float sub(float a, float b) { return S ? __fsub_rn(a, b) : a - b; }
+template <bool S> __device__ __forceinline__ float mul(float a, float b) { return S ? __fmul_rn(a, b) : a * b; }
 
-// Element (i, j, k) of a grid with `pitch` doubles per row and (n+1) rows per plane.
+// Element (i, j, k) of a grid with `pitch` elements per row and (n+1) rows per plane.
 __device__ __forceinline__ int64_t at(int64_t pitch, int n, int i, int j, int k) {
     return ((int64_t)k * (n + 1) + j) * pitch + i;
 }
+
+template <typename T> __device__ __forceinline__ const T* cp(const CGrid& g) { return static_cast<const T*>(g.p); }
+template <typename T> __device__ __forceinline__ T* wp(const Grid& g) { return static_cast<T*>(g.p); }
 
 // Value at (i, j[, k]) of the (bi/tri)linear interpolant of compact array d at stride 2^mp
 // (Sec. 2: linear interpolation S; exact dyadic weights). Summation order as in the oracle:
 // 2-D (w00 d00 + w10 d10) + (w01 d01 + w11 d11); 3-D x-pairs, then y, then z.
 // With DIFF, the interpolated field is d - d2 (the level-change kernel's stale values).
-template <int ND, bool S, bool DIFF>
-__device__ __forceinline__ double interp(CGrid d, CGrid d2, int mp, int i, int j, int k) {
+template <int ND, bool S, bool DIFF, typename T>
+__device__ __forceinline__ typename St<T>::C interp(CGrid d, CGrid d2, int mp, int i, int j, int k) {
+    using C = typename St<T>::C;
     const int lp = 1 << mp;
-    const double inv = ldexp(1.0, -mp);
+    const C inv = (C)ldexp(1.0, -mp);
     const int I0 = i >> mp, a = i & (lp - 1), I1 = a ? I0 + 1 : I0;
     const int J0 = j >> mp, b = j & (lp - 1), J1 = b ? J0 + 1 : J0;
-    const double wx0 = (double)(lp - a) * inv, wx1 = (double)a * inv;
-    const double wy0 = (double)(lp - b) * inv, wy1 = (double)b * inv;
-    auto val = [&](int I, int J, int K) -> double {
-        double v = d.p[at(d.pitch, d.n, I, J, K)];
-        if (DIFF) v = sub<S>(v, d2.p[at(d2.pitch, d2.n, I, J, K)]);
+    const C wx0 = (C)(lp - a) * inv, wx1 = (C)a * inv;
+    const C wy0 = (C)(lp - b) * inv, wy1 = (C)b * inv;
+    auto val = [&](int I, int J, int K) -> C {
+        C v = St<T>::rd(cp<T>(d) + at(d.pitch, d.n, I, J, K));
+        if (DIFF) v = sub<S>(v, St<T>::rd(cp<T>(d2) + at(d2.pitch, d2.n, I, J, K)));
         return v;
     };
     if (ND == 2) {
-        double t00 = mul<S>(mul<S>(wx0, wy0), val(I0, J0, 0));
-        double t10 = mul<S>(mul<S>(wx1, wy0), val(I1, J0, 0));
-        double t01 = mul<S>(mul<S>(wx0, wy1), val(I0, J1, 0));
-        double t11 = mul<S>(mul<S>(wx1, wy1), val(I1, J1, 0));
+        C t00 = mul<S>(mul<S>(wx0, wy0), val(I0, J0, 0));
+        C t10 = mul<S>(mul<S>(wx1, wy0), val(I1, J0, 0));
+        C t01 = mul<S>(mul<S>(wx0, wy1), val(I0, J1, 0));
+        C t11 = mul<S>(mul<S>(wx1, wy1), val(I1, J1, 0));
         return add<S>(add<S>(t00, t10), add<S>(t01, t11));
     } else {
         const int K0 = k >> mp, c = k & (lp - 1), K1 = c ? K0 + 1 : K0;
-        const double wz0 = (double)(lp - c) * inv, wz1 = (double)c * inv;
-        const double wx[2] = {wx0, wx1}, wy[2] = {wy0, wy1}, wz[2] = {wz0, wz1};
+        const C wz0 = (C)(lp - c) * inv, wz1 = (C)c * inv;
+        const C wx[2] = {wx0, wx1}, wy[2] = {wy0, wy1}, wz[2] = {wz0, wz1};
         const int Ix[2] = {I0, I1}, Jy[2] = {J0, J1}, Kz[2] = {K0, K1};
-        double t[2][2][2];
+        C t[2][2][2];
 #pragma unroll
         for (int z = 0; z < 2; ++z)
 #pragma unroll
@@ -69,30 +110,31 @@ __device__ __forceinline__ double interp(CGrid d, CGrid d2, int mp, int i, int j
 // the previous iteration's variations on the complementary nodes; Sec. 4: the interpolation is
 // delayed one iteration). e_old.p == nullptr means e_old = 0 (first iteration of a cycle).
 // ---------------------------------------------------------------------------------------------
-template <int ND, bool S>
+template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_iterate(IterArgs a) {
+    using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
     const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
     if (i >= n || j >= n) return;
     const bool zero = (a.e_old.p == nullptr);
-    auto E = [&](int ii, int jj, int kk) -> double {
-        return zero ? 0.0 : a.e_old.p[at(a.e_old.pitch, n, ii, jj, kk)];
+    auto E = [&](int ii, int jj, int kk) -> C {
+        return zero ? (C)0 : St<T>::rd(cp<T>(a.e_old) + at(a.e_old.pitch, n, ii, jj, kk));
     };
-    double v = E(i, j, k);
+    const C omega = (C)a.omega;
+    C v = E(i, j, k);
     const int l = 1 << a.m;
-    const int lat_mask = l - 1;
-    if (((i | j | (ND == 3 ? k : 0)) & lat_mask) == 0) {
-        double lap;
+    if (((i | j | (ND == 3 ? k : 0)) & (l - 1)) == 0) {
+        C lap;
         if (ND == 2) {
-            lap = mul<S>(4.0, v);
+            lap = mul<S>((C)4, v);
             lap = sub<S>(lap, E(i - l, j, 0));
             lap = sub<S>(lap, E(i + l, j, 0));
             lap = sub<S>(lap, E(i, j - l, 0));
             lap = sub<S>(lap, E(i, j + l, 0));
         } else {
-            lap = mul<S>(6.0, v);
+            lap = mul<S>((C)6, v);
             lap = sub<S>(lap, E(i - l, j, k));
             lap = sub<S>(lap, E(i + l, j, k));
             lap = sub<S>(lap, E(i, j - l, k));
@@ -101,36 +143,37 @@ __global__ void __launch_bounds__(BX * BY) k_iterate(IterArgs a) {
             lap = sub<S>(lap, E(i, j, k + l));
         }
         const int I = i >> a.m, J = j >> a.m, K = (ND == 3) ? (k >> a.m) : 0;
-        const double g = a.g.p[at(a.g.pitch, a.g.n, I, J, K)];
+        const C g = St<T>::rd(cp<T>(a.g) + at(a.g.pitch, a.g.n, I, J, K));
         // strict: g = h_m^2 F_m, delta = omega (g - lap); fast: g = omega h_m^2 F_m, delta = g - omega lap
-        const double delta = S ? mul<S>(a.omega, sub<S>(g, lap)) : fma(-a.omega, lap, g);
-        if (a.dnew.p) a.dnew.p[at(a.dnew.pitch, a.dnew.n, I, J, K)] = delta;
+        const C delta = S ? mul<S>(omega, sub<S>(g, lap)) : fma(-omega, lap, g);
+        if (a.dnew.p) wp<T>(a.dnew)[at(a.dnew.pitch, a.dnew.n, I, J, K)] = St<T>::put(delta);
         v = add<S>(v, delta);
     }
     if (a.mp >= 0) {
         const int lpm = (1 << a.mp) - 1;
-        if (((i | j | (ND == 3 ? k : 0)) & lpm) != 0) v = add<S>(v, interp<ND, S, false>(a.dprev, a.dprev, a.mp, i, j, k));
+        if (((i | j | (ND == 3 ? k : 0)) & lpm) != 0) v = add<S>(v, interp<ND, S, false, T>(a.dprev, a.dprev, a.mp, i, j, k));
     }
-    a.e_new.p[at(a.e_new.pitch, n, i, j, k)] = v;
+    wp<T>(a.e_new)[at(a.e_new.pitch, n, i, j, k)] = St<T>::put(v);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Lattice form, level change (see ProlongArgs): stale values of the finer lattice.
 // ---------------------------------------------------------------------------------------------
-template <int ND, bool S>
+template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_prolong(ProlongArgs a) {
+    using C = typename St<T>::C;
     const int n = a.G.n;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
     const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
     if (i >= n || j >= n) return;
     const int sm = (1 << a.s) - 1;
-    double v;
+    C v;
     if (((i | j | (ND == 3 ? k : 0)) & sm) == 0)
-        v = a.Gc.p[at(a.Gc.pitch, a.Gc.n, i >> a.s, j >> a.s, (ND == 3) ? (k >> a.s) : 0)];
+        v = St<T>::rd(cp<T>(a.Gc) + at(a.Gc.pitch, a.Gc.n, i >> a.s, j >> a.s, (ND == 3) ? (k >> a.s) : 0));
     else
-        v = interp<ND, S, true>(a.Gc, a.dl, a.s, i, j, k);
-    a.G.p[at(a.G.pitch, n, i, j, k)] = v;
+        v = interp<ND, S, true, T>(a.Gc, a.dl, a.s, i, j, k);
+    wp<T>(a.G)[at(a.G.pitch, n, i, j, k)] = St<T>::put(v);
 }
 
 // Fixed-order block sum of one value per thread (warp butterflies, then warps in order).
@@ -150,9 +193,10 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 
 // ---------------------------------------------------------------------------------------------
 // K2: update + residual (Sec. 2: residual r = f - A_h v of the two-grid scheme, restarted on the
-// residual equation after each cycle) and the level-0 source of the next cycle.
+// residual equation after each cycle) and the level-0 source of the next cycle. FP64 throughout;
+// e is widened from the cycle's storage type and g0 rounded to it.
 // ---------------------------------------------------------------------------------------------
-template <int ND, bool S>
+template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_residual(ResidArgs a, int n) {
     __shared__ double sh[BX * BY / 32];
     const int i = blockIdx.x * BX + threadIdx.x + 1;
@@ -166,7 +210,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual(ResidArgs a, int n) {
         if (ii <= 0 || jj <= 0 || ii >= n || jj >= n) return 0.0;
         if (ND == 3 && (kk <= 0 || kk >= n)) return 0.0;
         double v = uc[at(upitch, n, ii, jj, kk)];
-        if (a.e.p) v = add<S>(v, a.e.p[at(a.e.pitch, n, ii, jj, kk)]);
+        if (a.e.p) v = add<S>(v, (double)St<T>::rd(cp<T>(a.e) + at(a.e.pitch, n, ii, jj, kk)));
         return v;
     };
     double rr = 0.0, ff = 0.0;
@@ -191,7 +235,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual(ResidArgs a, int n) {
         const double fv = f[at(n + 1, n, i, j, k)];
         const double r = sub<S>(fv, mul<S>(lap, a.inv_h2));
         if (a.u_out.p) a.u_out.p[at(a.u_out.pitch, n, i, j, k)] = c;
-        if (a.g0.p) a.g0.p[at(a.g0.pitch, n, i, j, k)] = mul<S>(a.scale, r);
+        if (a.g0.p) wp<T>(a.g0)[at(a.g0.pitch, n, i, j, k)] = St<T>::put(St<T>::from_d(mul<S>(a.scale, r)));
         rr = r * r;
         ff = fv * fv;
     }
@@ -208,25 +252,26 @@ __global__ void __launch_bounds__(BX * BY) k_residual(ResidArgs a, int n) {
 // Restriction (Sec. 2: linearly weighted averages as nested reductions; full weighting).
 // g_c = 4 FW(g_f): sources stay pre-scaled by h_m^2, so this equals h_{m+1}^2 FW(F_m) exactly.
 // ---------------------------------------------------------------------------------------------
-template <int ND, bool S>
+template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_restrict(RestrictArgs a) {
+    using C = typename St<T>::C;
     const int nc = a.gc.n;
     const int I = blockIdx.x * BX + threadIdx.x + 1;
     const int J = blockIdx.y * BY + threadIdx.y + 1;
     const int K = (ND == 3) ? (int)blockIdx.z + 1 : 0;
     if (I >= nc || J >= nc) return;
     const int i = 2 * I, j = 2 * J, k = 2 * K;
-    auto F = [&](int ii, int jj, int kk) -> double { return a.gf.p[at(a.gf.pitch, a.gf.n, ii, jj, kk)]; };
-    double v;
+    auto F = [&](int ii, int jj, int kk) -> C { return St<T>::ld(cp<T>(a.gf) + at(a.gf.pitch, a.gf.n, ii, jj, kk)); };
+    C v;
     if (ND == 2) {
-        const double c = F(i, j, 0);
-        const double edges = add<S>(add<S>(add<S>(F(i - 1, j, 0), F(i + 1, j, 0)), F(i, j - 1, 0)), F(i, j + 1, 0));
-        const double corners =
+        const C c = F(i, j, 0);
+        const C edges = add<S>(add<S>(add<S>(F(i - 1, j, 0), F(i + 1, j, 0)), F(i, j - 1, 0)), F(i, j + 1, 0));
+        const C corners =
             add<S>(add<S>(add<S>(F(i - 1, j - 1, 0), F(i + 1, j - 1, 0)), F(i - 1, j + 1, 0)), F(i + 1, j + 1, 0));
-        v = mul<S>(add<S>(add<S>(mul<S>(4.0, c), mul<S>(2.0, edges)), corners), 0.25);
+        v = mul<S>(add<S>(add<S>(mul<S>((C)4, c), mul<S>((C)2, edges)), corners), (C)0.25);
     } else {
-        const double c = F(i, j, k);
-        double faces = 0.0, edges = 0.0, corners = 0.0;
+        const C c = F(i, j, k);
+        C faces = 0, edges = 0, corners = 0;
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
@@ -235,14 +280,14 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(RestrictArgs a) {
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int nz = (dx != 0) + (dy != 0) + (dz != 0);
                     if (nz == 0) continue;
-                    const double x = F(i + dx, j + dy, k + dz);
+                    const C x = F(i + dx, j + dy, k + dz);
                     if (nz == 1) faces = add<S>(faces, x);
                     else if (nz == 2) edges = add<S>(edges, x);
                     else corners = add<S>(corners, x);
                 }
-        v = mul<S>(add<S>(add<S>(add<S>(mul<S>(8.0, c), mul<S>(4.0, faces)), mul<S>(2.0, edges)), corners), 0.0625);
+        v = mul<S>(add<S>(add<S>(add<S>(mul<S>((C)8, c), mul<S>((C)4, faces)), mul<S>((C)2, edges)), corners), (C)0.0625);
     }
-    a.gc.p[at(a.gc.pitch, nc, I, J, K)] = v;
+    wp<T>(a.gc)[at(a.gc.pitch, nc, I, J, K)] = St<T>::put(v);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -313,178 +358,205 @@ __global__ void __launch_bounds__(BX * BY) k_copy_out(CopyOutArgs a, int n) {
     const State* st = a.st;
     double v = 0.0;
     if (!st->zero_u) {
-        const CGrid src = (st->cycle & 1) ? a.u1 : a.u0;
+        const CDGrid src = (st->cycle & 1) ? a.u1 : a.u0;
         v = src.p[at(src.pitch, n, i, j, k)];
     }
     st->u[at(n + 1, n, i, j, k)] = v;
 }
 
+// =============================================================================================
+// Fast kernels (strict_fp = 0).
+// =============================================================================================
+constexpr int JX = 128;  // threads per block along x (2-D)
+constexpr int JR = 16;   // nodes per thread along the march on large grids
 
-// ---------------------------------------------------------------------------------------------
+// Stride-2 interpolation along a marching column: X(J) is the x-interpolant of compact row J at
+// this thread's column (the lattice value itself on even columns); a fine row j takes X(j/2) when
+// j is even and the mean of X(j/2) and X(j/2 + 1) when j is odd. X is formed once per coarse row
+// and shared by the two fine rows it touches, and the form is branch-free across a warp.
+template <typename T>
+struct ColumnInterp2 {
+    using C = typename St<T>::C;
+    const T* d;    // compact array, offset to this column's left lattice neighbour
+    const T* d2;   // second compact array subtracted from d (nullptr: none)
+    int64_t pitch, pitch2;
+    C hx;          // 0.5 on odd columns, 0 on even ones
+    int cj = -1;
+    C x0 = 0, x1 = 0;  // X(cj), X(cj + 1)
+
+    __device__ __forceinline__ C X(int J) const {
+        C a = St<T>::ld(d + (int64_t)J * pitch), b = St<T>::ld(d + (int64_t)J * pitch + 1);
+        if (d2) {
+            a -= St<T>::ld(d2 + (int64_t)J * pitch2);
+            b -= St<T>::ld(d2 + (int64_t)J * pitch2 + 1);
+        }
+        return fma(hx, b - a, a);
+    }
+    __device__ __forceinline__ C at(int j) {
+        const int J0 = j >> 1;
+        if (J0 != cj) {
+            x0 = (J0 == cj + 1) ? x1 : X(J0);
+            x1 = X(J0 + 1);
+            cj = J0;
+        }
+        return (j & 1) ? (C)0.5 * (x0 + x1) : x0;
+    }
+};
+
 // Fast level-0 iteration (every iteration of the lattice form, the level-0 iterations of the
 // whole-grid form): damped Jacobi on every interior node with the source pre-scaled by omega,
 //   v' = (1 - c omega) v + omega * (sum of the 2d neighbours) + omega h^2 F
-// = 5 FP64 instructions per node in 2-D (7 in 3-D), plus the pending interpolation on the first
-// iteration of a level. Each thread marches one column (2-D: along y; 3-D: along z) keeping the
-// centre and its two neighbours along the march in registers; the other neighbours come through
-// L1. The FP64 pipe, not DRAM, bounds this kernel on GB300.
-// ---------------------------------------------------------------------------------------------
-constexpr int JX = 128;  // threads per block along x (2-D)
-constexpr int JR = 16;   // nodes per thread along the march
-
-// Pending interpolation at stride 2 (level change m+1 -> m, the common case): nodes with one odd
-// index take the mean of two lattice neighbours, nodes with two odd indexes the mean of four.
-__device__ __forceinline__ double pend2_s1(const CGrid& d, int i, int j) {
-    const int I0 = i >> 1, J0 = j >> 1;
-    const double* p = d.p + (int64_t)J0 * d.pitch + I0;
-    if ((j & 1) == 0) return 0.5 * (__ldg(p) + __ldg(p + 1));           // i odd
-    if ((i & 1) == 0) return 0.5 * (__ldg(p) + __ldg(p + d.pitch));     // j odd
-    return 0.25 * ((__ldg(p) + __ldg(p + 1)) + (__ldg(p + d.pitch) + __ldg(p + d.pitch + 1)));
-}
-
-template <int PEND, bool WD>
+// = 5 FP instructions per node in 2-D (7 in 3-D), plus the pending interpolation on the first
+// iteration of a level (PEND: 0 none, 1 stride 2, 2 any stride). Each thread marches one column
+// (2-D: along y; 3-D: along z) keeping the centre and its two neighbours along the march in
+// registers; the other neighbours come through L1. In FP64 the FP64 pipe bounds this kernel on
+// GB300; in FP32/bfloat16, DRAM does.
+template <int PEND, bool WD, typename T>
 __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
+    using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
     if (i >= n) return;
     const int j0 = blockIdx.y * rows + 1;
     const int j1 = min(j0 + rows, n);
-    const double* __restrict__ E = a.e_old.p;
+    const T* __restrict__ E = cp<T>(a.e_old);
     const int64_t pe = a.e_old.pitch;
-    double* __restrict__ O = a.e_new.p;
+    T* __restrict__ O = wp<T>(a.e_new);
     const int64_t po = a.e_new.pitch;
-    const double* __restrict__ G = a.g.p;
+    const T* __restrict__ G = cp<T>(a.g);
     const int64_t pg = a.g.pitch;
-    const double om = a.omega, c1 = 1.0 - 4.0 * a.omega;
+    const C om = (C)a.omega, c1 = (C)(1.0 - 4.0 * a.omega);
     const int lpm = PEND ? (1 << a.mp) - 1 : 0;
-    double vs = __ldg(E + (int64_t)(j0 - 1) * pe + i);
-    double vc = __ldg(E + (int64_t)j0 * pe + i);
+    ColumnInterp2<T> ci;
+    if (PEND == 1) {
+        ci.d = cp<T>(a.dprev) + (i >> 1);
+        ci.d2 = nullptr;
+        ci.pitch = a.dprev.pitch;
+        ci.pitch2 = 0;
+        ci.hx = (i & 1) ? (C)0.5 : (C)0;
+    }
+    C vs = St<T>::ld(E + (int64_t)(j0 - 1) * pe + i);
+    C vc = St<T>::ld(E + (int64_t)j0 * pe + i);
 #pragma unroll 4
     for (int j = j0; j < j1; ++j) {
-        const double* row = E + (int64_t)j * pe + i;
-        const double vn = __ldg(row + pe);
-        const double w = __ldg(row - 1), e = __ldg(row + 1);
-        const double g = __ldg(G + (int64_t)j * pg + i);
-        const double sum = (w + e) + (vs + vn);
-        double v = fma(c1, vc, fma(om, sum, g));
-        if (WD) a.dnew.p[(int64_t)j * a.dnew.pitch + i] = v - vc;
-        if (PEND == 1 && ((i | j) & 1)) v += pend2_s1(a.dprev, i, j);
-        if (PEND == 2 && ((i | j) & lpm)) v += interp<2, false, false>(a.dprev, a.dprev, a.mp, i, j, 0);
-        O[(int64_t)j * po + i] = v;
+        const T* row = E + (int64_t)j * pe + i;
+        const C vn = St<T>::ld(row + pe);
+        const C w = St<T>::ld(row - 1), e = St<T>::ld(row + 1);
+        const C g = St<T>::ld(G + (int64_t)j * pg + i);
+        const C sum = (w + e) + (vs + vn);
+        C v = fma(c1, vc, fma(om, sum, g));
+        if (WD) wp<T>(a.dnew)[(int64_t)j * a.dnew.pitch + i] = St<T>::put(v - vc);
+        if (PEND == 1) {
+            const C sv = ci.at(j);
+            v += ((i | j) & 1) ? sv : (C)0;
+        }
+        if (PEND == 2 && ((i | j) & lpm)) v += interp<2, false, false, T>(a.dprev, a.dprev, a.mp, i, j, 0);
+        O[(int64_t)j * po + i] = St<T>::put(v);
         vs = vc;
         vc = vn;
     }
 }
 
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
-// mean of the two or four surrounding values of Gc - dl.
+// stride-2 interpolant of Gc - dl, formed along each marching column (see ColumnInterp2).
+template <typename T>
 __global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
+    using C = typename St<T>::C;
     const int n = a.G.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
     if (i >= n) return;
     const int j0 = blockIdx.y * rows + 1;
     const int j1 = min(j0 + rows, n);
-    const int I0 = i >> 1;
     const bool iodd = i & 1;
-    const double* __restrict__ C = a.Gc.p;
-    const double* __restrict__ D = a.dl.p;
-    const int64_t pc = a.Gc.pitch, pd = a.dl.pitch;
+    ColumnInterp2<T> ci;
+    ci.d = cp<T>(a.Gc) + (i >> 1);
+    ci.d2 = cp<T>(a.dl) + (i >> 1);
+    ci.pitch = a.Gc.pitch;
+    ci.pitch2 = a.dl.pitch;
+    ci.hx = iodd ? (C)0.5 : (C)0;
     for (int j = j0; j < j1; ++j) {
-        const int J0 = j >> 1;
-        const double* c = C + (int64_t)J0 * pc + I0;
-        const double* d = D + (int64_t)J0 * pd + I0;
-        double v;
-        if (!(j & 1)) {
-            if (!iodd) v = __ldg(c);
-            else v = 0.5 * ((__ldg(c) - __ldg(d)) + (__ldg(c + 1) - __ldg(d + 1)));
-        } else if (!iodd) {
-            v = 0.5 * ((__ldg(c) - __ldg(d)) + (__ldg(c + pc) - __ldg(d + pd)));
-        } else {
-            v = 0.25 * (((__ldg(c) - __ldg(d)) + (__ldg(c + 1) - __ldg(d + 1))) +
-                        ((__ldg(c + pc) - __ldg(d + pd)) + (__ldg(c + pc + 1) - __ldg(d + pd + 1))));
-        }
-        a.G.p[(int64_t)j * a.G.pitch + i] = v;
+        C v = ci.at(j);
+        if (!(j & 1) && !iodd) v = St<T>::ld(cp<T>(a.Gc) + (int64_t)(j >> 1) * a.Gc.pitch + (i >> 1));
+        wp<T>(a.G)[(int64_t)j * a.G.pitch + i] = St<T>::put(v);
     }
 }
 
 constexpr int J3X = 32, J3Y = 4;
 
-template <bool PEND, bool WD>
+template <bool PEND, bool WD, typename T>
 __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
+    using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * J3X + threadIdx.x + 1;
     const int j = blockIdx.y * J3Y + threadIdx.y + 1;
     if (i >= n || j >= n) return;
     const int k0 = blockIdx.z * rows + 1;
     const int k1 = min(k0 + rows, n);
-    const double* __restrict__ E = a.e_old.p;
+    const T* __restrict__ E = cp<T>(a.e_old);
     const int64_t pe = a.e_old.pitch, ple = (int64_t)(n + 1) * pe;
-    double* __restrict__ O = a.e_new.p;
+    T* __restrict__ O = wp<T>(a.e_new);
     const int64_t po = a.e_new.pitch, plo = (int64_t)(n + 1) * po;
-    const double* __restrict__ G = a.g.p;
+    const T* __restrict__ G = cp<T>(a.g);
     const int64_t pg = a.g.pitch, plg = (int64_t)(n + 1) * pg;
-    const double om = a.omega, c1 = 1.0 - 6.0 * a.omega;
+    const C om = (C)a.omega, c1 = (C)(1.0 - 6.0 * a.omega);
     const int lpm = PEND ? (1 << a.mp) - 1 : 0;
-    const double* col = E + (int64_t)j * pe + i;
-    double vb = __ldg(col + (int64_t)(k0 - 1) * ple);
-    double vc = __ldg(col + (int64_t)k0 * ple);
+    const T* col = E + (int64_t)j * pe + i;
+    C vb = St<T>::ld(col + (int64_t)(k0 - 1) * ple);
+    C vc = St<T>::ld(col + (int64_t)k0 * ple);
 #pragma unroll 2
     for (int k = k0; k < k1; ++k) {
-        const double* p = col + (int64_t)k * ple;
-        const double vt = __ldg(p + ple);
-        const double w = __ldg(p - 1), e = __ldg(p + 1), sn = __ldg(p - pe), nn = __ldg(p + pe);
-        const double g = __ldg(G + (int64_t)k * plg + (int64_t)j * pg + i);
-        const double sum = ((w + e) + (sn + nn)) + (vb + vt);
-        double v = fma(c1, vc, fma(om, sum, g));
-        if (WD) a.dnew.p[(int64_t)k * (n + 1) * a.dnew.pitch + (int64_t)j * a.dnew.pitch + i] = v - vc;
-        if (PEND && ((i | j | k) & lpm)) v += interp<3, false, false>(a.dprev, a.dprev, a.mp, i, j, k);
-        O[(int64_t)k * plo + (int64_t)j * po + i] = v;
+        const T* p = col + (int64_t)k * ple;
+        const C vt = St<T>::ld(p + ple);
+        const C w = St<T>::ld(p - 1), e = St<T>::ld(p + 1), sn = St<T>::ld(p - pe), nn = St<T>::ld(p + pe);
+        const C g = St<T>::ld(G + (int64_t)k * plg + (int64_t)j * pg + i);
+        const C sum = ((w + e) + (sn + nn)) + (vb + vt);
+        C v = fma(c1, vc, fma(om, sum, g));
+        if (WD) wp<T>(a.dnew)[(int64_t)k * (n + 1) * a.dnew.pitch + (int64_t)j * a.dnew.pitch + i] = St<T>::put(v - vc);
+        if (PEND && ((i | j | k) & lpm)) v += interp<3, false, false, T>(a.dprev, a.dprev, a.mp, i, j, k);
+        O[(int64_t)k * plo + (int64_t)j * po + i] = St<T>::put(v);
         vb = vc;
         vc = vt;
     }
 }
 
-
-// ---------------------------------------------------------------------------------------------
 // Fast whole-grid iteration at level m >= 1 (2-D): every fine node adds the bilinear interpolant of
 // the pending variation (level mp >= 1) unless it lies on the level-mp lattice, and level-m
 // lattice nodes relax. Each thread marches one column; the interpolant along x is formed once per
 // coarse cell row (r0, r1 at the cell's lower and upper lattice rows) and shared down the column,
 // so a node off both lattices costs one FMA and one add.
-// ---------------------------------------------------------------------------------------------
-template <bool PEND>
+template <bool PEND, typename T>
 __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
+    using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
     if (i >= n) return;
     const int j0 = blockIdx.y * JR + 1;
     const int j1 = min(j0 + JR, n);
-    const double* __restrict__ E = a.e_old.p;
+    const T* __restrict__ E = cp<T>(a.e_old);
     const int64_t pe = a.e_old.pitch;
-    double* __restrict__ O = a.e_new.p;
+    T* __restrict__ O = wp<T>(a.e_new);
     const int64_t po = a.e_new.pitch;
     const int m = a.m, l = 1 << m, lm = l - 1;
-    const double om = a.omega;
+    const C om = (C)a.omega;
     const bool col_on_lattice = (i & lm) == 0;
-    // pending interpolation, per column
     const int mp = PEND ? a.mp : 0;
     const int lpm = (1 << mp) - 1;
     const int I0 = i >> mp;
-    const double alpha = PEND ? (double)(i & lpm) * ldexp(1.0, -mp) : 0.0;
-    const double beta_step = PEND ? ldexp(1.0, -mp) : 0.0;
-    const double* __restrict__ D = a.dprev.p;
+    const C alpha = PEND ? (C)(i & lpm) * (C)ldexp(1.0, -mp) : (C)0;
+    const C beta_step = PEND ? (C)ldexp(1.0, -mp) : (C)0;
+    const T* __restrict__ D = cp<T>(a.dprev);
     const int64_t pd = a.dprev.pitch;
     const bool col_on_prev = (i & lpm) == 0;
     int cell = -1;
-    double r0 = 0.0, dr = 0.0;
+    C r0 = 0, dr = 0;
     for (int j = j0; j < j1; ++j) {
-        double v = __ldg(E + (int64_t)j * pe + i);
+        C v = St<T>::ld(E + (int64_t)j * pe + i);
         if (col_on_lattice && (j & lm) == 0) {
-            const double sum = (__ldg(E + (int64_t)j * pe + i - l) + __ldg(E + (int64_t)j * pe + i + l)) +
-                               (__ldg(E + (int64_t)(j - l) * pe + i) + __ldg(E + (int64_t)(j + l) * pe + i));
-            const double g = __ldg(a.g.p + (int64_t)(j >> m) * a.g.pitch + (i >> m));
-            const double delta = fma(om, fma(-4.0, v, sum), g);
-            if (a.dnew.p) a.dnew.p[(int64_t)(j >> m) * a.dnew.pitch + (i >> m)] = delta;
+            const C sum = (St<T>::ld(E + (int64_t)j * pe + i - l) + St<T>::ld(E + (int64_t)j * pe + i + l)) +
+                          (St<T>::ld(E + (int64_t)(j - l) * pe + i) + St<T>::ld(E + (int64_t)(j + l) * pe + i));
+            const C g = St<T>::ld(cp<T>(a.g) + (int64_t)(j >> m) * a.g.pitch + (i >> m));
+            const C delta = fma(om, fma((C)-4, v, sum), g);
+            if (a.dnew.p) wp<T>(a.dnew)[(int64_t)(j >> m) * a.dnew.pitch + (i >> m)] = St<T>::put(delta);
             v += delta;
         }
         if (PEND) {
@@ -492,26 +564,25 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
             const int b = j & lpm;
             if (!(col_on_prev && b == 0)) {
                 if (J0 != cell) {
-                    const double* d0 = D + (int64_t)J0 * pd + I0;
-                    const double* d1 = d0 + pd;
-                    const double a0 = __ldg(d0), a1 = __ldg(d1);
-                    const double q0 = fma(alpha, __ldg(d0 + 1) - a0, a0);
-                    const double q1 = fma(alpha, __ldg(d1 + 1) - a1, a1);
+                    const T* d0 = D + (int64_t)J0 * pd + I0;
+                    const T* d1 = d0 + pd;
+                    const C a0 = St<T>::ld(d0), a1 = St<T>::ld(d1);
+                    const C q0 = fma(alpha, St<T>::ld(d0 + 1) - a0, a0);
+                    const C q1 = fma(alpha, St<T>::ld(d1 + 1) - a1, a1);
                     r0 = q0;
                     dr = q1 - q0;
                     cell = J0;
                 }
-                v += fma((double)b * beta_step, dr, r0);
+                v += fma((C)b * beta_step, dr, r0);
             }
         }
-        O[(int64_t)j * po + i] = v;
+        O[(int64_t)j * po + i] = St<T>::put(v);
     }
 }
 
-// ---------------------------------------------------------------------------------------------
 // Fast update + residual (2-D): one column per thread marching along y, u_new = u_in + e formed
 // once per node for the column and once for each side neighbour; 10 FP64 instructions per node.
-// ---------------------------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     __shared__ double sh[JX / 32];
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -521,15 +592,14 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     const bool upd = a.e.p != nullptr;
     const double* __restrict__ U = a.u_in.p ? a.u_in.p : a.st->u;
     const int64_t pu = a.u_in.p ? a.u_in.pitch : (int64_t)(n + 1);
-    const double* __restrict__ Ev = a.e.p;
+    const T* __restrict__ Ev = cp<T>(a.e);
     const int64_t pe = a.e.pitch;
     const double* __restrict__ F = a.st->f;
     const int64_t pf = n + 1;
-    // u_new at (ii, jj), 0 on the boundary
     auto un = [&](int ii, int jj) -> double {
         if (ii <= 0 || jj <= 0 || ii >= n || jj >= n) return 0.0;
         double v = __ldg(U + (int64_t)jj * pu + ii);
-        if (upd) v += __ldg(Ev + (int64_t)jj * pe + ii);
+        if (upd) v += (double)St<T>::ld(Ev + (int64_t)jj * pe + ii);
         return v;
     };
     double rr = 0.0, ff = 0.0;
@@ -542,7 +612,7 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
             const double fv = __ldg(F + (int64_t)j * pf + i);
             const double r = fma(a.inv_h2, fma(-4.0, vc, sum), fv);
             if (a.u_out.p) a.u_out.p[(int64_t)j * a.u_out.pitch + i] = vc;
-            if (a.g0.p) a.g0.p[(int64_t)j * a.g0.pitch + i] = a.scale * r;
+            if (a.g0.p) wp<T>(a.g0)[(int64_t)j * a.g0.pitch + i] = St<T>::put(St<T>::from_d(a.scale * r));
             rr = fma(r, r, rr);
             ff = fma(fv, fv, ff);
             vs = vc;
@@ -571,17 +641,23 @@ dim3 grid_for(int ndim, int n) {
     return dim3((unsigned)((n - 1 + BX - 1) / BX), (unsigned)((n - 1 + BY - 1) / BY), ndim == 3 ? (unsigned)(n - 1) : 1u);
 }
 
-}  // namespace
+// The fast 2-D residual uses its own grid: (n-1)/JX x (n-1)/JR blocks.
+dim3 resid_grid(int ndim, bool strict, int n) {
+    if (ndim == 2 && !strict) return dim3((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + JR - 1) / JR));
+    return grid_for(ndim, n);
+}
 
-cudaError_t launch_iterate(int ndim, bool strict, const IterArgs& a, cudaStream_t s) {
+// ---- launch templates ----------------------------------------------------------------------
+template <typename T>
+cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) {
+    const int n = a.e_new.n;
     if (!strict && a.m == 0 && a.e_old.p != nullptr) {
         const bool wd = a.dnew.p != nullptr;
-        const int n = a.e_new.n;
         const int rows = march_rows(ndim, n);
         if (ndim == 2) {
             const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows)), b(JX);
             const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
-#define JAC2(P, W) k_jacobi2<P, W><<<g, b, 0, s>>>(a, rows)
+#define JAC2(P, W) k_jacobi2<P, W, T><<<g, b, 0, s>>>(a, rows)
             if (pend == 0) { if (wd) JAC2(0, true); else JAC2(0, false); }
             else if (pend == 1) { if (wd) JAC2(1, true); else JAC2(1, false); }
             else { if (wd) JAC2(2, true); else JAC2(2, false); }
@@ -591,54 +667,92 @@ cudaError_t launch_iterate(int ndim, bool strict, const IterArgs& a, cudaStream_
             const dim3 g((unsigned)((n - 1 + J3X - 1) / J3X), (unsigned)((n - 1 + J3Y - 1) / J3Y),
                          (unsigned)((n - 1 + rows - 1) / rows)),
                 b(J3X, J3Y);
-            if (pend && wd) k_jacobi3<true, true><<<g, b, 0, s>>>(a, rows);
-            else if (pend) k_jacobi3<true, false><<<g, b, 0, s>>>(a, rows);
-            else if (wd) k_jacobi3<false, true><<<g, b, 0, s>>>(a, rows);
-            else k_jacobi3<false, false><<<g, b, 0, s>>>(a, rows);
+            if (pend && wd) k_jacobi3<true, true, T><<<g, b, 0, s>>>(a, rows);
+            else if (pend) k_jacobi3<true, false, T><<<g, b, 0, s>>>(a, rows);
+            else if (wd) k_jacobi3<false, true, T><<<g, b, 0, s>>>(a, rows);
+            else k_jacobi3<false, false, T><<<g, b, 0, s>>>(a, rows);
         }
         return cudaGetLastError();
     }
     if (!strict && ndim == 2 && a.m >= 1 && a.e_old.p != nullptr && a.mp != 0) {
-        const int n = a.e_new.n;
         const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + JR - 1) / JR)), b(JX);
-        if (a.mp >= 1) k_wholegrid2<true><<<g, b, 0, s>>>(a);
-        else k_wholegrid2<false><<<g, b, 0, s>>>(a);
+        if (a.mp >= 1) k_wholegrid2<true, T><<<g, b, 0, s>>>(a);
+        else k_wholegrid2<false, T><<<g, b, 0, s>>>(a);
         return cudaGetLastError();
     }
-    const dim3 g = grid_for(ndim, a.e_new.n), b(BX, BY);
+    const dim3 g = grid_for(ndim, n), b(BX, BY);
     if (ndim == 2) {
-        if (strict) k_iterate<2, true><<<g, b, 0, s>>>(a);
-        else k_iterate<2, false><<<g, b, 0, s>>>(a);
+        if (strict) k_iterate<2, true, T><<<g, b, 0, s>>>(a);
+        else k_iterate<2, false, T><<<g, b, 0, s>>>(a);
     } else {
-        if (strict) k_iterate<3, true><<<g, b, 0, s>>>(a);
-        else k_iterate<3, false><<<g, b, 0, s>>>(a);
+        if (strict) k_iterate<3, true, T><<<g, b, 0, s>>>(a);
+        else k_iterate<3, false, T><<<g, b, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(int ndim, bool strict, const ProlongArgs& a, cudaStream_t s) {
+template <typename T>
+cudaError_t prolong_t(int ndim, bool strict, const ProlongArgs& a, cudaStream_t s) {
     if (!strict && ndim == 2 && a.s == 1) {
         const int n = a.G.n;
         const int rows = march_rows(2, n);
         const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows));
-        k_prolong2_s1<<<g, dim3(JX), 0, s>>>(a, rows);
+        k_prolong2_s1<T><<<g, dim3(JX), 0, s>>>(a, rows);
         return cudaGetLastError();
     }
     const dim3 g = grid_for(ndim, a.G.n), b(BX, BY);
     if (ndim == 2) {
-        if (strict) k_prolong<2, true><<<g, b, 0, s>>>(a);
-        else k_prolong<2, false><<<g, b, 0, s>>>(a);
+        if (strict) k_prolong<2, true, T><<<g, b, 0, s>>>(a);
+        else k_prolong<2, false, T><<<g, b, 0, s>>>(a);
     } else {
-        if (strict) k_prolong<3, true><<<g, b, 0, s>>>(a);
-        else k_prolong<3, false><<<g, b, 0, s>>>(a);
+        if (strict) k_prolong<3, true, T><<<g, b, 0, s>>>(a);
+        else k_prolong<3, false, T><<<g, b, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
-// The fast 2-D residual uses its own grid: (n-1)/JX x (n-1)/JR blocks.
-static dim3 resid_grid(int ndim, bool strict, int n) {
-    if (ndim == 2 && !strict) return dim3((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + JR - 1) / JR));
-    return grid_for(ndim, n);
+template <typename T>
+cudaError_t residual_t(int ndim, bool strict, const ResidArgs& a, int n, cudaStream_t s) {
+    const dim3 g = resid_grid(ndim, strict, n);
+    if (ndim == 2) {
+        if (strict) k_residual<2, true, T><<<g, dim3(BX, BY), 0, s>>>(a, n);
+        else k_residual2_fast<T><<<g, dim3(JX), 0, s>>>(a, n);
+    } else {
+        if (strict) k_residual<3, true, T><<<g, dim3(BX, BY), 0, s>>>(a, n);
+        else k_residual<3, false, T><<<g, dim3(BX, BY), 0, s>>>(a, n);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t restrict_t(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s) {
+    const dim3 g = grid_for(ndim, a.gc.n), b(BX, BY);
+    if (ndim == 2) {
+        if (strict) k_restrict<2, true, T><<<g, b, 0, s>>>(a);
+        else k_restrict<2, false, T><<<g, b, 0, s>>>(a);
+    } else {
+        if (strict) k_restrict<3, true, T><<<g, b, 0, s>>>(a);
+        else k_restrict<3, false, T><<<g, b, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define DISPATCH_PREC(prec, CALL)                                    \
+    switch (prec) {                                                  \
+        case PREC_FP64: { using T = double; return CALL; }           \
+        case PREC_FP32: { using T = float; return CALL; }            \
+        case PREC_BF16: { using T = __nv_bfloat16; return CALL; }    \
+        default: return cudaErrorInvalidValue;                       \
+    }
+
+cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, cudaStream_t s) {
+    DISPATCH_PREC(prec, iterate_t<T>(ndim, strict, a, s));
+}
+
+cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a, cudaStream_t s) {
+    DISPATCH_PREC(prec, prolong_t<T>(ndim, strict, a, s));
 }
 
 int residual_blocks(int ndim, bool strict, int n) {
@@ -646,28 +760,12 @@ int residual_blocks(int ndim, bool strict, int n) {
     return (int)(g.x * g.y * g.z);
 }
 
-cudaError_t launch_residual(int ndim, bool strict, const ResidArgs& a, int n, cudaStream_t s) {
-    const dim3 g = resid_grid(ndim, strict, n);
-    if (ndim == 2) {
-        if (strict) k_residual<2, true><<<g, dim3(BX, BY), 0, s>>>(a, n);
-        else k_residual2_fast<<<g, dim3(JX), 0, s>>>(a, n);
-    } else {
-        if (strict) k_residual<3, true><<<g, dim3(BX, BY), 0, s>>>(a, n);
-        else k_residual<3, false><<<g, dim3(BX, BY), 0, s>>>(a, n);
-    }
-    return cudaGetLastError();
+cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a, int n, cudaStream_t s) {
+    DISPATCH_PREC(prec, residual_t<T>(ndim, strict, a, n, s));
 }
 
-cudaError_t launch_restrict(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s) {
-    const dim3 g = grid_for(ndim, a.gc.n), b(BX, BY);
-    if (ndim == 2) {
-        if (strict) k_restrict<2, true><<<g, b, 0, s>>>(a);
-        else k_restrict<2, false><<<g, b, 0, s>>>(a);
-    } else {
-        if (strict) k_restrict<3, true><<<g, b, 0, s>>>(a);
-        else k_restrict<3, false><<<g, b, 0, s>>>(a);
-    }
-    return cudaGetLastError();
+cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s) {
+    DISPATCH_PREC(prec, restrict_t<T>(ndim, strict, a, s));
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {

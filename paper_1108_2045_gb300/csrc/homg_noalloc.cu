@@ -101,7 +101,7 @@ extern "C" int homg_residual_norm_noalloc(int ndim, const int64_t* dims, const d
     a.inv_h2 = (double)n * (double)n;
     a.part_r = scratch + kStateDoubles;
     a.part_f = scratch + kStateDoubles + HOMG_NOALLOC_MAX_BLOCKS;
-    if (e == cudaSuccess) e = launch_residual(ndim, false, a, (int)n, s);
+    if (e == cudaSuccess) e = launch_residual(ndim, PREC_FP64, false, a, (int)n, s);
     FinalizeArgs fa{};
     fa.st = st;
     fa.part_r = a.part_r;

@@ -16,10 +16,12 @@ HOMG_OK, HOMG_NOT_CONVERGED, HOMG_DIVERGED, HOMG_TIMEOUT = 0, 1, 2, 3
 HOMG_EINVAL, HOMG_ESHAPE, HOMG_ECUDA, HOMG_ENOMEM = -1, -2, -3, -4
 HOMG_EXEC_AUTO, HOMG_EXEC_WHOLEGRID, HOMG_EXEC_LATTICE = 0, 1, 2
 HOMG_LAUNCH_GRAPH, HOMG_LAUNCH_STREAM = 0, 1
+HOMG_PREC_FP64, HOMG_PREC_FP32, HOMG_PREC_BF16 = 0, 1, 2
 HOMG_MAX_CYCLES = 200
 
 EXEC_MODES = {"auto": HOMG_EXEC_AUTO, "wholegrid": HOMG_EXEC_WHOLEGRID, "lattice": HOMG_EXEC_LATTICE}
 LAUNCH_MODES = {"graph": HOMG_LAUNCH_GRAPH, "stream": HOMG_LAUNCH_STREAM}
+PRECISIONS = {"fp64": HOMG_PREC_FP64, "fp32": HOMG_PREC_FP32, "bf16": HOMG_PREC_BF16}
 
 # Every entry point declared in include/homg.h (checked by the symbol test).
 EXPORTS = [
@@ -47,6 +49,7 @@ class homg_options(ctypes.Structure):
         ("strict_fp", ctypes.c_int),
         ("diverge_factor", ctypes.c_double),
         ("launch_mode", ctypes.c_int),
+        ("precision", ctypes.c_int),
     ]
 
 
@@ -55,6 +58,7 @@ class homg_stats(ctypes.Structure):
         ("cycles", ctypes.c_int),
         ("status", ctypes.c_int),
         ("exec_mode", ctypes.c_int),
+        ("precision", ctypes.c_int),
         ("iterations_per_cycle", ctypes.c_int),
         ("fine_iterations_per_cycle", ctypes.c_int),
         ("kernels_per_cycle", ctypes.c_int),
@@ -66,7 +70,7 @@ class homg_stats(ctypes.Structure):
         ("residual_ms", ctypes.c_double),
         ("setup_ms", ctypes.c_double),
         ("fine_bytes_per_iteration", ctypes.c_double),
-        ("fine_fp64_ops_per_iteration", ctypes.c_double),
+        ("fine_flops_per_iteration", ctypes.c_double),
         ("coarse_bytes_per_cycle", ctypes.c_double),
         ("coarse_fp64_ops_per_cycle", ctypes.c_double),
     ]
@@ -129,7 +133,7 @@ def _check(rc, handle):
 
 
 def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, schedule=None, exec_mode="auto",
-                strict_fp=False, diverge_factor=0.0, launch_mode="graph"):
+                strict_fp=False, diverge_factor=0.0, launch_mode="graph", precision="fp64"):
     """Create a handle for an (n_nodes)^ndim grid; returns an opaque handle (int)."""
     lib = load()
     o = homg_default_options()
@@ -139,6 +143,7 @@ def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, sche
     o.strict_fp = 1 if strict_fp else 0
     o.diverge_factor = diverge_factor
     o.launch_mode = LAUNCH_MODES[launch_mode] if isinstance(launch_mode, str) else int(launch_mode)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     keep = None
     if schedule is not None:
         keep = (ctypes.c_int * len(schedule))(*schedule)

@@ -47,7 +47,7 @@ def test_library_exports_every_declared_symbol(homg):
 def test_default_options(homg):
     o = homg.homg_default_options()
     assert o.max_i == 32 and o.exec_mode == homg.HOMG_EXEC_AUTO and o.diverge_factor == 1e3 and o.n_schedule == 0
-    assert o.launch_mode == homg.HOMG_LAUNCH_GRAPH
+    assert o.launch_mode == homg.HOMG_LAUNCH_GRAPH and o.precision == homg.HOMG_PREC_FP64
 
 
 @pytest.mark.parametrize(
@@ -79,7 +79,7 @@ def test_create_rejects_unequal_sides_and_bad_options(homg):
     assert h.value is None
     for kw in [dict(omega_j=-1.0), dict(max_i=-3), dict(exec_mode=7), dict(diverge_factor=0.5),
                dict(schedule=[1, 2]), dict(schedule=[3, 0]), dict(schedule=[0, 1, 0], exec_mode="lattice"),
-               dict(launch_mode=5)]:
+               dict(launch_mode=5), dict(precision=7)]:
         with pytest.raises(homg.HomgError) as ei:
             homg.homg_create(2, 33, 3, **kw)
         assert ei.value.code == homg.HOMG_EINVAL, kw
