@@ -42,12 +42,31 @@ struct Level {
     void* d[2] = {nullptr, nullptr};  // compact variations
 };
 
+// One instantiated solve graph: `stages` unrolled cycle stages (three conditional IF nodes each)
+// with event nodes between them; the handles of stage k sit at dhandles[3k .. 3k+2].
+struct SolveGraph {
+    cudaGraphExec_t exec = nullptr;
+    int stages = 0;
+    bool with_init = false;
+    std::vector<cudaEvent_t> ev;  // 3*stages + 3 events
+    cudaGraphConditionalHandle* dhandles = nullptr;
+};
+
+// Cycle stages unrolled in one graph. Stages a solve does not reach cost a few microseconds each
+// (their conditional nodes evaluate false), so the graph stays short and a solve that needs more
+// cycles relaunches the continuation graph (one host synchronisation per kStagesPerGraph cycles).
+constexpr int kStagesPerGraph = 12;  // even: keeps the ping-pong parity of the solution buffers
+
 struct Op {  // one kernel launch of a cycle part
-    enum Kind { ITER, PROLONG, RESTRICT } kind;
+    enum Kind { ITER, PROLONG, RESTRICT, BLOCK } kind;
     IterArgs it;
     ProlongArgs pr;
     RestrictArgs rs;
+    int block_first = 0, block_count = 0;  // BLOCK: range of the device op list
 };
+
+// Capacity of the coarse-lattice block's op list in the level buffer.
+constexpr int kMaxBlockOps = 1024;
 
 }  // namespace
 
@@ -79,12 +98,13 @@ struct homg_ctx {
     double* hhist = nullptr;  // pinned
 
     std::vector<Op> partA, partB;  // cycle parts (A: restriction + levels >= 1, B: level 0)
+    std::vector<BlockOp> block_ops; // coarse-lattice ops run by one block (fast lattice form)
+    BlockOp* dblock_ops = nullptr;
     int e_final = 0;               // index of e[] holding the cycle's result (whole-grid form)
     int fine_iters = 0, coarse_iters = 0;
 
-    cudaGraphExec_t exec_graph = nullptr;
-    int stages = 0;
-    std::vector<cudaEvent_t> ev;  // 3*stages + 3 events recorded by the solve graph
+    SolveGraph gfirst;            // initial residual + up to kStagesPerGraph cycle stages
+    SolveGraph gcont;             // continuation: further stages, launched while cycles remain
     std::vector<cudaEvent_t> sev; // events of the stream launch mode
 
     double* stage_f = nullptr;  // homg_solve_host staging
@@ -170,7 +190,17 @@ size_t layout(homg_ctx* h, char* base) {
     h->part_f = (double*)take((size_t)h->nparts * sizeof(double));
     h->dstate = (State*)take(sizeof(State));
     h->dhist = (double*)take((HOMG_MAX_CYCLES + 1) * sizeof(double));
+    h->dblock_ops = (BlockOp*)take(kMaxBlockOps * sizeof(BlockOp));
     return (size_t)round_up((int64_t)off, 256);
+}
+
+// Damped-Jacobi scalars of an iteration, computed once on the host (binary32 copies for the
+// binary32-arithmetic kernels).
+void set_weights(const homg_ctx* h, IterArgs& a) {
+    a.omega = h->omega;
+    a.c1 = 1.0 - 2.0 * h->ndim * h->omega;
+    a.omega_f = (float)a.omega;
+    a.c1_f = (float)a.c1;
 }
 
 // Kernel sequence of one cycle's parts A (restriction + levels >= 1) and B (level 0).
@@ -205,7 +235,7 @@ void plan_cycle(homg_ctx* h) {
             a.e_new = grid(h->e[cur ^ 1], h->pitch0, h->n);
             a.g = cgrid(h->L[m].g, h->L[m].pitch, h->L[m].n);
             a.m = m;
-            a.omega = h->omega;
+            set_weights(h, a);
             a.mp = -1;
             if (mprev >= 1) {
                 a.mp = mprev;
@@ -251,7 +281,7 @@ void plan_cycle(homg_ctx* h) {
                 a.e_new = grid(lv.G[cur ^ 1], lv.pitch, lv.n);
                 a.g = cgrid(lv.g, lv.pitch, lv.n);
                 a.m = 0;
-                a.omega = h->omega;
+                set_weights(h, a);
                 a.mp = -1;
                 if (q == 0 && !first_run) {
                     const Level& lc = h->L[mprev];
@@ -271,6 +301,49 @@ void plan_cycle(homg_ctx* h) {
     }
 }
 
+// Fast lattice form: the restrictions to, and the leading runs on, the coarsest lattices (at most
+// 16 intervals per side in 2-D, 8 in 3-D: a few hundred nodes, less than one per thread of the
+// block) become one single-block launch. Larger lattices run faster as separate launches.
+void group_coarse_block(homg_ctx* h) {
+    h->block_ops.clear();
+    if (h->strict || h->exec != HOMG_EXEC_LATTICE) return;
+    const int nb = (h->ndim == 2) ? 16 : 8;
+    std::vector<Op> kept;
+    std::vector<BlockOp> blk;
+    size_t q = 0;
+    // restrictions: the ones producing small lattices (they come last, coarsest)
+    for (; q < h->partA.size() && h->partA[q].kind == Op::RESTRICT; ++q) {
+        const Op& op = h->partA[q];
+        if (op.rs.gc.n <= nb) {
+            BlockOp b{};
+            b.kind = BLOCK_RESTRICT;
+            b.rs = op.rs;
+            blk.push_back(b);
+        } else {
+            kept.push_back(op);
+        }
+    }
+    // leading iterations / level changes on small lattices
+    for (; q < h->partA.size(); ++q) {
+        const Op& op = h->partA[q];
+        const int n = (op.kind == Op::ITER) ? op.it.e_new.n : op.pr.G.n;
+        if (n > nb) break;
+        BlockOp b{};
+        if (op.kind == Op::ITER) { b.kind = BLOCK_ITER; b.it = op.it; }
+        else { b.kind = BLOCK_PROLONG; b.pr = op.pr; }
+        blk.push_back(b);
+    }
+    if (blk.empty() || (int)blk.size() > kMaxBlockOps) return;
+    Op bop{};
+    bop.kind = Op::BLOCK;
+    bop.block_first = 0;
+    bop.block_count = (int)blk.size();
+    kept.push_back(bop);
+    for (; q < h->partA.size(); ++q) kept.push_back(h->partA[q]);
+    h->partA = kept;
+    h->block_ops = blk;
+}
+
 cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s) {
     for (const Op& op : ops) {
         cudaError_t e = cudaSuccess;
@@ -278,6 +351,9 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
             case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
             case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
+            case Op::BLOCK:
+                e = launch_coarse_block(h->ndim, h->prec, h->dblock_ops + op.block_first, op.block_count, s);
+                break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -306,7 +382,7 @@ ResidArgs resid_args(homg_ctx* h, int stage) {
     return a;
 }
 
-FinalizeArgs fin_args(homg_ctx* h, int mode) {
+FinalizeArgs fin_args(homg_ctx* h, int mode, const SolveGraph* g) {
     FinalizeArgs f{};
     f.st = h->dstate;
     f.hist = h->dhist;
@@ -314,19 +390,19 @@ FinalizeArgs fin_args(homg_ctx* h, int mode) {
     f.part_f = (mode == FIN_CYCLE) ? nullptr : h->part_f;
     f.nparts = h->nparts;
     f.mode = mode;
-    f.handles = h->dhandles;
-    f.nstages = h->stages;
+    f.handles = g ? g->dhandles : nullptr;
+    f.nstages = g ? g->stages : 0;
     return f;
 }
 
-void destroy_graph(homg_ctx* h) {
-    if (h->exec_graph) cudaGraphExecDestroy(h->exec_graph);
-    h->exec_graph = nullptr;
-    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-    h->ev.clear();
-    if (h->dhandles) cudaFree(h->dhandles);
-    h->dhandles = nullptr;
-    h->stages = 0;
+void destroy_graph(SolveGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+    g.ev.clear();
+    if (g.dhandles) cudaFree(g.dhandles);
+    g.dhandles = nullptr;
+    g.stages = 0;
 }
 
 // Capture `fn(stream)` into the body graph `body` (or a fresh graph when body == nullptr).
@@ -343,24 +419,26 @@ cudaError_t capture_into(cudaGraph_t body, cudaStream_t cap, Fn fn, cudaGraph_t*
     return e;
 }
 
-// Event layout: ev[0] before the initial residual, ev[1] after it (= start of stage 1); stage k
-// records ev[3k-1] after part A, ev[3k] after part B, ev[3k+1] after part C; ev[3S+2] at the end.
-int build_graph(homg_ctx* h, int stages) {
-    destroy_graph(h);
+// Event layout: ev[0] at the start, ev[1] after the initial residual (first graph only; the
+// continuation graph records ev[0], ev[1] back to back); stage k records ev[3k-1] after part A,
+// ev[3k] after part B, ev[3k+1] after part C; ev[3S+2] after the copy-out.
+int build_graph(homg_ctx* h, SolveGraph& G, int stages, bool with_init) {
+    destroy_graph(G);
     std::vector<cudaGraphConditionalHandle> handles(3 * (stages + 1), 0);
-    h->stages = stages;
-    h->ev.assign(3 * stages + 3, nullptr);
+    G.stages = stages;
+    G.with_init = with_init;
+    G.ev.assign(3 * stages + 3, nullptr);
     cudaError_t e = cudaSuccess;
-    for (auto& ev : h->ev)
+    for (auto& ev : G.ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
-    if (e == cudaSuccess) e = cudaMalloc(&h->dhandles, handles.size() * sizeof(cudaGraphConditionalHandle));
+    if (e == cudaSuccess) e = cudaMalloc(&G.dhandles, handles.size() * sizeof(cudaGraphConditionalHandle));
     cudaStream_t cap = nullptr;
     cudaGraph_t top = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaGraphCreate(&top, 0);
     cudaGraphNode_t last = nullptr, node = nullptr;
     auto add_event = [&](int idx) -> cudaError_t {
-        cudaError_t r = cudaGraphAddEventRecordNode(&node, top, last ? &last : nullptr, last ? 1 : 0, h->ev[idx]);
+        cudaError_t r = cudaGraphAddEventRecordNode(&node, top, last ? &last : nullptr, last ? 1 : 0, G.ev[idx]);
         if (r == cudaSuccess) last = node;
         return r;
     };
@@ -386,7 +464,9 @@ int build_graph(homg_ctx* h, int stages) {
     };
     auto add_if = [&](int k, int part, auto fn) -> cudaError_t {
         cudaGraphConditionalHandle hd;
-        cudaError_t r = cudaGraphConditionalHandleCreate(&hd, top, 0, cudaGraphCondAssignDefault);
+        // The first stage of the continuation graph runs whenever that graph is launched.
+        const unsigned def = (!with_init && k == 1) ? 1u : 0u;
+        cudaError_t r = cudaGraphConditionalHandleCreate(&hd, top, def, cudaGraphCondAssignDefault);
         if (r != cudaSuccess) return r;
         handles[3 * k + part] = hd;
         cudaGraphNodeParams p{};
@@ -400,10 +480,10 @@ int build_graph(homg_ctx* h, int stages) {
         return capture_into(p.conditional.phGraph_out[0], cap, fn, nullptr);
     };
     if (e == cudaSuccess) e = add_event(0);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && with_init)
         e = add_seq([&](cudaStream_t s) -> cudaError_t {
             cudaError_t r = launch_residual(h->ndim, h->prec, h->strict, resid_args(h, 0), h->n, s);
-            if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_INIT), s);
+            if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_INIT, &G), s);
             return r;
         });
     if (e == cudaSuccess) e = add_event(1);
@@ -415,7 +495,7 @@ int build_graph(homg_ctx* h, int stages) {
         if (e == cudaSuccess)
             e = add_if(k, 2, [&](cudaStream_t s) -> cudaError_t {
                 cudaError_t r = launch_residual(h->ndim, h->prec, h->strict, resid_args(h, k), h->n, s);
-                if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_CYCLE), s);
+                if (r == cudaSuccess) r = launch_finalize(fin_args(h, FIN_CYCLE, &G), s);
                 return r;
             });
         if (e == cudaSuccess) e = add_event(3 * k + 1);
@@ -430,19 +510,13 @@ int build_graph(homg_ctx* h, int stages) {
         });
     if (e == cudaSuccess) e = add_event(3 * stages + 2);
     if (e == cudaSuccess)
-        e = cudaMemcpy(h->dhandles, handles.data(), handles.size() * sizeof(handles[0]), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec_graph, top, 0);
+        e = cudaMemcpy(G.dhandles, handles.data(), handles.size() * sizeof(handles[0]), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, top, 0);
     int rc = (e == cudaSuccess) ? HOMG_OK : cuda_fail(h, e, "building the solve graph");
     if (top) cudaGraphDestroy(top);
     if (cap) cudaStreamDestroy(cap);
-    if (rc != HOMG_OK) destroy_graph(h);
+    if (rc != HOMG_OK) destroy_graph(G);
     return rc;
-}
-
-bool schedule_monotone(const std::vector<int>& s) {
-    for (size_t t = 1; t < s.size(); ++t)
-        if (s[t] > s[t - 1]) return false;
-    return true;
 }
 
 double elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -453,6 +527,23 @@ double elapsed(cudaEvent_t a, cudaEvent_t b) {
     }
     return ms;
 }
+
+// Per-part times of one graph launch, from its events (cycles [k0+1, k1] of the solve ran in it).
+void add_graph_times(homg_stats& st, const std::vector<cudaEvent_t>& E, int local_cycles, int end_ev) {
+    st.solve_ms += elapsed(E[0], E[end_ev]);
+    for (int k = 1; k <= local_cycles; ++k) {
+        st.coarse_ms += elapsed(E[3 * k - 2], E[3 * k - 1]);
+        st.fine_ms += elapsed(E[3 * k - 1], E[3 * k]);
+        st.residual_ms += elapsed(E[3 * k], E[3 * k + 1]);
+    }
+}
+
+bool schedule_monotone(const std::vector<int>& s) {
+    for (size_t t = 1; t < s.size(); ++t)
+        if (s[t] > s[t - 1]) return false;
+    return true;
+}
+
 
 }  // namespace
 
@@ -558,6 +649,15 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     }
     layout(h, h->arena);
     plan_cycle(h);
+    group_coarse_block(h);
+    if (!h->block_ops.empty()) {
+        ce = cudaMemcpy(h->dblock_ops, h->block_ops.data(), h->block_ops.size() * sizeof(BlockOp), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            int rc = cuda_fail(nullptr, ce, "copying the coarse-lattice op list");
+            homg_destroy(h);
+            return rc;
+        }
+    }
     *out = h;
     return HOMG_OK;
 }
@@ -584,20 +684,39 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     s->div_factor = h->opt.diverge_factor;
     s->max_cycles = max_cycles;
     s->status = -1;
-    const std::vector<cudaEvent_t>* ev = nullptr;
-    int end_ev = 0;
+    homg_stats& st = h->stats;
     if (h->opt.launch_mode == HOMG_LAUNCH_GRAPH) {
-        const int want = std::max(max_cycles, 1);
-        if (!h->exec_graph || h->stages < want) {
-            int rc = build_graph(h, std::max(want, h->stages));
+        // First graph: initial residual and up to kStagesPerGraph cycles. Grown (rebuilt) when a
+        // later solve allows more cycles, up to kStagesPerGraph.
+        const int want = std::min(std::max(max_cycles, 1), kStagesPerGraph);
+        if (!h->gfirst.exec || h->gfirst.stages < want) {
+            int rc = build_graph(h, h->gfirst, want, true);
             if (rc != HOMG_OK) return rc;
         }
-        s->stages = h->stages;
+        s->stages = h->gfirst.stages;
+        s->stage_base = 0;
         CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(state)");
-        CK(h, cudaGraphLaunch(h->exec_graph, h->stream), "cudaGraphLaunch");
+        CK(h, cudaGraphLaunch(h->gfirst.exec, h->stream), "cudaGraphLaunch");
         CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
-        ev = &h->ev;
-        end_ev = 3 * h->stages + 2;
+        CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        add_graph_times(st, h->gfirst.ev, s->cycle, 3 * h->gfirst.stages + 2);
+        // Continuation launches while the solve runs and cycles remain (one host sync per launch).
+        while (!s->done && s->cycle < max_cycles) {
+            if (!h->gcont.exec) {
+                int rc = build_graph(h, h->gcont, kStagesPerGraph, false);
+                if (rc != HOMG_OK) return rc;
+            }
+            const int base = s->cycle;
+            State* d = h->dstate;
+            s->stage_base = base;
+            s->stages = h->gcont.stages;
+            CK(h, cudaMemcpyAsync(&d->stage_base, &s->stage_base, sizeof(int), cudaMemcpyHostToDevice, h->stream),
+               "cudaMemcpyAsync(state)");
+            CK(h, cudaGraphLaunch(h->gcont.exec, h->stream), "cudaGraphLaunch");
+            CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
+            CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+            add_graph_times(st, h->gcont.ev, s->cycle - base, 3 * h->gcont.stages + 2);
+        }
     } else {
         // Stream launch mode: same kernels and event layout, the host reads the state once per cycle.
         const size_t need = 3 * (size_t)max_cycles + 3;
@@ -606,39 +725,34 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
             CK(h, cudaEventCreate(&e), "cudaEventCreate");
             h->sev.push_back(e);
         }
-        cudaStream_t st = h->stream;
-        CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(state)");
-        CK(h, cudaEventRecord(h->sev[0], st), "cudaEventRecord");
-        FinalizeArgs fi = fin_args(h, FIN_INIT);
-        fi.handles = nullptr;
-        fi.nstages = 0;
-        CK(h, launch_residual(h->ndim, h->prec, h->strict, resid_args(h, 0), h->n, st), "residual kernel");
-        CK(h, launch_finalize(fi, st), "finalize kernel");
-        CK(h, cudaEventRecord(h->sev[1], st), "cudaEventRecord");
-        CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync(state)");
-        CK(h, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        cudaStream_t sm = h->stream;
+        CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, sm), "cudaMemcpyAsync(state)");
+        CK(h, cudaEventRecord(h->sev[0], sm), "cudaEventRecord");
+        CK(h, launch_residual(h->ndim, h->prec, h->strict, resid_args(h, 0), h->n, sm), "residual kernel");
+        CK(h, launch_finalize(fin_args(h, FIN_INIT, nullptr), sm), "finalize kernel");
+        CK(h, cudaEventRecord(h->sev[1], sm), "cudaEventRecord");
+        CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
+        CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
         for (int k = 1; !s->done && k <= max_cycles; ++k) {
-            CK(h, enqueue_ops(h, h->partA, st), "cycle kernels");
-            CK(h, cudaEventRecord(h->sev[3 * k - 1], st), "cudaEventRecord");
-            CK(h, enqueue_ops(h, h->partB, st), "cycle kernels");
-            CK(h, cudaEventRecord(h->sev[3 * k], st), "cudaEventRecord");
-            FinalizeArgs fc = fin_args(h, FIN_CYCLE);
-            fc.handles = nullptr;
-            fc.nstages = 0;
-            CK(h, launch_residual(h->ndim, h->prec, h->strict, resid_args(h, k), h->n, st), "residual kernel");
-            CK(h, launch_finalize(fc, st), "finalize kernel");
-            CK(h, cudaEventRecord(h->sev[3 * k + 1], st), "cudaEventRecord");
-            CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync(state)");
-            CK(h, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+            CK(h, enqueue_ops(h, h->partA, sm), "cycle kernels");
+            CK(h, cudaEventRecord(h->sev[3 * k - 1], sm), "cudaEventRecord");
+            CK(h, enqueue_ops(h, h->partB, sm), "cycle kernels");
+            CK(h, cudaEventRecord(h->sev[3 * k], sm), "cudaEventRecord");
+            CK(h, launch_residual(h->ndim, h->prec, h->strict, resid_args(h, k), h->n, sm), "residual kernel");
+            CK(h, launch_finalize(fin_args(h, FIN_CYCLE, nullptr), sm), "finalize kernel");
+            CK(h, cudaEventRecord(h->sev[3 * k + 1], sm), "cudaEventRecord");
+            CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
+            CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
         }
         CopyOutArgs c{};
         c.st = h->dstate;
         c.u0 = cdgrid(h->uint_[0], h->pitch0, h->n);
         c.u1 = cdgrid(h->uint_[1], h->pitch0, h->n);
-        CK(h, launch_copy_out(h->ndim, c, h->n, st), "copy-out kernel");
-        end_ev = 3 * s->cycle + 2;
-        CK(h, cudaEventRecord(h->sev[end_ev], st), "cudaEventRecord");
-        ev = &h->sev;
+        CK(h, launch_copy_out(h->ndim, c, h->n, sm), "copy-out kernel");
+        const int end_ev = 3 * s->cycle + 2;
+        CK(h, cudaEventRecord(h->sev[end_ev], sm), "cudaEventRecord");
+        CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+        add_graph_times(st, h->sev, s->cycle, end_ev);
     }
     CK(h, cudaMemcpyAsync(h->hhist, h->dhist, (max_cycles + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
        "cudaMemcpyAsync(hist)");
@@ -646,7 +760,6 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     const int cycles = s->cycle;
     if (cycles_out) *cycles_out = cycles;
     if (relres_out) *relres_out = s->relres;
-    homg_stats& st = h->stats;
     st.cycles = cycles;
     st.status = s->status;
     st.exec_mode = h->exec;
@@ -655,13 +768,6 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     st.kernels_per_cycle = (int)(h->partA.size() + h->partB.size()) + 2;
     st.kernels_fixed = 3;
     st.kernel_launches = st.kernels_fixed + (long long)cycles * st.kernels_per_cycle;
-    const std::vector<cudaEvent_t>& E = *ev;
-    st.solve_ms = elapsed(E[0], E[end_ev]);
-    for (int k = 1; k <= cycles; ++k) {
-        st.coarse_ms += elapsed(E[3 * k - 2], E[3 * k - 1]);
-        st.fine_ms += elapsed(E[3 * k - 1], E[3 * k]);
-        st.residual_ms += elapsed(E[3 * k], E[3 * k + 1]);
-    }
     st.setup_ms = st.solve_ms - st.coarse_ms - st.fine_ms - st.residual_ms;
     const double pts = (h->ndim == 2) ? (double)(h->n - 1) * (h->n - 1) : (double)(h->n - 1) * (h->n - 1) * (h->n - 1);
     st.precision = h->prec;
@@ -704,7 +810,7 @@ int homg_residual_norm(homg_handle h, const double* f, const double* u, double* 
     a.part_r = h->part_r;
     a.part_f = h->part_f;
     CK(h, launch_residual(h->ndim, h->prec, h->strict, a, h->n, h->stream), "residual kernel");
-    FinalizeArgs fa = fin_args(h, FIN_NORM);
+    FinalizeArgs fa = fin_args(h, FIN_NORM, nullptr);
     fa.part_f = h->part_f;
     CK(h, launch_finalize(fa, h->stream), "finalize kernel");
     CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
@@ -731,7 +837,8 @@ const char* homg_last_error(homg_handle h) { return h ? h->err : g_create_error;
 void homg_destroy(homg_handle h) {
     if (!h) return;
     cudaSetDevice(h->device);
-    destroy_graph(h);
+    destroy_graph(h->gfirst);
+    destroy_graph(h->gcont);
     for (cudaEvent_t e : h->sev) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
     if (h->stage_f) cudaFree(h->stage_f);

@@ -21,6 +21,7 @@ struct State {
     double div_factor;
     int max_cycles;
     int stages;        // cycle stages unrolled in the solve graph
+    int stage_base;    // cycles completed before the current graph launch
     int cycle;         // cycles completed
     int status;        // -1 running, else HOMG_OK / HOMG_NOT_CONVERGED / HOMG_DIVERGED
     int done;
@@ -69,7 +70,10 @@ struct IterArgs {
     int mp;         // pending stride exponent, -1: none
     CGrid dprev;    // compact pending variation (level mp)
     Grid dnew;      // compact variation output (p == nullptr: not stored)
-    double omega;
+    double omega;   // damped-Jacobi weight omega_J / (2d)
+    double c1;      // 1 - 2d omega (fast forms)
+    float omega_f;  // the same, rounded to binary32, for the binary32-arithmetic kernels
+    float c1_f;
 };
 
 // Lattice form, level change: fine lattice G (stride 1) from the coarser lattice's final iterate
@@ -123,6 +127,16 @@ struct CopyOutArgs {
     CDGrid u1;   // ... after an odd number
 };
 
+// One op of the coarse-lattice block kernel (fast forms, lattice form only).
+enum BlockKind { BLOCK_RESTRICT = 0, BLOCK_PROLONG = 1, BLOCK_ITER = 2 };
+
+struct BlockOp {
+    int kind;
+    IterArgs it;
+    ProlongArgs pr;
+    RestrictArgs rs;
+};
+
 // Launchers (enqueue on `s`; return the launch error). `prec` is the storage precision of the
 // cycle arrays (Prec); `strict` selects the oracle's canonical operation order.
 cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, cudaStream_t s);
@@ -130,6 +144,7 @@ cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a
 cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a, int n, cudaStream_t s);
 int residual_blocks(int ndim, bool strict, int n);  // partial sums written by launch_residual
 cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s);
+cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s);
 

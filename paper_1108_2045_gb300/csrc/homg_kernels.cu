@@ -60,6 +60,22 @@ __device__ __forceinline__ int64_t at(int64_t pitch, int n, int i, int j, int k)
     return ((int64_t)k * (n + 1) + j) * pitch + i;
 }
 
+// 2^e in the arithmetic type (exact), and the per-type copy of a scalar argument.
+template <typename C> __device__ __forceinline__ C pow2(int e);
+template <> __device__ __forceinline__ double pow2<double>(int e) { return ldexp(1.0, e); }
+template <> __device__ __forceinline__ float pow2<float>(int e) { return ldexpf(1.0f, e); }
+template <typename C> __device__ __forceinline__ C pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+// Programmatic dependent launch: every kernel is launched so that it may start while its
+// predecessor in the stream finishes. Each kernel first waits until the predecessor grid has
+// completed and its writes are visible (griddepcontrol.wait), then lets its own successor launch.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 template <typename T> __device__ __forceinline__ const T* cp(const CGrid& g) { return static_cast<const T*>(g.p); }
 template <typename T> __device__ __forceinline__ T* wp(const Grid& g) { return static_cast<T*>(g.p); }
 
@@ -71,7 +87,7 @@ template <int ND, bool S, bool DIFF, typename T>
 __device__ __forceinline__ typename St<T>::C interp(CGrid d, CGrid d2, int mp, int i, int j, int k) {
     using C = typename St<T>::C;
     const int lp = 1 << mp;
-    const C inv = (C)ldexp(1.0, -mp);
+    const C inv = pow2<C>(-mp);
     const int I0 = i >> mp, a = i & (lp - 1), I1 = a ? I0 + 1 : I0;
     const int J0 = j >> mp, b = j & (lp - 1), J1 = b ? J0 + 1 : J0;
     const C wx0 = (C)(lp - a) * inv, wx1 = (C)a * inv;
@@ -111,18 +127,14 @@ __device__ __forceinline__ typename St<T>::C interp(CGrid d, CGrid d2, int mp, i
 // delayed one iteration). e_old.p == nullptr means e_old = 0 (first iteration of a cycle).
 // ---------------------------------------------------------------------------------------------
 template <int ND, bool S, typename T>
-__global__ void __launch_bounds__(BX * BY) k_iterate(IterArgs a) {
+__device__ __forceinline__ void iterate_point(const IterArgs& a, int i, int j, int k) {
     using C = typename St<T>::C;
     const int n = a.e_new.n;
-    const int i = blockIdx.x * BX + threadIdx.x + 1;
-    const int j = blockIdx.y * BY + threadIdx.y + 1;
-    const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
-    if (i >= n || j >= n) return;
     const bool zero = (a.e_old.p == nullptr);
     auto E = [&](int ii, int jj, int kk) -> C {
         return zero ? (C)0 : St<T>::rd(cp<T>(a.e_old) + at(a.e_old.pitch, n, ii, jj, kk));
     };
-    const C omega = (C)a.omega;
+    const C omega = pick<C>(a.omega, a.omega_f);
     C v = E(i, j, k);
     const int l = 1 << a.m;
     if (((i | j | (ND == 3 ? k : 0)) & (l - 1)) == 0) {
@@ -156,17 +168,24 @@ __global__ void __launch_bounds__(BX * BY) k_iterate(IterArgs a) {
     wp<T>(a.e_new)[at(a.e_new.pitch, n, i, j, k)] = St<T>::put(v);
 }
 
-// ---------------------------------------------------------------------------------------------
-// Lattice form, level change (see ProlongArgs): stale values of the finer lattice.
-// ---------------------------------------------------------------------------------------------
 template <int ND, bool S, typename T>
-__global__ void __launch_bounds__(BX * BY) k_prolong(ProlongArgs a) {
-    using C = typename St<T>::C;
-    const int n = a.G.n;
+__global__ void __launch_bounds__(BX * BY) k_iterate(IterArgs a) {
+    pdl_begin();
+    const int n = a.e_new.n;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
     const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
     if (i >= n || j >= n) return;
+    iterate_point<ND, S, T>(a, i, j, k);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Lattice form, level change (see ProlongArgs): stale values of the finer lattice.
+// ---------------------------------------------------------------------------------------------
+template <int ND, bool S, typename T>
+__device__ __forceinline__ void prolong_point(const ProlongArgs& a, int i, int j, int k) {
+    using C = typename St<T>::C;
+    const int n = a.G.n;
     const int sm = (1 << a.s) - 1;
     C v;
     if (((i | j | (ND == 3 ? k : 0)) & sm) == 0)
@@ -174,6 +193,17 @@ __global__ void __launch_bounds__(BX * BY) k_prolong(ProlongArgs a) {
     else
         v = interp<ND, S, true, T>(a.Gc, a.dl, a.s, i, j, k);
     wp<T>(a.G)[at(a.G.pitch, n, i, j, k)] = St<T>::put(v);
+}
+
+template <int ND, bool S, typename T>
+__global__ void __launch_bounds__(BX * BY) k_prolong(ProlongArgs a) {
+    pdl_begin();
+    const int n = a.G.n;
+    const int i = blockIdx.x * BX + threadIdx.x + 1;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
+    if (i >= n || j >= n) return;
+    prolong_point<ND, S, T>(a, i, j, k);
 }
 
 // Fixed-order block sum of one value per thread (warp butterflies, then warps in order).
@@ -198,6 +228,7 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 // ---------------------------------------------------------------------------------------------
 template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_residual(ResidArgs a, int n) {
+    pdl_begin();
     __shared__ double sh[BX * BY / 32];
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -253,15 +284,11 @@ __global__ void __launch_bounds__(BX * BY) k_residual(ResidArgs a, int n) {
 // g_c = 4 FW(g_f): sources stay pre-scaled by h_m^2, so this equals h_{m+1}^2 FW(F_m) exactly.
 // ---------------------------------------------------------------------------------------------
 template <int ND, bool S, typename T>
-__global__ void __launch_bounds__(BX * BY) k_restrict(RestrictArgs a) {
+__device__ __forceinline__ void restrict_point(const RestrictArgs& a, int I, int J, int K) {
     using C = typename St<T>::C;
     const int nc = a.gc.n;
-    const int I = blockIdx.x * BX + threadIdx.x + 1;
-    const int J = blockIdx.y * BY + threadIdx.y + 1;
-    const int K = (ND == 3) ? (int)blockIdx.z + 1 : 0;
-    if (I >= nc || J >= nc) return;
     const int i = 2 * I, j = 2 * J, k = 2 * K;
-    auto F = [&](int ii, int jj, int kk) -> C { return St<T>::ld(cp<T>(a.gf) + at(a.gf.pitch, a.gf.n, ii, jj, kk)); };
+    auto F = [&](int ii, int jj, int kk) -> C { return St<T>::rd(cp<T>(a.gf) + at(a.gf.pitch, a.gf.n, ii, jj, kk)); };
     C v;
     if (ND == 2) {
         const C c = F(i, j, 0);
@@ -290,12 +317,24 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(RestrictArgs a) {
     wp<T>(a.gc)[at(a.gc.pitch, nc, I, J, K)] = St<T>::put(v);
 }
 
+template <int ND, bool S, typename T>
+__global__ void __launch_bounds__(BX * BY) k_restrict(RestrictArgs a) {
+    pdl_begin();
+    const int nc = a.gc.n;
+    const int I = blockIdx.x * BX + threadIdx.x + 1;
+    const int J = blockIdx.y * BY + threadIdx.y + 1;
+    const int K = (ND == 3) ? (int)blockIdx.z + 1 : 0;
+    if (I >= nc || J >= nc) return;
+    restrict_point<ND, S, T>(a, I, J, K);
+}
+
 // ---------------------------------------------------------------------------------------------
 // K3: convergence test (Sec. 2, restart on the residual equation until the desired accuracy).
 // One block; partial sums are added in a fixed order so the decision is reproducible. Enables the
 // next cycle's conditional graph nodes while the solve continues.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_finalize(FinalizeArgs a) {
+    pdl_begin();
     __shared__ double sh[32];
     double sr = 0.0, sf = 0.0;
     for (int t = threadIdx.x; t < a.nparts; t += blockDim.x) {
@@ -343,14 +382,16 @@ __global__ void __launch_bounds__(1024) k_finalize(FinalizeArgs a) {
     else if (k >= st->max_cycles) status = HOMG_NOT_CONVERGED;
     st->status = status;
     st->done = (status >= 0);
-    if (status < 0 && k + 1 <= a.nstages) {
-        for (int p = 0; p < 3; ++p) cudaGraphSetConditional(a.handles[3 * (k + 1) + p], 1u);
+    const int local = k - st->stage_base;  // stage index within this graph launch
+    if (status < 0 && local + 1 <= a.nstages) {
+        for (int p = 0; p < 3; ++p) cudaGraphSetConditional(a.handles[3 * (local + 1) + p], 1u);
     }
 }
 
 // Copy the final iterate into the caller's u (interior nodes); u = 0 when ||f|| = 0.
 template <int ND>
 __global__ void __launch_bounds__(BX * BY) k_copy_out(CopyOutArgs a, int n) {
+    pdl_begin();
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
     const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
@@ -362,6 +403,34 @@ __global__ void __launch_bounds__(BX * BY) k_copy_out(CopyOutArgs a, int n) {
         v = src.p[at(src.pitch, n, i, j, k)];
     }
     st->u[at(n + 1, n, i, j, k)] = v;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Coarsest lattices in one block: the restrictions, iterations and level changes of every level
+// whose lattice is small run as one launch of a single 512-thread block, which steps through the
+// op list with a block barrier between ops (a barrier also makes each op's global writes visible to
+// the whole block). Replaces dozens of launches whose cost is pure launch latency.
+// ---------------------------------------------------------------------------------------------
+template <int ND, typename T>
+__global__ void __launch_bounds__(512) k_coarse_block(const BlockOp* __restrict__ ops, int nops) {
+    pdl_begin();
+    const int tid = threadIdx.x;
+    for (int o = 0; o < nops; ++o) {
+        const int kind = ops[o].kind;
+        int side;
+        if (kind == BLOCK_RESTRICT) side = ops[o].rs.gc.n - 1;
+        else if (kind == BLOCK_PROLONG) side = ops[o].pr.G.n - 1;
+        else side = ops[o].it.e_new.n - 1;
+        const int total = (ND == 2) ? side * side : side * side * side;
+        for (int q = tid; q < total; q += blockDim.x) {
+            const int i = q % side + 1, j = (q / side) % side + 1, k = (ND == 3) ? q / (side * side) + 1 : 0;
+            if (kind == BLOCK_RESTRICT) restrict_point<ND, false, T>(ops[o].rs, i, j, k);
+            else if (kind == BLOCK_PROLONG) prolong_point<ND, false, T>(ops[o].pr, i, j, k);
+            else iterate_point<ND, false, T>(ops[o].it, i, j, k);
+        }
+        __syncthreads();
+    }
 }
 
 // =============================================================================================
@@ -413,6 +482,7 @@ struct ColumnInterp2 {
 // GB300; in FP32/bfloat16, DRAM does.
 template <int PEND, bool WD, typename T>
 __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
+    pdl_begin();
     using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -425,7 +495,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
     const int64_t po = a.e_new.pitch;
     const T* __restrict__ G = cp<T>(a.g);
     const int64_t pg = a.g.pitch;
-    const C om = (C)a.omega, c1 = (C)(1.0 - 4.0 * a.omega);
+    const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
     const int lpm = PEND ? (1 << a.mp) - 1 : 0;
     ColumnInterp2<T> ci;
     if (PEND == 1) {
@@ -461,6 +531,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
 // stride-2 interpolant of Gc - dl, formed along each marching column (see ColumnInterp2).
 template <typename T>
 __global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
+    pdl_begin();
     using C = typename St<T>::C;
     const int n = a.G.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -485,6 +556,7 @@ constexpr int J3X = 32, J3Y = 4;
 
 template <bool PEND, bool WD, typename T>
 __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
+    pdl_begin();
     using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * J3X + threadIdx.x + 1;
@@ -498,7 +570,7 @@ __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
     const int64_t po = a.e_new.pitch, plo = (int64_t)(n + 1) * po;
     const T* __restrict__ G = cp<T>(a.g);
     const int64_t pg = a.g.pitch, plg = (int64_t)(n + 1) * pg;
-    const C om = (C)a.omega, c1 = (C)(1.0 - 6.0 * a.omega);
+    const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
     const int lpm = PEND ? (1 << a.mp) - 1 : 0;
     const T* col = E + (int64_t)j * pe + i;
     C vb = St<T>::ld(col + (int64_t)(k0 - 1) * ple);
@@ -526,6 +598,7 @@ __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
 // so a node off both lattices costs one FMA and one add.
 template <bool PEND, typename T>
 __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
+    pdl_begin();
     using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -537,13 +610,13 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
     T* __restrict__ O = wp<T>(a.e_new);
     const int64_t po = a.e_new.pitch;
     const int m = a.m, l = 1 << m, lm = l - 1;
-    const C om = (C)a.omega;
+    const C om = pick<C>(a.omega, a.omega_f);
     const bool col_on_lattice = (i & lm) == 0;
     const int mp = PEND ? a.mp : 0;
     const int lpm = (1 << mp) - 1;
     const int I0 = i >> mp;
-    const C alpha = PEND ? (C)(i & lpm) * (C)ldexp(1.0, -mp) : (C)0;
-    const C beta_step = PEND ? (C)ldexp(1.0, -mp) : (C)0;
+    const C alpha = PEND ? (C)(i & lpm) * pow2<C>(-mp) : (C)0;
+    const C beta_step = PEND ? pow2<C>(-mp) : (C)0;
     const T* __restrict__ D = cp<T>(a.dprev);
     const int64_t pd = a.dprev.pitch;
     const bool col_on_prev = (i & lpm) == 0;
@@ -584,6 +657,7 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
 // once per node for the column and once for each side neighbour; 10 FP64 instructions per node.
 template <typename T>
 __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
+    pdl_begin();
     __shared__ double sh[JX / 32];
     const int i = blockIdx.x * JX + threadIdx.x + 1;
     const int j0 = blockIdx.y * JR + 1;
@@ -648,6 +722,21 @@ dim3 resid_grid(int ndim, bool strict, int n) {
 }
 
 // ---- launch templates ----------------------------------------------------------------------
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T>
 cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) {
     const int n = a.e_new.n;
@@ -657,7 +746,7 @@ cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) 
         if (ndim == 2) {
             const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows)), b(JX);
             const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
-#define JAC2(P, W) k_jacobi2<P, W, T><<<g, b, 0, s>>>(a, rows)
+#define JAC2(P, W) launch_k(k_jacobi2<P, W, T>, g, b, s, a, rows)
             if (pend == 0) { if (wd) JAC2(0, true); else JAC2(0, false); }
             else if (pend == 1) { if (wd) JAC2(1, true); else JAC2(1, false); }
             else { if (wd) JAC2(2, true); else JAC2(2, false); }
@@ -667,26 +756,26 @@ cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) 
             const dim3 g((unsigned)((n - 1 + J3X - 1) / J3X), (unsigned)((n - 1 + J3Y - 1) / J3Y),
                          (unsigned)((n - 1 + rows - 1) / rows)),
                 b(J3X, J3Y);
-            if (pend && wd) k_jacobi3<true, true, T><<<g, b, 0, s>>>(a, rows);
-            else if (pend) k_jacobi3<true, false, T><<<g, b, 0, s>>>(a, rows);
-            else if (wd) k_jacobi3<false, true, T><<<g, b, 0, s>>>(a, rows);
-            else k_jacobi3<false, false, T><<<g, b, 0, s>>>(a, rows);
+            if (pend && wd) launch_k(k_jacobi3<true, true, T>, g, b, s, a, rows);
+            else if (pend) launch_k(k_jacobi3<true, false, T>, g, b, s, a, rows);
+            else if (wd) launch_k(k_jacobi3<false, true, T>, g, b, s, a, rows);
+            else launch_k(k_jacobi3<false, false, T>, g, b, s, a, rows);
         }
         return cudaGetLastError();
     }
     if (!strict && ndim == 2 && a.m >= 1 && a.e_old.p != nullptr && a.mp != 0) {
         const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + JR - 1) / JR)), b(JX);
-        if (a.mp >= 1) k_wholegrid2<true, T><<<g, b, 0, s>>>(a);
-        else k_wholegrid2<false, T><<<g, b, 0, s>>>(a);
+        if (a.mp >= 1) launch_k(k_wholegrid2<true, T>, g, b, s, a);
+        else launch_k(k_wholegrid2<false, T>, g, b, s, a);
         return cudaGetLastError();
     }
     const dim3 g = grid_for(ndim, n), b(BX, BY);
     if (ndim == 2) {
-        if (strict) k_iterate<2, true, T><<<g, b, 0, s>>>(a);
-        else k_iterate<2, false, T><<<g, b, 0, s>>>(a);
+        if (strict) launch_k(k_iterate<2, true, T>, g, b, s, a);
+        else launch_k(k_iterate<2, false, T>, g, b, s, a);
     } else {
-        if (strict) k_iterate<3, true, T><<<g, b, 0, s>>>(a);
-        else k_iterate<3, false, T><<<g, b, 0, s>>>(a);
+        if (strict) launch_k(k_iterate<3, true, T>, g, b, s, a);
+        else launch_k(k_iterate<3, false, T>, g, b, s, a);
     }
     return cudaGetLastError();
 }
@@ -697,16 +786,16 @@ cudaError_t prolong_t(int ndim, bool strict, const ProlongArgs& a, cudaStream_t 
         const int n = a.G.n;
         const int rows = march_rows(2, n);
         const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows));
-        k_prolong2_s1<T><<<g, dim3(JX), 0, s>>>(a, rows);
+        launch_k(k_prolong2_s1<T>, g, dim3(JX), s, a, rows);
         return cudaGetLastError();
     }
     const dim3 g = grid_for(ndim, a.G.n), b(BX, BY);
     if (ndim == 2) {
-        if (strict) k_prolong<2, true, T><<<g, b, 0, s>>>(a);
-        else k_prolong<2, false, T><<<g, b, 0, s>>>(a);
+        if (strict) launch_k(k_prolong<2, true, T>, g, b, s, a);
+        else launch_k(k_prolong<2, false, T>, g, b, s, a);
     } else {
-        if (strict) k_prolong<3, true, T><<<g, b, 0, s>>>(a);
-        else k_prolong<3, false, T><<<g, b, 0, s>>>(a);
+        if (strict) launch_k(k_prolong<3, true, T>, g, b, s, a);
+        else launch_k(k_prolong<3, false, T>, g, b, s, a);
     }
     return cudaGetLastError();
 }
@@ -715,11 +804,11 @@ template <typename T>
 cudaError_t residual_t(int ndim, bool strict, const ResidArgs& a, int n, cudaStream_t s) {
     const dim3 g = resid_grid(ndim, strict, n);
     if (ndim == 2) {
-        if (strict) k_residual<2, true, T><<<g, dim3(BX, BY), 0, s>>>(a, n);
-        else k_residual2_fast<T><<<g, dim3(JX), 0, s>>>(a, n);
+        if (strict) launch_k(k_residual<2, true, T>, g, dim3(BX, BY), s, a, n);
+        else launch_k(k_residual2_fast<T>, g, dim3(JX), s, a, n);
     } else {
-        if (strict) k_residual<3, true, T><<<g, dim3(BX, BY), 0, s>>>(a, n);
-        else k_residual<3, false, T><<<g, dim3(BX, BY), 0, s>>>(a, n);
+        if (strict) launch_k(k_residual<3, true, T>, g, dim3(BX, BY), s, a, n);
+        else launch_k(k_residual<3, false, T>, g, dim3(BX, BY), s, a, n);
     }
     return cudaGetLastError();
 }
@@ -728,11 +817,11 @@ template <typename T>
 cudaError_t restrict_t(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s) {
     const dim3 g = grid_for(ndim, a.gc.n), b(BX, BY);
     if (ndim == 2) {
-        if (strict) k_restrict<2, true, T><<<g, b, 0, s>>>(a);
-        else k_restrict<2, false, T><<<g, b, 0, s>>>(a);
+        if (strict) launch_k(k_restrict<2, true, T>, g, b, s, a);
+        else launch_k(k_restrict<2, false, T>, g, b, s, a);
     } else {
-        if (strict) k_restrict<3, true, T><<<g, b, 0, s>>>(a);
-        else k_restrict<3, false, T><<<g, b, 0, s>>>(a);
+        if (strict) launch_k(k_restrict<3, true, T>, g, b, s, a);
+        else launch_k(k_restrict<3, false, T>, g, b, s, a);
     }
     return cudaGetLastError();
 }
@@ -768,15 +857,20 @@ cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs&
     DISPATCH_PREC(prec, restrict_t<T>(ndim, strict, a, s));
 }
 
+cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, cudaStream_t s) {
+    if (ndim == 2) { DISPATCH_PREC(prec, (launch_k(k_coarse_block<2, T>, 1, 512, s, ops, nops), cudaGetLastError())); }
+    DISPATCH_PREC(prec, (launch_k(k_coarse_block<3, T>, 1, 512, s, ops, nops), cudaGetLastError()));
+}
+
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
-    k_finalize<<<1, 1024, 0, s>>>(a);
+    launch_k(k_finalize, 1, 1024, s, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s) {
     const dim3 g = grid_for(ndim, n), b(BX, BY);
-    if (ndim == 2) k_copy_out<2><<<g, b, 0, s>>>(a, n);
-    else k_copy_out<3><<<g, b, 0, s>>>(a, n);
+    if (ndim == 2) launch_k(k_copy_out<2>, g, b, s, a, n);
+    else launch_k(k_copy_out<3>, g, b, s, a, n);
     return cudaGetLastError();
 }
 
