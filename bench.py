@@ -111,6 +111,28 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x, device=None):
+    """Largest value of x over all ranks (x itself in a single process)."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, elapsed_s, device=None):
+    """Whole-job throughput of independent replicas: every rank's units over the slowest rank's time.
+
+    Replicas only (the solve does not shard across GPUs): the sole collectives are this max and a
+    barrier; no data crosses ranks."""
+    import torch
+
+    world = torch.distributed.get_world_size() if torch.distributed.is_initialized() else 1
+    return units_per_rank * world / max_over_ranks(elapsed_s, device)
+
+
 def oracle_cpu_baseline(f_np, cycles):
     """The oracle as it stands, single-threaded on a host core: one cycle on the benchmark grid
     (residual + restriction + 286 HOMG iterations), scaled by the solve's cycle count."""
@@ -123,6 +145,75 @@ def oracle_cpu_baseline(f_np, cycles):
     t_solve = dt * cycles
     return {"value": (N_SIDE - 1) ** 2 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "one oracle cycle on the 4097^2 grid (%.1f s), scaled by the %d cycles a solve takes" % (dt, cycles)}
+
+
+CFG3_SIDE = 512
+CFG3_LEVELS = 9
+
+
+def run_cfg3(args, homg, inputs, stream, barrier):
+    """3-D Poisson, 7-point stencil, 513^3 nodes, 9 levels: FP64 cycles against FP32 and bfloat16
+    cycles (FP64 residual, update and norms; iterative refinement) to relative residual 1e-10, for
+    f = 3 pi^2 sin sin sin and for f iid N(0, 1) (seed 0). Reports time to 1e-10, cycles, the error
+    against the FP64 solution and, for the sine case, against the closed-form discrete solution
+    c_h prod sin(pi x_k), c_h = pi^2 h^2 / (4 sin^2(pi h / 2))."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    n = CFG3_SIDE
+    out = {"workload": "3-D Poisson -Lap u = f, 7-point, 513^3 nodes, 9 levels, MaxI=32, to relres 1e-10"}
+    h = 1.0 / n
+    ch = np.pi ** 2 * h ** 2 / (4 * np.sin(np.pi * h / 2) ** 2)
+    for rhs in ("sine", "normal"):
+        f_np = inputs.sine_rhs(n, 3) if rhs == "sine" else inputs.normal_rhs(n, 3, seed=0)
+        f = torch.from_numpy(f_np).cuda()
+        del f_np
+        u = torch.zeros_like(f)
+        ref = None
+        res = {}
+        for prec in ("fp64", "fp32", "bf16"):
+            with homg.Solver(3, n + 1, CFG3_LEVELS, max_i=MAX_I, precision=prec) as s3:
+                s3.set_stream(stream)
+                u.zero_()
+                s3.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+                barrier()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.cfg3_steps):
+                    u.zero_()
+                    st, cyc, rr = s3.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+                e1.record(stream)
+                barrier()
+                ms = e0.elapsed_time(e1) / args.cfg3_steps
+                stats = s3.stats()
+            r = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms,
+                 "unknowns_per_s": (n - 1) ** 3 / (ms * 1e-3),
+                 "fine_launch_us": 1e3 * stats["fine_ms"] / max(1, stats["cycles"] * stats["fine_iterations_per_cycle"])}
+            if prec == "fp64":
+                ref = u.clone()
+            else:
+                r["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref))
+                r["speedup_vs_fp64"] = res["fp64"]["ms_per_solve"] / ms
+            if rhs == "sine":
+                x = torch.arange(n + 1, dtype=torch.float64, device=u.device) / n
+                sx = torch.sin(np.pi * x)
+                exact = ch * sx[:, None, None] * sx[None, :, None] * sx[None, None, :]
+                r["rel_err_vs_discrete_exact"] = float(torch.linalg.vector_norm(u - exact) / torch.linalg.vector_norm(exact))
+                del exact
+            if rhs == "normal" and prec == "fp32" and args.cfg3_oracle_check:
+                # the oracle's own FP64 residual of the mixed-precision solution
+                fn = f.cpu().numpy()
+                un = u.cpu().numpy()
+                r["oracle_relres"] = oracle.norm_interior(oracle.residual(fn, un)) / oracle.norm_interior(fn)
+                del fn, un
+            res[prec] = r
+        out[rhs] = res
+        del f, u, ref
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -209,13 +300,9 @@ def run(args):
             stats.append(solver.stats())
         t1.record(stream)
         barrier()
-    elapsed_ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     unknowns = (N_SIDE - 1) ** 2
-    value = unknowns * args.steps * world / (elapsed_ms * 1e-3)
+    value = replica_throughput(unknowns * args.steps, t0.elapsed_time(t1) * 1e-3, dev)
+    elapsed_ms = max_over_ranks(t0.elapsed_time(t1), dev)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     f_host = torch.from_numpy(f_np).pin_memory()
@@ -229,11 +316,7 @@ def run(args):
         if st != homg.HOMG_OK:
             raise RuntimeError("host solve did not converge")
     barrier()
-    e2e_s = time.perf_counter() - e0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_value = replica_throughput(unknowns * args.steps, time.perf_counter() - e0, dev)
     grid_bytes = f_np.nbytes
 
     # whole-grid form of the same iterates (the paper's one-launch-per-iteration layout), for contrast
@@ -294,6 +377,7 @@ def run(args):
                            "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
                                                       for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
 
+    cfg3 = run_cfg3(args, homg, inputs, stream, barrier) if (args.cfg3_steps > 0 and world == 1) else None
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
     launches = sum(s["cycles"] * s["fine_iterations_per_cycle"] for s in stats)
@@ -329,7 +413,7 @@ def run(args):
                    "l2": "working set ~0.8 GB > 126 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU", "launch": args.launch},
         "roofline": roofline,
-        "e2e": {"value": unknowns * args.steps * world / e2e_s, "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * grid_bytes, "d2h_bytes_per_step": grid_bytes},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "clocks": clk,
@@ -340,6 +424,8 @@ def run(args):
         line["wholegrid"] = wg
     if mixed:
         line["mixed_precision"] = mixed
+    if args.cfg3_steps > 0 and world == 1:
+        line["cfg3_3d"] = cfg3
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_cpu_baseline(f_np, stats[-1]["cycles"])
     solver.close()
@@ -364,6 +450,8 @@ def main():
                    help="stream: enqueue kernels directly (for profilers that cannot see inside conditional graphs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mixed-steps", type=int, default=3, help="timed solves per mixed-precision variant (0: skip)")
+    p.add_argument("--cfg3-steps", type=int, default=2, help="timed 513^3 solves per precision and RHS (0: skip)")
+    p.add_argument("--no-cfg3-oracle-check", dest="cfg3_oracle_check", action="store_false")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")

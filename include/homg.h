@@ -191,7 +191,7 @@ const char* homg_last_error(homg_handle h);
 void homg_destroy(homg_handle h);
 
 /* Capacity of the static scratch used by homg_residual_norm_noalloc: one partial sum per thread
- * block of the residual kernel, at most this many (2-D grids up to 8193^2, 3-D up to 257^3). */
+ * block of the residual kernel, at most this many (2-D grids up to 8193^2, 3-D up to 513^3). */
 #define HOMG_NOALLOC_MAX_BLOCKS 65536
 
 /* Allocation-free relative residual ||f - A u||_2 / ||f||_2 (interior nodes) of device arrays f

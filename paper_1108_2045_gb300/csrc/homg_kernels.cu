@@ -591,6 +591,117 @@ __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
     }
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Fast 3-D update + residual in two passes: k_update3 forms u_out = u_in + e (one FP64 add per
+// node), then k_residual3_fast marches each (i, j) column along z over the updated iterate with the
+// vertical neighbours in registers: 9 FP64 instructions per node, instead of re-forming u + e for
+// every neighbour.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(J3X * J3Y) k_copy_in3(ResidArgs a, int n, int rows) {
+    pdl_begin();
+    const int i = blockIdx.x * J3X + threadIdx.x + 1;
+    const int j = blockIdx.y * J3Y + threadIdx.y + 1;
+    if (i >= n || j >= n) return;
+    const int k0 = blockIdx.z * rows + 1;
+    const int k1 = min(k0 + rows, n);
+    for (int k = k0; k < k1; ++k)
+        a.u_out.p[at(a.u_out.pitch, n, i, j, k)] = a.st->u[at(n + 1, n, i, j, k)];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(J3X * J3Y) k_update3(ResidArgs a, int n, int rows) {
+    pdl_begin();
+    const int i = blockIdx.x * J3X + threadIdx.x + 1;
+    const int j = blockIdx.y * J3Y + threadIdx.y + 1;
+    if (i >= n || j >= n) return;
+    const int k0 = blockIdx.z * rows + 1;
+    const int k1 = min(k0 + rows, n);
+    for (int k = k0; k < k1; ++k) {
+        const double v = __ldg(a.u_in.p + at(a.u_in.pitch, n, i, j, k)) +
+                         (double)St<T>::ld(cp<T>(a.e) + at(a.e.pitch, n, i, j, k));
+        a.u_out.p[at(a.u_out.pitch, n, i, j, k)] = v;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(J3X * J3Y) k_residual3_fast(ResidArgs a, int n, int rows) {
+    pdl_begin();
+    __shared__ double sh[J3X * J3Y / 32];
+    const int i = blockIdx.x * J3X + threadIdx.x + 1;
+    const int j = blockIdx.y * J3Y + threadIdx.y + 1;
+    const int k0 = blockIdx.z * rows + 1;
+    const int k1 = min(k0 + rows, n);
+    const bool active = (i < n && j < n);
+    const double* __restrict__ U = a.u_in.p ? a.u_in.p : a.st->u;
+    const int64_t pu = a.u_in.p ? a.u_in.pitch : (int64_t)(n + 1);
+    const int64_t plu = (int64_t)(n + 1) * pu;
+    const double* __restrict__ F = a.st->f;
+    const int64_t pf = n + 1, plf = (int64_t)(n + 1) * pf;
+    double rr = 0.0, ff = 0.0;
+    if (active) {
+        // boundary nodes of the caller's u are not read: the operator takes 0 there
+        auto uval = [&](int ii, int jj, int kk) -> double {
+            if (ii <= 0 || jj <= 0 || kk <= 0 || ii >= n || jj >= n || kk >= n) return 0.0;
+            return __ldg(U + (int64_t)kk * plu + (int64_t)jj * pu + ii);
+        };
+        double vb = uval(i, j, k0 - 1), vc = uval(i, j, k0);
+        for (int k = k0; k < k1; ++k) {
+            const double vt = uval(i, j, k + 1);
+            const double sum = ((uval(i - 1, j, k) + uval(i + 1, j, k)) + (uval(i, j - 1, k) + uval(i, j + 1, k))) + (vb + vt);
+            const double fv = __ldg(F + (int64_t)k * plf + (int64_t)j * pf + i);
+            const double r = fma(a.inv_h2, fma(-6.0, vc, sum), fv);
+            if (a.g0.p) wp<T>(a.g0)[at(a.g0.pitch, n, i, j, k)] = St<T>::put(St<T>::from_d(a.scale * r));
+            rr = fma(r, r, rr);
+            ff = fma(fv, fv, ff);
+            vb = vc;
+            vc = vt;
+        }
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    double t = block_sum(rr, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) a.part_r[bid] = t;
+    if (a.part_f) {
+        t = block_sum(ff, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) a.part_f[bid] = t;
+    }
+}
+
+// Fast lattice-form level change at stride 2 (3-D): a node with p odd indexes takes the mean of the
+// 2^p surrounding values of Gc - dl; lattice nodes copy Gc.
+template <typename T>
+__global__ void __launch_bounds__(J3X * J3Y) k_prolong3_s1(ProlongArgs a, int rows) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    const int n = a.G.n;
+    const int i = blockIdx.x * J3X + threadIdx.x + 1;
+    const int j = blockIdx.y * J3Y + threadIdx.y + 1;
+    if (i >= n || j >= n) return;
+    const int k0 = blockIdx.z * rows + 1;
+    const int k1 = min(k0 + rows, n);
+    const int I0 = i >> 1, J0 = j >> 1;
+    const int ox = i & 1, oy = j & 1;
+    const T* C0 = cp<T>(a.Gc);
+    const T* D0 = cp<T>(a.dl);
+    const int nc = a.Gc.n;
+    for (int k = k0; k < k1; ++k) {
+        const int K0 = k >> 1, oz = k & 1;
+        C v;
+        if (!(ox | oy | oz)) {
+            v = St<T>::ld(C0 + at(a.Gc.pitch, nc, I0, J0, K0));
+        } else {
+            C acc = 0;
+            for (int dz = 0; dz <= oz; ++dz)
+                for (int dy = 0; dy <= oy; ++dy)
+                    for (int dx = 0; dx <= ox; ++dx)
+                        acc += St<T>::ld(C0 + at(a.Gc.pitch, nc, I0 + dx, J0 + dy, K0 + dz)) -
+                               St<T>::ld(D0 + at(a.dl.pitch, a.dl.n, I0 + dx, J0 + dy, K0 + dz));
+            v = acc * ((C)1 / (C)(1 << (ox + oy + oz)));
+        }
+        wp<T>(a.G)[at(a.G.pitch, n, i, j, k)] = St<T>::put(v);
+    }
+}
+
 // Fast whole-grid iteration at level m >= 1 (2-D): every fine node adds the bilinear interpolant of
 // the pending variation (level mp >= 1) unless it lies on the level-mp lattice, and level-m
 // lattice nodes relax. Each thread marches one column; the interpolant along x is formed once per
@@ -715,9 +826,14 @@ dim3 grid_for(int ndim, int n) {
     return dim3((unsigned)((n - 1 + BX - 1) / BX), (unsigned)((n - 1 + BY - 1) / BY), ndim == 3 ? (unsigned)(n - 1) : 1u);
 }
 
-// The fast 2-D residual uses its own grid: (n-1)/JX x (n-1)/JR blocks.
+// The fast residual kernels use their own grids: 2-D (n-1)/JX x (n-1)/JR blocks, 3-D
+// (n-1)/J3X x (n-1)/J3Y x (n-1)/rows.
 dim3 resid_grid(int ndim, bool strict, int n) {
     if (ndim == 2 && !strict) return dim3((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + JR - 1) / JR));
+    if (ndim == 3 && !strict) {
+        const int rows = march_rows(3, n);
+        return dim3((unsigned)((n - 1 + J3X - 1) / J3X), (unsigned)((n - 1 + J3Y - 1) / J3Y), (unsigned)((n - 1 + rows - 1) / rows));
+    }
     return grid_for(ndim, n);
 }
 
@@ -789,6 +905,13 @@ cudaError_t prolong_t(int ndim, bool strict, const ProlongArgs& a, cudaStream_t 
         launch_k(k_prolong2_s1<T>, g, dim3(JX), s, a, rows);
         return cudaGetLastError();
     }
+    if (!strict && ndim == 3 && a.s == 1) {
+        const int n = a.G.n;
+        const int rows = march_rows(3, n);
+        const dim3 g((unsigned)((n - 1 + J3X - 1) / J3X), (unsigned)((n - 1 + J3Y - 1) / J3Y), (unsigned)((n - 1 + rows - 1) / rows));
+        launch_k(k_prolong3_s1<T>, g, dim3(J3X, J3Y), s, a, rows);
+        return cudaGetLastError();
+    }
     const dim3 g = grid_for(ndim, a.G.n), b(BX, BY);
     if (ndim == 2) {
         if (strict) launch_k(k_prolong<2, true, T>, g, b, s, a);
@@ -806,9 +929,21 @@ cudaError_t residual_t(int ndim, bool strict, const ResidArgs& a, int n, cudaStr
     if (ndim == 2) {
         if (strict) launch_k(k_residual<2, true, T>, g, dim3(BX, BY), s, a, n);
         else launch_k(k_residual2_fast<T>, g, dim3(JX), s, a, n);
+    } else if (strict) {
+        launch_k(k_residual<3, true, T>, g, dim3(BX, BY), s, a, n);
     } else {
-        if (strict) launch_k(k_residual<3, true, T>, g, dim3(BX, BY), s, a, n);
-        else launch_k(k_residual<3, false, T>, g, dim3(BX, BY), s, a, n);
+        const int rows = march_rows(3, n);
+        ResidArgs b = a;
+        if (a.e.p) {  // update pass first; the residual then reads the updated iterate
+            launch_k(k_update3<T>, g, dim3(J3X, J3Y), s, a, n, rows);
+            b.u_in = CDGrid{a.u_out.p, a.u_out.pitch, a.u_out.n};
+            b.e = CGrid{nullptr, 0, n};
+        } else if (a.u_out.p) {  // initial residual: copy the caller's u in, then read the copy
+            ResidArgs c = a;
+            launch_k(k_copy_in3, g, dim3(J3X, J3Y), s, c, n, rows);
+            b.u_in = CDGrid{a.u_out.p, a.u_out.pitch, a.u_out.n};
+        }
+        launch_k(k_residual3_fast<T>, g, dim3(J3X, J3Y), s, b, n, rows);
     }
     return cudaGetLastError();
 }

@@ -70,7 +70,7 @@ extern "C" int homg_residual_norm_noalloc(int ndim, const int64_t* dims, const d
     if (nblocks > HOMG_NOALLOC_MAX_BLOCKS) {
         snprintf(msg, sizeof(msg),
                  "homg_residual_norm_noalloc: this grid needs %d partial sums, the static scratch holds %d "
-                 "(2-D grids up to 8193^2, 3-D grids up to 257^3)",
+                 "(2-D grids up to 8193^2, 3-D grids up to 513^3)",
                  nblocks, HOMG_NOALLOC_MAX_BLOCKS);
         return fail(HOMG_ESHAPE, msg);
     }
