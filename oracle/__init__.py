@@ -18,8 +18,11 @@ from .oracle import (  # noqa: F401
     iteration,
     mfmg_schedule,
     norm_interior,
+    prolong,
     residual,
     restrict,
     solve,
     solve_mixed,
+    solve_vcycle,
+    vcycle,
 )

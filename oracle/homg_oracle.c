@@ -648,3 +648,128 @@ int homg_oracle_solve_mixed(int ndim, int64_t n, int levels, const int *sched, i
     if (relres_out) *relres_out = rr;
     return status;
 }
+
+/* ========================================================================================== */
+/* Classic V(nu1, nu2) cycle, the comparator of the benchmark (Sec. 2, the two-grid correction   */
+/* scheme (a)-(e) applied recursively): (a) nu1 damped-Jacobi pre-smoothing sweeps, (b) the       */
+/* residual restricted to the next coarser grid by full weighting, (c) the coarse residual        */
+/* equation solved by the same cycle, (d) the coarse correction interpolated bilinearly and added,*/
+/* (e) nu2 post-smoothing sweeps. Coarse operators are rediscretised (5/7-point at spacing 2^m h).*/
+/* The coarsest level (reading of this build) is solved by max(1, n_c^2) undamped Jacobi sweeps   */
+/* from zero: exact in one sweep when it has a single interior node.                             */
+/* ========================================================================================== */
+
+/* (Bi/tri)linear prolongation of a compact coarse array (nc = nf/2 intervals) onto the fine   */
+/* compact grid: lattice nodes copy the coarse value, the others interpolate (weights 1/2, 1/4,  */
+/* 1/8). Boundary nodes are 0.                                                                  */
+void homg_oracle_prolong(int ndim, int64_t nf, const double *Ec, double *Ef) {
+    const int64_t side = nf + 1, nc = nf / 2;
+    const int64_t kmax = (ndim == 2) ? 0 : nf;
+    for (int64_t k = 0; k <= kmax; ++k)
+        for (int64_t j = 0; j <= nf; ++j)
+            for (int64_t i = 0; i <= nf; ++i) {
+                int64_t p = (k * side + j) * side + i;
+                int boundary = i == 0 || j == 0 || i == nf || j == nf || (ndim == 3 && (k == 0 || k == nf));
+                if (boundary) { Ef[p] = 0.0; continue; }
+                int on = (i % 2 == 0) && (j % 2 == 0) && (ndim == 2 || k % 2 == 0);
+                if (on) Ef[p] = Ec[((k / 2) * (nc + 1) + j / 2) * (nc + 1) + i / 2];
+                else Ef[p] = (ndim == 2) ? interp2(Ec, nf, 1, i, j) : interp3(Ec, nf, 1, i, j, k);
+            }
+}
+
+static int vcycle_level(int ndim, int64_t n, int m, int M, int nu1, int nu2, double omega, const double *Fm,
+                        double *em) {
+    const int64_t nm = n >> m;
+    const int64_t cnt = ipow(nm + 1, ndim);
+    double *tmp = (double *)malloc((size_t)cnt * sizeof(double));
+    double *dsc = (double *)malloc((size_t)cnt * sizeof(double));
+    int rc = HOMG_ORACLE_OK;
+    if (!tmp || !dsc) { free(tmp); free(dsc); return HOMG_ORACLE_ENOMEM; }
+    for (int64_t p = 0; p < cnt; ++p) em[p] = 0.0;
+    if (m == M) {
+        /* coarsest level: undamped Jacobi (omega = 1/(2d)) sweeps from zero */
+        int64_t sweeps = nm * nm > 1 ? nm * nm : 1;
+        for (int64_t s = 0; s < sweeps; ++s) {
+            homg_oracle_iteration(ndim, nm, 0, -1, 1.0 / (2.0 * ndim), Fm, NULL, em, tmp, dsc);
+            memcpy(em, tmp, (size_t)cnt * sizeof(double));
+        }
+        free(tmp); free(dsc);
+        return HOMG_ORACLE_OK;
+    }
+    const int64_t ncm = nm / 2;
+    const int64_t ccnt = ipow(ncm + 1, ndim);
+    double *r = (double *)malloc((size_t)cnt * sizeof(double));
+    double *Fc = (double *)malloc((size_t)ccnt * sizeof(double));
+    double *ec = (double *)malloc((size_t)ccnt * sizeof(double));
+    double *pe = (double *)malloc((size_t)cnt * sizeof(double));
+    if (!r || !Fc || !ec || !pe) { rc = HOMG_ORACLE_ENOMEM; goto done; }
+    for (int s = 0; s < nu1; ++s) {                            /* (a) pre-smoothing */
+        homg_oracle_iteration(ndim, nm, 0, -1, omega, Fm, NULL, em, tmp, dsc);
+        memcpy(em, tmp, (size_t)cnt * sizeof(double));
+    }
+    homg_oracle_residual(ndim, nm, Fm, em, r);                 /* (b) residual ...       */
+    homg_oracle_restrict(ndim, nm, r, Fc);                     /*     ... restricted     */
+    rc = vcycle_level(ndim, n, m + 1, M, nu1, nu2, omega, Fc, ec); /* (c) coarse equation */
+    if (rc != HOMG_ORACLE_OK) goto done;
+    homg_oracle_prolong(ndim, nm, ec, pe);                     /* (d) interpolate ...    */
+    for (int64_t p = 0; p < cnt; ++p) em[p] = em[p] + pe[p];   /*     ... and correct    */
+    for (int s = 0; s < nu2; ++s) {                            /* (e) post-smoothing */
+        homg_oracle_iteration(ndim, nm, 0, -1, omega, Fm, NULL, em, tmp, dsc);
+        memcpy(em, tmp, (size_t)cnt * sizeof(double));
+    }
+done:
+    free(tmp); free(dsc); free(r); free(Fc); free(ec); free(pe);
+    return rc;
+}
+
+/* One V(nu1, nu2) cycle on A e = F0 from e = 0 (levels 0 .. levels-1). */
+int homg_oracle_vcycle(int ndim, int64_t n, int levels, int nu1, int nu2, double omega_j, const double *F0, double *e) {
+    int K = log2_exact(n);
+    if ((ndim != 2 && ndim != 3) || K < 1 || levels < 1 || levels > K || nu1 < 0 || nu2 < 0) return HOMG_ORACLE_EINVAL;
+    return vcycle_level(ndim, n, 0, levels - 1, nu1, nu2, omega_j / (2.0 * ndim), F0, e);
+}
+
+/* Restarted V-cycle solve: the same loop and stopping rules as homg_oracle_solve. */
+int homg_oracle_solve_vcycle(int ndim, int64_t n, int levels, int nu1, int nu2, double omega_j, double div_factor,
+                             const double *f, double *u, double tol, int max_cycles, double *hist, int *cycles_out,
+                             double *relres_out) {
+    int K = log2_exact(n);
+    if ((ndim != 2 && ndim != 3) || K < 1 || levels < 1 || levels > K || max_cycles < 0) return HOMG_ORACLE_EINVAL;
+    const int64_t side = n + 1;
+    const int64_t total = ipow(side, ndim);
+    double fnorm = homg_oracle_norm_interior(ndim, n, f);
+    if (fnorm == 0.0) {
+        for (int64_t p = 0; p < total; ++p) {
+            int64_t i = p % side, j = (p / side) % side, k = (ndim == 3) ? p / (side * side) : 1;
+            if (i > 0 && j > 0 && k > 0 && i < n && j < n && k < n) u[p] = 0.0;
+        }
+        if (hist) hist[0] = 0.0;
+        if (cycles_out) *cycles_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        return HOMG_ORACLE_OK;
+    }
+    double *r = (double *)malloc((size_t)total * sizeof(double));
+    double *e = (double *)malloc((size_t)total * sizeof(double));
+    if (!r || !e) { free(r); free(e); return HOMG_ORACLE_ENOMEM; }
+    int status = HOMG_ORACLE_NOT_CONVERGED, k;
+    double rr = 0.0, rr0 = 0.0;
+    for (k = 0;; ++k) {
+        homg_oracle_residual(ndim, n, f, u, r);
+        rr = homg_oracle_norm_interior(ndim, n, r) / fnorm;
+        if (hist) hist[k] = rr;
+        if (k == 0) rr0 = rr;
+        if (rr <= tol) { status = HOMG_ORACLE_OK; break; }
+        if (!isfinite(rr) || rr > div_factor * rr0) { status = HOMG_ORACLE_DIVERGED; break; }
+        if (k == max_cycles) { status = HOMG_ORACLE_NOT_CONVERGED; break; }
+        int rc = homg_oracle_vcycle(ndim, n, levels, nu1, nu2, omega_j, r, e);
+        if (rc != HOMG_ORACLE_OK) { free(r); free(e); return rc; }
+        for (int64_t p = 0; p < total; ++p) {
+            int64_t i = p % side, j = (p / side) % side, kk = (ndim == 3) ? p / (side * side) : 1;
+            if (i > 0 && j > 0 && kk > 0 && i < n && j < n && kk < n) u[p] = u[p] + e[p];
+        }
+    }
+    free(r); free(e);
+    if (cycles_out) *cycles_out = k;
+    if (relres_out) *relres_out = rr;
+    return status;
+}

@@ -50,6 +50,12 @@ def _load(path=None):
         lib.homg_oracle_solve_mixed.argtypes = [ctypes.c_int, i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int,
                                                 P, IP, P]
+        lib.homg_oracle_prolong.argtypes = [ctypes.c_int, i64, P, P]
+        lib.homg_oracle_vcycle.argtypes = [ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           P, P]
+        lib.homg_oracle_solve_vcycle.argtypes = [ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_double, ctypes.c_double, P, P, ctypes.c_double,
+                                                 ctypes.c_int, P, IP, P]
         lib.homg_oracle_bf16_round.argtypes = [ctypes.c_float]
         lib.homg_oracle_bf16_round.restype = ctypes.c_float
         _lib = lib
@@ -153,6 +159,43 @@ def cycle(F0, levels, schedule=None, max_i=32, omega_j=None):
 
 
 PRECISIONS = {"fp32": 1, "bf16": 2}
+
+
+def prolong(Ec):
+    """Bilinear/trilinear prolongation of a compact coarse array onto the grid with twice the intervals."""
+    ndim, nc = _grid_n(Ec)
+    Ef = np.empty((2 * nc + 1,) * ndim)
+    _load().homg_oracle_prolong(ndim, 2 * nc, _p(np.ascontiguousarray(Ec)), _p(Ef))
+    return Ef
+
+
+def vcycle(F0, levels, nu1=2, nu2=2, omega_j=None):
+    """One classic V(nu1, nu2) cycle on A e = F0 from e = 0."""
+    ndim, n = _grid_n(F0)
+    if omega_j is None:
+        omega_j = default_omega_j(ndim)
+    e = np.empty_like(F0)
+    rc = _load().homg_oracle_vcycle(ndim, n, levels, nu1, nu2, omega_j, _p(np.ascontiguousarray(F0)), _p(e))
+    if rc != 0:
+        raise ValueError("oracle V-cycle rejected its arguments (rc=%d)" % rc)
+    return e
+
+
+def solve_vcycle(f, levels, nu1=2, nu2=2, u0=None, tol=1e-10, max_cycles=100, omega_j=None, div_factor=1e3):
+    """Restarted V(nu1, nu2) solve. Returns (u, status, cycles, hist)."""
+    ndim, n = _grid_n(f)
+    if omega_j is None:
+        omega_j = default_omega_j(ndim)
+    u = np.zeros_like(f) if u0 is None else np.array(u0, dtype=np.float64, order="C", copy=True)
+    hist = np.zeros(max_cycles + 1)
+    cyc = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    status = _load().homg_oracle_solve_vcycle(ndim, n, levels, nu1, nu2, omega_j, div_factor,
+                                              _p(np.ascontiguousarray(f)), _p(u), tol, max_cycles, _p(hist),
+                                              ctypes.byref(cyc), ctypes.byref(rr))
+    if status < 0:
+        raise ValueError("oracle V-cycle solve rejected its arguments (rc=%d)" % status)
+    return u, status, cyc.value, hist[: cyc.value + 1]
 
 
 def bf16_round(x):

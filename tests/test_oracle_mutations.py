@@ -15,6 +15,7 @@ import oracle
 from oracle import oracle as oracle_impl
 
 import test_oracle_pins as pins
+import test_oracle_vcycle as vpins
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "homg_oracle.c")
 
@@ -34,6 +35,9 @@ MUTATIONS = {
     "schedule_start_count": ("int64_t nm = 2;", "int64_t nm = 1;"),
     "omega_per_dimension": ("const double omega = omega_j / (2.0 * ndim);", "const double omega = omega_j / 4.0;"),
     "update_sign": ("u[p] = u[p] + e[p];", "u[p] = u[p] - e[p];"),
+    "vcycle_no_correction": ("for (int64_t p = 0; p < cnt; ++p) em[p] = em[p] + pe[p];", ""),
+    "vcycle_prolong_lattice_value": ("if (on) Ef[p] = Ec[((k / 2) * (nc + 1) + j / 2) * (nc + 1) + i / 2];", "if (on) Ef[p] = 0.5 * Ec[((k / 2) * (nc + 1) + j / 2) * (nc + 1) + i / 2];"),
+    "vcycle_coarse_sweeps": ("int64_t sweeps = nm * nm > 1 ? nm * nm : 1;", "int64_t sweeps = 1;"),
     "norm_not_squared": ("double x = v[j * (n + 1) + i]; s += x * x;", "double x = v[j * (n + 1) + i]; s += fabs(x);"),
 }
 
@@ -56,6 +60,10 @@ def run_pins():
         ("eigen_solution3", lambda: pins.test_solution_matches_discrete_eigen_closed_form(3, 4)),
         ("dense_solve", lambda: pins.test_solution_matches_dense_direct_solve(2, 3)),
         ("decrease", lambda: pins.test_residual_decreases_every_cycle("uniform")),
+        ("v_prolong", lambda: vpins.test_prolong_reproduces_multilinear(2, 8)),
+        ("v_coarse", lambda: vpins.test_coarsest_solve_is_undamped_jacobi(2, 4)),
+        ("v_dense", lambda: vpins.test_vcycle_solution_matches_dense_direct_solve(2, 4)),
+        ("v_rate", lambda: vpins.test_vcycle_contraction_is_resolution_independent()),
     ]
     failed = []
     for name, fn in checks:
