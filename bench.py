@@ -377,6 +377,33 @@ def run(args):
                            "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
                                                       for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
 
+    # classic V(2,2) cycle on the same workload and GPU (the comparator named by the benchmark config)
+    vcyc = {}
+    for prec in ([] if args.vcycle_steps <= 0 else ["fp64", "fp32"]):
+        with homg.Solver(2, N_SIDE + 1, LEVELS, cycle="v", precision=prec) as s4:
+            s4.set_stream(stream)
+            for _ in range(3):
+                u.zero_()
+                s4.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+            sts = []
+            barrier()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for _ in range(args.vcycle_steps):
+                u.zero_()
+                st4, c4, r4 = s4.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+                if st4 != homg.HOMG_OK:
+                    raise RuntimeError("V-cycle solve did not converge")
+                sts.append(s4.stats())
+            v1.record(stream)
+            barrier()
+            vms = v0.elapsed_time(v1) / args.vcycle_steps
+            homg_ms = (elapsed_ms / args.steps) if prec == "fp64" else mixed.get("fp32", {}).get("ms_per_step")
+            vcyc[prec] = {"value": unknowns / (vms * 1e-3), "ms_per_step": vms, "cycles": c4, "final_relres": r4,
+                          "homg_ms_over_v_ms": (homg_ms / vms) if homg_ms else None,
+                          "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
+                                                     for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
     cfg3 = run_cfg3(args, homg, inputs, stream, barrier) if (args.cfg3_steps > 0 and world == 1) else None
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
@@ -424,6 +451,8 @@ def run(args):
         line["wholegrid"] = wg
     if mixed:
         line["mixed_precision"] = mixed
+    if vcyc:
+        line["vcycle_v22"] = vcyc
     if args.cfg3_steps > 0 and world == 1:
         line["cfg3_3d"] = cfg3
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -451,6 +480,7 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mixed-steps", type=int, default=3, help="timed solves per mixed-precision variant (0: skip)")
     p.add_argument("--cfg3-steps", type=int, default=2, help="timed 513^3 solves per precision and RHS (0: skip)")
+    p.add_argument("--vcycle-steps", type=int, default=3, help="timed V(2,2) comparator solves (0: skip)")
     p.add_argument("--no-cfg3-oracle-check", dest="cfg3_oracle_check", action="store_false")
     args = p.parse_args()
     if args.warmup < 3:

@@ -102,7 +102,18 @@ typedef struct homg_options {
      * restart loop is iterative refinement and reaches the same tolerance (Sec. 4 ran the method in
      * single precision). */
     int precision;
+    /* HOMG_CYCLE_HOMG (default): the paper's MFMG cycle of fused HOMG iterations.
+     * HOMG_CYCLE_V: the classic V(v_pre, v_post) cycle of Sec. 2 (steps (a)-(e): damped-Jacobi
+     * smoothing, full-weighting restriction of the residual, bilinear correction, rediscretised
+     * coarse operators; coarsest level by max(1, n_c^2) undamped Jacobi sweeps), run through the
+     * same restart loop: the comparator the paper's method is measured against. */
+    int cycle;
+    int v_pre;   /* V-cycle pre-smoothing sweeps  (0 = 2) */
+    int v_post;  /* V-cycle post-smoothing sweeps (0 = 2) */
 } homg_options;
+
+#define HOMG_CYCLE_HOMG 0
+#define HOMG_CYCLE_V 1
 
 #define HOMG_PREC_FP64 0
 #define HOMG_PREC_FP32 1

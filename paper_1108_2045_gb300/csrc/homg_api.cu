@@ -58,10 +58,12 @@ struct SolveGraph {
 constexpr int kStagesPerGraph = 12;  // even: keeps the ping-pong parity of the solution buffers
 
 struct Op {  // one kernel launch of a cycle part
-    enum Kind { ITER, PROLONG, RESTRICT, BLOCK } kind;
+    enum Kind { ITER, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD } kind;
     IterArgs it;
     ProlongArgs pr;
     RestrictArgs rs;
+    VResidArgs vr;
+    ProlongAddArgs pa;
     int block_first = 0, block_count = 0;  // BLOCK: range of the device op list
 };
 
@@ -163,11 +165,18 @@ size_t layout(homg_ctx* h, char* base) {
     const int nd = h->ndim;
     const size_t es = (size_t)prec_bytes(h->prec);
     const bool lattice = (h->exec == HOMG_EXEC_LATTICE);
+    const bool vcyc = (h->opt.cycle == HOMG_CYCLE_V);
     for (int m = 0; m < h->levels; ++m) {
         Level& lv = h->L[m];
         const size_t bytes = (size_t)grid_elems(nd, lv.n, lv.pitch) * es;
         lv.g = take(bytes);
-        if (m >= 1) {
+        if (vcyc) {
+            if (m >= 1) {
+                lv.G[0] = take(bytes);
+                lv.G[1] = take(bytes);
+            }
+            lv.d[0] = take(bytes);
+        } else if (m >= 1) {
             if (lattice) {
                 lv.G[0] = take(bytes);
                 lv.G[1] = take(bytes);
@@ -203,8 +212,79 @@ void set_weights(const homg_ctx* h, IterArgs& a) {
     a.c1_f = (float)a.c1;
 }
 
+// V(v_pre, v_post) cycle on A e = F0 from e = 0 (Sec. 2 steps (a)-(e), recursively). Part A holds
+// everything up to the level-0 post-smoothing, part B the level-0 post-smoothing sweeps.
+void plan_vcycle(homg_ctx* h) {
+    h->partA.clear();
+    h->partB.clear();
+    const int M = h->levels - 1;
+    const int nu1 = h->opt.v_pre, nu2 = h->opt.v_post;
+    std::vector<int> cur(h->levels, 0);
+    int iters = 0;
+    auto sweep = [&](int m, bool from_zero, double omega, std::vector<Op>& out) {
+        Level& lv = h->L[m];
+        Op op{};
+        op.kind = Op::ITER;
+        IterArgs& a = op.it;
+        a.e_old = from_zero ? cgrid(nullptr, lv.pitch, lv.n) : cgrid(lv.G[cur[m]], lv.pitch, lv.n);
+        a.e_new = grid(lv.G[cur[m] ^ 1], lv.pitch, lv.n);
+        a.g = cgrid(lv.g, lv.pitch, lv.n);
+        a.m = 0;
+        a.mp = -1;
+        a.omega = omega;
+        a.c1 = 1.0 - 2.0 * h->ndim * omega;
+        a.omega_f = (float)a.omega;
+        a.c1_f = (float)a.c1;
+        a.dnew = grid(nullptr, 0, 0);
+        out.push_back(op);
+        cur[m] ^= 1;
+        ++iters;
+    };
+    const double omega_c = 1.0 / (2.0 * h->ndim);
+    for (int m = 0; m < M; ++m) {
+        Level& lv = h->L[m];
+        for (int s = 0; s < nu1; ++s) sweep(m, s == 0, h->omega, h->partA);
+        Op r{};
+        r.kind = Op::VRESID;
+        r.vr.e = cgrid(lv.G[cur[m]], lv.pitch, lv.n);
+        r.vr.g = cgrid(lv.g, lv.pitch, lv.n);
+        r.vr.rho = grid(lv.d[0], lv.pitch, lv.n);
+        r.vr.omega = h->omega;
+        h->partA.push_back(r);
+        Op rs{};
+        rs.kind = Op::RESTRICT;
+        rs.rs.gf = cgrid(lv.d[0], lv.pitch, lv.n);
+        rs.rs.gc = grid(h->L[m + 1].g, h->L[m + 1].pitch, h->L[m + 1].n);
+        // fast forms keep sources as omega h^2 F; the coarsest level relaxes with omega_c
+        rs.rs.scale = (m + 1 == M) ? omega_c / h->omega : 1.0;
+        h->partA.push_back(rs);
+    }
+    {
+        const int nm = h->L[M].n;
+        const long long sweeps = std::max<long long>(1, (long long)nm * nm);
+        for (long long s = 0; s < sweeps; ++s) sweep(M, s == 0, omega_c, h->partA);
+    }
+    for (int m = M - 1; m >= 0; --m) {
+        Level& lv = h->L[m];
+        Op pa{};
+        pa.kind = Op::PROLONG_ADD;
+        pa.pa.e = grid(lv.G[cur[m]], lv.pitch, lv.n);  // written by this cycle's pre-smoothing (v_pre >= 1)
+        pa.pa.ec = cgrid(h->L[m + 1].G[cur[m + 1]], h->L[m + 1].pitch, h->L[m + 1].n);
+        h->partA.push_back(pa);
+        for (int s = 0; s < nu2; ++s) sweep(m, false, h->omega, m == 0 ? h->partB : h->partA);
+    }
+    h->e_final = cur[0];
+    h->fine_iters = (M >= 1) ? nu2 : 0;
+    h->coarse_iters = iters - h->fine_iters;
+    h->sched.assign(iters, 0);
+}
+
 // Kernel sequence of one cycle's parts A (restriction + levels >= 1) and B (level 0).
 void plan_cycle(homg_ctx* h) {
+    if (h->opt.cycle == HOMG_CYCLE_V) {
+        plan_vcycle(h);
+        return;
+    }
     h->partA.clear();
     h->partB.clear();
     const int nd = h->ndim;
@@ -214,6 +294,7 @@ void plan_cycle(homg_ctx* h) {
         op.kind = Op::RESTRICT;
         op.rs.gf = cgrid(h->L[m - 1].g, h->L[m - 1].pitch, h->L[m - 1].n);
         op.rs.gc = grid(h->L[m].g, h->L[m].pitch, h->L[m].n);
+        op.rs.scale = 1.0;
         h->partA.push_back(op);
     }
     const std::vector<int>& s = h->sched;
@@ -306,7 +387,7 @@ void plan_cycle(homg_ctx* h) {
 // block) become one single-block launch. Larger lattices run faster as separate launches.
 void group_coarse_block(homg_ctx* h) {
     h->block_ops.clear();
-    if (h->strict || h->exec != HOMG_EXEC_LATTICE) return;
+    if (h->strict || h->exec != HOMG_EXEC_LATTICE || h->opt.cycle == HOMG_CYCLE_V) return;
     const int nb = (h->ndim == 2) ? 16 : 8;
     std::vector<Op> kept;
     std::vector<BlockOp> blk;
@@ -351,6 +432,8 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
             case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
             case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
+            case Op::VRESID: e = launch_vresid(h->ndim, h->prec, h->strict, op.vr, s); break;
+            case Op::PROLONG_ADD: e = launch_prolong_add(h->ndim, h->prec, h->strict, op.pa, s); break;
             case Op::BLOCK:
                 e = launch_coarse_block(h->ndim, h->prec, h->dblock_ops + op.block_first, op.block_count, s);
                 break;
@@ -585,10 +668,14 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     if (o.omega_j == 0.0) o.omega_j = (ndim == 2) ? 4.0 / 5.0 : 6.0 / 7.0;
     if (o.max_i == 0) o.max_i = 32;
     if (o.diverge_factor == 0.0) o.diverge_factor = 1e3;
+    if (o.v_pre == 0) o.v_pre = 2;
+    if (o.v_post == 0) o.v_post = 2;
     if (!(o.omega_j > 0.0 && o.omega_j <= 2.0) || o.max_i < 1 || !(o.diverge_factor > 1.0) || o.n_schedule < 0 ||
         (o.n_schedule > 0 && !o.schedule) || o.exec_mode < 0 || o.exec_mode > 2 || (o.strict_fp != 0 && o.strict_fp != 1) ||
         (o.launch_mode != HOMG_LAUNCH_GRAPH && o.launch_mode != HOMG_LAUNCH_STREAM) ||
-        (o.precision != HOMG_PREC_FP64 && o.precision != HOMG_PREC_FP32 && o.precision != HOMG_PREC_BF16))
+        (o.precision != HOMG_PREC_FP64 && o.precision != HOMG_PREC_FP32 && o.precision != HOMG_PREC_BF16) ||
+        (o.cycle != HOMG_CYCLE_HOMG && o.cycle != HOMG_CYCLE_V) || o.v_pre < 0 || o.v_post < 0 || o.v_pre > 64 ||
+        o.v_post > 64 || (o.cycle == HOMG_CYCLE_V && (o.n_schedule > 0 || o.exec_mode == HOMG_EXEC_WHOLEGRID)))
         return fail(nullptr, HOMG_EINVAL, "homg_create: invalid options%s%s");
 
     homg_ctx* h = new (std::nothrow) homg_ctx();
@@ -617,12 +704,18 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     } else {
         h->sched = mfmg(levels, o.max_i);
     }
+    if (o.cycle == HOMG_CYCLE_V && (n >> (levels - 1)) > 64) {
+        delete h;
+        return fail(nullptr, HOMG_EINVAL,
+                    "homg_create: the V-cycle's coarsest level must have at most 64 intervals per side%s%s");
+    }
     const bool mono = schedule_monotone(h->sched);
     if (o.exec_mode == HOMG_EXEC_LATTICE && !mono) {
         delete h;
         return fail(nullptr, HOMG_EINVAL, "homg_create: the lattice form needs a schedule whose levels never increase%s%s");
     }
     h->exec = (o.exec_mode == HOMG_EXEC_WHOLEGRID || !mono) ? HOMG_EXEC_WHOLEGRID : HOMG_EXEC_LATTICE;
+    if (o.cycle == HOMG_CYCLE_V) h->exec = HOMG_EXEC_LATTICE;  // level arrays are compact by nature
 
     cudaError_t ce = cudaGetDevice(&h->device);
     if (ce != cudaSuccess) {

@@ -101,10 +101,26 @@ struct ResidArgs {
     double* part_f; // nullptr: not accumulated
 };
 
-// Full weighting g_c = 4 * FW(g_f) (the factor 4 = 2^2 keeps the source pre-scaled by h_m^2).
+// Full weighting g_c = 4 * FW(g_f) (the factor 4 = 2^2 keeps the source pre-scaled by h_m^2),
+// times `scale` in the fast forms (the V-cycle's coarsest level uses another Jacobi weight).
 struct RestrictArgs {
     CGrid gf;
     Grid gc;
+    double scale;   // 1 in strict mode
+};
+
+// V-cycle comparator: level residual rho = g - omega lap(e) (pre-scaled like g; e_old == nullptr:
+// e = 0), and prolongation-add e += P ec (bilinear from the coarser compact grid, in place).
+struct VResidArgs {
+    CGrid e;
+    CGrid g;
+    Grid rho;
+    double omega;
+};
+
+struct ProlongAddArgs {
+    Grid e;
+    CGrid ec;
 };
 
 // Convergence test (one block): sums the residual partials in a fixed order and decides.
@@ -145,6 +161,8 @@ cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a,
 int residual_blocks(int ndim, bool strict, int n);  // partial sums written by launch_residual
 cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s);
 cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, cudaStream_t s);
+cudaError_t launch_vresid(int ndim, int prec, bool strict, const VResidArgs& a, cudaStream_t s);
+cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAddArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s);
 

@@ -296,6 +296,7 @@ __device__ __forceinline__ void restrict_point(const RestrictArgs& a, int I, int
         const C corners =
             add<S>(add<S>(add<S>(F(i - 1, j - 1, 0), F(i + 1, j - 1, 0)), F(i - 1, j + 1, 0)), F(i + 1, j + 1, 0));
         v = mul<S>(add<S>(add<S>(mul<S>((C)4, c), mul<S>((C)2, edges)), corners), (C)0.25);
+        if (!S) v *= (C)a.scale;
     } else {
         const C c = F(i, j, k);
         C faces = 0, edges = 0, corners = 0;
@@ -313,6 +314,7 @@ __device__ __forceinline__ void restrict_point(const RestrictArgs& a, int I, int
                     else corners = add<S>(corners, x);
                 }
         v = mul<S>(add<S>(add<S>(add<S>(mul<S>((C)8, c), mul<S>((C)4, faces)), mul<S>((C)2, edges)), corners), (C)0.0625);
+        if (!S) v *= (C)a.scale;
     }
     wp<T>(a.gc)[at(a.gc.pitch, nc, I, J, K)] = St<T>::put(v);
 }
@@ -405,6 +407,61 @@ __global__ void __launch_bounds__(BX * BY) k_copy_out(CopyOutArgs a, int n) {
     st->u[at(n + 1, n, i, j, k)] = v;
 }
 
+
+
+// ---------------------------------------------------------------------------------------------
+// V-cycle comparator (Sec. 2, the classic two-grid correction scheme). Level residual, pre-scaled
+// like the source: strict rho = g - lap(e) = h_m^2 (F_m - A_m e); fast rho = g - omega lap(e).
+// ---------------------------------------------------------------------------------------------
+template <int ND, bool S, typename T>
+__global__ void __launch_bounds__(BX * BY) k_vresid(VResidArgs a) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    const int n = a.rho.n;
+    const int i = blockIdx.x * BX + threadIdx.x + 1;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
+    if (i >= n || j >= n) return;
+    const bool zero = (a.e.p == nullptr);
+    auto E = [&](int ii, int jj, int kk) -> C {
+        return zero ? (C)0 : St<T>::rd(cp<T>(a.e) + at(a.e.pitch, n, ii, jj, kk));
+    };
+    C lap;
+    if (ND == 2) {
+        lap = mul<S>((C)4, E(i, j, 0));
+        lap = sub<S>(lap, E(i - 1, j, 0));
+        lap = sub<S>(lap, E(i + 1, j, 0));
+        lap = sub<S>(lap, E(i, j - 1, 0));
+        lap = sub<S>(lap, E(i, j + 1, 0));
+    } else {
+        lap = mul<S>((C)6, E(i, j, k));
+        lap = sub<S>(lap, E(i - 1, j, k));
+        lap = sub<S>(lap, E(i + 1, j, k));
+        lap = sub<S>(lap, E(i, j - 1, k));
+        lap = sub<S>(lap, E(i, j + 1, k));
+        lap = sub<S>(lap, E(i, j, k - 1));
+        lap = sub<S>(lap, E(i, j, k + 1));
+    }
+    const C g = St<T>::rd(cp<T>(a.g) + at(a.g.pitch, n, i, j, k));
+    const C rho = S ? sub<S>(g, lap) : fma(-pick<C>(a.omega, (float)a.omega), lap, g);
+    wp<T>(a.rho)[at(a.rho.pitch, n, i, j, k)] = St<T>::put(rho);
+}
+
+// Prolongation-add e += P ec in place: lattice nodes add the coarse value, the others its
+// (bi/tri)linear interpolant (Sec. 2 step (d): interpolation of the coarse correction).
+template <int ND, bool S, typename T>
+__global__ void __launch_bounds__(BX * BY) k_prolong_add(ProlongAddArgs a) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    const int n = a.e.n;
+    const int i = blockIdx.x * BX + threadIdx.x + 1;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
+    if (i >= n || j >= n) return;
+    T* p = wp<T>(a.e) + at(a.e.pitch, n, i, j, k);
+    const C v = St<T>::rd(p);
+    *p = St<T>::put(add<S>(v, interp<ND, S, false, T>(a.ec, a.ec, 1, i, j, k)));
+}
 
 // ---------------------------------------------------------------------------------------------
 // Coarsest lattices in one block: the restrictions, iterations and level changes of every level
@@ -549,6 +606,58 @@ __global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
         C v = ci.at(j);
         if (!(j & 1) && !iodd) v = St<T>::ld(cp<T>(a.Gc) + (int64_t)(j >> 1) * a.Gc.pitch + (i >> 1));
         wp<T>(a.G)[(int64_t)j * a.G.pitch + i] = St<T>::put(v);
+    }
+}
+
+
+// Fast V-cycle kernels (2-D, column marching): level residual rho = g + omega (sum - 4 v) in 5
+// instructions per node, and the stride-2 prolongation-add e += P ec with the x-interpolant shared
+// down each column (lattice nodes take the coarse value itself, which ColumnInterp2 returns there).
+template <typename T>
+__global__ void __launch_bounds__(JX) k_vresid2_fast(VResidArgs a, int rows) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    const int n = a.rho.n;
+    const int i = blockIdx.x * JX + threadIdx.x + 1;
+    if (i >= n) return;
+    const int j0 = blockIdx.y * rows + 1;
+    const int j1 = min(j0 + rows, n);
+    const T* __restrict__ E = cp<T>(a.e);
+    const int64_t pe = a.e.pitch;
+    const T* __restrict__ G = cp<T>(a.g);
+    const C om = pick<C>(a.omega, (float)a.omega);
+    C vs = St<T>::ld(E + (int64_t)(j0 - 1) * pe + i);
+    C vc = St<T>::ld(E + (int64_t)j0 * pe + i);
+    for (int j = j0; j < j1; ++j) {
+        const T* row = E + (int64_t)j * pe + i;
+        const C vn = St<T>::ld(row + pe);
+        const C sum = (St<T>::ld(row - 1) + St<T>::ld(row + 1)) + (vs + vn);
+        const C g = St<T>::ld(G + (int64_t)j * a.g.pitch + i);
+        wp<T>(a.rho)[(int64_t)j * a.rho.pitch + i] = St<T>::put(fma(om, fma((C)-4, vc, sum), g));
+        vs = vc;
+        vc = vn;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(JX) k_prolong_add2_s1(ProlongAddArgs a, int rows) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    const int n = a.e.n;
+    const int i = blockIdx.x * JX + threadIdx.x + 1;
+    if (i >= n) return;
+    const int j0 = blockIdx.y * rows + 1;
+    const int j1 = min(j0 + rows, n);
+    ColumnInterp2<T> ci;
+    ci.d = cp<T>(a.ec) + (i >> 1);
+    ci.d2 = nullptr;
+    ci.pitch = a.ec.pitch;
+    ci.pitch2 = 0;
+    ci.hx = (i & 1) ? (C)0.5 : (C)0;
+    T* __restrict__ E = wp<T>(a.e);
+    for (int j = j0; j < j1; ++j) {
+        T* p = E + (int64_t)j * a.e.pitch + i;
+        *p = St<T>::put(St<T>::rd(p) + ci.at(j));
     }
 }
 
@@ -995,6 +1104,52 @@ cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs&
 cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, cudaStream_t s) {
     if (ndim == 2) { DISPATCH_PREC(prec, (launch_k(k_coarse_block<2, T>, 1, 512, s, ops, nops), cudaGetLastError())); }
     DISPATCH_PREC(prec, (launch_k(k_coarse_block<3, T>, 1, 512, s, ops, nops), cudaGetLastError()));
+}
+
+template <typename T>
+cudaError_t vresid_t(int ndim, bool strict, const VResidArgs& a, cudaStream_t s) {
+    if (!strict && ndim == 2 && a.e.p != nullptr) {
+        const int n = a.rho.n, rows = march_rows(2, n);
+        launch_k(k_vresid2_fast<T>, dim3((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows)),
+                 dim3(JX), s, a, rows);
+        return cudaGetLastError();
+    }
+    const dim3 g = grid_for(ndim, a.rho.n), b(BX, BY);
+    if (ndim == 2) {
+        if (strict) launch_k(k_vresid<2, true, T>, g, b, s, a);
+        else launch_k(k_vresid<2, false, T>, g, b, s, a);
+    } else {
+        if (strict) launch_k(k_vresid<3, true, T>, g, b, s, a);
+        else launch_k(k_vresid<3, false, T>, g, b, s, a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prolong_add_t(int ndim, bool strict, const ProlongAddArgs& a, cudaStream_t s) {
+    if (!strict && ndim == 2) {
+        const int n = a.e.n, rows = march_rows(2, n);
+        launch_k(k_prolong_add2_s1<T>, dim3((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows)),
+                 dim3(JX), s, a, rows);
+        return cudaGetLastError();
+    }
+    const dim3 g = grid_for(ndim, a.e.n), b(BX, BY);
+    if (ndim == 2) {
+        if (strict) launch_k(k_prolong_add<2, true, T>, g, b, s, a);
+        else launch_k(k_prolong_add<2, false, T>, g, b, s, a);
+    } else {
+        if (strict) launch_k(k_prolong_add<3, true, T>, g, b, s, a);
+        else launch_k(k_prolong_add<3, false, T>, g, b, s, a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vresid(int ndim, int prec, bool strict, const VResidArgs& a, cudaStream_t s) {
+    DISPATCH_PREC(prec, vresid_t<T>(ndim, strict, a, s));
+}
+
+cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAddArgs& a, cudaStream_t s) {
+    DISPATCH_PREC(prec, prolong_add_t<T>(ndim, strict, a, s));
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {

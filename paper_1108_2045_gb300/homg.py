@@ -22,6 +22,8 @@ HOMG_MAX_CYCLES = 200
 EXEC_MODES = {"auto": HOMG_EXEC_AUTO, "wholegrid": HOMG_EXEC_WHOLEGRID, "lattice": HOMG_EXEC_LATTICE}
 LAUNCH_MODES = {"graph": HOMG_LAUNCH_GRAPH, "stream": HOMG_LAUNCH_STREAM}
 PRECISIONS = {"fp64": HOMG_PREC_FP64, "fp32": HOMG_PREC_FP32, "bf16": HOMG_PREC_BF16}
+HOMG_CYCLE_HOMG, HOMG_CYCLE_V = 0, 1
+CYCLES = {"homg": HOMG_CYCLE_HOMG, "v": HOMG_CYCLE_V}
 
 # Every entry point declared in include/homg.h (checked by the symbol test).
 EXPORTS = [
@@ -50,6 +52,9 @@ class homg_options(ctypes.Structure):
         ("diverge_factor", ctypes.c_double),
         ("launch_mode", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("cycle", ctypes.c_int),
+        ("v_pre", ctypes.c_int),
+        ("v_post", ctypes.c_int),
     ]
 
 
@@ -133,7 +138,8 @@ def _check(rc, handle):
 
 
 def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, schedule=None, exec_mode="auto",
-                strict_fp=False, diverge_factor=0.0, launch_mode="graph", precision="fp64"):
+                strict_fp=False, diverge_factor=0.0, launch_mode="graph", precision="fp64", cycle="homg", v_pre=0,
+                v_post=0):
     """Create a handle for an (n_nodes)^ndim grid; returns an opaque handle (int)."""
     lib = load()
     o = homg_default_options()
@@ -144,6 +150,9 @@ def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, sche
     o.diverge_factor = diverge_factor
     o.launch_mode = LAUNCH_MODES[launch_mode] if isinstance(launch_mode, str) else int(launch_mode)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
+    o.v_pre = v_pre
+    o.v_post = v_post
     keep = None
     if schedule is not None:
         keep = (ctypes.c_int * len(schedule))(*schedule)

@@ -79,10 +79,17 @@ def test_create_rejects_unequal_sides_and_bad_options(homg):
     assert h.value is None
     for kw in [dict(omega_j=-1.0), dict(max_i=-3), dict(exec_mode=7), dict(diverge_factor=0.5),
                dict(schedule=[1, 2]), dict(schedule=[3, 0]), dict(schedule=[0, 1, 0], exec_mode="lattice"),
-               dict(launch_mode=5), dict(precision=7)]:
+               dict(launch_mode=5), dict(precision=7), dict(cycle=3), dict(cycle="v", v_pre=-1),
+               dict(cycle="v", schedule=[1, 0]), dict(cycle="v", exec_mode="wholegrid")]:
         with pytest.raises(homg.HomgError) as ei:
             homg.homg_create(2, 33, 3, **kw)
         assert ei.value.code == homg.HOMG_EINVAL, kw
+
+
+def test_vcycle_coarsest_level_limit(homg):
+    with pytest.raises(homg.HomgError) as ei:
+        homg.homg_create(2, 1025, 3, cycle="v")  # coarsest lattice 256 intervals per side
+    assert ei.value.code == homg.HOMG_EINVAL and "coarsest" in str(ei.value)
 
 
 def test_null_handle_calls_are_rejected(homg):
