@@ -216,6 +216,80 @@ def run_cfg3(args, homg, inputs, stream, barrier):
     return out
 
 
+def run_cfg4(args, homg, stream, barrier):
+    """1024 independent 2-D Poisson problems of uneven sizes in one batched solve to relres 1e-10
+    each: FP32 cycles with FP64 refinement (FP64 cycles beside it). Per-problem solve times are
+    device-clock times from a problem's initial residual test to its convergence. Sampled problems
+    (two per size) are checked with the oracle's own FP64 residual; the oracle's time for the whole
+    batch is extrapolated from one timed oracle solve per size."""
+    import numpy as np
+    import torch
+
+    from paper_1108_2045_gb300 import inputs
+
+    ks, fs_np = inputs.uneven_batch(1024, seed=1)
+    ks_arr = np.array(ks)
+    fs = [torch.from_numpy(f).cuda() for f in fs_np]
+    us = [torch.zeros_like(f) for f in fs]
+    sides = [2 ** k + 1 for k in ks]
+    unknowns = float(sum((s - 2) ** 2 for s in sides))
+    sample = [i for k in range(6, 11) for i in np.flatnonzero(ks_arr == k)[:2]]
+    out = {"workload": "1024 2-D Poisson problems, 5-point, sides 2^k+1 with k ~ U{6..10} (seed 1), f iid N(0,1), "
+                       "each to relres 1e-10, one batched solve",
+           "problems_per_k": {str(k): int((ks_arr == k).sum()) for k in range(6, 11)}, "unknowns": unknowns}
+    for prec in ("fp32", "fp64"):
+        with homg.BatchSolver(sides, precision=prec) as b:
+            b.set_stream(stream)
+            for u in us:
+                u.zero_()
+            b.solve(fs, us, tol=TOL, max_cycles=MAX_CYCLES)
+            runs = []
+            for _ in range(args.cfg4_steps):
+                for u in us:
+                    u.zero_()
+                barrier()
+                rc, status, cycles, relres, ms = b.solve(fs, us, tol=TOL, max_cycles=MAX_CYCLES)
+                runs.append((b.stats()["solve_ms"], ms, status, cycles, relres))
+            st = b.stats()
+        batch_ms = min(r[0] for r in runs)
+        per = np.array(runs[-1][1])
+        r = {"batch_ms": batch_ms, "value": unknowns / (batch_ms * 1e-3), "unit": UNIT,
+             "all_converged": all(x == 0 for x in runs[-1][2]), "max_relres": max(runs[-1][4]),
+             "cycles_min_max": [min(runs[-1][3]), max(runs[-1][3])],
+             "solve_ms_p50": float(np.percentile(per, 50)), "solve_ms_p99": float(np.percentile(per, 99)),
+             "tuned_rows_level0": dict(zip([str(x) for x in st["sides"]], st["rows"])),
+             "tuned_sweep_us_level0": dict(zip([str(x) for x in st["sides"]], st["tuned_us"]))}
+        if prec == "fp32" and args.cfg4_oracle_check:
+            import oracle
+
+            oracle.build()
+            worst = 0.0
+            for i in sample:
+                un = us[i].cpu().numpy()
+                worst = max(worst, oracle.norm_interior(oracle.residual(fs_np[i], un)) / oracle.norm_interior(fs_np[i]))
+            r["oracle_relres_max_sampled"] = worst
+            r["oracle_sample"] = "two problems per k (the first of each size in batch order)"
+        out[prec] = r
+    del fs, us
+    torch.cuda.empty_cache()
+    if args.cfg4_oracle_time and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        est, per_k = 0.0, {}
+        for k in range(6, 11):
+            i = int(np.flatnonzero(ks_arr == k)[0])
+            t0 = time.perf_counter()
+            _, status, cyc, _ = oracle.solve_mixed(fs_np[i], k, precision="fp32", tol=TOL, max_cycles=MAX_CYCLES)
+            dt = time.perf_counter() - t0
+            per_k[str(k)] = {"seconds": dt, "cycles": cyc, "status": status}
+            est += dt * int((ks_arr == k).sum())
+        out["cpu_oracle"] = {"value": unknowns / est, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one FP32-cycle oracle solve per size, timed and multiplied by the problems "
+                                       "of that size (%.0f s estimated for the batch)" % est, "per_k": per_k}
+    return out
+
+
 def run_reference(args):
     world, rank, local = dist_setup(args)
     if rank != 0:
@@ -405,6 +479,7 @@ def run(args):
                           "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
                                                      for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
     cfg3 = run_cfg3(args, homg, inputs, stream, barrier) if (args.cfg3_steps > 0 and world == 1) else None
+    cfg4 = run_cfg4(args, homg, stream, barrier) if (args.cfg4_steps > 0 and world == 1) else None
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
     launches = sum(s["cycles"] * s["fine_iterations_per_cycle"] for s in stats)
@@ -455,6 +530,8 @@ def run(args):
         line["vcycle_v22"] = vcyc
     if args.cfg3_steps > 0 and world == 1:
         line["cfg3_3d"] = cfg3
+    if cfg4:
+        line["cfg4_batched"] = cfg4
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_cpu_baseline(f_np, stats[-1]["cycles"])
     solver.close()
@@ -481,6 +558,9 @@ def main():
     p.add_argument("--mixed-steps", type=int, default=3, help="timed solves per mixed-precision variant (0: skip)")
     p.add_argument("--cfg3-steps", type=int, default=2, help="timed 513^3 solves per precision and RHS (0: skip)")
     p.add_argument("--vcycle-steps", type=int, default=3, help="timed V(2,2) comparator solves (0: skip)")
+    p.add_argument("--cfg4-steps", type=int, default=2, help="timed batched solves of the 1024-problem batch (0: skip)")
+    p.add_argument("--no-cfg4-oracle-check", dest="cfg4_oracle_check", action="store_false")
+    p.add_argument("--no-cfg4-oracle-time", dest="cfg4_oracle_time", action="store_false")
     p.add_argument("--no-cfg3-oracle-check", dest="cfg3_oracle_check", action="store_false")
     args = p.parse_args()
     if args.warmup < 3:

@@ -201,6 +201,49 @@ const char* homg_last_error(homg_handle h);
 /* Release every resource of h (no-op for NULL). */
 void homg_destroy(homg_handle h);
 
+/* ---- batched solves (many independent 2-D problems of uneven sizes) --------------------------
+ * Problems of equal size form a group whose every kernel launch advances all of the group's
+ * problems at once (problem index = third launch dimension); each problem keeps its own cycle
+ * state and stops on its own test, its blocks exiting at once after it converged. Each group's
+ * solve graph runs on its own stream, forked from the caller's stream. At creation an autotuner
+ * times the level-0 sweep of every group with each candidate tile height (nodes per thread along
+ * the march) and keeps the fastest. Fast arithmetic, lattice form and the HOMG cycle only. */
+typedef struct homg_batch_ctx* homg_batch_handle;
+
+#define HOMG_BATCH_MAX_GROUPS 16
+
+typedef struct homg_batch_stats {
+    int groups;                              /* distinct grid sizes                              */
+    double solve_ms;                         /* last solve: caller-stream events around the batch */
+    int64_t sides[HOMG_BATCH_MAX_GROUPS];    /* per group: nodes per side                        */
+    int counts[HOMG_BATCH_MAX_GROUPS];       /* per group: problems                              */
+    int rows[HOMG_BATCH_MAX_GROUPS];         /* per group: tuned nodes per thread, level-0 sweep */
+    double tuned_us[HOMG_BATCH_MAX_GROUPS];  /* per group: time of one batched level-0 sweep      */
+} homg_batch_stats;
+
+/* Create a batch of nprob 2-D problems; sides[p] = 2^K_p + 1 nodes per side (levels = K_p each).
+ * opt as for homg_create (NULL = defaults); strict_fp, the whole-grid form, explicit schedules, the
+ * V-cycle and the stream launch mode are rejected (HOMG_EINVAL). At most HOMG_BATCH_MAX_GROUPS
+ * distinct sizes. Allocates one level buffer per group and runs the autotuner (on the device). */
+int homg_batch_create(int nprob, const int64_t* sides, const homg_options* opt, homg_batch_handle* out);
+
+/* Stream of the caller (NULL = legacy default stream): the groups fork from it and join it. */
+int homg_batch_set_stream(homg_batch_handle b, void* stream);
+
+/* Solve every problem (Sec. 2 restart loop, per problem): f[p], u[p] are device pointers to the
+ * (sides[p])^2 arrays of problem p (host array of nprob pointers). Optional outputs, nprob entries
+ * each: status (HOMG_OK / HOMG_NOT_CONVERGED / HOMG_DIVERGED), cycles, final relres, and solve_ms,
+ * the device time from the problem's initial residual test to its convergence (device clock).
+ * Returns 0 when every problem converged, HOMG_NOT_CONVERGED / HOMG_DIVERGED when one did not
+ * (worst status), or a negative code. Synchronises the caller's stream. */
+int homg_batch_solve(homg_batch_handle b, const double* const* f, double* const* u, double tol, int max_cycles,
+                     int* status, int* cycles, double* relres, double* solve_ms);
+
+int homg_batch_get_stats(homg_batch_handle b, homg_batch_stats* out);
+
+/* Release every resource of b (no-op for NULL). */
+void homg_batch_destroy(homg_batch_handle b);
+
 /* Capacity of the static scratch used by homg_residual_norm_noalloc: one partial sum per thread
  * block of the residual kernel, at most this many (2-D grids up to 8193^2, 3-D up to 513^3). */
 #define HOMG_NOALLOC_MAX_BLOCKS 65536

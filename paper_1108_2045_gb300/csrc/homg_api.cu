@@ -87,6 +87,9 @@ struct homg_ctx {
     int64_t pitch0 = 0;
     std::vector<Level> L;
     int prec = PREC_FP64;     // storage precision of the cycle arrays
+    int nbatch = 1;           // problems laid out at pstride bytes from each other (batch groups)
+    size_t pstride = 0;
+    unsigned int* dticket = nullptr;  // batch finalize: arrivals, cycles run, stage base
     double* uint_[2] = {nullptr, nullptr};
     void* e[2] = {nullptr, nullptr};
     double* part_r = nullptr;
@@ -154,6 +157,8 @@ CDGrid cdgrid(const double* p, int64_t pitch, int n) { return CDGrid{p, pitch, n
 DGrid dgrid(double* p, int64_t pitch, int n) { return DGrid{p, pitch, n}; }
 
 // Lay out every array in one buffer: returns bytes needed; assigns pointers when base != nullptr.
+// The per-problem arrays form one block, repeated nbatch times pstride bytes apart (pointers refer to
+// problem 0); the cycle states, histories, coarse-lattice op list and batch counters follow.
 size_t layout(homg_ctx* h, char* base) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> void* {
@@ -197,10 +202,35 @@ size_t layout(homg_ctx* h, char* base) {
     h->L[0].G[1] = h->e[1];
     h->part_r = (double*)take((size_t)h->nparts * sizeof(double));
     h->part_f = (double*)take((size_t)h->nparts * sizeof(double));
-    h->dstate = (State*)take(sizeof(State));
-    h->dhist = (double*)take((HOMG_MAX_CYCLES + 1) * sizeof(double));
+    h->pstride = (size_t)round_up((int64_t)off, 256);
+    off = h->pstride * (size_t)h->nbatch;
+    h->dstate = (State*)take((size_t)h->nbatch * sizeof(State));
+    h->dhist = (double*)take((size_t)h->nbatch * (HOMG_MAX_CYCLES + 1) * sizeof(double));
     h->dblock_ops = (BlockOp*)take(kMaxBlockOps * sizeof(BlockOp));
+    h->dticket = (unsigned int*)take(4 * sizeof(unsigned int));
     return (size_t)round_up((int64_t)off, 256);
+}
+
+// Batch groups: give every planned array its per-problem stride and every op the problem count
+// and the per-problem states (problem z of a launch = blockIdx.z).
+void apply_batch(homg_ctx* h) {
+    if (h->nbatch <= 1) return;
+    const int64_t sl = (int64_t)(h->pstride / (size_t)prec_bytes(h->prec));
+    auto g = [&](auto& grid_) { grid_.bstride = sl; };
+    auto fix_it = [&](IterArgs& a) { g(a.e_old); g(a.e_new); g(a.g); g(a.dprev); g(a.dnew); a.nb = h->nbatch; a.bst = h->dstate; };
+    auto fix_pr = [&](ProlongArgs& a) { g(a.G); g(a.Gc); g(a.dl); a.nb = h->nbatch; a.bst = h->dstate; };
+    auto fix_rs = [&](RestrictArgs& a) { g(a.gf); g(a.gc); a.nb = h->nbatch; a.bst = h->dstate; };
+    for (auto* part : {&h->partA, &h->partB})
+        for (Op& op : *part) {
+            if (op.kind == Op::ITER) fix_it(op.it);
+            else if (op.kind == Op::PROLONG) fix_pr(op.pr);
+            else if (op.kind == Op::RESTRICT) fix_rs(op.rs);
+        }
+    for (BlockOp& b : h->block_ops) {
+        if (b.kind == BLOCK_ITER) fix_it(b.it);
+        else if (b.kind == BLOCK_PROLONG) fix_pr(b.pr);
+        else fix_rs(b.rs);
+    }
 }
 
 // Damped-Jacobi scalars of an iteration, computed once on the host (binary32 copies for the
@@ -435,7 +465,7 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
             case Op::VRESID: e = launch_vresid(h->ndim, h->prec, h->strict, op.vr, s); break;
             case Op::PROLONG_ADD: e = launch_prolong_add(h->ndim, h->prec, h->strict, op.pa, s); break;
             case Op::BLOCK:
-                e = launch_coarse_block(h->ndim, h->prec, h->dblock_ops + op.block_first, op.block_count, s);
+                e = launch_coarse_block(h->ndim, h->prec, h->dblock_ops + op.block_first, op.block_count, h->nbatch, s);
                 break;
         }
         if (e != cudaSuccess) return e;
@@ -462,7 +492,30 @@ ResidArgs resid_args(homg_ctx* h, int stage) {
         a.e = cgrid(h->e[h->e_final], h->pitch0, h->n);
         a.u_out = dgrid(h->uint_[stage & 1], h->pitch0, h->n);
     }
+    if (h->nbatch > 1) {
+        const int64_t s64 = (int64_t)(h->pstride / sizeof(double)), slp = (int64_t)(h->pstride / prec_bytes(h->prec));
+        a.batch = 1;
+        a.nb = h->nbatch;
+        a.u_in.bstride = s64;
+        a.u_out.bstride = s64;
+        a.e.bstride = slp;
+        a.g0.bstride = slp;
+        a.part_bstride = s64;
+    }
     return a;
+}
+
+CopyOutArgs copy_args(homg_ctx* h) {
+    CopyOutArgs c{};
+    c.st = h->dstate;
+    c.u0 = cdgrid(h->uint_[0], h->pitch0, h->n);
+    c.u1 = cdgrid(h->uint_[1], h->pitch0, h->n);
+    if (h->nbatch > 1) {
+        c.batch = 1;
+        c.nb = h->nbatch;
+        c.u0.bstride = c.u1.bstride = (int64_t)(h->pstride / sizeof(double));
+    }
+    return c;
 }
 
 FinalizeArgs fin_args(homg_ctx* h, int mode, const SolveGraph* g) {
@@ -475,6 +528,12 @@ FinalizeArgs fin_args(homg_ctx* h, int mode, const SolveGraph* g) {
     f.mode = mode;
     f.handles = g ? g->dhandles : nullptr;
     f.nstages = g ? g->stages : 0;
+    if (h->nbatch > 1) {
+        f.batch = h->nbatch;
+        f.hist_bstride = HOMG_MAX_CYCLES + 1;
+        f.part_bstride = (int64_t)(h->pstride / sizeof(double));
+        f.ticket = h->dticket;
+    }
     return f;
 }
 
@@ -584,13 +643,7 @@ int build_graph(homg_ctx* h, SolveGraph& G, int stages, bool with_init) {
         if (e == cudaSuccess) e = add_event(3 * k + 1);
     }
     if (e == cudaSuccess)
-        e = add_seq([&](cudaStream_t s) -> cudaError_t {
-            CopyOutArgs c{};
-            c.st = h->dstate;
-            c.u0 = cdgrid(h->uint_[0], h->pitch0, h->n);
-            c.u1 = cdgrid(h->uint_[1], h->pitch0, h->n);
-            return launch_copy_out(h->ndim, c, h->n, s);
-        });
+        e = add_seq([&](cudaStream_t s) -> cudaError_t { return launch_copy_out(h->ndim, copy_args(h), h->n, s); });
     if (e == cudaSuccess) e = add_event(3 * stages + 2);
     if (e == cudaSuccess)
         e = cudaMemcpy(G.dhandles, handles.data(), handles.size() * sizeof(handles[0]), cudaMemcpyHostToDevice);
@@ -645,26 +698,30 @@ void homg_default_options(homg_options* opt) {
     opt->diverge_factor = 1e3;
 }
 
-int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const homg_options* opt, homg_handle* out) {
-    if (out) *out = nullptr;
-    g_create_error[0] = 0;
-    if (!out || !dims) return fail(nullptr, HOMG_EINVAL, "homg_create: null %s%s", !out ? "out" : "dims");
-    if (ndim != 2 && ndim != 3) return fail(nullptr, HOMG_EINVAL, "homg_create: ndim must be 2 or 3%s%s");
-    if ((ndim == 2 && stencil != 5) || (ndim == 3 && stencil != 7))
-        return fail(nullptr, HOMG_EINVAL, "homg_create: stencil must be 5 (2-D) or 7 (3-D)%s%s");
-    for (int d = 1; d < ndim; ++d)
-        if (dims[d] != dims[0]) return fail(nullptr, HOMG_ESHAPE, "homg_create: grid sides must be equal%s%s");
-    const int64_t n = dims[0] - 1;
+}  // extern "C"
+
+namespace {
+
+// Grid side n + 1 = 2^K + 1 with K >= 1 and within the maximum; returns K or a negative code.
+int grid_exponent(int ndim, int64_t side, const char* who) {
+    const int64_t n = side - 1;
     int K = 0;
     while (K < 62 && ((int64_t)1 << K) < n) ++K;
-    if (n < 2 || ((int64_t)1 << K) != n)
-        return fail(nullptr, HOMG_ESHAPE, "homg_create: grid side must be 2^K + 1 with K >= 1%s%s");
-    if (K > (ndim == 2 ? HOMG_MAX_K_2D : HOMG_MAX_K_3D))
-        return fail(nullptr, HOMG_ESHAPE, "homg_create: grid side above the supported maximum%s%s");
-    if (levels < 1 || levels > K) return fail(nullptr, HOMG_EINVAL, "homg_create: levels must be in [1, K]%s%s");
-    homg_options o;
-    homg_default_options(&o);
-    if (opt) o = *opt;
+    if (n < 2 || ((int64_t)1 << K) != n) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "%s: grid side must be 2^K + 1 with K >= 1", who);
+        return fail(nullptr, HOMG_ESHAPE, "%s%s", msg);
+    }
+    if (K > (ndim == 2 ? HOMG_MAX_K_2D : HOMG_MAX_K_3D)) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "%s: grid side above the supported maximum", who);
+        return fail(nullptr, HOMG_ESHAPE, "%s%s", msg);
+    }
+    return K;
+}
+
+// Defaults and validation of the options (shared by the single and batch entry points).
+int check_options(int ndim, homg_options& o) {
     if (o.omega_j == 0.0) o.omega_j = (ndim == 2) ? 4.0 / 5.0 : 6.0 / 7.0;
     if (o.max_i == 0) o.max_i = 32;
     if (o.diverge_factor == 0.0) o.diverge_factor = 1e3;
@@ -677,7 +734,12 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
         (o.cycle != HOMG_CYCLE_HOMG && o.cycle != HOMG_CYCLE_V) || o.v_pre < 0 || o.v_post < 0 || o.v_pre > 64 ||
         o.v_post > 64 || (o.cycle == HOMG_CYCLE_V && (o.n_schedule > 0 || o.exec_mode == HOMG_EXEC_WHOLEGRID)))
         return fail(nullptr, HOMG_EINVAL, "homg_create: invalid options%s%s");
+    return HOMG_OK;
+}
 
+// Build a solver context for nbatch equal-size problems (nbatch = 1: the single-problem handle).
+int create_ctx(int ndim, int64_t n, int K, int levels, int stencil, const homg_options& o, int nbatch, homg_ctx** out) {
+    *out = nullptr;
     homg_ctx* h = new (std::nothrow) homg_ctx();
     if (!h) return fail(nullptr, HOMG_ENOMEM, "homg_create: out of host memory%s%s");
     h->ndim = ndim;
@@ -688,6 +750,7 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     h->opt = o;
     h->strict = (o.strict_fp == 1);
     h->prec = o.precision;
+    h->nbatch = nbatch;
     h->omega = o.omega_j / (2.0 * ndim);
     if (o.n_schedule > 0) {
         h->sched.assign(o.schedule, o.schedule + o.n_schedule);
@@ -733,7 +796,7 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     h->arena_bytes = layout(h, nullptr);
     ce = cudaMalloc(&h->arena, h->arena_bytes);
     if (ce == cudaSuccess) ce = cudaMemset(h->arena, 0, h->arena_bytes);
-    if (ce == cudaSuccess) ce = cudaMallocHost(&h->hstate, sizeof(State));
+    if (ce == cudaSuccess) ce = cudaMallocHost(&h->hstate, (size_t)nbatch * sizeof(State));
     if (ce == cudaSuccess) ce = cudaMallocHost(&h->hhist, (HOMG_MAX_CYCLES + 1) * sizeof(double));
     if (ce != cudaSuccess) {
         int rc = cuda_fail(nullptr, ce, "allocating the level buffer");
@@ -743,6 +806,7 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     layout(h, h->arena);
     plan_cycle(h);
     group_coarse_block(h);
+    apply_batch(h);
     if (!h->block_ops.empty()) {
         ce = cudaMemcpy(h->dblock_ops, h->block_ops.data(), h->block_ops.size() * sizeof(BlockOp), cudaMemcpyHostToDevice);
         if (ce != cudaSuccess) {
@@ -753,6 +817,321 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     }
     *out = h;
     return HOMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const homg_options* opt, homg_handle* out) {
+    if (out) *out = nullptr;
+    g_create_error[0] = 0;
+    if (!out || !dims) return fail(nullptr, HOMG_EINVAL, "homg_create: null %s%s", !out ? "out" : "dims");
+    if (ndim != 2 && ndim != 3) return fail(nullptr, HOMG_EINVAL, "homg_create: ndim must be 2 or 3%s%s");
+    if ((ndim == 2 && stencil != 5) || (ndim == 3 && stencil != 7))
+        return fail(nullptr, HOMG_EINVAL, "homg_create: stencil must be 5 (2-D) or 7 (3-D)%s%s");
+    for (int d = 1; d < ndim; ++d)
+        if (dims[d] != dims[0]) return fail(nullptr, HOMG_ESHAPE, "homg_create: grid sides must be equal%s%s");
+    const int K = grid_exponent(ndim, dims[0], "homg_create");
+    if (K < 0) return K;
+    if (levels < 1 || levels > K) return fail(nullptr, HOMG_EINVAL, "homg_create: levels must be in [1, K]%s%s");
+    homg_options o;
+    homg_default_options(&o);
+    if (opt) o = *opt;
+    int rc = check_options(ndim, o);
+    if (rc != HOMG_OK) return rc;
+    homg_ctx* h = nullptr;
+    rc = create_ctx(ndim, dims[0] - 1, K, levels, stencil, o, 1, &h);
+    if (rc == HOMG_OK) *out = h;
+    return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batched solves
+// ---------------------------------------------------------------------------------------------
+struct homg_batch_ctx {
+    int nprob = 0;
+    std::vector<int> group_of, index_in_group;
+    std::vector<homg_ctx*> groups;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaStream_t stream = nullptr;
+    homg_batch_stats stats{};
+    unsigned int* hticket = nullptr;  // pinned, 4 per group: ticket counters read back after each launch
+};
+
+namespace {
+
+// Autotuner: for every lattice size the group sweeps with the marching Jacobi kernel, time the
+// plain sweep (all problems at once) for each candidate number of nodes per thread along the
+// march, keep the fastest, and use it for every sweep of that size. Reports the level-0 choice.
+int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us) {
+    *best_rows = 0;
+    *best_us = 0.0;
+    std::vector<const Op*> tmpl;
+    for (auto* part : {&h->partA, &h->partB})
+        for (const Op& op : *part) {
+            if (op.kind != Op::ITER || !op.it.e_old.p || op.it.m != 0) continue;
+            bool seen = false;
+            for (const Op* t : tmpl) seen |= t->it.e_new.n == op.it.e_new.n;
+            if (!seen) tmpl.push_back(&op);
+        }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(h, cudaEventCreate(&e0), "cudaEventCreate");
+    CK(h, cudaEventCreate(&e1), "cudaEventCreate");
+    for (const Op* t : tmpl) {
+        IterArgs a = t->it;
+        a.mp = -1;
+        a.dnew = Grid{nullptr, 0, 0};
+        const int n = a.e_new.n;
+        double best = 1e30;
+        int pick = 0;
+        for (int rows : {1, 2, 4, 8, 16, 32}) {
+            if (rows > n - 1) break;
+            a.rows = rows;
+            cudaError_t e = launch_iterate(h->ndim, h->prec, false, a, st);  // warm-up
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                if (r == 0) e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess) e = launch_iterate(h->ndim, h->prec, false, a, st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(h, e, "autotuning the sweep");
+            }
+            const double us = 1e3 * ms / 3.0;
+            if (us < best) { best = us; pick = rows; }
+        }
+        for (auto* part : {&h->partA, &h->partB})
+            for (Op& op : *part)
+                if (op.kind == Op::ITER && op.it.m == 0 && op.it.e_new.n == n) op.it.rows = pick;
+        if (n == h->n) {
+            *best_rows = pick;
+            *best_us = best;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return HOMG_OK;
+}
+
+void batch_destroy(homg_batch_ctx* b) {
+    for (homg_ctx* h : b->groups) homg_destroy(h);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->hticket) cudaFreeHost(b->hticket);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int homg_batch_create(int nprob, const int64_t* sides, const homg_options* opt, homg_batch_handle* out) {
+    if (out) *out = nullptr;
+    g_create_error[0] = 0;
+    if (!out || !sides || nprob < 1) return fail(nullptr, HOMG_EINVAL, "homg_batch_create: null argument or no problems%s%s");
+    homg_options o;
+    homg_default_options(&o);
+    if (opt) o = *opt;
+    int rc = check_options(2, o);
+    if (rc != HOMG_OK) return rc;
+    if (o.strict_fp || o.exec_mode == HOMG_EXEC_WHOLEGRID || o.n_schedule > 0 || o.cycle != HOMG_CYCLE_HOMG ||
+        o.launch_mode != HOMG_LAUNCH_GRAPH)
+        return fail(nullptr, HOMG_EINVAL,
+                    "homg_batch_create: batches use fast arithmetic, the lattice form, MFMG and graph launches%s%s");
+    std::vector<int64_t> distinct;
+    std::vector<int> group_of(nprob), index_in_group(nprob);
+    std::vector<int> counts;
+    for (int p = 0; p < nprob; ++p) {
+        if (grid_exponent(2, sides[p], "homg_batch_create") < 0) return HOMG_ESHAPE;
+        size_t g = 0;
+        while (g < distinct.size() && distinct[g] != sides[p]) ++g;
+        if (g == distinct.size()) {
+            if ((int)distinct.size() == HOMG_BATCH_MAX_GROUPS)
+                return fail(nullptr, HOMG_EINVAL, "homg_batch_create: more than HOMG_BATCH_MAX_GROUPS sizes%s%s");
+            distinct.push_back(sides[p]);
+            counts.push_back(0);
+        }
+        group_of[p] = (int)g;
+        index_in_group[p] = counts[g]++;
+    }
+    homg_batch_ctx* b = new (std::nothrow) homg_batch_ctx();
+    if (!b) return fail(nullptr, HOMG_ENOMEM, "homg_batch_create: out of host memory%s%s");
+    b->nprob = nprob;
+    b->group_of = group_of;
+    b->index_in_group = index_in_group;
+    cudaError_t ce = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&b->t0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&b->t1);
+    if (ce == cudaSuccess) ce = cudaMallocHost(&b->hticket, 4 * HOMG_BATCH_MAX_GROUPS * sizeof(unsigned int));
+    if (ce != cudaSuccess) {
+        rc = cuda_fail(nullptr, ce, "homg_batch_create");
+        batch_destroy(b);
+        return rc;
+    }
+    b->stats.groups = (int)distinct.size();
+    for (size_t g = 0; g < distinct.size(); ++g) {
+        const int K = grid_exponent(2, distinct[g], "homg_batch_create");
+        homg_ctx* h = nullptr;
+        rc = create_ctx(2, distinct[g] - 1, K, K, 5, o, counts[g], &h);
+        if (rc != HOMG_OK) {
+            batch_destroy(b);
+            return rc;
+        }
+        b->groups.push_back(h);
+        cudaStream_t s = nullptr;
+        cudaEvent_t j = nullptr;
+        ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(nullptr, ce, "homg_batch_create: streams");
+            batch_destroy(b);
+            return rc;
+        }
+        b->streams.push_back(s);
+        b->joins.push_back(j);
+        h->stream = s;
+        int rows = 0;
+        double us = 0.0;
+        rc = autotune_rows(h, s, &rows, &us);
+        if (rc != HOMG_OK) {
+            set_null_handle_error(h->err);
+            batch_destroy(b);
+            return rc;
+        }
+        b->stats.sides[g] = distinct[g];
+        b->stats.counts[g] = counts[g];
+        b->stats.rows[g] = rows;
+        b->stats.tuned_us[g] = us;
+    }
+    *out = b;
+    return HOMG_OK;
+}
+
+int homg_batch_set_stream(homg_batch_handle b, void* stream) {
+    if (!b) return HOMG_EINVAL;
+    b->stream = (cudaStream_t)stream;
+    return HOMG_OK;
+}
+
+int homg_batch_solve(homg_batch_handle b, const double* const* f, double* const* u, double tol, int max_cycles,
+                     int* status, int* cycles, double* relres, double* solve_ms) {
+    if (!b) return HOMG_EINVAL;
+    if (!f || !u) return fail(nullptr, HOMG_EINVAL, "homg_batch_solve: null %s%s", !f ? "f" : "u");
+    if (!(tol >= 0.0) || !std::isfinite(tol) || max_cycles < 0 || max_cycles > HOMG_MAX_CYCLES)
+        return fail(nullptr, HOMG_EINVAL, "homg_batch_solve: invalid tol or max_cycles%s%s");
+    for (int p = 0; p < b->nprob; ++p)
+        if (!f[p] || !u[p]) return fail(nullptr, HOMG_EINVAL, "homg_batch_solve: null problem array%s%s");
+    const int G = (int)b->groups.size();
+    auto cfail = [&](cudaError_t e, const char* where) { return cuda_fail(nullptr, e, where); };
+    cudaError_t e = cudaEventRecord(b->t0, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+    if (e != cudaSuccess) return cfail(e, "homg_batch_solve");
+    const int want = std::min(std::max(max_cycles, 1), kStagesPerGraph);
+    for (int g = 0; g < G; ++g) {
+        homg_ctx* h = b->groups[g];
+        for (int q = 0; q < h->nbatch; ++q) memset(&h->hstate[q], 0, sizeof(State));
+        for (int p = 0; p < b->nprob; ++p) {
+            if (b->group_of[p] != g) continue;
+            State& st = h->hstate[b->index_in_group[p]];
+            st.f = f[p];
+            st.u = u[p];
+            st.tol = tol;
+            st.div_factor = h->opt.diverge_factor;
+            st.max_cycles = max_cycles;
+            st.status = -1;
+        }
+        if (!h->gfirst.exec || h->gfirst.stages < want) {
+            int rc = build_graph(h, h->gfirst, want, true);
+            if (rc != HOMG_OK) {
+                set_null_handle_error(h->err);
+                return rc;
+            }
+        }
+        cudaStream_t s = b->streams[g];
+        e = cudaStreamWaitEvent(s, b->fork, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstate, h->hstate, (size_t)h->nbatch * sizeof(State), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->dticket, 0, 4 * sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaGraphLaunch(h->gfirst.exec, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->hstate, h->dstate, (size_t)h->nbatch * sizeof(State), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->hticket + 4 * g, h->dticket, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cfail(e, "homg_batch_solve: launching a group");
+    }
+    // Continuation launches while problems of a group still run and cycles remain. Each pass
+    // waits for one group at a time but re-launches it before moving on, so groups never wait
+    // for one another.
+    std::vector<int> pending;
+    for (int g = 0; g < G; ++g) pending.push_back(g);
+    while (!pending.empty()) {
+        std::vector<int> still;
+        for (int g : pending) {
+            homg_ctx* h = b->groups[g];
+            cudaStream_t s = b->streams[g];
+            unsigned int* tk = b->hticket + 4 * g;
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cfail(e, "homg_batch_solve");
+            int running = 0;
+            for (int q = 0; q < h->nbatch; ++q) running |= !h->hstate[q].done;
+            const int done_cycles = (int)tk[1];
+            if (!running || done_cycles >= max_cycles) {
+                e = cudaEventRecord(b->joins[g], s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[g], 0);
+                if (e != cudaSuccess) return cfail(e, "homg_batch_solve");
+                continue;
+            }
+            if (!h->gcont.exec) {
+                int rc = build_graph(h, h->gcont, kStagesPerGraph, false);
+                if (rc != HOMG_OK) {
+                    set_null_handle_error(h->err);
+                    return rc;
+                }
+            }
+            tk[2] = (unsigned int)done_cycles;
+            e = cudaMemcpyAsync(h->dticket + 2, tk + 2, sizeof(unsigned int), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaGraphLaunch(h->gcont.exec, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->hstate, h->dstate, (size_t)h->nbatch * sizeof(State), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tk, h->dticket, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return cfail(e, "homg_batch_solve: continuation");
+            still.push_back(g);
+        }
+        pending.swap(still);
+    }
+    e = cudaEventRecord(b->t1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b->t1);
+    if (e != cudaSuccess) return cfail(e, "homg_batch_solve");
+    b->stats.solve_ms = elapsed(b->t0, b->t1);
+    int worst = HOMG_OK;
+    for (int p = 0; p < b->nprob; ++p) {
+        const State& st = b->groups[b->group_of[p]]->hstate[b->index_in_group[p]];
+        if (status) status[p] = st.status;
+        if (cycles) cycles[p] = st.cycle;
+        if (relres) relres[p] = st.relres;
+        if (solve_ms) solve_ms[p] = 1e-6 * (double)(st.t_done - st.t_start);
+        if (st.status > worst) worst = st.status;
+    }
+    return worst;
+}
+
+int homg_batch_get_stats(homg_batch_handle b, homg_batch_stats* out) {
+    if (!b || !out) return HOMG_EINVAL;
+    *out = b->stats;
+    return HOMG_OK;
+}
+
+void homg_batch_destroy(homg_batch_handle b) {
+    if (!b) return;
+    batch_destroy(b);
 }
 
 int homg_set_stream(homg_handle h, void* stream) {
@@ -837,11 +1216,7 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
             CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
             CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
         }
-        CopyOutArgs c{};
-        c.st = h->dstate;
-        c.u0 = cdgrid(h->uint_[0], h->pitch0, h->n);
-        c.u1 = cdgrid(h->uint_[1], h->pitch0, h->n);
-        CK(h, launch_copy_out(h->ndim, c, h->n, sm), "copy-out kernel");
+        CK(h, launch_copy_out(h->ndim, copy_args(h), h->n, sm), "copy-out kernel");
         const int end_ev = 3 * s->cycle + 2;
         CK(h, cudaEventRecord(h->sev[end_ev], sm), "cudaEventRecord");
         CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");

@@ -26,6 +26,8 @@ struct State {
     int status;        // -1 running, else HOMG_OK / HOMG_NOT_CONVERGED / HOMG_DIVERGED
     int done;
     int zero_u;        // ||f|| == 0: the solution is u = 0
+    long long t_start; // batch solves: device clock (ns) at the initial test and at convergence
+    long long t_done;
     double fnorm;
     double rr0;
     double relres;
@@ -37,12 +39,14 @@ struct Grid {
     void* p;
     int64_t pitch;
     int n;
+    int64_t bstride = 0;  // elements between consecutive problems of a batch (0: one problem)
 };
 
 struct CGrid {
     const void* p;
     int64_t pitch;
     int n;
+    int64_t bstride = 0;  // elements between consecutive problems of a batch (0: one problem)
 };
 
 // An FP64 grid (solution iterates).
@@ -50,12 +54,14 @@ struct DGrid {
     double* p;
     int64_t pitch;
     int n;
+    int64_t bstride = 0;  // elements between consecutive problems of a batch (0: one problem)
 };
 
 struct CDGrid {
     const double* p;
     int64_t pitch;
     int n;
+    int64_t bstride = 0;  // elements between consecutive problems of a batch (0: one problem)
 };
 
 // One HOMG iteration on a grid of n intervals per side (the fine grid in the whole-grid form, a
@@ -63,6 +69,8 @@ struct CDGrid {
 //   relax the stride-2^m lattice (source g, compact, one value per lattice node),
 //   add the interpolation of the pending variation dprev (compact at stride 2^mp) off its lattice.
 struct IterArgs {
+    int nb = 1;                  // problems in the batch (launch z extent, 2-D only)
+    const State* bst = nullptr;  // batch: per-problem states (problem z = blockIdx.z); nullptr: one problem
     CGrid e_old;    // p == nullptr: e_old = 0
     Grid e_new;
     CGrid g;        // compact level-m source, pre-scaled: h_m^2 F_m (strict) or omega h_m^2 F_m
@@ -72,6 +80,7 @@ struct IterArgs {
     Grid dnew;      // compact variation output (p == nullptr: not stored)
     double omega;   // damped-Jacobi weight omega_J / (2d)
     double c1;      // 1 - 2d omega (fast forms)
+    int rows = 0;   // fast 2-D/3-D kernels: nodes per thread along the march (0: size heuristic)
     float omega_f;  // the same, rounded to binary32, for the binary32-arithmetic kernels
     float c1_f;
 };
@@ -81,6 +90,8 @@ struct IterArgs {
 // get the interpolant of (Gc - dl), the value the whole-grid iterate holds there before the
 // delayed interpolation of dl is applied.
 struct ProlongArgs {
+    int nb = 1;                  // problems in the batch (launch z extent, 2-D only)
+    const State* bst = nullptr;  // batch: per-problem states (problem z = blockIdx.z); nullptr: one problem
     Grid G;
     CGrid Gc;
     CGrid dl;
@@ -99,11 +110,16 @@ struct ResidArgs {
     double inv_h2;
     double* part_r;
     double* part_f; // nullptr: not accumulated
+    int64_t part_bstride = 0;  // batch: partials between consecutive problems
+    int batch = 0;             // batch: st points at per-problem states, problem z = blockIdx.z
+    int nb = 1;
 };
 
 // Full weighting g_c = 4 * FW(g_f) (the factor 4 = 2^2 keeps the source pre-scaled by h_m^2),
 // times `scale` in the fast forms (the V-cycle's coarsest level uses another Jacobi weight).
 struct RestrictArgs {
+    int nb = 1;                  // problems in the batch (launch z extent, 2-D only)
+    const State* bst = nullptr;  // batch: per-problem states (problem z = blockIdx.z); nullptr: one problem
     CGrid gf;
     Grid gc;
     double scale;   // 1 in strict mode
@@ -135,10 +151,18 @@ struct FinalizeArgs {
     int mode;
     const cudaGraphConditionalHandle* handles;  // 3 per stage, stage k at [3k, 3k+3)
     int nstages;
+    // batch (one block per problem): hist, partials and states advance by these strides;
+    // `ticket` counts finished blocks so the last one decides whether the next stage runs.
+    int batch = 0;
+    int64_t hist_bstride = 0;
+    int64_t part_bstride = 0;
+    unsigned int* ticket = nullptr;
 };
 
 struct CopyOutArgs {
     State* st;
+    int batch = 0;  // st points at per-problem states, problem z = blockIdx.z
+    int nb = 1;
     CDGrid u0;   // internal iterate after an even number of cycles
     CDGrid u1;   // ... after an odd number
 };
@@ -160,7 +184,7 @@ cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a
 cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a, int n, cudaStream_t s);
 int residual_blocks(int ndim, bool strict, int n);  // partial sums written by launch_residual
 cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s);
-cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, cudaStream_t s);
+cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, int nb, cudaStream_t s);
 cudaError_t launch_vresid(int ndim, int prec, bool strict, const VResidArgs& a, cudaStream_t s);
 cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAddArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);

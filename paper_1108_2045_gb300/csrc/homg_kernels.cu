@@ -79,6 +79,51 @@ __device__ __forceinline__ void pdl_begin() {
 template <typename T> __device__ __forceinline__ const T* cp(const CGrid& g) { return static_cast<const T*>(g.p); }
 template <typename T> __device__ __forceinline__ T* wp(const Grid& g) { return static_cast<T*>(g.p); }
 
+// ---- batches of equal-size 2-D problems: problem z = blockIdx.z, arrays z * bstride apart ------
+template <typename T> __device__ __forceinline__ void shift(CGrid& g, int z) {
+    if (g.p) g.p = static_cast<const T*>(g.p) + (int64_t)z * g.bstride;
+}
+template <typename T> __device__ __forceinline__ void shift(Grid& g, int z) {
+    if (g.p) g.p = static_cast<T*>(g.p) + (int64_t)z * g.bstride;
+}
+__device__ __forceinline__ void shift(CDGrid& g, int z) { if (g.p) g.p += (int64_t)z * g.bstride; }
+__device__ __forceinline__ void shift(DGrid& g, int z) { if (g.p) g.p += (int64_t)z * g.bstride; }
+
+// Move the arguments to this block's problem; false when that problem has already finished.
+template <typename T> __device__ __forceinline__ bool batch_view(IterArgs& a, int z) {
+    if (!a.bst) return true;
+    if (a.bst[z].done) return false;
+    shift<T>(a.e_old, z); shift<T>(a.e_new, z); shift<T>(a.g, z); shift<T>(a.dprev, z); shift<T>(a.dnew, z);
+    return true;
+}
+template <typename T> __device__ __forceinline__ bool batch_view(ProlongArgs& a, int z) {
+    if (!a.bst) return true;
+    if (a.bst[z].done) return false;
+    shift<T>(a.G, z); shift<T>(a.Gc, z); shift<T>(a.dl, z);
+    return true;
+}
+template <typename T> __device__ __forceinline__ bool batch_view(RestrictArgs& a, int z) {
+    if (!a.bst) return true;
+    if (a.bst[z].done) return false;
+    shift<T>(a.gf, z); shift<T>(a.gc, z);
+    return true;
+}
+template <typename T> __device__ __forceinline__ bool batch_view(ResidArgs& a, int z) {
+    if (!a.batch) return true;
+    a.st += z;
+    if (a.st->done) return false;
+    shift(a.u_in, z); shift<T>(a.e, z); shift(a.u_out, z); shift<T>(a.g0, z);
+    a.part_r += (int64_t)z * a.part_bstride;
+    if (a.part_f) a.part_f += (int64_t)z * a.part_bstride;
+    return true;
+}
+
+__device__ __forceinline__ long long device_clock_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Value at (i, j[, k]) of the (bi/tri)linear interpolant of compact array d at stride 2^mp
 // (Sec. 2: linear interpolation S; exact dyadic weights). Summation order as in the oracle:
 // 2-D (w00 d00 + w10 d10) + (w01 d01 + w11 d11); 3-D x-pairs, then y, then z.
@@ -171,6 +216,7 @@ __device__ __forceinline__ void iterate_point(const IterArgs& a, int i, int j, i
 template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_iterate(IterArgs a) {
     pdl_begin();
+    if (ND == 2 && !batch_view<T>(a, blockIdx.z)) return;
     const int n = a.e_new.n;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -198,6 +244,7 @@ __device__ __forceinline__ void prolong_point(const ProlongArgs& a, int i, int j
 template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_prolong(ProlongArgs a) {
     pdl_begin();
+    if (ND == 2 && !batch_view<T>(a, blockIdx.z)) return;
     const int n = a.G.n;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -322,6 +369,7 @@ __device__ __forceinline__ void restrict_point(const RestrictArgs& a, int I, int
 template <int ND, bool S, typename T>
 __global__ void __launch_bounds__(BX * BY) k_restrict(RestrictArgs a) {
     pdl_begin();
+    if (ND == 2 && !batch_view<T>(a, blockIdx.z)) return;
     const int nc = a.gc.n;
     const int I = blockIdx.x * BX + threadIdx.x + 1;
     const int J = blockIdx.y * BY + threadIdx.y + 1;
@@ -335,18 +383,9 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(RestrictArgs a) {
 // One block; partial sums are added in a fixed order so the decision is reproducible. Enables the
 // next cycle's conditional graph nodes while the solve continues.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_finalize(FinalizeArgs a) {
-    pdl_begin();
-    __shared__ double sh[32];
-    double sr = 0.0, sf = 0.0;
-    for (int t = threadIdx.x; t < a.nparts; t += blockDim.x) {
-        sr += a.part_r[t];
-        if (a.part_f) sf += a.part_f[t];
-    }
-    sr = block_sum(sr, sh);
-    if (a.part_f) sf = block_sum(sf, sh);
-    if (threadIdx.x != 0) return;
-    State* st = a.st;
+// Convergence decision for one problem (thread 0): relres, history, status, done; in single-problem
+// graphs also enables the next stage's conditional nodes.
+__device__ void finalize_decide(const FinalizeArgs& a, State* st, double* hist, double sr, double sf) {
     const double rn = sqrt(sr);
     if (a.mode == FIN_NORM) {
         const double fn = sqrt(sf);
@@ -360,12 +399,14 @@ __global__ void __launch_bounds__(1024) k_finalize(FinalizeArgs a) {
         const double fn = sqrt(sf);
         st->fnorm = fn;
         st->cycle = 0;
+        st->t_start = device_clock_ns();
         if (fn == 0.0) {
             st->zero_u = 1;
             st->relres = 0.0;
             st->status = HOMG_OK;
             st->done = 1;
-            a.hist[0] = 0.0;
+            st->t_done = st->t_start;
+            hist[0] = 0.0;
             return;
         }
         st->zero_u = 0;
@@ -376,7 +417,7 @@ __global__ void __launch_bounds__(1024) k_finalize(FinalizeArgs a) {
         k = ++st->cycle;
         rel = rn / st->fnorm;
     }
-    a.hist[k] = rel;
+    hist[k] = rel;
     st->relres = rel;
     int status = -1;
     if (rel <= st->tol) status = HOMG_OK;
@@ -384,9 +425,53 @@ __global__ void __launch_bounds__(1024) k_finalize(FinalizeArgs a) {
     else if (k >= st->max_cycles) status = HOMG_NOT_CONVERGED;
     st->status = status;
     st->done = (status >= 0);
+    if (st->done) st->t_done = device_clock_ns();
+    if (a.batch) return;
     const int local = k - st->stage_base;  // stage index within this graph launch
     if (status < 0 && local + 1 <= a.nstages) {
         for (int p = 0; p < 3; ++p) cudaGraphSetConditional(a.handles[3 * (local + 1) + p], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_finalize(FinalizeArgs a) {
+    pdl_begin();
+    __shared__ double sh[32];
+    const int z = a.batch ? blockIdx.x : 0;  // batch: one block per problem
+    State* st = a.st + z;
+    double* hist = a.hist + (int64_t)z * a.hist_bstride;
+    const double* pr = a.part_r + (int64_t)z * a.part_bstride;
+    const double* pf = a.part_f ? a.part_f + (int64_t)z * a.part_bstride : nullptr;
+    const bool skip = a.batch && a.mode == FIN_CYCLE && st->done;  // finished earlier
+    if (!skip) {
+        double sr = 0.0, sf = 0.0;
+        for (int t = threadIdx.x; t < a.nparts; t += blockDim.x) {
+            sr += pr[t];
+            if (pf) sf += pf[t];
+        }
+        sr = block_sum(sr, sh);
+        if (pf) sf = block_sum(sf, sh);
+        if (threadIdx.x == 0) finalize_decide(a, st, hist, sr, sf);
+    }
+    if (!a.batch) return;
+    // batch: the last block to arrive enables the next stage while any problem is still running
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(&a.ticket[0], 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int running = 0;
+    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) running |= !((volatile State*)a.st)[p].done;
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        a.ticket[0] = 0;
+        const int k = (a.mode == FIN_INIT) ? 0 : (int)++a.ticket[1];  // cycles run by the batch
+        const int local = k - (int)a.ticket[2];                       // stage within this graph launch
+        if (running && local + 1 <= a.nstages)
+            for (int q = 0; q < 3; ++q) cudaGraphSetConditional(a.handles[3 * (local + 1) + q], 1u);
     }
 }
 
@@ -399,9 +484,15 @@ __global__ void __launch_bounds__(BX * BY) k_copy_out(CopyOutArgs a, int n) {
     const int k = (ND == 3) ? (int)blockIdx.z + 1 : 0;
     if (i >= n || j >= n) return;
     const State* st = a.st;
+    CDGrid u0 = a.u0, u1 = a.u1;
+    if (ND == 2 && a.batch) {
+        st += blockIdx.z;
+        shift(u0, blockIdx.z);
+        shift(u1, blockIdx.z);
+    }
     double v = 0.0;
     if (!st->zero_u) {
-        const CDGrid src = (st->cycle & 1) ? a.u1 : a.u0;
+        const CDGrid src = (st->cycle & 1) ? u1 : u0;
         v = src.p[at(src.pitch, n, i, j, k)];
     }
     st->u[at(n + 1, n, i, j, k)] = v;
@@ -473,18 +564,24 @@ template <int ND, typename T>
 __global__ void __launch_bounds__(512) k_coarse_block(const BlockOp* __restrict__ ops, int nops) {
     pdl_begin();
     const int tid = threadIdx.x;
+    const int z = (ND == 2) ? blockIdx.z : 0;  // batch: one block per problem
     for (int o = 0; o < nops; ++o) {
         const int kind = ops[o].kind;
+        RestrictArgs rs = ops[o].rs;
+        ProlongArgs pr = ops[o].pr;
+        IterArgs it = ops[o].it;
+        bool live;
         int side;
-        if (kind == BLOCK_RESTRICT) side = ops[o].rs.gc.n - 1;
-        else if (kind == BLOCK_PROLONG) side = ops[o].pr.G.n - 1;
-        else side = ops[o].it.e_new.n - 1;
+        if (kind == BLOCK_RESTRICT) { live = batch_view<T>(rs, z); side = rs.gc.n - 1; }
+        else if (kind == BLOCK_PROLONG) { live = batch_view<T>(pr, z); side = pr.G.n - 1; }
+        else { live = batch_view<T>(it, z); side = it.e_new.n - 1; }
+        if (!live) return;  // this problem has converged (uniform over the block)
         const int total = (ND == 2) ? side * side : side * side * side;
         for (int q = tid; q < total; q += blockDim.x) {
             const int i = q % side + 1, j = (q / side) % side + 1, k = (ND == 3) ? q / (side * side) + 1 : 0;
-            if (kind == BLOCK_RESTRICT) restrict_point<ND, false, T>(ops[o].rs, i, j, k);
-            else if (kind == BLOCK_PROLONG) prolong_point<ND, false, T>(ops[o].pr, i, j, k);
-            else iterate_point<ND, false, T>(ops[o].it, i, j, k);
+            if (kind == BLOCK_RESTRICT) restrict_point<ND, false, T>(rs, i, j, k);
+            else if (kind == BLOCK_PROLONG) prolong_point<ND, false, T>(pr, i, j, k);
+            else iterate_point<ND, false, T>(it, i, j, k);
         }
         __syncthreads();
     }
@@ -540,6 +637,7 @@ struct ColumnInterp2 {
 template <int PEND, bool WD, typename T>
 __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
     pdl_begin();
+    if (!batch_view<T>(a, blockIdx.z)) return;
     using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -589,6 +687,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
 template <typename T>
 __global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
     pdl_begin();
+    if (!batch_view<T>(a, blockIdx.z)) return;
     using C = typename St<T>::C;
     const int n = a.G.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -878,6 +977,7 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     pdl_begin();
+    if (!batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
     __shared__ double sh[JX / 32];
     const int i = blockIdx.x * JX + threadIdx.x + 1;
     const int j0 = blockIdx.y * JR + 1;
@@ -922,10 +1022,11 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     }
 }
 
-// Nodes per thread along the march: long columns on large grids (fewer blocks, more reuse), short
-// ones on small grids, where a thread's serial chain of loads would otherwise set the time.
-int march_rows(int ndim, int n) {
-    const double nodes = (ndim == 2) ? (double)(n - 1) * (n - 1) : (double)(n - 1) * (n - 1) * (n - 1);
+// Nodes per thread along the march: long columns on large launches (fewer blocks, more reuse),
+// short ones on small launches, where a thread's serial chain of loads would otherwise set the
+// time. `nb` problems of a batch share the launch.
+int march_rows(int ndim, int n, int nb = 1) {
+    const double nodes = (double)nb * ((ndim == 2) ? (double)(n - 1) * (n - 1) : (double)(n - 1) * (n - 1) * (n - 1));
     if (nodes >= 8.0e6) return 16;
     if (nodes >= 1.0e6) return 4;
     return 1;
@@ -967,9 +1068,9 @@ cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) 
     const int n = a.e_new.n;
     if (!strict && a.m == 0 && a.e_old.p != nullptr) {
         const bool wd = a.dnew.p != nullptr;
-        const int rows = march_rows(ndim, n);
+        const int rows = a.rows > 0 ? a.rows : march_rows(ndim, n, a.nb);
         if (ndim == 2) {
-            const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows)), b(JX);
+            const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
             const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
 #define JAC2(P, W) launch_k(k_jacobi2<P, W, T>, g, b, s, a, rows)
             if (pend == 0) { if (wd) JAC2(0, true); else JAC2(0, false); }
@@ -994,7 +1095,9 @@ cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) 
         else launch_k(k_wholegrid2<false, T>, g, b, s, a);
         return cudaGetLastError();
     }
-    const dim3 g = grid_for(ndim, n), b(BX, BY);
+    dim3 g = grid_for(ndim, n);
+    const dim3 b(BX, BY);
+    if (ndim == 2) g.z = (unsigned)a.nb;
     if (ndim == 2) {
         if (strict) launch_k(k_iterate<2, true, T>, g, b, s, a);
         else launch_k(k_iterate<2, false, T>, g, b, s, a);
@@ -1009,8 +1112,8 @@ template <typename T>
 cudaError_t prolong_t(int ndim, bool strict, const ProlongArgs& a, cudaStream_t s) {
     if (!strict && ndim == 2 && a.s == 1) {
         const int n = a.G.n;
-        const int rows = march_rows(2, n);
-        const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows));
+        const int rows = march_rows(2, n, a.nb);
+        const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb);
         launch_k(k_prolong2_s1<T>, g, dim3(JX), s, a, rows);
         return cudaGetLastError();
     }
@@ -1021,7 +1124,9 @@ cudaError_t prolong_t(int ndim, bool strict, const ProlongArgs& a, cudaStream_t 
         launch_k(k_prolong3_s1<T>, g, dim3(J3X, J3Y), s, a, rows);
         return cudaGetLastError();
     }
-    const dim3 g = grid_for(ndim, a.G.n), b(BX, BY);
+    dim3 g = grid_for(ndim, a.G.n);
+    const dim3 b(BX, BY);
+    if (ndim == 2) g.z = (unsigned)a.nb;
     if (ndim == 2) {
         if (strict) launch_k(k_prolong<2, true, T>, g, b, s, a);
         else launch_k(k_prolong<2, false, T>, g, b, s, a);
@@ -1034,7 +1139,8 @@ cudaError_t prolong_t(int ndim, bool strict, const ProlongArgs& a, cudaStream_t 
 
 template <typename T>
 cudaError_t residual_t(int ndim, bool strict, const ResidArgs& a, int n, cudaStream_t s) {
-    const dim3 g = resid_grid(ndim, strict, n);
+    dim3 g = resid_grid(ndim, strict, n);
+    if (ndim == 2) g.z = (unsigned)a.nb;
     if (ndim == 2) {
         if (strict) launch_k(k_residual<2, true, T>, g, dim3(BX, BY), s, a, n);
         else launch_k(k_residual2_fast<T>, g, dim3(JX), s, a, n);
@@ -1059,7 +1165,9 @@ cudaError_t residual_t(int ndim, bool strict, const ResidArgs& a, int n, cudaStr
 
 template <typename T>
 cudaError_t restrict_t(int ndim, bool strict, const RestrictArgs& a, cudaStream_t s) {
-    const dim3 g = grid_for(ndim, a.gc.n), b(BX, BY);
+    dim3 g = grid_for(ndim, a.gc.n);
+    const dim3 b(BX, BY);
+    if (ndim == 2) g.z = (unsigned)a.nb;
     if (ndim == 2) {
         if (strict) launch_k(k_restrict<2, true, T>, g, b, s, a);
         else launch_k(k_restrict<2, false, T>, g, b, s, a);
@@ -1101,8 +1209,8 @@ cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs&
     DISPATCH_PREC(prec, restrict_t<T>(ndim, strict, a, s));
 }
 
-cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, cudaStream_t s) {
-    if (ndim == 2) { DISPATCH_PREC(prec, (launch_k(k_coarse_block<2, T>, 1, 512, s, ops, nops), cudaGetLastError())); }
+cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, int nb, cudaStream_t s) {
+    if (ndim == 2) { DISPATCH_PREC(prec, (launch_k(k_coarse_block<2, T>, dim3(1, 1, nb), 512, s, ops, nops), cudaGetLastError())); }
     DISPATCH_PREC(prec, (launch_k(k_coarse_block<3, T>, 1, 512, s, ops, nops), cudaGetLastError()));
 }
 
@@ -1153,12 +1261,14 @@ cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAdd
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
-    launch_k(k_finalize, 1, 1024, s, a);
+    launch_k(k_finalize, a.batch ? a.batch : 1, 1024, s, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s) {
-    const dim3 g = grid_for(ndim, n), b(BX, BY);
+    dim3 g = grid_for(ndim, n);
+    const dim3 b(BX, BY);
+    if (ndim == 2) g.z = (unsigned)a.nb;
     if (ndim == 2) launch_k(k_copy_out<2>, g, b, s, a, n);
     else launch_k(k_copy_out<3>, g, b, s, a, n);
     return cudaGetLastError();

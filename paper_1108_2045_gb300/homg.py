@@ -38,7 +38,14 @@ EXPORTS = [
     "homg_last_error",
     "homg_destroy",
     "homg_residual_norm_noalloc",
+    "homg_batch_create",
+    "homg_batch_set_stream",
+    "homg_batch_solve",
+    "homg_batch_get_stats",
+    "homg_batch_destroy",
 ]
+
+HOMG_BATCH_MAX_GROUPS = 16
 
 
 class homg_options(ctypes.Structure):
@@ -81,6 +88,17 @@ class homg_stats(ctypes.Structure):
     ]
 
 
+class homg_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("groups", ctypes.c_int),
+        ("solve_ms", ctypes.c_double),
+        ("sides", ctypes.c_int64 * HOMG_BATCH_MAX_GROUPS),
+        ("counts", ctypes.c_int * HOMG_BATCH_MAX_GROUPS),
+        ("rows", ctypes.c_int * HOMG_BATCH_MAX_GROUPS),
+        ("tuned_us", ctypes.c_double * HOMG_BATCH_MAX_GROUPS),
+    ]
+
+
 _lib = None
 
 
@@ -108,8 +126,16 @@ def load(path=LIB_PATH):
     lib.homg_residual_norm_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), vp, vp, dp, vp]
     lib.homg_destroy.argtypes = [vp]
     lib.homg_destroy.restype = None
+    vpp = ctypes.POINTER(ctypes.c_void_p)
+    lib.homg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(homg_options),
+                                      ctypes.POINTER(vp)]
+    lib.homg_batch_set_stream.argtypes = [vp, vp]
+    lib.homg_batch_solve.argtypes = [vp, vpp, vpp, ctypes.c_double, ctypes.c_int, ip, ip, dp, dp]
+    lib.homg_batch_get_stats.argtypes = [vp, ctypes.POINTER(homg_batch_stats)]
+    lib.homg_batch_destroy.argtypes = [vp]
+    lib.homg_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("homg_default_options", "homg_last_error", "homg_destroy"):
+        if name not in ("homg_default_options", "homg_last_error", "homg_destroy", "homg_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -135,6 +161,95 @@ def _check(rc, handle):
     if rc < 0:
         raise HomgError(rc, homg_last_error(handle))
     return rc
+
+
+def _options(omega_j=0.0, max_i=32, schedule=None, exec_mode="auto", strict_fp=False, diverge_factor=0.0,
+             launch_mode="graph", precision="fp64", cycle="homg", v_pre=0, v_post=0):
+    o = homg_default_options()
+    o.omega_j = omega_j
+    o.max_i = max_i
+    o.exec_mode = EXEC_MODES[exec_mode] if isinstance(exec_mode, str) else int(exec_mode)
+    o.strict_fp = 1 if strict_fp else 0
+    o.diverge_factor = diverge_factor
+    o.launch_mode = LAUNCH_MODES[launch_mode] if isinstance(launch_mode, str) else int(launch_mode)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
+    o.v_pre = v_pre
+    o.v_post = v_post
+    keep = None
+    if schedule is not None:
+        keep = (ctypes.c_int * len(schedule))(*schedule)
+        o.n_schedule = len(schedule)
+        o.schedule = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    return o, keep
+
+
+def homg_batch_create(sides, **opts):
+    """Create a batch of 2-D problems with the given nodes per side; returns an opaque handle."""
+    lib = load()
+    o, _keep = _options(**opts)
+    arr = (ctypes.c_int64 * len(sides))(*sides)
+    h = ctypes.c_void_p()
+    _check(lib.homg_batch_create(len(sides), arr, ctypes.byref(o), ctypes.byref(h)), None)
+    return h.value
+
+
+def homg_batch_set_stream(handle, stream):
+    raw = getattr(stream, "cuda_stream", stream) or 0
+    return _check(load().homg_batch_set_stream(handle, ctypes.c_void_p(raw)), None)
+
+
+def homg_batch_solve(handle, fs, us, tol=1e-10, max_cycles=50):
+    """Solve every problem in place (lists of device tensors). Returns (rc, status, cycles, relres, solve_ms)."""
+    n = len(fs)
+    fp = (ctypes.c_void_p * n)(*[_devptr(f, "f").value for f in fs])
+    up = (ctypes.c_void_p * n)(*[_devptr(u, "u").value for u in us])
+    st, cy = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+    rr, ms = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+    rc = load().homg_batch_solve(handle, fp, up, tol, max_cycles, st, cy, rr, ms)
+    _check(rc, None)
+    return rc, list(st), list(cy), list(rr), list(ms)
+
+
+def homg_batch_get_stats(handle):
+    s = homg_batch_stats()
+    _check(load().homg_batch_get_stats(handle, ctypes.byref(s)), None)
+    g = s.groups
+    return {"groups": g, "solve_ms": s.solve_ms, "sides": list(s.sides[:g]), "counts": list(s.counts[:g]),
+            "rows": list(s.rows[:g]), "tuned_us": list(s.tuned_us[:g])}
+
+
+def homg_batch_destroy(handle):
+    if handle:
+        load().homg_batch_destroy(handle)
+
+
+class BatchSolver:
+    """Owner of a batch handle (same options as homg_create)."""
+
+    def __init__(self, sides, **opts):
+        self.sides = list(sides)
+        self.handle = homg_batch_create(self.sides, **opts)
+
+    def set_stream(self, stream):
+        return homg_batch_set_stream(self.handle, stream)
+
+    def solve(self, fs, us, tol=1e-10, max_cycles=50):
+        return homg_batch_solve(self.handle, fs, us, tol, max_cycles)
+
+    def stats(self):
+        return homg_batch_get_stats(self.handle)
+
+    def close(self):
+        homg_batch_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
 
 def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, schedule=None, exec_mode="auto",

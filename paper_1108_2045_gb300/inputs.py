@@ -10,6 +10,8 @@ Workloads (stand-ins for the paper's Poisson experiments of Sec. 4; the paper us
 * ``uniform_rhs``  f iid uniform[-1, 1] over the interior nodes in layout order, numpy
                    ``default_rng(seed)`` (seed 0 for the 4097^2 benchmark grid).
 * ``normal_rhs``   f iid N(0, 1), same ordering.
+* ``uneven_batch`` a batch of 2-D problems with sides 2^k + 1, k uniform on 6..10, f iid N(0, 1)
+                   (seed 1 for the 1024-problem batch benchmark).
 * ``paper_poly_rhs`` / ``paper_poly_solution``: the polynomial test problem of Sec. 4, converted
                    to A = -Laplacian (the paper states Laplacian(u) = f, so f here is minus the
                    paper's source and the solution is the paper's u).
@@ -74,3 +76,18 @@ def paper_poly_rhs(n):
     x, y = node_coords(n, 2)
     f_paper = -2.0 * (y ** 2 * (1 - 6 * x ** 2) * (1 - y ** 2) + x ** 2 * (1 - 6 * y ** 2) * (1 - x ** 2))
     return _zero_boundary(np.ascontiguousarray(-f_paper + 0.0 * x * y))
+
+
+def uneven_batch(count, seed=1, kmin=6, kmax=10):
+    """A batch of 2-D problems of uneven sizes: `count` exponents k uniform on kmin..kmax (sides
+    2^k + 1), then for each problem in turn f iid N(0, 1) over its interior in layout order, all
+    drawn in that order from numpy's default_rng(seed). Returns (ks, fs)."""
+    rng = np.random.default_rng(seed)
+    ks = [int(k) for k in rng.integers(kmin, kmax + 1, size=count)]
+    fs = []
+    for k in ks:
+        n = 2 ** k
+        f = np.zeros((n + 1, n + 1))
+        f[1:-1, 1:-1] = rng.standard_normal((n - 1, n - 1))
+        fs.append(f)
+    return ks, fs

@@ -1,0 +1,135 @@
+"""Batched solves on the GPU (GB300 only): every problem of a batch must come out bit-identical to
+solving it alone (the batched launches run the same per-node arithmetic and reduction order), and
+problems must not influence each other's outcome."""
+
+import numpy as np
+import pytest
+
+from paper_1108_2045_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def homg():
+    import torch
+
+    import __graft_entry__
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    __graft_entry__.build()
+    from paper_1108_2045_gb300 import homg as binding
+
+    return binding
+
+
+def single(homg, f_np, tol, max_cycles, precision):
+    import torch
+
+    K = int(np.log2(f_np.shape[0] - 1))
+    with homg.Solver(2, f_np.shape[0], K, precision=precision) as s:
+        f = torch.from_numpy(f_np).cuda()
+        u = torch.zeros_like(f)
+        st, cyc, rr = s.solve(f, u, tol=tol, max_cycles=max_cycles)
+        return u.cpu().numpy(), st, cyc, rr
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "bf16"])
+def test_batch_matches_single_solves(homg, precision):
+    import torch
+
+    rng = np.random.default_rng(2)
+    ks = [5, 6, 7, 8, 6, 5, 7, 9, 6, 8, 5, 7]
+    fs_np = [inputs.normal_rhs(2 ** k, 2, seed=int(rng.integers(1 << 30))) for k in ks]
+    with homg.BatchSolver([2 ** k + 1 for k in ks], precision=precision) as b:
+        st = b.stats()
+        assert st["groups"] == 5 and sorted(st["counts"]) == [1, 2, 3, 3, 3] and all(r >= 1 for r in st["rows"])
+        fs = [torch.from_numpy(f).cuda() for f in fs_np]
+        us = [torch.zeros_like(f) for f in fs]
+        rc, status, cycles, relres, ms = b.solve(fs, us, tol=1e-10, max_cycles=40)
+        assert rc == homg.HOMG_OK and all(s == homg.HOMG_OK for s in status)
+        assert all(t > 0 for t in ms)
+        for p, f_np in enumerate(fs_np):
+            ref, st1, cyc1, rr1 = single(homg, f_np, 1e-10, 40, precision)
+            assert (status[p], cycles[p]) == (st1, cyc1)
+            assert relres[p] == rr1
+            np.testing.assert_array_equal(us[p].cpu().numpy(), ref)
+        # a second solve on the same handle reuses its graphs and gives the same answer
+        us2 = [torch.zeros_like(f) for f in fs]
+        rc2, status2, cycles2, relres2, _ = b.solve(fs, us2, tol=1e-10, max_cycles=40)
+        assert cycles2 == cycles and relres2 == relres
+        for a, c in zip(us, us2):
+            assert torch.equal(a, c)
+
+
+def test_batch_problems_are_independent(homg):
+    import torch
+
+    n = 64
+    good = inputs.uniform_rhs(n, 2, seed=1)
+    zero = np.zeros_like(good)
+    bad = good.copy()
+    bad[7, 9] = np.nan
+    f_np = [good, zero, bad, good]
+    with homg.BatchSolver([n + 1] * 4, precision="fp32") as b:
+        fs = [torch.from_numpy(f).cuda() for f in f_np]
+        us = [torch.zeros_like(f) for f in fs]
+        rc, status, cycles, relres, ms = b.solve(fs, us, tol=1e-10, max_cycles=40)
+    assert status == [homg.HOMG_OK, homg.HOMG_OK, homg.HOMG_DIVERGED, homg.HOMG_OK]
+    assert rc == homg.HOMG_DIVERGED
+    assert cycles[1] == 0 and relres[1] == 0.0 and torch.count_nonzero(us[1]) == 0
+    assert torch.equal(us[0], us[3]) and cycles[0] == cycles[3]
+    ref, _, cyc1, _ = single(homg, good, 1e-10, 40, "fp32")
+    np.testing.assert_array_equal(us[0].cpu().numpy(), ref)
+
+
+def test_batch_continuation_beyond_one_graph(homg):
+    # an unreachable tolerance runs to max_cycles, past the cycles one graph launch unrolls
+    import torch
+
+    n = 32
+    f_np = [inputs.uniform_rhs(n, 2, seed=s) for s in (3, 4)]
+    with homg.BatchSolver([n + 1] * 2, precision="fp64") as b:
+        fs = [torch.from_numpy(f).cuda() for f in f_np]
+        us = [torch.zeros_like(f) for f in fs]
+        rc, status, cycles, relres, ms = b.solve(fs, us, tol=0.0, max_cycles=30)
+    assert status == [homg.HOMG_NOT_CONVERGED] * 2 and cycles == [30, 30]
+    ref, st1, cyc1, rr1 = single(homg, f_np[0], 0.0, 30, "fp64")
+    assert cyc1 == 30 and relres[0] == rr1
+    np.testing.assert_array_equal(us[0].cpu().numpy(), ref)
+
+
+def test_batch_rejects_unsupported_options(homg):
+    for kw in [dict(strict_fp=True), dict(exec_mode="wholegrid"), dict(cycle="v"), dict(launch_mode="stream")]:
+        with pytest.raises(homg.HomgError):
+            homg.homg_batch_create([33, 65], **kw)
+    with pytest.raises(homg.HomgError):
+        homg.homg_batch_create([33, 64])
+
+
+def test_full_uneven_batch_sampled_against_oracle(homg):
+    # the benchmarked launch configuration: 1024 problems, sides 2^k + 1 with k ~ U{6..10} (seed 1),
+    # FP32 cycles; every problem converges, sampled solutions pass the oracle's own FP64 residual
+    # test and equal a solve of the same problem alone, bit for bit
+    import torch
+
+    import oracle
+
+    oracle.build()
+    ks, fs_np = inputs.uneven_batch(1024, seed=1)
+    fs = [torch.from_numpy(f).cuda() for f in fs_np]
+    us = [torch.zeros_like(f) for f in fs]
+    with homg.BatchSolver([2 ** k + 1 for k in ks], precision="fp32") as b:
+        rc, status, cycles, relres, ms = b.solve(fs, us, tol=1e-10, max_cycles=40)
+    assert rc == homg.HOMG_OK and all(s == homg.HOMG_OK for s in status) and max(relres) <= 1e-10
+    ks_arr = np.array(ks)
+    for k in range(6, 11):
+        for i in np.flatnonzero(ks_arr == k)[:2]:
+            un = us[i].cpu().numpy()
+            rr = oracle.norm_interior(oracle.residual(fs_np[i], un)) / oracle.norm_interior(fs_np[i])
+            # r = f - A u cancels to ~1e-10 of f, so the two FP64 residuals agree to ~1e-6 relative
+            assert rr <= 1.0001e-10 and abs(rr - relres[i]) <= 1e-4 * rr, (k, rr, relres[i])
+        i = int(np.flatnonzero(ks_arr == k)[-1])
+        ref, st1, cyc1, rr1 = single(homg, fs_np[i], 1e-10, 40, "fp32")
+        assert (st1, cyc1, rr1) == (status[i], cycles[i], relres[i])
+        np.testing.assert_array_equal(us[i].cpu().numpy(), ref)
