@@ -14,15 +14,19 @@ from .oracle import (  # noqa: F401
     build,
     cycle_lp,
     cycle,
+    cycle_vc,
     default_omega_j,
     iteration,
+    iteration_vc,
     mfmg_schedule,
     norm_interior,
     prolong,
     residual,
+    residual_vc,
     restrict,
     solve,
     solve_mixed,
+    solve_vc,
     solve_vcycle,
     vcycle,
 )

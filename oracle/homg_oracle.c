@@ -773,3 +773,226 @@ int homg_oracle_solve_vcycle(int ndim, int64_t n, int levels, int nu1, int nu2, 
     if (relres_out) *relres_out = rr;
     return status;
 }
+
+/* ========================================================================================== */
+/* Variable-coefficient diffusion (2-D), an extension of the paper's Poisson problem:            */
+/*   A u = -div(k grad u) on the unit square, zero Dirichlet boundary,                         */
+/* discretised in flux form on the five-point stencil,                                          */
+/*   (A u)(p) = sum over the four faces of p of k_f (u(p) - u(nb)) / h^2,                        */
+/* with each face coefficient the harmonic mean of the node coefficients at its two ends,       */
+/* k_f = 2 k(p) k(nb) / (k(p) + k(nb)), written ((2 a) b) / (a + b) (symmetric in a and b, bit   */
+/* for bit). Level m uses the same form between lattice neighbours at spacing h_m, with k taken  */
+/* by injection (its values at the lattice nodes). The HOMG relaxation (Sec. 2) becomes damped  */
+/* Jacobi with the node's own diagonal D = ((k_W + k_E) + k_S) + k_N:                            */
+/*   delta(p) = (omega_J / D) (h_m^2 F_m(p) - (A_m e)(p) h_m^2),                                 */
+/* which for k = 1 (D = 4) is the Poisson relaxation with omega = omega_J / 4. Restriction,     */
+/* interpolation, schedule and restart loop are the Poisson solver's. k is a node array on the   */
+/* (n+1)^2 grid, boundary included: boundary faces use the boundary node values.               */
+/* ========================================================================================== */
+static double face_coef(double a, double b) { return ((2.0 * a) * b) / (a + b); }
+
+/* Face coefficients of lattice node (i, j) at lattice spacing l (fine-grid index units). */
+static void vc_faces(const double *kc, int64_t n, int64_t l, int64_t i, int64_t j, double *kw, double *ke,
+                     double *ks, double *kn) {
+    const int64_t side = n + 1;
+    const double kp = kc[j * side + i];
+    *kw = face_coef(kp, kc[j * side + (i - l)]);
+    *ke = face_coef(kp, kc[j * side + (i + l)]);
+    *ks = face_coef(kp, kc[(j - l) * side + i]);
+    *kn = face_coef(kp, kc[(j + l) * side + i]);
+}
+
+void homg_oracle_residual_vc(int64_t n, const double *kc, const double *f, const double *u, double *r) {
+    const double h = 1.0 / (double)n;
+    const double h2 = h * h;
+    for (int64_t j = 0; j <= n; ++j)
+        for (int64_t i = 0; i <= n; ++i) {
+            int64_t p = j * (n + 1) + i;
+            if (i == 0 || j == 0 || i == n || j == n) { r[p] = 0.0; continue; }
+            double kw, ke, ks, kn;
+            vc_faces(kc, n, 1, i, j, &kw, &ke, &ks, &kn);
+            const double uc = u_at2(u, n, i, j);
+            double au = kw * (uc - u_at2(u, n, i - 1, j));
+            au = au + ke * (uc - u_at2(u, n, i + 1, j));
+            au = au + ks * (uc - u_at2(u, n, i, j - 1));
+            au = au + kn * (uc - u_at2(u, n, i, j + 1));
+            r[p] = f[p] - au / h2;
+        }
+}
+
+/* One HOMG iteration with the variable-coefficient relaxation (see homg_oracle_iteration). */
+void homg_oracle_iteration_vc(int64_t n, int m, int mprev, double omega_j, const double *kc, const double *Fm,
+                              const double *dprev, const double *e_old, double *e_new, double *d_new) {
+    const int64_t l = (int64_t)1 << m, nm = n >> m, side = n + 1;
+    const int64_t lp = (mprev >= 0) ? ((int64_t)1 << mprev) : 1;
+    const double h = 1.0 / (double)n;
+    const double hm = h * (double)l;
+    const double hm2 = hm * hm;
+    for (int64_t q = 0; q < (nm + 1) * (nm + 1); ++q) d_new[q] = 0.0;
+    for (int64_t j = 0; j <= n; ++j)
+        for (int64_t i = 0; i <= n; ++i) {
+            int64_t p = j * side + i;
+            if (i == 0 || j == 0 || i == n || j == n) { e_new[p] = 0.0; continue; }
+            double v = e_old[p];
+            if ((i & (l - 1)) == 0 && (j & (l - 1)) == 0) { /* p on the level-m lattice */
+                double kw, ke, ks, kn;
+                vc_faces(kc, n, l, i, j, &kw, &ke, &ks, &kn);
+                const double D = ((kw + ke) + ks) + kn;
+                double ae = kw * (v - e_old[j * side + (i - l)]);
+                ae = ae + ke * (v - e_old[j * side + (i + l)]);
+                ae = ae + ks * (v - e_old[(j - l) * side + i]);
+                ae = ae + kn * (v - e_old[(j + l) * side + i]);
+                int64_t q = (j >> m) * (nm + 1) + (i >> m);
+                double delta = (omega_j / D) * (hm2 * Fm[q] - ae);
+                d_new[q] = delta;
+                v = v + delta;
+            }
+            if (mprev >= 0 && !((i & (lp - 1)) == 0 && (j & (lp - 1)) == 0)) v = v + interp2(dprev, n, mprev, i, j);
+            e_new[p] = v;
+        }
+}
+
+/* The same iteration in binary32 (stored at prec: 1 binary32, 2 bfloat16). The coefficients are */
+/* formed in binary64 as above and rounded once to binary32: k_f, and the weight omega_J / D.    */
+void homg_oracle_iteration_vc_lp(int64_t n, int m, int mprev, double omega_j, const double *kc, const float *Fm,
+                                 const float *dprev, const float *e_old, float *e_new, float *d_new, int prec) {
+    const int64_t l = (int64_t)1 << m, nm = n >> m, side = n + 1;
+    const int64_t lp = (mprev >= 0) ? ((int64_t)1 << mprev) : 1;
+    const float h = 1.0f / (float)n;
+    const float hm = h * (float)l;
+    const float hm2 = hm * hm;
+    for (int64_t q = 0; q < (nm + 1) * (nm + 1); ++q) d_new[q] = 0.0f;
+    for (int64_t j = 0; j <= n; ++j)
+        for (int64_t i = 0; i <= n; ++i) {
+            int64_t p = j * side + i;
+            if (i == 0 || j == 0 || i == n || j == n) { e_new[p] = 0.0f; continue; }
+            float v = e_old[p];
+            if ((i & (l - 1)) == 0 && (j & (l - 1)) == 0) {
+                double kw, ke, ks, kn;
+                vc_faces(kc, n, l, i, j, &kw, &ke, &ks, &kn);
+                const float wd = (float)(omega_j / (((kw + ke) + ks) + kn));
+                float ae = (float)kw * (v - e_old[j * side + (i - l)]);
+                ae = ae + (float)ke * (v - e_old[j * side + (i + l)]);
+                ae = ae + (float)ks * (v - e_old[(j - l) * side + i]);
+                ae = ae + (float)kn * (v - e_old[(j + l) * side + i]);
+                int64_t q = (j >> m) * (nm + 1) + (i >> m);
+                float delta = wd * (hm2 * Fm[q] - ae);
+                d_new[q] = store_lp(delta, prec);
+                v = v + delta;
+            }
+            if (mprev >= 0 && !((i & (lp - 1)) == 0 && (j & (lp - 1)) == 0)) v = v + interp2f(dprev, n, mprev, i, j);
+            e_new[p] = store_lp(v, prec);
+        }
+}
+
+/* One variable-coefficient HOMG cycle on A e = F0 from e = 0 (see homg_oracle_cycle); prec 0:   */
+/* binary64, 1: binary32, 2: bfloat16 storage (see homg_oracle_cycle_lp).                        */
+int homg_oracle_cycle_vc(int64_t n, int levels, const int *sched, int nsched, double omega_j, int prec,
+                         const double *kc, const double *F0, double *e) {
+    int K = log2_exact(n);
+    if (K < 1 || levels < 1 || levels > K || nsched < 1 || prec < 0 || prec > 2) return HOMG_ORACLE_EINVAL;
+    for (int t = 0; t < nsched; ++t)
+        if (sched[t] < 0 || sched[t] >= levels) return HOMG_ORACLE_EINVAL;
+    if (sched[nsched - 1] != 0) return HOMG_ORACLE_EINVAL;
+    const int64_t total = (n + 1) * (n + 1);
+    int rc = HOMG_ORACLE_OK;
+    if (prec == 0) {
+        double **F = (double **)calloc((size_t)levels, sizeof(double *));
+        double *ebuf = (double *)malloc((size_t)total * sizeof(double));
+        double *dA = (double *)malloc((size_t)total * sizeof(double));
+        double *dB = (double *)malloc((size_t)total * sizeof(double));
+        if (!F || !ebuf || !dA || !dB) { rc = HOMG_ORACLE_ENOMEM; goto done64; }
+        F[0] = (double *)F0;
+        for (int m = 1; m < levels; ++m) {
+            F[m] = (double *)malloc((size_t)(((n >> m) + 1) * ((n >> m) + 1)) * sizeof(double));
+            if (!F[m]) { rc = HOMG_ORACLE_ENOMEM; goto done64; }
+            homg_oracle_restrict(2, n >> (m - 1), F[m - 1], F[m]);
+        }
+        for (int64_t p = 0; p < total; ++p) e[p] = 0.0;
+        {
+            double *e_old = e, *e_new = ebuf, *dprev = dA, *dnew = dB;
+            int mprev = -1;
+            for (int t = 0; t < nsched; ++t) {
+                int m = sched[t];
+                homg_oracle_iteration_vc(n, m, mprev, omega_j, kc, F[m], dprev, e_old, e_new, dnew);
+                double *tmp = e_old; e_old = e_new; e_new = tmp;
+                tmp = dprev; dprev = dnew; dnew = tmp;
+                mprev = m;
+            }
+            if (e_old != e) memcpy(e, e_old, (size_t)total * sizeof(double));
+        }
+    done64:
+        if (F) for (int m = 1; m < levels; ++m) free(F[m]);
+        free(F); free(ebuf); free(dA); free(dB);
+        return rc;
+    }
+    float **F = (float **)calloc((size_t)levels, sizeof(float *));
+    float *ea = (float *)calloc((size_t)total, sizeof(float));
+    float *eb = (float *)malloc((size_t)total * sizeof(float));
+    float *dA = (float *)malloc((size_t)total * sizeof(float));
+    float *dB = (float *)malloc((size_t)total * sizeof(float));
+    if (!F || !ea || !eb || !dA || !dB) { rc = HOMG_ORACLE_ENOMEM; goto donelp; }
+    for (int m = 0; m < levels; ++m) {
+        F[m] = (float *)malloc((size_t)(((n >> m) + 1) * ((n >> m) + 1)) * sizeof(float));
+        if (!F[m]) { rc = HOMG_ORACLE_ENOMEM; goto donelp; }
+    }
+    for (int64_t p = 0; p < total; ++p) F[0][p] = store_lp((float)F0[p], prec);
+    for (int m = 1; m < levels; ++m) homg_oracle_restrict_lp(2, n >> (m - 1), F[m - 1], F[m], prec);
+    {
+        float *e_old = ea, *e_new = eb, *dprev = dA, *dnew = dB;
+        int mprev = -1;
+        for (int t = 0; t < nsched; ++t) {
+            int m = sched[t];
+            homg_oracle_iteration_vc_lp(n, m, mprev, omega_j, kc, F[m], dprev, e_old, e_new, dnew, prec);
+            float *tmp = e_old; e_old = e_new; e_new = tmp;
+            tmp = dprev; dprev = dnew; dnew = tmp;
+            mprev = m;
+        }
+        for (int64_t p = 0; p < total; ++p) e[p] = (double)e_old[p];
+    }
+donelp:
+    if (F) for (int m = 0; m < levels; ++m) free(F[m]);
+    free(F); free(ea); free(eb); free(dA); free(dB);
+    return rc;
+}
+
+/* Restarted variable-coefficient solve (see homg_oracle_solve; binary64 residual, update and   */
+/* norms around cycles of precision prec).                                                      */
+int homg_oracle_solve_vc(int64_t n, int levels, const int *sched, int nsched, double omega_j, double div_factor,
+                         int prec, const double *kc, const double *f, double *u, double tol, int max_cycles,
+                         double *hist, int *cycles_out, double *relres_out) {
+    int K = log2_exact(n);
+    if (K < 1 || levels < 1 || levels > K || max_cycles < 0 || prec < 0 || prec > 2) return HOMG_ORACLE_EINVAL;
+    const int64_t side = n + 1, total = side * side;
+    double fnorm = homg_oracle_norm_interior(2, n, f);
+    if (fnorm == 0.0) {
+        for (int64_t j = 1; j < n; ++j)
+            for (int64_t i = 1; i < n; ++i) u[j * side + i] = 0.0;
+        if (hist) hist[0] = 0.0;
+        if (cycles_out) *cycles_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        return HOMG_ORACLE_OK;
+    }
+    double *r = (double *)malloc((size_t)total * sizeof(double));
+    double *e = (double *)malloc((size_t)total * sizeof(double));
+    if (!r || !e) { free(r); free(e); return HOMG_ORACLE_ENOMEM; }
+    int status = HOMG_ORACLE_NOT_CONVERGED, k;
+    double rr = 0.0, rr0 = 0.0;
+    for (k = 0;; ++k) {
+        homg_oracle_residual_vc(n, kc, f, u, r);
+        rr = homg_oracle_norm_interior(2, n, r) / fnorm;
+        if (hist) hist[k] = rr;
+        if (k == 0) rr0 = rr;
+        if (rr <= tol) { status = HOMG_ORACLE_OK; break; }
+        if (!isfinite(rr) || rr > div_factor * rr0) { status = HOMG_ORACLE_DIVERGED; break; }
+        if (k == max_cycles) { status = HOMG_ORACLE_NOT_CONVERGED; break; }
+        int rc = homg_oracle_cycle_vc(n, levels, sched, nsched, omega_j, prec, kc, r, e);
+        if (rc != HOMG_ORACLE_OK) { free(r); free(e); return rc; }
+        for (int64_t j = 1; j < n; ++j)
+            for (int64_t i = 1; i < n; ++i) u[j * side + i] = u[j * side + i] + e[j * side + i];
+    }
+    free(r); free(e);
+    if (cycles_out) *cycles_out = k;
+    if (relres_out) *relres_out = rr;
+    return status;
+}

@@ -56,6 +56,12 @@ def _load(path=None):
         lib.homg_oracle_solve_vcycle.argtypes = [ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_double, ctypes.c_double, P, P, ctypes.c_double,
                                                  ctypes.c_int, P, IP, P]
+        lib.homg_oracle_residual_vc.argtypes = [i64, P, P, P, P]
+        lib.homg_oracle_iteration_vc.argtypes = [i64, ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P, P, P, P, P]
+        lib.homg_oracle_cycle_vc.argtypes = [i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             P, P, P]
+        lib.homg_oracle_solve_vc.argtypes = [i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int, P, P, P, ctypes.c_double, ctypes.c_int, P, IP, P]
         lib.homg_oracle_bf16_round.argtypes = [ctypes.c_float]
         lib.homg_oracle_bf16_round.restype = ctypes.c_float
         _lib = lib
@@ -253,6 +259,78 @@ def solve(f, levels, u0=None, tol=1e-10, max_cycles=100, schedule=None, max_i=32
     status = _load().homg_oracle_solve(ndim, n, levels, cs, len(sched), omega_j, div_factor,
                                        _p(np.ascontiguousarray(f)), _p(u), tol, max_cycles, _p(hist),
                                        ctypes.byref(cyc), ctypes.byref(rr))
+    if status < 0:
+        raise ValueError("oracle solve rejected its arguments (rc=%d)" % status)
+    return u, status, cyc.value, hist[: cyc.value + 1]
+
+
+# ---- variable-coefficient diffusion, 2-D: A u = -div(k grad u), harmonic-mean face coefficients ----
+VC_PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+
+def _k(kc, n):
+    kc = np.ascontiguousarray(kc, dtype=np.float64)
+    assert kc.shape == (n + 1, n + 1), kc.shape
+    return kc
+
+
+def residual_vc(kc, f, u):
+    """r = f - A u for A = -div(k grad .) (flux form, harmonic-mean faces); 0 on the boundary."""
+    ndim, n = _grid_n(f)
+    assert ndim == 2
+    kc = _k(kc, n)
+    r = np.empty_like(f)
+    _load().homg_oracle_residual_vc(n, _p(kc), _p(np.ascontiguousarray(f)), _p(np.ascontiguousarray(u)), _p(r))
+    return r
+
+
+def iteration_vc(n, m, mprev, omega_j, kc, Fm, dprev, e_old):
+    """One variable-coefficient HOMG iteration at level m (k injected on the lattice); returns (e_new, d_new)."""
+    kc = _k(kc, n)
+    e_new = np.empty_like(e_old)
+    d_new = np.empty(((n >> m) + 1,) * 2)
+    if dprev is None:
+        dprev = np.zeros(1)
+        mprev = -1
+    _load().homg_oracle_iteration_vc(n, m, mprev, omega_j, _p(kc), _p(Fm), _p(dprev), _p(e_old), _p(e_new),
+                                     _p(d_new))
+    return e_new, d_new
+
+
+def cycle_vc(kc, F0, levels, precision="fp64", schedule=None, max_i=32, omega_j=None):
+    """One variable-coefficient HOMG cycle on A e = F0 from e = 0 (fp64, or fp32 / bf16 storage)."""
+    ndim, n = _grid_n(F0)
+    assert ndim == 2
+    kc = _k(kc, n)
+    if omega_j is None:
+        omega_j = default_omega_j(2)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    e = np.empty_like(F0)
+    rc = _load().homg_oracle_cycle_vc(n, levels, cs, len(sched), omega_j, VC_PRECISIONS[precision], _p(kc),
+                                      _p(np.ascontiguousarray(F0)), _p(e))
+    if rc != 0:
+        raise ValueError("oracle cycle rejected its arguments (rc=%d)" % rc)
+    return e
+
+
+def solve_vc(kc, f, levels, precision="fp64", u0=None, tol=1e-10, max_cycles=100, schedule=None, max_i=32,
+             omega_j=None, div_factor=1e3):
+    """Restarted variable-coefficient solve (binary64 residual/update/norms). Returns (u, status, cycles, hist)."""
+    ndim, n = _grid_n(f)
+    assert ndim == 2
+    kc = _k(kc, n)
+    if omega_j is None:
+        omega_j = default_omega_j(2)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    u = np.zeros_like(f) if u0 is None else np.array(u0, dtype=np.float64, order="C", copy=True)
+    hist = np.zeros(max_cycles + 1)
+    cyc = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    status = _load().homg_oracle_solve_vc(n, levels, cs, len(sched), omega_j, div_factor, VC_PRECISIONS[precision],
+                                          _p(kc), _p(np.ascontiguousarray(f)), _p(u), tol, max_cycles, _p(hist),
+                                          ctypes.byref(cyc), ctypes.byref(rr))
     if status < 0:
         raise ValueError("oracle solve rejected its arguments (rc=%d)" % status)
     return u, status, cyc.value, hist[: cyc.value + 1]

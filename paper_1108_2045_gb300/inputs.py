@@ -10,6 +10,10 @@ Workloads (stand-ins for the paper's Poisson experiments of Sec. 4; the paper us
 * ``uniform_rhs``  f iid uniform[-1, 1] over the interior nodes in layout order, numpy
                    ``default_rng(seed)`` (seed 0 for the 4097^2 benchmark grid).
 * ``normal_rhs``   f iid N(0, 1), same ordering.
+* ``grf_coefficient`` k = exp(g) on the node grid, g a stationary Gaussian random field with
+                   variance sigma^2 and squared-exponential correlation exp(-r^2 / (2 ell^2)),
+                   sampled exactly by circulant embedding (seed 2 and sigma = 1, ell = 0.05 for
+                   the 2049^2 variable-coefficient workload).
 * ``uneven_batch`` a batch of 2-D problems with sides 2^k + 1, k uniform on 6..10, f iid N(0, 1)
                    (seed 1 for the 1024-problem batch benchmark).
 * ``paper_poly_rhs`` / ``paper_poly_solution``: the polynomial test problem of Sec. 4, converted
@@ -91,3 +95,22 @@ def uneven_batch(count, seed=1, kmin=6, kmax=10):
         f[1:-1, 1:-1] = rng.standard_normal((n - 1, n - 1))
         fs.append(f)
     return ks, fs
+
+
+def grf_coefficient(n, sigma=1.0, ell=0.05, seed=2):
+    """k = exp(g) on the (n+1)^2 nodes of the unit square (h = 1/n), g a stationary Gaussian random field
+    with mean 0, variance sigma^2 and correlation exp(-r^2 / (2 ell^2)).
+
+    Circulant embedding: the covariance is laid out on a periodic (2(n+1))^2 grid (periodic distance,
+    so the embedding is at least twice the domain), its FFT gives the eigenvalues (clipped at 0; for
+    ell well below the embedding period they are non-negative to rounding), and g is the inverse FFT
+    of sqrt(eigenvalues) times the FFT of real white noise N(0, 1) drawn from default_rng(seed) over
+    the periodic grid in layout order; the (n+1)^2 corner block is kept."""
+    N = 2 * (n + 1)
+    h = 1.0 / n
+    d = np.minimum(np.arange(N), N - np.arange(N)) * h
+    cov = sigma ** 2 * np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2.0 * ell ** 2))
+    lam = np.maximum(np.fft.fft2(cov).real, 0.0)
+    w = np.random.default_rng(seed).standard_normal((N, N))
+    g = np.fft.ifft2(np.sqrt(lam) * np.fft.fft2(w)).real
+    return np.ascontiguousarray(np.exp(g[: n + 1, : n + 1]))

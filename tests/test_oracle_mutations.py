@@ -15,6 +15,7 @@ import oracle
 from oracle import oracle as oracle_impl
 
 import test_oracle_pins as pins
+import test_oracle_vc as vcpins
 import test_oracle_vcycle as vpins
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "homg_oracle.c")
@@ -38,6 +39,13 @@ MUTATIONS = {
     "vcycle_no_correction": ("for (int64_t p = 0; p < cnt; ++p) em[p] = em[p] + pe[p];", ""),
     "vcycle_prolong_lattice_value": ("if (on) Ef[p] = Ec[((k / 2) * (nc + 1) + j / 2) * (nc + 1) + i / 2];", "if (on) Ef[p] = 0.5 * Ec[((k / 2) * (nc + 1) + j / 2) * (nc + 1) + i / 2];"),
     "vcycle_coarse_sweeps": ("int64_t sweeps = nm * nm > 1 ? nm * nm : 1;", "int64_t sweeps = 1;"),
+    "vc_face_arithmetic_mean": ("static double face_coef(double a, double b) { return ((2.0 * a) * b) / (a + b); }",
+                                "static double face_coef(double a, double b) { return (a + b) / 2.0; }"),
+    "vc_residual_dropped_face": ("au = au + kn * (uc - u_at2(u, n, i, j + 1));", ""),
+    "vc_residual_face_transposed": ("*ks = face_coef(kp, kc[(j - l) * side + i]);", "*ks = face_coef(kp, kc[j * side + (i - l)]);"),
+    "vc_relax_fixed_weight": ("double delta = (omega_j / D) * (hm2 * Fm[q] - ae);", "double delta = (omega_j / 4.0) * (hm2 * Fm[q] - ae);"),
+    "vc_relax_fine_coefficients": ("vc_faces(kc, n, l, i, j, &kw, &ke, &ks, &kn);\n                const double D", "vc_faces(kc, n, 1, i, j, &kw, &ke, &ks, &kn);\n                const double D"),
+    "vc_relax_dropped_diagonal_term": ("const double D = ((kw + ke) + ks) + kn;", "const double D = (kw + ke) + ks;"),
     "norm_not_squared": ("double x = v[j * (n + 1) + i]; s += x * x;", "double x = v[j * (n + 1) + i]; s += fabs(x);"),
 }
 
@@ -64,6 +72,10 @@ def run_pins():
         ("v_coarse", lambda: vpins.test_coarsest_solve_is_undamped_jacobi(2, 4)),
         ("v_dense", lambda: vpins.test_vcycle_solution_matches_dense_direct_solve(2, 4)),
         ("v_rate", lambda: vpins.test_vcycle_contraction_is_resolution_independent()),
+        ("vc_assembly", lambda: vcpins.test_residual_matches_face_assembly(8)),
+        ("vc_jacobi", lambda: vcpins.test_single_level_cycle_is_damped_jacobi(5)),
+        ("vc_coarse", lambda: vcpins.test_coarse_level_relaxation_uses_injected_coefficients(1)),
+        ("vc_dense_solve", lambda: vcpins.test_solution_matches_dense_direct_solve(16, 4)),
     ]
     failed = []
     for name, fn in checks:
