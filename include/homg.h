@@ -184,6 +184,22 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
 int homg_solve_host(homg_handle h, const double* f_host, double* u_host, double tol, int max_cycles,
                     int* cycles_out, double* relres_out);
 
+/* Switch h to the variable-coefficient operator A u = -div(k grad u) (an extension: the paper
+ * solves the Poisson equation only). Five-point flux form: each face carries the harmonic mean
+ * 2 k(p) k(q) / (k(p) + k(q)) of its two end nodes' coefficients; level m uses the same form
+ * between lattice neighbours at spacing 2^m h with k taken at the lattice nodes (injection); the
+ * HOMG relaxation (Sec. 2) becomes damped Jacobi with each node's own diagonal D (sum of its four
+ * face coefficients) and weight omega_J / D, omega_J as in the options (4/5 by default).
+ *   k  device pointer, FP64 node coefficients on the whole (n+1)^2 grid, boundary included (the
+ *      boundary faces use them), row-major with x fastest, unpadded; only read during this call
+ *      (the handle keeps its own derived coefficients). NULL switches back to the Poisson operator.
+ * Needs a 2-D handle with HOMG cycles in the fast lattice form (not strict_fp, not the whole-grid
+ * form, not the V-cycle): HOMG_EINVAL otherwise. k must be positive and finite at every node:
+ * HOMG_EINVAL otherwise (the handle then stays on the Poisson operator). Later homg_solve and
+ * homg_residual_norm calls use the operator. Allocates the coefficient arrays on first use
+ * (~1/3 more than three fine-grid arrays) and synchronises the handle's stream. */
+int homg_set_coefficient(homg_handle h, const double* k);
+
 /* ||f - A u||_2 / ||f||_2 over interior nodes for device arrays f, u (relres_out required);
  * 0 when ||f|| = 0 and u's interior is 0, +inf when ||f|| = 0 otherwise. Synchronises the stream. */
 int homg_residual_norm(homg_handle h, const double* f, const double* u, double* relres_out);

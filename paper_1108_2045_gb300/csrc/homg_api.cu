@@ -115,6 +115,15 @@ struct homg_ctx {
     double* stage_f = nullptr;  // homg_solve_host staging
     double* stage_u = nullptr;
 
+    // Variable coefficients (homg_set_coefficient): per level the east/north face coefficients and
+    // Jacobi weights in the cycle's coefficient type, and the FP64 level-0 faces of the residual.
+    bool vc = false;
+    char* vc_arena = nullptr;
+    std::vector<void*> vkx, vky, vwd;
+    double* kx0 = nullptr;
+    double* ky0 = nullptr;
+    int* dbad = nullptr;
+
     homg_stats stats{};
     char err[512] = "";
 };
@@ -401,6 +410,12 @@ void plan_cycle(homg_ctx* h) {
                 }
                 a.dnew = grid(nullptr, 0, 0);
                 if (q == c - 1 && m >= 1) a.dnew = grid(lv.d[0], lv.pitch, lv.n);
+                if (h->vc) {
+                    a.kx = h->vkx[m];
+                    a.ky = h->vky[m];
+                    a.wd = h->vwd[m];
+                    a.kpitch = lv.pitch;
+                }
                 (m == 0 ? h->partB : h->partA).push_back(op);
                 cur ^= 1;
             }
@@ -417,7 +432,7 @@ void plan_cycle(homg_ctx* h) {
 // block) become one single-block launch. Larger lattices run faster as separate launches.
 void group_coarse_block(homg_ctx* h) {
     h->block_ops.clear();
-    if (h->strict || h->exec != HOMG_EXEC_LATTICE || h->opt.cycle == HOMG_CYCLE_V) return;
+    if (h->strict || h->exec != HOMG_EXEC_LATTICE || h->opt.cycle == HOMG_CYCLE_V || h->vc) return;
     const int nb = (h->ndim == 2) ? 16 : 8;
     std::vector<Op> kept;
     std::vector<BlockOp> blk;
@@ -479,6 +494,12 @@ ResidArgs resid_args(homg_ctx* h, int stage) {
     const double hh = 1.0 / (double)h->n;
     a.inv_h2 = (double)h->n * (double)h->n;
     a.scale = h->strict ? hh * hh : h->omega * hh * hh;  // fast mode stores omega h^2 F
+    if (h->vc) {  // variable coefficients: h^2 F (each node applies its own weight)
+        a.scale = hh * hh;
+        a.kx = h->kx0;
+        a.ky = h->ky0;
+        a.kpitch = h->pitch0;
+    }
     a.part_r = h->part_r;
     a.part_f = nullptr;
     a.g0 = grid(h->L[0].g, h->L[0].pitch, h->n);
@@ -1263,6 +1284,72 @@ int homg_solve_host(homg_handle h, const double* f_host, double* u_host, double 
     return rc;
 }
 
+int homg_set_coefficient(homg_handle h, const double* k) {
+    if (!h) return HOMG_EINVAL;
+    CK(h, cudaSetDevice(h->device), "cudaSetDevice");
+    if (k && (h->ndim != 2 || h->exec != HOMG_EXEC_LATTICE || h->strict || h->opt.cycle != HOMG_CYCLE_HOMG ||
+              h->nbatch != 1))
+        return fail(h, HOMG_EINVAL,
+                    "homg_set_coefficient: variable coefficients need a 2-D handle with HOMG cycles in the fast "
+                    "lattice form%s%s");
+    if (k) {
+        const bool dbl = (h->prec == PREC_FP64);
+        const size_t ks = dbl ? sizeof(double) : sizeof(float);
+        if (!h->vc_arena) {
+            size_t off = 0;
+            auto take = [&](size_t bytes) { off = (size_t)round_up((int64_t)off, 256); size_t o = off; off += bytes; return o; };
+            std::vector<size_t> ox, oy, ow;
+            for (int m = 0; m < h->levels; ++m) {
+                const size_t bytes = (size_t)grid_elems(2, h->L[m].n, h->L[m].pitch) * ks;
+                ox.push_back(take(bytes));
+                oy.push_back(take(bytes));
+                ow.push_back(take(bytes));
+            }
+            const size_t b0 = (size_t)grid_elems(2, h->n, h->pitch0) * sizeof(double);
+            const size_t o0x = dbl ? 0 : take(b0), o0y = dbl ? 0 : take(b0);
+            const size_t obad = take(sizeof(int));
+            CK(h, cudaMalloc(&h->vc_arena, (size_t)round_up((int64_t)off, 256)), "allocating the coefficient arrays");
+            for (int m = 0; m < h->levels; ++m) {
+                h->vkx.push_back(h->vc_arena + ox[m]);
+                h->vky.push_back(h->vc_arena + oy[m]);
+                h->vwd.push_back(h->vc_arena + ow[m]);
+            }
+            h->kx0 = dbl ? (double*)h->vkx[0] : (double*)(h->vc_arena + o0x);
+            h->ky0 = dbl ? (double*)h->vky[0] : (double*)(h->vc_arena + o0y);
+            h->dbad = (int*)(h->vc_arena + obad);
+        }
+        CK(h, cudaMemsetAsync(h->dbad, 0, sizeof(int), h->stream), "cudaMemsetAsync");
+        for (int m = 0; m < h->levels; ++m)
+            CK(h, launch_vc_setup(k, h->n, m, dbl, h->vkx[m], h->vky[m], h->vwd[m], h->L[m].pitch, h->opt.omega_j,
+                                  h->dbad, h->stream),
+               "coefficient set-up kernel");
+        if (!dbl)
+            CK(h, launch_vc_setup(k, h->n, 0, true, h->kx0, h->ky0, nullptr, h->pitch0, h->opt.omega_j, h->dbad,
+                                  h->stream),
+               "coefficient set-up kernel");
+        int bad = 0;
+        CK(h, cudaMemcpyAsync(&bad, h->dbad, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
+        CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        if (bad) {
+            h->vc = false;
+            plan_cycle(h);
+            group_coarse_block(h);
+            destroy_graph(h->gfirst);
+            destroy_graph(h->gcont);
+            return fail(h, HOMG_EINVAL, "homg_set_coefficient: k must be positive and finite at every node%s%s");
+        }
+    }
+    h->vc = (k != nullptr);
+    plan_cycle(h);
+    group_coarse_block(h);
+    if (!h->block_ops.empty())
+        CK(h, cudaMemcpy(h->dblock_ops, h->block_ops.data(), h->block_ops.size() * sizeof(BlockOp), cudaMemcpyHostToDevice),
+           "copying the coarse-lattice op list");
+    destroy_graph(h->gfirst);
+    destroy_graph(h->gcont);
+    return HOMG_OK;
+}
+
 int homg_residual_norm(homg_handle h, const double* f, const double* u, double* relres_out) {
     if (!h) return HOMG_EINVAL;
     if (!f || !u || !relres_out) return fail(h, HOMG_EINVAL, "homg_residual_norm: null argument%s%s");
@@ -1277,6 +1364,11 @@ int homg_residual_norm(homg_handle h, const double* f, const double* u, double* 
     a.inv_h2 = (double)h->n * (double)h->n;
     a.part_r = h->part_r;
     a.part_f = h->part_f;
+    if (h->vc) {
+        a.kx = h->kx0;
+        a.ky = h->ky0;
+        a.kpitch = h->pitch0;
+    }
     CK(h, launch_residual(h->ndim, h->prec, h->strict, a, h->n, h->stream), "residual kernel");
     FinalizeArgs fa = fin_args(h, FIN_NORM, nullptr);
     fa.part_f = h->part_f;
@@ -1309,6 +1401,7 @@ void homg_destroy(homg_handle h) {
     destroy_graph(h->gcont);
     for (cudaEvent_t e : h->sev) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
+    if (h->vc_arena) cudaFree(h->vc_arena);
     if (h->stage_f) cudaFree(h->stage_f);
     if (h->stage_u) cudaFree(h->stage_u);
     if (h->hstate) cudaFreeHost(h->hstate);

@@ -83,6 +83,13 @@ struct IterArgs {
     int rows = 0;   // fast 2-D/3-D kernels: nodes per thread along the march (0: size heuristic)
     float omega_f;  // the same, rounded to binary32, for the binary32-arithmetic kernels
     float c1_f;
+    // Variable coefficients (2-D lattice form; nullptr: Poisson): per lattice node the east-face
+    // and north-face coefficients and the Jacobi weight omega_J / D, in double for FP64 cycles and
+    // float otherwise, rows of `kpitch` elements. The source g is then h_m^2 F_m (not omega-scaled).
+    const void* kx = nullptr;
+    const void* ky = nullptr;
+    const void* wd = nullptr;
+    int64_t kpitch = 0;
 };
 
 // Lattice form, level change: fine lattice G (stride 1) from the coarser lattice's final iterate
@@ -113,6 +120,9 @@ struct ResidArgs {
     int64_t part_bstride = 0;  // batch: partials between consecutive problems
     int batch = 0;             // batch: st points at per-problem states, problem z = blockIdx.z
     int nb = 1;
+    const double* kx = nullptr;  // variable coefficients (2-D): east / north face coefficients of
+    const double* ky = nullptr;  // the fine grid, rows of kpitch; nullptr: Poisson
+    int64_t kpitch = 0;
 };
 
 // Full weighting g_c = 4 * FW(g_f) (the factor 4 = 2^2 keeps the source pre-scaled by h_m^2),
@@ -188,6 +198,11 @@ cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops
 cudaError_t launch_vresid(int ndim, int prec, bool strict, const VResidArgs& a, cudaStream_t s);
 cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAddArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+// Variable coefficients of level m from the node coefficient k ((n+1)^2, unpadded, FP64): for each
+// lattice node the east- and north-face harmonic means and (wd != nullptr) the weight omega_J / D,
+// stored as double (dbl) or float. Sets *bad when a node value is not positive and finite.
+cudaError_t launch_vc_setup(const double* k, int n, int m, bool dbl, void* kx, void* ky, void* wd, int64_t pitch,
+                            double omega_j, int* bad, cudaStream_t s);
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s);
 
 // Message reported by homg_last_error(NULL) (errors of calls made without a handle).

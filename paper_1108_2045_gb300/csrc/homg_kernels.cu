@@ -682,6 +682,121 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
     }
 }
 
+// Coefficient storage of the variable-coefficient kernels: double for FP64 cycles, float otherwise.
+template <typename T> struct KT { using type = float; };
+template <> struct KT<double> { using type = double; };
+
+// Fast variable-coefficient iteration (2-D lattice form): damped Jacobi with each node's own weight
+// wd = omega_J / D on -div(k grad .) with harmonic-mean faces,
+//   v' = (1 - omega_J) v + wd (h_m^2 F + k_W w + k_E e + k_S s + k_N n)
+// = 6 FP instructions per node. kx holds each node's east-face coefficient (the west face is the
+// left neighbour's), ky its north face; the south face rides down the march in a register. The
+// first iteration of a cycle (e_old = 0) reduces to v' = wd h_m^2 F.
+template <int PEND, bool WD, typename T>
+__global__ void __launch_bounds__(JX) k_jacobi2_vc(IterArgs a, int rows) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    using K = typename KT<T>::type;
+    const int n = a.e_new.n;
+    const int i = blockIdx.x * JX + threadIdx.x + 1;
+    if (i >= n) return;
+    const int j0 = blockIdx.y * rows + 1;
+    const int j1 = min(j0 + rows, n);
+    const T* __restrict__ E = cp<T>(a.e_old);
+    const int64_t pe = a.e_old.pitch;
+    T* __restrict__ O = wp<T>(a.e_new);
+    const int64_t po = a.e_new.pitch;
+    const T* __restrict__ G = cp<T>(a.g);
+    const int64_t pg = a.g.pitch;
+    const K* __restrict__ KX = static_cast<const K*>(a.kx);
+    const K* __restrict__ KY = static_cast<const K*>(a.ky);
+    const K* __restrict__ W = static_cast<const K*>(a.wd);
+    const int64_t pk = a.kpitch;
+    const C c1 = pick<C>(a.c1, a.c1_f);
+    if (E == nullptr) {
+        for (int j = j0; j < j1; ++j) {
+            const C v = (C)__ldg(W + (int64_t)j * pk + i) * St<T>::ld(G + (int64_t)j * pg + i);
+            if (WD) wp<T>(a.dnew)[(int64_t)j * a.dnew.pitch + i] = St<T>::put(v);
+            O[(int64_t)j * po + i] = St<T>::put(v);
+        }
+        return;
+    }
+    const int lpm = PEND ? (1 << a.mp) - 1 : 0;
+    ColumnInterp2<T> ci;
+    if (PEND == 1) {
+        ci.d = cp<T>(a.dprev) + (i >> 1);
+        ci.d2 = nullptr;
+        ci.pitch = a.dprev.pitch;
+        ci.pitch2 = 0;
+        ci.hx = (i & 1) ? (C)0.5 : (C)0;
+    }
+    C vs = St<T>::ld(E + (int64_t)(j0 - 1) * pe + i);
+    C vc = St<T>::ld(E + (int64_t)j0 * pe + i);
+    C ks = (C)__ldg(KY + (int64_t)(j0 - 1) * pk + i);
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const T* row = E + (int64_t)j * pe + i;
+        const C vn = St<T>::ld(row + pe);
+        const C w = St<T>::ld(row - 1), e = St<T>::ld(row + 1);
+        const C g = St<T>::ld(G + (int64_t)j * pg + i);
+        const K* kr = KX + (int64_t)j * pk + i;
+        const C kw = (C)__ldg(kr - 1), ke = (C)__ldg(kr);
+        const C kn = (C)__ldg(KY + (int64_t)j * pk + i);
+        const C wd = (C)__ldg(W + (int64_t)j * pk + i);
+        C t = fma(kw, w, g);
+        t = fma(ke, e, t);
+        t = fma(ks, vs, t);
+        t = fma(kn, vn, t);
+        C v = fma(c1, vc, wd * t);
+        if (WD) wp<T>(a.dnew)[(int64_t)j * a.dnew.pitch + i] = St<T>::put(v - vc);
+        if (PEND == 1) {
+            const C sv = ci.at(j);
+            v += ((i | j) & 1) ? sv : (C)0;
+        }
+        if (PEND == 2 && ((i | j) & lpm)) v += interp<2, false, false, T>(a.dprev, a.dprev, a.mp, i, j, 0);
+        O[(int64_t)j * po + i] = St<T>::put(v);
+        ks = kn;
+        vs = vc;
+        vc = vn;
+    }
+}
+
+// Harmonic mean ((2 a) b) / (a + b) of two node coefficients in round-to-nearest steps (the same
+// value, bit for bit, whichever end comes first).
+__device__ __forceinline__ double face_coef(double a, double b) {
+    return __ddiv_rn(__dmul_rn(__dmul_rn(2.0, a), b), __dadd_rn(a, b));
+}
+
+// Coefficients of level m, one thread per lattice node (I, J) of the (n_m+1)^2 compact lattice:
+// east face (I < n_m), north face (J < n_m), and at interior nodes the weight
+// omega_J / (((k_W + k_E) + k_S) + k_N).
+template <typename K>
+__global__ void k_vc_setup(const double* __restrict__ k, int n, int m, K* kx, K* ky, K* wd, int64_t pitch,
+                           double omega_j, int* bad) {
+    const int nm = n >> m, l = 1 << m;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I > nm || J > nm) return;
+    const int64_t side = n + 1;
+    const int64_t i = (int64_t)I << m, j = (int64_t)J << m;
+    const double kp = k[j * side + i];
+    if (!(kp > 0.0) || !isfinite(kp)) atomicOr(bad, 1);
+    const int64_t q = (int64_t)J * pitch + I;
+    const double ke = (I < nm) ? face_coef(kp, k[j * side + i + l]) : 0.0;
+    const double kn = (J < nm) ? face_coef(kp, k[(j + l) * side + i]) : 0.0;
+    kx[q] = (K)ke;
+    ky[q] = (K)kn;
+    if (wd) {
+        double w = 0.0;
+        if (I > 0 && J > 0 && I < nm && J < nm) {
+            const double kw = face_coef(kp, k[j * side + i - l]);
+            const double ks = face_coef(kp, k[(j - l) * side + i]);
+            w = __ddiv_rn(omega_j, __dadd_rn(__dadd_rn(__dadd_rn(kw, ke), ks), kn));
+        }
+        wd[q] = (K)w;
+    }
+}
+
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
 // stride-2 interpolant of Gc - dl, formed along each marching column (see ColumnInterp2).
 template <typename T>
@@ -974,7 +1089,7 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
 
 // Fast update + residual (2-D): one column per thread marching along y, u_new = u_in + e formed
 // once per node for the column and once for each side neighbour; 10 FP64 instructions per node.
-template <typename T>
+template <typename T, bool VC>
 __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     pdl_begin();
     if (!batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
@@ -999,12 +1114,26 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     double rr = 0.0, ff = 0.0;
     if (active) {
         double vs = un(i, j0 - 1), vc = un(i, j0);
+        double ks = VC ? __ldg(a.ky + (int64_t)(j0 - 1) * a.kpitch + i) : 0.0;
         for (int j = j0; j < j1; ++j) {
             const double vn = un(i, j + 1);
             const double w = un(i - 1, j), e = un(i + 1, j);
-            const double sum = (w + e) + (vs + vn);
             const double fv = __ldg(F + (int64_t)j * pf + i);
-            const double r = fma(a.inv_h2, fma(-4.0, vc, sum), fv);
+            double r;
+            if (VC) {  // r = f - (D u - sum k_nb u_nb) / h^2, D = sum of the four face coefficients
+                const double* kr = a.kx + (int64_t)j * a.kpitch + i;
+                const double kw = __ldg(kr - 1), ke = __ldg(kr), kn = __ldg(a.ky + (int64_t)j * a.kpitch + i);
+                double t = kw * w;
+                t = fma(ke, e, t);
+                t = fma(ks, vs, t);
+                t = fma(kn, vn, t);
+                const double d = ((kw + ke) + ks) + kn;
+                r = fma(-a.inv_h2, fma(d, vc, -t), fv);
+                ks = kn;
+            } else {
+                const double sum = (w + e) + (vs + vn);
+                r = fma(a.inv_h2, fma(-4.0, vc, sum), fv);
+            }
             if (a.u_out.p) a.u_out.p[(int64_t)j * a.u_out.pitch + i] = vc;
             if (a.g0.p) wp<T>(a.g0)[(int64_t)j * a.g0.pitch + i] = St<T>::put(St<T>::from_d(a.scale * r));
             rr = fma(r, r, rr);
@@ -1066,6 +1195,18 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 g, dim3 b, cudaStream_t s, A
 template <typename T>
 cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) {
     const int n = a.e_new.n;
+    if (a.kx != nullptr) {  // variable coefficients: 2-D fast lattice form only (checked by the host)
+        const bool wd = a.dnew.p != nullptr;
+        const int rows = a.rows > 0 ? a.rows : march_rows(2, n, a.nb);
+        const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows)), b(JX);
+        const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
+#define JVC(P, W) launch_k(k_jacobi2_vc<P, W, T>, g, b, s, a, rows)
+        if (pend == 0) { if (wd) JVC(0, true); else JVC(0, false); }
+        else if (pend == 1) { if (wd) JVC(1, true); else JVC(1, false); }
+        else { if (wd) JVC(2, true); else JVC(2, false); }
+#undef JVC
+        return cudaGetLastError();
+    }
     if (!strict && a.m == 0 && a.e_old.p != nullptr) {
         const bool wd = a.dnew.p != nullptr;
         const int rows = a.rows > 0 ? a.rows : march_rows(ndim, n, a.nb);
@@ -1143,7 +1284,8 @@ cudaError_t residual_t(int ndim, bool strict, const ResidArgs& a, int n, cudaStr
     if (ndim == 2) g.z = (unsigned)a.nb;
     if (ndim == 2) {
         if (strict) launch_k(k_residual<2, true, T>, g, dim3(BX, BY), s, a, n);
-        else launch_k(k_residual2_fast<T>, g, dim3(JX), s, a, n);
+        else if (a.kx) launch_k(k_residual2_fast<T, true>, g, dim3(JX), s, a, n);
+        else launch_k(k_residual2_fast<T, false>, g, dim3(JX), s, a, n);
     } else if (strict) {
         launch_k(k_residual<3, true, T>, g, dim3(BX, BY), s, a, n);
     } else {
@@ -1207,6 +1349,15 @@ cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a,
 
 cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s) {
     DISPATCH_PREC(prec, restrict_t<T>(ndim, strict, a, s));
+}
+
+cudaError_t launch_vc_setup(const double* k, int n, int m, bool dbl, void* kx, void* ky, void* wd, int64_t pitch,
+                            double omega_j, int* bad, cudaStream_t s) {
+    const int nm = n >> m;
+    const dim3 b(32, 8), g((unsigned)((nm + 1 + 31) / 32), (unsigned)((nm + 1 + 7) / 8));
+    if (dbl) k_vc_setup<double><<<g, b, 0, s>>>(k, n, m, (double*)kx, (double*)ky, (double*)wd, pitch, omega_j, bad);
+    else k_vc_setup<float><<<g, b, 0, s>>>(k, n, m, (float*)kx, (float*)ky, (float*)wd, pitch, omega_j, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, int nb, cudaStream_t s) {

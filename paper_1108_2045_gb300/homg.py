@@ -33,6 +33,7 @@ EXPORTS = [
     "homg_solve",
     "homg_solve_host",
     "homg_residual_norm",
+    "homg_set_coefficient",
     "homg_get_history",
     "homg_get_stats",
     "homg_last_error",
@@ -119,6 +120,7 @@ def load(path=LIB_PATH):
     lib.homg_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp]
     lib.homg_solve_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp]
     lib.homg_residual_norm.argtypes = [vp, vp, vp, dp]
+    lib.homg_set_coefficient.argtypes = [vp, vp]
     lib.homg_get_history.argtypes = [vp, dp, ctypes.c_int]
     lib.homg_get_stats.argtypes = [vp, ctypes.POINTER(homg_stats)]
     lib.homg_last_error.argtypes = [vp]
@@ -327,6 +329,12 @@ def homg_residual_norm(handle, f, u):
     return rr.value
 
 
+def homg_set_coefficient(handle, k):
+    """Switch the handle to A u = -div(k grad u) with the FP64 device tensor k of node coefficients
+    (None: back to the Poisson operator)."""
+    _check(load().homg_set_coefficient(handle, None if k is None else _devptr(k, "k")), handle)
+
+
 def homg_residual_norm_noalloc(f, u, stream=None):
     """||f - A u|| / ||f|| of device tensors without a handle; the library allocates nothing for it
     (its scratch is a fixed static device array shared by all calls: do not overlap calls)."""
@@ -374,6 +382,9 @@ class Solver:
 
     def residual_norm(self, f, u):
         return homg_residual_norm(self.handle, f, u)
+
+    def set_coefficient(self, k):
+        return homg_set_coefficient(self.handle, k)
 
     def history(self):
         return homg_get_history(self.handle)
