@@ -38,6 +38,9 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_OPS = 0.625e12
 
 
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -151,7 +154,7 @@ CFG3_SIDE = 512
 CFG3_LEVELS = 9
 
 
-def run_cfg3(args, homg, inputs, stream, barrier):
+def run_cfg3(args, homg, inputs, stream, barrier, pending):
     """3-D Poisson, 7-point stencil, 513^3 nodes, 9 levels: FP64 cycles against FP32 and bfloat16
     cycles (FP64 residual, update and norms; iterative refinement) to relative residual 1e-10, for
     f = 3 pi^2 sin sin sin and for f iid N(0, 1) (seed 0). Reports time to 1e-10, cycles, the error
@@ -159,8 +162,6 @@ def run_cfg3(args, homg, inputs, stream, barrier):
     c_h prod sin(pi x_k), c_h = pi^2 h^2 / (4 sin^2(pi h / 2))."""
     import numpy as np
     import torch
-
-    import oracle
 
     n = CFG3_SIDE
     out = {"workload": "3-D Poisson -Lap u = f, 7-point, 513^3 nodes, 9 levels, MaxI=32, to relres 1e-10"}
@@ -204,11 +205,8 @@ def run_cfg3(args, homg, inputs, stream, barrier):
                 r["rel_err_vs_discrete_exact"] = float(torch.linalg.vector_norm(u - exact) / torch.linalg.vector_norm(exact))
                 del exact
             if rhs == "normal" and prec == "fp32" and args.cfg3_oracle_check:
-                # the oracle's own FP64 residual of the mixed-precision solution
-                fn = f.cpu().numpy()
-                un = u.cpu().numpy()
-                r["oracle_relres"] = oracle.norm_interior(oracle.residual(fn, un)) / oracle.norm_interior(fn)
-                del fn, un
+                # checked later, by the oracle's own FP64 residual (CPU leg)
+                pending.append((r, "poisson", None, f.cpu().numpy(), u.cpu().numpy()))
             res[prec] = r
         out[rhs] = res
         del f, u, ref
@@ -216,12 +214,12 @@ def run_cfg3(args, homg, inputs, stream, barrier):
     return out
 
 
-def run_cfg4(args, homg, stream, barrier):
+def run_cfg4(args, homg, stream, barrier, pending):
     """1024 independent 2-D Poisson problems of uneven sizes in one batched solve to relres 1e-10
     each: FP32 cycles with FP64 refinement (FP64 cycles beside it). Per-problem solve times are
     device-clock times from a problem's initial residual test to its convergence. Sampled problems
     (two per size) are checked with the oracle's own FP64 residual; the oracle's time for the whole
-    batch is extrapolated from one timed oracle solve per size."""
+    batch is extrapolated from one timed oracle solve per size (both in the CPU leg)."""
     import numpy as np
     import torch
 
@@ -260,34 +258,165 @@ def run_cfg4(args, homg, stream, barrier):
              "tuned_rows_level0": dict(zip([str(x) for x in st["sides"]], st["rows"])),
              "tuned_sweep_us_level0": dict(zip([str(x) for x in st["sides"]], st["tuned_us"]))}
         if prec == "fp32" and args.cfg4_oracle_check:
-            import oracle
-
-            oracle.build()
-            worst = 0.0
-            for i in sample:
-                un = us[i].cpu().numpy()
-                worst = max(worst, oracle.norm_interior(oracle.residual(fs_np[i], un)) / oracle.norm_interior(fs_np[i]))
-            r["oracle_relres_max_sampled"] = worst
             r["oracle_sample"] = "two problems per k (the first of each size in batch order)"
+            for i in sample:  # checked later by the oracle's own FP64 residual (CPU leg)
+                pending.append((r, "poisson_max", None, fs_np[i], us[i].cpu().numpy()))
         out[prec] = r
     del fs, us
     torch.cuda.empty_cache()
-    if args.cfg4_oracle_time and not args.no_cpu_baseline:
-        import oracle
-
-        oracle.build()
-        est, per_k = 0.0, {}
-        for k in range(6, 11):
-            i = int(np.flatnonzero(ks_arr == k)[0])
-            t0 = time.perf_counter()
-            _, status, cyc, _ = oracle.solve_mixed(fs_np[i], k, precision="fp32", tol=TOL, max_cycles=MAX_CYCLES)
-            dt = time.perf_counter() - t0
-            per_k[str(k)] = {"seconds": dt, "cycles": cyc, "status": status}
-            est += dt * int((ks_arr == k).sum())
-        out["cpu_oracle"] = {"value": unknowns / est, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one FP32-cycle oracle solve per size, timed and multiplied by the problems "
-                                       "of that size (%.0f s estimated for the batch)" % est, "per_k": per_k}
+    if args.cfg4_oracle_time:
+        per_k = {k: (fs_np[int(np.flatnonzero(ks_arr == k)[0])], int((ks_arr == k).sum())) for k in range(6, 11)}
+        pending.append((out, "batch_time", None, per_k, unknowns))
     return out
+
+
+CFG5_SIDE = 2048
+CFG5_LEVELS = 11
+
+
+def run_cfg5(args, homg, stream, barrier, pending):
+    """Variable-coefficient diffusion -div(k grad u) = f on 2049^2 nodes, 11 levels, k = exp(g) with g
+    a Gaussian random field (sigma 1, squared-exponential correlation length 0.05, seed 2), f iid
+    N(0, 1) (seed 0), to relres 1e-10: plain HOMG (FP64 and FP32 cycles) against the learned
+    corrector ahead of every cycle. The corrector is trained here, from scratch, on 20,000 64 x 64
+    patches of error/residual pairs the solver produces on four other right-hand sides (seeds
+    100-103; iterates after 2, 3 and 4 cycles, whose errors a 9 x 9 receptive field predicts best);
+    training time is reported, not timed as a solve."""
+    import numpy as np
+    import torch
+
+    from paper_1108_2045_gb300 import inputs, learned
+
+    n, L = CFG5_SIDE, CFG5_LEVELS
+    kc = inputs.grf_coefficient(n, sigma=1.0, ell=0.05, seed=2)
+    f_np = inputs.normal_rhs(n, 2, seed=0)
+    k = torch.from_numpy(kc).cuda()
+    f = torch.from_numpy(f_np).cuda()
+    u = torch.zeros_like(f)
+    unknowns = float((n - 1) ** 2)
+    out = {"workload": "2-D -div(k grad u) = f, 5-point flux form with harmonic-mean faces, 2049^2 nodes, 11 levels, "
+                       "k = exp(GRF sigma 1, ell 0.05, seed 2), f iid N(0,1) seed 0, to relres 1e-10",
+           "k_range": [float(kc.min()), float(kc.max())]}
+
+    def timed(fn, steps):
+        fn()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            res = fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / steps, res
+
+    plain = {}
+    for prec in ("fp64", "fp32"):
+        with homg.Solver(2, n + 1, L, max_i=MAX_I, precision=prec) as s:
+            s.set_stream(stream)
+            s.set_coefficient(k)
+
+            def solve():
+                u.zero_()
+                return s.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+
+            ms, (st, cyc, rr) = timed(solve, args.cfg5_steps)
+        plain[prec] = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms, "unknowns_per_s": unknowns / (ms * 1e-3)}
+    out["plain"] = plain
+    with homg.Solver(2, n + 1, L, max_i=MAX_I, precision="fp32") as s, homg.Net() as net:
+        s.set_stream(stream)
+        net.set_stream(stream)
+        s.set_coefficient(k)
+        net.set_params(learned.init_params(args.cfg5_seed))
+        t0 = time.perf_counter()
+        fs_train = [torch.from_numpy(inputs.normal_rhs(n, 2, seed=100 + i)).cuda() for i in range(4)]
+        X, T = learned.make_training_set(s, net, fs_train, cycles=(2, 3, 4), patches=args.cfg5_patches, seed=1)
+        data_s = time.perf_counter() - t0
+        target_ms = float((T.double() ** 2).mean())
+        del fs_train
+        losses, train_s = learned.train(net, X, T, epochs=args.cfg5_epochs, seed=2)
+        del X, T
+        out["training"] = {"patches": args.cfg5_patches, "patch": 64, "epochs": args.cfg5_epochs, "batch": 64,
+                           "iterates_after_cycles": [2, 3, 4],
+                           "data_seconds": data_s, "train_seconds": train_s, "loss_per_epoch": losses,
+                           "target_mean_square": target_ms, "variance_explained": 1.0 - losses[-1] / target_ms}
+        # the network alone on the full grid: tensor-core convolution throughput
+        x_img = torch.zeros(1, n + 1, 2, n + 1, 8, dtype=torch.bfloat16, device="cuda")
+        y_img = torch.zeros(1, n + 1, n + 1, dtype=torch.float32, device="cuda")
+        u.zero_()
+        homg.homg_features(s.handle, f, u, x_img)
+        fwd_ms, _ = timed(lambda: net.forward(x_img, y_img), 5)
+        px = float((n + 1) ** 2)
+        flop_real = px * 2 * 9 * (2 * 32 + 32 * 32 * 2 + 32 * 1)
+        flop_exec = px * 2 * 9 * (16 * 32 + 32 * 32 * 2 + 32 * 16)
+        peaks, psrc = measured_peaks()
+        bf16_peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS)
+        out["network"] = {"forward_ms": fwd_ms, "algorithmic_tflops": flop_real / (fwd_ms * 1e-3) / 1e12,
+                          "executed_tflops": flop_exec / (fwd_ms * 1e-3) / 1e12,
+                          "bf16_peak_tflops": bf16_peak, "peak_source": psrc,
+                          "frac_of_bf16_peak": flop_exec / (fwd_ms * 1e-3) / 1e12 / bf16_peak,
+                          "note": "4 tcgen05 convolution launches; executed FLOPs count the zero-padded channels "
+                                  "(2 -> 16 inputs of layer 1, 1 -> 16 outputs of layer 4)"}
+        del x_img, y_img
+        learned_res = {}
+        for prec in ("fp32", "fp64"):
+            with homg.Solver(2, n + 1, L, max_i=MAX_I, precision=prec) as s2:
+                s2.set_stream(stream)
+                s2.set_coefficient(k)
+
+                def lsolve():
+                    u.zero_()
+                    return homg.homg_solve_learned(s2.handle, net, f, u, tol=TOL, max_cycles=MAX_CYCLES)
+
+                ms, (st, cyc, rr, acc) = timed(lsolve, args.cfg5_steps)
+            r = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms, "unknowns_per_s": unknowns / (ms * 1e-3),
+                 "proposals_kept": int(sum(acc)), "speedup_vs_plain_fp64": plain["fp64"]["ms_per_solve"] / ms,
+                 "speedup_vs_plain_same_precision": plain[prec]["ms_per_solve"] / ms}
+            if prec == "fp32" and args.cfg5_oracle_check:
+                pending.append((r, "vc", kc, f_np, u.cpu().numpy()))
+            learned_res[prec] = r
+        out["learned"] = learned_res
+    if args.cfg5_oracle_time:
+        pending.append((out, "vc_time", kc, f_np, plain["fp64"]["cycles"]))
+    del f, u, k
+    torch.cuda.empty_cache()
+    return out
+
+
+def cpu_leg(pending):
+    """Everything the oracle does in a bench run (the CPU-baseline leg): its own FP64 residual of
+    results the GPU legs kept, and its timing on samples of their workloads."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    for target, kind, kc, a, b in pending:
+        if kind in ("poisson", "poisson_max"):
+            rr = oracle.norm_interior(oracle.residual(a, b)) / oracle.norm_interior(a)
+            key = "oracle_relres" if kind == "poisson" else "oracle_relres_max_sampled"
+            target[key] = max(rr, target.get(key, 0.0))
+        elif kind == "vc":
+            target["oracle_relres"] = oracle.norm_interior(oracle.residual_vc(kc, a, b)) / oracle.norm_interior(a)
+        elif kind == "batch_time":
+            est, per_k = 0.0, {}
+            for kk, (fk, cnt) in a.items():
+                t0 = time.perf_counter()
+                _, status, cyc, _ = oracle.solve_mixed(fk, kk, precision="fp32", tol=TOL, max_cycles=MAX_CYCLES)
+                dt = time.perf_counter() - t0
+                per_k[str(kk)] = {"seconds": dt, "cycles": cyc, "status": status}
+                est += dt * cnt
+            target["cpu_oracle"] = {"value": b / est, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "one FP32-cycle oracle solve per size, timed and multiplied by the problems "
+                                              "of that size (%.0f s estimated for the batch)" % est, "per_k": per_k}
+        elif kind == "vc_time":
+            t0 = time.perf_counter()
+            oracle.cycle_vc(kc, a, CFG5_LEVELS)
+            dt = time.perf_counter() - t0
+            n = kc.shape[0] - 1
+            target["cpu_oracle"] = {"value": (n - 1) ** 2 / (dt * b), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "one FP64 variable-coefficient oracle cycle on the 2049^2 grid (%.1f s), "
+                                              "scaled by the %d cycles plain HOMG takes" % (dt, b)}
 
 
 def run_reference(args):
@@ -478,8 +607,10 @@ def run(args):
                           "homg_ms_over_v_ms": (homg_ms / vms) if homg_ms else None,
                           "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
                                                      for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
-    cfg3 = run_cfg3(args, homg, inputs, stream, barrier) if (args.cfg3_steps > 0 and world == 1) else None
-    cfg4 = run_cfg4(args, homg, stream, barrier) if (args.cfg4_steps > 0 and world == 1) else None
+    pending = []  # oracle work of the CPU leg (rank 0, one GPU only)
+    cfg3 = run_cfg3(args, homg, inputs, stream, barrier, pending) if (args.cfg3_steps > 0 and world == 1) else None
+    cfg4 = run_cfg4(args, homg, stream, barrier, pending) if (args.cfg4_steps > 0 and world == 1) else None
+    cfg5 = run_cfg5(args, homg, stream, barrier, pending) if (args.cfg5_steps > 0 and world == 1) else None
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
     launches = sum(s["cycles"] * s["fine_iterations_per_cycle"] for s in stats)
@@ -532,8 +663,11 @@ def run(args):
         line["cfg3_3d"] = cfg3
     if cfg4:
         line["cfg4_batched"] = cfg4
+    if cfg5:
+        line["cfg5_learned"] = cfg5
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_cpu_baseline(f_np, stats[-1]["cycles"])
+        cpu_leg(pending)
     solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -561,6 +695,12 @@ def main():
     p.add_argument("--cfg4-steps", type=int, default=2, help="timed batched solves of the 1024-problem batch (0: skip)")
     p.add_argument("--no-cfg4-oracle-check", dest="cfg4_oracle_check", action="store_false")
     p.add_argument("--no-cfg4-oracle-time", dest="cfg4_oracle_time", action="store_false")
+    p.add_argument("--cfg5-steps", type=int, default=2, help="timed solves per form of the 2049^2 variable-coefficient workload (0: skip)")
+    p.add_argument("--cfg5-epochs", type=int, default=6, help="training epochs of the learned corrector")
+    p.add_argument("--cfg5-patches", type=int, default=20000)
+    p.add_argument("--cfg5-seed", type=int, default=0, help="seed of the network's initial parameters")
+    p.add_argument("--no-cfg5-oracle-check", dest="cfg5_oracle_check", action="store_false")
+    p.add_argument("--no-cfg5-oracle-time", dest="cfg5_oracle_time", action="store_false")
     p.add_argument("--no-cfg3-oracle-check", dest="cfg3_oracle_check", action="store_false")
     args = p.parse_args()
     if args.warmup < 3:

@@ -1,0 +1,110 @@
+/*
+ * Learned corrector for the HOMG restart loop -- C ABI.
+ *
+ * The paper has no learned component: this is an extension. A small convolutional network maps
+ * the residual of the current iterate (and log k) to a proposed correction; the plain solver
+ * judges every proposal with its FP64 residual and keeps it only when the residual norm drops,
+ * then runs the ordinary HOMG cycle (Sec. 2 and the restart of Sec. 4) on the result. The
+ * network runs on the tcgen05 tensor cores in bfloat16 with binary32 accumulation; it is trained
+ * by this library's own kernels on error/residual pairs that the solver itself produces.
+ *
+ * Network (fixed): four 3x3 convolutions, zero padding, 2 -> 32 -> 32 -> 32 -> 1 channels, ReLU
+ * after the first three. Parameters are binary32 ("master"), flat, per layer l = 0..3 the weights
+ * W_l[out][in][3][3] (row-major) followed by the biases b_l[out]; homg_net_param_count() values.
+ * Weights are rounded to bfloat16 for every use; hidden activations are stored in bfloat16.
+ *
+ * Image layout (device, bfloat16 bit patterns as uint16): B images of H x W pixels with 16
+ * channels in two groups of 8, element (b, c, y, x) at ((b*H + y)*2 + c/8)*W*8 + x*8 + c%8.
+ * Channel 0 = x_0, channel 1 = x_1, channels 2..15 must be 0. Outputs and targets: binary32,
+ * [B][H][W].
+ *
+ * Features of a solver grid (homg_features): x_0(p) = h^2 r(p) / (D(p) rho) at interior nodes
+ * (0 on the boundary), x_1(p) = log k(p), with r = f - A u (FP64), D(p) the sum of the node's four
+ * face coefficients and rho the root mean square of h^2 r / D over the interior. The network's
+ * output y is a correction in units of rho: u <- u + rho y.
+ *
+ * Return codes are those of homg.h. Every call synchronises the handle's stream unless stated.
+ */
+#ifndef HOMG_NET_H
+#define HOMG_NET_H
+
+#include <stdint.h>
+
+#include "homg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct homg_net* homg_net_handle;
+
+#define HOMG_NET_LAYERS 4
+#define HOMG_NET_WIDTH 32
+#define HOMG_NET_IN 2
+
+/* Number of binary32 parameters of the network (weights and biases of the four layers). */
+int64_t homg_net_param_count(void);
+
+/* Create a network on the current device with all parameters 0 and fresh Adam state. Device
+ * scratch for activations is allocated by later calls as image sizes require. */
+int homg_net_create(homg_net_handle* out);
+
+/* Use `stream` (a cudaStream_t, NULL = legacy default stream) for every later call on net. */
+int homg_net_set_stream(homg_net_handle net, void* stream);
+
+/* Copy `count` (= homg_net_param_count()) host binary32 parameters in / out. Setting parameters
+ * resets the Adam state and the step counter. HOMG_EINVAL for a wrong count or null pointer. */
+int homg_net_set_params(homg_net_handle net, const float* params, int64_t count);
+int homg_net_get_params(homg_net_handle net, float* params, int64_t count);
+
+/* Copy the parameter gradients of the last homg_net_train_step (same order and count as the
+ * parameters; binary32) to the host. */
+int homg_net_get_grads(homg_net_handle net, float* grads, int64_t count);
+
+/* Inference: y[b][y][x] = network(x) for B device images (layout above) of H x W pixels.
+ * B, H, W >= 1 and B*H*W < 2^31. */
+int homg_net_forward(homg_net_handle net, const void* x, int B, int H, int W, float* y);
+
+/* One training step on a batch: forward, mean squared error against t ([B][H][W] device), the
+ * gradient of every parameter (binary32 accumulation), one Adam step (beta1 0.9, beta2 0.999,
+ * eps 1e-8) with learning rate lr > 0. *loss_out (optional) receives the batch loss before the
+ * step. */
+int homg_net_train_step(homg_net_handle net, const void* x, const float* t, int B, int H, int W, float lr,
+                        float* loss_out);
+
+/* Gather B square P x P patches from one device image x (H x W, layout above) and its target t
+ * ([H][W]); corners (device int32, 2 per patch: row, column of the patch's first pixel) must
+ * keep every patch inside the image (HOMG_EINVAL is not detected on the device: the caller owns
+ * this). Writes xp ([B] images of P x P) and tp ([B][P][P]). Does not synchronise. */
+int homg_net_gather_patches(homg_net_handle net, const void* x, const float* t, int H, int W, const int32_t* corners,
+                            int B, int P, void* xp, float* tp);
+
+/* Message of the last hard error on net (or of the last failed homg_net_create when net is NULL). */
+const char* homg_net_last_error(homg_net_handle net);
+
+void homg_net_destroy(homg_net_handle net);
+
+/* Network features of the grid iterate u for right-hand side f on a handle with variable
+ * coefficients (homg_set_coefficient): x_out (one image of (n+1) x (n+1) pixels, layout above)
+ * and *rho_out; when u_ref is given, t_out[(n+1)^2] receives the scaled error (u_ref - u) / rho
+ * at interior nodes (0 on the boundary). f, u, u_ref: FP64 device arrays, unpadded (n+1)^2.
+ * HOMG_EINVAL when the handle has no coefficient or rho = 0. */
+int homg_features(homg_handle h, const double* f, const double* u, const double* u_ref, void* x_out, float* t_out,
+                  double* rho_out);
+
+/* Restarted solve with the learned corrector ahead of every HOMG cycle (variable-coefficient
+ * handles, HOMG_LAUNCH_GRAPH or STREAM alike: this loop is host-driven, one synchronisation per
+ * proposal and per cycle): r = f - A u; stop as homg_solve does; features -> network -> proposal
+ * u' = u + rho y; keep u' when ||f - A u'|| < ||r|| (FP64, the same reduction for both norms);
+ * one HOMG cycle on the kept iterate's residual. Once two proposals in a row have been rejected
+ * the network proposes nothing more in this solve (plain HOMG cycles only). accepted_out
+ * (optional, max_cycles ints) receives the judge's decisions (0 for cycles without a proposal).
+ * Returns like homg_solve. */
+int homg_solve_learned(homg_handle h, homg_net_handle net, const double* f, double* u, double tol, int max_cycles,
+                       int* cycles_out, double* relres_out, int* accepted_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOMG_NET_H */

@@ -20,7 +20,9 @@
 #include <vector>
 
 #include "../../include/homg.h"
+#include "../../include/homg_net.h"
 #include "homg_internal.h"
+#include "homg_net_internal.h"
 
 using namespace homg;
 
@@ -123,6 +125,18 @@ struct homg_ctx {
     double* kx0 = nullptr;
     double* ky0 = nullptr;
     int* dbad = nullptr;
+    uint16_t* logk = nullptr;  // bfloat16(log k) per node, the learned corrector's second input
+
+    // Learned solve (homg_solve_learned / homg_features): network input image and output, the
+    // proposal's correction and residual source, partial sums and device scalars.
+    char* learn_arena = nullptr;
+    void* lx = nullptr;
+    float* ly = nullptr;
+    void* lcorr = nullptr;
+    void* lg0 = nullptr;
+    double* lpart = nullptr;
+    double* lpart2 = nullptr;
+    double* lscal = nullptr;  // [0] rho, [1] ||r||^2, [2] ||r'||^2
 
     homg_stats stats{};
     char err[512] = "";
@@ -1308,6 +1322,7 @@ int homg_set_coefficient(homg_handle h, const double* k) {
             const size_t b0 = (size_t)grid_elems(2, h->n, h->pitch0) * sizeof(double);
             const size_t o0x = dbl ? 0 : take(b0), o0y = dbl ? 0 : take(b0);
             const size_t obad = take(sizeof(int));
+            const size_t olog = take((size_t)(h->n + 1) * (h->n + 1) * sizeof(uint16_t));
             CK(h, cudaMalloc(&h->vc_arena, (size_t)round_up((int64_t)off, 256)), "allocating the coefficient arrays");
             for (int m = 0; m < h->levels; ++m) {
                 h->vkx.push_back(h->vc_arena + ox[m]);
@@ -1317,6 +1332,7 @@ int homg_set_coefficient(homg_handle h, const double* k) {
             h->kx0 = dbl ? (double*)h->vkx[0] : (double*)(h->vc_arena + o0x);
             h->ky0 = dbl ? (double*)h->vky[0] : (double*)(h->vc_arena + o0y);
             h->dbad = (int*)(h->vc_arena + obad);
+            h->logk = (uint16_t*)(h->vc_arena + olog);
         }
         CK(h, cudaMemsetAsync(h->dbad, 0, sizeof(int), h->stream), "cudaMemsetAsync");
         for (int m = 0; m < h->levels; ++m)
@@ -1327,6 +1343,7 @@ int homg_set_coefficient(homg_handle h, const double* k) {
             CK(h, launch_vc_setup(k, h->n, 0, true, h->kx0, h->ky0, nullptr, h->pitch0, h->opt.omega_j, h->dbad,
                                   h->stream),
                "coefficient set-up kernel");
+        CK(h, launch_logk(k, h->n, h->logk, h->stream), "log-coefficient kernel");
         int bad = 0;
         CK(h, cudaMemcpyAsync(&bad, h->dbad, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
         CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -1348,6 +1365,184 @@ int homg_set_coefficient(homg_handle h, const double* k) {
     destroy_graph(h->gfirst);
     destroy_graph(h->gcont);
     return HOMG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Buffers of the learned solve, allocated once per handle.
+int ensure_learned(homg_ctx* h) {
+    if (h->learn_arena) return HOMG_OK;
+    const int64_t side = h->n + 1;
+    const size_t es = (size_t)prec_bytes(h->prec);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = (size_t)round_up((int64_t)off, 256); size_t o = off; off += bytes; return o; };
+    const size_t ox = take((size_t)side * side * 16 * 2);
+    const size_t oy = take((size_t)side * side * sizeof(float));
+    const size_t oc = take((size_t)grid_elems(2, h->n, h->pitch0) * es);
+    const size_t og = take((size_t)grid_elems(2, h->n, h->pitch0) * es);
+    const size_t op = take((size_t)std::max(feat_parts(h->n), h->nparts) * sizeof(double));
+    const size_t op2 = take((size_t)h->nparts * sizeof(double));
+    const size_t os = take(4 * sizeof(double));
+    CK(h, cudaMalloc(&h->learn_arena, (size_t)round_up((int64_t)off, 256)), "allocating the learned-solve buffers");
+    CK(h, cudaMemset(h->learn_arena, 0, (size_t)round_up((int64_t)off, 256)), "cudaMemset");
+    h->lx = h->learn_arena + ox;
+    h->ly = (float*)(h->learn_arena + oy);
+    h->lcorr = h->learn_arena + oc;
+    h->lg0 = h->learn_arena + og;
+    h->lpart = (double*)(h->learn_arena + op);
+    h->lpart2 = (double*)(h->learn_arena + op2);
+    h->lscal = (double*)(h->learn_arena + os);
+    return HOMG_OK;
+}
+
+// Features of the residual currently held in g0 (h^2 r): rho into lscal[0], the image into x.
+cudaError_t enqueue_features(homg_ctx* h, const void* g0, void* x, cudaStream_t s) {
+    const double cnt = (double)(h->n - 1) * (double)(h->n - 1);
+    cudaError_t e = launch_feat_stats(h->prec, g0, h->pitch0, h->kx0, h->ky0, h->pitch0, h->n, h->lpart, s);
+    if (e == cudaSuccess) e = launch_reduce(h->lpart, feat_parts(h->n), cnt, h->lscal, s);
+    if (e == cudaSuccess)
+        e = launch_feat_write(h->prec, g0, h->pitch0, h->kx0, h->ky0, h->pitch0, h->n, h->lscal, h->logk, x, s);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int homg_features(homg_handle h, const double* f, const double* u, const double* u_ref, void* x_out, float* t_out,
+                  double* rho_out) {
+    if (!h) return HOMG_EINVAL;
+    if (!f || !u || !x_out || !rho_out || (t_out && !u_ref))
+        return fail(h, HOMG_EINVAL, "homg_features: null argument%s%s");
+    if (!h->vc) return fail(h, HOMG_EINVAL, "homg_features: the handle has no coefficient (homg_set_coefficient)%s%s");
+    CK(h, cudaSetDevice(h->device), "cudaSetDevice");
+    int rc = ensure_learned(h);
+    if (rc != HOMG_OK) return rc;
+    cudaStream_t sm = h->stream;
+    State* s = h->hstate;
+    memset(s, 0, sizeof(*s));
+    s->f = f;
+    s->u = (double*)u;
+    CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, sm), "cudaMemcpyAsync(state)");
+    ResidArgs a = resid_args(h, 0);
+    a.u_out = dgrid(nullptr, 0, h->n);
+    a.part_f = nullptr;
+    CK(h, launch_residual(2, h->prec, false, a, h->n, sm), "residual kernel");
+    CK(h, enqueue_features(h, h->L[0].g, x_out, sm), "feature kernels");
+    if (t_out) CK(h, launch_target(u_ref, u, h->n, h->lscal, t_out, sm), "target kernel");
+    double rho = 0.0;
+    CK(h, cudaMemcpyAsync(&rho, h->lscal, sizeof(double), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync");
+    CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+    *rho_out = rho;
+    if (!(rho > 0.0) || !std::isfinite(rho)) return fail(h, HOMG_EINVAL, "homg_features: zero or non-finite residual scale%s%s");
+    return HOMG_OK;
+}
+
+int homg_solve_learned(homg_handle h, homg_net_handle net, const double* f, double* u, double tol, int max_cycles,
+                       int* cycles_out, double* relres_out, int* accepted_out) {
+    if (!h) return HOMG_EINVAL;
+    memset(&h->stats, 0, sizeof(h->stats));
+    if (!net || !f || !u) return fail(h, HOMG_EINVAL, "homg_solve_learned: null argument%s%s");
+    if (!h->vc) return fail(h, HOMG_EINVAL, "homg_solve_learned: the handle has no coefficient (homg_set_coefficient)%s%s");
+    if (!(tol >= 0.0) || !std::isfinite(tol) || max_cycles < 0 || max_cycles > HOMG_MAX_CYCLES)
+        return fail(h, HOMG_EINVAL, "homg_solve_learned: invalid tol or max_cycles%s%s");
+    CK(h, cudaSetDevice(h->device), "cudaSetDevice");
+    int rc = ensure_learned(h);
+    if (rc != HOMG_OK) return rc;
+    cudaStream_t sm = h->stream;
+    const int side = h->n + 1;
+    const size_t gbytes = (size_t)grid_elems(2, h->n, h->pitch0) * (size_t)prec_bytes(h->prec);
+    State* s = h->hstate;
+    memset(s, 0, sizeof(*s));
+    s->f = f;
+    s->u = u;
+    s->tol = tol;
+    s->div_factor = h->opt.diverge_factor;
+    s->max_cycles = max_cycles;
+    s->status = -1;
+    while (h->sev.size() < 2) {
+        cudaEvent_t e;
+        CK(h, cudaEventCreate(&e), "cudaEventCreate");
+        h->sev.push_back(e);
+    }
+    CK(h, cudaEventRecord(h->sev[0], sm), "cudaEventRecord");
+    CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, sm), "cudaMemcpyAsync(state)");
+    CK(h, launch_residual(2, h->prec, false, resid_args(h, 0), h->n, sm), "residual kernel");
+    CK(h, launch_reduce(h->part_r, h->nparts, 0.0, h->lscal + 1, sm), "norm kernel");
+    CK(h, launch_finalize(fin_args(h, FIN_INIT, nullptr), sm), "finalize kernel");
+    CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
+    CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+    int cur = 0;  // uint_[cur] holds the iterate
+    int kept = 0, rejected_in_a_row = 0;
+    ResidArgs base = resid_args(h, 1);
+    for (int k = 1; !s->done && k <= max_cycles; ++k) {
+        if (accepted_out) accepted_out[k - 1] = 0;
+        // after two rejections in a row the network stops proposing: plain HOMG cycles only
+        if (rejected_in_a_row < 2) {
+        // proposal from the network
+        CK(h, enqueue_features(h, h->L[0].g, h->lx, sm), "feature kernels");
+        rc = net_forward_dev(net, h->lx, 1, side, side, h->ly, sm);
+        if (rc != HOMG_OK) return fail(h, rc, "homg_solve_learned: network inference failed: %s%s", homg_net_last_error(net));
+        CK(h, launch_correct(h->prec, h->ly, h->n, h->lscal, h->lcorr, h->pitch0, sm), "correction kernel");
+        ResidArgs p = base;
+        p.u_in = cdgrid(h->uint_[cur], h->pitch0, h->n);
+        p.e = cgrid(h->lcorr, h->pitch0, h->n);
+        p.u_out = dgrid(h->uint_[cur ^ 1], h->pitch0, h->n);
+        p.g0 = grid(h->lg0, h->pitch0, h->n);
+        p.part_r = h->lpart2;
+        p.part_f = nullptr;
+        CK(h, launch_residual(2, h->prec, false, p, h->n, sm), "residual kernel");
+        CK(h, launch_reduce(h->lpart2, h->nparts, 0.0, h->lscal + 2, sm), "norm kernel");
+        double nrm[2] = {0.0, 0.0};
+        CK(h, cudaMemcpyAsync(nrm, h->lscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync");
+        CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+        rc = net_check_error(net);
+        if (rc != HOMG_OK) return fail(h, rc, "homg_solve_learned: %s%s", homg_net_last_error(net));
+        const bool keep = nrm[1] < nrm[0];  // the plain solver's FP64 residual judges the proposal
+        if (accepted_out) accepted_out[k - 1] = keep ? 1 : 0;
+        if (keep) {
+            ++kept;
+            rejected_in_a_row = 0;
+            cur ^= 1;
+            CK(h, cudaMemcpyAsync(h->L[0].g, h->lg0, gbytes, cudaMemcpyDeviceToDevice, sm), "cudaMemcpyAsync");
+        } else {
+            ++rejected_in_a_row;
+        }
+        }
+        // one HOMG cycle on the kept iterate's residual
+        CK(h, enqueue_ops(h, h->partA, sm), "cycle kernels");
+        CK(h, enqueue_ops(h, h->partB, sm), "cycle kernels");
+        ResidArgs c = base;
+        c.u_in = cdgrid(h->uint_[cur], h->pitch0, h->n);
+        c.e = cgrid(h->e[h->e_final], h->pitch0, h->n);
+        c.u_out = dgrid(h->uint_[cur ^ 1], h->pitch0, h->n);
+        CK(h, launch_residual(2, h->prec, false, c, h->n, sm), "residual kernel");
+        CK(h, launch_reduce(h->part_r, h->nparts, 0.0, h->lscal + 1, sm), "norm kernel");
+        CK(h, launch_finalize(fin_args(h, FIN_CYCLE, nullptr), sm), "finalize kernel");
+        cur ^= 1;
+        CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
+        CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+    }
+    CopyOutArgs co = copy_args(h);
+    co.u0 = co.u1 = cdgrid(h->uint_[cur], h->pitch0, h->n);
+    CK(h, launch_copy_out(2, co, h->n, sm), "copy-out kernel");
+    CK(h, cudaEventRecord(h->sev[1], sm), "cudaEventRecord");
+    CK(h, cudaMemcpyAsync(h->hhist, h->dhist, (max_cycles + 1) * sizeof(double), cudaMemcpyDeviceToHost, sm),
+       "cudaMemcpyAsync(hist)");
+    CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+    homg_stats& st = h->stats;
+    st.cycles = s->cycle;
+    st.status = s->status;
+    st.exec_mode = h->exec;
+    st.precision = h->prec;
+    st.iterations_per_cycle = (int)h->sched.size();
+    st.solve_ms = elapsed(h->sev[0], h->sev[1]);
+    st.kernels_fixed = kept;  // proposals the judge kept
+    if (cycles_out) *cycles_out = s->cycle;
+    if (relres_out) *relres_out = s->relres;
+    return s->status;
 }
 
 int homg_residual_norm(homg_handle h, const double* f, const double* u, double* relres_out) {
@@ -1402,6 +1597,7 @@ void homg_destroy(homg_handle h) {
     for (cudaEvent_t e : h->sev) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
     if (h->vc_arena) cudaFree(h->vc_arena);
+    if (h->learn_arena) cudaFree(h->learn_arena);
     if (h->stage_f) cudaFree(h->stage_f);
     if (h->stage_u) cudaFree(h->stage_u);
     if (h->hstate) cudaFreeHost(h->hstate);

@@ -44,6 +44,19 @@ EXPORTS = [
     "homg_batch_solve",
     "homg_batch_get_stats",
     "homg_batch_destroy",
+    "homg_net_param_count",
+    "homg_net_create",
+    "homg_net_set_stream",
+    "homg_net_set_params",
+    "homg_net_get_params",
+    "homg_net_get_grads",
+    "homg_net_forward",
+    "homg_net_train_step",
+    "homg_net_gather_patches",
+    "homg_net_last_error",
+    "homg_net_destroy",
+    "homg_features",
+    "homg_solve_learned",
 ]
 
 HOMG_BATCH_MAX_GROUPS = 16
@@ -121,6 +134,22 @@ def load(path=LIB_PATH):
     lib.homg_solve_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp]
     lib.homg_residual_norm.argtypes = [vp, vp, vp, dp]
     lib.homg_set_coefficient.argtypes = [vp, vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.homg_net_param_count.restype = ctypes.c_int64
+    lib.homg_net_create.argtypes = [ctypes.POINTER(vp)]
+    lib.homg_net_set_stream.argtypes = [vp, vp]
+    lib.homg_net_set_params.argtypes = [vp, fp, ctypes.c_int64]
+    lib.homg_net_get_params.argtypes = [vp, fp, ctypes.c_int64]
+    lib.homg_net_get_grads.argtypes = [vp, fp, ctypes.c_int64]
+    lib.homg_net_forward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+    lib.homg_net_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, fp]
+    lib.homg_net_gather_patches.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
+                                            vp, vp]
+    lib.homg_net_last_error.argtypes = [vp]
+    lib.homg_net_last_error.restype = ctypes.c_char_p
+    lib.homg_net_destroy.argtypes = [vp]
+    lib.homg_features.argtypes = [vp, vp, vp, vp, vp, vp, dp]
+    lib.homg_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp, ip]
     lib.homg_get_history.argtypes = [vp, dp, ctypes.c_int]
     lib.homg_get_stats.argtypes = [vp, ctypes.POINTER(homg_stats)]
     lib.homg_last_error.argtypes = [vp]
@@ -296,6 +325,15 @@ def _devptr(t, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _devptr_any(t, name):
+    """Device pointer of a contiguous CUDA tensor of any dtype (network images, targets, corners)."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise TypeError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def homg_solve(handle, f, u, tol=1e-10, max_cycles=50):
     """Solve in place on device tensors; returns (status, cycles, relres)."""
     cyc, rr = ctypes.c_int(0), ctypes.c_double(0.0)
@@ -409,3 +447,119 @@ class Solver:
                 self.close()
         except Exception:
             pass
+
+
+# ---- learned corrector (include/homg_net.h) -------------------------------------------------------
+def _net_check(rc, net):
+    if rc < 0:
+        msg = load().homg_net_last_error(net)
+        raise HomgError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def image_channels_first_to_device_layout(x):
+    """[C, H, W] (C = 2 or 16) array -> the library's row-chunked 16-channel layout [H][2][W][8] (numpy, same dtype)."""
+    import numpy as np
+
+    C, H, W = x.shape
+    full = np.zeros((16, H, W), dtype=x.dtype)
+    full[:C] = x
+    return np.ascontiguousarray(full.reshape(2, 8, H, W).transpose(2, 0, 3, 1))
+
+
+def image_device_layout_to_channels_first(xr):
+    """Inverse of image_channels_first_to_device_layout for one image: [H][2][W][8] -> [16, H, W]."""
+    import numpy as np
+
+    H, G, W, E = xr.shape
+    return np.ascontiguousarray(xr.transpose(1, 3, 0, 2).reshape(G * E, H, W))
+
+
+class Net:
+    """Owner of a learned-corrector network handle (include/homg_net.h)."""
+
+    def __init__(self):
+        lib = load()
+        h = ctypes.c_void_p()
+        _net_check(lib.homg_net_create(ctypes.byref(h)), None)
+        self.handle = h.value
+        self.count = lib.homg_net_param_count()
+
+    def set_stream(self, stream):
+        raw = getattr(stream, "cuda_stream", stream) or 0
+        _net_check(load().homg_net_set_stream(self.handle, ctypes.c_void_p(raw)), self.handle)
+
+    def set_params(self, flat):
+        import numpy as np
+
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.count
+        _net_check(load().homg_net_set_params(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+                   self.handle)
+
+    def get_params(self):
+        import numpy as np
+
+        a = np.empty(self.count, dtype=np.float32)
+        _net_check(load().homg_net_get_params(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+                   self.handle)
+        return a
+
+    def get_grads(self):
+        import numpy as np
+
+        a = np.empty(self.count, dtype=np.float32)
+        _net_check(load().homg_net_get_grads(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+                   self.handle)
+        return a
+
+    def forward(self, x, y):
+        """x: device bfloat16 tensor [B, H, 2, W, 8]; y: device float32 tensor [B, H, W]."""
+        B, H, _, W, _ = x.shape
+        _net_check(load().homg_net_forward(self.handle, _devptr_any(x, "x"), B, H, W, _devptr_any(y, "y")), self.handle)
+
+    def train_step(self, x, t, lr):
+        B, H, _, W, _ = x.shape
+        loss = ctypes.c_float(0.0)
+        _net_check(load().homg_net_train_step(self.handle, _devptr_any(x, "x"), _devptr_any(t, "t"), B, H, W, float(lr),
+                                              ctypes.byref(loss)), self.handle)
+        return loss.value
+
+    def gather_patches(self, x, t, corners, P, xp, tp):
+        """x: [1, H, 2, W, 8] image, t: [H, W]; corners: device int32 [B, 2]; writes xp [B, P, 2, P, 8], tp [B, P, P]."""
+        H, W = t.shape
+        B = corners.shape[0]
+        _net_check(load().homg_net_gather_patches(self.handle, _devptr_any(x, "x"), _devptr_any(t, "t"), H, W,
+                                                  _devptr_any(corners, "corners"), B, P, _devptr_any(xp, "xp"),
+                                                  _devptr_any(tp, "tp")), self.handle)
+
+    def close(self):
+        if self.handle:
+            load().homg_net_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+def homg_features(handle, f, u, x_out, u_ref=None, t_out=None):
+    """Network features of iterate u (device FP64) on a variable-coefficient handle; returns rho."""
+    rho = ctypes.c_double(0.0)
+    _check(load().homg_features(handle, _devptr(f, "f"), _devptr(u, "u"),
+                                None if u_ref is None else _devptr(u_ref, "u_ref"), _devptr_any(x_out, "x_out"),
+                                None if t_out is None else _devptr_any(t_out, "t_out"), ctypes.byref(rho)), handle)
+    return rho.value
+
+
+def homg_solve_learned(handle, net, f, u, tol=1e-10, max_cycles=50):
+    """Learned-corrector solve; returns (status, cycles, relres, accepted list)."""
+    cyc = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    acc = (ctypes.c_int * max(1, max_cycles))()
+    st = _check(load().homg_solve_learned(handle, net.handle, _devptr(f, "f"), _devptr(u, "u"), tol, max_cycles,
+                                          ctypes.byref(cyc), ctypes.byref(rr), acc), handle)
+    return st, cyc.value, rr.value, [bool(acc[i]) for i in range(cyc.value)]
