@@ -544,10 +544,13 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
     static int per_sm = 0;
     if (!per_sm) {
         cudaError_t e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3x3<CIN, COUT, MODE>, NT, S::SMEM);
-        if (e != cudaSuccess) return e;
-        // resident CTAs of one SM must fit in its 512 TMEM columns together
+        // CTAs per SM: as many as the 228 KB of shared memory hold (1 KB reserved per CTA), never
+        // more than the SM's 512 TMEM columns hold together
+        per_sm = 233472 / (S::SMEM + 1024);
         per_sm = per_sm < (int)(512 / S::NCOLS) ? per_sm : (int)(512 / S::NCOLS);
         if (per_sm < 1) per_sm = 1;
     }
