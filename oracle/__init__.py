@@ -20,6 +20,11 @@ from .oracle import (  # noqa: F401
     iteration_vc,
     mfmg_schedule,
     norm_interior,
+    pow2_cycle,
+    pow2_iteration,
+    pow2_local_side,
+    pow2_restrict,
+    pow2_solve,
     prolong,
     residual,
     residual_vc,

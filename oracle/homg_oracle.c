@@ -996,3 +996,243 @@ int homg_oracle_solve_vc(int64_t n, int levels, const int *sched, int nsched, do
     if (relres_out) *relres_out = rr;
     return status;
 }
+
+/* ========================================================================================== */
+/* Power-of-two grids (Sec. 3), 2-D, whole-grid form. Reading of this build (Fig. 2 is missing): */
+/*   the grid has N = 2^K nodes per side, boundary nodes included (h = 1 / (N - 1)); it is split */
+/*   into four quadrants of H = N/2 nodes per side. Quadrant q (qx = q & 1, qy = q >> 1) has its */
+/*   external corner at (cx, cy), cx = qx ? N-1 : 0, and points inward with sx = qx ? -1 : +1    */
+/*   (likewise y). Its level-m lattice (m >= 1) is marked from that corner: local nodes (a, b),  */
+/*   0 <= a, b <= n_m = H >> m, at fine node (cx + sx a 2^m, cy + sy b 2^m). The last local row  */
+/*   and column (a or b = n_m) lie just outside the quadrant, on the far side of the centre      */
+/*   lines, so the coarsest level (m = K-1) holds exactly one point per quadrant: the four        */
+/*   central points. Local nodes with a = 0 or b = 0 are domain boundary; all others are marked  */
+/*   and relaxed. The four lattices of a level are disjoint (N - 1 is odd).                      */
+/*   Restriction: F_m = the m-fold nested full weighting of the fine residual, evaluated at each */
+/*   quadrant's lattice nodes as one separable hat stencil (see homg_oracle_pow2_restrict).      */
+/*   Relaxation at a marked node p of level m: delta = omega (h_m^2 F - lap_m e)(p), lap_m reading */
+/*   the fine iterate at distance 2^m (0 outside the grid).                                       */
+/*   Interpolation of the pending level-mp variation at a node not marked at level mp: bilinear  */
+/*   from the lattice of the quadrant that contains the node, nothing from other quadrants.      */
+/*   Level 0 is the whole fine grid (every interior node marked).                                 */
+/* Arrays: the fine iterate and residual are N x N; per level m >= 1 the four quadrants' local    */
+/* arrays of (n_m+1)^2 values are stored one after another (quadrant q at q (n_m+1)^2).           */
+/* ========================================================================================== */
+static int pow2_exponent(int64_t N) {
+    int K = 0;
+    while (((int64_t)1 << K) < N) ++K;
+    return (((int64_t)1 << K) == N) ? K : -1;
+}
+
+static double e_at_pow2(const double *e, int64_t N, int64_t x, int64_t y) {
+    if (x < 0 || y < 0 || x >= N || y >= N) return 0.0;
+    return e[y * N + x];
+}
+
+/* Local lattice coordinate of fine index x along one axis for quadrant bit qb, or -1 when x is not  */
+/* on the level-m lattice of that quadrant.                                                          */
+static int64_t pow2_local(int64_t N, int m, int qb, int64_t x) {
+    const int64_t H = N / 2, nm = H >> m, l = (int64_t)1 << m;
+    const int64_t d = qb ? (N - 1 - x) : x;  /* distance from the external corner */
+    if (d < 0 || (d & (l - 1)) != 0) return -1;
+    const int64_t a = d >> m;
+    return (a <= nm) ? a : -1;
+}
+
+/* quadrant bit of fine index x along one axis */
+static int pow2_qbit(int64_t N, int64_t x) { return x >= N / 2; }
+
+/* marked at level m: on some quadrant's lattice, not domain boundary (level 0: every interior node) */
+static int pow2_marked(int64_t N, int m, int64_t x, int64_t y, int *q_out, int64_t *a_out, int64_t *b_out) {
+    if (x <= 0 || y <= 0 || x >= N - 1 || y >= N - 1) return 0;
+    if (m == 0) return 1;
+    for (int q = 0; q < 4; ++q) {
+        int64_t a = pow2_local(N, m, q & 1, x), b = pow2_local(N, m, q >> 1, y);
+        if (a > 0 && b > 0) {
+            if (q_out) *q_out = q;
+            if (a_out) *a_out = a;
+            if (b_out) *b_out = b;
+            return 1;
+        }
+    }
+    return 0;
+}
+
+/* Level m (>= 1) sources of the four quadrants from the fine N x N residual r: at lattice node p,  */
+/* F_m(p) = sum over |dx|, |dy| < 2^m of w(dx) w(dy) r(p + (dx, dy)), w(d) = (2^m - |d|) / 4^m (zero  */
+/* outside the grid), the composition of m full weightings at strides 1, 2, ..., 2^(m-1). At nodes   */
+/* whose stencils stay inside one quadrant's lattices it equals the nested full weighting; at the    */
+/* far row and column it reads the fine residual across the centre lines. Summation: rows of the     */
+/* stencil first (dx ascending), then the row sums (dy ascending). Fc holds 4 (n_m+1)^2 values.     */
+void homg_oracle_pow2_restrict(int64_t N, int m, const double *r, double *Fc) {
+    const int64_t H = N / 2, nm = H >> m, side = nm + 1, l = (int64_t)1 << m;
+    const double l2 = (double)l * (double)l;
+    for (int q = 0; q < 4; ++q) {
+        const int qx = q & 1, qy = q >> 1;
+        double *out = Fc + (int64_t)q * side * side;
+        for (int64_t b = 0; b <= nm; ++b)
+            for (int64_t a = 0; a <= nm; ++a) {
+                if (a == 0 || b == 0) { out[b * side + a] = 0.0; continue; }
+                const int64_t x = qx ? (N - 1 - a * l) : a * l, y = qy ? (N - 1 - b * l) : b * l;
+                double acc = 0.0;
+                for (int64_t dy = -(l - 1); dy <= l - 1; ++dy) {
+                    double row = 0.0;
+                    for (int64_t dx = -(l - 1); dx <= l - 1; ++dx)
+                        row = row + ((double)(l - (dx < 0 ? -dx : dx)) / l2) * e_at_pow2(r, N, x + dx, y + dy);
+                    acc = acc + ((double)(l - (dy < 0 ? -dy : dy)) / l2) * row;
+                }
+                out[b * side + a] = acc;
+            }
+    }
+}
+
+/* Bilinear value at fine node (x, y) of quadrant q's level-mp variation (4 local arrays). */
+static double pow2_interp(const double *d, int64_t N, int mp, int q, int64_t x, int64_t y) {
+    const int64_t H = N / 2, nm = H >> mp, lp = (int64_t)1 << mp, side = nm + 1;
+    const int qx = q & 1, qy = q >> 1;
+    const int64_t dx = qx ? (N - 1 - x) : x, dy = qy ? (N - 1 - y) : y;
+    const int64_t A0 = dx >> mp, fa = dx & (lp - 1), B0 = dy >> mp, fb = dy & (lp - 1);
+    const int64_t A1 = fa ? A0 + 1 : A0, B1 = fb ? B0 + 1 : B0;
+    const double wx0 = (double)(lp - fa) / (double)lp, wx1 = (double)fa / (double)lp;
+    const double wy0 = (double)(lp - fb) / (double)lp, wy1 = (double)fb / (double)lp;
+    const double *dq = d + (int64_t)q * side * side;
+    const double d00 = dq[B0 * side + A0], d10 = dq[B0 * side + A1];
+    const double d01 = dq[B1 * side + A0], d11 = dq[B1 * side + A1];
+    return ((wx0 * wy0) * d00 + (wx1 * wy0) * d10) + ((wx0 * wy1) * d01 + (wx1 * wy1) * d11);
+}
+
+/* One HOMG iteration on the power-of-two grid (see homg_oracle_iteration): relax the nodes marked  */
+/* at level m (source Fm: the fine residual for m = 0, else the four local arrays), and add the      */
+/* interpolation of the pending level-mprev variation at the nodes not marked at level mprev.        */
+/* d_new receives delta at the marked nodes (level m >= 1: four local arrays; level 0: unused).      */
+void homg_oracle_pow2_iteration(int64_t N, int m, int mprev, double omega, const double *Fm, const double *dprev,
+                                const double *e_old, double *e_new, double *d_new) {
+    const int64_t H = N / 2, l = (int64_t)1 << m;
+    const double h = 1.0 / (double)(N - 1);
+    const double hm = h * (double)l;
+    const double hm2 = hm * hm;
+    if (m >= 1) {
+        const int64_t side = (H >> m) + 1;
+        for (int64_t p = 0; p < 4 * side * side; ++p) d_new[p] = 0.0;
+    }
+    for (int64_t y = 0; y < N; ++y)
+        for (int64_t x = 0; x < N; ++x) {
+            const int64_t p = y * N + x;
+            if (x == 0 || y == 0 || x == N - 1 || y == N - 1) { e_new[p] = 0.0; continue; }
+            double v = e_old[p];
+            int q = 0;
+            int64_t a = 0, b = 0;
+            if (pow2_marked(N, m, x, y, &q, &a, &b)) {
+                double lap = 4.0 * v;
+                lap = lap - e_at_pow2(e_old, N, x - l, y);
+                lap = lap - e_at_pow2(e_old, N, x + l, y);
+                lap = lap - e_at_pow2(e_old, N, x, y - l);
+                lap = lap - e_at_pow2(e_old, N, x, y + l);
+                double F;
+                if (m == 0) F = Fm[p];
+                else {
+                    const int64_t side = (H >> m) + 1;
+                    F = Fm[(int64_t)q * side * side + b * side + a];
+                }
+                const double delta = omega * (hm2 * F - lap);
+                if (m >= 1) {
+                    const int64_t side = (H >> m) + 1;
+                    d_new[(int64_t)q * side * side + b * side + a] = delta;
+                }
+                v = v + delta;
+            }
+            if (mprev >= 1 && !pow2_marked(N, mprev, x, y, NULL, NULL, NULL))
+                v = v + pow2_interp(dprev, N, mprev, pow2_qbit(N, x) | (pow2_qbit(N, y) << 1), x, y);
+            e_new[p] = v;
+        }
+}
+
+/* One power-of-two HOMG cycle on A e = F0 (N x N fine residual) from e = 0. */
+int homg_oracle_pow2_cycle(int64_t N, int levels, const int *sched, int nsched, double omega_j, const double *F0,
+                           double *e) {
+    const int K = pow2_exponent(N);
+    if (K < 2 || levels < 1 || levels > K || nsched < 1) return HOMG_ORACLE_EINVAL;
+    for (int t = 0; t < nsched; ++t)
+        if (sched[t] < 0 || sched[t] >= levels) return HOMG_ORACLE_EINVAL;
+    if (sched[nsched - 1] != 0) return HOMG_ORACLE_EINVAL;
+    const double omega = omega_j / 4.0;
+    const int64_t total = N * N, H = N / 2;
+    double **F = (double **)calloc((size_t)levels, sizeof(double *));
+    double **D = (double **)calloc((size_t)2 * levels, sizeof(double *));
+    double *ebuf = (double *)malloc((size_t)total * sizeof(double));
+    int rc = HOMG_ORACLE_OK;
+    if (!F || !D || !ebuf) { rc = HOMG_ORACLE_ENOMEM; goto done; }
+    F[0] = (double *)F0;
+    for (int m = 1; m < levels; ++m) {
+        const int64_t side = (H >> m) + 1;
+        F[m] = (double *)malloc((size_t)(4 * side * side) * sizeof(double));
+        D[2 * m] = (double *)calloc((size_t)(4 * side * side), sizeof(double));
+        D[2 * m + 1] = (double *)calloc((size_t)(4 * side * side), sizeof(double));
+        if (!F[m] || !D[2 * m] || !D[2 * m + 1]) { rc = HOMG_ORACLE_ENOMEM; goto done; }
+        homg_oracle_pow2_restrict(N, m, F0, F[m]);
+    }
+    for (int64_t p = 0; p < total; ++p) e[p] = 0.0;
+    {
+        double *e_old = e, *e_new = ebuf;
+        int mprev = -1;
+        int par[64] = {0};
+        const double *dprev = NULL;
+        for (int t = 0; t < nsched; ++t) {
+            const int m = sched[t];
+            double *dnew = (m >= 1) ? D[2 * m + par[m]] : NULL;
+            double dummy = 0.0;
+            homg_oracle_pow2_iteration(N, m, mprev, omega, F[m], dprev, e_old, e_new, dnew ? dnew : &dummy);
+            if (m >= 1) par[m] ^= 1;
+            dprev = dnew;
+            double *tmp = e_old; e_old = e_new; e_new = tmp;
+            mprev = m;
+        }
+        if (e_old != e) memcpy(e, e_old, (size_t)total * sizeof(double));
+    }
+done:
+    if (F) for (int m = 1; m < levels; ++m) free(F[m]);
+    if (D) for (int m = 0; m < 2 * levels; ++m) free(D[m]);
+    free(F); free(D); free(ebuf);
+    return rc;
+}
+
+/* Restarted solve on the power-of-two grid (see homg_oracle_solve): the residual is the five-point */
+/* Poisson residual of the N x N node grid (n = N - 1 intervals, h = 1/(N-1)).                      */
+int homg_oracle_pow2_solve(int64_t N, int levels, const int *sched, int nsched, double omega_j, double div_factor,
+                           const double *f, double *u, double tol, int max_cycles, double *hist, int *cycles_out,
+                           double *relres_out) {
+    const int K = pow2_exponent(N);
+    if (K < 2 || levels < 1 || levels > K || max_cycles < 0) return HOMG_ORACLE_EINVAL;
+    const int64_t n = N - 1, total = N * N;
+    double fnorm = homg_oracle_norm_interior(2, n, f);
+    if (fnorm == 0.0) {
+        for (int64_t y = 1; y < n; ++y)
+            for (int64_t x = 1; x < n; ++x) u[y * N + x] = 0.0;
+        if (hist) hist[0] = 0.0;
+        if (cycles_out) *cycles_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        return HOMG_ORACLE_OK;
+    }
+    double *r = (double *)malloc((size_t)total * sizeof(double));
+    double *e = (double *)malloc((size_t)total * sizeof(double));
+    if (!r || !e) { free(r); free(e); return HOMG_ORACLE_ENOMEM; }
+    int status = HOMG_ORACLE_NOT_CONVERGED, k;
+    double rr = 0.0, rr0 = 0.0;
+    for (k = 0;; ++k) {
+        homg_oracle_residual(2, n, f, u, r);
+        rr = homg_oracle_norm_interior(2, n, r) / fnorm;
+        if (hist) hist[k] = rr;
+        if (k == 0) rr0 = rr;
+        if (rr <= tol) { status = HOMG_ORACLE_OK; break; }
+        if (!isfinite(rr) || rr > div_factor * rr0) { status = HOMG_ORACLE_DIVERGED; break; }
+        if (k == max_cycles) { status = HOMG_ORACLE_NOT_CONVERGED; break; }
+        int rc = homg_oracle_pow2_cycle(N, levels, sched, nsched, omega_j, r, e);
+        if (rc != HOMG_ORACLE_OK) { free(r); free(e); return rc; }
+        for (int64_t y = 1; y < n; ++y)
+            for (int64_t x = 1; x < n; ++x) u[y * N + x] = u[y * N + x] + e[y * N + x];
+    }
+    free(r); free(e);
+    if (cycles_out) *cycles_out = k;
+    if (relres_out) *relres_out = rr;
+    return status;
+}

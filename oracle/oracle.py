@@ -62,6 +62,11 @@ def _load(path=None):
                                              P, P, P]
         lib.homg_oracle_solve_vc.argtypes = [i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, P, P, P, ctypes.c_double, ctypes.c_int, P, IP, P]
+        lib.homg_oracle_pow2_restrict.argtypes = [i64, ctypes.c_int, P, P]
+        lib.homg_oracle_pow2_iteration.argtypes = [i64, ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P, P, P, P]
+        lib.homg_oracle_pow2_cycle.argtypes = [i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double, P, P]
+        lib.homg_oracle_pow2_solve.argtypes = [i64, ctypes.c_int, IP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               P, P, ctypes.c_double, ctypes.c_int, P, IP, P]
         lib.homg_oracle_bf16_round.argtypes = [ctypes.c_float]
         lib.homg_oracle_bf16_round.restype = ctypes.c_float
         _lib = lib
@@ -331,6 +336,66 @@ def solve_vc(kc, f, levels, precision="fp64", u0=None, tol=1e-10, max_cycles=100
     status = _load().homg_oracle_solve_vc(n, levels, cs, len(sched), omega_j, div_factor, VC_PRECISIONS[precision],
                                           _p(kc), _p(np.ascontiguousarray(f)), _p(u), tol, max_cycles, _p(hist),
                                           ctypes.byref(cyc), ctypes.byref(rr))
+    if status < 0:
+        raise ValueError("oracle solve rejected its arguments (rc=%d)" % status)
+    return u, status, cyc.value, hist[: cyc.value + 1]
+
+
+# ---- power-of-two grids (Sec. 3), 2-D: N = 2^K nodes per side, four quadrant lattices per level ----
+def pow2_local_side(N, m):
+    """Nodes per side of one quadrant's level-m local lattice (m >= 1)."""
+    return (N // 2 >> m) + 1
+
+
+def pow2_restrict(r, m):
+    """Level-m sources of the four quadrants [4, s, s] from the fine N x N residual r (m >= 1)."""
+    N = r.shape[0]
+    s = pow2_local_side(N, m)
+    Fc = np.empty((4, s, s))
+    _load().homg_oracle_pow2_restrict(N, m, _p(np.ascontiguousarray(r, dtype=np.float64)), _p(Fc))
+    return Fc
+
+
+def pow2_iteration(N, m, mprev, omega, Fm, dprev, e_old):
+    """One power-of-two HOMG iteration; returns (e_new, d_new) (d_new: [4, s, s] for m >= 1, None for m = 0)."""
+    e_new = np.empty_like(e_old)
+    d_new = np.empty((4, pow2_local_side(N, m), pow2_local_side(N, m))) if m >= 1 else np.zeros(1)
+    if dprev is None:
+        dprev, mprev = np.zeros(1), -1
+    _load().homg_oracle_pow2_iteration(N, m, mprev, omega, _p(np.ascontiguousarray(Fm, dtype=np.float64)),
+                                       _p(np.ascontiguousarray(dprev, dtype=np.float64)), _p(e_old), _p(e_new),
+                                       _p(d_new))
+    return e_new, (d_new if m >= 1 else None)
+
+
+def pow2_cycle(F0, levels, schedule=None, max_i=32, omega_j=None):
+    """One power-of-two HOMG cycle on A e = F0 (N x N, N = 2^K) from e = 0."""
+    N = F0.shape[0]
+    if omega_j is None:
+        omega_j = default_omega_j(2)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    e = np.empty_like(F0)
+    rc = _load().homg_oracle_pow2_cycle(N, levels, cs, len(sched), omega_j, _p(np.ascontiguousarray(F0)), _p(e))
+    if rc != 0:
+        raise ValueError("oracle cycle rejected its arguments (rc=%d)" % rc)
+    return e
+
+
+def pow2_solve(f, levels, u0=None, tol=1e-10, max_cycles=100, schedule=None, max_i=32, omega_j=None, div_factor=1e3):
+    """Restarted power-of-two HOMG solve on the N x N node grid. Returns (u, status, cycles, hist)."""
+    N = f.shape[0]
+    if omega_j is None:
+        omega_j = default_omega_j(2)
+    sched = mfmg_schedule(levels, max_i) if schedule is None else list(schedule)
+    cs = (ctypes.c_int * len(sched))(*sched)
+    u = np.zeros_like(f) if u0 is None else np.array(u0, dtype=np.float64, order="C", copy=True)
+    hist = np.zeros(max_cycles + 1)
+    cyc = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    status = _load().homg_oracle_pow2_solve(N, levels, cs, len(sched), omega_j, div_factor,
+                                            _p(np.ascontiguousarray(f)), _p(u), tol, max_cycles, _p(hist),
+                                            ctypes.byref(cyc), ctypes.byref(rr))
     if status < 0:
         raise ValueError("oracle solve rejected its arguments (rc=%d)" % status)
     return u, status, cyc.value, hist[: cyc.value + 1]

@@ -15,6 +15,7 @@ import oracle
 from oracle import oracle as oracle_impl
 
 import test_oracle_pins as pins
+import test_oracle_pow2 as p2pins
 import test_oracle_vc as vcpins
 import test_oracle_vcycle as vpins
 
@@ -46,6 +47,15 @@ MUTATIONS = {
     "vc_relax_fixed_weight": ("double delta = (omega_j / D) * (hm2 * Fm[q] - ae);", "double delta = (omega_j / 4.0) * (hm2 * Fm[q] - ae);"),
     "vc_relax_fine_coefficients": ("vc_faces(kc, n, l, i, j, &kw, &ke, &ks, &kn);\n                const double D", "vc_faces(kc, n, 1, i, j, &kw, &ke, &ks, &kn);\n                const double D"),
     "vc_relax_dropped_diagonal_term": ("const double D = ((kw + ke) + ks) + kn;", "const double D = (kw + ke) + ks;"),
+    "pow2_hat_weight": ("row = row + ((double)(l - (dx < 0 ? -dx : dx)) / l2) * e_at_pow2(r, N, x + dx, y + dy);",
+                        "row = row + ((double)(l - (dx < 0 ? -dx : dx)) / (double)l) * e_at_pow2(r, N, x + dx, y + dy);"),
+    "pow2_restrict_truncated_at_quadrant": ("row = row + ((double)(l - (dx < 0 ? -dx : dx)) / l2) * e_at_pow2(r, N, x + dx, y + dy);",
+                                            "row = row + ((double)(l - (dx < 0 ? -dx : dx)) / l2) * (((qx ? (N - 1 - x - dx) : (x + dx)) < H) ? e_at_pow2(r, N, x + dx, y + dy) : 0.0);"),
+    "pow2_corner_not_mirrored": ("const int64_t d = qb ? (N - 1 - x) : x;", "const int64_t d = x;"),
+    "pow2_no_far_row": ("return (a <= nm) ? a : -1;", "return (a < nm) ? a : -1;"),
+    "pow2_interp_from_one_quadrant": ("v = v + pow2_interp(dprev, N, mprev, pow2_qbit(N, x) | (pow2_qbit(N, y) << 1), x, y);",
+                                      "v = v + pow2_interp(dprev, N, mprev, 0, x, y);"),
+    "pow2_relax_stride": ("lap = lap - e_at_pow2(e_old, N, x - l, y);", "lap = lap - e_at_pow2(e_old, N, x - 1, y);"),
     "norm_not_squared": ("double x = v[j * (n + 1) + i]; s += x * x;", "double x = v[j * (n + 1) + i]; s += fabs(x);"),
 }
 
@@ -76,6 +86,12 @@ def run_pins():
         ("vc_jacobi", lambda: vcpins.test_single_level_cycle_is_damped_jacobi(5)),
         ("vc_coarse", lambda: vcpins.test_coarse_level_relaxation_uses_injected_coefficients(1)),
         ("vc_dense_solve", lambda: vcpins.test_solution_matches_dense_direct_solve(16, 4)),
+        ("p2_structure", lambda: p2pins.test_lattice_structure(16)),
+        ("p2_restrict", lambda: p2pins.test_restriction_is_nested_full_weighting(32, 2)),
+        ("p2_interp", lambda: p2pins.test_interpolation_uses_the_nodes_own_quadrant(32, 2)),
+        ("p2_dense", lambda: p2pins.test_solution_matches_dense_direct_solve(16)),
+        ("p2_rate", lambda: p2pins.test_contraction_is_resolution_independent((5, 6, 7))),
+        ("p2_symmetry", lambda: p2pins.test_mirror_symmetry()),
     ]
     failed = []
     for name, fn in checks:
