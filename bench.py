@@ -383,6 +383,46 @@ def run_cfg5(args, homg, stream, barrier, pending):
     return out
 
 
+def run_pow2(args, homg, stream, barrier, pending):
+    """Power-of-two grids (Sec. 3): 4096^2 nodes (boundary included), 12 levels, f iid uniform[-1, 1]
+    over the interior (seed 0), whole-grid form, to relres 1e-10, FP64 and FP32 cycles."""
+    import numpy as np
+    import torch
+
+    N, L = 4096, 12
+    f_np = np.zeros((N, N))
+    f_np[1:-1, 1:-1] = np.random.default_rng(0).uniform(-1, 1, (N - 2, N - 2))
+    f = torch.from_numpy(f_np).cuda()
+    u = torch.zeros_like(f)
+    out = {"workload": "2-D Poisson, power-of-two grid of 4096^2 nodes (Sec. 3 quadrant lattices), 12 levels, "
+                       "f iid uniform[-1,1] seed 0, whole-grid HOMG form, to relres 1e-10"}
+    for prec in ("fp64", "fp32"):
+        with homg.Solver(2, N, L, max_i=MAX_I, precision=prec, geometry="pow2") as s:
+            s.set_stream(stream)
+            u.zero_()
+            s.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.pow2_steps):
+                u.zero_()
+                st, cyc, rr = s.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+            e1.record(stream)
+            barrier()
+            ms = e0.elapsed_time(e1) / args.pow2_steps
+            stats = s.stats()
+        r = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms,
+             "unknowns_per_s": (N - 2) ** 2 / (ms * 1e-3), "iterations_per_cycle": stats["iterations_per_cycle"],
+             "kernel_launches": stats["kernel_launches"]}
+        if prec == "fp64" and args.pow2_oracle_check:
+            pending.append((r, "poisson", None, f_np, u.cpu().numpy()))
+        out[prec] = r
+    del f, u
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_leg(pending):
     """Everything the oracle does in a bench run (the CPU-baseline leg): its own FP64 residual of
     results the GPU legs kept, and its timing on samples of their workloads."""
@@ -611,6 +651,7 @@ def run(args):
     cfg3 = run_cfg3(args, homg, inputs, stream, barrier, pending) if (args.cfg3_steps > 0 and world == 1) else None
     cfg4 = run_cfg4(args, homg, stream, barrier, pending) if (args.cfg4_steps > 0 and world == 1) else None
     cfg5 = run_cfg5(args, homg, stream, barrier, pending) if (args.cfg5_steps > 0 and world == 1) else None
+    pow2 = run_pow2(args, homg, stream, barrier, pending) if (args.pow2_steps > 0 and world == 1) else None
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
     launches = sum(s["cycles"] * s["fine_iterations_per_cycle"] for s in stats)
@@ -665,6 +706,8 @@ def run(args):
         line["cfg4_batched"] = cfg4
     if cfg5:
         line["cfg5_learned"] = cfg5
+    if pow2:
+        line["pow2_grid"] = pow2
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_cpu_baseline(f_np, stats[-1]["cycles"])
         cpu_leg(pending)
@@ -701,6 +744,8 @@ def main():
     p.add_argument("--cfg5-seed", type=int, default=0, help="seed of the network's initial parameters")
     p.add_argument("--no-cfg5-oracle-check", dest="cfg5_oracle_check", action="store_false")
     p.add_argument("--no-cfg5-oracle-time", dest="cfg5_oracle_time", action="store_false")
+    p.add_argument("--pow2-steps", type=int, default=2, help="timed solves on the 4096^2 power-of-two grid (0: skip)")
+    p.add_argument("--no-pow2-oracle-check", dest="pow2_oracle_check", action="store_false")
     p.add_argument("--no-cfg3-oracle-check", dest="cfg3_oracle_check", action="store_false")
     args = p.parse_args()
     if args.warmup < 3:

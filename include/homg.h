@@ -110,7 +110,20 @@ typedef struct homg_options {
     int cycle;
     int v_pre;   /* V-cycle pre-smoothing sweeps  (0 = 2) */
     int v_post;  /* V-cycle post-smoothing sweeps (0 = 2) */
+    /* HOMG_GEOM_NESTED (default): nested grids of 2^K + 1 nodes per side.
+     * HOMG_GEOM_POW2: the power-of-two grids of Sec. 3 (2-D, 2^K nodes per side, boundary nodes
+     * included, h = 1/(2^K - 1)): the grid is split into four quadrants; at every level m >= 1
+     * each quadrant's lattice is marked from its external corner (spacing 2^m) and reaches one
+     * row/column past the centre lines, so the coarsest level holds the four central points;
+     * relaxations run on all marked nodes, interpolations on the rest from the node's own
+     * quadrant only; level sources are the m-fold nested full weighting of the fine residual
+     * (one hat stencil per node). HOMG cycles in the whole-grid form only (the default exec mode
+     * selects it), levels <= K, not with strict_fp, the V-cycle, batches or coefficients. */
+    int geometry;
 } homg_options;
+
+#define HOMG_GEOM_NESTED 0
+#define HOMG_GEOM_POW2 1
 
 #define HOMG_CYCLE_HOMG 0
 #define HOMG_CYCLE_V 1
@@ -151,9 +164,11 @@ typedef struct homg_ctx* homg_handle;
 /* Fill *opt with the defaults described above. */
 void homg_default_options(homg_options* opt);
 
-/* Create a solver for a (2^K+1)^ndim node grid (Sec. 2: nested grids doubling the spacing).
+/* Create a solver for a (2^K+1)^ndim node grid (Sec. 2: nested grids doubling the spacing), or a
+ * (2^K)^2 grid with geometry HOMG_GEOM_POW2 (Sec. 3).
  *   ndim     2 or 3.
- *   dims     ndim node counts, all equal to 2^K + 1 with K >= 1 (ESHAPE otherwise).
+ *   dims     ndim node counts, all equal to 2^K + 1 with K >= 1 (power-of-two geometry: 2^K with
+ *            2 <= K <= HOMG_MAX_K_2D) (ESHAPE otherwise).
  *   levels   number of levels L, 1 <= L <= K; level m has spacing 2^m h, the coarsest is L-1.
  *   stencil  5 (ndim 2) or 7 (ndim 3).
  *   opt      NULL for defaults.

@@ -60,8 +60,10 @@ struct SolveGraph {
 constexpr int kStagesPerGraph = 12;  // even: keeps the ping-pong parity of the solution buffers
 
 struct Op {  // one kernel launch of a cycle part
-    enum Kind { ITER, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD } kind;
+    enum Kind { ITER, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD, POW2_ITER, POW2_RESTRICT } kind;
     IterArgs it;
+    Pow2IterArgs p2;
+    Pow2RestrictArgs p2r;
     ProlongArgs pr;
     RestrictArgs rs;
     VResidArgs vr;
@@ -88,6 +90,8 @@ struct homg_ctx {
     size_t arena_bytes = 0;
     int64_t pitch0 = 0;
     std::vector<Level> L;
+    int geometry = HOMG_GEOM_NESTED;
+    double* p2tmp = nullptr;  // power-of-two geometry: the restriction's row-pass buffer
     int prec = PREC_FP64;     // storage precision of the cycle arrays
     int nbatch = 1;           // problems laid out at pstride bytes from each other (batch groups)
     size_t pstride = 0;
@@ -194,7 +198,19 @@ size_t layout(homg_ctx* h, char* base) {
     const size_t es = (size_t)prec_bytes(h->prec);
     const bool lattice = (h->exec == HOMG_EXEC_LATTICE);
     const bool vcyc = (h->opt.cycle == HOMG_CYCLE_V);
+    const bool pow2 = (h->geometry == HOMG_GEOM_POW2);
     for (int m = 0; m < h->levels; ++m) {
+        if (pow2) {  // four quadrant arrays per level m >= 1; level 0 only holds the fine source
+            Level& lv = h->L[m];
+            const int qn = (m == 0) ? 1 : 4;
+            const size_t bytes = (size_t)qn * (size_t)grid_elems(nd, lv.n, lv.pitch) * es;
+            lv.g = take(bytes);
+            if (m >= 1) {
+                lv.d[0] = take(bytes);
+                lv.d[1] = take(bytes);
+            }
+            continue;
+        }
         Level& lv = h->L[m];
         const size_t bytes = (size_t)grid_elems(nd, lv.n, lv.pitch) * es;
         lv.g = take(bytes);
@@ -225,6 +241,7 @@ size_t layout(homg_ctx* h, char* base) {
     h->L[0].G[1] = h->e[1];
     h->part_r = (double*)take((size_t)h->nparts * sizeof(double));
     h->part_f = (double*)take((size_t)h->nparts * sizeof(double));
+    if (pow2 && h->levels > 1) h->p2tmp = (double*)take((size_t)(h->n + 1) * 2 * (size_t)(h->L[1].n + 1) * sizeof(double));
     h->pstride = (size_t)round_up((int64_t)off, 256);
     off = h->pstride * (size_t)h->nbatch;
     h->dstate = (State*)take((size_t)h->nbatch * sizeof(State));
@@ -332,10 +349,91 @@ void plan_vcycle(homg_ctx* h) {
     h->sched.assign(iters, 0);
 }
 
+// Power-of-two geometry (whole-grid form): part A = restriction of every level m >= 1 from the
+// fine source (hat stencil, two passes) and the iterations on levels >= 1; part B = the level-0
+// iterations (the first one also interpolates the pending level; the others are plain sweeps run by
+// the marching Jacobi kernel).
+void plan_pow2(homg_ctx* h) {
+    h->partA.clear();
+    h->partB.clear();
+    const int N = h->n + 1;
+    auto qs = [&](int m) { return (int64_t)grid_elems(2, h->L[m].n, h->L[m].pitch); };
+    for (int m = 1; m < h->levels; ++m) {
+        Op op{};
+        op.kind = Op::POW2_RESTRICT;
+        op.p2r.N = N;
+        op.p2r.m = m;
+        op.p2r.g0 = cgrid(h->L[0].g, h->pitch0, h->n);
+        op.p2r.tmp = h->p2tmp;
+        op.p2r.gm = grid(h->L[m].g, h->L[m].pitch, h->L[m].n);
+        op.p2r.gm.bstride = qs(m);
+        h->partA.push_back(op);
+    }
+    const std::vector<int>& s = h->sched;
+    const int T = (int)s.size();
+    int tail = T;
+    while (tail > 0 && s[tail - 1] == 0) --tail;
+    h->fine_iters = T - tail;
+    h->coarse_iters = tail;
+    int cur = 0, mprev = -1;
+    int dpar[32] = {0};
+    for (int t = 0; t < T; ++t) {
+        const int m = s[t];
+        Op op{};
+        const bool plain = (m == 0 && mprev <= 0 && t > 0);
+        if (plain) {
+            op.kind = Op::ITER;
+            IterArgs& a = op.it;
+            a.e_old = cgrid(h->e[cur], h->pitch0, h->n);
+            a.e_new = grid(h->e[cur ^ 1], h->pitch0, h->n);
+            a.g = cgrid(h->L[0].g, h->pitch0, h->n);
+            a.m = 0;
+            a.mp = -1;
+            a.dnew = grid(nullptr, 0, 0);
+            set_weights(h, a);
+        } else {
+            op.kind = Op::POW2_ITER;
+            Pow2IterArgs& a = op.p2;
+            a.N = N;
+            a.m = m;
+            a.mp = (mprev >= 1) ? mprev : -1;
+            a.e_old = (t == 0) ? cgrid(nullptr, h->pitch0, h->n) : cgrid(h->e[cur], h->pitch0, h->n);
+            a.e_new = grid(h->e[cur ^ 1], h->pitch0, h->n);
+            if (m == 0) {
+                a.g = cgrid(h->L[0].g, h->pitch0, h->n);
+                a.dnew = grid(nullptr, 0, 0);
+            } else {
+                a.g = cgrid(h->L[m].g, h->L[m].pitch, h->L[m].n);
+                a.g.bstride = qs(m);
+                a.dnew = grid(h->L[m].d[dpar[m]], h->L[m].pitch, h->L[m].n);
+                a.dnew.bstride = qs(m);
+            }
+            if (a.mp >= 1) {
+                const Level& lp = h->L[mprev];
+                a.dprev = cgrid(lp.d[dpar[mprev] ^ 1], lp.pitch, lp.n);
+                a.dprev.bstride = qs(mprev);
+            }
+            a.omega = h->omega;
+            a.c1 = 1.0 - 4.0 * h->omega;
+            a.omega_f = (float)a.omega;
+            a.c1_f = (float)a.c1;
+        }
+        if (m >= 1) dpar[m] ^= 1;
+        (t < tail ? h->partA : h->partB).push_back(op);
+        cur ^= 1;
+        mprev = m;
+    }
+    h->e_final = cur;
+}
+
 // Kernel sequence of one cycle's parts A (restriction + levels >= 1) and B (level 0).
 void plan_cycle(homg_ctx* h) {
     if (h->opt.cycle == HOMG_CYCLE_V) {
         plan_vcycle(h);
+        return;
+    }
+    if (h->geometry == HOMG_GEOM_POW2) {
+        plan_pow2(h);
         return;
     }
     h->partA.clear();
@@ -493,6 +591,8 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
             case Op::VRESID: e = launch_vresid(h->ndim, h->prec, h->strict, op.vr, s); break;
             case Op::PROLONG_ADD: e = launch_prolong_add(h->ndim, h->prec, h->strict, op.pa, s); break;
+            case Op::POW2_ITER: e = launch_pow2_iterate(h->prec, op.p2, s); break;
+            case Op::POW2_RESTRICT: e = launch_pow2_restrict(h->prec, op.p2r, s); break;
             case Op::BLOCK:
                 e = launch_coarse_block(h->ndim, h->prec, h->dblock_ops + op.block_first, op.block_count, h->nbatch, s);
                 break;
@@ -767,8 +867,13 @@ int check_options(int ndim, homg_options& o) {
         (o.launch_mode != HOMG_LAUNCH_GRAPH && o.launch_mode != HOMG_LAUNCH_STREAM) ||
         (o.precision != HOMG_PREC_FP64 && o.precision != HOMG_PREC_FP32 && o.precision != HOMG_PREC_BF16) ||
         (o.cycle != HOMG_CYCLE_HOMG && o.cycle != HOMG_CYCLE_V) || o.v_pre < 0 || o.v_post < 0 || o.v_pre > 64 ||
-        o.v_post > 64 || (o.cycle == HOMG_CYCLE_V && (o.n_schedule > 0 || o.exec_mode == HOMG_EXEC_WHOLEGRID)))
+        o.v_post > 64 || (o.cycle == HOMG_CYCLE_V && (o.n_schedule > 0 || o.exec_mode == HOMG_EXEC_WHOLEGRID)) ||
+        (o.geometry != HOMG_GEOM_NESTED && o.geometry != HOMG_GEOM_POW2))
         return fail(nullptr, HOMG_EINVAL, "homg_create: invalid options%s%s");
+    if (o.geometry == HOMG_GEOM_POW2 &&
+        (ndim != 2 || o.cycle != HOMG_CYCLE_HOMG || o.strict_fp || o.exec_mode == HOMG_EXEC_LATTICE))
+        return fail(nullptr, HOMG_EINVAL,
+                    "homg_create: power-of-two grids are 2-D HOMG cycles in the whole-grid fast form%s%s");
     return HOMG_OK;
 }
 
@@ -785,6 +890,7 @@ int create_ctx(int ndim, int64_t n, int K, int levels, int stencil, const homg_o
     h->opt = o;
     h->strict = (o.strict_fp == 1);
     h->prec = o.precision;
+    h->geometry = o.geometry;
     h->nbatch = nbatch;
     h->omega = o.omega_j / (2.0 * ndim);
     if (o.n_schedule > 0) {
@@ -814,6 +920,7 @@ int create_ctx(int ndim, int64_t n, int K, int levels, int stencil, const homg_o
     }
     h->exec = (o.exec_mode == HOMG_EXEC_WHOLEGRID || !mono) ? HOMG_EXEC_WHOLEGRID : HOMG_EXEC_LATTICE;
     if (o.cycle == HOMG_CYCLE_V) h->exec = HOMG_EXEC_LATTICE;  // level arrays are compact by nature
+    if (o.geometry == HOMG_GEOM_POW2) h->exec = HOMG_EXEC_WHOLEGRID;
 
     cudaError_t ce = cudaGetDevice(&h->device);
     if (ce != cudaSuccess) {
@@ -824,7 +931,8 @@ int create_ctx(int ndim, int64_t n, int K, int levels, int stencil, const homg_o
     h->pitch0 = round_up(n + 1, 16);
     h->L.resize(levels);
     for (int m = 0; m < levels; ++m) {
-        h->L[m].n = (int)(n >> m);
+        // power-of-two grids: n + 1 = 2^K nodes; level m >= 1 holds quadrant lattices of n_m = 2^(K-1-m)
+        h->L[m].n = (m == 0) ? (int)n : (o.geometry == HOMG_GEOM_POW2 ? (int)(((n + 1) / 2) >> m) : (int)(n >> m));
         h->L[m].pitch = (m == 0) ? h->pitch0 : round_up(h->L[m].n + 1, 16);
     }
     h->nparts = residual_blocks(ndim, h->strict, (int)n);
@@ -867,12 +975,20 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
         return fail(nullptr, HOMG_EINVAL, "homg_create: stencil must be 5 (2-D) or 7 (3-D)%s%s");
     for (int d = 1; d < ndim; ++d)
         if (dims[d] != dims[0]) return fail(nullptr, HOMG_ESHAPE, "homg_create: grid sides must be equal%s%s");
-    const int K = grid_exponent(ndim, dims[0], "homg_create");
-    if (K < 0) return K;
-    if (levels < 1 || levels > K) return fail(nullptr, HOMG_EINVAL, "homg_create: levels must be in [1, K]%s%s");
     homg_options o;
     homg_default_options(&o);
     if (opt) o = *opt;
+    int K;
+    if (o.geometry == HOMG_GEOM_POW2) {
+        K = 0;
+        while (K < 62 && ((int64_t)1 << K) < dims[0]) ++K;
+        if (dims[0] < 4 || ((int64_t)1 << K) != dims[0] || K > HOMG_MAX_K_2D)
+            return fail(nullptr, HOMG_ESHAPE, "homg_create: power-of-two grid side must be 2^K with 2 <= K <= HOMG_MAX_K_2D%s%s");
+    } else {
+        K = grid_exponent(ndim, dims[0], "homg_create");
+        if (K < 0) return K;
+    }
+    if (levels < 1 || levels > K) return fail(nullptr, HOMG_EINVAL, "homg_create: levels must be in [1, K]%s%s");
     int rc = check_options(ndim, o);
     if (rc != HOMG_OK) return rc;
     homg_ctx* h = nullptr;
@@ -982,7 +1098,7 @@ int homg_batch_create(int nprob, const int64_t* sides, const homg_options* opt, 
     int rc = check_options(2, o);
     if (rc != HOMG_OK) return rc;
     if (o.strict_fp || o.exec_mode == HOMG_EXEC_WHOLEGRID || o.n_schedule > 0 || o.cycle != HOMG_CYCLE_HOMG ||
-        o.launch_mode != HOMG_LAUNCH_GRAPH)
+        o.launch_mode != HOMG_LAUNCH_GRAPH || o.geometry != HOMG_GEOM_NESTED)
         return fail(nullptr, HOMG_EINVAL,
                     "homg_batch_create: batches use fast arithmetic, the lattice form, MFMG and graph launches%s%s");
     std::vector<int64_t> distinct;

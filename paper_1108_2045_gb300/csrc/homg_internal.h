@@ -177,6 +177,31 @@ struct CopyOutArgs {
     CDGrid u1;   // ... after an odd number
 };
 
+// Power-of-two grids (Sec. 3): N = 2^K nodes per side, four quadrant lattices per level m >= 1,
+// each marked from its external corner (local nodes (a, b), 0 <= a, b <= n_m = (N/2) >> m), one
+// row/column past the centre lines; quadrant q's level arrays sit at q * bstride elements.
+struct Pow2IterArgs {
+    int N;          // nodes per side; fine arrays hold N rows of `pitch` elements
+    int m;          // relaxation level (0: every interior node)
+    int mp;         // pending level >= 1, or -1
+    CGrid e_old;    // fine iterate (p == nullptr: 0)
+    Grid e_new;
+    CGrid g;        // m = 0: fine source; m >= 1: the four quadrant arrays (pre-scaled: omega h_m^2 F)
+    CGrid dprev;    // level mp: four quadrant arrays
+    Grid dnew;      // level m >= 1: four quadrant arrays (p == nullptr: not stored)
+    double omega, c1;
+    float omega_f, c1_f;
+};
+
+// Level-m sources from the fine source g0 by the separable hat stencil (the m-fold nested full
+// weighting), times 4^m to keep the h_m^2 scaling: a row pass into tmp, then a column pass.
+struct Pow2RestrictArgs {
+    int N, m;
+    CGrid g0;       // fine source
+    double* tmp;    // N rows x 2 x (n_m + 1)
+    Grid gm;        // the four quadrant arrays of level m
+};
+
 // One op of the coarse-lattice block kernel (fast forms, lattice form only).
 enum BlockKind { BLOCK_RESTRICT = 0, BLOCK_PROLONG = 1, BLOCK_ITER = 2 };
 
@@ -197,6 +222,8 @@ cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs&
 cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, int nb, cudaStream_t s);
 cudaError_t launch_vresid(int ndim, int prec, bool strict, const VResidArgs& a, cudaStream_t s);
 cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAddArgs& a, cudaStream_t s);
+cudaError_t launch_pow2_iterate(int prec, const Pow2IterArgs& a, cudaStream_t s);
+cudaError_t launch_pow2_restrict(int prec, const Pow2RestrictArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 // Variable coefficients of level m from the node coefficient k ((n+1)^2, unpadded, FP64): for each
 // lattice node the east- and north-face harmonic means and (wd != nullptr) the weight omega_J / D,

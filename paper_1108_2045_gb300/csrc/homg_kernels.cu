@@ -1151,6 +1151,135 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     }
 }
 
+// =============================================================================================
+// Power-of-two grids (Sec. 3), whole-grid form.
+// =============================================================================================
+// Local lattice index of fine index x along one axis for quadrant half qb at level m >= 1, or -1.
+__device__ __forceinline__ int p2_local(int N, int m, int qb, int x) {
+    const int d = qb ? (N - 1 - x) : x;
+    if (d & ((1 << m) - 1)) return -1;
+    const int a = d >> m;
+    return a <= ((N >> 1) >> m) ? a : -1;
+}
+
+// Marked at level m >= 1 (an interior node of one quadrant's lattice): quadrant and local indexes.
+// The halves' lattices are disjoint along each axis (N - 1 is odd), so at most one matches.
+__device__ __forceinline__ bool p2_marked(int N, int m, int x, int y, int& q, int& a, int& b) {
+    const int a0 = p2_local(N, m, 0, x), b0 = p2_local(N, m, 0, y);
+    a = a0 >= 0 ? a0 : p2_local(N, m, 1, x);
+    b = b0 >= 0 ? b0 : p2_local(N, m, 1, y);
+    q = (a0 >= 0 ? 0 : 1) | ((b0 >= 0 ? 0 : 1) << 1);
+    return a > 0 && b > 0;
+}
+
+// One whole-grid iteration: relax the nodes marked at level m (fast form v' = c1 v + omega sum + g,
+// neighbours at distance 2^m, 0 outside the grid), store the variation in the quadrant's array, and
+// add the bilinear interpolation of the pending level-mp variation from the node's own quadrant at
+// the nodes not marked at level mp.
+template <typename T>
+__global__ void __launch_bounds__(BX * BY) k_pow2_iterate(Pow2IterArgs a) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    const int N = a.N;
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+    if (x >= N || y >= N) return;
+    T* O = wp<T>(a.e_new);
+    const int64_t po = a.e_new.pitch;
+    if (x == 0 || y == 0 || x == N - 1 || y == N - 1) {
+        O[(int64_t)y * po + x] = St<T>::put((C)0);
+        return;
+    }
+    const T* E = cp<T>(a.e_old);
+    const int64_t pe = a.e_old.pitch;
+    auto ev = [&](int xx, int yy) -> C {
+        if (E == nullptr || xx < 0 || yy < 0 || xx >= N || yy >= N) return (C)0;
+        return St<T>::ld(E + (int64_t)yy * pe + xx);
+    };
+    C v = ev(x, y);
+    int q = 0, la = 0, lb = 0;
+    if (a.m == 0 || p2_marked(N, a.m, x, y, q, la, lb)) {
+        const int l = 1 << a.m;
+        const C sum = (ev(x - l, y) + ev(x + l, y)) + (ev(x, y - l) + ev(x, y + l));
+        const C g = (a.m == 0) ? St<T>::ld(cp<T>(a.g) + (int64_t)y * a.g.pitch + x)
+                               : St<T>::ld(cp<T>(a.g) + (int64_t)q * a.g.bstride + (int64_t)lb * a.g.pitch + la);
+        const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
+        const C nv = fma(c1, v, fma(om, sum, g));
+        if (a.dnew.p) wp<T>(a.dnew)[(int64_t)q * a.dnew.bstride + (int64_t)lb * a.dnew.pitch + la] = St<T>::put(nv - v);
+        v = nv;
+    }
+    int q2, a2, b2;
+    if (a.mp >= 1 && !p2_marked(N, a.mp, x, y, q2, a2, b2)) {
+        const int H = N >> 1, qx = x >= H, qy = y >= H, lp = 1 << a.mp;
+        const int dx = qx ? N - 1 - x : x, dy = qy ? N - 1 - y : y;
+        const int A0 = dx >> a.mp, fa = dx & (lp - 1), B0 = dy >> a.mp, fb = dy & (lp - 1);
+        const int A1 = fa ? A0 + 1 : A0, B1 = fb ? B0 + 1 : B0;
+        const T* D = cp<T>(a.dprev) + (int64_t)(qx | (qy << 1)) * a.dprev.bstride;
+        const int64_t pd = a.dprev.pitch;
+        const C inv = pow2<C>(-a.mp);
+        const C wx0 = (C)(lp - fa) * inv, wx1 = (C)fa * inv, wy0 = (C)(lp - fb) * inv, wy1 = (C)fb * inv;
+        const C d00 = St<T>::ld(D + (int64_t)B0 * pd + A0), d10 = St<T>::ld(D + (int64_t)B0 * pd + A1);
+        const C d01 = St<T>::ld(D + (int64_t)B1 * pd + A0), d11 = St<T>::ld(D + (int64_t)B1 * pd + A1);
+        v += ((wx0 * wy0) * d00 + (wx1 * wy0) * d10) + ((wx0 * wy1) * d01 + (wx1 * wy1) * d11);
+    }
+    O[(int64_t)y * po + x] = St<T>::put(v);
+}
+
+// Hat-weighted sum sum_{|d| < l} (l - |d|)/l * f(d) over one stencil line: by one thread (short
+// lines) or by a warp (long lines, lanes striding, shuffle reduction).
+template <bool WARP, typename F>
+__device__ __forceinline__ double hat_sum(int l, F f) {
+    double acc = 0.0;
+    const double inv = 1.0 / (double)l;  // exact: l is a power of two
+    if (!WARP) {
+        for (int d = -(l - 1); d <= l - 1; ++d) acc = fma((double)(l - abs(d)) * inv, f(d), acc);
+        return acc;
+    }
+    for (int d = -(l - 1) + (int)(threadIdx.x & 31); d <= l - 1; d += 32) acc = fma((double)(l - abs(d)) * inv, f(d), acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Row pass: tmp[(y*2 + qx)*(n_m+1) + a] = hat sum of g0 along row y around x(qx, a).
+template <typename T, bool WARP>
+__global__ void k_pow2_rows(Pow2RestrictArgs r) {
+    pdl_begin();
+    const int N = r.N, m = r.m, l = 1 << m, nm = (N >> 1) >> m;
+    const int64_t outs = (int64_t)N * 2 * (nm + 1);
+    const int64_t id = WARP ? ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= outs) return;
+    const int a = (int)(id % (nm + 1)), qx = (int)((id / (nm + 1)) % 2), y = (int)(id / (2 * (nm + 1)));
+    const int x = qx ? N - 1 - a * l : a * l;
+    const T* G = cp<T>(r.g0) + (int64_t)y * r.g0.pitch;
+    const double s = hat_sum<WARP>(l, [&](int d) -> double {
+        const int xx = x + d;
+        return (xx < 0 || xx >= N) ? 0.0 : (double)St<T>::ld(G + xx);
+    });
+    if (!WARP || (threadIdx.x & 31) == 0) r.tmp[id] = s;
+}
+
+// Column pass: gm[q][b][a] = hat sum of tmp down column (qx, a) around y(qy, b); 0 on the domain
+// boundary (a == 0 or b == 0).
+template <typename T, bool WARP>
+__global__ void k_pow2_cols(Pow2RestrictArgs r) {
+    pdl_begin();
+    const int N = r.N, m = r.m, l = 1 << m, nm = (N >> 1) >> m;
+    const int64_t outs = (int64_t)4 * (nm + 1) * (nm + 1);
+    const int64_t id = WARP ? ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= outs) return;
+    const int a = (int)(id % (nm + 1)), b = (int)((id / (nm + 1)) % (nm + 1)), q = (int)(id / ((int64_t)(nm + 1) * (nm + 1)));
+    const int qx = q & 1, qy = q >> 1;
+    const int y = qy ? N - 1 - b * l : b * l;
+    double s = 0.0;
+    if (a > 0 && b > 0)
+        s = hat_sum<WARP>(l, [&](int d) -> double {
+            const int yy = y + d;
+            return (yy < 0 || yy >= N) ? 0.0 : r.tmp[((int64_t)yy * 2 + qx) * (nm + 1) + a];
+        });
+    // times 4^m = l^2 keeps the source pre-scaled by h_m^2: each pass carries a factor l
+    if (!WARP || (threadIdx.x & 31) == 0)
+        wp<T>(r.gm)[(int64_t)q * r.gm.bstride + (int64_t)b * r.gm.pitch + a] = St<T>::put(St<T>::from_d(s));
+}
+
 // Nodes per thread along the march: long columns on large launches (fewer blocks, more reuse),
 // short ones on small launches, where a thread's serial chain of loads would otherwise set the
 // time. `nb` problems of a batch share the launch.
@@ -1349,6 +1478,37 @@ cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a,
 
 cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s) {
     DISPATCH_PREC(prec, restrict_t<T>(ndim, strict, a, s));
+}
+
+cudaError_t launch_pow2_iterate(int prec, const Pow2IterArgs& a, cudaStream_t s) {
+    const dim3 g((unsigned)((a.N + BX - 1) / BX), (unsigned)((a.N + BY - 1) / BY)), b(BX, BY);
+    DISPATCH_PREC(prec, (launch_k(k_pow2_iterate<T>, g, b, s, a), cudaGetLastError()));
+}
+
+cudaError_t launch_pow2_restrict(int prec, const Pow2RestrictArgs& a, cudaStream_t s) {
+    const int l = 1 << a.m, nm = (a.N >> 1) >> a.m;
+    const bool warp = l > 16;
+    const int64_t rows = (int64_t)a.N * 2 * (nm + 1), cols = (int64_t)4 * (nm + 1) * (nm + 1);
+    const int64_t tr = warp ? rows * 32 : rows, tc = warp ? cols * 32 : cols;
+    const dim3 gr((unsigned)((tr + 255) / 256)), gc((unsigned)((tc + 255) / 256));
+    cudaError_t e = cudaSuccess;
+    switch (prec) {
+        case PREC_FP64:
+            e = warp ? launch_k(k_pow2_rows<double, true>, gr, 256, s, a) : launch_k(k_pow2_rows<double, false>, gr, 256, s, a);
+            if (e == cudaSuccess) e = warp ? launch_k(k_pow2_cols<double, true>, gc, 256, s, a) : launch_k(k_pow2_cols<double, false>, gc, 256, s, a);
+            break;
+        case PREC_FP32:
+            e = warp ? launch_k(k_pow2_rows<float, true>, gr, 256, s, a) : launch_k(k_pow2_rows<float, false>, gr, 256, s, a);
+            if (e == cudaSuccess) e = warp ? launch_k(k_pow2_cols<float, true>, gc, 256, s, a) : launch_k(k_pow2_cols<float, false>, gc, 256, s, a);
+            break;
+        case PREC_BF16:
+            e = warp ? launch_k(k_pow2_rows<__nv_bfloat16, true>, gr, 256, s, a) : launch_k(k_pow2_rows<__nv_bfloat16, false>, gr, 256, s, a);
+            if (e == cudaSuccess) e = warp ? launch_k(k_pow2_cols<__nv_bfloat16, true>, gc, 256, s, a) : launch_k(k_pow2_cols<__nv_bfloat16, false>, gc, 256, s, a);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_vc_setup(const double* k, int n, int m, bool dbl, void* kx, void* ky, void* wd, int64_t pitch,

@@ -76,6 +76,7 @@ class homg_options(ctypes.Structure):
         ("cycle", ctypes.c_int),
         ("v_pre", ctypes.c_int),
         ("v_post", ctypes.c_int),
+        ("geometry", ctypes.c_int),
     ]
 
 
@@ -194,8 +195,12 @@ def _check(rc, handle):
     return rc
 
 
+GEOMETRIES = {"nested": 0, "pow2": 1}
+HOMG_GEOM_NESTED, HOMG_GEOM_POW2 = 0, 1
+
+
 def _options(omega_j=0.0, max_i=32, schedule=None, exec_mode="auto", strict_fp=False, diverge_factor=0.0,
-             launch_mode="graph", precision="fp64", cycle="homg", v_pre=0, v_post=0):
+             launch_mode="graph", precision="fp64", cycle="homg", v_pre=0, v_post=0, geometry="nested"):
     o = homg_default_options()
     o.omega_j = omega_j
     o.max_i = max_i
@@ -207,6 +212,7 @@ def _options(omega_j=0.0, max_i=32, schedule=None, exec_mode="auto", strict_fp=F
     o.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
     o.v_pre = v_pre
     o.v_post = v_post
+    o.geometry = GEOMETRIES[geometry] if isinstance(geometry, str) else int(geometry)
     keep = None
     if schedule is not None:
         keep = (ctypes.c_int * len(schedule))(*schedule)
@@ -283,27 +289,12 @@ class BatchSolver:
         return False
 
 
-def homg_create(ndim, n_nodes, levels, stencil=None, omega_j=0.0, max_i=32, schedule=None, exec_mode="auto",
-                strict_fp=False, diverge_factor=0.0, launch_mode="graph", precision="fp64", cycle="homg", v_pre=0,
-                v_post=0):
-    """Create a handle for an (n_nodes)^ndim grid; returns an opaque handle (int)."""
+def homg_create(ndim, n_nodes, levels, stencil=None, **opts):
+    """Create a handle for an (n_nodes)^ndim grid; returns an opaque handle (int). Options as in
+    homg_options (omega_j, max_i, schedule, exec_mode, strict_fp, diverge_factor, launch_mode,
+    precision, cycle, v_pre, v_post, geometry)."""
     lib = load()
-    o = homg_default_options()
-    o.omega_j = omega_j
-    o.max_i = max_i
-    o.exec_mode = EXEC_MODES[exec_mode] if isinstance(exec_mode, str) else int(exec_mode)
-    o.strict_fp = 1 if strict_fp else 0
-    o.diverge_factor = diverge_factor
-    o.launch_mode = LAUNCH_MODES[launch_mode] if isinstance(launch_mode, str) else int(launch_mode)
-    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    o.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
-    o.v_pre = v_pre
-    o.v_post = v_post
-    keep = None
-    if schedule is not None:
-        keep = (ctypes.c_int * len(schedule))(*schedule)
-        o.n_schedule = len(schedule)
-        o.schedule = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    o, _keep = _options(**opts)
     dims = (ctypes.c_int64 * ndim)(*([n_nodes] * ndim))
     h = ctypes.c_void_p()
     stencil = stencil if stencil is not None else (5 if ndim == 2 else 7)

@@ -105,3 +105,21 @@ def test_binding_refuses_host_tensors_for_device_calls(homg):
 
     with pytest.raises(TypeError):
         homg._devptr(torch.zeros(3, dtype=torch.float64), "f")
+
+
+def test_power_of_two_geometry_argument_checks(homg):
+    cases = [((2, 129, 5), {}, homg.HOMG_ESHAPE),          # 2^K + 1 is the nested geometry's side
+             ((2, 2, 1), {}, homg.HOMG_ESHAPE),            # K >= 2
+             ((2, 64, 7), {}, homg.HOMG_EINVAL),           # levels <= K
+             ((3, 64, 3), {}, homg.HOMG_EINVAL),           # 2-D only
+             ((2, 64, 4), dict(strict_fp=True), homg.HOMG_EINVAL),
+             ((2, 64, 4), dict(exec_mode="lattice"), homg.HOMG_EINVAL),
+             ((2, 64, 4), dict(cycle="v"), homg.HOMG_EINVAL)]
+    for args, kw, code in cases:
+        with pytest.raises(homg.HomgError) as ei:
+            homg.homg_create(*args, geometry="pow2", **kw)
+        assert ei.value.code == code, (args, kw)
+    with pytest.raises(homg.HomgError):
+        homg.homg_create(2, 33, 3, geometry=7)
+    with pytest.raises(homg.HomgError):
+        homg.homg_batch_create([33, 65], geometry="pow2")
