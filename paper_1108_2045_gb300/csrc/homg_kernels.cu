@@ -634,10 +634,10 @@ struct ColumnInterp2 {
 // (2-D: along y; 3-D: along z) keeping the centre and its two neighbours along the march in
 // registers; the other neighbours come through L1. In FP64 the FP64 pipe bounds this kernel on
 // GB300; in FP32/bfloat16, DRAM does.
-template <int PEND, bool WD, typename T>
+template <int PEND, bool WD, typename T, bool BATCH>
 __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
     pdl_begin();
-    if (!batch_view<T>(a, blockIdx.z)) return;
+    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // compiled into batch launches only
     using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -799,10 +799,10 @@ __global__ void k_vc_setup(const double* __restrict__ k, int n, int m, K* kx, K*
 
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
 // stride-2 interpolant of Gc - dl, formed along each marching column (see ColumnInterp2).
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
     pdl_begin();
-    if (!batch_view<T>(a, blockIdx.z)) return;
+    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // compiled into batch launches only
     using C = typename St<T>::C;
     const int n = a.G.n;
     const int i = blockIdx.x * JX + threadIdx.x + 1;
@@ -1342,7 +1342,7 @@ cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) 
         if (ndim == 2) {
             const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
             const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
-#define JAC2(P, W) launch_k(k_jacobi2<P, W, T>, g, b, s, a, rows)
+#define JAC2(P, W) (a.bst ? launch_k(k_jacobi2<P, W, T, true>, g, b, s, a, rows) : launch_k(k_jacobi2<P, W, T, false>, g, b, s, a, rows))
             if (pend == 0) { if (wd) JAC2(0, true); else JAC2(0, false); }
             else if (pend == 1) { if (wd) JAC2(1, true); else JAC2(1, false); }
             else { if (wd) JAC2(2, true); else JAC2(2, false); }
@@ -1384,7 +1384,8 @@ cudaError_t prolong_t(int ndim, bool strict, const ProlongArgs& a, cudaStream_t 
         const int n = a.G.n;
         const int rows = march_rows(2, n, a.nb);
         const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb);
-        launch_k(k_prolong2_s1<T>, g, dim3(JX), s, a, rows);
+        if (a.bst) launch_k(k_prolong2_s1<T, true>, g, dim3(JX), s, a, rows);
+        else launch_k(k_prolong2_s1<T, false>, g, dim3(JX), s, a, rows);
         return cudaGetLastError();
     }
     if (!strict && ndim == 3 && a.s == 1) {
