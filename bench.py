@@ -39,6 +39,7 @@ FP64_PEAK_OPS = 0.625e12
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
+LEVEL0_FP64_DRAM_BYTES = 382.45e6  # k_jacobi2<0, 0, double> on 4097^2, mean of two captured launches
 
 
 def measured_peaks():
@@ -663,8 +664,13 @@ def run(args):
     hbm_achieved = bts / per_launch_s / 1e9
     clk = clocks.summary()
     kname = "k_jacobi2 (level-0 HOMG iteration: damped Jacobi on every interior node)"
+    # DRAM bytes (read + write) per launch of this kernel from ncu (profiles/k_jacobi2_fp64_4097.md);
+    # only the FP64 build of the kernel was captured in its current form
+    traffic = LEVEL0_FP64_DRAM_BYTES if args.precision == "fp64" else None
     common = {"kernel": kname, "launch_us": per_launch_s * 1e6, "launches": launches,
-              "algorithmic_flops_per_launch": ops, "algorithmic_bytes_per_launch": bts, "traffic": None}
+              "algorithmic_flops_per_launch": ops, "algorithmic_bytes_per_launch": bts, "traffic": traffic,
+              "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_jacobi2_fp64_4097.md"
+              if traffic else None}
     if args.precision == "fp64":
         # FP64 pipe bound on GB300: 5 FP64 instructions per node against 0.625e12 instructions/s
         roofline = dict(common, bound="alu", achieved=alu_achieved, peak=FP64_PEAK_OPS / 1e12, unit="TFP64op/s",
