@@ -1162,6 +1162,22 @@ __device__ __forceinline__ int p2_local(int N, int m, int qb, int x) {
     return a <= ((N >> 1) >> m) ? a : -1;
 }
 
+// f * 2^-e for 0 <= f < 2^e (e <= 30), exactly, assembled from the IEEE-754 fields with integer
+// operations only: exponent floor(log2 f) - e, fraction the bits of f below its leading one.
+template <typename C> __device__ __forceinline__ C dyadic(int f, int e);
+template <> __device__ __forceinline__ double dyadic<double>(int f, int e) {
+    if (f == 0) return 0.0;
+    const int p = 31 - __clz(f);
+    const unsigned long long frac = ((unsigned long long)f << (52 - p)) & ((1ull << 52) - 1);
+    return __longlong_as_double((long long)(((unsigned long long)(p - e + 1023) << 52) | frac));
+}
+template <> __device__ __forceinline__ float dyadic<float>(int f, int e) {
+    if (f == 0) return 0.f;
+    const int p = 31 - __clz(f);
+    const unsigned frac = ((unsigned)f << (23 - p)) & ((1u << 23) - 1);
+    return __uint_as_float(((unsigned)(p - e + 127) << 23) | frac);
+}
+
 // Marked at level m >= 1 (an interior node of one quadrant's lattice): quadrant and local indexes.
 // The halves' lattices are disjoint along each axis (N - 1 is odd), so at most one matches.
 __device__ __forceinline__ bool p2_marked(int N, int m, int x, int y, int& q, int& a, int& b) {
@@ -1209,17 +1225,19 @@ __global__ void __launch_bounds__(BX * BY) k_pow2_iterate(Pow2IterArgs a) {
     }
     int q2, a2, b2;
     if (a.mp >= 1 && !p2_marked(N, a.mp, x, y, q2, a2, b2)) {
+        // bilinear as two x-lerps and a y-lerp (7 FP instructions); the dyadic weights f 2^-mp are
+        // built from integer bits, so no floating-point work goes into them
         const int H = N >> 1, qx = x >= H, qy = y >= H, lp = 1 << a.mp;
         const int dx = qx ? N - 1 - x : x, dy = qy ? N - 1 - y : y;
         const int A0 = dx >> a.mp, fa = dx & (lp - 1), B0 = dy >> a.mp, fb = dy & (lp - 1);
         const int A1 = fa ? A0 + 1 : A0, B1 = fb ? B0 + 1 : B0;
         const T* D = cp<T>(a.dprev) + (int64_t)(qx | (qy << 1)) * a.dprev.bstride;
         const int64_t pd = a.dprev.pitch;
-        const C inv = pow2<C>(-a.mp);
-        const C wx0 = (C)(lp - fa) * inv, wx1 = (C)fa * inv, wy0 = (C)(lp - fb) * inv, wy1 = (C)fb * inv;
+        const C wx = dyadic<C>(fa, a.mp), wy = dyadic<C>(fb, a.mp);
         const C d00 = St<T>::ld(D + (int64_t)B0 * pd + A0), d10 = St<T>::ld(D + (int64_t)B0 * pd + A1);
         const C d01 = St<T>::ld(D + (int64_t)B1 * pd + A0), d11 = St<T>::ld(D + (int64_t)B1 * pd + A1);
-        v += ((wx0 * wy0) * d00 + (wx1 * wy0) * d10) + ((wx0 * wy1) * d01 + (wx1 * wy1) * d11);
+        const C r0 = fma(wx, d10 - d00, d00), r1 = fma(wx, d11 - d01, d01);
+        v += fma(wy, r1 - r0, r0);
     }
     O[(int64_t)y * po + x] = St<T>::put(v);
 }
