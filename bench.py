@@ -266,7 +266,10 @@ def run_cfg4(args, homg, stream, barrier, pending):
     del fs, us
     torch.cuda.empty_cache()
     if args.cfg4_oracle_time:
-        per_k = {k: (fs_np[int(np.flatnonzero(ks_arr == k)[0])], int((ks_arr == k).sum())) for k in range(6, 11)}
+        # problems timed per size (the first ones of each size in batch order), bounded CPU time
+        nsample = {6: 8, 7: 8, 8: 4, 9: 2, 10: 1}
+        per_k = {k: ([fs_np[int(i)] for i in np.flatnonzero(ks_arr == k)[:nsample[k]]], int((ks_arr == k).sum()))
+                 for k in range(6, 11)}
         pending.append((out, "batch_time", None, per_k, unknowns))
     return out
 
@@ -384,6 +387,52 @@ def run_cfg5(args, homg, stream, barrier, pending):
     return out
 
 
+def run_cfg1(args, homg, stream, barrier, pending):
+    """cfg1: 129^2 nodes, 7 levels, f = 2 pi^2 sin(pi x) sin(pi y), to relres 1e-10 (the small case
+    the oracle solves in full, timed beside it in the CPU leg); and T-paper: one cycle on the Sec. 4
+    polynomial problem at 129^2 with MaxI 2, 4 and 32, the normalised L1 error against the analytic
+    solution (the quantity of Fig. 4; the paper prints 5 % and 1.6 % for MaxI 4 and 32)."""
+    import numpy as np
+    import torch
+
+    from paper_1108_2045_gb300 import inputs
+
+    n, L = 128, 7
+    f_np = inputs.sine_rhs(n, 2)
+    f = torch.from_numpy(f_np).cuda()
+    u = torch.zeros_like(f)
+    out = {"workload": "2-D Poisson, 129^2 nodes, 7 levels, f = 2 pi^2 sin sin, to relres 1e-10"}
+    with homg.Solver(2, n + 1, L, max_i=MAX_I) as s:
+        s.set_stream(stream)
+        u.zero_()
+        s.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.cfg1_steps):
+            u.zero_()
+            st, cyc, rr = s.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / args.cfg1_steps
+    out.update(status=st, cycles=cyc, relres=rr, ms_per_solve=ms, unknowns_per_s=(n - 1) ** 2 / (ms * 1e-3))
+    if args.cfg1_oracle_time:
+        pending.append((out, "full_solve_time", None, f_np, L))
+    fp = torch.from_numpy(inputs.paper_poly_rhs(n)).cuda()
+    ue = inputs.paper_poly_solution(n)
+    tp = {}
+    for maxi in (2, 4, 32):
+        with homg.Solver(2, n + 1, L, max_i=maxi) as s:
+            s.set_stream(stream)
+            up = torch.zeros_like(fp)
+            s.solve(fp, up, tol=0.0, max_cycles=1)
+            got = up.cpu().numpy()
+        tp["max_i_%d" % maxi] = float(np.abs(got - ue).sum() / np.abs(ue).sum())
+    out["tpaper_l1_error_one_cycle"] = tp
+    return out
+
+
 def run_pow2(args, homg, stream, barrier, pending):
     """Power-of-two grids (Sec. 3): 4096^2 nodes (boundary included), 12 levels, f iid uniform[-1, 1]
     over the interior (seed 0), whole-grid form, to relres 1e-10, FP64 and FP32 cycles."""
@@ -441,15 +490,28 @@ def cpu_leg(pending):
             target["oracle_relres"] = oracle.norm_interior(oracle.residual_vc(kc, a, b)) / oracle.norm_interior(a)
         elif kind == "batch_time":
             est, per_k = 0.0, {}
-            for kk, (fk, cnt) in a.items():
-                t0 = time.perf_counter()
-                _, status, cyc, _ = oracle.solve_mixed(fk, kk, precision="fp32", tol=TOL, max_cycles=MAX_CYCLES)
-                dt = time.perf_counter() - t0
-                per_k[str(kk)] = {"seconds": dt, "cycles": cyc, "status": status}
-                est += dt * cnt
+            for kk, (fks, cnt) in a.items():
+                times, cycs = [], []
+                for fk in fks:
+                    t0 = time.perf_counter()
+                    _, status, cyc, _ = oracle.solve_mixed(fk, kk, precision="fp32", tol=TOL, max_cycles=MAX_CYCLES)
+                    times.append(time.perf_counter() - t0)
+                    cycs.append(cyc)
+                mean = sum(times) / len(times)
+                per_k[str(kk)] = {"sampled": len(fks), "mean_seconds": mean, "cycles": cycs}
+                est += mean * cnt
             target["cpu_oracle"] = {"value": b / est, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "one FP32-cycle oracle solve per size, timed and multiplied by the problems "
-                                              "of that size (%.0f s estimated for the batch)" % est, "per_k": per_k}
+                                    "sample": "FP32-cycle oracle solves of 8/8/4/2/1 problems of sides 65..1025, mean time "
+                                              "per size times the problems of that size (%.0f s estimated for the batch)" % est,
+                                    "per_k": per_k}
+        elif kind == "full_solve_time":
+            t0 = time.perf_counter()
+            _, status, cyc, _ = oracle.solve(a, b, tol=TOL, max_cycles=MAX_CYCLES, max_i=MAX_I)
+            dt = time.perf_counter() - t0
+            n = a.shape[0] - 1
+            target["cpu_oracle"] = {"value": (n - 1) ** 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "the full oracle solve (%d cycles, %.2f s)" % (cyc, dt),
+                                    "ms_per_solve": 1e3 * dt}
         elif kind == "vc_time":
             t0 = time.perf_counter()
             oracle.cycle_vc(kc, a, CFG5_LEVELS)
@@ -649,6 +711,7 @@ def run(args):
                           "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
                                                      for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
     pending = []  # oracle work of the CPU leg (rank 0, one GPU only)
+    cfg1 = run_cfg1(args, homg, stream, barrier, pending) if (args.cfg1_steps > 0 and world == 1) else None
     cfg3 = run_cfg3(args, homg, inputs, stream, barrier, pending) if (args.cfg3_steps > 0 and world == 1) else None
     cfg4 = run_cfg4(args, homg, stream, barrier, pending) if (args.cfg4_steps > 0 and world == 1) else None
     cfg5 = run_cfg5(args, homg, stream, barrier, pending) if (args.cfg5_steps > 0 and world == 1) else None
@@ -708,6 +771,8 @@ def run(args):
         line["vcycle_v22"] = vcyc
     if args.cfg3_steps > 0 and world == 1:
         line["cfg3_3d"] = cfg3
+    if cfg1:
+        line["cfg1_small"] = cfg1
     if cfg4:
         line["cfg4_batched"] = cfg4
     if cfg5:
@@ -750,6 +815,8 @@ def main():
     p.add_argument("--cfg5-seed", type=int, default=0, help="seed of the network's initial parameters")
     p.add_argument("--no-cfg5-oracle-check", dest="cfg5_oracle_check", action="store_false")
     p.add_argument("--no-cfg5-oracle-time", dest="cfg5_oracle_time", action="store_false")
+    p.add_argument("--cfg1-steps", type=int, default=5, help="timed solves of the 129^2 case (0: skip)")
+    p.add_argument("--no-cfg1-oracle-time", dest="cfg1_oracle_time", action="store_false")
     p.add_argument("--pow2-steps", type=int, default=2, help="timed solves on the 4096^2 power-of-two grid (0: skip)")
     p.add_argument("--no-pow2-oracle-check", dest="pow2_oracle_check", action="store_false")
     p.add_argument("--no-cfg3-oracle-check", dest="cfg3_oracle_check", action="store_false")
