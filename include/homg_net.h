@@ -79,6 +79,13 @@ int homg_net_train_step(homg_net_handle net, const void* x, const float* t, int 
 int homg_net_gather_patches(homg_net_handle net, const void* x, const float* t, int H, int W, const int32_t* corners,
                             int B, int P, void* xp, float* tp);
 
+/* Self-test of the failure path: launches one convolution whose tensor-core completion barrier
+ * is never signalled (no MMA is issued). Every wait on such a barrier gives up after 0.5 s, records
+ * the failure and frees the block's tensor memory, so the call returns HOMG_ECUDA with a timeout
+ * message, *waited_ms holding the kernel's duration, and the context stays usable (the next call
+ * on net works). HOMG_OK here would mean the wait is not bounded as documented. */
+int homg_net_check_barrier_timeout(homg_net_handle net, double* waited_ms);
+
 /* Message of the last hard error on net (or of the last failed homg_net_create when net is NULL). */
 const char* homg_net_last_error(homg_net_handle net);
 

@@ -41,7 +41,7 @@ constexpr int TW = 128;           // output pixels per accumulator row (MMA M)
 constexpr int TR = 4;             // output rows per CTA tile (one accumulator each)
 constexpr int BANDW = TW + 2;     // staged pixels per band row (one-pixel halo each side)
 constexpr int NT = 128;           // threads per conv CTA: one per TMEM lane
-constexpr long long kWaitPolls = 1ll << 24;  // bound on mbarrier polls before giving up
+constexpr long long kWaitNs = 500000000ll;  // a barrier wait gives up after 0.5 s
 
 // ---- PTX wrappers ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -69,10 +69,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false once kWaitNs have passed without the phase completing.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long i = 0; i < kWaitPolls; ++i)
+    const long long t0 = global_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -155,6 +163,7 @@ struct ConvArgs {
     const bf16* mask;   // CONV_MASK: out = acc where mask > 0, else 0 ([B, COUT, H, W])
     int B, H, W;
     int* err;
+    int unsignalled;    // self-test of the bounded wait: issue no MMA, so the barrier never completes
 };
 
 template <int CIN, int COUT>
@@ -218,7 +227,7 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a) {
         cp_async_wait_all();
         fence_proxy_async();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !a.unsignalled) {
             tc_fence_after();
             const uint32_t bb = smem_u32(band), wb = smem_u32(wsm);
 #pragma unroll 1
@@ -287,9 +296,10 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a) {
     }
     if (!ok) {
         // an MMA batch did not report completion in time: record it, give the tensor cores one more
-        // bounded wait to finish before the accumulators are released, and leave
+        // bounded wait to finish before the accumulators are released, and leave (in the self-test
+        // no MMA was issued, so there is nothing to wait for)
         if (tid == 0) atomicExch(a.err, 1);
-        mbar_wait(bar, parity ^ 1u);
+        if (!a.unsignalled) mbar_wait(bar, parity ^ 1u);
         __syncthreads();
     }
     tc_fence_before();
@@ -905,6 +915,29 @@ int homg_net_train_step(homg_net_handle net, const void* xv, const float* t, int
     NCK(net, cudaMemcpyAsync(&loss, net->dloss, sizeof(double), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
     NCK(net, cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (loss_out) *loss_out = (float)(loss / (double)px);
+    return homg::net_check_error(net);
+}
+
+int homg_net_check_barrier_timeout(homg_net_handle net, double* waited_ms) {
+    if (!net || !waited_ms) return HOMG_EINVAL;
+    NCK(net, cudaSetDevice(net->device), "cudaSetDevice");
+    int rc = ensure_scratch(net, 16 * 16);
+    if (rc != HOMG_OK) return rc;
+    cudaEvent_t e0, e1;
+    NCK(net, cudaEventCreate(&e0), "cudaEventCreate");
+    NCK(net, cudaEventCreate(&e1), "cudaEventCreate");
+    ConvArgs c = conv_args(net, net->act[0], 1, net->act[1], nullptr, 1, 16, 16);
+    c.unsignalled = 1;
+    cudaError_t e = cudaEventRecord(e0, net->stream);
+    if (e == cudaSuccess) e = launch_conv<32, 32, CONV_RELU>(c, net->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, net->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return net_cuda(net, e, "homg_net_check_barrier_timeout");
+    *waited_ms = ms;
     return homg::net_check_error(net);
 }
 

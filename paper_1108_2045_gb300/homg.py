@@ -53,6 +53,7 @@ EXPORTS = [
     "homg_net_forward",
     "homg_net_train_step",
     "homg_net_gather_patches",
+    "homg_net_check_barrier_timeout",
     "homg_net_last_error",
     "homg_net_destroy",
     "homg_features",
@@ -146,6 +147,7 @@ def load(path=LIB_PATH):
     lib.homg_net_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, fp]
     lib.homg_net_gather_patches.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
                                             vp, vp]
+    lib.homg_net_check_barrier_timeout.argtypes = [vp, dp]
     lib.homg_net_last_error.argtypes = [vp]
     lib.homg_net_last_error.restype = ctypes.c_char_p
     lib.homg_net_destroy.argtypes = [vp]
@@ -166,8 +168,11 @@ def load(path=LIB_PATH):
     lib.homg_batch_get_stats.argtypes = [vp, ctypes.POINTER(homg_batch_stats)]
     lib.homg_batch_destroy.argtypes = [vp]
     lib.homg_batch_destroy.restype = None
+    lib.homg_net_destroy.restype = None
+    not_int = ("homg_default_options", "homg_last_error", "homg_destroy", "homg_batch_destroy", "homg_net_last_error",
+               "homg_net_destroy", "homg_net_param_count")
     for name in EXPORTS:
-        if name not in ("homg_default_options", "homg_last_error", "homg_destroy", "homg_batch_destroy"):
+        if name not in not_int:
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -443,9 +448,14 @@ class Solver:
 # ---- learned corrector (include/homg_net.h) -------------------------------------------------------
 def _net_check(rc, net):
     if rc < 0:
-        msg = load().homg_net_last_error(net)
-        raise HomgError(rc, msg.decode() if msg else "")
+        raise HomgError(rc, homg_net_last_error(net))
     return rc
+
+
+def homg_net_last_error(net):
+    """Message of the last hard error on a network handle (None: of the last failed creation)."""
+    msg = load().homg_net_last_error(net)
+    return msg.decode() if msg else ""
 
 
 def image_channels_first_to_device_layout(x):
@@ -523,6 +533,12 @@ class Net:
         _net_check(load().homg_net_gather_patches(self.handle, _devptr_any(x, "x"), _devptr_any(t, "t"), H, W,
                                                   _devptr_any(corners, "corners"), B, P, _devptr_any(xp, "xp"),
                                                   _devptr_any(tp, "tp")), self.handle)
+
+    def check_barrier_timeout(self):
+        """Run the failure-path self-test; returns (return code, milliseconds the kernel took)."""
+        ms = ctypes.c_double(0.0)
+        rc = load().homg_net_check_barrier_timeout(self.handle, ctypes.byref(ms))
+        return rc, ms.value
 
     def close(self):
         if self.handle:

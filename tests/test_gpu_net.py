@@ -266,3 +266,17 @@ def test_full_size_network_sampled_against_oracle(homg):
         crop = ximg[:, py - 4:py + 5, px - 4:px + 5]
         ref = cnn.forward(params, crop)[0][4, 4]
         assert abs(yg[py, px] - ref) <= 2e-2 * max(1.0, abs(ref)), (py, px, yg[py, px], ref)
+
+
+def test_barrier_wait_gives_up_and_context_stays_usable(homg):
+    # a convolution whose completion barrier nothing signals: the bounded wait must return an error
+    # status (after 0.5 s, not hang), and the same network must work normally afterwards
+    rng = np.random.default_rng(18)
+    params = integer_network(19)
+    xs = [rng.integers(-2, 3, size=(2, 9, 20)).astype(np.float64)]
+    with homg.Net() as net:
+        rc, ms = net.check_barrier_timeout()
+        assert rc == homg.HOMG_ECUDA and "timed out" in homg.homg_net_last_error(net.handle)
+        assert 400.0 <= ms <= 5000.0, ms
+    ref = np.stack([cnn.forward(params, x)[0] for x in xs])
+    np.testing.assert_array_equal(gpu_forward(homg, params, xs), ref)
