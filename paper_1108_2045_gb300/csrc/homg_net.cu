@@ -14,13 +14,17 @@
 // Activations use a row-chunked layout: element (b, c, y, x) of a [B, C, H, W] tensor at
 // ((b*H + y)*(C/8) + c/8)*W*8 + x*8 + c%8, so that, for a fixed row and group of 8 channels, the
 // pixels' 16-byte chunks are contiguous -- exactly the core-matrix rows of the no-swizzle
-// K-major operand layout.
+// K-major operand layout. A CTA's input band arrives by one TMA tensor copy: the layout is a 5-D
+// tensor (8 channels, W pixels, C/8 groups, H rows, B images) whose box (8 x 130 x C/8 x 6 x 1)
+// lands in shared memory in exactly the band's order, zero-filled outside the image.
 //
 // Training kernels: weight packing (forward and transposed/flipped for the data gradient), the
 // MSE loss and its gradient, the weight gradient (CUDA cores, binary32), Adam. Solver-side
 // kernels turn an FP64 residual into features and a network output into a correction.
+#include <cuda.h>  // CUtensorMap and its enums (types only; the encoder comes from the runtime's entry-point query)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -81,6 +85,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         if (mbar_try_wait(bar, parity)) return true;
         if (global_ns() - t0 > kWaitNs) return false;
     }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 5-D tiled TMA load of the tensor map's box at the given coordinates (innermost first) into shared
+// memory; completion counts the box's bytes on the mbarrier.
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -174,7 +192,7 @@ struct ConvShape {
     static constexpr uint32_t NCOLS = TR * COUT;
     // Shared memory requested per CTA: at least enough that no more CTAs fit on one SM (228 KB)
     // than its 512 TMEM columns can hold at once, so no CTA ever waits in tcgen05.alloc.
-    static constexpr int SMEM_USED = BAND + WB + 16;
+    static constexpr int SMEM_USED = BAND + WB + 32;
     static constexpr int SMEM_FLOOR = 233472 / (int)(512 / NCOLS + 1) + 1024;
     static constexpr int SMEM = SMEM_USED > SMEM_FLOOR ? SMEM_USED : SMEM_FLOOR;
     static constexpr uint32_t IDESC = idesc_bf16(TW, COUT);
@@ -183,14 +201,15 @@ struct ConvShape {
 };
 
 template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a) {
+__global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constant__ CUtensorMap tmap) {
     using S = ConvShape<CIN, COUT>;
     constexpr int GI = S::GI, GO = S::GO;
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* band = smem;
     unsigned char* wsm = smem + S::BAND;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(wsm + S::WB);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wsm + S::WB);  // MMA completion
+    uint64_t* tbar = bar + 1;                                     // band arrival (TMA)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
     __shared__ float sbias[COUT];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int H = a.H, W = a.W;
@@ -198,7 +217,10 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a) {
     for (int i = tid; i < S::WB / 16; i += NT) cp_async16(wsm + i * 16, a.w + (int64_t)i * 8, 16);
     cp_async_commit();
     if (tid < COUT) sbias[tid] = (MODE == CONV_MASK || tid >= a.nbias) ? 0.f : a.bias[tid];
-    if (tid == 0) mbar_init(bar, 1);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(tbar, 1);
+    }
     if (warp == 0) tmem_alloc(tslot, S::NCOLS);
     cp_async_wait_all();
     fence_proxy_async();
@@ -209,24 +231,24 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a) {
 
     const int tx = (W + TW - 1) / TW, ty = (H + TR - 1) / TR;
     const long long tiles = (long long)a.B * ty * tx;
-    uint32_t parity = 0;
-    bool ok = true;
+    uint32_t parity = 0, tparity = 0;
+    bool ok = true, copy_pending = false, mma_pending = false;
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int b = (int)(t / ((long long)ty * tx));
         const int rem = (int)(t % ((long long)ty * tx));
         const int y0 = (rem / tx) * TR, x0 = (rem % tx) * TW;
-        // stage input rows y0-1 .. y0+TR and pixels x0-1 .. x0+TW (zero outside the image)
-        for (int i = tid; i < (TR + 2) * GI * BANDW; i += NT) {
-            const int px = i % BANDW, g = (i / BANDW) % GI, r = i / (BANDW * GI);
-            const int y = y0 - 1 + r, x = x0 - 1 + px;
-            const bool inb = (y >= 0 && y < H && x >= 0 && x < W);
-            const bf16* src = inb ? a.in + ((((int64_t)b * H + y) * GI + g) * W + x) * 8 : a.in;
-            cp_async16(band + (int64_t)i * 16, src, inb ? 16 : 0);
+        // input rows y0-1 .. y0+TR and pixels x0-1 .. x0+TW (zero outside the image): one TMA copy
+        if (tid == 0) {
+            mbar_expect_tx(tbar, (uint32_t)S::BAND);
+            tma_load_5d(band, &tmap, 0, x0 - 1, 0, y0 - 1, b, tbar);
         }
-        cp_async_commit();
-        cp_async_wait_all();
-        fence_proxy_async();
-        __syncthreads();
+        const bool arrived = mbar_wait(tbar, tparity);
+        tparity ^= 1u;
+        if (!__syncthreads_and(arrived)) {
+            ok = false;
+            copy_pending = true;
+            break;
+        }
         if (tid == 0 && !a.unsignalled) {
             tc_fence_after();
             const uint32_t bb = smem_u32(band), wb = smem_u32(wsm);
@@ -249,7 +271,10 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a) {
         parity ^= 1u;
         ok = __syncthreads_and(done);
         tc_fence_after();
-        if (!ok) break;
+        if (!ok) {
+            mma_pending = !a.unsignalled;
+            break;
+        }
         // epilogue: thread tid holds pixel x0 + tid of each accumulator row
 #pragma unroll 1
         for (int r = 0; r < TR; ++r) {
@@ -295,11 +320,12 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a) {
         __syncthreads();
     }
     if (!ok) {
-        // an MMA batch did not report completion in time: record it, give the tensor cores one more
-        // bounded wait to finish before the accumulators are released, and leave (in the self-test
-        // no MMA was issued, so there is nothing to wait for)
+        // a band copy or an MMA batch did not report completion in time: record it, give it one
+        // more bounded wait (on the phase it was issued in) before shared and tensor memory are
+        // released, and leave (the self-test issues no MMA, so there is nothing to wait for)
         if (tid == 0) atomicExch(a.err, 1);
-        if (!a.unsignalled) mbar_wait(bar, parity ^ 1u);
+        if (copy_pending) mbar_wait(tbar, tparity ^ 1u);
+        if (mma_pending) mbar_wait(bar, parity ^ 1u);
         __syncthreads();
     }
     tc_fence_before();
@@ -548,6 +574,34 @@ int num_sms() {
     return sms;
 }
 
+// cuTensorMapEncodeTiled, obtained once through the runtime's driver entry-point query.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// The band tensor map of a row-chunked [B, 8 G, H, W] bf16 tensor: dims (8, W, G, H, B), box
+// (8, 130, G, TR + 2, 1), zero fill outside.
+cudaError_t band_tensor_map(CUtensorMap* map, const bf16* base, int B, int H, int W, int G) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)G * W * 16, (cuuint64_t)H * G * W * 16};
+    const cuuint32_t box[5] = {8, BANDW, (cuuint32_t)G, TR + 2, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CIN, int COUT, int MODE>
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
     using S = ConvShape<CIN, COUT>;
@@ -567,7 +621,10 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
     const long long tiles = (long long)a.B * ((a.H + TR - 1) / TR) * ((a.W + TW - 1) / TW);
     const long long cap = (long long)num_sms() * per_sm;
     const int grid = (int)(tiles < cap ? tiles : cap);
-    k_conv3x3<CIN, COUT, MODE><<<grid, NT, S::SMEM, s>>>(a);
+    CUtensorMap map;
+    cudaError_t e = band_tensor_map(&map, a.in, a.B, a.H, a.W, CIN / 8);
+    if (e != cudaSuccess) return e;
+    k_conv3x3<CIN, COUT, MODE><<<grid, NT, S::SMEM, s>>>(a, map);
     return cudaGetLastError();
 }
 
