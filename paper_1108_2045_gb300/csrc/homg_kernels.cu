@@ -1256,12 +1256,12 @@ template <bool WARP, typename F>
 __device__ __forceinline__ double hat_sum(int l, F f) {
     double acc = 0.0;
     const double inv = 1.0 / (double)l;  // exact: l is a power of two
-    if (!WARP) {
+    if constexpr (!WARP) {
         for (int d = -(l - 1); d <= l - 1; ++d) acc = fma((double)(l - abs(d)) * inv, f(d), acc);
-        return acc;
+    } else {
+        for (int d = -(l - 1) + (int)(threadIdx.x & 31); d <= l - 1; d += 32) acc = fma((double)(l - abs(d)) * inv, f(d), acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     }
-    for (int d = -(l - 1) + (int)(threadIdx.x & 31); d <= l - 1; d += 32) acc = fma((double)(l - abs(d)) * inv, f(d), acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return acc;
 }
 

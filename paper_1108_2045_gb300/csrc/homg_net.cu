@@ -285,10 +285,9 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constan
             const int y = y0 + r, x = x0 + tid;
             if (y >= H || x >= W) continue;
             const int64_t pix = ((int64_t)b * H + y);
-            if (MODE == CONV_LAST) {
+            if constexpr (MODE == CONV_LAST) {
                 a.outf[pix * W + x] = v[0] + sbias[0];
-                continue;
-            }
+            } else {
 #pragma unroll
             for (int g = 0; g < GO; ++g) {
                 const int64_t off = ((pix * GO + g) * W + x) * 8;
@@ -314,6 +313,7 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constan
                 st.z = pack_bf16x2(o[4], o[5]);
                 st.w = pack_bf16x2(o[6], o[7]);
                 *reinterpret_cast<uint4*>(a.out + off) = st;
+            }
             }
         }
         tc_fence_before();
