@@ -53,7 +53,7 @@ def oracle_kw(kw):
     return {k: v for k, v in kw.items() if k in ("max_i", "omega_j", "schedule")}
 
 
-CASES_2D = [(3, 3), (5, 5), (7, 7), (8, 8), (8, 5), (10, 10), (10, 6)]
+CASES_2D = [(1, 1), (2, 2), (2, 1), (3, 3), (5, 5), (7, 7), (8, 8), (8, 5), (10, 10), (10, 6)]
 
 
 @pytest.mark.parametrize("K,levels", CASES_2D)
@@ -73,7 +73,7 @@ def test_cycles_match_oracle_2d(homg, K, levels, mode, strict):
         np.testing.assert_allclose(hist, rhist, rtol=1e-9)
 
 
-@pytest.mark.parametrize("K,levels", [(3, 3), (4, 4), (5, 5), (6, 4)])
+@pytest.mark.parametrize("K,levels", [(1, 1), (2, 2), (3, 3), (4, 4), (5, 5), (6, 4)])
 @pytest.mark.parametrize("mode", ["wholegrid", "lattice"])
 @pytest.mark.parametrize("strict", [True, False])
 def test_cycles_match_oracle_3d(homg, K, levels, mode, strict):
