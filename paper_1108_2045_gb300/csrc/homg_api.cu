@@ -60,7 +60,7 @@ struct SolveGraph {
 constexpr int kStagesPerGraph = 12;  // even: keeps the ping-pong parity of the solution buffers
 
 struct Op {  // one kernel launch of a cycle part
-    enum Kind { ITER, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD, POW2_ITER, POW2_RESTRICT } kind;
+    enum Kind { ITER, ITER2, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD, POW2_ITER, POW2_RESTRICT } kind;
     IterArgs it;
     Pow2IterArgs p2;
     Pow2RestrictArgs p2r;
@@ -262,7 +262,7 @@ void apply_batch(homg_ctx* h) {
     auto fix_rs = [&](RestrictArgs& a) { g(a.gf); g(a.gc); a.nb = h->nbatch; a.bst = h->dstate; };
     for (auto* part : {&h->partA, &h->partB})
         for (Op& op : *part) {
-            if (op.kind == Op::ITER) fix_it(op.it);
+            if (op.kind == Op::ITER || op.kind == Op::ITER2) fix_it(op.it);
             else if (op.kind == Op::PROLONG) fix_pr(op.pr);
             else if (op.kind == Op::RESTRICT) fix_rs(op.rs);
         }
@@ -505,7 +505,27 @@ void plan_cycle(homg_ctx* h) {
                 op.pr.s = mprev - m;
                 h->partA.push_back(op);
             }
+            // binary32-arithmetic cycles pair consecutive plain sweeps (no pending interpolation, no
+            // variation output) into one two-sweep launch: half the DRAM traffic, same results
+            const bool pairable = !h->strict && h->prec != PREC_FP64 && h->ndim == 2 && !h->vc && lv.n > 16;
+            auto plain = [&](int q) { return q >= 1 && !(q == c - 1 && m >= 1); };
             for (int q = 0; q < c; ++q) {
+                if (pairable && plain(q) && q + 1 < c && plain(q + 1)) {
+                    Op op{};
+                    op.kind = Op::ITER2;
+                    IterArgs& a = op.it;
+                    a.e_old = cgrid(lv.G[cur], lv.pitch, lv.n);
+                    a.e_new = grid(lv.G[cur ^ 1], lv.pitch, lv.n);
+                    a.g = cgrid(lv.g, lv.pitch, lv.n);
+                    a.m = 0;
+                    set_weights(h, a);
+                    a.mp = -1;
+                    a.dnew = grid(nullptr, 0, 0);
+                    (m == 0 ? h->partB : h->partA).push_back(op);
+                    cur ^= 1;
+                    ++q;
+                    continue;
+                }
                 Op op{};
                 op.kind = Op::ITER;
                 IterArgs& a = op.it;
@@ -564,6 +584,7 @@ void group_coarse_block(homg_ctx* h) {
     // leading iterations / level changes on small lattices
     for (; q < h->partA.size(); ++q) {
         const Op& op = h->partA[q];
+        if (op.kind != Op::ITER && op.kind != Op::PROLONG) break;
         const int n = (op.kind == Op::ITER) ? op.it.e_new.n : op.pr.G.n;
         if (n > nb) break;
         BlockOp b{};
@@ -587,6 +608,7 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
         cudaError_t e = cudaSuccess;
         switch (op.kind) {
             case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
+            case Op::ITER2: e = launch_iterate2(h->prec, op.it, s); break;
             case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
             case Op::VRESID: e = launch_vresid(h->ndim, h->prec, h->strict, op.vr, s); break;
@@ -1016,37 +1038,48 @@ struct homg_batch_ctx {
 
 namespace {
 
-// Autotuner: for every lattice size the group sweeps with the marching Jacobi kernel, time the
-// plain sweep (all problems at once) for each candidate number of nodes per thread along the
-// march, keep the fastest, and use it for every sweep of that size. Reports the level-0 choice.
+// Autotuner: for every lattice size the group sweeps with the marching Jacobi kernels (single and
+// paired sweeps separately), time the plain sweep (all problems at once) for each candidate number
+// of nodes per thread along the march, keep the fastest, and use it for every sweep of that kind
+// and size. Reports the level-0 choice of the single sweep (of the paired one when the level has
+// no single plain sweep).
 int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us) {
     *best_rows = 0;
     *best_us = 0.0;
     std::vector<const Op*> tmpl;
     for (auto* part : {&h->partA, &h->partB})
         for (const Op& op : *part) {
-            if (op.kind != Op::ITER || !op.it.e_old.p || op.it.m != 0) continue;
+            const bool single = op.kind == Op::ITER && op.it.e_old.p;
+            if ((!single && op.kind != Op::ITER2) || op.it.m != 0) continue;
             bool seen = false;
-            for (const Op* t : tmpl) seen |= t->it.e_new.n == op.it.e_new.n;
+            for (const Op* t : tmpl) seen |= t->kind == op.kind && t->it.e_new.n == op.it.e_new.n;
             if (!seen) tmpl.push_back(&op);
         }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0), "cudaEventCreate");
     CK(h, cudaEventCreate(&e1), "cudaEventCreate");
+    bool level0_single = false;
     for (const Op* t : tmpl) {
+        const Op::Kind kind = t->kind;
         IterArgs a = t->it;
         a.mp = -1;
         a.dnew = Grid{nullptr, 0, 0};
         const int n = a.e_new.n;
+        auto launch = [&]() {
+            return kind == Op::ITER2 ? launch_iterate2(h->prec, a, st) : launch_iterate(h->ndim, h->prec, false, a, st);
+        };
         double best = 1e30;
         int pick = 0;
-        for (int rows : {1, 2, 4, 8, 16, 32}) {
+        static const int kSingle[] = {1, 2, 4, 8, 16, 32}, kPaired[] = {4, 8, 16, 32, 64};
+        const int* cand = kind == Op::ITER2 ? kPaired : kSingle;
+        for (int c = 0; c < (kind == Op::ITER2 ? 5 : 6); ++c) {
+            const int rows = cand[c];
             if (rows > n - 1) break;
             a.rows = rows;
-            cudaError_t e = launch_iterate(h->ndim, h->prec, false, a, st);  // warm-up
+            cudaError_t e = launch();  // warm-up
             for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
                 if (r == 0) e = cudaEventRecord(e0, st);
-                if (e == cudaSuccess) e = launch_iterate(h->ndim, h->prec, false, a, st);
+                if (e == cudaSuccess) e = launch();
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1062,10 +1095,11 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us)
         }
         for (auto* part : {&h->partA, &h->partB})
             for (Op& op : *part)
-                if (op.kind == Op::ITER && op.it.m == 0 && op.it.e_new.n == n) op.it.rows = pick;
-        if (n == h->n) {
+                if (op.kind == kind && op.it.m == 0 && op.it.e_new.n == n) op.it.rows = pick;
+        if (n == h->n && (kind == Op::ITER || !level0_single)) {
             *best_rows = pick;
             *best_us = best;
+            level0_single |= kind == Op::ITER;
         }
     }
     cudaEventDestroy(e0);

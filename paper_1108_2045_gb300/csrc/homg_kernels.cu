@@ -797,6 +797,84 @@ __global__ void k_vc_setup(const double* __restrict__ k, int n, int m, K* kx, K*
     }
 }
 
+// Value of a stored element in the arithmetic type (undoes St<T>::put's rounding step only).
+template <typename T> __device__ __forceinline__ typename St<T>::C as_c(T x) { return x; }
+template <> __device__ __forceinline__ float as_c<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Two plain damped-Jacobi sweeps in one pass (binary32 arithmetic: FP32 and bfloat16 cycles, where
+// a sweep is DRAM-bound). Each warp owns a strip of 32 columns and marches down it: step r computes
+// the first sweep's value at row r on all 32 columns (exactly a single sweep's operation order,
+// rounded to the storage type; the column window of the input iterate rides in registers, the
+// side neighbours come through L1) and the second sweep's value at row r - 1 on the 30 inner
+// columns, the warp's output, taking the side neighbours' first-sweep values by shuffle. Strips
+// overlap by one column on each side; a warp's rows overlap its neighbours' by one row above and
+// below. No barrier: warps march independently and the unrolled march keeps several rows of loads
+// in flight. Per node and pair of sweeps this reads e and g once and writes e once (12 B instead
+// of 24 in FP32), and the result is bit-identical to two single sweeps.
+constexpr int X2_OUT = 30;  // output columns per warp
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
+    pdl_begin();
+    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
+    using C = typename St<T>::C;
+    const int n = a.e_new.n;
+    const int lane = threadIdx.x & 31;
+    const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
+    if (strip * X2_OUT + 1 > n - 1) return;  // strip past the last column: the whole warp leaves
+    const int i = strip * X2_OUT + lane;     // first-sweep column
+    const bool col_in = i >= 1 && i <= n - 1;
+    const bool out = col_in && lane >= 1 && lane <= X2_OUT;
+    const int il = min(max(i, 1), n - 1);    // lanes outside the interior load from inside, keep 0
+    const int j0 = blockIdx.y * rows + 1;    // second sweep: rows j0 .. j1 - 1
+    const int j1 = min(j0 + rows, n);
+    const int r0 = j0 - 1;                   // first sweep: rows r0 .. j1 (0 on rows 0 and n)
+    const int64_t pe = a.e_old.pitch, pg = a.g.pitch, po = a.e_new.pitch;
+    const int ra = max(r0, 1);
+    const T* __restrict__ pE = cp<T>(a.e_old) + (int64_t)ra * pe + il;  // row r of the march
+    const T* __restrict__ pG = cp<T>(a.g) + (int64_t)ra * pg + il;
+    T* __restrict__ pO = wp<T>(a.e_new) + (int64_t)j0 * po + i;         // next output row
+    const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
+    C em = St<T>::ld(pE - pe), ec = St<T>::ld(pE);  // input iterate at rows r - 1, r
+    // first sweep at row r (1 <= r <= n - 1), then advance the march one row
+    auto first = [&](C& g) -> C {
+        const C ep = St<T>::ld(pE + pe), w = St<T>::ld(pE - 1), e = St<T>::ld(pE + 1);
+        g = St<T>::ld(pG);
+        const C sum = (w + e) + (em + ep);
+        const C v = as_c<T>(St<T>::put(fma(c1, ec, fma(om, sum, g))));
+        em = ec;
+        ec = ep;
+        pE += pe;
+        pG += pg;
+        return col_in ? v : (C)0;
+    };
+    C s_prev = 0, s_cur = 0, g_cur = 0;  // first-sweep values at rows r - 2, r - 1; g at row r - 1
+    // second sweep at row r - 1 given the first-sweep value v at row r
+    auto second = [&](C v) {
+        const C sw = __shfl_up_sync(0xffffffffu, s_cur, 1), se = __shfl_down_sync(0xffffffffu, s_cur, 1);
+        if (out) *pO = St<T>::put(fma(c1, s_cur, fma(om, (sw + se) + (s_prev + v), g_cur)));
+        pO += po;
+    };
+    if (r0 >= 1) s_cur = first(g_cur);  // row r0 (its g is never used)
+    {
+        C g;
+        const C v = first(g);  // row j0
+        s_prev = s_cur;
+        s_cur = v;
+        g_cur = g;
+    }
+    const int rb = min(j1, n - 1);
+#pragma unroll 4
+    for (int r = j0 + 1; r <= rb; ++r) {
+        C g;
+        const C v = first(g);
+        second(v);
+        s_prev = s_cur;
+        s_cur = v;
+        g_cur = g;
+    }
+    if (j1 == n) second((C)0);  // the first-sweep value on the boundary row n is 0
+}
+
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
 // stride-2 interpolant of Gc - dl, formed along each marching column (see ColumnInterp2).
 template <typename T, bool BATCH>
@@ -1489,6 +1567,24 @@ cudaError_t restrict_t(int ndim, bool strict, const RestrictArgs& a, cudaStream_
 
 cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, cudaStream_t s) {
     DISPATCH_PREC(prec, iterate_t<T>(ndim, strict, a, s));
+}
+
+cudaError_t launch_iterate2(int prec, const IterArgs& a, cudaStream_t s) {
+    const int n = a.e_new.n;
+    // each warp also computes the first sweep one row above and one below its own rows: march
+    // further than a single sweep does, to keep that overhead small
+    const int xb = (((n - 1 + X2_OUT - 1) / X2_OUT) + JX / 32 - 1) / (JX / 32);  // blocks across: JX / 32 strips each
+    const double nodes = (double)a.nb * (double)(n - 1) * (double)(n - 1);
+    const int rows = a.rows > 0 ? a.rows : (nodes >= 1.0e6 ? 16 : 8);
+    const dim3 g((unsigned)xb, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
+    switch (prec) {
+        case PREC_FP32:
+            return a.bst ? launch_k(k_jacobi2_x2<float, true>, g, b, s, a, rows) : launch_k(k_jacobi2_x2<float, false>, g, b, s, a, rows);
+        case PREC_BF16:
+            return a.bst ? launch_k(k_jacobi2_x2<__nv_bfloat16, true>, g, b, s, a, rows)
+                         : launch_k(k_jacobi2_x2<__nv_bfloat16, false>, g, b, s, a, rows);
+        default: return cudaErrorInvalidValue;  // FP64 sweeps are FP64-bound: never paired
+    }
 }
 
 cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a, cudaStream_t s) {
