@@ -61,6 +61,7 @@ constexpr int kStagesPerGraph = 12;  // even: keeps the ping-pong parity of the 
 
 struct Op {  // one kernel launch of a cycle part
     enum Kind { ITER, ITER2, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD, POW2_ITER, POW2_RESTRICT } kind;
+    int sweeps = 1;  // ITER2: plain sweeps fused into the launch (2 or 4)
     IterArgs it;
     Pow2IterArgs p2;
     Pow2RestrictArgs p2r;
@@ -511,8 +512,12 @@ void plan_cycle(homg_ctx* h) {
             auto plain = [&](int q) { return q >= 1 && !(q == c - 1 && m >= 1); };
             for (int q = 0; q < c; ++q) {
                 if (pairable && plain(q) && q + 1 < c && plain(q + 1)) {
+                    // batches: four sweeps where the run allows (their launches cover every problem of
+                    // the group, where the halved traffic outweighs the longer march); otherwise two
+                    const int k = (h->nbatch > 1 && q + 3 < c && plain(q + 3)) ? 4 : 2;
                     Op op{};
                     op.kind = Op::ITER2;
+                    op.sweeps = k;
                     IterArgs& a = op.it;
                     a.e_old = cgrid(lv.G[cur], lv.pitch, lv.n);
                     a.e_new = grid(lv.G[cur ^ 1], lv.pitch, lv.n);
@@ -523,7 +528,7 @@ void plan_cycle(homg_ctx* h) {
                     a.dnew = grid(nullptr, 0, 0);
                     (m == 0 ? h->partB : h->partA).push_back(op);
                     cur ^= 1;
-                    ++q;
+                    q += k - 1;
                     continue;
                 }
                 Op op{};
@@ -608,7 +613,7 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
         cudaError_t e = cudaSuccess;
         switch (op.kind) {
             case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
-            case Op::ITER2: e = launch_iterate2(h->prec, op.it, s); break;
+            case Op::ITER2: e = launch_iterate2(h->prec, op.sweeps, op.it, s); break;
             case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
             case Op::VRESID: e = launch_vresid(h->ndim, h->prec, h->strict, op.vr, s); break;
@@ -1052,7 +1057,7 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us)
             const bool single = op.kind == Op::ITER && op.it.e_old.p;
             if ((!single && op.kind != Op::ITER2) || op.it.m != 0) continue;
             bool seen = false;
-            for (const Op* t : tmpl) seen |= t->kind == op.kind && t->it.e_new.n == op.it.e_new.n;
+            for (const Op* t : tmpl) seen |= t->kind == op.kind && t->sweeps == op.sweeps && t->it.e_new.n == op.it.e_new.n;
             if (!seen) tmpl.push_back(&op);
         }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1061,12 +1066,13 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us)
     bool level0_single = false;
     for (const Op* t : tmpl) {
         const Op::Kind kind = t->kind;
+        const int sweeps = t->sweeps;
         IterArgs a = t->it;
         a.mp = -1;
         a.dnew = Grid{nullptr, 0, 0};
         const int n = a.e_new.n;
         auto launch = [&]() {
-            return kind == Op::ITER2 ? launch_iterate2(h->prec, a, st) : launch_iterate(h->ndim, h->prec, false, a, st);
+            return kind == Op::ITER2 ? launch_iterate2(h->prec, sweeps, a, st) : launch_iterate(h->ndim, h->prec, false, a, st);
         };
         double best = 1e30;
         int pick = 0;
@@ -1095,7 +1101,7 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us)
         }
         for (auto* part : {&h->partA, &h->partB})
             for (Op& op : *part)
-                if (op.kind == kind && op.it.m == 0 && op.it.e_new.n == n) op.it.rows = pick;
+                if (op.kind == kind && op.sweeps == sweeps && op.it.m == 0 && op.it.e_new.n == n) op.it.rows = pick;
         if (n == h->n && (kind == Op::ITER || !level0_single)) {
             *best_rows = pick;
             *best_us = best;

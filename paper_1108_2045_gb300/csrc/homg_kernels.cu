@@ -875,6 +875,73 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
     if (j1 == n) second((C)0);  // the first-sweep value on the boundary row n is 0
 }
 
+// K plain damped-Jacobi sweeps in one pass (K >= 3; binary32 arithmetic), the K-level form of
+// k_jacobi2_x2: each warp marches a strip of 32 columns; step r computes sweep 1 at row r, sweep 2
+// at row r - 1, ..., sweep K at row r - K + 1 (the output), each from the previous sweep's values
+// at three rows (registers) and its side neighbours (shuffle), every intermediate rounded to the
+// storage type as a stored sweep would be. A strip outputs its 34 - 2K inner columns; a block's
+// march starts K - 1 rows above its output rows and ends K - 1 below. Sweep values on the boundary
+// rows and columns are 0. Per node and K sweeps this reads e and g once and writes e once.
+template <typename T, bool BATCH, int K>
+__global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
+    pdl_begin();
+    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
+    using C = typename St<T>::C;
+    constexpr int OUTK = 34 - 2 * K;
+    const int n = a.e_new.n;
+    const int lane = threadIdx.x & 31;
+    const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
+    if (strip * OUTK + 1 > n - 1) return;        // strip past the last column: the whole warp leaves
+    const int i = strip * OUTK + lane - (K - 2);  // this lane's column
+    const bool col_in = i >= 1 && i <= n - 1;
+    const bool out = col_in && lane >= K - 1 && lane <= 32 - K;
+    const int il = min(max(i, 1), n - 1);  // lanes outside the interior load from inside, keep 0
+    const int j0 = blockIdx.y * rows + 1;  // output rows j0 .. j1 - 1
+    const int j1 = min(j0 + rows, n);
+    const int64_t pe = a.e_old.pitch, pg = a.g.pitch, po = a.e_new.pitch;
+    const T* __restrict__ E0 = cp<T>(a.e_old) + il;
+    const T* __restrict__ G0 = cp<T>(a.g) + il;
+    T* __restrict__ O0 = wp<T>(a.e_new) + i;
+    const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
+    // Loads use rows clamped into 0..n, so that the march has no branch and the unrolled loop can
+    // issue several rows of loads ahead; values on rows outside 1..n-1 are then replaced by 0.
+    auto rowE = [&](int row) { return E0 + (int64_t)min(max(row, 0), n) * pe; };
+    const int rf = j0 - (K - 1), rl = j1 + K - 2;  // sweep-1 rows of the march
+    C em = St<T>::ld(rowE(rf - 1)), ec = St<T>::ld(rowE(rf));  // input iterate at rows r - 1, r (exact where used)
+    C sp[K], sc[K], gq[K];  // sweep l (1..K-1) at rows x - 1, x of sweep l + 1's row x; g at rows r .. r - K + 1
+#pragma unroll
+    for (int l = 0; l < K; ++l) sp[l] = sc[l] = gq[l] = 0;
+#pragma unroll 4
+    for (int r = rf; r <= rl; ++r) {
+        C v[K + 1];
+        const T* p = rowE(r);
+        const C ep = St<T>::ld(rowE(r + 1)), w = St<T>::ld(p - 1), e = St<T>::ld(p + 1);
+        const C g = St<T>::ld(G0 + (int64_t)min(max(r, 0), n) * pg);
+        {
+            const C y = as_c<T>(St<T>::put(fma(c1, ec, fma(om, (w + e) + (em + ep), g))));
+            v[1] = (col_in && r >= 1 && r <= n - 1) ? y : (C)0;
+        }
+        em = ec;
+        ec = ep;
+#pragma unroll
+        for (int l = K - 1; l >= 1; --l) gq[l] = gq[l - 1];
+        gq[0] = g;
+#pragma unroll
+        for (int l = 2; l <= K; ++l) {
+            const int x = r - l + 1;  // sweep l's row: sweep l - 1 is known at x - 1, x, x + 1
+            const C sw = __shfl_up_sync(0xffffffffu, sc[l - 1], 1), se = __shfl_down_sync(0xffffffffu, sc[l - 1], 1);
+            const C y = fma(c1, sc[l - 1], fma(om, (sw + se) + (sp[l - 1] + v[l - 1]), gq[l - 1]));
+            if (l < K) {
+                v[l] = (col_in && x >= 1 && x <= n - 1) ? as_c<T>(St<T>::put(y)) : (C)0;
+            } else if (out && x >= j0 && x < j1) {
+                O0[(int64_t)x * po] = St<T>::put(y);
+            }
+            sp[l - 1] = sc[l - 1];
+            sc[l - 1] = v[l - 1];
+        }
+    }
+}
+
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
 // stride-2 interpolant of Gc - dl, formed along each marching column (see ColumnInterp2).
 template <typename T, bool BATCH>
@@ -1569,7 +1636,23 @@ cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, c
     DISPATCH_PREC(prec, iterate_t<T>(ndim, strict, a, s));
 }
 
-cudaError_t launch_iterate2(int prec, const IterArgs& a, cudaStream_t s) {
+template <typename T, int K> cudaError_t iterate_k_t(const IterArgs& a, cudaStream_t s) {
+    const int n = a.e_new.n;
+    constexpr int OUTK = 34 - 2 * K;
+    const int xb = (((n - 1 + OUTK - 1) / OUTK) + JX / 32 - 1) / (JX / 32);
+    const double nodes = (double)a.nb * (double)(n - 1) * (double)(n - 1);
+    const int rows = a.rows > 0 ? a.rows : (nodes >= 1.0e6 ? 32 : 8);
+    const dim3 g((unsigned)xb, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
+    return a.bst ? launch_k(k_jacobi2_xk<T, true, K>, g, b, s, a, rows) : launch_k(k_jacobi2_xk<T, false, K>, g, b, s, a, rows);
+}
+
+cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_t s) {
+    if (sweeps == 4) {
+        if (prec == PREC_FP32) return iterate_k_t<float, 4>(a, s);
+        if (prec == PREC_BF16) return iterate_k_t<__nv_bfloat16, 4>(a, s);
+        return cudaErrorInvalidValue;
+    }
+    if (sweeps != 2) return cudaErrorInvalidValue;
     const int n = a.e_new.n;
     // each warp also computes the first sweep one row above and one below its own rows: march
     // further than a single sweep does, to keep that overhead small
