@@ -193,7 +193,7 @@ def run_cfg3(args, homg, inputs, stream, barrier, pending):
                 stats = s3.stats()
             r = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms,
                  "unknowns_per_s": (n - 1) ** 3 / (ms * 1e-3),
-                 "fine_launch_us": 1e3 * stats["fine_ms"] / max(1, stats["cycles"] * stats["fine_iterations_per_cycle"])}
+                 "fine_launch_us": 1e3 * stats["fine_ms"] / max(1, stats["cycles"] * stats["fine_launches_per_cycle"])}
             if prec == "fp64":
                 ref = u.clone()
             else:
@@ -673,11 +673,17 @@ def run(args):
             m1.record(stream)
             barrier()
             mms = m0.elapsed_time(m1) / args.mixed_steps
-            fl = sum(x["cycles"] * x["fine_iterations_per_cycle"] for x in sts)
-            fus = 1e3 * sum(x["fine_ms"] for x in sts) / fl
+            # level 0: consecutive plain sweeps run fused (two per launch), each launch moving the
+            # algorithmic bytes of one sweep
+            fl = sum(x["cycles"] * x["fine_launches_per_cycle"] for x in sts)
+            fi = sum(x["cycles"] * x["fine_iterations_per_cycle"] for x in sts)
+            fine_total_ms = sum(x["fine_ms"] for x in sts)
+            fus = 1e3 * fine_total_ms / fl
             fb = sts[0]["fine_bytes_per_iteration"]
             mixed[prec] = {"value": unknowns / (mms * 1e-3), "ms_per_step": mms, "cycles": c3, "final_relres": r3,
                            "speedup_vs_fp64": (elapsed_ms / args.steps) / mms,
+                           "fine_launches_per_cycle": sts[0]["fine_launches_per_cycle"],
+                           "fine_sweep_us": 1e3 * fine_total_ms / fi,
                            "fine_launch_us": fus, "fine_hbm_gbs": fb / (fus * 1e-6) / 1e9,
                            "fine_hbm_frac": fb / (fus * 1e-6) / 1e9 / hbm_peak_mp,
                            "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
@@ -718,15 +724,20 @@ def run(args):
     pow2 = run_pow2(args, homg, stream, barrier, pending) if (args.pow2_steps > 0 and world == 1) else None
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     # dominant kernel: the level-0 HOMG iteration (damped Jacobi over every interior node)
-    launches = sum(s["cycles"] * s["fine_iterations_per_cycle"] for s in stats)
+    # (binary32 cycles fuse consecutive plain sweeps: a launch then does two sweeps' arithmetic on one
+    # sweep's traffic)
+    launches = sum(s["cycles"] * s["fine_launches_per_cycle"] for s in stats)
     fine_ms = sum(s["fine_ms"] for s in stats)
     per_launch_s = fine_ms * 1e-3 / launches
-    ops = stats[0]["fine_flops_per_iteration"]
+    sweeps_per_launch = stats[0]["fine_iterations_per_cycle"] / stats[0]["fine_launches_per_cycle"]
+    ops = stats[0]["fine_flops_per_iteration"] * sweeps_per_launch
     bts = stats[0]["fine_bytes_per_iteration"]
     alu_achieved = ops / per_launch_s / 1e12
     hbm_achieved = bts / per_launch_s / 1e9
     clk = clocks.summary()
-    kname = "k_jacobi2 (level-0 HOMG iteration: damped Jacobi on every interior node)"
+    kname = ("k_jacobi2 (level-0 HOMG iteration: damped Jacobi on every interior node)" if sweeps_per_launch == 1 else
+             "k_jacobi2_x2 / k_jacobi2 (level-0 HOMG iterations, consecutive plain sweeps fused two per launch; "
+             "average over the level's launches)")
     # DRAM bytes (read + write) per launch of this kernel from ncu (profiles/k_jacobi2_fp64_4097.md);
     # only the FP64 build of the kernel was captured in its current form
     traffic = LEVEL0_FP64_DRAM_BYTES if args.precision == "fp64" else None

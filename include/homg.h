@@ -157,6 +157,10 @@ typedef struct homg_stats {
                                         * by precision) of one level-0 iteration                  */
     double coarse_bytes_per_cycle;     /* algorithmic DRAM bytes of the levels >= 1 per cycle   */
     double coarse_fp64_ops_per_cycle;  /* algorithmic FP64 instructions of levels >= 1 per cycle */
+    int fine_launches_per_cycle;       /* level-0 sweep launches per cycle (binary32 cycles fuse
+                                        * consecutive plain sweeps, so this can be fewer than
+                                        * fine_iterations_per_cycle; each launch moves about
+                                        * fine_bytes_per_iteration)                              */
 } homg_stats;
 
 typedef struct homg_ctx* homg_handle;

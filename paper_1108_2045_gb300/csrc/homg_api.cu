@@ -1424,6 +1424,8 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     st.exec_mode = h->exec;
     st.iterations_per_cycle = (int)h->sched.size();
     st.fine_iterations_per_cycle = h->fine_iters;
+    st.fine_launches_per_cycle = 0;
+    for (const Op& op : h->partB) st.fine_launches_per_cycle += (op.kind == Op::ITER || op.kind == Op::ITER2) ? 1 : 0;
     st.kernels_per_cycle = (int)(h->partA.size() + h->partB.size()) + 2;
     st.kernels_fixed = 3;
     st.kernel_launches = st.kernels_fixed + (long long)cycles * st.kernels_per_cycle;

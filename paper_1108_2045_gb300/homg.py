@@ -101,6 +101,7 @@ class homg_stats(ctypes.Structure):
         ("fine_flops_per_iteration", ctypes.c_double),
         ("coarse_bytes_per_cycle", ctypes.c_double),
         ("coarse_fp64_ops_per_cycle", ctypes.c_double),
+        ("fine_launches_per_cycle", ctypes.c_int),
     ]
 
 

@@ -91,3 +91,32 @@ def test_mixed_solve_reaches_tolerance(homg, precision, ndim, K):
     u64, _, c64, _ = oracle.solve(f, K, tol=1e-10)
     cond = (np.sin(np.pi * (n - 1) / (2 * n)) / np.sin(np.pi / (2 * n))) ** 2
     assert rel(got, u64) <= 2e-10 * cond
+
+
+@pytest.mark.parametrize("precision,strict,want", [("fp32", False, 17), ("bf16", False, 17), ("fp32", True, 32),
+                                                   ("fp64", False, 32)])
+def test_plain_sweeps_fuse_two_per_launch(homg, precision, strict, want):
+    # binary32 fast lattice cycles fuse consecutive plain level-0 sweeps: of the 32 sweeps, the first
+    # (level change) and the last stay single launches, the 30 in between run as 15 two-sweep launches
+    import torch
+
+    with homg.Solver(2, 129, 7, precision=precision, strict_fp=strict, exec_mode="lattice") as s:
+        f = torch.from_numpy(inputs.uniform_rhs(128, 2, seed=5)).cuda()
+        u = torch.zeros_like(f)
+        s.solve(f, u, tol=0.0, max_cycles=1)
+        st = s.stats()
+    assert st["fine_iterations_per_cycle"] == 32 and st["fine_launches_per_cycle"] == want
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("schedule", [[3, 3, 3, 2, 2, 1, 1, 1, 1, 1, 0, 0, 0], [2, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0]])
+def test_fused_sweeps_follow_oracle_on_short_runs(homg, precision, schedule):
+    # runs of 2 to 9 sweeps per level: fused pairs plus single leftovers follow the oracle's cycle
+    n, levels = 256, 8
+    f = inputs.uniform_rhs(n, 2, seed=3)
+    for k in (1, 2):
+        ref, _, _, _ = oracle.solve_mixed(f, levels, precision, tol=0.0, max_cycles=k, schedule=schedule)
+        got, st, cyc, rr, hist = gpu_solve(homg, f, levels, max_cycles=k, exec_mode="lattice", precision=precision,
+                                           schedule=schedule)
+        assert cyc == k
+        assert rel(got, ref) <= TOL[precision], (k, rel(got, ref))
