@@ -223,6 +223,14 @@ int homg_set_coefficient(homg_handle h, const double* k);
  * 0 when ||f|| = 0 and u's interior is 0, +inf when ||f|| = 0 otherwise. Synchronises the stream. */
 int homg_residual_norm(homg_handle h, const double* f, const double* u, double* relres_out);
 
+/* Self-test of the library's own binary64 <-> binary32 conversions. The fast residual kernels form
+ * them with integer operations, from the IEEE 754 formats, to keep them off GB300's narrow FP64
+ * pipe. For k < n: f_out[k] = d_in[k] rounded to binary32 (round to nearest, ties to even), d_out[k] =
+ * f_in[k] widened to binary64. All four are device pointers; runs on the current device on the legacy
+ * default stream and synchronises. Both results must equal the hardware conversions bit for bit.
+ * HOMG_EINVAL for n < 0 or a null pointer with n > 0 (message in homg_last_error(NULL)). */
+int homg_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n);
+
 /* Relative residual before every cycle of the last solve: hist[0] = initial, hist[k] after k
  * cycles. Copies min(cap, cycles + 1) values; returns that count or a negative code. */
 int homg_get_history(homg_handle h, double* hist, int cap);

@@ -1732,6 +1732,15 @@ int homg_residual_norm(homg_handle h, const double* f, const double* u, double* 
     return HOMG_OK;
 }
 
+int homg_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n) {
+    if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out)))
+        return fail(nullptr, HOMG_EINVAL, "homg_check_conversions: n < 0 or a null pointer%s%s");
+    cudaError_t e = launch_check_conversions(d_in, f_out, f_in, d_out, n, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "homg_check_conversions");
+    return HOMG_OK;
+}
+
 int homg_get_history(homg_handle h, double* hist, int cap) {
     if (!h || !hist || cap < 0) return HOMG_EINVAL;
     const int cnt = std::min(cap, h->stats.cycles + 1);

@@ -215,6 +215,10 @@ struct BlockOp {
 // Launchers (enqueue on `s`; return the launch error). `prec` is the storage precision of the
 // cycle arrays (Prec); `strict` selects the oracle's canonical operation order.
 cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, cudaStream_t s);
+// f_out = binary64 -> binary32 (round to nearest even) of d_in, d_out = binary32 -> binary64 of f_in,
+// with the integer conversions of the fast residual kernels (n elements, device pointers).
+cudaError_t launch_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n,
+                                     cudaStream_t s);
 // `sweeps` (2 or 4) plain lattice-form sweeps in one launch (2-D, FP32 / bfloat16 storage, no
 // pending interpolation, no variation output): e_new = sweep(...sweep(e_old)).
 cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_t s);

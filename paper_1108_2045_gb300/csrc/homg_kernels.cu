@@ -47,6 +47,52 @@ template <> struct St<__nv_bfloat16> {
     static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
 };
 
+// ---- binary32 <-> binary64 conversions with integer operations ----------------------------------
+// GB300 issues FP64 instructions, conversions to and from binary64 among them, at a small fraction
+// of its integer rate, and the fast residual kernels are bound by that pipe. These two conversions
+// are written out from the IEEE 754 formats (binary32: 1 sign, 8 exponent bits biased by 127, 23
+// fraction bits; binary64: 1, 11 biased by 1023, 52): normal numbers and zeros take integer
+// operations only; subnormals, infinities and NaNs, which these kernels practically never meet,
+// use the hardware conversion. Both are exact copies of it (homg_check_conversions tests that).
+
+// binary32 -> binary64 (exact): re-bias the exponent, move the fraction to the top of the 52 bits.
+__device__ __forceinline__ double widen_f32(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned ex = (b >> 23) & 0xffu;
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    if (ex == 0u || ex == 0xffu) return (double)x;
+    const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// binary64 -> binary32, round to nearest, ties to even: keep the top 23 of the 52 fraction bits and
+// round on the 29 dropped ones; a carry out of the fraction steps the exponent (to infinity above
+// the largest binary32, as rounding to nearest requires).
+__device__ __forceinline__ float narrow_rn(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sg = hi & 0x80000000u;
+    if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(sg);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // binary32 biased exponent
+    if (e <= 0 || e >= 255) return __double2float_rn(d);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float((sg | ((unsigned)e << 23) | m) + up);
+}
+
+// Stored value -> binary64, and binary64 -> stored value (via binary32 for bfloat16, the oracle's
+// storage rounding), with the conversions above.
+template <typename T> __device__ __forceinline__ double to_d(T x);
+template <> __device__ __forceinline__ double to_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ double to_d<float>(float x) { return widen_f32(x); }
+template <typename T> __device__ __forceinline__ T from_d_store(double x);
+template <> __device__ __forceinline__ double from_d_store<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_d_store<float>(double x) { return narrow_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d_store<__nv_bfloat16>(double x) {
+    return __float2bfloat16_rn(narrow_rn(x));
+}
+
 // ---- arithmetic in the canonical order (S) or freely contracted ------------------------------
 template <bool S> __device__ __forceinline__ double add(double a, double b) { return S ? __dadd_rn(a, b) : a + b; }
 template <bool S> __device__ __forceinline__ double sub(double a, double b) { return S ? __dsub_rn(a, b) : a - b; }
@@ -1087,7 +1133,7 @@ __global__ void __launch_bounds__(J3X * J3Y) k_update3(ResidArgs a, int n, int r
     const int k1 = min(k0 + rows, n);
     for (int k = k0; k < k1; ++k) {
         const double v = __ldg(a.u_in.p + at(a.u_in.pitch, n, i, j, k)) +
-                         (double)St<T>::ld(cp<T>(a.e) + at(a.e.pitch, n, i, j, k));
+                         to_d(St<T>::ld(cp<T>(a.e) + at(a.e.pitch, n, i, j, k)));
         a.u_out.p[at(a.u_out.pitch, n, i, j, k)] = v;
     }
 }
@@ -1119,9 +1165,9 @@ __global__ void __launch_bounds__(J3X * J3Y) k_residual3_fast(ResidArgs a, int n
             const double sum = ((uval(i - 1, j, k) + uval(i + 1, j, k)) + (uval(i, j - 1, k) + uval(i, j + 1, k))) + (vb + vt);
             const double fv = __ldg(F + (int64_t)k * plf + (int64_t)j * pf + i);
             const double r = fma(a.inv_h2, fma(-6.0, vc, sum), fv);
-            if (a.g0.p) wp<T>(a.g0)[at(a.g0.pitch, n, i, j, k)] = St<T>::put(St<T>::from_d(a.scale * r));
+            if (a.g0.p) wp<T>(a.g0)[at(a.g0.pitch, n, i, j, k)] = from_d_store<T>(a.scale * r);
             rr = fma(r, r, rr);
-            ff = fma(fv, fv, ff);
+            if (a.part_f) ff = fma(fv, fv, ff);
             vb = vc;
             vc = vt;
         }
@@ -1232,21 +1278,26 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
     }
 }
 
-// Fast update + residual (2-D): one column per thread marching along y, u_new = u_in + e formed
-// once per node; the west and east neighbours' updated values come from the adjacent lanes by warp
-// shuffle (the warp's edge lanes form theirs by hand), so a node costs 8 FP64 instructions (9 with
-// the norm of f on the initial residual). Results are bit-identical to forming every neighbour
-// locally.
+// Fast update + residual (2-D): each warp marches a strip of 32 columns along y; every lane forms
+// u_new = u_in + e once per node of its column, the 30 inner lanes own their nodes and take the west
+// and east neighbours' updated values by shuffle, the two edge lanes only supply theirs. Every
+// instruction is issued once per warp and row for 30 nodes, none for an edge lane alone: 8 FP64
+// instructions per node (9 with the norm of f on the initial residual). Widening e and rounding the
+// source to the cycle's storage use the integer conversions above. Results are bit-identical to
+// forming every neighbour locally.
+constexpr int RS_OUT = 30;  // nodes per warp strip
 template <typename T, bool VC, bool BATCH>
 __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     pdl_begin();
     if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
     __shared__ double sh[JX / 32];
-    const int i = blockIdx.x * JX + threadIdx.x + 1;
     const int lane = threadIdx.x & 31;
+    const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
+    const int i = strip * RS_OUT + lane;  // this lane's column
+    const bool col_in = i >= 1 && i <= n - 1;
+    const bool active = col_in && lane >= 1 && lane <= RS_OUT;
     const int j0 = blockIdx.y * JR + 1;
     const int j1 = min(j0 + JR, n);
-    const bool active = i < n;
     const bool upd = a.e.p != nullptr;
     const double* __restrict__ U = a.u_in.p ? a.u_in.p : a.st->u;
     const int64_t pu = a.u_in.p ? a.u_in.pitch : (int64_t)(n + 1);
@@ -1255,25 +1306,22 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     const double* __restrict__ F = a.st->f;
     const int64_t pf = n + 1;
     const bool want_f = a.part_f != nullptr;
-    auto un = [&](int ii, int jj) -> double {
-        if (ii <= 0 || jj <= 0 || ii >= n || jj >= n) return 0.0;
-        double v = __ldg(U + (int64_t)jj * pu + ii);
-        if (upd) v += (double)St<T>::ld(Ev + (int64_t)jj * pe + ii);
+    auto un = [&](int jj) -> double {  // updated iterate at (i, jj); 0 on the boundary and outside
+        if (!col_in || jj <= 0 || jj >= n) return 0.0;
+        double v = __ldg(U + (int64_t)jj * pu + i);
+        if (upd) v += to_d(St<T>::ld(Ev + (int64_t)jj * pe + i));
         return v;
     };
     double rr = 0.0, ff = 0.0;
-    // every lane runs the march (inactive lanes hold 0, the boundary value) so the shuffles see a full warp
-    double vs = un(i, j0 - 1), vc = un(i, j0);
+    double vs = un(j0 - 1), vc = un(j0);
     double ks = (VC && active) ? __ldg(a.ky + (int64_t)(j0 - 1) * a.kpitch + i) : 0.0;
     for (int j = j0; j < j1; ++j) {
-        const double vn = un(i, j + 1);
-        double w = __shfl_up_sync(0xffffffffu, vc, 1), e = __shfl_down_sync(0xffffffffu, vc, 1);
-        if (lane == 0) w = un(i - 1, j);
-        if (lane == 31) e = un(i + 1, j);
+        const double vn = un(j + 1);
+        const double w = __shfl_up_sync(0xffffffffu, vc, 1), e = __shfl_down_sync(0xffffffffu, vc, 1);
         if (active) {
             const double fv = __ldg(F + (int64_t)j * pf + i);
             double r;
-            if (VC) {  // r = f - (D u - sum k_nb u_nb) / h^2, D = sum of the four face coefficients
+            if constexpr (VC) {  // r = f - (D u - sum k_nb u_nb) / h^2, D = sum of the four face coefficients
                 const double* kr = a.kx + (int64_t)j * a.kpitch + i;
                 const double kw = __ldg(kr - 1), ke = __ldg(kr), kn = __ldg(a.ky + (int64_t)j * a.kpitch + i);
                 double t = kw * w;
@@ -1288,7 +1336,7 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
                 r = fma(a.inv_h2, fma(-4.0, vc, sum), fv);
             }
             if (a.u_out.p) a.u_out.p[(int64_t)j * a.u_out.pitch + i] = vc;
-            if (a.g0.p) wp<T>(a.g0)[(int64_t)j * a.g0.pitch + i] = St<T>::put(St<T>::from_d(a.scale * r));
+            if (a.g0.p) wp<T>(a.g0)[(int64_t)j * a.g0.pitch + i] = from_d_store<T>(a.scale * r);
             rr = fma(r, r, rr);
             if (want_f) ff = fma(fv, fv, ff);
         }
@@ -1465,10 +1513,11 @@ dim3 grid_for(int ndim, int n) {
     return dim3((unsigned)((n - 1 + BX - 1) / BX), (unsigned)((n - 1 + BY - 1) / BY), ndim == 3 ? (unsigned)(n - 1) : 1u);
 }
 
-// The fast residual kernels use their own grids: 2-D (n-1)/JX x (n-1)/JR blocks, 3-D
+// The fast residual kernels use their own grids: 2-D (n-1)/(30 * JX/32) x (n-1)/JR blocks, 3-D
 // (n-1)/J3X x (n-1)/J3Y x (n-1)/rows.
 dim3 resid_grid(int ndim, bool strict, int n) {
-    if (ndim == 2 && !strict) return dim3((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + JR - 1) / JR));
+    if (ndim == 2 && !strict)
+        return dim3((unsigned)((((n - 1 + RS_OUT - 1) / RS_OUT) + JX / 32 - 1) / (JX / 32)), (unsigned)((n - 1 + JR - 1) / JR));
     if (ndim == 3 && !strict) {
         const int rows = march_rows(3, n);
         return dim3((unsigned)((n - 1 + J3X - 1) / J3X), (unsigned)((n - 1 + J3Y - 1) / J3Y), (unsigned)((n - 1 + rows - 1) / rows));
@@ -1668,6 +1717,21 @@ cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_
                          : launch_k(k_jacobi2_x2<__nv_bfloat16, false>, g, b, s, a, rows);
         default: return cudaErrorInvalidValue;  // FP64 sweeps are FP64-bound: never paired
     }
+}
+
+__global__ void k_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        f_out[k] = narrow_rn(d_in[k]);
+        d_out[k] = widen_f32(f_in[k]);
+    }
+}
+
+cudaError_t launch_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n,
+                                     cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256, blocks = want < 152 * 16 ? want : 152 * 16;
+    k_check_conversions<<<(unsigned)blocks, 256, 0, s>>>(d_in, f_out, f_in, d_out, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a, cudaStream_t s) {

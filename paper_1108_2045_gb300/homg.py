@@ -39,6 +39,7 @@ EXPORTS = [
     "homg_last_error",
     "homg_destroy",
     "homg_residual_norm_noalloc",
+    "homg_check_conversions",
     "homg_batch_create",
     "homg_batch_set_stream",
     "homg_batch_solve",
@@ -380,6 +381,22 @@ def homg_residual_norm_noalloc(f, u, stream=None):
     _check(load().homg_residual_norm_noalloc(ndim, dims, _devptr(f, "f"), _devptr(u, "u"), ctypes.byref(rr),
                                              ctypes.c_void_p(raw)), None)
     return rr.value
+
+
+def homg_check_conversions(d_in, f_in):
+    """The library's integer binary64 -> binary32 (round to nearest even) and binary32 -> binary64
+    conversions of device tensors d_in (float64) and f_in (float32, same element count): returns
+    (f_out, d_out)."""
+    import torch
+
+    if d_in.dtype != torch.float64 or f_in.dtype != torch.float32 or d_in.numel() != f_in.numel():
+        raise TypeError("d_in must be float64 and f_in float32 with the same element count")
+    f_out = torch.empty(d_in.shape, dtype=torch.float32, device=d_in.device)
+    d_out = torch.empty(f_in.shape, dtype=torch.float64, device=f_in.device)
+    _check(load().homg_check_conversions(_devptr_any(d_in, "d_in"), _devptr_any(f_out, "f_out"),
+                                         _devptr_any(f_in, "f_in"), _devptr_any(d_out, "d_out"),
+                                         ctypes.c_int64(d_in.numel())), None)
+    return f_out, d_out
 
 
 def homg_get_history(handle, cap=HOMG_MAX_CYCLES + 1):
