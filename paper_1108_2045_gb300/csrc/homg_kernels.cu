@@ -55,12 +55,17 @@ template <> struct St<__nv_bfloat16> {
 // operations only; subnormals, infinities and NaNs, which these kernels practically never meet,
 // use the hardware conversion. Both are exact copies of it (homg_check_conversions tests that).
 
+// The rare classes go through out-of-line hardware conversions, so that the compiler cannot
+// if-convert them into conversions issued for every element.
+__device__ __noinline__ double widen_hw(float x) { return (double)x; }
+__device__ __noinline__ float narrow_hw(double d) { return __double2float_rn(d); }
+
 // binary32 -> binary64 (exact): re-bias the exponent, move the fraction to the top of the 52 bits.
 __device__ __forceinline__ double widen_f32(float x) {
     const unsigned b = __float_as_uint(x);
     const unsigned ex = (b >> 23) & 0xffu;
     if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-    if (ex == 0u || ex == 0xffu) return (double)x;
+    if (__builtin_expect(ex == 0u || ex == 0xffu, 0)) return widen_hw(x);
     const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
     return __hiloint2double((int)hi, (int)(b << 29));
 }
@@ -74,7 +79,7 @@ __device__ __forceinline__ float narrow_rn(double d) {
     const unsigned sg = hi & 0x80000000u;
     if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(sg);
     const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // binary32 biased exponent
-    if (e <= 0 || e >= 255) return __double2float_rn(d);
+    if (__builtin_expect(e <= 0 || e >= 255, 0)) return narrow_hw(d);
     const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
     const unsigned rem = lo & 0x1fffffffu;
     const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
