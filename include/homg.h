@@ -179,7 +179,9 @@ void homg_default_options(homg_options* opt);
  *   out      receives the handle (NULL on failure).
  * Allocates one device buffer holding every level (all compact level arrays, the fine iterates,
  * the per-level restricted sources, norm partials and the cycle state) on the current device,
- * and creates the handle's events and pinned host state. Returns 0 or a negative code. */
+ * and creates the handle's events and pinned host state. A 2-D handle in the fast lattice form
+ * then times its marching sweeps once per lattice size on the legacy default stream (a few ms;
+ * the choice changes launch shapes only, never results). Returns 0 or a negative code. */
 int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const homg_options* opt, homg_handle* out);
 
 /* Use `stream` (a cudaStream_t, NULL = legacy default stream) for every later call on h. */

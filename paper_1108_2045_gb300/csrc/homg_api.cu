@@ -993,6 +993,14 @@ int create_ctx(int ndim, int64_t n, int K, int levels, int stencil, const homg_o
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us, double min_nodes = 0.0);
+}
+
+extern "C" {
+
 int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const homg_options* opt, homg_handle* out) {
     if (out) *out = nullptr;
     g_create_error[0] = 0;
@@ -1020,8 +1028,22 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     if (rc != HOMG_OK) return rc;
     homg_ctx* h = nullptr;
     rc = create_ctx(ndim, dims[0] - 1, K, levels, stencil, o, 1, &h);
-    if (rc == HOMG_OK) *out = h;
-    return rc;
+    if (rc != HOMG_OK) return rc;
+    // fast 2-D lattice form: time the marching sweeps of the lattices of a million nodes or more
+    // once, as the batches do (smaller sweeps are launch-latency bound, and timing them alone is
+    // too noisy to beat the size heuristic)
+    if (ndim == 2 && !h->strict && h->exec == HOMG_EXEC_LATTICE && h->geometry == HOMG_GEOM_NESTED) {
+        int rows = 0;
+        double us = 0.0;
+        rc = autotune_rows(h, h->stream, &rows, &us, 1.0e6);
+        if (rc != HOMG_OK) {
+            set_null_handle_error(h->err);
+            homg_destroy(h);
+            return rc;
+        }
+    }
+    *out = h;
+    return HOMG_OK;
 }
 
 }  // extern "C"
@@ -1044,11 +1066,11 @@ struct homg_batch_ctx {
 namespace {
 
 // Autotuner: for every lattice size the group sweeps with the marching Jacobi kernels (single and
-// paired sweeps separately), time the plain sweep (all problems at once) for each candidate number
-// of nodes per thread along the march, keep the fastest, and use it for every sweep of that kind
-// and size. Reports the level-0 choice of the single sweep (of the paired one when the level has
+// paired sweeps separately; sizes of at least min_nodes nodes over all problems), time the plain
+// sweep (all problems at once, 5 launches after 2 warm-ups) for each candidate number of nodes per
+// thread along the march, keep the fastest, and use it for every sweep of that kind and size. Reports the level-0 choice of the single sweep (of the paired one when the level has
 // no single plain sweep).
-int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us) {
+int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us, double min_nodes) {
     *best_rows = 0;
     *best_us = 0.0;
     std::vector<const Op*> tmpl;
@@ -1056,6 +1078,8 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us)
         for (const Op& op : *part) {
             const bool single = op.kind == Op::ITER && op.it.e_old.p;
             if ((!single && op.kind != Op::ITER2) || op.it.m != 0) continue;
+            const double nodes = (double)h->nbatch * (double)(op.it.e_new.n - 1) * (double)(op.it.e_new.n - 1);
+            if (nodes < min_nodes) continue;
             bool seen = false;
             for (const Op* t : tmpl) seen |= t->kind == op.kind && t->sweeps == op.sweeps && t->it.e_new.n == op.it.e_new.n;
             if (!seen) tmpl.push_back(&op);
@@ -1083,7 +1107,8 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us)
             if (rows > n - 1) break;
             a.rows = rows;
             cudaError_t e = launch();  // warm-up
-            for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            if (e == cudaSuccess) e = launch();
+            for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
                 if (r == 0) e = cudaEventRecord(e0, st);
                 if (e == cudaSuccess) e = launch();
             }
@@ -1096,7 +1121,7 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us)
                 cudaEventDestroy(e1);
                 return cuda_fail(h, e, "autotuning the sweep");
             }
-            const double us = 1e3 * ms / 3.0;
+            const double us = 1e3 * ms / 5.0;
             if (us < best) { best = us; pick = rows; }
         }
         for (auto* part : {&h->partA, &h->partB})
