@@ -1066,10 +1066,11 @@ struct homg_batch_ctx {
 namespace {
 
 // Autotuner: for every lattice size the group sweeps with the marching Jacobi kernels (single and
-// paired sweeps separately; sizes of at least min_nodes nodes over all problems), time the plain
+// fused sweeps separately; sizes of at least min_nodes nodes over all problems), time the plain
 // sweep (all problems at once, 5 launches after 2 warm-ups) for each candidate number of nodes per
-// thread along the march, keep the fastest, and use it for every sweep of that kind and size. Reports the level-0 choice of the single sweep (of the paired one when the level has
-// no single plain sweep).
+// thread along the march, keep the fastest, and use it for every sweep of that kind and size.
+// Reports the level-0 choice of the single sweep (of the fused one when the level has no single
+// plain sweep).
 int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us, double min_nodes) {
     *best_rows = 0;
     *best_us = 0.0;
@@ -1086,7 +1087,10 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us,
         }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0), "cudaEventCreate");
-    CK(h, cudaEventCreate(&e1), "cudaEventCreate");
+    if (cudaError_t ce = cudaEventCreate(&e1); ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(h, ce, "cudaEventCreate");
+    }
     bool level0_single = false;
     for (const Op* t : tmpl) {
         const Op::Kind kind = t->kind;

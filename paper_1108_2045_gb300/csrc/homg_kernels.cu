@@ -952,7 +952,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
     const int64_t pe = a.e_old.pitch, pg = a.g.pitch, po = a.e_new.pitch;
     const T* __restrict__ E0 = cp<T>(a.e_old) + il;
     const T* __restrict__ G0 = cp<T>(a.g) + il;
-    T* __restrict__ O0 = wp<T>(a.e_new) + i;
+    T* __restrict__ O = wp<T>(a.e_new);
     const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
     // Loads use rows clamped into 0..n, so that the march has no branch and the unrolled loop can
     // issue several rows of loads ahead; values on rows outside 1..n-1 are then replaced by 0.
@@ -985,7 +985,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
             if (l < K) {
                 v[l] = (col_in && x >= 1 && x <= n - 1) ? as_c<T>(St<T>::put(y)) : (C)0;
             } else if (out && x >= j0 && x < j1) {
-                O0[(int64_t)x * po] = St<T>::put(y);
+                O[(int64_t)x * po + i] = St<T>::put(y);
             }
             sp[l - 1] = sc[l - 1];
             sc[l - 1] = v[l - 1];
