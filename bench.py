@@ -40,6 +40,8 @@ FP64_PEAK_OPS = 0.625e12
 
 FALLBACK_BF16_TFLOPS = 1900.0
 LEVEL0_FP64_DRAM_BYTES = 382.45e6  # k_jacobi2<0, 0, double> on 4097^2, mean of two captured launches
+# k_jacobi2_x2<float> (two fused sweeps) on 4097^2, one captured launch: 134.8 MB read + 38.2 MB written
+LEVEL0_FP32_DRAM_BYTES = 173.01e6
 
 
 def measured_peaks():
@@ -738,13 +740,15 @@ def run(args):
     kname = ("k_jacobi2 (level-0 HOMG iteration: damped Jacobi on every interior node)" if sweeps_per_launch == 1 else
              "k_jacobi2_x2 / k_jacobi2 (level-0 HOMG iterations, consecutive plain sweeps fused two per launch; "
              "average over the level's launches)")
-    # DRAM bytes (read + write) per launch of this kernel from ncu (profiles/k_jacobi2_fp64_4097.md);
-    # only the FP64 build of the kernel was captured in its current form
-    traffic = LEVEL0_FP64_DRAM_BYTES if args.precision == "fp64" else None
+    # DRAM bytes (read + write) per launch of this kernel from ncu: the FP64 sweep
+    # (profiles/k_jacobi2_fp64_4097.md) and the fused FP32 pair (profiles/k_jacobi2_x2_fp32_4097.md;
+    # the level's two single FP32 sweeps move the same bytes); the bfloat16 build was not captured
+    traffic, traffic_src = {"fp64": (LEVEL0_FP64_DRAM_BYTES, "profiles/k_jacobi2_fp64_4097.md"),
+                            "fp32": (LEVEL0_FP32_DRAM_BYTES, "profiles/k_jacobi2_x2_fp32_4097.md")}.get(
+        args.precision, (None, None))
     common = {"kernel": kname, "launch_us": per_launch_s * 1e6, "launches": launches,
               "algorithmic_flops_per_launch": ops, "algorithmic_bytes_per_launch": bts, "traffic": traffic,
-              "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_jacobi2_fp64_4097.md"
-              if traffic else None}
+              "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + traffic_src if traffic else None}
     if args.precision == "fp64":
         # FP64 pipe bound on GB300: 5 FP64 instructions per node against 0.625e12 instructions/s
         roofline = dict(common, bound="alu", achieved=alu_achieved, peak=FP64_PEAK_OPS / 1e12, unit="TFP64op/s",
