@@ -303,12 +303,16 @@ void homg_batch_destroy(homg_batch_handle b);
  *   stream     cudaStream_t to run on (NULL = legacy default stream); synchronised before return.
  *   relres_out host pointer receiving the result (0 when f = 0 and u's interior is 0, +inf when
  *              f = 0 otherwise).
- * Scratch: a fixed 1 MiB file-scope device array, held by every GPU that loads the library until
- * the process exits, shared by all calls and keeping the last call's contents (every value a call
- * reads is written by that call first). Calls whose work overlaps on one GPU (other host threads,
- * other streams) race on it: serialise them. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) once for that device; make that first call before any
- * stream capture. Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+ * Scratch: a fixed file-scope device array of (32 + 2 * HOMG_NOALLOC_MAX_BLOCKS) doubles
+ * (1,048,832 bytes, just over 1 MiB), held by every GPU that loads the library until the process
+ * exits, shared by all calls and keeping the last call's contents (every value a call reads is
+ * written by that call first). Calls whose work overlaps on one GPU (other host threads, other
+ * streams) race on it: serialise them. The current device must be the one holding f and u. Each
+ * call made outside stream capture looks up the array's device address on the current device
+ * (cudaGetSymbolAddress), so a device reset leaves the entry point usable; a call made while
+ * `stream` is capturing reuses the address found by the last call outside capture on that device,
+ * so make the first call on each device before any stream capture. Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine. */
 int homg_residual_norm_noalloc(int ndim, const int64_t* dims, const double* f, const double* u, double* relres_out,
                                void* stream);
 

@@ -14,8 +14,9 @@
  * Problem (Sec. 2, Eq. 1; Sec. 4, Eq. "poisson"): A u = f on the unit square (cube) with zero
  * Dirichlet boundary, A = -Laplacian discretised with the 5-point (2-D) or 7-point (3-D) stencil
  * on a node grid of (n+1)^d nodes, n = 2^K, h = 1/n. The paper writes the Poisson equation with
- * the opposite sign; the positive-definite form is used here so that damped Jacobi is stable
- * (reading A1 of the design notes).
+ * the opposite sign, and its relaxation formula, read with that sign, would grow the error for
+ * any positive weight; the positive-definite form is used here so that damped Jacobi is stable,
+ * and the paper's own test source is passed in with its sign flipped.
  *
  * Layout: node (i, j[, k]) of a grid with n intervals per side lives at
  *   2-D: j*(n+1) + i          3-D: (k*(n+1) + j)*(n+1) + i        (x fastest).

@@ -30,17 +30,24 @@ static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 256;
 std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};  // device address of g_scratch, per device ordinal
+double* g_scratch_addr[kMaxDevices] = {};  // device address of g_scratch last looked up, per device ordinal
 
 int fail(int code, const char* msg) {
     set_null_handle_error(msg);
     return code;
 }
 
-// Device address of g_scratch on the current device (looked up once per device).
-cudaError_t scratch_address(int dev, double** out) {
+// Device address of g_scratch on the current device. A call made outside stream capture looks it
+// up again every time: after cudaDeviceReset (or any other end of the device's context) the
+// library's module is loaded anew and the array may sit at another address. A call made while `s`
+// is capturing, or whose capture status cannot be read, reuses the address that the last call
+// outside capture found on this device, and looks it up only if there is none yet.
+cudaError_t scratch_address(int dev, cudaStream_t s, double** out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool known = cudaStreamIsCapturing(s, &cs) == cudaSuccess;
+    if (!known) cudaGetLastError();
+    if (!g_scratch_addr[dev] || (known && cs == cudaStreamCaptureStatusNone)) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
@@ -80,14 +87,14 @@ extern "C" int homg_residual_norm_noalloc(int ndim, const int64_t* dims, const d
         cudaGetLastError();
         return fail(HOMG_ECUDA, "homg_residual_norm_noalloc: no usable current device");
     }
+    cudaStream_t s = (cudaStream_t)stream;
     double* scratch = nullptr;
-    e = scratch_address(dev, &scratch);
+    e = scratch_address(dev, s, &scratch);
     if (e != cudaSuccess) {
         snprintf(msg, sizeof(msg), "homg_residual_norm_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         cudaGetLastError();
         return fail(HOMG_ECUDA, msg);
     }
-    cudaStream_t s = (cudaStream_t)stream;
     State* st = (State*)scratch;
     // The arguments block is rewritten on every call; each partial slot the reduction reads is
     // written by its block first, so nothing left by an earlier call is read.

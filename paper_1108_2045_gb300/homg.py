@@ -373,13 +373,27 @@ def homg_set_coefficient(handle, k):
 
 def homg_residual_norm_noalloc(f, u, stream=None):
     """||f - A u|| / ||f|| of device tensors without a handle; the library allocates nothing for it
-    (its scratch is a fixed static device array shared by all calls: do not overlap calls)."""
+    (its scratch is a fixed static device array shared by all calls: do not overlap calls).
+
+    f and u must be contiguous float64 tensors of the same (2^K+1)^ndim shape on the same GPU; the
+    call runs with that GPU current. Mismatches raise TypeError before anything reaches the device."""
+    import torch
+
     ndim = f.dim()
+    if ndim not in (2, 3) or any(d != f.shape[0] for d in f.shape):
+        raise TypeError("f must be a square (2-D) or cubic (3-D) node grid, got shape %s" % (tuple(f.shape),))
+    if tuple(u.shape) != tuple(f.shape):
+        raise TypeError("u must have f's shape %s, got %s" % (tuple(f.shape), tuple(u.shape)))
+    if u.device != f.device:
+        raise TypeError("u and f must be on the same device, got %s and %s" % (u.device, f.device))
+    if f.dtype != torch.float64 or u.dtype != torch.float64:
+        raise TypeError("f and u must be float64")
     dims = (ctypes.c_int64 * ndim)(*f.shape)
     rr = ctypes.c_double(0.0)
     raw = getattr(stream, "cuda_stream", stream) or 0
-    _check(load().homg_residual_norm_noalloc(ndim, dims, _devptr(f, "f"), _devptr(u, "u"), ctypes.byref(rr),
-                                             ctypes.c_void_p(raw)), None)
+    fp, up = _devptr(f, "f"), _devptr(u, "u")
+    with torch.cuda.device(f.device):
+        _check(load().homg_residual_norm_noalloc(ndim, dims, fp, up, ctypes.byref(rr), ctypes.c_void_p(raw)), None)
     return rr.value
 
 

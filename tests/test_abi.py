@@ -123,3 +123,34 @@ def test_power_of_two_geometry_argument_checks(homg):
         homg.homg_create(2, 33, 3, geometry=7)
     with pytest.raises(homg.HomgError):
         homg.homg_batch_create([33, 65], geometry="pow2")
+
+
+def test_noalloc_binding_rejects_mismatched_tensors_before_the_device(homg):
+    """The allocation-free residual's binding checks shapes, devices and dtypes before it hands any
+    pointer to the library (a smaller u would otherwise be read past its end)."""
+    import torch
+
+    f = torch.zeros(9, 9, dtype=torch.float64)
+    cases = [torch.zeros(5, 5, dtype=torch.float64),                    # smaller u
+             torch.zeros(9, 9, 9, dtype=torch.float64),                 # other dimension
+             torch.zeros(9, 9, dtype=torch.float64, device="meta"),     # other device
+             torch.zeros(9, 9, dtype=torch.float32)]                    # other dtype
+    for u in cases:
+        with pytest.raises(TypeError):
+            homg.homg_residual_norm_noalloc(f, u)
+    with pytest.raises(TypeError):
+        homg.homg_residual_norm_noalloc(torch.zeros(9, 5, dtype=torch.float64), torch.zeros(9, 5, dtype=torch.float64))
+    with pytest.raises(TypeError):  # host tensors never reach the library
+        homg.homg_residual_norm_noalloc(f, torch.zeros(9, 9, dtype=torch.float64))
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch_on_the_host(homg):
+    """Grids needing more partial sums than the static scratch holds are refused by the size check,
+    which runs before any device access."""
+    lib = homg.load()
+    for ndim, side, parts in ((2, 16385, 140288), (3, 1025, 524288)):
+        dims = (ctypes.c_int64 * ndim)(*([side] * ndim))
+        rr = ctypes.c_double(0.0)
+        rc = lib.homg_residual_norm_noalloc(ndim, dims, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(rr), None)
+        assert rc == homg.HOMG_ESHAPE
+        assert ("needs %d partial sums" % parts) in homg.homg_last_error(None)

@@ -28,7 +28,10 @@ def homg():
     return binding
 
 
-@pytest.mark.parametrize("ndim,n,levels", [(2, 256, 8), (2, 4096, 12), (3, 64, 6)])
+# 8193^2 (35,328 partial sums) and 513^3 (exactly HOMG_NOALLOC_MAX_BLOCKS = 65,536) are the largest
+# grids the header promises; a change of the residual kernel's launch shape that shrinks that range
+# fails here.
+@pytest.mark.parametrize("ndim,n,levels", [(2, 256, 8), (2, 4096, 12), (3, 64, 6), (2, 8192, 13), (3, 512, 9)])
 def test_noalloc_matches_handle_entry_point_twice(homg, ndim, n, levels):
     import torch
 
@@ -49,8 +52,12 @@ def test_noalloc_rejects_grids_beyond_its_scratch(homg):
     import ctypes
 
     lib = homg.load()
-    dims = (ctypes.c_int64 * 2)(16385, 16385)  # needs 131072 partial sums: rejected before any device access
-    rr = ctypes.c_double(0.0)
-    rc = lib.homg_residual_norm_noalloc(2, dims, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(rr), None)
-    assert rc == homg.HOMG_ESHAPE
-    assert "static scratch" in homg.homg_last_error(None)
+    # 16385^2 needs 137 x 1024 = 140,288 partial sums and 1025^3 needs 32 x 256 x 64 = 524,288: both
+    # are rejected by the size check, before any device access
+    for ndim, side, parts in ((2, 16385, 140288), (3, 1025, 524288)):
+        dims = (ctypes.c_int64 * ndim)(*([side] * ndim))
+        rr = ctypes.c_double(0.0)
+        rc = lib.homg_residual_norm_noalloc(ndim, dims, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(rr), None)
+        assert rc == homg.HOMG_ESHAPE
+        msg = homg.homg_last_error(None)
+        assert "static scratch" in msg and ("needs %d partial sums" % parts) in msg, msg
