@@ -33,9 +33,9 @@ WORKLOAD = ("2-D Poisson -Lap u = f, 5-point, 4097x4097 nodes, 12 levels, FP64, 
 
 # Peaks for the roofline (denominators).
 FALLBACK_HBM_GBS = 6800.0
-# FP64 issue rate: nominal 1.25 TFLOP/s (FMA = 2 flops) = 0.625e12 FP64 instructions/s,
-# i.e. 2 FP64 instructions per clock per SM x 152 SMs x 2.07 GHz.
-FP64_PEAK_OPS = 0.625e12
+# Nominal FP64 issue rate, for context only: 1.25 TFLOP/s (FMA = 2 flops) = 0.625e12 FP64
+# instructions/s. The denominator of the FP64 ALU fraction is measured live (measure_fp64_peak).
+FP64_NOMINAL_OPS = 0.625e12
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -139,18 +139,126 @@ def replica_throughput(units_per_rank, elapsed_s, device=None):
     return units_per_rank * world / max_over_ranks(elapsed_s, device)
 
 
-def oracle_cpu_baseline(f_np, cycles):
-    """The oracle as it stands, single-threaded on a host core: one cycle on the benchmark grid
-    (residual + restriction + 286 HOMG iterations), scaled by the solve's cycle count."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def oracle_cpu_baseline(f_np, full=True):
+    """The oracle as it stands, single-threaded on one host core: the complete benchmark solve
+    (u0 = 0 to relres 1e-10) on the 4097^2 grid, timed in full; or (full=False) one cycle of it,
+    scaled by the oracle's own cycle count at 1025^2."""
     import oracle
 
     oracle.build()
     t0 = time.perf_counter()
+    if full:
+        _, status, cycles, hist = oracle.solve(f_np, LEVELS, tol=TOL, max_cycles=MAX_CYCLES, max_i=MAX_I)
+        dt = time.perf_counter() - t0
+        if status != oracle.OK:
+            raise RuntimeError("oracle solve did not converge (status %d)" % status)
+        return {"value": (N_SIDE - 1) ** 2 / dt, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle",
+                "sample": "the full oracle solve of the 4097^2 workload, u0 = 0 to relres 1e-10 "
+                          "(%d cycles, final relres %.2e, %.1f s, one thread)" % (cycles, hist[-1], dt),
+                "ms_per_solve": 1e3 * dt, "cycles": cycles}
     oracle.solve(f_np, LEVELS, tol=0.0, max_cycles=1, max_i=MAX_I)
     dt = time.perf_counter() - t0
-    t_solve = dt * cycles
-    return {"value": (N_SIDE - 1) ** 2 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one oracle cycle on the 4097^2 grid (%.1f s), scaled by the %d cycles a solve takes" % (dt, cycles)}
+    _, _, cycles, _ = oracle.solve(inputs_uniform(1024), 10, tol=TOL, max_cycles=MAX_CYCLES, max_i=MAX_I)
+    return {"value": (N_SIDE - 1) ** 2 / (dt * cycles), "unit": UNIT, "cores": 1, "host_cores": host_cores(),
+            "kind": "oracle",
+            "sample": "one oracle cycle on the 4097^2 grid (%.1f s), scaled by the %d cycles the oracle needs at "
+                      "1025^2" % (dt, cycles)}
+
+
+def inputs_uniform(n):
+    from paper_1108_2045_gb300 import inputs
+
+    return inputs.uniform_rhs(n, 2, seed=0)
+
+
+def measure_fp64_peak(homg, stream, dev, clocks_index):
+    """The FP64 instruction issue rate of this GPU, measured now: the library's probe kernel (8
+    independent chains of dependent FP64 fused multiply-adds, or additions, per thread; 8 blocks of
+    256 threads per SM) launched 20 times back to back after 3 warm-up launches, each launch timed
+    with CUDA events on the stream. Returns the mean and best rates per op and the SM clock seen."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 8 * sms
+    sink = torch.empty(blocks * homg.HOMG_PROBE_THREADS, dtype=torch.float64, device=dev)
+    out = {"kernel": "homg_fp64_issue_probe (k_fp64_issue)", "blocks": blocks,
+           "threads_per_block": homg.HOMG_PROBE_THREADS}
+    iters = 2048
+    with ClockSampler(clocks_index) as clk:
+        for op, name in ((0, "fma"), (1, "add")):
+            for _ in range(3):
+                instr = homg.homg_fp64_issue_probe(op, blocks, iters, sink, stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(21)]
+            ev[0].record(stream)
+            for i in range(20):
+                homg.homg_fp64_issue_probe(op, blocks, iters, sink, stream)
+                ev[i + 1].record(stream)
+            torch.cuda.synchronize(dev)
+            ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(20)]
+            out[name] = {"instructions_per_launch": instr, "launch_ms_mean": sum(ms) / len(ms),
+                         "mean_tinstr_per_s": instr / (sum(ms) / len(ms) * 1e-3) / 1e12,
+                         "best_tinstr_per_s": instr / (min(ms) * 1e-3) / 1e12}
+    out["clocks"] = clk.summary()
+    out["peak_tinstr_per_s"] = max(out["fma"]["mean_tinstr_per_s"], out["add"]["mean_tinstr_per_s"])
+    return out
+
+
+def run_cfg2_sine(args, homg, inputs, stream, barrier, pending):
+    """The manufactured right-hand side of the 4097^2 workload, f = 2 pi^2 sin(pi x) sin(pi y), whose
+    discrete solution is c_h sin(pi x) sin(pi y) with c_h = pi^2 h^2 / (4 sin^2(pi h / 2)). The FP64
+    rounding of that exact solution alone leaves a relative residual (the floor, measured here with the
+    library's residual of the rounded closed form, and by the oracle in the CPU leg) above 1e-10 at
+    this size, so HOMG and the classic V(2,2) cycle solve to tol = max(1e-10, 4 x floor), FP64 cycles.
+    Reports cycles, time, the attained relres and the error against the closed form."""
+    import numpy as np
+    import torch
+
+    n, L = N_SIDE, LEVELS
+    h = 1.0 / n
+    ch = np.pi ** 2 * h ** 2 / (4 * np.sin(np.pi * h / 2) ** 2)
+    f_np = inputs.sine_rhs(n, 2)
+    exact_np = ch * inputs.sine_solution(n, 2)
+    f = torch.from_numpy(f_np).cuda()
+    exact = torch.from_numpy(exact_np).cuda()
+    u = torch.zeros_like(f)
+    with homg.Solver(2, n + 1, L) as s:
+        s.set_stream(stream)
+        floor = s.residual_norm(f, exact)
+    tol = max(TOL, 4.0 * floor)
+    out = {"workload": "2-D Poisson, 4097^2 nodes, 12 levels, f = 2 pi^2 sin(pi x) sin(pi y), u0 = 0, FP64 cycles",
+           "floor_relres": floor, "tol": tol}
+    for name, kw in (("homg", dict(max_i=MAX_I)), ("v22", dict(cycle="v"))):
+        with homg.Solver(2, n + 1, L, **kw) as s:
+            s.set_stream(stream)
+            u.zero_()
+            s.solve(f, u, tol=tol, max_cycles=MAX_CYCLES)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.cfg2_sine_steps):
+                u.zero_()
+                st, cyc, rr = s.solve(f, u, tol=tol, max_cycles=MAX_CYCLES)
+            e1.record(stream)
+            barrier()
+            ms = e0.elapsed_time(e1) / args.cfg2_sine_steps
+        r = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms, "unknowns_per_s": (n - 1) ** 2 / (ms * 1e-3),
+             "rel_err_vs_discrete_exact": float(torch.linalg.vector_norm(u - exact) / torch.linalg.vector_norm(exact))}
+        if name == "homg":
+            pending.append((r, "poisson", None, f_np, u.cpu().numpy()))
+        out[name] = r
+    out["homg_ms_over_v22_ms"] = out["homg"]["ms_per_solve"] / out["v22"]["ms_per_solve"]
+    pending.append((out, "floor", None, f_np, exact_np))
+    del f, u, exact
+    torch.cuda.empty_cache()
+    return out
 
 
 CFG3_SIDE = 512
@@ -488,6 +596,8 @@ def cpu_leg(pending):
             rr = oracle.norm_interior(oracle.residual(a, b)) / oracle.norm_interior(a)
             key = "oracle_relres" if kind == "poisson" else "oracle_relres_max_sampled"
             target[key] = max(rr, target.get(key, 0.0))
+        elif kind == "floor":
+            target["oracle_floor_relres"] = oracle.norm_interior(oracle.residual(a, b)) / oracle.norm_interior(a)
         elif kind == "vc":
             target["oracle_relres"] = oracle.norm_interior(oracle.residual_vc(kc, a, b)) / oracle.norm_interior(a)
         elif kind == "batch_time":
@@ -525,37 +635,108 @@ def cpu_leg(pending):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper publishes no code) on the benchmark workload, one
+    thread of the host. A step is one MFMG cycle of the restarted oracle solve (restriction, 286
+    HOMG iterations over the 4097^2 grid, update and residual); consecutive steps continue the same
+    solve from u0 = 0, so the run itself observes how many cycles reach relres 1e-10 (cycles are
+    added, untimed, if warm-up plus timed steps end first). ms_per_step is the measured mean time of
+    a timed step; value = unknowns / (that time x the observed cycle count)."""
     world, rank, local = dist_setup(args)
     if rank != 0:
         return 0
+    import numpy as np
+
     import oracle
     from paper_1108_2045_gb300 import inputs
 
     oracle.build()
     f = inputs.uniform_rhs(N_SIDE, 2, seed=0)
-    # cycle count of the full solve (resolution-independent contraction): from the oracle at 1025^2
-    fs = inputs.uniform_rhs(1024, 2, seed=0)
-    _, _, cycles, _ = oracle.solve(fs, 10, tol=TOL, max_cycles=MAX_CYCLES, max_i=MAX_I)
-    times = []
+    u = np.zeros_like(f)
+    times, relres, converged_after = [], None, None
+    cycles_done = 0
+
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.solve(f, LEVELS, tol=0.0, max_cycles=1, max_i=MAX_I)
+        u_next, _, _, hist = oracle.solve(f, LEVELS, u0=u, tol=0.0, max_cycles=1, max_i=MAX_I)
         dt = time.perf_counter() - t0
+        u = u_next
+        cycles_done += 1
+        relres = hist[-1]
+        if converged_after is None and relres <= TOL:
+            converged_after = cycles_done
         if step >= args.warmup:
-            times.append(dt * cycles)
-    total = sum(times)
-    value = (N_SIDE - 1) ** 2 * args.steps / total
-    sample = ("each step: one oracle cycle on the 4097^2 grid, scaled by the %d cycles the solve needs "
-              "(cycle count from the oracle's full solve at 1025^2)" % cycles)
+            times.append(dt)
+    while converged_after is None and cycles_done < MAX_CYCLES:  # untimed: only to count cycles
+        u, _, _, hist = oracle.solve(f, LEVELS, u0=u, tol=0.0, max_cycles=1, max_i=MAX_I)
+        cycles_done += 1
+        relres = hist[-1]
+        if relres <= TOL:
+            converged_after = cycles_done
+    if converged_after is None:
+        raise RuntimeError("the oracle solve did not reach relres %g" % TOL)
+    step_s = sum(times) / len(times)
+    value = (N_SIDE - 1) ** 2 / (step_s * converged_after)
+    sample = ("each step: one MFMG cycle of the oracle's restarted solve on the 4097^2 grid (one thread), steps "
+              "continuing one solve from u0 = 0; relres 1e-10 after %d cycles (observed in this run); "
+              "value = unknowns / (mean step time %.1f s x %d)" % (converged_after, step_s, converged_after))
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle", "sample": sample}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL},
-            "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL,
+                       "step": "one oracle MFMG cycle", "cycles_to_tol": converged_after},
+            "impl": "reference", "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def legs_digest(line):
+    """Compact summary of every leg of the line (ms per solve, cycles, checks), kept short so that it
+    fits at the end of the printed line."""
+    def r3(x):
+        return None if x is None else float("%.4g" % x)
+
+    d = {"fp64_ms": r3(line["ms_per_step"]), "fp64_cyc": line["config"]["cycles"],
+         "roof_hbm": r3(line["roofline"]["frac"])}
+    alu = line["roofline"].get("alu", {})
+    if "frac" in alu:
+        d["roof_fp64pipe"] = r3(alu["frac"])
+        d["fp64_peak_T"] = r3(alu["peak"])
+    if "e2e" in line:
+        d["e2e_Mps"] = r3(line["e2e"]["value"] / 1e6)
+    for k, v in line.get("mixed_precision", {}).items():
+        d[k + "_ms"] = [r3(v["ms_per_step"]), v["cycles"], r3(v["fine_hbm_frac"])]
+    for k, v in line.get("vcycle_v22", {}).items():
+        d["v22_" + k + "_ms"] = [r3(v["ms_per_step"]), v["cycles"]]
+    if "wholegrid" in line:
+        d["wg_ms"] = r3(line["wholegrid"]["ms_per_step"])
+    c = line.get("cfg2_manufactured")
+    if c:
+        d["sine4097"] = {"floor": r3(c["floor_relres"]), "homg": [r3(c["homg"]["ms_per_solve"]), c["homg"]["cycles"]],
+                         "v22": [r3(c["v22"]["ms_per_solve"]), c["v22"]["cycles"]],
+                         "orc_rr": r3(c["homg"].get("oracle_relres"))}
+    c = line.get("cfg1_small")
+    if c:
+        d["cfg1"] = [r3(c["ms_per_solve"]), c["cycles"], r3(c.get("cpu_oracle", {}).get("ms_per_solve"))]
+    c = line.get("cfg3_3d")
+    if c:
+        d["cfg3"] = {rhs: {p: [r3(v["ms_per_solve"]), v["cycles"]] for p, v in c[rhs].items()}
+                     for rhs in ("sine", "normal") if rhs in c}
+    c = line.get("cfg4_batched")
+    if c:
+        d["cfg4"] = {p: [r3(c[p]["batch_ms"]), r3(c[p]["solve_ms_p50"]), r3(c[p]["solve_ms_p99"]), c[p]["all_converged"]]
+                     for p in ("fp32", "fp64", "fp32_persistent") if p in c}
+    c = line.get("cfg5_learned")
+    if c:
+        d["cfg5"] = {"plain": {p: r3(v["ms_per_solve"]) for p, v in c["plain"].items()},
+                     "learned": {p: [r3(v["ms_per_solve"]), v["proposals_kept"]] for p, v in c.get("learned", {}).items()}}
+    c = line.get("pow2_grid")
+    if c:
+        d["pow2"] = {p: [r3(c[p]["ms_per_solve"]), c[p]["cycles"]] for p in ("fp64", "fp32") if p in c}
+    if "cpu_baseline" in line:
+        d["cpu_Mps"] = r3(line["cpu_baseline"]["value"] / 1e6)
+    return d
 
 
 def run(args):
@@ -718,7 +899,10 @@ def run(args):
                           "homg_ms_over_v_ms": (homg_ms / vms) if homg_ms else None,
                           "time_split_ms_per_step": {k: sum(x[k] for x in sts) / len(sts)
                                                      for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms")}}
+    # the FP64 pipe's issue rate on this GPU, now (denominator of the FP64 ALU fraction)
+    fp64_peak = measure_fp64_peak(homg, stream, dev, local) if args.fp64_probe else None
     pending = []  # oracle work of the CPU leg (rank 0, one GPU only)
+    cfg2s = run_cfg2_sine(args, homg, inputs, stream, barrier, pending) if (args.cfg2_sine_steps > 0 and world == 1) else None
     cfg1 = run_cfg1(args, homg, stream, barrier, pending) if (args.cfg1_steps > 0 and world == 1) else None
     cfg3 = run_cfg3(args, homg, inputs, stream, barrier, pending) if (args.cfg3_steps > 0 and world == 1) else None
     cfg4 = run_cfg4(args, homg, stream, barrier, pending) if (args.cfg4_steps > 0 and world == 1) else None
@@ -749,16 +933,24 @@ def run(args):
     common = {"kernel": kname, "launch_us": per_launch_s * 1e6, "launches": launches,
               "algorithmic_flops_per_launch": ops, "algorithmic_bytes_per_launch": bts, "traffic": traffic,
               "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + traffic_src if traffic else None}
-    if args.precision == "fp64":
-        # FP64 pipe bound on GB300: 5 FP64 instructions per node against 0.625e12 instructions/s
-        roofline = dict(common, bound="alu", achieved=alu_achieved, peak=FP64_PEAK_OPS / 1e12, unit="TFP64op/s",
-                        frac=alu_achieved / (FP64_PEAK_OPS / 1e12),
-                        peak_source="nominal FP64 rate (1.25 TFLOP/s = 0.625e12 FP64 instr/s)",
-                        hbm_achieved_gbs=hbm_achieved, hbm_peak_gbs=hbm_peak, hbm_frac=hbm_achieved / hbm_peak,
-                        hbm_peak_source=peak_src)
-    else:
-        roofline = dict(common, bound="hbm", achieved=hbm_achieved, peak=hbm_peak, unit="GB/s",
-                        frac=hbm_achieved / hbm_peak, peak_source=peak_src)
+    # The roofline is the HBM one (algorithmic bytes per launch / launch time / measured copy
+    # bandwidth). An FP64 sweep is bound on GB300 by the FP64 pipe instead (5 FP64 instructions per
+    # 24 bytes): its ALU fraction, against the issue rate measured in this run, is carried beside it.
+    roofline = dict(common, bound="hbm", achieved=hbm_achieved, peak=hbm_peak, unit="GB/s",
+                    frac=hbm_achieved / hbm_peak, peak_source=peak_src + " (MEASURED_PEAKS.json hbm_gbs)")
+    if fp64_peak:
+        p_meas = fp64_peak["peak_tinstr_per_s"]
+        instr_unit = "T FP64 instr/s" if args.precision == "fp64" else "T FP32 instr/s"
+        roofline["alu"] = {"binding": args.precision == "fp64", "achieved": alu_achieved, "unit": instr_unit,
+                           "instructions_per_launch": ops}
+        if args.precision == "fp64":
+            roofline["alu"].update(peak=p_meas, frac=alu_achieved / p_meas,
+                                   peak_source="measured in this run: homg_fp64_issue_probe, mean of 20 back-to-back "
+                                               "launches (FMA %.3f, ADD %.3f T instr/s; SM clock median %s MHz)" % (
+                                                   fp64_peak["fma"]["mean_tinstr_per_s"],
+                                                   fp64_peak["add"]["mean_tinstr_per_s"],
+                                                   fp64_peak["clocks"].get("sm_mhz")),
+                                   nominal_peak=FP64_NOMINAL_OPS / 1e12, frac_of_nominal=alu_achieved / (FP64_NOMINAL_OPS / 1e12))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -778,8 +970,12 @@ def run(args):
         "time_split_ms_per_step": {k: sum(s[k] for s in stats) / len(stats)
                                    for k in ("coarse_ms", "fine_ms", "residual_ms", "setup_ms", "solve_ms")},
     }
+    if fp64_peak:
+        line["fp64_issue_probe"] = fp64_peak
     if wg:
         line["wholegrid"] = wg
+    if cfg2s:
+        line["cfg2_manufactured"] = cfg2s
     if mixed:
         line["mixed_precision"] = mixed
     if vcyc:
@@ -795,8 +991,10 @@ def run(args):
     if pow2:
         line["pow2_grid"] = pow2
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_cpu_baseline(f_np, stats[-1]["cycles"])
+        line["cpu_baseline"] = oracle_cpu_baseline(f_np, full=args.cpu_baseline == "full")
         cpu_leg(pending)
+    # last key: a compact digest of every leg, so that the end of the printed line carries them all
+    line["legs"] = legs_digest(line)
     solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -818,6 +1016,11 @@ def main():
     p.add_argument("--launch", default="graph", choices=["graph", "stream"],
                    help="stream: enqueue kernels directly (for profilers that cannot see inside conditional graphs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-baseline", default="full", choices=["full", "cycle"],
+                   help="full: time the oracle's complete 4097^2 solve (about 2 minutes on one core); cycle: one cycle, scaled")
+    p.add_argument("--no-fp64-probe", dest="fp64_probe", action="store_false")
+    p.add_argument("--cfg2-sine-steps", type=int, default=2,
+                   help="timed solves per cycle type of the 4097^2 manufactured right-hand side (0: skip)")
     p.add_argument("--mixed-steps", type=int, default=3, help="timed solves per mixed-precision variant (0: skip)")
     p.add_argument("--cfg3-steps", type=int, default=2, help="timed 513^3 solves per precision and RHS (0: skip)")
     p.add_argument("--vcycle-steps", type=int, default=3, help="timed V(2,2) comparator solves (0: skip)")

@@ -289,6 +289,23 @@ int homg_batch_get_stats(homg_batch_handle b, homg_batch_stats* out);
 /* Release every resource of b (no-op for NULL). */
 void homg_batch_destroy(homg_batch_handle b);
 
+/* Threads per block of homg_fp64_issue_probe. */
+#define HOMG_PROBE_THREADS 256
+
+/* Measurement service (the paper has no counterpart): the GPU's FP64 instruction issue rate, the
+ * ceiling of this library's FP64 stencil kernels on GB300, whose FP64 pipe is far narrower than its
+ * DRAM (a level-0 sweep issues 5 FP64 instructions per 24 bytes). Enqueues one kernel of `blocks`
+ * blocks of HOMG_PROBE_THREADS threads on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * every thread runs 8 independent chains of `iters` dependent FP64 instructions, x <- x * a + b
+ * (op 0, fused multiply-add) or x <- x + b (op 1, addition), and stores the sum of its chains at
+ * sink[block * HOMG_PROBE_THREADS + thread] (caller-owned device array of at least
+ * blocks * HOMG_PROBE_THREADS doubles). *instructions_out (host) receives the FP64 instructions the
+ * launch executes, blocks * HOMG_PROBE_THREADS * iters * 8 (plus 8 per thread for the sums). The
+ * caller times the launch (CUDA events on `stream`); the call does not synchronise. HOMG_EINVAL
+ * for op outside {0, 1}, blocks or iters < 1, or a null pointer; HOMG_ECUDA if the launch fails
+ * (message in homg_last_error(NULL)). */
+int homg_fp64_issue_probe(int op, int blocks, int iters, double* sink, void* stream, double* instructions_out);
+
 /* Capacity of the static scratch used by homg_residual_norm_noalloc: one partial sum per thread
  * block of the residual kernel, at most this many (2-D grids up to 8193^2, 3-D up to 513^3). */
 #define HOMG_NOALLOC_MAX_BLOCKS 65536

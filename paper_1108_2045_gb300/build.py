@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libhomg.so")
-SOURCES = ["homg_kernels.cu", "homg_api.cu", "homg_noalloc.cu", "homg_net.cu"]
+SOURCES = ["homg_kernels.cu", "homg_api.cu", "homg_noalloc.cu", "homg_net.cu", "homg_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 

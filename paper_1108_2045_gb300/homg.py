@@ -40,6 +40,7 @@ EXPORTS = [
     "homg_destroy",
     "homg_residual_norm_noalloc",
     "homg_check_conversions",
+    "homg_fp64_issue_probe",
     "homg_batch_create",
     "homg_batch_set_stream",
     "homg_batch_solve",
@@ -160,6 +161,7 @@ def load(path=LIB_PATH):
     lib.homg_last_error.argtypes = [vp]
     lib.homg_last_error.restype = ctypes.c_char_p
     lib.homg_residual_norm_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), vp, vp, dp, vp]
+    lib.homg_fp64_issue_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, dp]
     lib.homg_destroy.argtypes = [vp]
     lib.homg_destroy.restype = None
     vpp = ctypes.POINTER(ctypes.c_void_p)
@@ -395,6 +397,22 @@ def homg_residual_norm_noalloc(f, u, stream=None):
     with torch.cuda.device(f.device):
         _check(load().homg_residual_norm_noalloc(ndim, dims, fp, up, ctypes.byref(rr), ctypes.c_void_p(raw)), None)
     return rr.value
+
+
+HOMG_PROBE_THREADS = 256
+
+
+def homg_fp64_issue_probe(op, blocks, iters, sink, stream=None):
+    """Enqueue the FP64 issue-rate probe kernel (op 0: fused multiply-adds, op 1: additions) on
+    `stream`; sink is a float64 CUDA tensor of at least blocks * HOMG_PROBE_THREADS elements.
+    Returns the FP64 instructions the launch executes (time it with CUDA events on `stream`)."""
+    if sink.numel() < blocks * HOMG_PROBE_THREADS:
+        raise TypeError("sink must hold blocks * %d doubles" % HOMG_PROBE_THREADS)
+    raw = getattr(stream, "cuda_stream", stream) or 0
+    instr = ctypes.c_double(0.0)
+    _check(load().homg_fp64_issue_probe(op, blocks, iters, _devptr(sink, "sink"), ctypes.c_void_p(raw),
+                                        ctypes.byref(instr)), None)
+    return instr.value
 
 
 def homg_check_conversions(d_in, f_in):

@@ -27,7 +27,7 @@ def homg():
 def declared_functions():
     src = "\n".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(homg_[a-z_]+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(homg_[a-z0-9_]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
