@@ -133,3 +133,42 @@ def test_full_uneven_batch_sampled_against_oracle(homg):
         ref, st1, cyc1, rr1 = single(homg, fs_np[i], 1e-10, 40, "fp32")
         assert (st1, cyc1, rr1) == (status[i], cycles[i], relres[i])
         np.testing.assert_array_equal(us[i].cpu().numpy(), ref)
+
+
+def _rel(a, b):
+    """Larger of the relative 2-norm error and the worst node's error against max |b|."""
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+BATCH_ITERATE_TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 5e-2}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_batch_iterates_match_oracle(homg, precision):
+    """The iterates of a batch after one and two cycles against the oracle's own solve of each
+    problem (FP64 cycles: oracle.solve; binary32 / bfloat16 cycles: oracle.solve_mixed), one problem
+    of every side class 65..1025 of the benchmark batch plus repeats, so that every group of the
+    batched launches is checked, not only the batch against the GPU's single solves. Tolerances are
+    those of the single-problem parity tests."""
+    import torch
+
+    import oracle
+
+    oracle.build()
+    ks = [6, 7, 8, 9, 10, 7, 6]
+    fs_np = [inputs.normal_rhs(2 ** k, 2, seed=40 + i) for i, k in enumerate(ks)]
+    fs = [torch.from_numpy(f).cuda() for f in fs_np]
+    with homg.BatchSolver([2 ** k + 1 for k in ks], precision=precision) as b:
+        for cycles in (1, 2):
+            us = [torch.zeros_like(f) for f in fs]
+            rc, status, cyc, relres, _ = b.solve(fs, us, tol=0.0, max_cycles=cycles)
+            assert rc == homg.HOMG_NOT_CONVERGED and cyc == [cycles] * len(ks)
+            for p, (k, f_np) in enumerate(zip(ks, fs_np)):
+                if precision == "fp64":
+                    ref, _, _, rhist = oracle.solve(f_np, k, tol=0.0, max_cycles=cycles)
+                else:
+                    ref, _, _, rhist = oracle.solve_mixed(f_np, k, precision, tol=0.0, max_cycles=cycles)
+                err = _rel(us[p].cpu().numpy(), ref)
+                assert err <= BATCH_ITERATE_TOL[precision], (precision, cycles, k, err)
+                if precision == "fp64":
+                    assert abs(relres[p] - rhist[-1]) <= 1e-9 * rhist[-1], (cycles, k, relres[p], rhist[-1])

@@ -1,6 +1,7 @@
 """GPU path vs the CPU oracle, element by element on the same seeded inputs (GB300 only).
 
-Bar (floating point): after every cycle, ||u_gpu - u_oracle||_2 / ||u_oracle||_2 <= 1e-12. The
+Bar (floating point): after every cycle, ||u_gpu - u_oracle||_2 / ||u_oracle||_2 <= 1e-12 and
+max |u_gpu - u_oracle| / max |u_oracle| <= 1e-12 (every node, not only the norm). The
 whole-grid form with strict_fp evaluates every formula in the oracle's order and must reproduce its
 iterates bit for bit. Grid sides are 2^K + 1, so every size has a ragged tail against the kernels'
 32 x 8 tiles.
@@ -45,8 +46,12 @@ def gpu_solve(homg, f_np, levels, u0=None, tol=0.0, max_cycles=1, **kw):
 
 
 def rel(a, b):
+    """The larger of two relative errors of a against b: in the 2-norm over the grid, and at the
+    worst single node against the largest |b| (so no single node can hide in a large grid's norm)."""
     nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+    mb = np.max(np.abs(b)) if b.size else 0.0
+    return max(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0),
+               (np.max(np.abs(a - b)) if b.size else 0.0) / (mb if mb > 0 else 1.0))
 
 
 def oracle_kw(kw):

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from oracle import oracle as oracle_impl
 
+import test_oracle_lp_pin as lppins
 import test_oracle_pins as pins
 import test_oracle_pow2 as p2pins
 import test_oracle_vc as vcpins
@@ -56,6 +57,18 @@ MUTATIONS = {
     "pow2_interp_from_one_quadrant": ("v = v + pow2_interp(dprev, N, mprev, pow2_qbit(N, x) | (pow2_qbit(N, y) << 1), x, y);",
                                       "v = v + pow2_interp(dprev, N, mprev, 0, x, y);"),
     "pow2_relax_stride": ("lap = lap - e_at_pow2(e_old, N, x - l, y);", "lap = lap - e_at_pow2(e_old, N, x - 1, y);"),
+    "lp_variation_not_stored_rounded": ("d_new[q] = store_lp(delta, prec);\n                    v = v + delta;",
+                                        "d_new[q] = delta;\n                    v = v + delta;"),
+    "lp_update_uses_stored_variation": ("d_new[q] = store_lp(delta, prec);\n                    v = v + delta;",
+                                        "d_new[q] = store_lp(delta, prec);\n                    v = v + d_new[q];"),
+    "lp_iterate_not_stored_rounded": ("e_new[p] = store_lp(v, prec);\n            }\n}\n\n/* One low-precision HOMG cycle",
+                                      "e_new[p] = v;\n            }\n}\n\n/* One low-precision HOMG cycle"),
+    "lp_restriction_not_stored_rounded": ("Fc[q] = store_lp((4.0f * c + 2.0f * edges + corners) / 16.0f, prec);",
+                                          "Fc[q] = (4.0f * c + 2.0f * edges + corners) / 16.0f;"),
+    "lp_source_rounded_twice": ("F[0][p] = store_lp((float)F0[p], prec);\n    for (int m = 1; m < levels; ++m) homg_oracle_restrict_lp(ndim",
+                                "F[0][p] = store_lp((float)(double)bf16_round((float)F0[p]), prec);\n    for (int m = 1; m < levels; ++m) homg_oracle_restrict_lp(ndim"),
+    "lp_interp_weights_in_double": ("return ((wx0 * wy0) * d00 + (wx1 * wy0) * d10) + ((wx0 * wy1) * d01 + (wx1 * wy1) * d11);\n}\n\nstatic float interp3f",
+                                    "return (float)(((double)(wx0 * wy0) * d00 + (double)(wx1 * wy0) * d10) + ((double)(wx0 * wy1) * d01 + (double)(wx1 * wy1) * d11));\n}\n\nstatic float interp3f"),
     "norm_not_squared": ("double x = v[j * (n + 1) + i]; s += x * x;", "double x = v[j * (n + 1) + i]; s += fabs(x);"),
 }
 
@@ -92,6 +105,9 @@ def run_pins():
         ("p2_dense", lambda: p2pins.test_solution_matches_dense_direct_solve(16)),
         ("p2_rate", lambda: p2pins.test_contraction_is_resolution_independent((5, 6, 7))),
         ("p2_symmetry", lambda: p2pins.test_mirror_symmetry()),
+        ("lp_fp32", lambda: lppins.test_low_precision_cycle_bit_exact("fp32", 4, 4, [3, 1, 2, 0, 1, 0, 0])),
+        ("lp_bf16", lambda: lppins.test_low_precision_cycle_bit_exact("bf16", 4, 4, [3, 1, 2, 0, 1, 0, 0])),
+        ("lp_bf16_mfmg", lambda: lppins.test_low_precision_cycle_bit_exact("bf16", 3, 3, None)),
     ]
     failed = []
     for name, fn in checks:
