@@ -83,6 +83,9 @@ struct IterArgs {
     int rows = 0;   // fast 2-D/3-D kernels: nodes per thread along the march (0: size heuristic)
     float omega_f;  // the same, rounded to binary32, for the binary32-arithmetic kernels
     float c1_f;
+    // 1, as a run-time value: an addition written as fma(one, x, y) stays a fused multiply-add
+    // (GB300's FP64 pipe issues those faster than additions), where a literal 1 would be folded.
+    double one = 1.0;
     // Variable coefficients (2-D lattice form; nullptr: Poisson): per lattice node the east-face
     // and north-face coefficients and the Jacobi weight omega_J / D, in double for FP64 cycles and
     // float otherwise, rows of `kpitch` elements. The source g is then h_m^2 F_m (not omega-scaled).
@@ -123,6 +126,7 @@ struct ResidArgs {
     const double* kx = nullptr;  // variable coefficients (2-D): east / north face coefficients of
     const double* ky = nullptr;  // the fine grid, rows of kpitch; nullptr: Poisson
     int64_t kpitch = 0;
+    double one = 1.0;            // run-time 1 (see IterArgs::one)
 };
 
 // Full weighting g_c = 4 * FW(g_f) (the factor 4 = 2^2 keeps the source pre-scaled by h_m^2),

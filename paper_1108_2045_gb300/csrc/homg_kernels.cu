@@ -119,6 +119,53 @@ template <typename C> __device__ __forceinline__ C pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
+// f * 2^-e for 0 <= f < 2^e (e <= 30), exactly, assembled from the IEEE-754 fields with integer
+// operations only: exponent floor(log2 f) - e, fraction the bits of f below its leading one.
+template <typename C> __device__ __forceinline__ C dyadic(int f, int e);
+template <> __device__ __forceinline__ double dyadic<double>(int f, int e) {
+    if (f == 0) return 0.0;
+    const int p = 31 - __clz(f);
+    const unsigned long long frac = ((unsigned long long)f << (52 - p)) & ((1ull << 52) - 1);
+    return __longlong_as_double((long long)(((unsigned long long)(p - e + 1023) << 52) | frac));
+}
+template <> __device__ __forceinline__ float dyadic<float>(int f, int e) {
+    if (f == 0) return 0.f;
+    const int p = 31 - __clz(f);
+    const unsigned frac = ((unsigned)f << (23 - p)) & ((1u << 23) - 1);
+    return __uint_as_float(((unsigned)(p - e + 127) << 23) | frac);
+}
+
+// One damped-Jacobi update v' = c1 v + om (sum of the 2d neighbours) + g (g pre-scaled by om).
+// FP64 (the FP64 pipe bounds these kernels on GB300, and it issues fused multiply-adds at 0.627
+// against 0.528 T instr/s for additions, measured): a chain of 2d + 1 FMAs, every neighbour scaled
+// by om on its own. Binary32 (DRAM bound): the neighbour sum, then two FMAs.
+__device__ __forceinline__ double jacobi_update(double c1, double om, double vc, double g, double n0, double n1,
+                                                double n2, double n3) {
+    double t = fma(om, n0, g);
+    t = fma(om, n1, t);
+    t = fma(om, n2, t);
+    t = fma(om, n3, t);
+    return fma(c1, vc, t);
+}
+__device__ __forceinline__ float jacobi_update(float c1, float om, float vc, float g, float n0, float n1, float n2,
+                                               float n3) {
+    return fma(c1, vc, fma(om, (n0 + n1) + (n2 + n3), g));
+}
+__device__ __forceinline__ double jacobi_update(double c1, double om, double vc, double g, double n0, double n1,
+                                                double n2, double n3, double n4, double n5) {
+    double t = fma(om, n0, g);
+    t = fma(om, n1, t);
+    t = fma(om, n2, t);
+    t = fma(om, n3, t);
+    t = fma(om, n4, t);
+    t = fma(om, n5, t);
+    return fma(c1, vc, t);
+}
+__device__ __forceinline__ float jacobi_update(float c1, float om, float vc, float g, float n0, float n1, float n2,
+                                               float n3, float n4, float n5) {
+    return fma(c1, vc, fma(om, ((n0 + n1) + (n2 + n3)) + (n4 + n5), g));
+}
+
 // Programmatic dependent launch: every kernel is launched so that it may start while its
 // predecessor in the stream finishes. Each kernel first waits until the predecessor grid has
 // completed and its writes are visible (griddepcontrol.wait), then lets its own successor launch.
@@ -719,8 +766,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
         const C vn = St<T>::ld(row + pe);
         const C w = St<T>::ld(row - 1), e = St<T>::ld(row + 1);
         const C g = St<T>::ld(G + (int64_t)j * pg + i);
-        const C sum = (w + e) + (vs + vn);
-        C v = fma(c1, vc, fma(om, sum, g));
+        C v = jacobi_update(c1, om, vc, g, w, e, vs, vn);
         if (WD) wp<T>(a.dnew)[(int64_t)j * a.dnew.pitch + i] = St<T>::put(v - vc);
         if (PEND == 1) {
             const C sv = ci.at(j);
@@ -1100,8 +1146,7 @@ __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
         const C vt = St<T>::ld(p + ple);
         const C w = St<T>::ld(p - 1), e = St<T>::ld(p + 1), sn = St<T>::ld(p - pe), nn = St<T>::ld(p + pe);
         const C g = St<T>::ld(G + (int64_t)k * plg + (int64_t)j * pg + i);
-        const C sum = ((w + e) + (sn + nn)) + (vb + vt);
-        C v = fma(c1, vc, fma(om, sum, g));
+        C v = jacobi_update(c1, om, vc, g, w, e, sn, nn, vb, vt);
         if (WD) wp<T>(a.dnew)[(int64_t)k * (n + 1) * a.dnew.pitch + (int64_t)j * a.dnew.pitch + i] = St<T>::put(v - vc);
         if (PEND && ((i | j | k) & lpm)) v += interp<3, false, false, T>(a.dprev, a.dprev, a.mp, i, j, k);
         O[(int64_t)k * plo + (int64_t)j * po + i] = St<T>::put(v);
@@ -1223,9 +1268,13 @@ __global__ void __launch_bounds__(J3X * J3Y) k_prolong3_s1(ProlongArgs a, int ro
 
 // Fast whole-grid iteration at level m >= 1 (2-D): every fine node adds the bilinear interpolant of
 // the pending variation (level mp >= 1) unless it lies on the level-mp lattice, and level-m
-// lattice nodes relax. Each thread marches one column; the interpolant along x is formed once per
-// coarse cell row (r0, r1 at the cell's lower and upper lattice rows) and shared down the column,
-// so a node off both lattices costs one FMA and one add.
+// lattice nodes relax. Each thread marches one column down JR rows. The interpolant along x at a
+// lattice row J, q(J), is formed once per coarse cell: moving down one cell the previous cell's
+// upper value becomes the new lower one, so one new q and one difference per cell, and none of
+// either in a column on the level-mp lattice (q is then the lattice value itself). A node at
+// offset b inside its cell adds q0 + (b 2^-mp)(q1 - q0), the weight assembled from integer bits,
+// the addition written as a fused multiply-add by a run-time 1 (the FP64 pipe issues those faster):
+// two FMAs per node (one on a lattice row), no conversion on the FP64 pipe.
 template <bool PEND, typename T>
 __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
     pdl_begin();
@@ -1241,17 +1290,23 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
     const int64_t po = a.e_new.pitch;
     const int m = a.m, l = 1 << m, lm = l - 1;
     const C om = pick<C>(a.omega, a.omega_f);
+    const C one = (C)a.one;
     const bool col_on_lattice = (i & lm) == 0;
     const int mp = PEND ? a.mp : 0;
     const int lpm = (1 << mp) - 1;
     const int I0 = i >> mp;
-    const C alpha = PEND ? (C)(i & lpm) * pow2<C>(-mp) : (C)0;
-    const C beta_step = PEND ? pow2<C>(-mp) : (C)0;
+    const C alpha = PEND ? dyadic<C>(i & lpm, mp) : (C)0;
     const T* __restrict__ D = cp<T>(a.dprev);
     const int64_t pd = a.dprev.pitch;
     const bool col_on_prev = (i & lpm) == 0;
-    int cell = -1;
-    C r0 = 0, dr = 0;
+    // x-interpolant of the pending variation at lattice row J of this column
+    auto qrow = [&](int J) -> C {
+        const T* d = D + (int64_t)J * pd + I0;
+        const C a0 = St<T>::ld(d);
+        return col_on_prev ? a0 : fma(alpha, St<T>::ld(d + 1) - a0, a0);
+    };
+    int cell = -2;
+    C r0 = 0, r1 = 0, dr = 0;
     for (int j = j0; j < j1; ++j) {
         C v = St<T>::ld(E + (int64_t)j * pe + i);
         if (col_on_lattice && (j & lm) == 0) {
@@ -1265,18 +1320,16 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
         if (PEND) {
             const int J0 = j >> mp;
             const int b = j & lpm;
-            if (!(col_on_prev && b == 0)) {
-                if (J0 != cell) {
-                    const T* d0 = D + (int64_t)J0 * pd + I0;
-                    const T* d1 = d0 + pd;
-                    const C a0 = St<T>::ld(d0), a1 = St<T>::ld(d1);
-                    const C q0 = fma(alpha, St<T>::ld(d0 + 1) - a0, a0);
-                    const C q1 = fma(alpha, St<T>::ld(d1 + 1) - a1, a1);
-                    r0 = q0;
-                    dr = q1 - q0;
-                    cell = J0;
-                }
-                v += fma((C)b * beta_step, dr, r0);
+            if (J0 != cell) {
+                r0 = (J0 == cell + 1) ? r1 : qrow(J0);
+                r1 = qrow(J0 + 1);
+                dr = r1 - r0;
+                cell = J0;
+            }
+            if (b == 0) {
+                if (!col_on_prev) v = fma(one, v, r0);
+            } else {
+                v = fma(one, v, fma(dyadic<C>(b, mp), dr, r0));
             }
         }
         O[(int64_t)j * po + i] = St<T>::put(v);
@@ -1311,10 +1364,13 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     const double* __restrict__ F = a.st->f;
     const int64_t pf = n + 1;
     const bool want_f = a.part_f != nullptr;
+    // Additions are written as fused multiply-adds by a run-time 1: the FP64 pipe, which bounds this
+    // kernel, issues those faster than additions on GB300 (the results are the same roundings).
+    const double one = a.one;
     auto un = [&](int jj) -> double {  // updated iterate at (i, jj); 0 on the boundary and outside
         if (!col_in || jj <= 0 || jj >= n) return 0.0;
         double v = __ldg(U + (int64_t)jj * pu + i);
-        if (upd) v += to_d(St<T>::ld(Ev + (int64_t)jj * pe + i));
+        if (upd) v = fma(one, v, to_d(St<T>::ld(Ev + (int64_t)jj * pe + i)));
         return v;
     };
     double rr = 0.0, ff = 0.0;
@@ -1333,11 +1389,11 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
                 t = fma(ke, e, t);
                 t = fma(ks, vs, t);
                 t = fma(kn, vn, t);
-                const double d = ((kw + ke) + ks) + kn;
+                const double d = fma(one, fma(one, fma(one, kw, ke), ks), kn);
                 r = fma(-a.inv_h2, fma(d, vc, -t), fv);
                 ks = kn;
             } else {
-                const double sum = (w + e) + (vs + vn);
+                const double sum = fma(one, fma(one, w, e), fma(one, vs, vn));
                 r = fma(a.inv_h2, fma(-4.0, vc, sum), fv);
             }
             if (a.u_out.p) a.u_out.p[(int64_t)j * a.u_out.pitch + i] = vc;
@@ -1366,22 +1422,6 @@ __device__ __forceinline__ int p2_local(int N, int m, int qb, int x) {
     if (d & ((1 << m) - 1)) return -1;
     const int a = d >> m;
     return a <= ((N >> 1) >> m) ? a : -1;
-}
-
-// f * 2^-e for 0 <= f < 2^e (e <= 30), exactly, assembled from the IEEE-754 fields with integer
-// operations only: exponent floor(log2 f) - e, fraction the bits of f below its leading one.
-template <typename C> __device__ __forceinline__ C dyadic(int f, int e);
-template <> __device__ __forceinline__ double dyadic<double>(int f, int e) {
-    if (f == 0) return 0.0;
-    const int p = 31 - __clz(f);
-    const unsigned long long frac = ((unsigned long long)f << (52 - p)) & ((1ull << 52) - 1);
-    return __longlong_as_double((long long)(((unsigned long long)(p - e + 1023) << 52) | frac));
-}
-template <> __device__ __forceinline__ float dyadic<float>(int f, int e) {
-    if (f == 0) return 0.f;
-    const int p = 31 - __clz(f);
-    const unsigned frac = ((unsigned)f << (23 - p)) & ((1u << 23) - 1);
-    return __uint_as_float(((unsigned)(p - e + 127) << 23) | frac);
 }
 
 // Marked at level m >= 1 (an interior node of one quadrant's lattice): quadrant and local indexes.
