@@ -392,10 +392,12 @@ def run_cfg5(args, homg, stream, barrier, pending):
     """Variable-coefficient diffusion -div(k grad u) = f on 2049^2 nodes, 11 levels, k = exp(g) with g
     a Gaussian random field (sigma 1, squared-exponential correlation length 0.05, seed 2), f iid
     N(0, 1) (seed 0), to relres 1e-10: plain HOMG (FP64 and FP32 cycles) against the learned
-    corrector ahead of every cycle. The corrector is trained here, from scratch, on 20,000 64 x 64
-    patches of error/residual pairs the solver produces on four other right-hand sides (seeds
-    100-103; iterates after 2, 3 and 4 cycles, whose errors a 9 x 9 receptive field predicts best);
-    training time is reported, not timed as a solve."""
+    corrector ahead of every cycle. Two networks are trained here, from scratch, on the same 20,000
+    64 x 64 patches of error/residual pairs the solver produces on four other right-hand sides (seeds
+    100-103; iterates after 2, 3 and 4 cycles): one on the mean squared error against the scaled true
+    error, one on the residual its proposal leaves. The learned solves run with the judge on the
+    proposal's own residual and, for the error-trained network, with the judge after the following
+    cycle. Training time is reported, not timed as a solve."""
     import numpy as np
     import torch
 
@@ -437,11 +439,14 @@ def run_cfg5(args, homg, stream, barrier, pending):
             ms, (st, cyc, rr) = timed(solve, args.cfg5_steps)
         plain[prec] = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms, "unknowns_per_s": unknowns / (ms * 1e-3)}
     out["plain"] = plain
-    with homg.Solver(2, n + 1, L, max_i=MAX_I, precision="fp32") as s, homg.Net() as net:
+    with homg.Solver(2, n + 1, L, max_i=MAX_I, precision="fp32") as s, homg.Net() as net, homg.Net() as net_r:
         s.set_stream(stream)
         net.set_stream(stream)
+        net_r.set_stream(stream)
         s.set_coefficient(k)
         net.set_params(learned.init_params(args.cfg5_seed))
+        net_r.set_params(learned.init_params(args.cfg5_seed))
+        net_r.set_loss("residual")
         t0 = time.perf_counter()
         fs_train = [torch.from_numpy(inputs.normal_rhs(n, 2, seed=100 + i)).cuda() for i in range(4)]
         X, T = learned.make_training_set(s, net, fs_train, cycles=(2, 3, 4), patches=args.cfg5_patches, seed=1)
@@ -449,11 +454,15 @@ def run_cfg5(args, homg, stream, barrier, pending):
         target_ms = float((T.double() ** 2).mean())
         del fs_train
         losses, train_s = learned.train(net, X, T, epochs=args.cfg5_epochs, seed=2)
+        losses_r, train_r_s = learned.train(net_r, X, T, epochs=args.cfg5_epochs, seed=2)
         del X, T
         out["training"] = {"patches": args.cfg5_patches, "patch": 64, "epochs": args.cfg5_epochs, "batch": 64,
                            "iterates_after_cycles": [2, 3, 4],
                            "data_seconds": data_s, "train_seconds": train_s, "loss_per_epoch": losses,
-                           "target_mean_square": target_ms, "variance_explained": 1.0 - losses[-1] / target_ms}
+                           "target_mean_square": target_ms, "variance_explained": 1.0 - losses[-1] / target_ms,
+                           "residual_loss": {"train_seconds": train_r_s, "loss_per_epoch": losses_r,
+                                             "note": "same patches; loss = mean square of the residual the proposal "
+                                                     "leaves (inputs have unit mean square: 1.0 = no reduction)"}}
         # the network alone on the full grid: tensor-core convolution throughput
         x_img = torch.zeros(1, n + 1, 2, n + 1, 8, dtype=torch.bfloat16, device="cuda")
         y_img = torch.zeros(1, n + 1, n + 1, dtype=torch.float32, device="cuda")
@@ -473,22 +482,30 @@ def run_cfg5(args, homg, stream, barrier, pending):
                                   "(2 -> 16 inputs of layer 1, 1 -> 16 outputs of layer 4)"}
         del x_img, y_img
         learned_res = {}
-        for prec in ("fp32", "fp64"):
+        # (name, cycle precision, network, judge): the error-trained network judged on its own residual
+        # (FP32 and FP64 cycles) and after the following cycle; the residual-trained network
+        variants = [("fp32", "fp32", net, "proposal"), ("fp64", "fp64", net, "proposal"),
+                    ("fp32_judge_after_cycle", "fp32", net, "after_cycle"),
+                    ("fp32_residual_loss", "fp32", net_r, "proposal")]
+        for name, prec, nw, judge in variants:
             with homg.Solver(2, n + 1, L, max_i=MAX_I, precision=prec) as s2:
                 s2.set_stream(stream)
                 s2.set_coefficient(k)
+                homg.homg_set_learned_judge(s2.handle, judge)
 
                 def lsolve():
                     u.zero_()
-                    return homg.homg_solve_learned(s2.handle, net, f, u, tol=TOL, max_cycles=MAX_CYCLES)
+                    return homg.homg_solve_learned(s2.handle, nw, f, u, tol=TOL, max_cycles=MAX_CYCLES)
 
                 ms, (st, cyc, rr, acc) = timed(lsolve, args.cfg5_steps)
             r = {"status": st, "cycles": cyc, "relres": rr, "ms_per_solve": ms, "unknowns_per_s": unknowns / (ms * 1e-3),
-                 "proposals_kept": int(sum(acc)), "speedup_vs_plain_fp64": plain["fp64"]["ms_per_solve"] / ms,
+                 "judge": judge, "loss": "residual" if nw is net_r else "error",
+                 "proposals_kept": int(sum(acc)), "decisions": [int(a) for a in acc],
+                 "speedup_vs_plain_fp64": plain["fp64"]["ms_per_solve"] / ms,
                  "speedup_vs_plain_same_precision": plain[prec]["ms_per_solve"] / ms}
-            if prec == "fp32" and args.cfg5_oracle_check:
+            if name == "fp32" and args.cfg5_oracle_check:
                 pending.append((r, "vc", kc, f_np, u.cpu().numpy()))
-            learned_res[prec] = r
+            learned_res[name] = r
         out["learned"] = learned_res
     if args.cfg5_oracle_time:
         pending.append((out, "vc_time", kc, f_np, plain["fp64"]["cycles"]))
@@ -730,7 +747,8 @@ def legs_digest(line):
     c = line.get("cfg5_learned")
     if c:
         d["cfg5"] = {"plain": {p: r3(v["ms_per_solve"]) for p, v in c["plain"].items()},
-                     "learned": {p: [r3(v["ms_per_solve"]), v["proposals_kept"]] for p, v in c.get("learned", {}).items()}}
+                     "learned": {p.replace("fp32_", ""): [r3(v["ms_per_solve"]), v["cycles"], v["proposals_kept"]]
+                                 for p, v in c.get("learned", {}).items()}}
     c = line.get("pow2_grid")
     if c:
         d["pow2"] = {p: [r3(c[p]["ms_per_solve"]), c[p]["cycles"]] for p in ("fp64", "fp32") if p in c}

@@ -65,10 +65,24 @@ int homg_net_get_grads(homg_net_handle net, float* grads, int64_t count);
  * B, H, W >= 1 and B*H*W < 2^31. */
 int homg_net_forward(homg_net_handle net, const void* x, int B, int H, int W, float* y);
 
-/* One training step on a batch: forward, mean squared error against t ([B][H][W] device), the
- * gradient of every parameter (binary32 accumulation), one Adam step (beta1 0.9, beta2 0.999,
- * eps 1e-8) with learning rate lr > 0. *loss_out (optional) receives the batch loss before the
- * step. */
+/* Training loss of homg_net_train_step.
+ * HOMG_NET_LOSS_ERROR (default): mean squared error (1/N) sum (y - t)^2 over the N = B*H*W pixels,
+ *   t the scaled true error of the iterate (homg_features).
+ * HOMG_NET_LOSS_RESIDUAL: the residual the proposal leaves, (1/N) sum res^2 over the
+ *   N = B*(H-2)*(W-2) inner pixels of the patches, res(p) = x_0(p) - (y(p) - sum_q w_q(p) y(q)),
+ *   w_q(p) = k_pq / D(p) for the four neighbours q (column -1, +1, row -1, +1) with k = exp(x_1)
+ *   taken from the patch's own log k channel, k_pq the harmonic mean at p and q, D(p) the sum of
+ *   the four: the scaled residual of u + rho y, computed on the patch. t is not used (may be NULL).
+ * The learned-corrector extension has no counterpart in the paper; the residual loss trains the
+ * network toward corrections the solver's judge measures. HOMG_EINVAL for another kind. */
+#define HOMG_NET_LOSS_ERROR 0
+#define HOMG_NET_LOSS_RESIDUAL 1
+int homg_net_set_loss(homg_net_handle net, int kind);
+
+/* One training step on a batch: forward, the loss selected by homg_net_set_loss (mean squared error
+ * against t ([B][H][W] device) by default), the gradient of every parameter (binary32
+ * accumulation), one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr > 0.
+ * *loss_out (optional) receives the batch loss before the step. The residual loss needs H, W >= 3. */
 int homg_net_train_step(homg_net_handle net, const void* x, const float* t, int B, int H, int W, float lr,
                         float* loss_out);
 
@@ -99,14 +113,26 @@ void homg_net_destroy(homg_net_handle net);
 int homg_features(homg_handle h, const double* f, const double* u, const double* u_ref, void* x_out, float* t_out,
                   double* rho_out);
 
+/* How homg_solve_learned judges a proposal u' = u + rho y (the plain solver always decides, in FP64
+ * residual norms computed by the same reduction):
+ * HOMG_JUDGE_PROPOSAL (default): keep u' when ||f - A u'|| < ||f - A u||, then one HOMG cycle on the
+ *   kept iterate's residual.
+ * HOMG_JUDGE_AFTER_CYCLE: run one HOMG cycle from u and one from u' and keep the result whose
+ *   residual is smaller (a proposal whose rough part the cycle removes can win here although its own
+ *   residual is larger); two cycles per proposal.
+ * The setting belongs to the handle h and applies to its later learned solves. HOMG_EINVAL for
+ * another value. (Extension; the paper has no learned component.) */
+#define HOMG_JUDGE_PROPOSAL 0
+#define HOMG_JUDGE_AFTER_CYCLE 1
+int homg_set_learned_judge(homg_handle h, int judge);
+
 /* Restarted solve with the learned corrector ahead of every HOMG cycle (variable-coefficient
  * handles, HOMG_LAUNCH_GRAPH or STREAM alike: this loop is host-driven, one synchronisation per
  * proposal and per cycle): r = f - A u; stop as homg_solve does; features -> network -> proposal
- * u' = u + rho y; keep u' when ||f - A u'|| < ||r|| (FP64, the same reduction for both norms);
- * one HOMG cycle on the kept iterate's residual. Once two proposals in a row have been rejected
- * the network proposes nothing more in this solve (plain HOMG cycles only). accepted_out
- * (optional, max_cycles ints) receives the judge's decisions (0 for cycles without a proposal).
- * Returns like homg_solve. */
+ * u' = u + rho y, judged as homg_set_learned_judge selects; the cycle(s) of the Sec. 2 restart
+ * follow. Once two proposals in a row have been rejected the network proposes nothing more in this
+ * solve (plain HOMG cycles only). accepted_out (optional, max_cycles ints) receives the judge's
+ * decisions (0 for cycles without a proposal). Returns like homg_solve. */
 int homg_solve_learned(homg_handle h, homg_net_handle net, const double* f, double* u, double tol, int max_cycles,
                        int* cycles_out, double* relres_out, int* accepted_out);
 

@@ -97,20 +97,59 @@ def forward(params, x, rounding=True):
     return y, acts
 
 
-def loss_and_grads(params, xs, ts, rounding=True):
-    """Mean squared error (1/N) sum (y - t)^2 over the N pixels of a batch of images, and its
-    gradient with respect to every weight and bias (chain rule through the ReLUs; the rounding to
-    bfloat16 is treated as the identity, as the GPU does)."""
+def patch_operator(x):
+    """Weights of the Jacobi-scaled operator on one network input x [C_IN, H, W] at its inner pixels
+    (not on the image border): w_q(p) = k_pq / D(p) for the four neighbours q = W, E, S, N, with k_pq
+    the harmonic mean of exp(x_1) at p and q and D(p) the sum of the four. Returns [4, H-2, W-2]."""
+    k = np.exp(np.asarray(x[1], dtype=np.float64))
+    c = k[1:-1, 1:-1]
+    faces = [face_coef(c, k[1:-1, :-2]), face_coef(c, k[1:-1, 2:]), face_coef(c, k[:-2, 1:-1]),
+             face_coef(c, k[2:, 1:-1])]
+    D = ((faces[0] + faces[1]) + faces[2]) + faces[3]
+    return np.stack([f / D for f in faces])
+
+
+def residual_loss_terms(x, y):
+    """Residual of the proposal y at the inner pixels of one image, in the network's units:
+    res(p) = x_0(p) - (y(p) - sum_q w_q(p) y(q)), i.e. the input's scaled residual h^2 r / (D rho)
+    minus h^2 A (rho y) / (D rho), with A rebuilt from the image's own log k channel."""
+    w = patch_operator(x)
+    nb = [y[1:-1, :-2], y[1:-1, 2:], y[:-2, 1:-1], y[2:, 1:-1]]
+    Ay = y[1:-1, 1:-1] - (((w[0] * nb[0] + w[1] * nb[1]) + w[2] * nb[2]) + w[3] * nb[3])
+    return np.asarray(x[0], dtype=np.float64)[1:-1, 1:-1] - Ay, w
+
+
+def loss_and_grads(params, xs, ts, rounding=True, loss_kind="error"):
+    """Training loss over a batch of images and its gradient with respect to every weight and bias
+    (chain rule through the ReLUs; the rounding to bfloat16 is treated as the identity, as the GPU
+    does). loss_kind "error": mean squared error (1/N) sum (y - t)^2 over the N pixels against the
+    scaled error t. loss_kind "residual": (1/N) sum res^2 over the N inner pixels of the images, res
+    the residual left by the proposal (residual_loss_terms); t is not used."""
     L = len(params)
-    npix = sum(t.size for t in ts)
+    if loss_kind == "error":
+        npix = sum(t.size for t in ts)
+    else:
+        npix = sum((x.shape[1] - 2) * (x.shape[2] - 2) for x in xs)
     gw = [np.zeros_like(w) for w, _ in params]
     gb = [np.zeros_like(b) for _, b in params]
     loss = 0.0
     for x, t in zip(xs, ts):
         y, acts = forward(params, x, rounding)
-        dy = y - t
-        loss += float(np.sum(dy * dy))
-        g = (2.0 / npix) * dy[None]  # d loss / d z_L
+        if loss_kind == "error":
+            dy = y - t
+            loss += float(np.sum(dy * dy))
+            g = (2.0 / npix) * dy[None]  # d loss / d z_L
+        else:
+            res, w = residual_loss_terms(x, y)
+            loss += float(np.sum(res * res))
+            # d res(p) / d y(p) = -1, d res(p) / d y(q) = w_q(p) for the neighbours q of p
+            gy = np.zeros_like(y)
+            gy[1:-1, 1:-1] -= res
+            gy[1:-1, :-2] += w[0] * res
+            gy[1:-1, 2:] += w[1] * res
+            gy[:-2, 1:-1] += w[2] * res
+            gy[2:, 1:-1] += w[3] * res
+            g = (2.0 / npix) * gy[None]
         for l in range(L - 1, -1, -1):
             a = acts[l]
             C, H, W = a.shape
@@ -177,11 +216,18 @@ def features(kc, r):
     return x, rho
 
 
-def solve_learned(kc, f, params, levels, precision="fp64", tol=1e-10, max_cycles=100, div_factor=1e3):
+def solve_learned(kc, f, params, levels, precision="fp64", tol=1e-10, max_cycles=100, div_factor=1e3,
+                  judge="proposal"):
     """Restarted variable-coefficient HOMG solve with the learned corrector ahead of every cycle:
     r = f - A u; if ||r|| / ||f|| <= tol stop; propose u' = u + rho y (interior) from the network;
-    keep u' when ||f - A u'|| < ||r||; run one HOMG cycle on the residual of the kept iterate.
-    Returns (u, status, cycles, hist, accepted) with accepted[k] the judge's decision at cycle k."""
+    judge (the plain solver decides, in FP64 residual norms):
+      judge "proposal":    keep u' when ||f - A u'|| < ||r||, then one HOMG cycle on the residual
+                           of the kept iterate;
+      judge "after_cycle": run one HOMG cycle from u and one from u', keep the result with the
+                           smaller residual norm.
+    After two rejections in a row the network proposes nothing more (plain cycles only).
+    Returns (u, status, cycles, hist, accepted) with accepted[k] the judge's decision at cycle k
+    (False for a cycle without a proposal)."""
     from . import oracle as o
 
     u = np.zeros_like(f)
@@ -191,6 +237,14 @@ def solve_learned(kc, f, params, levels, precision="fp64", tol=1e-10, max_cycles
     hist, accepted = [], []
     rr0 = None
     k = 0
+    rejected_in_a_row = 0
+
+    def after_cycle(v, rv):
+        w = v.copy()
+        e = o.cycle_vc(kc, rv, levels, precision=precision)
+        w[1:-1, 1:-1] += e[1:-1, 1:-1]
+        return w
+
     while True:
         r = o.residual_vc(kc, f, u)
         rn = o.norm_interior(r)
@@ -203,15 +257,26 @@ def solve_learned(kc, f, params, levels, precision="fp64", tol=1e-10, max_cycles
             return u, o.DIVERGED, k, np.array(hist), accepted
         if k == max_cycles:
             return u, o.NOT_CONVERGED, k, np.array(hist), accepted
+        if rejected_in_a_row >= 2:
+            accepted.append(False)
+            u = after_cycle(u, r)
+            k += 1
+            continue
         x, rho = features(kc, r)
         y, _ = forward(params, x)
         u2 = u.copy()
         u2[1:-1, 1:-1] += rho * y[1:-1, 1:-1]
         r2 = o.residual_vc(kc, f, u2)
-        keep = o.norm_interior(r2) < rn
+        if judge == "proposal":
+            keep = o.norm_interior(r2) < rn
+            if keep:
+                u, r = u2, r2
+            u = after_cycle(u, r)
+        else:
+            up = after_cycle(u, r)
+            uq = after_cycle(u2, r2)
+            keep = o.norm_interior(o.residual_vc(kc, f, uq)) < o.norm_interior(o.residual_vc(kc, f, up))
+            u = uq if keep else up
         accepted.append(bool(keep))
-        if keep:
-            u, r = u2, r2
-        e = o.cycle_vc(kc, r, levels, precision=precision)
-        u[1:-1, 1:-1] += e[1:-1, 1:-1]
+        rejected_in_a_row = 0 if keep else rejected_in_a_row + 1
         k += 1

@@ -142,6 +142,10 @@ struct homg_ctx {
     double* lpart = nullptr;
     double* lpart2 = nullptr;
     double* lscal = nullptr;  // [0] rho, [1] ||r||^2, [2] ||r'||^2
+    int learn_judge = HOMG_JUDGE_PROPOSAL;
+    double* lu2 = nullptr;    // judged after the cycle: third FP64 iterate, saved source, partials
+    void* lgs = nullptr;
+    double* lpart3 = nullptr;
 
     homg_stats stats{};
     char err[512] = "";
@@ -1572,6 +1576,9 @@ int ensure_learned(homg_ctx* h) {
     const size_t op = take((size_t)std::max(feat_parts(h->n), h->nparts) * sizeof(double));
     const size_t op2 = take((size_t)h->nparts * sizeof(double));
     const size_t os = take(4 * sizeof(double));
+    const size_t ou2 = take((size_t)grid_elems(2, h->n, h->pitch0) * sizeof(double));
+    const size_t ogs = take((size_t)grid_elems(2, h->n, h->pitch0) * es);
+    const size_t op3 = take((size_t)h->nparts * sizeof(double));
     CK(h, cudaMalloc(&h->learn_arena, (size_t)round_up((int64_t)off, 256)), "allocating the learned-solve buffers");
     CK(h, cudaMemset(h->learn_arena, 0, (size_t)round_up((int64_t)off, 256)), "cudaMemset");
     h->lx = h->learn_arena + ox;
@@ -1581,6 +1588,9 @@ int ensure_learned(homg_ctx* h) {
     h->lpart = (double*)(h->learn_arena + op);
     h->lpart2 = (double*)(h->learn_arena + op2);
     h->lscal = (double*)(h->learn_arena + os);
+    h->lu2 = (double*)(h->learn_arena + ou2);
+    h->lgs = h->learn_arena + ogs;
+    h->lpart3 = (double*)(h->learn_arena + op3);
     return HOMG_OK;
 }
 
@@ -1627,6 +1637,14 @@ int homg_features(homg_handle h, const double* f, const double* u, const double*
     return HOMG_OK;
 }
 
+int homg_set_learned_judge(homg_handle h, int judge) {
+    if (!h) return HOMG_EINVAL;
+    if (judge != HOMG_JUDGE_PROPOSAL && judge != HOMG_JUDGE_AFTER_CYCLE)
+        return fail(h, HOMG_EINVAL, "homg_set_learned_judge: judge must be HOMG_JUDGE_PROPOSAL or HOMG_JUDGE_AFTER_CYCLE%s%s");
+    h->learn_judge = judge;
+    return HOMG_OK;
+}
+
 int homg_solve_learned(homg_handle h, homg_net_handle net, const double* f, double* u, double tol, int max_cycles,
                        int* cycles_out, double* relres_out, int* accepted_out) {
     if (!h) return HOMG_EINVAL;
@@ -1661,59 +1679,106 @@ int homg_solve_learned(homg_handle h, homg_net_handle net, const double* f, doub
     CK(h, launch_finalize(fin_args(h, FIN_INIT, nullptr), sm), "finalize kernel");
     CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
     CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
-    int cur = 0;  // uint_[cur] holds the iterate
+    // Three FP64 iterates: U[cur] holds the current one; the others receive a proposal or a branch.
+    double* U[3] = {h->uint_[0], h->uint_[1], h->lu2};
+    int cur = 0;
     int kept = 0, rejected_in_a_row = 0;
+    const bool after_cycle = h->learn_judge == HOMG_JUDGE_AFTER_CYCLE;
     ResidArgs base = resid_args(h, 1);
+    // u_out = u_in + e, its residual source into g0 and the partial sums of ||r||^2 into part
+    auto update = [&](const double* u_in, const void* e, double* u_out, void* g0, double* part) {
+        ResidArgs c = base;
+        c.u_in = cdgrid(u_in, h->pitch0, h->n);
+        c.e = cgrid(e, h->pitch0, h->n);
+        c.u_out = dgrid(u_out, h->pitch0, h->n);
+        c.g0 = grid(g0, h->pitch0, h->n);
+        c.part_r = part;
+        c.part_f = nullptr;
+        return launch_residual(2, h->prec, false, c, h->n, sm);
+    };
+    auto cycle = [&]() -> cudaError_t {  // one HOMG cycle on the source in g0: the correction in e[e_final]
+        cudaError_t e = enqueue_ops(h, h->partA, sm);
+        if (e == cudaSuccess) e = enqueue_ops(h, h->partB, sm);
+        return e;
+    };
     for (int k = 1; !s->done && k <= max_cycles; ++k) {
         if (accepted_out) accepted_out[k - 1] = 0;
+        bool keep = false;
+        int next = cur;  // iterate after this cycle
         // after two rejections in a row the network stops proposing: plain HOMG cycles only
         if (rejected_in_a_row < 2) {
-        // proposal from the network
-        CK(h, enqueue_features(h, h->L[0].g, h->lx, sm), "feature kernels");
-        rc = net_forward_dev(net, h->lx, 1, side, side, h->ly, sm);
-        if (rc != HOMG_OK) return fail(h, rc, "homg_solve_learned: network inference failed: %s%s", homg_net_last_error(net));
-        CK(h, launch_correct(h->prec, h->ly, h->n, h->lscal, h->lcorr, h->pitch0, sm), "correction kernel");
-        ResidArgs p = base;
-        p.u_in = cdgrid(h->uint_[cur], h->pitch0, h->n);
-        p.e = cgrid(h->lcorr, h->pitch0, h->n);
-        p.u_out = dgrid(h->uint_[cur ^ 1], h->pitch0, h->n);
-        p.g0 = grid(h->lg0, h->pitch0, h->n);
-        p.part_r = h->lpart2;
-        p.part_f = nullptr;
-        CK(h, launch_residual(2, h->prec, false, p, h->n, sm), "residual kernel");
-        CK(h, launch_reduce(h->lpart2, h->nparts, 0.0, h->lscal + 2, sm), "norm kernel");
-        double nrm[2] = {0.0, 0.0};
-        CK(h, cudaMemcpyAsync(nrm, h->lscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync");
-        CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
-        rc = net_check_error(net);
-        if (rc != HOMG_OK) return fail(h, rc, "homg_solve_learned: %s%s", homg_net_last_error(net));
-        const bool keep = nrm[1] < nrm[0];  // the plain solver's FP64 residual judges the proposal
-        if (accepted_out) accepted_out[k - 1] = keep ? 1 : 0;
-        if (keep) {
-            ++kept;
-            rejected_in_a_row = 0;
-            cur ^= 1;
-            CK(h, cudaMemcpyAsync(h->L[0].g, h->lg0, gbytes, cudaMemcpyDeviceToDevice, sm), "cudaMemcpyAsync");
+            const int a = (cur + 1) % 3, b = (cur + 2) % 3;
+            // proposal u' = u + rho y into U[a], its residual source into lg0
+            CK(h, enqueue_features(h, h->L[0].g, h->lx, sm), "feature kernels");
+            rc = net_forward_dev(net, h->lx, 1, side, side, h->ly, sm);
+            if (rc != HOMG_OK) return fail(h, rc, "homg_solve_learned: network inference failed: %s%s", homg_net_last_error(net));
+            CK(h, launch_correct(h->prec, h->ly, h->n, h->lscal, h->lcorr, h->pitch0, sm), "correction kernel");
+            CK(h, update(U[cur], h->lcorr, U[a], h->lg0, h->lpart2), "residual kernel");
+            CK(h, launch_reduce(h->lpart2, h->nparts, 0.0, h->lscal + 2, sm), "norm kernel");
+            if (!after_cycle) {
+                // judge the proposal's own residual against the current one
+                double nrm[2] = {0.0, 0.0};
+                CK(h, cudaMemcpyAsync(nrm, h->lscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync");
+                CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+                rc = net_check_error(net);
+                if (rc != HOMG_OK) return fail(h, rc, "homg_solve_learned: %s%s", homg_net_last_error(net));
+                keep = nrm[1] < nrm[0];  // the plain solver's FP64 residual judges the proposal
+                int from = cur;
+                if (keep) {
+                    from = a;
+                    CK(h, cudaMemcpyAsync(h->L[0].g, h->lg0, gbytes, cudaMemcpyDeviceToDevice, sm), "cudaMemcpyAsync");
+                }
+                // one HOMG cycle on the kept iterate's residual
+                CK(h, cycle(), "cycle kernels");
+                next = (from == cur) ? a : b;
+                CK(h, update(U[from], h->e[h->e_final], U[next], h->L[0].g, h->part_r), "residual kernel");
+            } else {
+                // judge after the cycle: one HOMG cycle from u (into U[b]) and one from u' (into U[cur]),
+                // keep the result with the smaller FP64 residual
+                CK(h, cudaMemcpyAsync(h->lgs, h->L[0].g, gbytes, cudaMemcpyDeviceToDevice, sm), "cudaMemcpyAsync");
+                CK(h, cycle(), "cycle kernels");
+                CK(h, update(U[cur], h->e[h->e_final], U[b], h->lgs, h->part_r), "residual kernel");
+                CK(h, launch_reduce(h->part_r, h->nparts, 0.0, h->lscal + 1, sm), "norm kernel");
+                CK(h, cudaMemcpyAsync(h->L[0].g, h->lg0, gbytes, cudaMemcpyDeviceToDevice, sm), "cudaMemcpyAsync");
+                CK(h, cycle(), "cycle kernels");
+                CK(h, update(U[a], h->e[h->e_final], U[cur], h->L[0].g, h->lpart3), "residual kernel");
+                CK(h, launch_reduce(h->lpart3, h->nparts, 0.0, h->lscal + 2, sm), "norm kernel");
+                double nrm[2] = {0.0, 0.0};
+                CK(h, cudaMemcpyAsync(nrm, h->lscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync");
+                CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
+                rc = net_check_error(net);
+                if (rc != HOMG_OK) return fail(h, rc, "homg_solve_learned: %s%s", homg_net_last_error(net));
+                keep = nrm[1] < nrm[0];
+                if (keep) {
+                    next = cur;  // the proposal's branch; its source is in g0 already
+                    CK(h, cudaMemcpyAsync(h->part_r, h->lpart3, (size_t)h->nparts * sizeof(double), cudaMemcpyDeviceToDevice,
+                                          sm), "cudaMemcpyAsync");
+                } else {
+                    next = b;  // the plain branch
+                    CK(h, cudaMemcpyAsync(h->L[0].g, h->lgs, gbytes, cudaMemcpyDeviceToDevice, sm), "cudaMemcpyAsync");
+                }
+            }
+            if (accepted_out) accepted_out[k - 1] = keep ? 1 : 0;
+            if (keep) {
+                ++kept;
+                rejected_in_a_row = 0;
+            } else {
+                ++rejected_in_a_row;
+            }
         } else {
-            ++rejected_in_a_row;
+            CK(h, cycle(), "cycle kernels");
+            next = (cur + 1) % 3;
+            CK(h, update(U[cur], h->e[h->e_final], U[next], h->L[0].g, h->part_r), "residual kernel");
         }
-        }
-        // one HOMG cycle on the kept iterate's residual
-        CK(h, enqueue_ops(h, h->partA, sm), "cycle kernels");
-        CK(h, enqueue_ops(h, h->partB, sm), "cycle kernels");
-        ResidArgs c = base;
-        c.u_in = cdgrid(h->uint_[cur], h->pitch0, h->n);
-        c.e = cgrid(h->e[h->e_final], h->pitch0, h->n);
-        c.u_out = dgrid(h->uint_[cur ^ 1], h->pitch0, h->n);
-        CK(h, launch_residual(2, h->prec, false, c, h->n, sm), "residual kernel");
+        // the test on the kept iterate's residual
         CK(h, launch_reduce(h->part_r, h->nparts, 0.0, h->lscal + 1, sm), "norm kernel");
         CK(h, launch_finalize(fin_args(h, FIN_CYCLE, nullptr), sm), "finalize kernel");
-        cur ^= 1;
+        cur = next;
         CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
         CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
     }
     CopyOutArgs co = copy_args(h);
-    co.u0 = co.u1 = cdgrid(h->uint_[cur], h->pitch0, h->n);
+    co.u0 = co.u1 = cdgrid(U[cur], h->pitch0, h->n);
     CK(h, launch_copy_out(2, co, h->n, sm), "copy-out kernel");
     CK(h, cudaEventRecord(h->sev[1], sm), "cudaEventRecord");
     CK(h, cudaMemcpyAsync(h->hhist, h->dhist, (max_cycles + 1) * sizeof(double), cudaMemcpyDeviceToHost, sm),

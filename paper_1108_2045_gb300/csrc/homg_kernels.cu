@@ -1275,12 +1275,22 @@ __global__ void __launch_bounds__(J3X * J3Y) k_prolong3_s1(ProlongArgs a, int ro
 // offset b inside its cell adds q0 + (b 2^-mp)(q1 - q0), the weight assembled from integer bits,
 // the addition written as a fused multiply-add by a run-time 1 (the FP64 pipe issues those faster):
 // two FMAs per node (one on a lattice row), no conversion on the FP64 pipe.
+//
+// Columns are dealt to the block's threads by residue class: with L = 2^min(m, 2), the first JX/L
+// threads take the columns on the level-min(m, 2) lattice, the next JX/L the next class, and so on,
+// so that whether a column relaxes (and, for mp <= 2, whether it lies on the pending lattice) is
+// the same for every lane of a warp. Otherwise every warp would issue the relaxation's FP64
+// instructions on every lattice row for its few lattice lanes, and GB300's FP64 pipe takes a warp
+// instruction's full time whatever the number of active lanes.
 template <bool PEND, typename T>
 __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
     pdl_begin();
     using C = typename St<T>::C;
     const int n = a.e_new.n;
-    const int i = blockIdx.x * JX + threadIdx.x + 1;
+    const int Lp = a.m >= 2 ? 4 : 2, per = JX / Lp;  // m >= 1 here
+    const int cls = threadIdx.x / per;
+    const int off = (threadIdx.x % per) * Lp + ((Lp - 1 - cls) & (Lp - 1));
+    const int i = blockIdx.x * JX + off + 1;
     if (i >= n) return;
     const int j0 = blockIdx.y * JR + 1;
     const int j1 = min(j0 + JR, n);

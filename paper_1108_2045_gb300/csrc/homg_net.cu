@@ -378,6 +378,78 @@ __global__ void k_loss(const float* y, const float* t, int B, int H, int W, floa
     }
 }
 
+// ---- residual loss ----------------------------------------------------------------------------
+// The proposal y leaves the residual res(p) = x_0(p) - (y(p) - sum_q w_q(p) y(q)) at an inner pixel
+// p of a patch (not on its border), in the network's units: x_0 = h^2 r / (D rho) is the scaled
+// residual, and w_q(p) = k_pq / D(p) the Jacobi-scaled operator rebuilt from the patch's own log k
+// channel (k = exp(x_1), faces k_pq the harmonic means, D(p) their sum; W, E, S, N = column - 1,
+// column + 1, row - 1, row + 1). Loss: (1/N) sum res^2 over the N inner pixels of the batch.
+// Pass 1 writes per pixel [res, w_W, w_E, w_S, w_N] (zeros on the border) and the partial sums of
+// res^2; pass 2 forms dL/dy(q) = (2/N) (-res(q) + sum over the inner neighbours p of q of w(p) res(p),
+// w(p) the weight p gives q) and writes it as channel 0 of the gradient image.
+__device__ __forceinline__ float img_ch(const bf16* x, int b, int H, int W, int yy, int xx, int c) {
+    return __bfloat162float(x[(((int64_t)b * H + yy) * 2 + c / 8) * W * 8 + (int64_t)xx * 8 + c % 8]);
+}
+
+__global__ void k_loss_resid_a(const float* y, const bf16* x, int B, int H, int W, float* R, double* part) {
+    __shared__ double sh[8];
+    const int64_t n = (int64_t)B * H * W;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / ((int64_t)H * W));
+        const int rem = (int)(i % ((int64_t)H * W));
+        const int r = rem / W, c = rem % W;
+        float* o = R + 5 * i;
+        if (r == 0 || c == 0 || r == H - 1 || c == W - 1) {
+            o[0] = o[1] = o[2] = o[3] = o[4] = 0.f;
+            continue;
+        }
+        const float kp = expf(img_ch(x, b, H, W, r, c, 1));
+        const float kq[4] = {expf(img_ch(x, b, H, W, r, c - 1, 1)), expf(img_ch(x, b, H, W, r, c + 1, 1)),
+                             expf(img_ch(x, b, H, W, r - 1, c, 1)), expf(img_ch(x, b, H, W, r + 1, c, 1))};
+        float f[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[q] = ((2.f * kp) * kq[q]) / (kp + kq[q]);
+        const float D = ((f[0] + f[1]) + f[2]) + f[3];
+        const float w[4] = {f[0] / D, f[1] / D, f[2] / D, f[3] / D};
+        const float* yb = y + (int64_t)b * H * W;
+        const float ay = yb[r * W + c] - (((w[0] * yb[r * W + c - 1] + w[1] * yb[r * W + c + 1]) + w[2] * yb[(r - 1) * W + c]) +
+                                          w[3] * yb[(r + 1) * W + c]);
+        const float res = img_ch(x, b, H, W, r, c, 0) - ay;
+        o[0] = res;
+        o[1] = w[0];
+        o[2] = w[1];
+        o[3] = w[2];
+        o[4] = w[3];
+        acc += (double)res * res;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_loss_resid_b(const float* R, int B, int H, int W, float scale, bf16* g) {
+    const int64_t n = (int64_t)B * H * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int rem = (int)(i % ((int64_t)H * W));
+        const int r = rem / W, c = rem % W;
+        float d = -R[5 * i];
+        if (c + 1 < W) d += R[5 * (i + 1) + 1] * R[5 * (i + 1)];       // q is the west neighbour of (r, c+1)
+        if (c - 1 >= 0) d += R[5 * (i - 1) + 2] * R[5 * (i - 1)];      // ... the east neighbour of (r, c-1)
+        if (r + 1 < H) d += R[5 * (i + W) + 3] * R[5 * (i + W)];       // ... the south neighbour of (r+1, c)
+        if (r - 1 >= 0) d += R[5 * (i - W) + 4] * R[5 * (i - W)];      // ... the north neighbour of (r-1, c)
+        const int64_t x = i % W, row = i / W;
+        uint4 c0 = make_uint4(pack_bf16x2(scale * d, 0.f), 0u, 0u, 0u), z = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(g + ((row * 2 + 0) * W + x) * 8) = c0;
+        *reinterpret_cast<uint4*>(g + ((row * 2 + 1) * W + x) * 8) = z;
+    }
+}
+
 // ---- weight gradient (CUDA cores) -------------------------------------------------------------
 // dW[o][c][p][q] += sum over pixels g[o](y, x) a[c](y + p - 1, x + q - 1); db[o] += sum g[o].
 // A block takes 32-pixel row segments; each thread owns a fixed set of (o, c, p, q) outputs and
@@ -664,6 +736,8 @@ struct homg_net {
     bf16* gB = nullptr;
     bf16* g4 = nullptr;  // last-layer gradient ([*, 16, H, W])
     float* y = nullptr;  // training output
+    float* lres = nullptr;  // residual loss: [res, w_W, w_E, w_S, w_N] per pixel
+    int loss_kind = HOMG_NET_LOSS_ERROR;
     double* part = nullptr;
     double* dloss = nullptr;
     int* derr = nullptr;
@@ -712,14 +786,17 @@ int ensure_scratch(homg_net* n, int64_t px) {
     if (n->gB) cudaFree(n->gB);
     if (n->g4) cudaFree(n->g4);
     if (n->y) cudaFree(n->y);
+    if (n->lres) cudaFree(n->lres);
     n->gA = n->gB = n->g4 = nullptr;
     n->y = nullptr;
+    n->lres = nullptr;
     n->cap_px = 0;
     for (auto*& p : n->act) NCK(n, cudaMalloc(&p, (size_t)px * 32 * sizeof(bf16)), "allocating activations");
     NCK(n, cudaMalloc(&n->gA, (size_t)px * 32 * sizeof(bf16)), "allocating gradients");
     NCK(n, cudaMalloc(&n->gB, (size_t)px * 32 * sizeof(bf16)), "allocating gradients");
     NCK(n, cudaMalloc(&n->g4, (size_t)px * 16 * sizeof(bf16)), "allocating gradients");
     NCK(n, cudaMalloc(&n->y, (size_t)px * sizeof(float)), "allocating outputs");
+    NCK(n, cudaMalloc(&n->lres, (size_t)px * 5 * sizeof(float)), "allocating the residual-loss scratch");
     n->cap_px = px;
     return HOMG_OK;
 }
@@ -915,7 +992,8 @@ int homg_net_forward(homg_net_handle net, const void* x, int B, int H, int W, fl
 int homg_net_train_step(homg_net_handle net, const void* xv, const float* t, int B, int H, int W, float lr,
                         float* loss_out) {
     if (!net) return HOMG_EINVAL;
-    if (!xv || !t || !dims_ok(B, H, W) || !(lr > 0.f))
+    const bool resid = net->loss_kind == HOMG_NET_LOSS_RESIDUAL;
+    if (!xv || (!t && !resid) || !dims_ok(B, H, W) || !(lr > 0.f) || (resid && (H < 3 || W < 3)))
         return net_fail(net, HOMG_EINVAL, "homg_net_train_step: null pointer, bad sizes or lr <= 0");
     NCK(net, cudaSetDevice(net->device), "cudaSetDevice");
     const int64_t px = (int64_t)B * H * W;
@@ -926,7 +1004,14 @@ int homg_net_train_step(homg_net_handle net, const void* xv, const float* t, int
     rc = forward(net, x, B, H, W, net->y, true, s);
     if (rc != HOMG_OK) return rc;
     const int lb = (int)((px + 255) / 256 < kLossBlocks ? (px + 255) / 256 : kLossBlocks);
-    k_loss<<<lb, 256, 0, s>>>(net->y, t, B, H, W, (float)(2.0 / (double)px), net->g4, net->part);
+    // loss terms: every pixel (error loss) or the inner pixels of every patch (residual loss)
+    const int64_t nl = resid ? (int64_t)B * (H - 2) * (W - 2) : px;
+    if (resid) {
+        k_loss_resid_a<<<lb, 256, 0, s>>>(net->y, x, B, H, W, net->lres, net->part);
+        k_loss_resid_b<<<lb, 256, 0, s>>>(net->lres, B, H, W, (float)(2.0 / (double)nl), net->g4);
+    } else {
+        k_loss<<<lb, 256, 0, s>>>(net->y, t, B, H, W, (float)(2.0 / (double)px), net->g4, net->part);
+    }
     NCK(net, cudaGetLastError(), "loss kernel");
     NCK(net, homg::launch_reduce(net->part, lb, 0.0, net->dloss, s), "loss reduction");
     NCK(net, cudaMemsetAsync(net->grads, 0, (size_t)net->np * sizeof(float), s), "cudaMemsetAsync");
@@ -971,8 +1056,16 @@ int homg_net_train_step(homg_net_handle net, const void* xv, const float* t, int
     double loss = 0.0;
     NCK(net, cudaMemcpyAsync(&loss, net->dloss, sizeof(double), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
     NCK(net, cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    if (loss_out) *loss_out = (float)(loss / (double)px);
+    if (loss_out) *loss_out = (float)(loss / (double)nl);
     return homg::net_check_error(net);
+}
+
+int homg_net_set_loss(homg_net_handle net, int kind) {
+    if (!net) return HOMG_EINVAL;
+    if (kind != HOMG_NET_LOSS_ERROR && kind != HOMG_NET_LOSS_RESIDUAL)
+        return net_fail(net, HOMG_EINVAL, "homg_net_set_loss: kind must be HOMG_NET_LOSS_ERROR or HOMG_NET_LOSS_RESIDUAL");
+    net->loss_kind = kind;
+    return HOMG_OK;
 }
 
 int homg_net_check_barrier_timeout(homg_net_handle net, double* waited_ms) {

@@ -60,6 +60,8 @@ EXPORTS = [
     "homg_net_destroy",
     "homg_features",
     "homg_solve_learned",
+    "homg_net_set_loss",
+    "homg_set_learned_judge",
 ]
 
 HOMG_BATCH_MAX_GROUPS = 16
@@ -156,6 +158,8 @@ def load(path=LIB_PATH):
     lib.homg_net_destroy.argtypes = [vp]
     lib.homg_features.argtypes = [vp, vp, vp, vp, vp, vp, dp]
     lib.homg_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp, ip]
+    lib.homg_net_set_loss.argtypes = [vp, ctypes.c_int]
+    lib.homg_set_learned_judge.argtypes = [vp, ctypes.c_int]
     lib.homg_get_history.argtypes = [vp, dp, ctypes.c_int]
     lib.homg_get_stats.argtypes = [vp, ctypes.POINTER(homg_stats)]
     lib.homg_last_error.argtypes = [vp]
@@ -526,6 +530,16 @@ def image_device_layout_to_channels_first(xr):
     return np.ascontiguousarray(xr.transpose(1, 3, 0, 2).reshape(G * E, H, W))
 
 
+NET_LOSSES = {"error": 0, "residual": 1}
+JUDGES = {"proposal": 0, "after_cycle": 1}
+
+
+def homg_set_learned_judge(handle, judge):
+    """How homg_solve_learned judges proposals on this handle: "proposal" (the proposal's own
+    residual) or "after_cycle" (the residuals after one HOMG cycle from each candidate)."""
+    _check(load().homg_set_learned_judge(handle, JUDGES[judge] if isinstance(judge, str) else judge), handle)
+
+
 class Net:
     """Owner of a learned-corrector network handle (include/homg_net.h)."""
 
@@ -568,6 +582,11 @@ class Net:
         """x: device bfloat16 tensor [B, H, 2, W, 8]; y: device float32 tensor [B, H, W]."""
         B, H, _, W, _ = x.shape
         _net_check(load().homg_net_forward(self.handle, _devptr_any(x, "x"), B, H, W, _devptr_any(y, "y")), self.handle)
+
+    def set_loss(self, kind):
+        """Training loss: "error" (mean squared error against the scaled error target) or "residual"
+        (the residual the proposal leaves on each patch; the target is then not used)."""
+        _net_check(load().homg_net_set_loss(self.handle, NET_LOSSES[kind] if isinstance(kind, str) else kind), self.handle)
 
     def train_step(self, x, t, lr):
         B, H, _, W, _ = x.shape

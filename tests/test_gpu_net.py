@@ -280,3 +280,80 @@ def test_barrier_wait_gives_up_and_context_stays_usable(homg):
         assert 400.0 <= ms <= 5000.0, ms
     ref = np.stack([cnn.forward(params, x)[0] for x in xs])
     np.testing.assert_array_equal(gpu_forward(homg, params, xs), ref)
+
+
+def test_residual_loss_train_step_matches_oracle(homg):
+    """The residual loss (homg_net_set_loss) against oracle/cnn.py's residual loss and its gradients,
+    on patches whose log k channel varies (so the rebuilt operator's weights are not all 1/4)."""
+    import torch
+
+    rng = np.random.default_rng(30)
+    params = [(w, cnn.f32(rng.standard_normal(b.shape) * 0.05)) for w, b in cnn.init_weights(31)]
+    params[-1] = (params[-1][0] * 10.0, params[-1][1])
+    B, P = 3, 64
+    xs = [np.stack([cnn.bf16(rng.standard_normal((P, P))), cnn.bf16(rng.uniform(-2.0, 2.0, (P, P)))]) for _ in range(B)]
+    ts = [np.zeros((P, P))] * B
+    loss_ref, gw, gb = cnn.loss_and_grads(params, xs, ts, loss_kind="residual")
+    x = to_device_images(homg, xs)
+    t = torch.zeros(B, P, P, dtype=torch.float32, device="cuda")
+    with homg.Net() as net:
+        net.set_params(flat(params))
+        net.set_loss("residual")
+        loss = net.train_step(x, t, 1e-3)
+        grads = unflat(net.get_grads())
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref, (loss, loss_ref)
+    for l in range(len(params)):
+        gW, gB = grads[l]
+        assert np.linalg.norm(gW - gw[l]) <= 3e-2 * np.linalg.norm(gw[l]), l
+        assert np.linalg.norm(gB - gb[l]) <= 3e-2 * np.linalg.norm(gb[l]) + 1e-12, l
+
+
+def jacobi_network(c):
+    """Output exactly c x_0 (see tests/test_oracle_cnn.py): the proposal is a damped-Jacobi step."""
+    params = [(np.zeros((co, ci, 3, 3)), np.zeros(co)) for co, ci in cnn.shapes()]
+    params[0][0][0, 0, 1, 1] = 1.0
+    params[0][0][1, 0, 1, 1] = -1.0
+    for l in (1, 2):
+        params[l][0][0, 0, 1, 1] = 1.0
+        params[l][0][1, 1, 1, 1] = 1.0
+    params[3][0][0, 0, 1, 1] = c
+    params[3][0][0, 1, 1, 1] = -c
+    return params
+
+
+# Iterates of the learned loop against the oracle's: the network input is a bfloat16 rounding of the
+# scaled FP64 residual, and the GPU's residual (another summation order) rounds to a neighbouring
+# bfloat16 value at a few nodes, so the proposals differ there by one bfloat16 unit (2^-8 relative).
+LEARNED_ITERATE_TOL = 2e-2
+
+
+@pytest.mark.parametrize("judge", ["proposal", "after_cycle"])
+@pytest.mark.parametrize("c", [0.75, -1.0])
+def test_learned_loop_matches_oracle(homg, judge, c):
+    """homg_solve_learned with a fixed non-zero network (a damped-Jacobi step of weight c: 0.75 is
+    kept by the judge, -1 is rejected and then dropped) gives the oracle's keep/reject sequence and
+    iterates within LEARNED_ITERATE_TOL after every cycle, under both judges."""
+    import torch
+
+    n, levels = 128, 7
+    kc = inputs.grf_coefficient(n, ell=0.1, seed=32)
+    f_np = inputs.normal_rhs(n, 2, seed=33)
+    params = jacobi_network(c)
+    f = torch.from_numpy(f_np).cuda()
+    with homg.Solver(2, n + 1, levels) as s, homg.Net() as net:
+        s.set_coefficient(torch.from_numpy(kc).cuda())
+        homg.homg_set_learned_judge(s.handle, judge)
+        net.set_params(flat(params))
+        for k in (1, 2, 3, 4):
+            ref, rst, rcyc, rhist, racc = cnn.solve_learned(kc, f_np, params, levels, tol=0.0, max_cycles=k, judge=judge)
+            u = torch.zeros_like(f)
+            st, cyc, rr, acc = homg.homg_solve_learned(s.handle, net, f, u, tol=0.0, max_cycles=k)
+            assert cyc == rcyc == k
+            assert acc == racc, (k, acc, racc)
+            got = u.cpu().numpy()
+            err = max(np.linalg.norm(got - ref) / np.linalg.norm(ref), np.abs(got - ref).max() / np.abs(ref).max())
+            assert err <= LEARNED_ITERATE_TOL, (k, err)
+    if c > 0:
+        assert racc[0]
+    else:
+        assert racc == [False, False, False, False]

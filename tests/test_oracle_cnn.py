@@ -124,3 +124,99 @@ def test_learned_solve_reaches_tolerance_with_a_random_network():
     u, st, cyc, hist, acc = cnn.solve_learned(kc, f, params, levels, tol=1e-10)
     assert st == oracle.OK and hist[-1] <= 1e-10
     assert oracle.norm_interior(oracle.residual_vc(kc, f, u)) / oracle.norm_interior(f) <= 1e-10
+
+
+def jacobi_network(c, width=32):
+    """A network whose output is exactly c x_0: the first layer splits x_0 into relu(x_0) and
+    relu(-x_0), two identity layers carry them, the last layer forms c (relu(x_0) - relu(-x_0)).
+    Its proposal u + rho c x_0 = u + c h^2 r / D is one damped-Jacobi step of weight c."""
+    shapes = cnn.shapes(width=width)
+    params = [(np.zeros((co, ci, 3, 3)), np.zeros(co)) for co, ci in shapes]
+    params[0][0][0, 0, 1, 1] = 1.0
+    params[0][0][1, 0, 1, 1] = -1.0
+    for l in (1, 2):
+        params[l][0][0, 0, 1, 1] = 1.0
+        params[l][0][1, 1, 1, 1] = 1.0
+    params[3][0][0, 0, 1, 1] = c
+    params[3][0][0, 1, 1, 1] = -c
+    return params
+
+
+def test_jacobi_network_output_is_exact():
+    rng = np.random.default_rng(20)
+    x = cnn.bf16(rng.standard_normal((2, 9, 11)))
+    y, _ = cnn.forward(jacobi_network(0.75), x)
+    np.testing.assert_array_equal(y, 0.75 * x[0])
+
+
+def test_residual_loss_vanishes_for_the_exact_local_correction():
+    # when x_0 is exactly the scaled operator applied to y, the proposal y removes the whole
+    # residual at every inner pixel: the loss is 0 (up to rounding)
+    rng = np.random.default_rng(21)
+    x = np.stack([np.zeros((7, 8)), rng.uniform(-1.0, 1.0, (7, 8))])
+    y = rng.standard_normal((7, 8))
+    w = cnn.patch_operator(x)
+    nb = [y[1:-1, :-2], y[1:-1, 2:], y[:-2, 1:-1], y[2:, 1:-1]]
+    x[0, 1:-1, 1:-1] = y[1:-1, 1:-1] - sum(wq * q for wq, q in zip(w, nb))
+    res, _ = cnn.residual_loss_terms(x, y)
+    assert np.max(np.abs(res)) <= 1e-14
+    # constant coefficient: every weight is 1/4, the scaled operator is y - mean of the 4 neighbours
+    xc = np.stack([np.zeros((5, 5)), np.full((5, 5), 0.3)])
+    assert np.allclose(cnn.patch_operator(xc), 0.25, rtol=0, atol=1e-15)
+
+
+def test_residual_loss_gradients_match_finite_differences():
+    rng = np.random.default_rng(22)
+    params = cnn.init_weights(5, c_in=2, width=4, layers=3)
+    params = [(w, rng.standard_normal(b.shape) * 0.1) for w, b in params]
+    xs = [np.stack([rng.standard_normal((6, 7)), rng.uniform(-1, 1, (6, 7))]) for _ in range(2)]
+    ts = [np.zeros((6, 7))] * 2
+    loss, gw, gb = cnn.loss_and_grads(params, xs, ts, rounding=False, loss_kind="residual")
+    eps = 1e-6
+    for l in range(3):
+        w, b = params[l]
+        for idx in [(0, 0, 0, 0), (0, 1, 2, 1), (w.shape[0] - 1, w.shape[1] - 1, 1, 2)]:
+            wp, wm = w.copy(), w.copy()
+            wp[idx] += eps
+            wm[idx] -= eps
+            lp = cnn.loss_and_grads([(wp, b) if k == l else params[k] for k in range(3)], xs, ts, rounding=False,
+                                    loss_kind="residual")[0]
+            lm = cnn.loss_and_grads([(wm, b) if k == l else params[k] for k in range(3)], xs, ts, rounding=False,
+                                    loss_kind="residual")[0]
+            assert abs((lp - lm) / (2 * eps) - gw[l][idx]) <= 1e-6 * max(1.0, abs(gw[l][idx])), (l, idx)
+
+
+@pytest.mark.parametrize("judge", ["proposal", "after_cycle"])
+def test_zero_network_is_plain_homg_under_both_judges(judge):
+    # a zero proposal never wins (equal residuals), so after two rejections the solve is plain HOMG
+    n, levels = 32, 5
+    kc = inputs.grf_coefficient(n, ell=0.1, seed=23)
+    f = inputs.normal_rhs(n, 2, seed=24)
+    params = [(np.zeros_like(w), np.zeros_like(b)) for w, b in cnn.init_weights(0, width=8)]
+    u, st, cyc, hist, acc = cnn.solve_learned(kc, f, params, levels, tol=1e-10, judge=judge)
+    u0, st0, cyc0, hist0 = oracle.solve_vc(kc, f, levels, tol=1e-10)
+    assert (st, cyc) == (st0, cyc0) and acc == [False] * cyc
+    np.testing.assert_array_equal(u, u0)
+
+
+def test_jacobi_proposals_are_kept_and_an_amplifier_is_dropped_after_two_rejections():
+    # constant coefficient: a damped-Jacobi step (weight 3/4) strictly lowers the residual norm, so the
+    # judge keeps it; a step of weight -1 raises it, is rejected twice and then no longer proposed
+    n, levels = 32, 5
+    kc = np.full((n + 1, n + 1), 1.7)
+    f = inputs.normal_rhs(n, 2, seed=25)
+    _, st, cyc, _, acc = cnn.solve_learned(kc, f, jacobi_network(0.75, width=8), levels, tol=1e-10, max_cycles=3)
+    assert acc[0] is True
+    _, st, cyc, _, acc = cnn.solve_learned(kc, f, jacobi_network(-1.0, width=8), levels, tol=1e-10, max_cycles=4)
+    assert acc == [False, False, False, False]
+    # judged after the cycle, the proposal's result wins exactly when its residual after the cycle is lower
+    u, st, cyc, hist, acc = cnn.solve_learned(kc, f, jacobi_network(0.75, width=8), levels, tol=0.0, max_cycles=1,
+                                              judge="after_cycle")
+    x, rho = cnn.features(kc, oracle.residual_vc(kc, f, np.zeros_like(f)))
+    up = oracle.cycle_vc(kc, oracle.residual_vc(kc, f, np.zeros_like(f)), levels)
+    u2 = np.zeros_like(f)
+    u2[1:-1, 1:-1] = rho * 0.75 * x[0][1:-1, 1:-1]
+    uq = u2 + oracle.cycle_vc(kc, oracle.residual_vc(kc, f, u2), levels)
+    better = oracle.norm_interior(oracle.residual_vc(kc, f, uq)) < oracle.norm_interior(oracle.residual_vc(kc, f, up))
+    assert acc == [better]
+    np.testing.assert_array_equal(u, uq if better else up)
