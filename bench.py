@@ -346,8 +346,9 @@ def run_cfg4(args, homg, stream, barrier, pending):
     out = {"workload": "1024 2-D Poisson problems, 5-point, sides 2^k+1 with k ~ U{6..10} (seed 1), f iid N(0,1), "
                        "each to relres 1e-10, one batched solve",
            "problems_per_k": {str(k): int((ks_arr == k).sum()) for k in range(6, 11)}, "unknowns": unknowns}
-    for prec in ("fp32", "fp64"):
-        with homg.BatchSolver(sides, precision=prec) as b:
+    # FP32 and FP64 cycles with the per-group graphs; FP32 cycles in one persistent launch
+    for name, prec, mode in (("fp32", "fp32", "graph"), ("fp64", "fp64", "graph"), ("fp32_persistent", "fp32", "persistent")):
+        with homg.BatchSolver(sides, precision=prec, launch_mode=mode) as b:
             b.set_stream(stream)
             for u in us:
                 u.zero_()
@@ -362,7 +363,7 @@ def run_cfg4(args, homg, stream, barrier, pending):
             st = b.stats()
         batch_ms = min(r[0] for r in runs)
         per = np.array(runs[-1][1])
-        r = {"batch_ms": batch_ms, "value": unknowns / (batch_ms * 1e-3), "unit": UNIT,
+        r = {"batch_ms": batch_ms, "value": unknowns / (batch_ms * 1e-3), "unit": UNIT, "launch": mode,
              "all_converged": all(x == 0 for x in runs[-1][2]), "max_relres": max(runs[-1][4]),
              "cycles_min_max": [min(runs[-1][3]), max(runs[-1][3])],
              "solve_ms_p50": float(np.percentile(per, 50)), "solve_ms_p99": float(np.percentile(per, 99)),
@@ -372,7 +373,8 @@ def run_cfg4(args, homg, stream, barrier, pending):
             r["oracle_sample"] = "two problems per k (the first of each size in batch order)"
             for i in sample:  # checked later by the oracle's own FP64 residual (CPU leg)
                 pending.append((r, "poisson_max", None, fs_np[i], us[i].cpu().numpy()))
-        out[prec] = r
+        out[name] = r
+    out["persistent_over_graph_ms"] = out["fp32_persistent"]["batch_ms"] / out["fp32"]["batch_ms"]
     del fs, us
     torch.cuda.empty_cache()
     if args.cfg4_oracle_time:

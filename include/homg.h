@@ -45,7 +45,7 @@ extern "C" {
 #define HOMG_OK 0
 #define HOMG_NOT_CONVERGED 1 /* max_cycles cycles done, relative residual still above tol       */
 #define HOMG_DIVERGED 2      /* relative residual not finite, or above diverge_factor * initial   */
-#define HOMG_TIMEOUT 3       /* reserved for bounded device-side waits; no current kernel waits   */
+#define HOMG_TIMEOUT 3       /* a bounded device-side wait (persistent batch grid barrier) gave up */
 #define HOMG_EINVAL (-1)     /* invalid argument (null pointer, level count, stencil, options ...)  */
 #define HOMG_ESHAPE (-2)     /* grid sides not 2^K + 1, not all equal, or too large                 */
 #define HOMG_ECUDA (-3)      /* a CUDA runtime call failed                                          */
@@ -134,6 +134,13 @@ typedef struct homg_options {
 
 #define HOMG_LAUNCH_GRAPH 0
 #define HOMG_LAUNCH_STREAM 1
+/* Batches only (homg_batch_create; homg_create rejects it): the whole batch solve is ONE
+ * cooperative launch of a persistent kernel. Phase j of a cycle holds op j of every size group's
+ * cycle (the same ops, with the same arithmetic, that the group's graph launches). A phase's work is
+ * a queue of (op, problem, tile) items that the resident blocks draw from a counter, and a grid
+ * barrier separates phases. Every barrier wait is bounded: a block that waits longer than a few
+ * seconds records the failure, every block leaves the launch, and the solve returns HOMG_TIMEOUT. */
+#define HOMG_LAUNCH_PERSISTENT 2
 
 /* Statistics of the last homg_solve on a handle (times from CUDA events recorded on the handle's
  * stream inside the solve graph; zero when the last call failed). */
@@ -288,6 +295,15 @@ int homg_batch_get_stats(homg_batch_handle b, homg_batch_stats* out);
 
 /* Release every resource of b (no-op for NULL). */
 void homg_batch_destroy(homg_batch_handle b);
+
+/* Self-test of the persistent batch kernel's failure path (b created with HOMG_LAUNCH_PERSISTENT):
+ * launches the kernel so that its first grid barrier waits for one block more than the launch has,
+ * with a 0.25 s limit. Nothing reads or writes problem data. Every block gives up, records the
+ * failure and leaves, so the call returns HOMG_TIMEOUT with a message in homg_last_error(NULL),
+ * *waited_ms (optional) the launch's duration, and the context stays usable (the next
+ * homg_batch_solve works). HOMG_OK here would mean the wait is not bounded as documented;
+ * HOMG_EINVAL for a batch without the persistent mode. Synchronises the batch's stream. */
+int homg_batch_check_barrier_timeout(homg_batch_handle b, double* waited_ms);
 
 /* Threads per block of homg_fp64_issue_probe. */
 #define HOMG_PROBE_THREADS 256

@@ -895,7 +895,8 @@ int check_options(int ndim, homg_options& o) {
     if (o.v_post == 0) o.v_post = 2;
     if (!(o.omega_j > 0.0 && o.omega_j <= 2.0) || o.max_i < 1 || !(o.diverge_factor > 1.0) || o.n_schedule < 0 ||
         (o.n_schedule > 0 && !o.schedule) || o.exec_mode < 0 || o.exec_mode > 2 || (o.strict_fp != 0 && o.strict_fp != 1) ||
-        (o.launch_mode != HOMG_LAUNCH_GRAPH && o.launch_mode != HOMG_LAUNCH_STREAM) ||
+        (o.launch_mode != HOMG_LAUNCH_GRAPH && o.launch_mode != HOMG_LAUNCH_STREAM &&
+         o.launch_mode != HOMG_LAUNCH_PERSISTENT) ||
         (o.precision != HOMG_PREC_FP64 && o.precision != HOMG_PREC_FP32 && o.precision != HOMG_PREC_BF16) ||
         (o.cycle != HOMG_CYCLE_HOMG && o.cycle != HOMG_CYCLE_V) || o.v_pre < 0 || o.v_post < 0 || o.v_pre > 64 ||
         o.v_post > 64 || (o.cycle == HOMG_CYCLE_V && (o.n_schedule > 0 || o.exec_mode == HOMG_EXEC_WHOLEGRID)) ||
@@ -1030,6 +1031,8 @@ int homg_create(int ndim, const int64_t* dims, int levels, int stencil, const ho
     if (levels < 1 || levels > K) return fail(nullptr, HOMG_EINVAL, "homg_create: levels must be in [1, K]%s%s");
     int rc = check_options(ndim, o);
     if (rc != HOMG_OK) return rc;
+    if (o.launch_mode == HOMG_LAUNCH_PERSISTENT)
+        return fail(nullptr, HOMG_EINVAL, "homg_create: the persistent launch mode is for batches (homg_batch_create)%s%s");
     homg_ctx* h = nullptr;
     rc = create_ctx(ndim, dims[0] - 1, K, levels, stencil, o, 1, &h);
     if (rc != HOMG_OK) return rc;
@@ -1065,6 +1068,15 @@ struct homg_batch_ctx {
     cudaStream_t stream = nullptr;
     homg_batch_stats stats{};
     unsigned int* hticket = nullptr;  // pinned, 4 per group: ticket counters read back after each launch
+    // HOMG_LAUNCH_PERSISTENT: the program of the persistent kernel (items, phases, the groups' coarse
+    // op lists) and its counters, in one device allocation
+    bool persistent = false;
+    int prec = PREC_FP64;
+    char* parena = nullptr;
+    PersistArgs pargs{};
+    size_t nqueue = 0;
+    int pblocks = 0;
+    int* herr = nullptr;  // pinned: the kernel's barrier failure flag, read back after a launch
 };
 
 namespace {
@@ -1146,6 +1158,166 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us,
     return HOMG_OK;
 }
 
+// A group of one problem was planned without batch views (nothing to index). Inside the persistent
+// kernel every op must still skip a problem that has converged, so its ops get the views too.
+void force_views(homg_ctx* h, PersistItem& it) {
+    if (h->nbatch > 1) return;
+    it.it.bst = h->dstate;
+    it.it.nb = 1;
+    it.pr.bst = h->dstate;
+    it.pr.nb = 1;
+    it.rs.bst = h->dstate;
+    it.rs.nb = 1;
+    if (it.kind == PK_RESID) {
+        it.ra.batch = 1;
+        it.ra.nb = 1;
+    }
+}
+
+// The persistent kernel's program: per group the item lists of the initial residual and test, of a
+// cycle with odd and with even stage (the solution buffers alternate), and of the copy-out; phase j
+// of a segment holds item j of every group's list. One device allocation holds the items, the
+// phases, copies of the groups' coarse-lattice op lists (with batch views), the barrier and running
+// counters, the per-phase work counters and the failure flag.
+int build_persistent(homg_batch_ctx* b) {
+    const int G = (int)b->groups.size();
+    std::vector<std::vector<BlockOp>> bops(G);
+    std::vector<size_t> bop_off(G, 0);
+    size_t nbops = 0;
+    for (int g = 0; g < G; ++g) {
+        homg_ctx* h = b->groups[g];
+        bops[g] = h->block_ops;
+        if (h->nbatch <= 1)
+            for (BlockOp& o : bops[g]) {
+                o.it.bst = o.pr.bst = o.rs.bst = h->dstate;
+                o.it.nb = o.pr.nb = o.rs.nb = 1;
+            }
+        bop_off[g] = nbops;
+        nbops += bops[g].size();
+    }
+    // item lists per group; BLOCK items get their op pointer once the allocation exists
+    enum { SEG_INIT = 0, SEG_ODD = 1, SEG_EVEN = 2, SEG_COPY = 3 };
+    std::vector<std::vector<PersistItem>> lists[4];
+    std::vector<std::vector<int>> block_first[4];
+    for (int seg = 0; seg < 4; ++seg) {
+        lists[seg].resize(G);
+        block_first[seg].resize(G);
+    }
+    for (int g = 0; g < G; ++g) {
+        homg_ctx* h = b->groups[g];
+        auto push = [&](int seg, PersistItem it, int bfirst) {
+            force_views(h, it);
+            lists[seg][g].push_back(it);
+            block_first[seg][g].push_back(bfirst);
+        };
+        {
+            PersistItem r, f;
+            persist_resid(resid_args(h, 0), h->n, r);
+            persist_final(fin_args(h, FIN_INIT, nullptr), f);
+            push(SEG_INIT, r, -1);
+            push(SEG_INIT, f, -1);
+        }
+        for (int seg : {SEG_ODD, SEG_EVEN}) {
+            for (auto* part : {&h->partA, &h->partB})
+                for (const Op& op : *part) {
+                    PersistItem it;
+                    int bf = -1;
+                    switch (op.kind) {
+                        case Op::ITER: persist_iter(op.it, it); break;
+                        case Op::ITER2: persist_iter2(op.sweeps, op.it, it); break;
+                        case Op::PROLONG: persist_prolong(op.pr, it); break;
+                        case Op::RESTRICT: persist_restrict(op.rs, it); break;
+                        case Op::BLOCK:
+                            persist_block(nullptr, op.block_count, h->nbatch, it);
+                            bf = (int)(bop_off[g] + (size_t)op.block_first);
+                            break;
+                        default: return fail(nullptr, HOMG_EINVAL, "homg_batch_create: op without a persistent form%s%s");
+                    }
+                    push(seg, it, bf);
+                }
+            PersistItem r, f;
+            persist_resid(resid_args(h, seg == SEG_ODD ? 1 : 2), h->n, r);
+            persist_final(fin_args(h, FIN_CYCLE, nullptr), f);
+            push(seg, r, -1);
+            push(seg, f, -1);
+        }
+        PersistItem c;
+        persist_copy(copy_args(h), h->n, c);
+        push(SEG_COPY, c, -1);
+    }
+    // merge: phase j of a segment = item j of every group that has one
+    std::vector<PersistItem> items;
+    std::vector<int> item_bfirst;
+    std::vector<PersistPhase> phases;
+    int seg_first[4], seg_count[4];
+    for (int seg = 0; seg < 4; ++seg) {
+        size_t len = 0;
+        for (int g = 0; g < G; ++g) len = std::max(len, lists[seg][g].size());
+        seg_first[seg] = (int)phases.size();
+        seg_count[seg] = (int)len;
+        for (size_t j = 0; j < len; ++j) {
+            PersistPhase ph{(int)items.size(), 0, 0};
+            for (int g = 0; g < G; ++g) {
+                if (j >= lists[seg][g].size()) continue;
+                const PersistItem& it = lists[seg][g][j];
+                items.push_back(it);
+                item_bfirst.push_back(block_first[seg][g][j]);
+                ph.count += 1;
+                ph.blocks += it.gx * it.gy * it.gz;
+            }
+            phases.push_back(ph);
+        }
+    }
+    if (seg_count[SEG_ODD] != seg_count[SEG_EVEN])
+        return fail(nullptr, HOMG_EINVAL, "homg_batch_create: cycle programs of unequal length%s%s");
+    b->nqueue = (size_t)seg_count[SEG_INIT] + (size_t)HOMG_MAX_CYCLES * seg_count[SEG_ODD] + (size_t)seg_count[SEG_COPY];
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = (size_t)round_up((int64_t)off, 256); size_t o = off; off += bytes; return o; };
+    const size_t o_items = take(items.size() * sizeof(PersistItem));
+    const size_t o_phases = take(phases.size() * sizeof(PersistPhase));
+    const size_t o_bops = take(std::max<size_t>(nbops, 1) * sizeof(BlockOp));
+    const size_t o_sync = take(8 * sizeof(unsigned int));
+    const size_t o_err = take(sizeof(int));
+    const size_t o_queue = take(b->nqueue * sizeof(unsigned int));
+    CK(nullptr, cudaMalloc(&b->parena, (size_t)round_up((int64_t)off, 256)), "allocating the persistent program");
+    CK(nullptr, cudaMallocHost(&b->herr, sizeof(int)), "cudaMallocHost");
+    BlockOp* dbops = (BlockOp*)(b->parena + o_bops);
+    for (size_t q = 0; q < items.size(); ++q)
+        if (item_bfirst[q] >= 0) items[q].ops = dbops + item_bfirst[q];
+    for (int g = 0; g < G; ++g)
+        if (!bops[g].empty())
+            CK(nullptr, cudaMemcpy(dbops + bop_off[g], bops[g].data(), bops[g].size() * sizeof(BlockOp), cudaMemcpyHostToDevice),
+               "uploading the persistent program");
+    CK(nullptr, cudaMemcpy(b->parena + o_items, items.data(), items.size() * sizeof(PersistItem), cudaMemcpyHostToDevice),
+       "uploading the persistent program");
+    CK(nullptr, cudaMemcpy(b->parena + o_phases, phases.data(), phases.size() * sizeof(PersistPhase), cudaMemcpyHostToDevice),
+       "uploading the persistent program");
+    PersistArgs& a = b->pargs;
+    a.items = (const PersistItem*)(b->parena + o_items);
+    a.phases = (const PersistPhase*)(b->parena + o_phases);
+    a.init_first = seg_first[SEG_INIT];
+    a.init_count = seg_count[SEG_INIT];
+    a.cyc_first[1] = seg_first[SEG_ODD];   // cycle k odd
+    a.cyc_first[0] = seg_first[SEG_EVEN];  // cycle k even
+    a.cyc_count = seg_count[SEG_ODD];
+    a.copy_first = seg_first[SEG_COPY];
+    a.copy_count = seg_count[SEG_COPY];
+    a.sync = (unsigned int*)(b->parena + o_sync);
+    a.err = (int*)(b->parena + o_err);
+    a.queue = (unsigned int*)(b->parena + o_queue);
+    a.timeout_ns = 5000000000LL;
+    b->persistent = true;
+    return HOMG_OK;
+}
+
+// Clear the persistent kernel's counters and failure flag on `s` (before every launch).
+cudaError_t persistent_reset(homg_batch_ctx* b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b->pargs.sync, 0, 8 * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->pargs.err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->pargs.queue, 0, b->nqueue * sizeof(unsigned int), s);
+    return e;
+}
+
 void batch_destroy(homg_batch_ctx* b) {
     for (homg_ctx* h : b->groups) homg_destroy(h);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
@@ -1154,6 +1326,8 @@ void batch_destroy(homg_batch_ctx* b) {
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
     if (b->hticket) cudaFreeHost(b->hticket);
+    if (b->herr) cudaFreeHost(b->herr);
+    if (b->parena) cudaFree(b->parena);
     delete b;
 }
 
@@ -1171,9 +1345,11 @@ int homg_batch_create(int nprob, const int64_t* sides, const homg_options* opt, 
     int rc = check_options(2, o);
     if (rc != HOMG_OK) return rc;
     if (o.strict_fp || o.exec_mode == HOMG_EXEC_WHOLEGRID || o.n_schedule > 0 || o.cycle != HOMG_CYCLE_HOMG ||
-        o.launch_mode != HOMG_LAUNCH_GRAPH || o.geometry != HOMG_GEOM_NESTED)
+        o.launch_mode == HOMG_LAUNCH_STREAM || o.geometry != HOMG_GEOM_NESTED)
         return fail(nullptr, HOMG_EINVAL,
-                    "homg_batch_create: batches use fast arithmetic, the lattice form, MFMG and graph launches%s%s");
+                    "homg_batch_create: batches use fast arithmetic, the lattice form, MFMG and graph or persistent launches%s%s");
+    const bool persistent = o.launch_mode == HOMG_LAUNCH_PERSISTENT;
+    o.launch_mode = HOMG_LAUNCH_GRAPH;  // the groups themselves are planned as for graph launches
     std::vector<int64_t> distinct;
     std::vector<int> group_of(nprob), index_in_group(nprob);
     std::vector<int> counts;
@@ -1239,6 +1415,14 @@ int homg_batch_create(int nprob, const int64_t* sides, const homg_options* opt, 
         b->stats.rows[g] = rows;
         b->stats.tuned_us[g] = us;
     }
+    b->prec = o.precision;
+    if (persistent) {
+        rc = build_persistent(b);
+        if (rc != HOMG_OK) {
+            batch_destroy(b);
+            return rc;
+        }
+    }
     *out = b;
     return HOMG_OK;
 }
@@ -1262,6 +1446,43 @@ int homg_batch_solve(homg_batch_handle b, const double* const* f, double* const*
     cudaError_t e = cudaEventRecord(b->t0, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
     if (e != cudaSuccess) return cfail(e, "homg_batch_solve");
+    if (b->persistent) {
+        // one cooperative launch on the caller's stream: states in, the kernel, states out
+        for (int g = 0; g < G; ++g) {
+            homg_ctx* h = b->groups[g];
+            for (int q = 0; q < h->nbatch; ++q) memset(&h->hstate[q], 0, sizeof(State));
+        }
+        for (int p = 0; p < b->nprob; ++p) {
+            homg_ctx* h = b->groups[b->group_of[p]];
+            State& st = h->hstate[b->index_in_group[p]];
+            st.f = f[p];
+            st.u = u[p];
+            st.tol = tol;
+            st.div_factor = h->opt.diverge_factor;
+            st.max_cycles = max_cycles;
+            st.status = -1;
+        }
+        for (int g = 0; g < G && e == cudaSuccess; ++g) {
+            homg_ctx* h = b->groups[g];
+            e = cudaMemcpyAsync(h->dstate, h->hstate, (size_t)h->nbatch * sizeof(State), cudaMemcpyHostToDevice, b->stream);
+        }
+        if (e == cudaSuccess) e = persistent_reset(b, b->stream);
+        PersistArgs pa = b->pargs;
+        pa.max_cycles = max_cycles;
+        pa.stall = 0;
+        if (e == cudaSuccess) e = launch_persistent(b->prec, pa, &b->pblocks, b->stream);
+        for (int g = 0; g < G && e == cudaSuccess; ++g) {
+            homg_ctx* h = b->groups[g];
+            e = cudaMemcpyAsync(h->hstate, h->dstate, (size_t)h->nbatch * sizeof(State), cudaMemcpyDeviceToHost, b->stream);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->herr, b->pargs.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b->t1);
+        if (e != cudaSuccess) return cfail(e, "homg_batch_solve: the persistent kernel");
+        b->stats.solve_ms = elapsed(b->t0, b->t1);
+        if (*b->herr)
+            return fail(nullptr, HOMG_TIMEOUT, "homg_batch_solve: a grid barrier of the persistent kernel gave up%s%s");
+    } else {
     const int want = std::min(std::max(max_cycles, 1), kStagesPerGraph);
     for (int g = 0; g < G; ++g) {
         homg_ctx* h = b->groups[g];
@@ -1335,6 +1556,7 @@ int homg_batch_solve(homg_batch_handle b, const double* const* f, double* const*
     if (e == cudaSuccess) e = cudaEventSynchronize(b->t1);
     if (e != cudaSuccess) return cfail(e, "homg_batch_solve");
     b->stats.solve_ms = elapsed(b->t0, b->t1);
+    }
     int worst = HOMG_OK;
     for (int p = 0; p < b->nprob; ++p) {
         const State& st = b->groups[b->group_of[p]]->hstate[b->index_in_group[p]];
@@ -1345,6 +1567,28 @@ int homg_batch_solve(homg_batch_handle b, const double* const* f, double* const*
         if (st.status > worst) worst = st.status;
     }
     return worst;
+}
+
+int homg_batch_check_barrier_timeout(homg_batch_handle b, double* waited_ms) {
+    if (!b) return HOMG_EINVAL;
+    if (!b->persistent)
+        return fail(nullptr, HOMG_EINVAL, "homg_batch_check_barrier_timeout: the batch has no persistent kernel%s%s");
+    PersistArgs pa = b->pargs;
+    pa.stall = 1;  // the first barrier waits for one block more than the launch has
+    pa.timeout_ns = 250000000LL;
+    pa.max_cycles = 0;
+    cudaError_t e = persistent_reset(b, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->t0, b->stream);
+    int blocks = 0;
+    if (e == cudaSuccess) e = launch_persistent(b->prec, pa, &blocks, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->herr, b->pargs.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "homg_batch_check_barrier_timeout");
+    if (waited_ms) *waited_ms = elapsed(b->t0, b->t1);
+    if (*b->herr)
+        return fail(nullptr, HOMG_TIMEOUT, "homg_batch_check_barrier_timeout: the grid barrier gave up after its time limit%s%s");
+    return HOMG_OK;
 }
 
 int homg_batch_get_stats(homg_batch_handle b, homg_batch_stats* out) {

@@ -216,6 +216,74 @@ struct BlockOp {
     RestrictArgs rs;
 };
 
+// ---- persistent batch kernel ------------------------------------------------------------------
+// One cooperative launch runs a whole batch: every size group's cycle is a list of ops (the same
+// ops its graph launches), and phase j of the launch holds op j of every group. A phase's work is a
+// queue of (op, problem, tile) items, the op's blocks over all of its group's problems, which the
+// resident blocks draw from a counter; a grid barrier separates phases.
+enum PersistKind {
+    PK_ITER = 0,      // marching damped-Jacobi sweep (sub = 2 * pending mode + variation stored)
+    PK_ITER2 = 1,     // two fused plain sweeps
+    PK_ITER4 = 2,     // four fused plain sweeps
+    PK_ITERG = 3,     // generic HOMG iteration (tiles of BX x BY nodes)
+    PK_PROLONG2 = 4,  // stride-2 level change (marching)
+    PK_PROLONG = 5,   // generic level change (tiles)
+    PK_RESTRICT = 6,  // full weighting (tiles)
+    PK_BLOCK = 7,     // coarse-lattice op list, one block per problem
+    PK_RESID = 8,     // update + residual + source + norm partials
+    PK_FINAL = 9,     // convergence test, one block per problem
+    PK_COPY = 10      // copy-out (tiles)
+};
+
+struct PersistItem {
+    int kind = 0;
+    int sub = 0;
+    int rows = 0;               // nodes per thread along the march
+    int n = 0;                  // PK_RESID, PK_COPY: intervals per side
+    int gx = 1, gy = 1, gz = 1; // the op's blocks (gz: problems of the group)
+    int nops = 0;               // PK_BLOCK
+    const BlockOp* ops = nullptr;
+    IterArgs it;
+    ProlongArgs pr;
+    RestrictArgs rs;
+    ResidArgs ra;
+    FinalizeArgs fa;
+    CopyOutArgs co;
+};
+
+struct PersistPhase {
+    int first, count;  // items
+    int blocks;        // their blocks in total
+};
+
+struct PersistArgs {
+    const PersistItem* items = nullptr;
+    const PersistPhase* phases = nullptr;
+    int init_first = 0, init_count = 0;  // initial residual and test
+    int cyc_first[2] = {0, 0};           // a cycle of even / odd stage
+    int cyc_count = 0;
+    int copy_first = 0, copy_count = 0;
+    int max_cycles = 0;
+    unsigned int* sync = nullptr;        // [0] arrivals, [1] generation, [2..4] running problems (rotating)
+    unsigned int* queue = nullptr;       // one work counter per phase executed, zero at launch
+    int* err = nullptr;                  // 1 when a grid barrier gave up
+    long long timeout_ns = 0;            // longest wait at one grid barrier
+    int stall = 0;                       // self-test: the first barrier waits for one block more than exist
+};
+
+// Item builders (the same kernels and launch shapes as the graph launches of launch_iterate & co.)
+void persist_iter(const IterArgs& a, PersistItem& it);
+void persist_iter2(int sweeps, const IterArgs& a, PersistItem& it);
+void persist_prolong(const ProlongArgs& a, PersistItem& it);
+void persist_restrict(const RestrictArgs& a, PersistItem& it);
+void persist_block(const BlockOp* ops, int nops, int nb, PersistItem& it);
+void persist_resid(const ResidArgs& a, int n, PersistItem& it);
+void persist_final(const FinalizeArgs& a, PersistItem& it);
+void persist_copy(const CopyOutArgs& a, int n, PersistItem& it);
+// Cooperative launch of the persistent kernel for storage precision prec: as many blocks as can be
+// resident on the device at once (*blocks receives the count).
+cudaError_t launch_persistent(int prec, const PersistArgs& a, int* blocks, cudaStream_t s);
+
 // Launchers (enqueue on `s`; return the launch error). `prec` is the storage precision of the
 // cycle arrays (Prec); `strict` selects the oracle's canonical operation order.
 cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, cudaStream_t s);

@@ -11,6 +11,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "../../include/homg.h"
 #include "homg_internal.h"
 
@@ -46,6 +48,25 @@ template <> struct St<__nv_bfloat16> {
     // double -> binary32 -> bfloat16, each round-to-nearest (the oracle's storage rounding)
     static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
 };
+
+// Loads of the marching kernels. In their own launches they read through the read-only path
+// (__ldg). Inside the persistent batch kernel (P = true), a phase reads values that other blocks of
+// the same launch wrote in an earlier phase, which the read-only path does not promise to see:
+// those loads go to L2 (__ldcg), the point of coherence, after the grid barrier's fences.
+template <typename T> __device__ __forceinline__ typename St<T>::C ld_cg(const T* p);
+template <> __device__ __forceinline__ double ld_cg<double>(const double* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ld_cg<float>(const float* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ld_cg<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+}
+template <typename T, bool P> __device__ __forceinline__ typename St<T>::C ldv(const T* p) {
+    if constexpr (P) return ld_cg<T>(p);
+    else return St<T>::ld(p);
+}
+template <bool P> __device__ __forceinline__ double ld64(const double* p) {
+    if constexpr (P) return __ldcg(p);
+    else return __ldg(p);
+}
 
 // ---- binary32 <-> binary64 conversions with integer operations ----------------------------------
 // GB300 issues FP64 instructions, conversions to and from binary64 among them, at a small fraction
@@ -659,10 +680,8 @@ __global__ void __launch_bounds__(BX * BY) k_prolong_add(ProlongAddArgs a) {
 // the whole block). Replaces dozens of launches whose cost is pure launch latency.
 // ---------------------------------------------------------------------------------------------
 template <int ND, typename T>
-__global__ void __launch_bounds__(512) k_coarse_block(const BlockOp* __restrict__ ops, int nops) {
-    pdl_begin();
+__device__ __forceinline__ void coarse_block_body(const BlockOp* __restrict__ ops, int nops, int z) {
     const int tid = threadIdx.x;
-    const int z = (ND == 2) ? blockIdx.z : 0;  // batch: one block per problem
     for (int o = 0; o < nops; ++o) {
         const int kind = ops[o].kind;
         RestrictArgs rs = ops[o].rs;
@@ -685,6 +704,12 @@ __global__ void __launch_bounds__(512) k_coarse_block(const BlockOp* __restrict_
     }
 }
 
+template <int ND, typename T>
+__global__ void __launch_bounds__(512) k_coarse_block(const BlockOp* __restrict__ ops, int nops) {
+    pdl_begin();
+    coarse_block_body<ND, T>(ops, nops, (ND == 2) ? (int)blockIdx.z : 0);  // batch: one block per problem
+}
+
 // =============================================================================================
 // Fast kernels (strict_fp = 0).
 // =============================================================================================
@@ -695,7 +720,7 @@ constexpr int JR = 16;   // nodes per thread along the march on large grids
 // this thread's column (the lattice value itself on even columns); a fine row j takes X(j/2) when
 // j is even and the mean of X(j/2) and X(j/2 + 1) when j is odd. X is formed once per coarse row
 // and shared by the two fine rows it touches, and the form is branch-free across a warp.
-template <typename T>
+template <typename T, bool P = false>
 struct ColumnInterp2 {
     using C = typename St<T>::C;
     const T* d;    // compact array, offset to this column's left lattice neighbour
@@ -706,10 +731,10 @@ struct ColumnInterp2 {
     C x0 = 0, x1 = 0;  // X(cj), X(cj + 1)
 
     __device__ __forceinline__ C X(int J) const {
-        C a = St<T>::ld(d + (int64_t)J * pitch), b = St<T>::ld(d + (int64_t)J * pitch + 1);
+        C a = ldv<T, P>(d + (int64_t)J * pitch), b = ldv<T, P>(d + (int64_t)J * pitch + 1);
         if (d2) {
-            a -= St<T>::ld(d2 + (int64_t)J * pitch2);
-            b -= St<T>::ld(d2 + (int64_t)J * pitch2 + 1);
+            a -= ldv<T, P>(d2 + (int64_t)J * pitch2);
+            b -= ldv<T, P>(d2 + (int64_t)J * pitch2 + 1);
         }
         return fma(hx, b - a, a);
     }
@@ -732,15 +757,14 @@ struct ColumnInterp2 {
 // (2-D: along y; 3-D: along z) keeping the centre and its two neighbours along the march in
 // registers; the other neighbours come through L1. In FP64 the FP64 pipe bounds this kernel on
 // GB300; in FP32/bfloat16, DRAM does.
-template <int PEND, bool WD, typename T, bool BATCH>
-__global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
-    pdl_begin();
-    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // compiled into batch launches only
+template <int PEND, bool WD, typename T, bool BATCH, bool P>
+__device__ __forceinline__ void jacobi2_body(IterArgs a, int rows, int bx, int by, int bz) {
+    if (BATCH && !batch_view<T>(a, bz)) return;  // compiled into batch launches only
     using C = typename St<T>::C;
     const int n = a.e_new.n;
-    const int i = blockIdx.x * JX + threadIdx.x + 1;
+    const int i = bx * JX + threadIdx.x + 1;
     if (i >= n) return;
-    const int j0 = blockIdx.y * rows + 1;
+    const int j0 = by * rows + 1;
     const int j1 = min(j0 + rows, n);
     const T* __restrict__ E = cp<T>(a.e_old);
     const int64_t pe = a.e_old.pitch;
@@ -750,7 +774,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
     const int64_t pg = a.g.pitch;
     const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
     const int lpm = PEND ? (1 << a.mp) - 1 : 0;
-    ColumnInterp2<T> ci;
+    ColumnInterp2<T, P> ci;
     if (PEND == 1) {
         ci.d = cp<T>(a.dprev) + (i >> 1);
         ci.d2 = nullptr;
@@ -758,14 +782,14 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
         ci.pitch2 = 0;
         ci.hx = (i & 1) ? (C)0.5 : (C)0;
     }
-    C vs = St<T>::ld(E + (int64_t)(j0 - 1) * pe + i);
-    C vc = St<T>::ld(E + (int64_t)j0 * pe + i);
+    C vs = ldv<T, P>(E + (int64_t)(j0 - 1) * pe + i);
+    C vc = ldv<T, P>(E + (int64_t)j0 * pe + i);
 #pragma unroll 4
     for (int j = j0; j < j1; ++j) {
         const T* row = E + (int64_t)j * pe + i;
-        const C vn = St<T>::ld(row + pe);
-        const C w = St<T>::ld(row - 1), e = St<T>::ld(row + 1);
-        const C g = St<T>::ld(G + (int64_t)j * pg + i);
+        const C vn = ldv<T, P>(row + pe);
+        const C w = ldv<T, P>(row - 1), e = ldv<T, P>(row + 1);
+        const C g = ldv<T, P>(G + (int64_t)j * pg + i);
         C v = jacobi_update(c1, om, vc, g, w, e, vs, vn);
         if (WD) wp<T>(a.dnew)[(int64_t)j * a.dnew.pitch + i] = St<T>::put(v - vc);
         if (PEND == 1) {
@@ -777,6 +801,12 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
         vs = vc;
         vc = vn;
     }
+}
+
+template <int PEND, bool WD, typename T, bool BATCH>
+__global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
+    pdl_begin();
+    jacobi2_body<PEND, WD, T, BATCH, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Coefficient storage of the variable-coefficient kernels: double for FP64 cycles, float otherwise.
@@ -909,20 +939,19 @@ template <> __device__ __forceinline__ float as_c<__nv_bfloat16>(__nv_bfloat16 x
 // in flight. Per node and pair of sweeps this reads e and g once and writes e once (12 B instead
 // of 24 in FP32), and the result is bit-identical to two single sweeps.
 constexpr int X2_OUT = 30;  // output columns per warp
-template <typename T, bool BATCH>
-__global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
-    pdl_begin();
-    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
+template <typename T, bool BATCH, bool P>
+__device__ __forceinline__ void jacobi2_x2_body(IterArgs a, int rows, int bx, int by, int bz) {
+    if (BATCH && !batch_view<T>(a, bz)) return;  // uniform over the block
     using C = typename St<T>::C;
     const int n = a.e_new.n;
     const int lane = threadIdx.x & 31;
-    const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
+    const int strip = bx * (JX / 32) + (threadIdx.x >> 5);
     if (strip * X2_OUT + 1 > n - 1) return;  // strip past the last column: the whole warp leaves
     const int i = strip * X2_OUT + lane;     // first-sweep column
     const bool col_in = i >= 1 && i <= n - 1;
     const bool out = col_in && lane >= 1 && lane <= X2_OUT;
     const int il = min(max(i, 1), n - 1);    // lanes outside the interior load from inside, keep 0
-    const int j0 = blockIdx.y * rows + 1;    // second sweep: rows j0 .. j1 - 1
+    const int j0 = by * rows + 1;    // second sweep: rows j0 .. j1 - 1
     const int j1 = min(j0 + rows, n);
     const int r0 = j0 - 1;                   // first sweep: rows r0 .. j1 (0 on rows 0 and n)
     const int64_t pe = a.e_old.pitch, pg = a.g.pitch, po = a.e_new.pitch;
@@ -931,11 +960,11 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
     const T* __restrict__ pG = cp<T>(a.g) + (int64_t)ra * pg + il;
     T* __restrict__ pO = wp<T>(a.e_new) + (int64_t)j0 * po + i;         // next output row
     const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
-    C em = St<T>::ld(pE - pe), ec = St<T>::ld(pE);  // input iterate at rows r - 1, r
+    C em = ldv<T, P>(pE - pe), ec = ldv<T, P>(pE);  // input iterate at rows r - 1, r
     // first sweep at row r (1 <= r <= n - 1), then advance the march one row
     auto first = [&](C& g) -> C {
-        const C ep = St<T>::ld(pE + pe), w = St<T>::ld(pE - 1), e = St<T>::ld(pE + 1);
-        g = St<T>::ld(pG);
+        const C ep = ldv<T, P>(pE + pe), w = ldv<T, P>(pE - 1), e = ldv<T, P>(pE + 1);
+        g = ldv<T, P>(pG);
         const C sum = (w + e) + (em + ep);
         const C v = as_c<T>(St<T>::put(fma(c1, ec, fma(om, sum, g))));
         em = ec;
@@ -972,6 +1001,12 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
     if (j1 == n) second((C)0);  // the first-sweep value on the boundary row n is 0
 }
 
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
+    pdl_begin();
+    jacobi2_x2_body<T, BATCH, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // K plain damped-Jacobi sweeps in one pass (K >= 3; binary32 arithmetic), the K-level form of
 // k_jacobi2_x2: each warp marches a strip of 32 columns; step r computes sweep 1 at row r, sweep 2
 // at row r - 1, ..., sweep K at row r - K + 1 (the output), each from the previous sweep's values
@@ -979,21 +1014,20 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
 // storage type as a stored sweep would be. A strip outputs its 34 - 2K inner columns; a block's
 // march starts K - 1 rows above its output rows and ends K - 1 below. Sweep values on the boundary
 // rows and columns are 0. Per node and K sweeps this reads e and g once and writes e once.
-template <typename T, bool BATCH, int K>
-__global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
-    pdl_begin();
-    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
+template <typename T, bool BATCH, int K, bool P>
+__device__ __forceinline__ void jacobi2_xk_body(IterArgs a, int rows, int bx, int by, int bz) {
+    if (BATCH && !batch_view<T>(a, bz)) return;  // uniform over the block
     using C = typename St<T>::C;
     constexpr int OUTK = 34 - 2 * K;
     const int n = a.e_new.n;
     const int lane = threadIdx.x & 31;
-    const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
+    const int strip = bx * (JX / 32) + (threadIdx.x >> 5);
     if (strip * OUTK + 1 > n - 1) return;        // strip past the last column: the whole warp leaves
     const int i = strip * OUTK + lane - (K - 2);  // this lane's column
     const bool col_in = i >= 1 && i <= n - 1;
     const bool out = col_in && lane >= K - 1 && lane <= 32 - K;
     const int il = min(max(i, 1), n - 1);  // lanes outside the interior load from inside, keep 0
-    const int j0 = blockIdx.y * rows + 1;  // output rows j0 .. j1 - 1
+    const int j0 = by * rows + 1;  // output rows j0 .. j1 - 1
     const int j1 = min(j0 + rows, n);
     const int64_t pe = a.e_old.pitch, pg = a.g.pitch, po = a.e_new.pitch;
     const T* __restrict__ E0 = cp<T>(a.e_old) + il;
@@ -1004,7 +1038,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
     // issue several rows of loads ahead; values on rows outside 1..n-1 are then replaced by 0.
     auto rowE = [&](int row) { return E0 + (int64_t)min(max(row, 0), n) * pe; };
     const int rf = j0 - (K - 1), rl = j1 + K - 2;  // sweep-1 rows of the march
-    C em = St<T>::ld(rowE(rf - 1)), ec = St<T>::ld(rowE(rf));  // input iterate at rows r - 1, r (exact where used)
+    C em = ldv<T, P>(rowE(rf - 1)), ec = ldv<T, P>(rowE(rf));  // input iterate at rows r - 1, r (exact where used)
     C sp[K], sc[K], gq[K];  // sweep l (1..K-1) at rows x - 1, x of sweep l + 1's row x; g at rows r .. r - K + 1
 #pragma unroll
     for (int l = 0; l < K; ++l) sp[l] = sc[l] = gq[l] = 0;
@@ -1012,8 +1046,8 @@ __global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
     for (int r = rf; r <= rl; ++r) {
         C v[K + 1];
         const T* p = rowE(r);
-        const C ep = St<T>::ld(rowE(r + 1)), w = St<T>::ld(p - 1), e = St<T>::ld(p + 1);
-        const C g = St<T>::ld(G0 + (int64_t)min(max(r, 0), n) * pg);
+        const C ep = ldv<T, P>(rowE(r + 1)), w = ldv<T, P>(p - 1), e = ldv<T, P>(p + 1);
+        const C g = ldv<T, P>(G0 + (int64_t)min(max(r, 0), n) * pg);
         {
             const C y = as_c<T>(St<T>::put(fma(c1, ec, fma(om, (w + e) + (em + ep), g))));
             v[1] = (col_in && r >= 1 && r <= n - 1) ? y : (C)0;
@@ -1039,20 +1073,25 @@ __global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
     }
 }
 
+template <typename T, bool BATCH, int K>
+__global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
+    pdl_begin();
+    jacobi2_xk_body<T, BATCH, K, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
 // stride-2 interpolant of Gc - dl, formed along each marching column (see ColumnInterp2).
-template <typename T, bool BATCH>
-__global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
-    pdl_begin();
-    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // compiled into batch launches only
+template <typename T, bool BATCH, bool P>
+__device__ __forceinline__ void prolong2_s1_body(ProlongArgs a, int rows, int bx, int by, int bz) {
+    if (BATCH && !batch_view<T>(a, bz)) return;  // compiled into batch launches only
     using C = typename St<T>::C;
     const int n = a.G.n;
-    const int i = blockIdx.x * JX + threadIdx.x + 1;
+    const int i = bx * JX + threadIdx.x + 1;
     if (i >= n) return;
-    const int j0 = blockIdx.y * rows + 1;
+    const int j0 = by * rows + 1;
     const int j1 = min(j0 + rows, n);
     const bool iodd = i & 1;
-    ColumnInterp2<T> ci;
+    ColumnInterp2<T, P> ci;
     ci.d = cp<T>(a.Gc) + (i >> 1);
     ci.d2 = cp<T>(a.dl) + (i >> 1);
     ci.pitch = a.Gc.pitch;
@@ -1060,11 +1099,16 @@ __global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
     ci.hx = iodd ? (C)0.5 : (C)0;
     for (int j = j0; j < j1; ++j) {
         C v = ci.at(j);
-        if (!(j & 1) && !iodd) v = St<T>::ld(cp<T>(a.Gc) + (int64_t)(j >> 1) * a.Gc.pitch + (i >> 1));
+        if (!(j & 1) && !iodd) v = ldv<T, P>(cp<T>(a.Gc) + (int64_t)(j >> 1) * a.Gc.pitch + (i >> 1));
         wp<T>(a.G)[(int64_t)j * a.G.pitch + i] = St<T>::put(v);
     }
 }
 
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
+    pdl_begin();
+    prolong2_s1_body<T, BATCH, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
+}
 
 // Fast V-cycle kernels (2-D, column marching): level residual rho = g + omega (sum - 4 v) in 5
 // instructions per node, and the stride-2 prolongation-add e += P ec with the x-interpolant shared
@@ -1354,17 +1398,16 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
 // source to the cycle's storage use the integer conversions above. Results are bit-identical to
 // forming every neighbour locally.
 constexpr int RS_OUT = 30;  // nodes per warp strip
-template <typename T, bool VC, bool BATCH>
-__global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
-    pdl_begin();
-    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
+template <typename T, bool VC, bool BATCH, bool P>
+__device__ __forceinline__ void residual2_fast_body(ResidArgs a, int n, int bx, int by, int bz, int gx) {
+    if (BATCH && !batch_view<T>(a, bz)) return;  // uniform over the block
     __shared__ double sh[JX / 32];
     const int lane = threadIdx.x & 31;
-    const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
+    const int strip = bx * (JX / 32) + (threadIdx.x >> 5);
     const int i = strip * RS_OUT + lane;  // this lane's column
     const bool col_in = i >= 1 && i <= n - 1;
     const bool active = col_in && lane >= 1 && lane <= RS_OUT;
-    const int j0 = blockIdx.y * JR + 1;
+    const int j0 = by * JR + 1;
     const int j1 = min(j0 + JR, n);
     const bool upd = a.e.p != nullptr;
     const double* __restrict__ U = a.u_in.p ? a.u_in.p : a.st->u;
@@ -1379,8 +1422,8 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
     const double one = a.one;
     auto un = [&](int jj) -> double {  // updated iterate at (i, jj); 0 on the boundary and outside
         if (!col_in || jj <= 0 || jj >= n) return 0.0;
-        double v = __ldg(U + (int64_t)jj * pu + i);
-        if (upd) v = fma(one, v, to_d(St<T>::ld(Ev + (int64_t)jj * pe + i)));
+        double v = ld64<P>(U + (int64_t)jj * pu + i);
+        if (upd) v = fma(one, v, to_d(ldv<T, P>(Ev + (int64_t)jj * pe + i)));
         return v;
     };
     double rr = 0.0, ff = 0.0;
@@ -1414,13 +1457,19 @@ __global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
         vs = vc;
         vc = vn;
     }
-    const int bid = blockIdx.x + gridDim.x * blockIdx.y;
+    const int bid = bx + gx * by;
     double t = block_sum(rr, sh);
     if (threadIdx.x == 0) a.part_r[bid] = t;
     if (a.part_f) {
         t = block_sum(ff, sh);
         if (threadIdx.x == 0) a.part_f[bid] = t;
     }
+}
+
+template <typename T, bool VC, bool BATCH>
+__global__ void __launch_bounds__(JX) k_residual2_fast(ResidArgs a, int n) {
+    pdl_begin();
+    residual2_fast_body<T, VC, BATCH, false>(a, n, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x);
 }
 
 // =============================================================================================
@@ -1726,6 +1775,182 @@ cudaError_t restrict_t(int ndim, bool strict, const RestrictArgs& a, cudaStream_
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Persistent batch kernel (see PersistArgs): one cooperative launch runs every size group's cycles.
+// ---------------------------------------------------------------------------------------------
+
+// Grid barrier with a bounded wait. Thread 0 of each block arrives (release fence, then the arrival
+// counter); the last block to arrive resets the counter and advances the generation; the others poll
+// the generation until it moves, another block has given up, or timeout_ns has passed, and then
+// fence (acquire) so that the next phase sees every block's writes of this one. On timeout the
+// block records the failure in *err; false tells the caller to leave the kernel. Every wait is
+// bounded, so the launch ends whatever another block does.
+__device__ bool grid_barrier(const PersistArgs& P, unsigned int target) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = P.sync + 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(P.sync, 1u) + 1u;
+        int ok = 1;
+        if (arrived == target) {
+            atomicExch(P.sync, 0u);
+            __threadfence();
+            atomicAdd(P.sync + 1, 1u);
+        } else {
+            const long long t0 = device_clock_ns();
+            while (*gen == g) {
+                if (*(volatile int*)P.err) { ok = 0; break; }
+                if (device_clock_ns() - t0 > P.timeout_ns) { atomicExch(P.err, 1); ok = 0; break; }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+// Convergence test of problem z of a group (the batch finalize's per-problem part); counts the
+// problems still running into *running.
+__device__ void finalize_problem(const FinalizeArgs& a, int z, unsigned int* running) {
+    __shared__ double sh[JX / 32];
+    State* st = a.st + z;
+    double* hist = a.hist + (int64_t)z * a.hist_bstride;
+    const double* pr = a.part_r + (int64_t)z * a.part_bstride;
+    const double* pf = a.part_f ? a.part_f + (int64_t)z * a.part_bstride : nullptr;
+    const bool skip = a.mode == FIN_CYCLE && st->done;
+    if (!skip) {
+        double sr = 0.0, sf = 0.0;
+        for (int t = threadIdx.x; t < a.nparts; t += blockDim.x) {
+            sr += pr[t];
+            if (pf) sf += pf[t];
+        }
+        sr = block_sum(sr, sh);
+        if (pf) sf = block_sum(sf, sh);
+        if (threadIdx.x == 0) finalize_decide(a, st, hist, sr, sf);
+    }
+    if (threadIdx.x == 0 && !st->done) atomicAdd(running, 1u);
+}
+
+// One block of one op: block r of the op's gx x gy x gz blocks. The marching ops run their own
+// kernels' bodies; the tiled ops (BX x BY nodes) take two passes of the JX threads.
+template <typename T>
+__device__ void run_item(const PersistItem& I, int r, unsigned int* running) {
+    const int bx = r % I.gx, by = (r / I.gx) % I.gy, bz = r / (I.gx * I.gy);
+    constexpr bool B32 = !std::is_same<T, double>::value;  // fused sweeps: binary32 cycles only
+    switch (I.kind) {
+        case PK_ITER:
+            switch (I.sub) {
+                case 0: jacobi2_body<0, false, T, true, true>(I.it, I.rows, bx, by, bz); break;
+                case 1: jacobi2_body<0, true, T, true, true>(I.it, I.rows, bx, by, bz); break;
+                case 2: jacobi2_body<1, false, T, true, true>(I.it, I.rows, bx, by, bz); break;
+                case 3: jacobi2_body<1, true, T, true, true>(I.it, I.rows, bx, by, bz); break;
+                case 4: jacobi2_body<2, false, T, true, true>(I.it, I.rows, bx, by, bz); break;
+                default: jacobi2_body<2, true, T, true, true>(I.it, I.rows, bx, by, bz); break;
+            }
+            break;
+        case PK_ITER2:
+            if constexpr (B32) jacobi2_x2_body<T, true, true>(I.it, I.rows, bx, by, bz);
+            break;
+        case PK_ITER4:
+            if constexpr (B32) jacobi2_xk_body<T, true, 4, true>(I.it, I.rows, bx, by, bz);
+            break;
+        case PK_PROLONG2: prolong2_s1_body<T, true, true>(I.pr, I.rows, bx, by, bz); break;
+        case PK_BLOCK: coarse_block_body<2, T>(I.ops, I.nops, bz); break;
+        case PK_RESID: residual2_fast_body<T, false, true, true>(I.ra, I.n, bx, by, bz, I.gx); break;
+        case PK_FINAL: finalize_problem(I.fa, bz, running); break;
+        default: {  // tiled ops
+            IterArgs it = I.it;
+            ProlongArgs pr = I.pr;
+            RestrictArgs rs = I.rs;
+            bool live = true;
+            int side = 0;
+            if (I.kind == PK_ITERG) { live = batch_view<T>(it, bz); side = it.e_new.n; }
+            else if (I.kind == PK_PROLONG) { live = batch_view<T>(pr, bz); side = pr.G.n; }
+            else if (I.kind == PK_RESTRICT) { live = batch_view<T>(rs, bz); side = rs.gc.n; }
+            else side = I.n;
+            if (!live) break;
+            for (int pass = 0; pass < BY * BX / JX; ++pass) {
+                const int i = bx * BX + (threadIdx.x & (BX - 1)) + 1;
+                const int j = by * BY + (threadIdx.x / BX) + pass * (JX / BX) + 1;
+                if (i >= side || j >= side) continue;
+                if (I.kind == PK_ITERG) iterate_point<2, false, T>(it, i, j, 0);
+                else if (I.kind == PK_PROLONG) prolong_point<2, false, T>(pr, i, j, 0);
+                else if (I.kind == PK_RESTRICT) restrict_point<2, false, T>(rs, i, j, 0);
+                else {  // PK_COPY (see k_copy_out)
+                    const State* st = I.co.st;
+                    CDGrid u0 = I.co.u0, u1 = I.co.u1;
+                    if (I.co.batch) {
+                        st += bz;
+                        shift(u0, bz);
+                        shift(u1, bz);
+                    }
+                    double v = 0.0;
+                    if (!st->zero_u) {
+                        const CDGrid src = (st->cycle & 1) ? u1 : u0;
+                        v = src.p[at(src.pitch, side, i, j, 0)];
+                    }
+                    st->u[at(side + 1, side, i, j, 0)] = v;
+                }
+            }
+        }
+    }
+}
+
+// The work queue of one phase: blocks draw item blocks from the phase's counter until none is left.
+template <typename T>
+__device__ void run_phase(const PersistArgs& P, const PersistPhase& ph, unsigned int* counter, unsigned int* running) {
+    __shared__ int t_sh;
+    for (;;) {
+        if (threadIdx.x == 0) t_sh = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int t = t_sh;
+        __syncthreads();
+        if (t >= ph.blocks) return;
+        int r = t, q = ph.first;
+        for (;; ++q) {
+            const int nb = P.items[q].gx * P.items[q].gy * P.items[q].gz;
+            if (r < nb) break;
+            r -= nb;
+        }
+        run_item<T>(P.items[q], r, running);
+        __syncthreads();  // the bodies' shared memory is reused by the next item
+    }
+}
+
+// Runs `count` phases from `first`; false when a grid barrier gave up.
+template <typename T>
+__device__ bool run_segment(const PersistArgs& P, int first, int count, unsigned int& gp, unsigned int target,
+                            unsigned int* running) {
+    for (int q = 0; q < count; ++q) {
+        run_phase<T>(P, P.phases[first + q], P.queue + gp++, running);
+        if (!grid_barrier(P, target)) return false;
+    }
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(JX, 4) k_batch_persistent(PersistArgs P) {
+    const unsigned int target = gridDim.x + (P.stall ? 1u : 0u);
+    if (P.stall) {  // self-test: a barrier that cannot complete, before any problem data is touched
+        grid_barrier(P, target);
+        return;
+    }
+    unsigned int gp = 0;
+    unsigned int* cnt = P.sync + 2;  // running problems after the test of cycle k: cnt[k % 3]
+    if (!run_segment<T>(P, P.init_first, P.init_count, gp, target, cnt)) return;
+    if (*(volatile unsigned int*)cnt == 0u) P.max_cycles = 0;  // nothing to solve
+    for (int k = 1; k <= P.max_cycles; ++k) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(k + 1) % 3] = 0u;  // counter of cycle k + 1
+        if (!run_segment<T>(P, P.cyc_first[k & 1], P.cyc_count, gp, target, cnt + k % 3)) return;
+        if (*(volatile unsigned int*)(cnt + k % 3) == 0u) break;
+    }
+    run_segment<T>(P, P.copy_first, P.copy_count, gp, target, cnt);
+}
+
 }  // namespace
 
 #define DISPATCH_PREC(prec, CALL)                                    \
@@ -1900,6 +2125,116 @@ cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAdd
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
     launch_k(k_finalize, a.batch ? a.batch : 1, 1024, s, a);
     return cudaGetLastError();
+}
+
+void persist_iter(const IterArgs& a, PersistItem& it) {
+    const int n = a.e_new.n;
+    it.it = a;
+    if (a.m == 0 && a.e_old.p != nullptr) {  // as iterate_t: the marching sweep
+        const int rows = a.rows > 0 ? a.rows : march_rows(2, n, a.nb);
+        const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
+        it.kind = PK_ITER;
+        it.sub = 2 * pend + (a.dnew.p != nullptr ? 1 : 0);
+        it.rows = rows;
+        it.gx = (n - 1 + JX - 1) / JX;
+        it.gy = (n - 1 + rows - 1) / rows;
+    } else {
+        it.kind = PK_ITERG;
+        it.gx = (n - 1 + BX - 1) / BX;
+        it.gy = (n - 1 + BY - 1) / BY;
+    }
+    it.gz = a.nb;
+}
+
+void persist_iter2(int sweeps, const IterArgs& a, PersistItem& it) {
+    const int n = a.e_new.n;
+    const double nodes = (double)a.nb * (double)(n - 1) * (double)(n - 1);
+    const int out = (sweeps == 4) ? 34 - 2 * 4 : X2_OUT;
+    const int rows = a.rows > 0 ? a.rows : (nodes >= 1.0e6 ? (sweeps == 4 ? 32 : 16) : 8);
+    it.it = a;
+    it.kind = (sweeps == 4) ? PK_ITER4 : PK_ITER2;
+    it.rows = rows;
+    it.gx = (((n - 1 + out - 1) / out) + JX / 32 - 1) / (JX / 32);
+    it.gy = (n - 1 + rows - 1) / rows;
+    it.gz = a.nb;
+}
+
+void persist_prolong(const ProlongArgs& a, PersistItem& it) {
+    const int n = a.G.n;
+    it.pr = a;
+    if (a.s == 1) {
+        const int rows = march_rows(2, n, a.nb);
+        it.kind = PK_PROLONG2;
+        it.rows = rows;
+        it.gx = (n - 1 + JX - 1) / JX;
+        it.gy = (n - 1 + rows - 1) / rows;
+    } else {
+        it.kind = PK_PROLONG;
+        it.gx = (n - 1 + BX - 1) / BX;
+        it.gy = (n - 1 + BY - 1) / BY;
+    }
+    it.gz = a.nb;
+}
+
+void persist_restrict(const RestrictArgs& a, PersistItem& it) {
+    it.rs = a;
+    it.kind = PK_RESTRICT;
+    it.gx = (a.gc.n - 1 + BX - 1) / BX;
+    it.gy = (a.gc.n - 1 + BY - 1) / BY;
+    it.gz = a.nb;
+}
+
+void persist_block(const BlockOp* ops, int nops, int nb, PersistItem& it) {
+    it.kind = PK_BLOCK;
+    it.ops = ops;
+    it.nops = nops;
+    it.gx = it.gy = 1;
+    it.gz = nb;
+}
+
+void persist_resid(const ResidArgs& a, int n, PersistItem& it) {
+    const dim3 g = resid_grid(2, false, n);
+    it.ra = a;
+    it.kind = PK_RESID;
+    it.n = n;
+    it.gx = (int)g.x;
+    it.gy = (int)g.y;
+    it.gz = a.nb;
+}
+
+void persist_final(const FinalizeArgs& a, PersistItem& it) {
+    it.fa = a;
+    it.kind = PK_FINAL;
+    it.gx = it.gy = 1;
+    it.gz = a.batch ? a.batch : 1;
+}
+
+void persist_copy(const CopyOutArgs& a, int n, PersistItem& it) {
+    it.co = a;
+    it.kind = PK_COPY;
+    it.n = n;
+    it.gx = (n - 1 + BX - 1) / BX;
+    it.gy = (n - 1 + BY - 1) / BY;
+    it.gz = a.batch ? a.nb : 1;
+}
+
+template <typename T>
+cudaError_t persistent_t(const PersistArgs& a, int* blocks, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent<T>, JX, 0);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    const int nb = sms * per;
+    if (blocks) *blocks = nb;
+    PersistArgs p = a;
+    void* args[] = {&p};
+    return cudaLaunchCooperativeKernel((const void*)k_batch_persistent<T>, dim3(nb), dim3(JX), args, 0, s);
+}
+
+cudaError_t launch_persistent(int prec, const PersistArgs& a, int* blocks, cudaStream_t s) {
+    DISPATCH_PREC(prec, persistent_t<T>(a, blocks, s));
 }
 
 cudaError_t launch_copy_out(int ndim, const CopyOutArgs& a, int n, cudaStream_t s) {

@@ -15,12 +15,12 @@ LIB_PATH = os.path.join(HERE, "lib", "libhomg.so")
 HOMG_OK, HOMG_NOT_CONVERGED, HOMG_DIVERGED, HOMG_TIMEOUT = 0, 1, 2, 3
 HOMG_EINVAL, HOMG_ESHAPE, HOMG_ECUDA, HOMG_ENOMEM = -1, -2, -3, -4
 HOMG_EXEC_AUTO, HOMG_EXEC_WHOLEGRID, HOMG_EXEC_LATTICE = 0, 1, 2
-HOMG_LAUNCH_GRAPH, HOMG_LAUNCH_STREAM = 0, 1
+HOMG_LAUNCH_GRAPH, HOMG_LAUNCH_STREAM, HOMG_LAUNCH_PERSISTENT = 0, 1, 2
 HOMG_PREC_FP64, HOMG_PREC_FP32, HOMG_PREC_BF16 = 0, 1, 2
 HOMG_MAX_CYCLES = 200
 
 EXEC_MODES = {"auto": HOMG_EXEC_AUTO, "wholegrid": HOMG_EXEC_WHOLEGRID, "lattice": HOMG_EXEC_LATTICE}
-LAUNCH_MODES = {"graph": HOMG_LAUNCH_GRAPH, "stream": HOMG_LAUNCH_STREAM}
+LAUNCH_MODES = {"graph": HOMG_LAUNCH_GRAPH, "stream": HOMG_LAUNCH_STREAM, "persistent": HOMG_LAUNCH_PERSISTENT}
 PRECISIONS = {"fp64": HOMG_PREC_FP64, "fp32": HOMG_PREC_FP32, "bf16": HOMG_PREC_BF16}
 HOMG_CYCLE_HOMG, HOMG_CYCLE_V = 0, 1
 CYCLES = {"homg": HOMG_CYCLE_HOMG, "v": HOMG_CYCLE_V}
@@ -46,6 +46,7 @@ EXPORTS = [
     "homg_batch_solve",
     "homg_batch_get_stats",
     "homg_batch_destroy",
+    "homg_batch_check_barrier_timeout",
     "homg_net_param_count",
     "homg_net_create",
     "homg_net_set_stream",
@@ -174,6 +175,7 @@ def load(path=LIB_PATH):
     lib.homg_batch_set_stream.argtypes = [vp, vp]
     lib.homg_batch_solve.argtypes = [vp, vpp, vpp, ctypes.c_double, ctypes.c_int, ip, ip, dp, dp]
     lib.homg_batch_get_stats.argtypes = [vp, ctypes.POINTER(homg_batch_stats)]
+    lib.homg_batch_check_barrier_timeout.argtypes = [vp, dp]
     lib.homg_batch_destroy.argtypes = [vp]
     lib.homg_batch_destroy.restype = None
     lib.homg_net_destroy.restype = None
@@ -289,6 +291,13 @@ class BatchSolver:
 
     def stats(self):
         return homg_batch_get_stats(self.handle)
+
+    def check_barrier_timeout(self):
+        """Persistent batches: run the grid barrier's failure-path self-test; returns (return code,
+        milliseconds the launch took)."""
+        ms = ctypes.c_double(0.0)
+        rc = load().homg_batch_check_barrier_timeout(self.handle, ctypes.byref(ms))
+        return rc, ms.value
 
     def close(self):
         homg_batch_destroy(self.handle)

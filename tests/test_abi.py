@@ -154,3 +154,11 @@ def test_noalloc_rejects_grids_beyond_its_scratch_on_the_host(homg):
         rc = lib.homg_residual_norm_noalloc(ndim, dims, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(rr), None)
         assert rc == homg.HOMG_ESHAPE
         assert ("needs %d partial sums" % parts) in homg.homg_last_error(None)
+
+
+def test_persistent_launch_mode_is_for_batches_only(homg):
+    with pytest.raises(homg.HomgError) as ei:
+        homg.homg_create(2, 33, 3, launch_mode="persistent")
+    assert ei.value.code == homg.HOMG_EINVAL and "batches" in str(ei.value)
+    lib = homg.load()
+    assert lib.homg_batch_check_barrier_timeout(None, None) == homg.HOMG_EINVAL

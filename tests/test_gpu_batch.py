@@ -172,3 +172,94 @@ def test_batch_iterates_match_oracle(homg, precision):
                 assert err <= BATCH_ITERATE_TOL[precision], (precision, cycles, k, err)
                 if precision == "fp64":
                     assert abs(relres[p] - rhist[-1]) <= 1e-9 * rhist[-1], (cycles, k, relres[p], rhist[-1])
+
+
+def test_persistent_batch_matches_graph_batch(homg):
+    """The persistent kernel runs the same ops with the same arithmetic as the per-group graphs:
+    after a fixed number of cycles the iterates are bit-identical (only the order of the final norm
+    sums differs, so the relative residuals agree to rounding), and a solve to 1e-10 takes the same
+    cycles and ends on the same solution."""
+    import torch
+
+    rng = np.random.default_rng(3)
+    ks = [5, 6, 7, 8, 6, 5, 7, 9, 6, 8, 5, 10]
+    fs_np = [inputs.normal_rhs(2 ** k, 2, seed=int(rng.integers(1 << 30))) for k in ks]
+    sides = [2 ** k + 1 for k in ks]
+    fs = [torch.from_numpy(f).cuda() for f in fs_np]
+    for precision in ("fp32", "fp64", "bf16"):
+        with homg.BatchSolver(sides, precision=precision) as bg, \
+                homg.BatchSolver(sides, precision=precision, launch_mode="persistent") as bp:
+            for tol, cyc in ((0.0, 2), (1e-10, 40)):
+                ug = [torch.zeros_like(f) for f in fs]
+                up = [torch.zeros_like(f) for f in fs]
+                rg = bg.solve(fs, ug, tol=tol, max_cycles=cyc)
+                rp = bp.solve(fs, up, tol=tol, max_cycles=cyc)
+                assert rp[0] == rg[0] and rp[1] == rg[1] and rp[2] == rg[2], (precision, tol, rp[:3], rg[:3])
+                for a, b in zip(rp[3], rg[3]):
+                    assert abs(a - b) <= 1e-12 * b, (precision, a, b)
+                for a, b in zip(up, ug):
+                    assert torch.equal(a, b), precision
+
+
+def test_persistent_batch_iterates_match_oracle(homg):
+    import torch
+
+    import oracle
+
+    oracle.build()
+    ks = [6, 7, 8, 9, 10, 7]
+    fs_np = [inputs.normal_rhs(2 ** k, 2, seed=60 + i) for i, k in enumerate(ks)]
+    fs = [torch.from_numpy(f).cuda() for f in fs_np]
+    with homg.BatchSolver([2 ** k + 1 for k in ks], precision="fp32", launch_mode="persistent") as b:
+        us = [torch.zeros_like(f) for f in fs]
+        rc, status, cyc, relres, _ = b.solve(fs, us, tol=0.0, max_cycles=2)
+        assert cyc == [2] * len(ks)
+        for p, (k, f_np) in enumerate(zip(ks, fs_np)):
+            ref, _, _, _ = oracle.solve_mixed(f_np, k, "fp32", tol=0.0, max_cycles=2)
+            assert _rel(us[p].cpu().numpy(), ref) <= BATCH_ITERATE_TOL["fp32"], k
+        us = [torch.zeros_like(f) for f in fs]
+        rc, status, cyc, relres, ms = b.solve(fs, us, tol=1e-10, max_cycles=40)
+        assert rc == homg.HOMG_OK and all(t > 0 for t in ms)
+        for p, f_np in enumerate(fs_np):
+            rr = oracle.norm_interior(oracle.residual(f_np, us[p].cpu().numpy())) / oracle.norm_interior(f_np)
+            assert rr <= 1.0001e-10, (p, rr)
+
+
+def test_persistent_batch_problems_are_independent(homg):
+    import torch
+
+    n = 64
+    good = inputs.uniform_rhs(n, 2, seed=1)
+    bad = good.copy()
+    bad[7, 9] = np.nan
+    f_np = [good, np.zeros_like(good), bad, good, inputs.uniform_rhs(32, 2, seed=2)]
+    with homg.BatchSolver([f.shape[0] for f in f_np], precision="fp32", launch_mode="persistent") as b:
+        fs = [torch.from_numpy(f).cuda() for f in f_np]
+        us = [torch.zeros_like(f) for f in fs]
+        rc, status, cycles, relres, ms = b.solve(fs, us, tol=1e-10, max_cycles=40)
+    assert status == [homg.HOMG_OK, homg.HOMG_OK, homg.HOMG_DIVERGED, homg.HOMG_OK, homg.HOMG_OK]
+    assert rc == homg.HOMG_DIVERGED and cycles[1] == 0 and torch.count_nonzero(us[1]) == 0
+    assert torch.equal(us[0], us[3])
+    ref, _, _, _ = single(homg, good, 1e-10, 40, "fp32")
+    np.testing.assert_array_equal(us[0].cpu().numpy(), ref)
+
+
+def test_persistent_barrier_wait_gives_up_and_context_stays_usable(homg):
+    """A grid barrier that can never complete (it waits for one block more than the launch has):
+    every block's bounded wait gives up after 0.25 s, the call reports HOMG_TIMEOUT, and the same
+    batch then solves normally."""
+    import torch
+
+    n = 32
+    f_np = [inputs.uniform_rhs(n, 2, seed=s) for s in (5, 6)]
+    with homg.BatchSolver([n + 1] * 2, precision="fp32", launch_mode="persistent") as b:
+        rc, ms = b.check_barrier_timeout()
+        assert rc == homg.HOMG_TIMEOUT and "gave up" in homg.homg_last_error(None)
+        assert 200.0 <= ms <= 5000.0, ms
+        fs = [torch.from_numpy(f).cuda() for f in f_np]
+        us = [torch.zeros_like(f) for f in fs]
+        rc, status, cycles, relres, _ = b.solve(fs, us, tol=1e-10, max_cycles=40)
+    assert rc == homg.HOMG_OK
+    ref, _, cyc1, _ = single(homg, f_np[0], 1e-10, 40, "fp32")
+    assert cycles[0] == cyc1
+    np.testing.assert_array_equal(us[0].cpu().numpy(), ref)

@@ -305,7 +305,14 @@ def test_residual_loss_train_step_matches_oracle(homg):
     for l in range(len(params)):
         gW, gB = grads[l]
         assert np.linalg.norm(gW - gw[l]) <= 3e-2 * np.linalg.norm(gw[l]), l
-        assert np.linalg.norm(gB - gb[l]) <= 3e-2 * np.linalg.norm(gb[l]) + 1e-12, l
+        if l < len(params) - 1:
+            assert np.linalg.norm(gB - gb[l]) <= 3e-2 * np.linalg.norm(gb[l]) + 1e-12, l
+        else:
+            # the last bias's gradient is exactly 0 (the weights w_q(p) sum to 1, so a constant shift
+            # of the output leaves every residual unchanged): only rounding of the bfloat16 gradient
+            # image remains, judged against the layer's weight gradient
+            assert np.linalg.norm(gb[l]) <= 1e-12 * np.linalg.norm(gw[l])
+            assert np.linalg.norm(gB) <= 1e-2 * np.linalg.norm(gw[l]), (gB, np.linalg.norm(gw[l]))
 
 
 def jacobi_network(c):

@@ -172,6 +172,9 @@ def test_residual_loss_gradients_match_finite_differences():
     xs = [np.stack([rng.standard_normal((6, 7)), rng.uniform(-1, 1, (6, 7))]) for _ in range(2)]
     ts = [np.zeros((6, 7))] * 2
     loss, gw, gb = cnn.loss_and_grads(params, xs, ts, rounding=False, loss_kind="residual")
+    # a constant added to the output changes no residual (the weights w_q(p) sum to 1): the last
+    # bias has gradient 0
+    assert np.abs(gb[-1]).max() <= 1e-12 * np.abs(gw[-1]).max()
     eps = 1e-6
     for l in range(3):
         w, b = params[l]
