@@ -53,18 +53,26 @@ template <> struct St<__nv_bfloat16> {
 // (__ldg). Inside the persistent batch kernel (P = true), a phase reads values that other blocks of
 // the same launch wrote in an earlier phase, which the read-only path does not promise to see:
 // those loads go to L2 (__ldcg), the point of coherence, after the grid barrier's fences.
+#ifndef HOMG_PERSIST_L1
+#define HOMG_PERSIST_L1 0
+#endif
+#if HOMG_PERSIST_L1
+#define HOMG_LDP __ldca
+#else
+#define HOMG_LDP __ldcg
+#endif
 template <typename T> __device__ __forceinline__ typename St<T>::C ld_cg(const T* p);
-template <> __device__ __forceinline__ double ld_cg<double>(const double* p) { return __ldcg(p); }
-template <> __device__ __forceinline__ float ld_cg<float>(const float* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double ld_cg<double>(const double* p) { return HOMG_LDP(p); }
+template <> __device__ __forceinline__ float ld_cg<float>(const float* p) { return HOMG_LDP(p); }
 template <> __device__ __forceinline__ float ld_cg<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+    return __bfloat162float(__ushort_as_bfloat16(HOMG_LDP(reinterpret_cast<const unsigned short*>(p))));
 }
 template <typename T, bool P> __device__ __forceinline__ typename St<T>::C ldv(const T* p) {
     if constexpr (P) return ld_cg<T>(p);
     else return St<T>::ld(p);
 }
 template <bool P> __device__ __forceinline__ double ld64(const double* p) {
-    if constexpr (P) return __ldcg(p);
+    if constexpr (P) return HOMG_LDP(p);
     else return __ldg(p);
 }
 
@@ -1933,7 +1941,10 @@ __device__ bool run_segment(const PersistArgs& P, int first, int count, unsigned
 }
 
 template <typename T>
-__global__ void __launch_bounds__(JX, 4) k_batch_persistent(PersistArgs P) {
+#ifndef HOMG_PERSIST_MINB
+#define HOMG_PERSIST_MINB 4
+#endif
+__global__ void __launch_bounds__(JX, HOMG_PERSIST_MINB) k_batch_persistent(PersistArgs P) {
     const unsigned int target = gridDim.x + (P.stall ? 1u : 0u);
     if (P.stall) {  // self-test: a barrier that cannot complete, before any problem data is touched
         grid_barrier(P, target);
