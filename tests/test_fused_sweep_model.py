@@ -202,3 +202,107 @@ def test_k_sweep_model_equals_k_sweeps(n, rows, K):
     for _ in range(K):
         want = plain_sweep(want, G, OM, C1, n)
     assert np.array_equal(grid.O[1:n, 1:n], want[1:n, 1:n])
+
+
+class PaddedGrid(Grid):
+    """Rows padded to a multiple of 16 elements, as the level buffer lays them out: aligned vector
+    groups may read the padding (never past it), which holds arbitrary values."""
+
+    def __init__(self, E, G, n, rng):
+        super().__init__(E, G, n)
+        self.pitch = (n + 1 + 15) // 16 * 16
+        pad = lambda A: np.concatenate([A, rng.standard_normal((n + 1, self.pitch - n - 1)).astype(np.float32) * 1e3], 1)  # noqa: E731
+        self.Ep, self.Gp = pad(E), pad(G)
+
+    def vld(self, A, c0, r, V):
+        assert c0 % V == 0 and 0 <= c0 and c0 + V - 1 <= self.pitch - 1 and 0 <= r <= self.n, (c0, r)
+        return [A[r, c0 + k] for k in range(V)]
+
+
+def model_x2v(grid, om, c1, rows, V):
+    """k_jacobi2_x2v: V columns per lane loaded as one aligned group, 30 V output columns per strip."""
+    n = grid.n
+    W = 30 * V
+    xb = (((n - 1 + W - 1) // W) + JX // 32 - 1) // (JX // 32)
+    zero = np.float32(0)
+    for by in range((n - 1 + rows - 1) // rows):
+        j0 = by * rows + 1
+        j1 = min(j0 + rows, n)
+        r0, ra, rb = j0 - 1, max(j0 - 1, 1), min(j1, n - 1)
+        for strip in range(xb * (JX // 32)):
+            base = strip * W
+            if base + 1 > n - 1:
+                continue
+            lanes = []
+            for lane in range(32):
+                c0 = base - V + V * lane
+                cols = [c0 + k for k in range(V)]
+                d = dict(c0=c0, grp=0 <= c0 <= n, ein=[0 <= c <= n for c in cols], inn=[1 <= c <= n - 1 for c in cols],
+                         out=[1 <= c <= n - 1 and base + 1 <= c <= base + W for c in cols], r=ra, ro=j0)
+                d["full"] = all(d["out"])
+                lanes.append(d)
+
+            def row(d, A, r):
+                x = grid.vld(A, d["c0"], r, V) if d["grp"] else [zero] * V
+                return [x[k] if (d["grp"] and d["ein"][k]) else zero for k in range(V)]
+
+            for d in lanes:
+                d["em"], d["ec"] = row(d, grid.Ep, d["r"] - 1), row(d, grid.Ep, d["r"])
+                d["sp"] = d["sc"] = d["gc"] = [zero] * V
+
+            def first():
+                res = []
+                left = [lanes[l - 1]["ec"][V - 1] if l > 0 else lanes[l]["ec"][V - 1] for l in range(32)]
+                right = [lanes[l + 1]["ec"][0] if l < 31 else lanes[l]["ec"][0] for l in range(32)]
+                for l, d in enumerate(lanes):
+                    r = d["r"]
+                    assert 1 <= r <= n - 1
+                    ep, g = row(d, grid.Ep, r + 1), row(d, grid.Gp, r)
+                    v = []
+                    for k in range(V):
+                        w = d["ec"][k - 1] if k > 0 else left[l]
+                        e = d["ec"][k + 1] if k < V - 1 else right[l]
+                        s = np.float32(np.float32(w + e) + np.float32(d["em"][k] + ep[k]))
+                        y = step32(c1, d["ec"][k], om, s, g[k])
+                        v.append(y if d["inn"][k] else zero)
+                    d["em"], d["ec"], d["r"] = d["ec"], ep, r + 1
+                    res.append((v, g))
+                return res
+
+            def second(vs):
+                left = [lanes[l - 1]["sc"][V - 1] if l > 0 else lanes[l]["sc"][V - 1] for l in range(32)]
+                right = [lanes[l + 1]["sc"][0] if l < 31 else lanes[l]["sc"][0] for l in range(32)]
+                for l, d in enumerate(lanes):
+                    for k in range(V):
+                        sw = d["sc"][k - 1] if k > 0 else left[l]
+                        se = d["sc"][k + 1] if k < V - 1 else right[l]
+                        s = np.float32(np.float32(sw + se) + np.float32(d["sp"][k] + vs[l][k]))
+                        o = step32(c1, d["sc"][k], om, s, d["gc"][k])
+                        if d["full"] or d["out"][k]:
+                            assert d["out"][k] and d["c0"] % V == 0
+                            grid.store(d["c0"] + k, d["ro"], o)
+                    d["ro"] += 1
+
+            if r0 >= 1:
+                for d, (v, _) in zip(lanes, first()):
+                    d["sc"] = v
+            for d, (v, g) in zip(lanes, first()):
+                d["sp"], d["sc"], d["gc"] = d["sc"], v, g
+            for _ in range(j0 + 1, rb + 1):
+                res = first()
+                second([v for v, _ in res])
+                for d, (v, g) in zip(lanes, res):
+                    d["sp"], d["sc"], d["gc"] = d["sc"], v, g
+            if j1 == n:
+                second([[zero] * V] * 32)
+
+
+@pytest.mark.parametrize("V", [4, 8])
+@pytest.mark.parametrize("n,rows", [(2, 1), (3, 1), (8, 3), (17, 8), (31, 4), (64, 63), (127, 8), (130, 16), (260, 5), (512, 16)])
+def test_vector_pair_model_equals_two_sweeps(n, rows, V):
+    E, G = problem(n, 200 + n)
+    grid = PaddedGrid(E, G, n, np.random.default_rng(n))
+    model_x2v(grid, OM, C1, rows, V)
+    grid.check_coverage()
+    want = plain_sweep(plain_sweep(E, G, OM, C1, n), G, OM, C1, n)
+    assert np.array_equal(grid.O[1:n, 1:n], want[1:n, 1:n])
