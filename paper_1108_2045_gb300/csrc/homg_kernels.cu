@@ -1019,7 +1019,8 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
 // vector (float4, or four / eight bfloat16 values): the same march and arithmetic as k_jacobi2_x2,
 // element by element, so the result is again bit-identical to two single sweeps, with a fraction of
 // its load, store and shuffle instructions per node. A warp strip covers 32 V columns starting at
-// the aligned column 30 V s - V and outputs the 30 V columns 30 V s + 1 .. 30 V s + 30 V; a lane's
+// the aligned column W s - V and outputs the W columns W s + 1 .. W s + W, W the largest multiple of
+// V with W + 2 <= 31 V - 1 (the first sweep's last column still has its east neighbour); a lane's
 // side neighbours are its own vector's elements or, at the vector's ends, the next lanes' (shuffle).
 // Rows are padded to 16 elements and start 256-byte aligned, so every group a lane loads lies inside
 // its row; groups left of column 0 are not loaded, and columns past n read as 0.
@@ -1027,6 +1028,14 @@ template <typename T, int V> __device__ __forceinline__ void vload(const T* p, f
 template <> __device__ __forceinline__ void vload<float, 4>(const float* p, float* x) {
     const float4 q = __ldg(reinterpret_cast<const float4*>(p));
     x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+}
+template <> __device__ __forceinline__ void vload<float, 2>(const float* p, float* x) {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+    x[0] = q.x; x[1] = q.y;
+}
+template <> __device__ __forceinline__ void vload<__nv_bfloat16, 2>(const __nv_bfloat16* p, float* x) {
+    const unsigned q = __ldg(reinterpret_cast<const unsigned*>(p));
+    x[0] = __uint_as_float(q << 16); x[1] = __uint_as_float(q & 0xffff0000u);
 }
 template <> __device__ __forceinline__ void vload<__nv_bfloat16, 4>(const __nv_bfloat16* p, float* x) {
     const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
@@ -1046,6 +1055,13 @@ template <typename T, int V> __device__ __forceinline__ void vstore(T* p, const 
 template <> __device__ __forceinline__ void vstore<float, 4>(float* p, const float* x) {
     *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
 }
+template <> __device__ __forceinline__ void vstore<float, 2>(float* p, const float* x) {
+    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+}
+template <> __device__ __forceinline__ void vstore<__nv_bfloat16, 2>(__nv_bfloat16* p, const float* x) {
+    *reinterpret_cast<unsigned*>(p) =
+        (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[0])) | ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[1])) << 16);
+}
 template <> __device__ __forceinline__ void vstore<__nv_bfloat16, 4>(__nv_bfloat16* p, const float* x) {
     uint2 q;
     q.x = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[0])) | ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[1])) << 16);
@@ -1064,11 +1080,22 @@ template <> __device__ __forceinline__ void vstore<__nv_bfloat16, 8>(__nv_bfloat
 #ifndef X2V_BF16
 #define X2V_BF16 8  // bfloat16 columns per lane of the vector pair kernel
 #endif
+#ifndef X2V_F32
+#define X2V_F32 4   // binary32 columns per lane of the vector pair kernel
+#endif
+#ifndef X2V_UNROLL
+#define X2V_UNROLL 2
+#endif
+#ifndef X2V_OFF
+#define X2V_OFF 0   // 1: pairs run on the per-column kernel k_jacobi2_x2
+#endif
+#define X2V_PRAGMA(x) _Pragma(#x)
+#define X2V_UNROLL_PRAGMA(u) X2V_PRAGMA(unroll u)
 template <typename T, int V, bool BATCH>
 __global__ void __launch_bounds__(JX) k_jacobi2_x2v(IterArgs a, int rows) {
     pdl_begin();
     if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
-    constexpr int W = 30 * V;                            // output columns per strip
+    constexpr int W = V * (31 - (V + 2) / V);            // output columns per strip: a multiple of V, at most 31 V - 3
     const int n = a.e_new.n;
     const int lane = threadIdx.x & 31;
     const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
@@ -1159,7 +1186,7 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2v(IterArgs a, int rows) {
         }
     }
     const int rb = min(j1, n - 1);
-#pragma unroll 2
+    X2V_UNROLL_PRAGMA(X2V_UNROLL)
     for (int r = j0 + 1; r <= rb; ++r) {
         float v[V], g[V];
         first(v, g);
@@ -2106,7 +2133,7 @@ __device__ bool run_segment(const PersistArgs& P, int first, int count, unsigned
 
 template <typename T>
 #ifndef HOMG_PERSIST_MINB
-#define HOMG_PERSIST_MINB 4
+#define HOMG_PERSIST_MINB 10
 #endif
 __global__ void __launch_bounds__(JX, HOMG_PERSIST_MINB) k_batch_persistent(PersistArgs P) {
     const unsigned int target = gridDim.x + (P.stall ? 1u : 0u);
@@ -2162,14 +2189,25 @@ cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_
     // further than a single sweep does, to keep that overhead small
     const double nodes = (double)a.nb * (double)(n - 1) * (double)(n - 1);
     const int rows = a.rows > 0 ? a.rows : (nodes >= 1.0e6 ? 16 : 8);
-    // vector lanes: 4 binary32 (16 B) or 8 bfloat16 (16 B) columns each, 30 V output columns per strip
-    const int V = (prec == PREC_BF16) ? X2V_BF16 : 4;
-    const int xb = (((n - 1 + 30 * V - 1) / (30 * V)) + JX / 32 - 1) / (JX / 32);  // blocks across: JX / 32 strips each
+    if (X2V_OFF) {
+        const int xb1 = (((n - 1 + X2_OUT - 1) / X2_OUT) + JX / 32 - 1) / (JX / 32);
+        const dim3 g1((unsigned)xb1, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b1(JX);
+        if (prec == PREC_FP32)
+            return a.bst ? launch_k(k_jacobi2_x2<float, true>, g1, b1, s, a, rows) : launch_k(k_jacobi2_x2<float, false>, g1, b1, s, a, rows);
+        if (prec == PREC_BF16)
+            return a.bst ? launch_k(k_jacobi2_x2<__nv_bfloat16, true>, g1, b1, s, a, rows)
+                         : launch_k(k_jacobi2_x2<__nv_bfloat16, false>, g1, b1, s, a, rows);
+        return cudaErrorInvalidValue;
+    }
+    // vector lanes: V binary32 or bfloat16 columns each, 30 V output columns per strip
+    const int V = (prec == PREC_BF16) ? X2V_BF16 : X2V_F32;
+    const int W = V * (31 - (V + 2) / V);  // output columns per strip (see k_jacobi2_x2v)
+    const int xb = (((n - 1 + W - 1) / W) + JX / 32 - 1) / (JX / 32);  // blocks across: JX / 32 strips each
     const dim3 g((unsigned)xb, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
     switch (prec) {
         case PREC_FP32:
-            return a.bst ? launch_k(k_jacobi2_x2v<float, 4, true>, g, b, s, a, rows)
-                         : launch_k(k_jacobi2_x2v<float, 4, false>, g, b, s, a, rows);
+            return a.bst ? launch_k(k_jacobi2_x2v<float, X2V_F32, true>, g, b, s, a, rows)
+                         : launch_k(k_jacobi2_x2v<float, X2V_F32, false>, g, b, s, a, rows);
         case PREC_BF16:
             return a.bst ? launch_k(k_jacobi2_x2v<__nv_bfloat16, X2V_BF16, true>, g, b, s, a, rows)
                          : launch_k(k_jacobi2_x2v<__nv_bfloat16, X2V_BF16, false>, g, b, s, a, rows);

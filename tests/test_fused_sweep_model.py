@@ -220,9 +220,9 @@ class PaddedGrid(Grid):
 
 
 def model_x2v(grid, om, c1, rows, V):
-    """k_jacobi2_x2v: V columns per lane loaded as one aligned group, 30 V output columns per strip."""
+    """k_jacobi2_x2v: V columns per lane loaded as one aligned group, W output columns per strip."""
     n = grid.n
-    W = 30 * V
+    W = V * (31 - (V + 2) // V)
     xb = (((n - 1 + W - 1) // W) + JX // 32 - 1) // (JX // 32)
     zero = np.float32(0)
     for by in range((n - 1 + rows - 1) // rows):
@@ -297,7 +297,7 @@ def model_x2v(grid, om, c1, rows, V):
                 second([[zero] * V] * 32)
 
 
-@pytest.mark.parametrize("V", [4, 8])
+@pytest.mark.parametrize("V", [2, 4, 8])
 @pytest.mark.parametrize("n,rows", [(2, 1), (3, 1), (8, 3), (17, 8), (31, 4), (64, 63), (127, 8), (130, 16), (260, 5), (512, 16)])
 def test_vector_pair_model_equals_two_sweeps(n, rows, V):
     E, G = problem(n, 200 + n)
