@@ -262,7 +262,6 @@ def run_cfg2_sine(args, homg, inputs, stream, barrier, pending):
 
 
 CFG3_SIDE = 512
-CFG3_LEVELS = 9
 
 
 def run_cfg3(args, homg, inputs, stream, barrier, pending):
@@ -274,8 +273,9 @@ def run_cfg3(args, homg, inputs, stream, barrier, pending):
     import numpy as np
     import torch
 
-    n = CFG3_SIDE
-    out = {"workload": "3-D Poisson -Lap u = f, 7-point, 513^3 nodes, 9 levels, MaxI=32, to relres 1e-10"}
+    n = args.cfg3_side
+    levels = n.bit_length() - 1
+    out = {"workload": "3-D Poisson -Lap u = f, 7-point, %d^3 nodes, %d levels, MaxI=32, to relres 1e-10" % (n + 1, levels)}
     h = 1.0 / n
     ch = np.pi ** 2 * h ** 2 / (4 * np.sin(np.pi * h / 2) ** 2)
     for rhs in ("sine", "normal"):
@@ -286,7 +286,7 @@ def run_cfg3(args, homg, inputs, stream, barrier, pending):
         ref = None
         res = {}
         for prec in ("fp64", "fp32", "bf16"):
-            with homg.Solver(3, n + 1, CFG3_LEVELS, max_i=MAX_I, precision=prec) as s3:
+            with homg.Solver(3, n + 1, levels, max_i=MAX_I, precision=prec, launch_mode=args.launch) as s3:
                 s3.set_stream(stream)
                 u.zero_()
                 s3.solve(f, u, tol=TOL, max_cycles=MAX_CYCLES)
@@ -1043,6 +1043,8 @@ def main():
                    help="timed solves per cycle type of the 4097^2 manufactured right-hand side (0: skip)")
     p.add_argument("--mixed-steps", type=int, default=3, help="timed solves per mixed-precision variant (0: skip)")
     p.add_argument("--cfg3-steps", type=int, default=2, help="timed 513^3 solves per precision and RHS (0: skip)")
+    p.add_argument("--cfg3-side", type=int, default=CFG3_SIDE, choices=[64, 128, 256, 512],
+                   help="intervals per side of the 3-D leg (512: the 513^3 workload; smaller for profiling)")
     p.add_argument("--vcycle-steps", type=int, default=3, help="timed V(2,2) comparator solves (0: skip)")
     p.add_argument("--cfg4-steps", type=int, default=2, help="timed batched solves of the 1024-problem batch (0: skip)")
     p.add_argument("--no-cfg4-oracle-check", dest="cfg4_oracle_check", action="store_false")

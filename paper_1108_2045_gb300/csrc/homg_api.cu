@@ -512,7 +512,8 @@ void plan_cycle(homg_ctx* h) {
             }
             // binary32-arithmetic cycles pair consecutive plain sweeps (no pending interpolation, no
             // variation output) into one two-sweep launch: half the DRAM traffic, same results
-            const bool pairable = !h->strict && h->prec != PREC_FP64 && h->ndim == 2 && !h->vc && lv.n > 16;
+            const bool pairable = !h->strict && h->prec != PREC_FP64 && !h->vc &&
+                                  ((h->ndim == 2 && lv.n > 16) || (h->ndim == 3 && lv.n > 8));
             auto plain = [&](int q) { return q >= 1 && !(q == c - 1 && m >= 1); };
             for (int q = 0; q < c; ++q) {
                 if (pairable && plain(q) && q + 1 < c && plain(q + 1)) {
@@ -617,7 +618,9 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
         cudaError_t e = cudaSuccess;
         switch (op.kind) {
             case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
-            case Op::ITER2: e = launch_iterate2(h->prec, op.sweeps, op.it, s); break;
+            case Op::ITER2:
+                e = (h->ndim == 3) ? launch_iterate3_2(h->prec, op.it, s) : launch_iterate2(h->prec, op.sweeps, op.it, s);
+                break;
             case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
             case Op::VRESID: e = launch_vresid(h->ndim, h->prec, h->strict, op.vr, s); break;

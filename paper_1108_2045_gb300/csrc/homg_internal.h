@@ -294,6 +294,8 @@ cudaError_t launch_check_conversions(const double* d_in, float* f_out, const flo
 // `sweeps` (2 or 4) plain lattice-form sweeps in one launch (2-D, FP32 / bfloat16 storage, no
 // pending interpolation, no variation output): e_new = sweep(...sweep(e_old)).
 cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_t s);
+// Two plain 3-D lattice-form sweeps in one launch (FP32 / bfloat16 storage).
+cudaError_t launch_iterate3_2(int prec, const IterArgs& a, cudaStream_t s);
 cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a, cudaStream_t s);
 cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a, int n, cudaStream_t s);
 int residual_blocks(int ndim, bool strict, int n);  // partial sums written by launch_residual

@@ -1015,197 +1015,6 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
     jacobi2_x2_body<T, BATCH, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// Two plain sweeps in one pass with V adjacent columns per lane, loaded and stored as one aligned
-// vector (float4, or four / eight bfloat16 values): the same march and arithmetic as k_jacobi2_x2,
-// element by element, so the result is again bit-identical to two single sweeps, with a fraction of
-// its load, store and shuffle instructions per node. A warp strip covers 32 V columns starting at
-// the aligned column W s - V and outputs the W columns W s + 1 .. W s + W, W the largest multiple of
-// V with W + 2 <= 31 V - 1 (the first sweep's last column still has its east neighbour); a lane's
-// side neighbours are its own vector's elements or, at the vector's ends, the next lanes' (shuffle).
-// Rows are padded to 16 elements and start 256-byte aligned, so every group a lane loads lies inside
-// its row; groups left of column 0 are not loaded, and columns past n read as 0.
-template <typename T, int V> __device__ __forceinline__ void vload(const T* p, float* x);
-template <> __device__ __forceinline__ void vload<float, 4>(const float* p, float* x) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-    x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
-}
-template <> __device__ __forceinline__ void vload<float, 2>(const float* p, float* x) {
-    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
-    x[0] = q.x; x[1] = q.y;
-}
-template <> __device__ __forceinline__ void vload<__nv_bfloat16, 2>(const __nv_bfloat16* p, float* x) {
-    const unsigned q = __ldg(reinterpret_cast<const unsigned*>(p));
-    x[0] = __uint_as_float(q << 16); x[1] = __uint_as_float(q & 0xffff0000u);
-}
-template <> __device__ __forceinline__ void vload<__nv_bfloat16, 4>(const __nv_bfloat16* p, float* x) {
-    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
-    x[0] = __uint_as_float(q.x << 16); x[1] = __uint_as_float(q.x & 0xffff0000u);
-    x[2] = __uint_as_float(q.y << 16); x[3] = __uint_as_float(q.y & 0xffff0000u);
-}
-template <> __device__ __forceinline__ void vload<__nv_bfloat16, 8>(const __nv_bfloat16* p, float* x) {
-    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
-    const unsigned w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        x[2 * t] = __uint_as_float(w[t] << 16);
-        x[2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
-    }
-}
-template <typename T, int V> __device__ __forceinline__ void vstore(T* p, const float* x);
-template <> __device__ __forceinline__ void vstore<float, 4>(float* p, const float* x) {
-    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
-}
-template <> __device__ __forceinline__ void vstore<float, 2>(float* p, const float* x) {
-    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
-}
-template <> __device__ __forceinline__ void vstore<__nv_bfloat16, 2>(__nv_bfloat16* p, const float* x) {
-    *reinterpret_cast<unsigned*>(p) =
-        (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[0])) | ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[1])) << 16);
-}
-template <> __device__ __forceinline__ void vstore<__nv_bfloat16, 4>(__nv_bfloat16* p, const float* x) {
-    uint2 q;
-    q.x = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[0])) | ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[1])) << 16);
-    q.y = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[2])) | ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[3])) << 16);
-    *reinterpret_cast<uint2*>(p) = q;
-}
-template <> __device__ __forceinline__ void vstore<__nv_bfloat16, 8>(__nv_bfloat16* p, const float* x) {
-    unsigned w[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-        w[t] = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * t])) |
-               ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * t + 1])) << 16);
-    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-#ifndef X2V_BF16
-#define X2V_BF16 8  // bfloat16 columns per lane of the vector pair kernel
-#endif
-#ifndef X2V_F32
-#define X2V_F32 4   // binary32 columns per lane of the vector pair kernel
-#endif
-#ifndef X2V_UNROLL
-#define X2V_UNROLL 2
-#endif
-#ifndef X2V_OFF
-#define X2V_OFF 0   // 1: pairs run on the per-column kernel k_jacobi2_x2
-#endif
-#define X2V_PRAGMA(x) _Pragma(#x)
-#define X2V_UNROLL_PRAGMA(u) X2V_PRAGMA(unroll u)
-template <typename T, int V, bool BATCH>
-__global__ void __launch_bounds__(JX) k_jacobi2_x2v(IterArgs a, int rows) {
-    pdl_begin();
-    if (BATCH && !batch_view<T>(a, blockIdx.z)) return;  // uniform over the block
-    constexpr int W = V * (31 - (V + 2) / V);            // output columns per strip: a multiple of V, at most 31 V - 3
-    const int n = a.e_new.n;
-    const int lane = threadIdx.x & 31;
-    const int strip = blockIdx.x * (JX / 32) + (threadIdx.x >> 5);
-    const int base = strip * W;                          // outputs base + 1 .. base + W
-    if (base + 1 > n - 1) return;                        // strip past the last column: the whole warp leaves
-    const int c0 = base - V + V * lane;                  // this lane's first column (a multiple of V)
-    const bool grp = c0 >= 0 && c0 <= n;                 // the group holds a column of the row
-    bool ein[V], inn[V], outm[V];
-    bool full = true;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const int c = c0 + k;
-        ein[k] = c >= 0 && c <= n;                       // an input value of the row (boundary: stored 0)
-        inn[k] = c >= 1 && c <= n - 1;                   // an interior column: sweep values live here
-        outm[k] = inn[k] && c >= base + 1 && c <= base + W;
-        full = full && outm[k];
-    }
-    const int j0 = blockIdx.y * rows + 1;                // second sweep: rows j0 .. j1 - 1
-    const int j1 = min(j0 + rows, n);
-    const int r0 = j0 - 1;                               // first sweep: rows r0 .. j1 (0 on rows 0 and n)
-    const int64_t pe = a.e_old.pitch, pg = a.g.pitch, po = a.e_new.pitch;
-    const int ra = max(r0, 1);
-    const T* pE = cp<T>(a.e_old) + (int64_t)ra * pe + c0;  // row r of the march (dereferenced only when grp)
-    const T* pG = cp<T>(a.g) + (int64_t)ra * pg + c0;
-    T* pO = wp<T>(a.e_new) + (int64_t)j0 * po + c0;        // next output row
-    const float om = a.omega_f, c1 = a.c1_f;
-    auto row = [&](const T* p, float* x) {
-        if (grp) vload<T, V>(p, x);
-#pragma unroll
-        for (int k = 0; k < V; ++k) x[k] = (grp && ein[k]) ? x[k] : 0.f;
-    };
-    float em[V], ec[V];
-    row(pE - pe, em);
-    row(pE, ec);
-    // first sweep at row r (1 <= r <= n - 1) on the lane's V columns, then advance the march one row
-    auto first = [&](float* v, float* g) {
-        float ep[V];
-        row(pE + pe, ep);
-        row(pG, g);
-        const float left = __shfl_up_sync(0xffffffffu, ec[V - 1], 1), right = __shfl_down_sync(0xffffffffu, ec[0], 1);
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const float w = k > 0 ? ec[k - 1] : left, e = k < V - 1 ? ec[k + 1] : right;
-            const float y = as_c<T>(St<T>::put(fma(c1, ec[k], fma(om, (w + e) + (em[k] + ep[k]), g[k]))));
-            v[k] = inn[k] ? y : 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            em[k] = ec[k];
-            ec[k] = ep[k];
-        }
-        pE += pe;
-        pG += pg;
-    };
-    float s_prev[V], s_cur[V], g_cur[V];  // first-sweep values at rows r - 2, r - 1; g at row r - 1
-#pragma unroll
-    for (int k = 0; k < V; ++k) s_prev[k] = s_cur[k] = g_cur[k] = 0.f;
-    // second sweep at row r - 1 given the first-sweep values v at row r
-    auto second = [&](const float* v) {
-        const float left = __shfl_up_sync(0xffffffffu, s_cur[V - 1], 1), right = __shfl_down_sync(0xffffffffu, s_cur[0], 1);
-        float o[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const float sw = k > 0 ? s_cur[k - 1] : left, se = k < V - 1 ? s_cur[k + 1] : right;
-            o[k] = fma(c1, s_cur[k], fma(om, (sw + se) + (s_prev[k] + v[k]), g_cur[k]));
-        }
-        if (full) {
-            vstore<T, V>(pO, o);
-        } else {
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-                if (outm[k]) pO[k] = St<T>::put(o[k]);
-        }
-        pO += po;
-    };
-    if (r0 >= 1) {
-        float g[V];
-        first(s_cur, g);  // row r0 (its g is never used)
-    }
-    {
-        float v[V], g[V];
-        first(v, g);  // row j0
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            s_prev[k] = s_cur[k];
-            s_cur[k] = v[k];
-            g_cur[k] = g[k];
-        }
-    }
-    const int rb = min(j1, n - 1);
-    X2V_UNROLL_PRAGMA(X2V_UNROLL)
-    for (int r = j0 + 1; r <= rb; ++r) {
-        float v[V], g[V];
-        first(v, g);
-        second(v);
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            s_prev[k] = s_cur[k];
-            s_cur[k] = v[k];
-            g_cur[k] = g[k];
-        }
-    }
-    if (j1 == n) {
-        float z[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) z[k] = 0.f;
-        second(z);  // the first-sweep value on the boundary row n is 0
-    }
-}
-
 // K plain damped-Jacobi sweeps in one pass (K >= 3; binary32 arithmetic), the K-level form of
 // k_jacobi2_x2: each warp marches a strip of 32 columns; step r computes sweep 1 at row r, sweep 2
 // at row r - 1, ..., sweep K at row r - K + 1 (the output), each from the previous sweep's values
@@ -1398,6 +1207,92 @@ __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
     }
 }
 
+
+// Two plain sweeps of the 3-D lattice form in one pass (binary32 arithmetic: FP32 and bfloat16
+// cycles, where a sweep is DRAM bound). A block of 32 x J3Y2 threads owns a tile of columns
+// (x, y) and marches down z: step r computes the first sweep at plane r on every thread of the
+// tile (exactly a single sweep's operation order, rounded to the storage type; side neighbours
+// through L1, the neighbours along z in registers) and the second sweep at plane r - 1 on the inner
+// (32 - 2) x (J3Y2 - 2) threads, taking the first-sweep values of the x neighbours by shuffle and of
+// the y neighbours from the previous step's plane in shared memory. Planes are triple-buffered, so
+// one block barrier per step separates every write from the reads of it and from its next
+// overwrite. Tiles overlap by one column and row on each side; a block's march starts one plane
+// above its output planes and ends one below. Threads outside the interior load from inside (clamped
+// indexes) and keep 0. Per node and pair of sweeps this reads e and g once and writes e once, and
+// the result is bit-identical to two single sweeps.
+constexpr int J3Y2 = 16;  // thread rows of the 3-D pair kernel
+template <typename T>
+__global__ void __launch_bounds__(J3X * J3Y2) k_jacobi3_x2(IterArgs a, int rows) {
+    pdl_begin();
+    using C = typename St<T>::C;
+    __shared__ C pl[3][J3Y2][J3X];  // first-sweep planes, plane r in pl[r % 3]
+    const int n = a.e_new.n;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * (J3X - 2) + tx;   // outputs on tx 1 .. J3X - 2
+    const int j = blockIdx.y * (J3Y2 - 2) + ty;  // outputs on ty 1 .. J3Y2 - 2
+    const bool col_in = i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1;
+    const bool out = col_in && tx >= 1 && tx <= J3X - 2 && ty >= 1 && ty <= J3Y2 - 2;
+    const int il = min(max(i, 1), n - 1), jl = min(max(j, 1), n - 1);
+    const int k0 = blockIdx.z * rows + 1;  // second sweep: planes k0 .. k1 - 1
+    const int k1 = min(k0 + rows, n);
+    const int r0 = k0 - 1;                 // first sweep: planes r0 .. k1 (0 on planes 0 and n)
+    const int64_t pe = a.e_old.pitch, ple = (int64_t)(n + 1) * pe;
+    const int64_t pg = a.g.pitch, plg = (int64_t)(n + 1) * pg;
+    const int64_t po = a.e_new.pitch, plo = (int64_t)(n + 1) * po;
+    const T* __restrict__ colE = cp<T>(a.e_old) + (int64_t)jl * pe + il;
+    const T* __restrict__ colG = cp<T>(a.g) + (int64_t)jl * pg + il;
+    T* __restrict__ colO = wp<T>(a.e_new) + (int64_t)j * po + i;
+    const C om = pick<C>(a.omega, a.omega_f), c1 = pick<C>(a.c1, a.c1_f);
+    const int ra = max(r0, 1);
+    C em = St<T>::ld(colE + (int64_t)(ra - 1) * ple), ec = St<T>::ld(colE + (int64_t)ra * ple);
+    // first sweep at plane r (1 <= r <= n - 1); returns the value (0 off the interior) and its g
+    auto first = [&](int r, C& g) -> C {
+        const T* p = colE + (int64_t)r * ple;
+        const C ep = St<T>::ld(p + ple);
+        const C w = St<T>::ld(p - 1), e = St<T>::ld(p + 1), sn = St<T>::ld(p - pe), nn = St<T>::ld(p + pe);
+        g = St<T>::ld(colG + (int64_t)r * plg);
+        const C y = as_c<T>(St<T>::put(fma(c1, ec, fma(om, ((w + e) + (sn + nn)) + (em + ep), g))));
+        em = ec;
+        ec = ep;
+        return col_in ? y : (C)0;
+    };
+    C s_prev = 0, s_cur = 0, g_cur = 0;  // first-sweep values at planes x - 1, x; g at plane x
+    // second sweep at plane x given the first-sweep value v at plane x + 1 (pl[x % 3] complete)
+    auto second = [&](int x, C v) {
+        const C sw = __shfl_up_sync(0xffffffffu, s_cur, 1), se = __shfl_down_sync(0xffffffffu, s_cur, 1);
+        if (out) {
+            const C ss = pl[x % 3][ty - 1][tx], sn = pl[x % 3][ty + 1][tx];
+            colO[(int64_t)x * plo] = St<T>::put(fma(c1, s_cur, fma(om, ((sw + se) + (ss + sn)) + (s_prev + v), g_cur)));
+        }
+    };
+    if (r0 >= 1) {
+        C g;
+        s_cur = first(r0, g);  // plane r0: only its own value is used (the z neighbour of plane k0)
+    }
+    {
+        C g;
+        const C v = first(k0, g);
+        pl[k0 % 3][ty][tx] = v;
+        s_prev = s_cur;
+        s_cur = v;
+        g_cur = g;
+    }
+    const int rb = min(k1, n - 1);
+    for (int r = k0 + 1; r <= rb; ++r) {
+        C g;
+        const C v = first(r, g);
+        pl[r % 3][ty][tx] = v;
+        __syncthreads();  // plane r - 1 is complete (written last step); plane r's buffer is free
+        second(r - 1, v);
+        s_prev = s_cur;
+        s_cur = v;
+        g_cur = g;
+    }
+    if (k1 == n) {
+        __syncthreads();
+        second(n - 1, (C)0);  // the first-sweep value on the boundary plane n is 0
+    }
+}
 
 // ---------------------------------------------------------------------------------------------
 // Fast 3-D update + residual in two passes: k_update3 forms u_out = u_in + e (one FP64 add per
@@ -2177,6 +2072,20 @@ template <typename T, int K> cudaError_t iterate_k_t(const IterArgs& a, cudaStre
     return a.bst ? launch_k(k_jacobi2_xk<T, true, K>, g, b, s, a, rows) : launch_k(k_jacobi2_xk<T, false, K>, g, b, s, a, rows);
 }
 
+cudaError_t launch_iterate3_2(int prec, const IterArgs& a, cudaStream_t s) {
+    const int n = a.e_new.n;
+    const double nodes = (double)(n - 1) * (double)(n - 1) * (double)(n - 1);
+    const int rows = a.rows > 0 ? a.rows : (nodes >= 8.0e6 ? 32 : 8);
+    const dim3 g((unsigned)((n - 1 + J3X - 3) / (J3X - 2)), (unsigned)((n - 1 + J3Y2 - 3) / (J3Y2 - 2)),
+                 (unsigned)((n - 1 + rows - 1) / rows)),
+        b(J3X, J3Y2);
+    switch (prec) {
+        case PREC_FP32: return launch_k(k_jacobi3_x2<float>, g, b, s, a, rows);
+        case PREC_BF16: return launch_k(k_jacobi3_x2<__nv_bfloat16>, g, b, s, a, rows);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_t s) {
     if (sweeps == 4) {
         if (prec == PREC_FP32) return iterate_k_t<float, 4>(a, s);
@@ -2189,28 +2098,14 @@ cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_
     // further than a single sweep does, to keep that overhead small
     const double nodes = (double)a.nb * (double)(n - 1) * (double)(n - 1);
     const int rows = a.rows > 0 ? a.rows : (nodes >= 1.0e6 ? 16 : 8);
-    if (X2V_OFF) {
-        const int xb1 = (((n - 1 + X2_OUT - 1) / X2_OUT) + JX / 32 - 1) / (JX / 32);
-        const dim3 g1((unsigned)xb1, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b1(JX);
-        if (prec == PREC_FP32)
-            return a.bst ? launch_k(k_jacobi2_x2<float, true>, g1, b1, s, a, rows) : launch_k(k_jacobi2_x2<float, false>, g1, b1, s, a, rows);
-        if (prec == PREC_BF16)
-            return a.bst ? launch_k(k_jacobi2_x2<__nv_bfloat16, true>, g1, b1, s, a, rows)
-                         : launch_k(k_jacobi2_x2<__nv_bfloat16, false>, g1, b1, s, a, rows);
-        return cudaErrorInvalidValue;
-    }
-    // vector lanes: V binary32 or bfloat16 columns each, 30 V output columns per strip
-    const int V = (prec == PREC_BF16) ? X2V_BF16 : X2V_F32;
-    const int W = V * (31 - (V + 2) / V);  // output columns per strip (see k_jacobi2_x2v)
-    const int xb = (((n - 1 + W - 1) / W) + JX / 32 - 1) / (JX / 32);  // blocks across: JX / 32 strips each
+    const int xb = (((n - 1 + X2_OUT - 1) / X2_OUT) + JX / 32 - 1) / (JX / 32);  // blocks across: JX / 32 strips each
     const dim3 g((unsigned)xb, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
     switch (prec) {
         case PREC_FP32:
-            return a.bst ? launch_k(k_jacobi2_x2v<float, X2V_F32, true>, g, b, s, a, rows)
-                         : launch_k(k_jacobi2_x2v<float, X2V_F32, false>, g, b, s, a, rows);
+            return a.bst ? launch_k(k_jacobi2_x2<float, true>, g, b, s, a, rows) : launch_k(k_jacobi2_x2<float, false>, g, b, s, a, rows);
         case PREC_BF16:
-            return a.bst ? launch_k(k_jacobi2_x2v<__nv_bfloat16, X2V_BF16, true>, g, b, s, a, rows)
-                         : launch_k(k_jacobi2_x2v<__nv_bfloat16, X2V_BF16, false>, g, b, s, a, rows);
+            return a.bst ? launch_k(k_jacobi2_x2<__nv_bfloat16, true>, g, b, s, a, rows)
+                         : launch_k(k_jacobi2_x2<__nv_bfloat16, false>, g, b, s, a, rows);
         default: return cudaErrorInvalidValue;  // FP64 sweeps are FP64-bound: never paired
     }
 }

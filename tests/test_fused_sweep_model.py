@@ -204,105 +204,102 @@ def test_k_sweep_model_equals_k_sweeps(n, rows, K):
     assert np.array_equal(grid.O[1:n, 1:n], want[1:n, 1:n])
 
 
-class PaddedGrid(Grid):
-    """Rows padded to a multiple of 16 elements, as the level buffer lays them out: aligned vector
-    groups may read the padding (never past it), which holds arbitrary values."""
-
-    def __init__(self, E, G, n, rng):
-        super().__init__(E, G, n)
-        self.pitch = (n + 1 + 15) // 16 * 16
-        pad = lambda A: np.concatenate([A, rng.standard_normal((n + 1, self.pitch - n - 1)).astype(np.float32) * 1e3], 1)  # noqa: E731
-        self.Ep, self.Gp = pad(E), pad(G)
-
-    def vld(self, A, c0, r, V):
-        assert c0 % V == 0 and 0 <= c0 and c0 + V - 1 <= self.pitch - 1 and 0 <= r <= self.n, (c0, r)
-        return [A[r, c0 + k] for k in range(V)]
+J3X, J3Y2 = 32, 16  # threads of the 3-D pair kernel: a warp along x, J3Y2 warps along y
 
 
-def model_x2v(grid, om, c1, rows, V):
-    """k_jacobi2_x2v: V columns per lane loaded as one aligned group, W output columns per strip."""
-    n = grid.n
-    W = V * (31 - (V + 2) // V)
-    xb = (((n - 1 + W - 1) // W) + JX // 32 - 1) // (JX // 32)
+def plain_sweep3(E, G, om, c1, n):
+    O = np.zeros_like(E)
+    for k in range(1, n):
+        for j in range(1, n):
+            for i in range(1, n):
+                s = np.float32(np.float32(np.float32(E[k, j, i - 1] + E[k, j, i + 1]) + np.float32(E[k, j - 1, i] + E[k, j + 1, i]))
+                               + np.float32(E[k - 1, j, i] + E[k + 1, j, i]))
+                O[k, j, i] = step32(c1, E[k, j, i], om, s, G[k, j, i])
+    return O
+
+
+def model_x2_3d(E, G, om, c1, n, rows):
+    """k_jacobi3_x2: tiles of 32 x J3Y2 columns marching down z, the first sweep on every thread, the
+    second on the inner (32 - 2) x (J3Y2 - 2), x neighbours by shuffle, y neighbours from the
+    previous step's plane in (triple-buffered) shared memory. Returns the output and write counts."""
+    O = np.zeros_like(E)
+    written = np.zeros(E.shape, dtype=int)
     zero = np.float32(0)
-    for by in range((n - 1 + rows - 1) // rows):
-        j0 = by * rows + 1
-        j1 = min(j0 + rows, n)
-        r0, ra, rb = j0 - 1, max(j0 - 1, 1), min(j1, n - 1)
-        for strip in range(xb * (JX // 32)):
-            base = strip * W
-            if base + 1 > n - 1:
-                continue
-            lanes = []
-            for lane in range(32):
-                c0 = base - V + V * lane
-                cols = [c0 + k for k in range(V)]
-                d = dict(c0=c0, grp=0 <= c0 <= n, ein=[0 <= c <= n for c in cols], inn=[1 <= c <= n - 1 for c in cols],
-                         out=[1 <= c <= n - 1 and base + 1 <= c <= base + W for c in cols], r=ra, ro=j0)
-                d["full"] = all(d["out"])
-                lanes.append(d)
 
-            def row(d, A, r):
-                x = grid.vld(A, d["c0"], r, V) if d["grp"] else [zero] * V
-                return [x[k] if (d["grp"] and d["ein"][k]) else zero for k in range(V)]
+    def ld(A, k, j, i):
+        assert 0 <= i <= n and 0 <= j <= n and 0 <= k <= n, (k, j, i)
+        return A[k, j, i]
 
-            for d in lanes:
-                d["em"], d["ec"] = row(d, grid.Ep, d["r"] - 1), row(d, grid.Ep, d["r"])
-                d["sp"] = d["sc"] = d["gc"] = [zero] * V
+    gx, gy, gz = (n - 1 + J3X - 3) // (J3X - 2), (n - 1 + J3Y2 - 3) // (J3Y2 - 2), (n - 1 + rows - 1) // rows
+    for bz in range(gz):
+        k0 = bz * rows + 1
+        k1 = min(k0 + rows, n)
+        r0 = k0 - 1
+        ra, rb = max(r0, 1), min(k1, n - 1)
+        for by in range(gy):
+            for bx in range(gx):
+                th = {}
+                for ty in range(J3Y2):
+                    for tx in range(J3X):
+                        i, j = bx * (J3X - 2) + tx, by * (J3Y2 - 2) + ty
+                        col_in = 1 <= i <= n - 1 and 1 <= j <= n - 1
+                        il, jl = min(max(i, 1), n - 1), min(max(j, 1), n - 1)
+                        th[ty, tx] = dict(i=i, j=j, il=il, jl=jl, col_in=col_in,
+                                          out=col_in and 1 <= tx <= J3X - 2 and 1 <= ty <= J3Y2 - 2,
+                                          em=ld(E, ra - 1, jl, il), ec=ld(E, ra, jl, il), sp=zero, sc=zero, gc=zero)
+                pl = {}
 
-            def first():
-                res = []
-                left = [lanes[l - 1]["ec"][V - 1] if l > 0 else lanes[l]["ec"][V - 1] for l in range(32)]
-                right = [lanes[l + 1]["ec"][0] if l < 31 else lanes[l]["ec"][0] for l in range(32)]
-                for l, d in enumerate(lanes):
-                    r = d["r"]
+                def first(d, r):
+                    il, jl = d["il"], d["jl"]
                     assert 1 <= r <= n - 1
-                    ep, g = row(d, grid.Ep, r + 1), row(d, grid.Gp, r)
-                    v = []
-                    for k in range(V):
-                        w = d["ec"][k - 1] if k > 0 else left[l]
-                        e = d["ec"][k + 1] if k < V - 1 else right[l]
-                        s = np.float32(np.float32(w + e) + np.float32(d["em"][k] + ep[k]))
-                        y = step32(c1, d["ec"][k], om, s, g[k])
-                        v.append(y if d["inn"][k] else zero)
-                    d["em"], d["ec"], d["r"] = d["ec"], ep, r + 1
-                    res.append((v, g))
-                return res
+                    ep = ld(E, r + 1, jl, il)
+                    s = np.float32(np.float32(np.float32(ld(E, r, jl, il - 1) + ld(E, r, jl, il + 1))
+                                              + np.float32(ld(E, r, jl - 1, il) + ld(E, r, jl + 1, il))) + np.float32(d["em"] + ep))
+                    g = ld(G, r, jl, il)
+                    y = step32(c1, d["ec"], om, s, g)
+                    d["em"], d["ec"] = d["ec"], ep
+                    return (y if d["col_in"] else zero), g
 
-            def second(vs):
-                left = [lanes[l - 1]["sc"][V - 1] if l > 0 else lanes[l]["sc"][V - 1] for l in range(32)]
-                right = [lanes[l + 1]["sc"][0] if l < 31 else lanes[l]["sc"][0] for l in range(32)]
-                for l, d in enumerate(lanes):
-                    for k in range(V):
-                        sw = d["sc"][k - 1] if k > 0 else left[l]
-                        se = d["sc"][k + 1] if k < V - 1 else right[l]
-                        s = np.float32(np.float32(sw + se) + np.float32(d["sp"][k] + vs[l][k]))
-                        o = step32(c1, d["sc"][k], om, s, d["gc"][k])
-                        if d["full"] or d["out"][k]:
-                            assert d["out"][k] and d["c0"] % V == 0
-                            grid.store(d["c0"] + k, d["ro"], o)
-                    d["ro"] += 1
+                def second(x, vs):
+                    for ty in range(J3Y2):
+                        for tx in range(J3X):
+                            d = th[ty, tx]
+                            sw = th[ty, tx - 1]["sc"] if tx > 0 else d["sc"]
+                            se = th[ty, tx + 1]["sc"] if tx < J3X - 1 else d["sc"]
+                            if d["out"]:
+                                ss, sn = pl[x % 3][ty - 1, tx], pl[x % 3][ty + 1, tx]
+                                s = np.float32(np.float32(np.float32(sw + se) + np.float32(ss + sn)) + np.float32(d["sp"] + vs[ty, tx]))
+                                O[x, d["j"], d["i"]] = step32(c1, d["sc"], om, s, d["gc"])
+                                written[x, d["j"], d["i"]] += 1
 
-            if r0 >= 1:
-                for d, (v, _) in zip(lanes, first()):
-                    d["sc"] = v
-            for d, (v, g) in zip(lanes, first()):
-                d["sp"], d["sc"], d["gc"] = d["sc"], v, g
-            for _ in range(j0 + 1, rb + 1):
-                res = first()
-                second([v for v, _ in res])
-                for d, (v, g) in zip(lanes, res):
+                if r0 >= 1:
+                    for d in th.values():
+                        d["sc"], _ = first(d, r0)
+                pl[k0 % 3] = {}
+                for key, d in th.items():
+                    v, g = first(d, k0)
+                    pl[k0 % 3][key] = v
                     d["sp"], d["sc"], d["gc"] = d["sc"], v, g
-            if j1 == n:
-                second([[zero] * V] * 32)
+                for r in range(k0 + 1, rb + 1):
+                    res = {key: first(d, r) for key, d in th.items()}
+                    pl[r % 3] = {key: v for key, (v, _) in res.items()}
+                    second(r - 1, {key: v for key, (v, _) in res.items()})
+                    for key, (v, g) in res.items():
+                        d = th[key]
+                        d["sp"], d["sc"], d["gc"] = d["sc"], v, g
+                if k1 == n:
+                    second(n - 1, {key: zero for key in th})
+    return O, written
 
 
-@pytest.mark.parametrize("V", [2, 4, 8])
-@pytest.mark.parametrize("n,rows", [(2, 1), (3, 1), (8, 3), (17, 8), (31, 4), (64, 63), (127, 8), (130, 16), (260, 5), (512, 16)])
-def test_vector_pair_model_equals_two_sweeps(n, rows, V):
-    E, G = problem(n, 200 + n)
-    grid = PaddedGrid(E, G, n, np.random.default_rng(n))
-    model_x2v(grid, OM, C1, rows, V)
-    grid.check_coverage()
-    want = plain_sweep(plain_sweep(E, G, OM, C1, n), G, OM, C1, n)
-    assert np.array_equal(grid.O[1:n, 1:n], want[1:n, 1:n])
+@pytest.mark.parametrize("n,rows", [(2, 1), (3, 1), (5, 2), (9, 8), (17, 4), (18, 32), (33, 8)])
+def test_3d_pair_model_equals_two_sweeps(n, rows):
+    rng = np.random.default_rng(300 + n)
+    E = np.zeros((n + 1,) * 3, np.float32)
+    G = np.zeros_like(E)
+    E[1:n, 1:n, 1:n] = rng.standard_normal((n - 1,) * 3)
+    G[1:n, 1:n, 1:n] = rng.standard_normal((n - 1,) * 3)
+    O, written = model_x2_3d(E, G, OM, C1, n, rows)
+    assert (written[1:n, 1:n, 1:n] == 1).all() and written.sum() == (n - 1) ** 3
+    want = plain_sweep3(plain_sweep3(E, G, OM, C1, n), G, OM, C1, n)
+    assert np.array_equal(O[1:n, 1:n, 1:n], want[1:n, 1:n, 1:n])

@@ -125,3 +125,23 @@ def test_fused_sweeps_follow_oracle_on_short_runs(homg, precision, schedule):
                                            schedule=schedule)
         assert cyc == k
         assert rel(got, ref) <= TOL[precision], (k, rel(got, ref))
+
+
+@pytest.mark.parametrize("precision,want", [("fp32", 17), ("bf16", 17), ("fp64", 32)])
+def test_3d_plain_sweeps_fuse_two_per_launch(homg, precision, want):
+    # 3-D binary32 lattice cycles pair plain level-0 sweeps too (k_jacobi3_x2); the iterates still
+    # follow the oracle's low-precision cycle
+    import torch
+
+    n, levels = 64, 6
+    f_np = inputs.normal_rhs(n, 3, seed=7)
+    with homg.Solver(3, n + 1, levels, precision=precision, exec_mode="lattice") as s:
+        f = torch.from_numpy(f_np).cuda()
+        u = torch.zeros_like(f)
+        s.solve(f, u, tol=0.0, max_cycles=2)
+        st = s.stats()
+        got = u.cpu().numpy()
+    assert st["fine_iterations_per_cycle"] == 32 and st["fine_launches_per_cycle"] == want
+    if precision != "fp64":
+        ref, _, _, _ = oracle.solve_mixed(f_np, levels, precision, tol=0.0, max_cycles=2)
+        assert rel(got, ref) <= TOL[precision], rel(got, ref)
