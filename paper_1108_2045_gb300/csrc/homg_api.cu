@@ -72,12 +72,6 @@ struct Op {  // one kernel launch of a cycle part
     int block_first = 0, block_count = 0;  // BLOCK: range of the device op list
 };
 
-// Largest lattice (intervals per side) of a single problem whose plain binary32 sweeps run four per
-// launch; larger ones run in pairs (the four-sweep march is instruction bound there).
-#ifndef HOMG_QUAD_MAX_N
-#define HOMG_QUAD_MAX_N 0
-#endif
-
 // Capacity of the coarse-lattice block's op list in the level buffer.
 constexpr int kMaxBlockOps = 1024;
 
@@ -523,11 +517,9 @@ void plan_cycle(homg_ctx* h) {
             auto plain = [&](int q) { return q >= 1 && !(q == c - 1 && m >= 1); };
             for (int q = 0; q < c; ++q) {
                 if (pairable && plain(q) && q + 1 < c && plain(q + 1)) {
-                    // four sweeps where the run allows, in batches (their launches cover every problem
-                    // of the group, where the halved traffic outweighs the longer march) and on the
-                    // small 2-D lattices of one problem (launch latency dominates there); otherwise two
-                    const bool quad = h->ndim == 2 && (h->nbatch > 1 || lv.n <= HOMG_QUAD_MAX_N);
-                    const int k = (quad && q + 3 < c && plain(q + 3)) ? 4 : 2;
+                    // batches: four sweeps where the run allows (their launches cover every problem of
+                    // the group, where the halved traffic outweighs the longer march); otherwise two
+                    const int k = (h->nbatch > 1 && q + 3 < c && plain(q + 3)) ? 4 : 2;
                     Op op{};
                     op.kind = Op::ITER2;
                     op.sweeps = k;

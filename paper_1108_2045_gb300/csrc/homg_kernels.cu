@@ -21,6 +21,8 @@ namespace {
 
 constexpr int BX = 32;
 constexpr int BY = 8;
+constexpr int P2X = 128;  // power-of-two iteration: columns per block (dealt by residue class)
+constexpr int P2Y = 2;
 
 // ---- storage traits -------------------------------------------------------------------------
 template <typename T> struct St;
@@ -53,26 +55,18 @@ template <> struct St<__nv_bfloat16> {
 // (__ldg). Inside the persistent batch kernel (P = true), a phase reads values that other blocks of
 // the same launch wrote in an earlier phase, which the read-only path does not promise to see:
 // those loads go to L2 (__ldcg), the point of coherence, after the grid barrier's fences.
-#ifndef HOMG_PERSIST_L1
-#define HOMG_PERSIST_L1 0
-#endif
-#if HOMG_PERSIST_L1
-#define HOMG_LDP __ldca
-#else
-#define HOMG_LDP __ldcg
-#endif
 template <typename T> __device__ __forceinline__ typename St<T>::C ld_cg(const T* p);
-template <> __device__ __forceinline__ double ld_cg<double>(const double* p) { return HOMG_LDP(p); }
-template <> __device__ __forceinline__ float ld_cg<float>(const float* p) { return HOMG_LDP(p); }
+template <> __device__ __forceinline__ double ld_cg<double>(const double* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ld_cg<float>(const float* p) { return __ldcg(p); }
 template <> __device__ __forceinline__ float ld_cg<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __bfloat162float(__ushort_as_bfloat16(HOMG_LDP(reinterpret_cast<const unsigned short*>(p))));
+    return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p))));
 }
 template <typename T, bool P> __device__ __forceinline__ typename St<T>::C ldv(const T* p) {
     if constexpr (P) return ld_cg<T>(p);
     else return St<T>::ld(p);
 }
 template <bool P> __device__ __forceinline__ double ld64(const double* p) {
-    if constexpr (P) return HOMG_LDP(p);
+    if constexpr (P) return __ldcg(p);
     else return __ldg(p);
 }
 
@@ -1592,11 +1586,22 @@ __device__ __forceinline__ bool p2_marked(int N, int m, int x, int y, int& q, in
 // add the bilinear interpolation of the pending level-mp variation from the node's own quadrant at
 // the nodes not marked at level mp.
 template <typename T>
-__global__ void __launch_bounds__(BX * BY) k_pow2_iterate(Pow2IterArgs a) {
+__global__ void __launch_bounds__(P2X * P2Y) k_pow2_iterate(Pow2IterArgs a) {
     pdl_begin();
     using C = typename St<T>::C;
     const int N = a.N;
-    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+    // Columns by residue class (see k_wholegrid2): with L = min(2^max(m, mp), 4), the block's P2X
+    // columns are dealt so that each warp holds one residue of x mod L, the lattice residue first:
+    // 0 in the left half, L - 1 in the right half (its lattices are marked from x = N - 1). A block
+    // lies in one half when N >= 2 P2X; whether a lane relaxes, or lies on the pending lattice, is
+    // then the same for the whole warp on the level-min(m, 2) lattice.
+    const int mm = a.m > a.mp ? a.m : a.mp;
+    const int L = mm >= 2 ? 4 : 2, per = P2X / L;
+    const int x0 = blockIdx.x * P2X;
+    const int rlat = (x0 >= (N >> 1)) ? L - 1 : 0;
+    const int u = threadIdx.x, cls = u / per;
+    const int x = x0 + (u % per) * L + ((rlat + cls) & (L - 1));
+    const int y = blockIdx.y * P2Y + threadIdx.y;
     if (x >= N || y >= N) return;
     T* O = wp<T>(a.e_new);
     const int64_t po = a.e_new.pitch;
@@ -2027,10 +2032,10 @@ __device__ bool run_segment(const PersistArgs& P, int first, int count, unsigned
 }
 
 template <typename T>
-#ifndef HOMG_PERSIST_MINB
-#define HOMG_PERSIST_MINB 10
-#endif
-__global__ void __launch_bounds__(JX, HOMG_PERSIST_MINB) k_batch_persistent(PersistArgs P) {
+// 10 blocks of JX threads per SM: the union of the bodies then spills to local memory, which
+// measured faster than fewer resident blocks without spills (253 ms for the 1024-problem batch
+// against 437 ms at 4 blocks and 317 ms at 6).
+__global__ void __launch_bounds__(JX, 10) k_batch_persistent(PersistArgs P) {
     const unsigned int target = gridDim.x + (P.stall ? 1u : 0u);
     if (P.stall) {  // self-test: a barrier that cannot complete, before any problem data is touched
         grid_barrier(P, target);
@@ -2143,7 +2148,7 @@ cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs&
 }
 
 cudaError_t launch_pow2_iterate(int prec, const Pow2IterArgs& a, cudaStream_t s) {
-    const dim3 g((unsigned)((a.N + BX - 1) / BX), (unsigned)((a.N + BY - 1) / BY)), b(BX, BY);
+    const dim3 g((unsigned)((a.N + P2X - 1) / P2X), (unsigned)((a.N + P2Y - 1) / P2Y)), b(P2X, P2Y);
     DISPATCH_PREC(prec, (launch_k(k_pow2_iterate<T>, g, b, s, a), cudaGetLastError()));
 }
 
