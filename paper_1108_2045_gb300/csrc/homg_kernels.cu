@@ -19,6 +19,9 @@
 namespace homg {
 namespace {
 
+#define HOMG_PRAGMA(x) _Pragma(#x)
+#define X2V_UNROLL_PRAGMA(u) HOMG_PRAGMA(unroll u)
+
 constexpr int BX = 32;
 constexpr int BY = 8;
 constexpr int P2X = 128;  // power-of-two iteration: columns per block (dealt by residue class)
@@ -786,7 +789,10 @@ __device__ __forceinline__ void jacobi2_body(IterArgs a, int rows, int bx, int b
     }
     C vs = ldv<T, P>(E + (int64_t)(j0 - 1) * pe + i);
     C vc = ldv<T, P>(E + (int64_t)j0 * pe + i);
-#pragma unroll 4
+#ifndef J2_UNROLL
+#define J2_UNROLL 4
+#endif
+    X2V_UNROLL_PRAGMA(J2_UNROLL)
     for (int j = j0; j < j1; ++j) {
         const T* row = E + (int64_t)j * pe + i;
         const C vn = ldv<T, P>(row + pe);
