@@ -19,9 +19,6 @@
 namespace homg {
 namespace {
 
-#define HOMG_PRAGMA(x) _Pragma(#x)
-#define X2V_UNROLL_PRAGMA(u) HOMG_PRAGMA(unroll u)
-
 constexpr int BX = 32;
 constexpr int BY = 8;
 constexpr int P2X = 128;  // power-of-two iteration: columns per block (dealt by residue class)
@@ -789,10 +786,7 @@ __device__ __forceinline__ void jacobi2_body(IterArgs a, int rows, int bx, int b
     }
     C vs = ldv<T, P>(E + (int64_t)(j0 - 1) * pe + i);
     C vc = ldv<T, P>(E + (int64_t)j0 * pe + i);
-#ifndef J2_UNROLL
-#define J2_UNROLL 4
-#endif
-    X2V_UNROLL_PRAGMA(J2_UNROLL)
+#pragma unroll 4
     for (int j = j0; j < j1; ++j) {
         const T* row = E + (int64_t)j * pe + i;
         const C vn = ldv<T, P>(row + pe);
@@ -1425,7 +1419,8 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
     pdl_begin();
     using C = typename St<T>::C;
     const int n = a.e_new.n;
-    const int Lp = a.m >= 2 ? 4 : 2, per = JX / Lp;  // m >= 1 here
+    // (FP64 only: the binary32 arithmetic kernels are memory bound and keep contiguous lanes)
+    const int Lp = std::is_same<T, double>::value ? (a.m >= 2 ? 4 : 2) : 1, per = JX / Lp;  // m >= 1 here
     const int cls = threadIdx.x / per;
     const int off = (threadIdx.x % per) * Lp + ((Lp - 1 - cls) & (Lp - 1));
     const int i = blockIdx.x * JX + off + 1;
@@ -1602,7 +1597,8 @@ __global__ void __launch_bounds__(P2X * P2Y) k_pow2_iterate(Pow2IterArgs a) {
     // lies in one half when N >= 2 P2X; whether a lane relaxes, or lies on the pending lattice, is
     // then the same for the whole warp on the level-min(m, 2) lattice.
     const int mm = a.m > a.mp ? a.m : a.mp;
-    const int L = mm >= 2 ? 4 : 2, per = P2X / L;
+    // (FP64 only: the binary32 arithmetic kernels are memory bound and keep contiguous lanes)
+    const int L = std::is_same<T, double>::value ? (mm >= 2 ? 4 : 2) : 1, per = P2X / L;
     const int x0 = blockIdx.x * P2X;
     const int rlat = (x0 >= (N >> 1)) ? L - 1 : 0;
     const int u = threadIdx.x, cls = u / per;
