@@ -240,6 +240,21 @@ int homg_residual_norm(homg_handle h, const double* f, const double* u, double* 
  * HOMG_EINVAL for n < 0 or a null pointer with n > 0 (message in homg_last_error(NULL)). */
 int homg_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n);
 
+/* Self-test of the two-sweep kernels of binary32 cycles: consecutive plain damped-Jacobi sweeps
+ * (Sec. 2, the relaxation formula) that the fast lattice form fuses two per launch. On a lattice of n
+ * intervals per side (n+1 rows of `pitch` elements; pitch >= n + 2 and even) of `precision`
+ * HOMG_PREC_FP32 (float) or HOMG_PREC_BF16 (bfloat16), two sweeps v' = c1 v + omega (sum of the four
+ * neighbours) + g of the input e_old (binary32 arithmetic, each sweep's values rounded to the storage
+ * type) are written to the interior of e_packed by the kernel with two columns per lane (packed
+ * binary32 pairs) and to the interior of e_column by the kernel with one column per lane; boundary
+ * nodes and padding of both outputs are left untouched, and e_old's boundary nodes are read as
+ * stored. rows: lattice rows per block (0: 8). Device pointers aligned to two elements; runs on the
+ * current device on the legacy default stream and synchronises. The two results must be equal bit
+ * for bit. HOMG_EINVAL for another precision, n < 2, a null pointer, an odd or short pitch or an
+ * unaligned pointer (message in homg_last_error(NULL)). */
+int homg_check_sweep_pair(int precision, int n, int64_t pitch, const void* e_old, const void* g, void* e_packed,
+                          void* e_column, double omega, double c1, int rows);
+
 /* Relative residual before every cycle of the last solve: hist[0] = initial, hist[k] after k
  * cycles. Copies min(cap, cycles + 1) values; returns that count or a negative code. */
 int homg_get_history(homg_handle h, double* hist, int cap);

@@ -2082,6 +2082,32 @@ int homg_check_conversions(const double* d_in, float* f_out, const float* f_in, 
     return HOMG_OK;
 }
 
+int homg_check_sweep_pair(int precision, int n, int64_t pitch, const void* e_old, const void* g, void* e_packed,
+                          void* e_column, double omega, double c1, int rows) {
+    if ((precision != HOMG_PREC_FP32 && precision != HOMG_PREC_BF16) || n < 2 || n > (1 << 20) || rows < 0 ||
+        !e_old || !g || !e_packed || !e_column || !(omega == omega) || !(c1 == c1))
+        return fail(nullptr, HOMG_EINVAL, "homg_check_sweep_pair: bad precision, size, rows or pointer%s%s");
+    IterArgs a;
+    a.e_old = CGrid{e_old, pitch, n};
+    a.g = CGrid{g, pitch, n};
+    a.e_new = Grid{e_column, pitch, n};
+    a.m = 0;
+    a.mp = -1;
+    a.dprev = CGrid{nullptr, pitch, n};
+    a.dnew = Grid{nullptr, pitch, n};
+    a.omega = omega;
+    a.c1 = c1;
+    a.omega_f = (float)omega;
+    a.c1_f = (float)c1;
+    a.rows = rows;
+    cudaError_t e = launch_check_sweep_pair(precision, a, e_packed, nullptr);
+    if (e == cudaErrorInvalidValue)
+        return fail(nullptr, HOMG_EINVAL, "homg_check_sweep_pair: pitch < n + 2, odd, or an unaligned pointer%s%s");
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "homg_check_sweep_pair");
+    return HOMG_OK;
+}
+
 int homg_get_history(homg_handle h, double* hist, int cap) {
     if (!h || !hist || cap < 0) return HOMG_EINVAL;
     const int cnt = std::min(cap, h->stats.cycles + 1);

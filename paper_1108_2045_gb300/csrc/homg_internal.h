@@ -289,6 +289,8 @@ cudaError_t launch_persistent(int prec, const PersistArgs& a, int* blocks, cudaS
 cudaError_t launch_iterate(int ndim, int prec, bool strict, const IterArgs& a, cudaStream_t s);
 // f_out = binary64 -> binary32 (round to nearest even) of d_in, d_out = binary32 -> binary64 of f_in,
 // with the integer conversions of the fast residual kernels (n elements, device pointers).
+bool pairs_ok(int prec, const IterArgs& a);
+cudaError_t launch_check_sweep_pair(int prec, const IterArgs& a, void* out_packed, cudaStream_t s);
 cudaError_t launch_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n,
                                      cudaStream_t s);
 // `sweeps` (2 or 4) plain lattice-form sweeps in one launch (2-D, FP32 / bfloat16 storage, no

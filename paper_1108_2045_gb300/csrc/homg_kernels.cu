@@ -1009,6 +1009,145 @@ __global__ void __launch_bounds__(JX) k_jacobi2_x2(IterArgs a, int rows) {
     jacobi2_x2_body<T, BATCH, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// Packed binary32 pairs: add.f32x2 and fma.f32x2 (sm_100 and later) compute two binary32 results
+// per instruction, each rounded exactly as the scalar instruction rounds it. (Written as PTX: the
+// kernel below measured faster with these than with the runtime's intrinsics for the same
+// instructions, 26.9 against 29.4 us per level-0 launch, at the same 32 registers.)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+// Two adjacent stored values (4-byte aligned bfloat16 pair, 8-byte aligned binary32 pair) as
+// binary32, the store of such a pair, and the storage rounding of a pair (bfloat16: to nearest).
+template <typename T> __device__ __forceinline__ float2 ld2(const T* p);
+template <> __device__ __forceinline__ float2 ld2<float>(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ float2 unpack_bf16x2(unsigned w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+template <> __device__ __forceinline__ float2 ld2<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return unpack_bf16x2(__ldg(reinterpret_cast<const unsigned*>(p)));
+}
+__device__ __forceinline__ unsigned pack_bf16x2_rn(float2 v) {
+    const __nv_bfloat162 t = __floats2bfloat162_rn(v.x, v.y);
+    return *reinterpret_cast<const unsigned*>(&t);
+}
+template <typename T> __device__ __forceinline__ void st2(T* p, float2 v);
+template <> __device__ __forceinline__ void st2<float>(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+template <> __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16* p, float2 v) {
+    *reinterpret_cast<unsigned*>(p) = pack_bf16x2_rn(v);
+}
+template <typename T> __device__ __forceinline__ float2 round2(float2 v) { return v; }
+template <> __device__ __forceinline__ float2 round2<__nv_bfloat16>(float2 v) { return unpack_bf16x2(pack_bf16x2_rn(v)); }
+
+// Two plain damped-Jacobi sweeps in one pass, two adjacent columns per lane (binary32 arithmetic):
+// the march of k_jacobi2_x2 with half the instructions per node. Lane L of a strip holds columns
+// c0 and c0 + 1, c0 = 60 s - 2 + 2 L (even), and reads each row of e and g with one aligned pair
+// load; the side neighbours of its two columns are its own pair and, for the outer ones, the
+// adjacent lanes' (shuffle). Both sweeps run as packed binary32 pairs in the per-column kernel's
+// operation order, so the result is bit-identical to two single sweeps. The first sweep runs on
+// all 64 columns; lanes 1..30 store the second (60 output columns per strip). Pairs are loaded
+// from column min(max(c0, 0), n rounded down to even), which may be the row's padding column
+// n + 1 (the caller guarantees pitch >= n + 2); values of columns outside 1..n-1 are replaced by 0
+// before any unmasked use.
+// The solver uses this kernel for bfloat16 storage on lattices of at least X2P_MIN_N intervals:
+// there the per-column kernel issues about 50 warp instructions per 32 nodes and pair of sweeps and
+// is issue bound (70 % issue active), this one about 29. With binary32 storage (DRAM bound) and on
+// smaller lattices (half as many warps) the per-column kernel measured faster.
+constexpr int X2P_OUT = 60;     // output columns per warp
+constexpr int X2P_MIN_N = 2048;
+template <typename T, bool BATCH>
+__device__ __forceinline__ void jacobi2_x2p_body(IterArgs a, int rows, int bx, int by, int bz) {
+    if (BATCH && !batch_view<T>(a, bz)) return;  // uniform over the block
+    const int n = a.e_new.n;
+    const int lane = threadIdx.x & 31;
+    const int strip = bx * (JX / 32) + (threadIdx.x >> 5);
+    if (strip * X2P_OUT > n - 1) return;  // strip past the last column: the whole warp leaves
+    const int c0 = strip * X2P_OUT - 2 + 2 * lane;
+    const int cl = min(max(c0, 0), n & ~1);
+    const bool m0 = c0 >= 1 && c0 <= n - 1, m1 = c0 + 1 >= 1 && c0 + 1 <= n - 1;  // interior columns
+    const bool mid = lane >= 1 && lane <= 30;
+    const bool o0 = mid && m0, o1 = mid && m1;  // stored columns
+    const int j0 = by * rows + 1;  // second sweep: rows j0 .. j1 - 1
+    const int j1 = min(j0 + rows, n);
+    const int r0 = j0 - 1;         // first sweep: rows r0 .. j1 (0 on rows 0 and n)
+    const int64_t pe = a.e_old.pitch, pg = a.g.pitch, po = a.e_new.pitch;
+    const int ra = max(r0, 1);
+    const T* __restrict__ pE = cp<T>(a.e_old) + (int64_t)ra * pe + cl;  // row r of the march
+    const T* __restrict__ pG = cp<T>(a.g) + (int64_t)ra * pg + cl;
+    T* __restrict__ pO = wp<T>(a.e_new) + (int64_t)j0 * po + c0;        // next output row (stored when o0 or o1)
+    const float2 om = make_float2(a.omega_f, a.omega_f), c1 = make_float2(a.c1_f, a.c1_f);
+    float2 em = ld2<T>(pE - pe), ec = ld2<T>(pE);  // input iterate at rows r - 1, r
+    // first sweep at row r (1 <= r <= n - 1) on the lane's two columns, then advance one row
+    auto first = [&](float2& g) -> float2 {
+        const float2 ep = ld2<T>(pE + pe);
+        g = ld2<T>(pG);
+        const float left = __shfl_up_sync(0xffffffffu, ec.y, 1), right = __shfl_down_sync(0xffffffffu, ec.x, 1);
+        const float2 sum = add2(make_float2(left + ec.y, ec.x + right), add2(em, ep));  // (w + e) + (n + s)
+        float2 v = round2<T>(fma2(c1, ec, fma2(om, sum, g)));
+        v.x = m0 ? v.x : 0.f;
+        v.y = m1 ? v.y : 0.f;
+        em = ec;
+        ec = ep;
+        pE += pe;
+        pG += pg;
+        return v;
+    };
+    float2 s_prev = make_float2(0.f, 0.f), s_cur = s_prev, g_cur = s_prev;  // rows r - 2, r - 1; g at r - 1
+    // second sweep at row r - 1 given the first-sweep values v at row r
+    auto second = [&](float2 v) {
+        const float sw = __shfl_up_sync(0xffffffffu, s_cur.y, 1), se = __shfl_down_sync(0xffffffffu, s_cur.x, 1);
+        const float2 sum = add2(make_float2(sw + s_cur.y, s_cur.x + se), add2(s_prev, v));
+        const float2 o = fma2(c1, s_cur, fma2(om, sum, g_cur));
+        if (o0 && o1) st2<T>(pO, o);
+        else {
+            if (o0) pO[0] = St<T>::put(o.x);
+            if (o1) pO[1] = St<T>::put(o.y);
+        }
+        pO += po;
+    };
+    if (r0 >= 1) s_cur = first(g_cur);  // row r0 (its g is never used)
+    {
+        float2 g;
+        const float2 v = first(g);  // row j0
+        s_prev = s_cur;
+        s_cur = v;
+        g_cur = g;
+    }
+    const int rb = min(j1, n - 1);
+#pragma unroll 4
+    for (int r = j0 + 1; r <= rb; ++r) {
+        float2 g;
+        const float2 v = first(g);
+        second(v);
+        s_prev = s_cur;
+        s_cur = v;
+        g_cur = g;
+    }
+    if (j1 == n) second(make_float2(0.f, 0.f));  // the first-sweep value on the boundary row n is 0
+}
+
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(JX, 16) k_jacobi2_x2p(IterArgs a, int rows) {  // 32 registers: full occupancy
+    pdl_begin();
+    jacobi2_x2p_body<T, BATCH>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // K plain damped-Jacobi sweeps in one pass (K >= 3; binary32 arithmetic), the K-level form of
 // k_jacobi2_x2: each warp marches a strip of 32 columns; step r computes sweep 1 at row r, sweep 2
 // at row r - 1, ..., sweep K at row r - K + 1 (the output), each from the previous sweep's values
@@ -2093,6 +2232,20 @@ cudaError_t launch_iterate3_2(int prec, const IterArgs& a, cudaStream_t s) {
     }
 }
 
+// The packed pair kernel's layout conditions: every row holds the padding column n + 1, and every
+// pair load (even column, every problem of a batch) is aligned to two elements.
+bool pairs_ok(int prec, const IterArgs& a) {
+    if (prec != PREC_FP32 && prec != PREC_BF16) return false;
+    const size_t es = (prec == PREC_FP32) ? sizeof(float) : sizeof(__nv_bfloat16);
+    const int n = a.e_new.n;
+    auto fits = [&](const void* p, int64_t pitch, int64_t bstride) {
+        return p != nullptr && pitch >= (int64_t)n + 2 && pitch % 2 == 0 && bstride % 2 == 0 &&
+               reinterpret_cast<uintptr_t>(p) % (2 * es) == 0;
+    };
+    return fits(a.e_old.p, a.e_old.pitch, a.e_old.bstride) && fits(a.g.p, a.g.pitch, a.g.bstride) &&
+           fits(a.e_new.p, a.e_new.pitch, a.e_new.bstride);
+}
+
 cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_t s) {
     if (sweeps == 4) {
         if (prec == PREC_FP32) return iterate_k_t<float, 4>(a, s);
@@ -2105,8 +2258,15 @@ cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_
     // further than a single sweep does, to keep that overhead small
     const double nodes = (double)a.nb * (double)(n - 1) * (double)(n - 1);
     const int rows = a.rows > 0 ? a.rows : (nodes >= 1.0e6 ? 16 : 8);
+    const dim3 b(JX);
+    if (prec == PREC_BF16 && n >= X2P_MIN_N && pairs_ok(prec, a)) {
+        const int xp = (((n + X2P_OUT - 1) / X2P_OUT) + JX / 32 - 1) / (JX / 32);  // strips cover columns 0 .. n - 1
+        const dim3 g((unsigned)xp, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb);
+        return a.bst ? launch_k(k_jacobi2_x2p<__nv_bfloat16, true>, g, b, s, a, rows)
+                     : launch_k(k_jacobi2_x2p<__nv_bfloat16, false>, g, b, s, a, rows);
+    }
     const int xb = (((n - 1 + X2_OUT - 1) / X2_OUT) + JX / 32 - 1) / (JX / 32);  // blocks across: JX / 32 strips each
-    const dim3 g((unsigned)xb, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
+    const dim3 g((unsigned)xb, (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb);
     switch (prec) {
         case PREC_FP32:
             return a.bst ? launch_k(k_jacobi2_x2<float, true>, g, b, s, a, rows) : launch_k(k_jacobi2_x2<float, false>, g, b, s, a, rows);
@@ -2115,6 +2275,27 @@ cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_
                          : launch_k(k_jacobi2_x2<__nv_bfloat16, false>, g, b, s, a, rows);
         default: return cudaErrorInvalidValue;  // FP64 sweeps are FP64-bound: never paired
     }
+}
+
+// The library's self-test of the two-sweep kernels: the packed kernel writes into out_packed, the
+// per-column kernel into a.e_new, from the same input.
+cudaError_t launch_check_sweep_pair(int prec, const IterArgs& a, void* out_packed, cudaStream_t s) {
+    IterArgs p = a;
+    p.e_new.p = out_packed;
+    if (!pairs_ok(prec, a) || !pairs_ok(prec, p)) return cudaErrorInvalidValue;
+    const int n = a.e_new.n, rows = a.rows > 0 ? a.rows : 8;
+    const dim3 b(JX);
+    const dim3 gp((unsigned)((((n + X2P_OUT - 1) / X2P_OUT) + JX / 32 - 1) / (JX / 32)), (unsigned)((n - 1 + rows - 1) / rows));
+    const dim3 gc((unsigned)((((n - 1 + X2_OUT - 1) / X2_OUT) + JX / 32 - 1) / (JX / 32)), gp.y);
+    cudaError_t e;
+    if (prec == PREC_FP32) {
+        e = launch_k(k_jacobi2_x2p<float, false>, gp, b, s, p, rows);
+        if (e == cudaSuccess) e = launch_k(k_jacobi2_x2<float, false>, gc, b, s, a, rows);
+    } else {
+        e = launch_k(k_jacobi2_x2p<__nv_bfloat16, false>, gp, b, s, p, rows);
+        if (e == cudaSuccess) e = launch_k(k_jacobi2_x2<__nv_bfloat16, false>, gc, b, s, a, rows);
+    }
+    return e;
 }
 
 __global__ void k_check_conversions(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n) {

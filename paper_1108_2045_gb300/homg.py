@@ -40,6 +40,7 @@ EXPORTS = [
     "homg_destroy",
     "homg_residual_norm_noalloc",
     "homg_check_conversions",
+    "homg_check_sweep_pair",
     "homg_fp64_issue_probe",
     "homg_batch_create",
     "homg_batch_set_stream",
@@ -167,6 +168,8 @@ def load(path=LIB_PATH):
     lib.homg_last_error.restype = ctypes.c_char_p
     lib.homg_residual_norm_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), vp, vp, dp, vp]
     lib.homg_fp64_issue_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, dp]
+    lib.homg_check_sweep_pair.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int]
     lib.homg_destroy.argtypes = [vp]
     lib.homg_destroy.restype = None
     vpp = ctypes.POINTER(ctypes.c_void_p)
@@ -426,6 +429,27 @@ def homg_fp64_issue_probe(op, blocks, iters, sink, stream=None):
     _check(load().homg_fp64_issue_probe(op, blocks, iters, _devptr(sink, "sink"), ctypes.c_void_p(raw),
                                         ctypes.byref(instr)), None)
     return instr.value
+
+
+def homg_check_sweep_pair(e_old, g, e_packed, e_column, n, omega, c1, rows=0):
+    """Both two-sweep kernels of binary32 cycles on one lattice of n intervals (the library's
+    self-test): two damped-Jacobi sweeps of e_old with source g, by the packed kernel into e_packed
+    and by the per-column kernel into e_column (interiors only). All four are device tensors of
+    shape (n + 1, pitch), float32 or bfloat16 alike, pitch >= n + 2 and even."""
+    import torch
+
+    kinds = {torch.float32: HOMG_PREC_FP32, torch.bfloat16: HOMG_PREC_BF16}
+    ts = (e_old, g, e_packed, e_column)
+    if e_old.dtype not in kinds or any(t.dtype != e_old.dtype for t in ts):
+        raise TypeError("e_old, g, e_packed and e_column must all be float32 or all bfloat16")
+    if any(t.dim() != 2 or t.shape != e_old.shape or not t.is_contiguous() or t.device != e_old.device for t in ts):
+        raise TypeError("e_old, g, e_packed and e_column must be contiguous 2-D tensors of one shape and device")
+    if e_old.shape[0] != n + 1:
+        raise TypeError("the tensors must have n + 1 rows")
+    with torch.cuda.device(e_old.device):
+        _check(load().homg_check_sweep_pair(kinds[e_old.dtype], int(n), ctypes.c_int64(e_old.shape[1]),
+                                            *(_devptr_any(t, nm) for t, nm in zip(ts, ("e_old", "g", "e_packed", "e_column"))),
+                                            float(omega), float(c1), int(rows)), None)
 
 
 def homg_check_conversions(d_in, f_in):

@@ -1,5 +1,6 @@
-"""A CPU model of the fused-sweep kernels' launch geometry: k_jacobi2_x2 (two sweeps) and
-k_jacobi2_xk (K sweeps), restated step by step as the kernels march. The model covers warp strips
+"""A CPU model of the fused-sweep kernels' launch geometry: k_jacobi2_x2 (two sweeps),
+k_jacobi2_x2p (two sweeps, two columns per lane) and k_jacobi2_xk (K sweeps), restated step by step
+as the kernels march. The model covers warp strips
 of 32 lanes with 30 (34 - 2K) owning lanes, blocks of four strips, clamped load columns and rows,
 the peeled boundary rows, and the register windows and shuffles.
 
@@ -120,6 +121,95 @@ def model_x2(grid, om, c1, rows):
                 second([np.float32(0)] * 32)
 
 
+def model_x2p(E, G, om, c1, n, rows, pitch):
+    """k_jacobi2_x2p: two sweeps with two adjacent columns per lane (one aligned pair load per row of
+    e and of g, packed binary32 arithmetic). Lane L of strip s holds columns c0, c0 + 1 with
+    c0 = 60 s - 2 + 2 L; the pair is loaded from column min(max(c0, 0), n rounded down to even),
+    which may reach the row's padding (column n + 1 < pitch). The first sweep runs on both columns
+    of every lane, side neighbours from the lane's own pair or the adjacent lane's (shuffle);
+    lanes 1..30 store the second sweep (60 columns). E and G are (n+1) x pitch arrays whose
+    padding holds NaN, so that a padding value reaching an unmasked result shows. Returns the
+    output and the write counts."""
+    O = np.zeros_like(E)
+    written = np.zeros(E.shape, dtype=int)
+    zero = np.float32(0)
+    ne = n & ~1
+
+    def ld2(A, c, r):
+        assert c % 2 == 0 and 0 <= c and c + 1 <= pitch - 1 and 0 <= r <= n, (c, r)
+        return [A[r, c], A[r, c + 1]]
+
+    strips = (n + 59) // 60
+    xb = (strips + JX // 32 - 1) // (JX // 32)
+    for by in range((n - 1 + rows - 1) // rows):
+        j0 = by * rows + 1
+        j1 = min(j0 + rows, n)
+        r0, ra, rb = j0 - 1, max(j0 - 1, 1), min(j1, n - 1)
+        for strip in range(xb * (JX // 32)):
+            if 60 * strip > n - 1:
+                continue  # the whole warp leaves
+            lanes = []
+            for lane in range(32):
+                c0 = 60 * strip - 2 + 2 * lane
+                cl = min(max(c0, 0), ne)
+                m = [1 <= c0 + k <= n - 1 for k in range(2)]
+                o = [m[k] and 1 <= lane <= 30 for k in range(2)]
+                lanes.append(dict(c0=c0, cl=cl, m=m, o=o, r=ra, ro=j0, em=ld2(E, cl, ra - 1), ec=ld2(E, cl, ra),
+                                  sp=[zero, zero], sc=[zero, zero], gc=[zero, zero]))
+
+            def first_all():
+                left = [d["ec"][1] for d in lanes]
+                right = [d["ec"][0] for d in lanes]
+                up, _ = shuffles(left)
+                _, down = shuffles(right)
+                res = []
+                for lane, d in enumerate(lanes):
+                    r = d["r"]
+                    assert 1 <= r <= n - 1
+                    ep = ld2(E, d["cl"], r + 1)
+                    g = ld2(G, d["cl"], r)
+                    ec, em = d["ec"], d["em"]
+                    w = [up[lane], ec[0]]
+                    e = [ec[1], down[lane]]
+                    v = []
+                    for k in range(2):
+                        s = np.float32(np.float32(w[k] + e[k]) + np.float32(em[k] + ep[k]))
+                        y = step32(c1, ec[k], om, s, g[k])
+                        v.append(y if d["m"][k] else zero)
+                    d["em"], d["ec"], d["r"] = ec, ep, r + 1
+                    res.append((v, g))
+                return res
+
+            def second(vs):
+                up, _ = shuffles([d["sc"][1] for d in lanes])
+                _, down = shuffles([d["sc"][0] for d in lanes])
+                for lane, d in enumerate(lanes):
+                    sc = d["sc"]
+                    sw = [up[lane], sc[0]]
+                    se = [sc[1], down[lane]]
+                    for k in range(2):
+                        s = np.float32(np.float32(sw[k] + se[k]) + np.float32(d["sp"][k] + vs[lane][k]))
+                        y = step32(c1, sc[k], om, s, d["gc"][k])
+                        if d["o"][k]:
+                            O[d["ro"], d["c0"] + k] = y
+                            written[d["ro"], d["c0"] + k] += 1
+                    d["ro"] += 1
+
+            if r0 >= 1:
+                for d, (v, g) in zip(lanes, first_all()):
+                    d["sc"], d["gc"] = v, g
+            for d, (v, g) in zip(lanes, first_all()):
+                d["sp"], d["sc"], d["gc"] = d["sc"], v, g
+            for _ in range(j0 + 1, rb + 1):
+                res = first_all()
+                second([v for v, _ in res])
+                for d, (v, g) in zip(lanes, res):
+                    d["sp"], d["sc"], d["gc"] = d["sc"], v, g
+            if j1 == n:
+                second([[zero, zero]] * 32)
+    return O, written
+
+
 def model_xk(grid, om, c1, rows, K):
     """k_jacobi2_xk<K>: sweep l at row r - l + 1 in step r, loads from rows clamped into 0..n, sweep
     values outside rows/columns 1..n-1 replaced by 0, the 34 - 2K inner lanes storing sweep K."""
@@ -189,6 +279,20 @@ def test_two_sweep_model_equals_two_sweeps(n, rows):
     grid.check_coverage()
     want = plain_sweep(plain_sweep(E, G, OM, C1, n), G, OM, C1, n)
     assert np.array_equal(grid.O[1:n, 1:n], want[1:n, 1:n])
+
+
+@pytest.mark.parametrize("n,rows", [(2, 1), (3, 1), (4, 2), (17, 8), (32, 16), (60, 4), (61, 7), (64, 63),
+                                    (120, 16), (128, 16), (130, 5), (256, 16)])
+def test_packed_pair_model_equals_two_sweeps(n, rows):
+    pitch = -(-(n + 1) // 16) * 16
+    E, G = problem(n, 200 + n)
+    Ep = np.full((n + 1, pitch), np.nan, np.float32)
+    Gp = np.full((n + 1, pitch), np.nan, np.float32)
+    Ep[:, :n + 1], Gp[:, :n + 1] = E, G
+    O, written = model_x2p(Ep, Gp, OM, C1, n, rows, pitch)
+    assert (written[1:n, 1:n] == 1).all() and written.sum() == (n - 1) ** 2
+    want = plain_sweep(plain_sweep(E, G, OM, C1, n), G, OM, C1, n)
+    assert np.array_equal(O[1:n, 1:n], want[1:n, 1:n])
 
 
 @pytest.mark.parametrize("K", [3, 4])
