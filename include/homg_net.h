@@ -93,6 +93,13 @@ int homg_net_train_step(homg_net_handle net, const void* x, const float* t, int 
 int homg_net_gather_patches(homg_net_handle net, const void* x, const float* t, int H, int W, const int32_t* corners,
                             int B, int P, void* xp, float* tp);
 
+/* Output rows per convolution tile (4 or 8, default 4; HOMG_EINVAL otherwise). A tile's
+ * accumulators take rows x 32 TMEM columns and its staged input rows + 2 band rows of shared
+ * memory; taller tiles make wider tensor-core instructions (a slice of up to three vertical taps
+ * per instruction, see homg_net.cu) and fewer of them per output row. Results do not depend on it.
+ * A tuning option of this library's network; the paper has no counterpart. */
+int homg_net_set_tile_rows(homg_net_handle net, int rows);
+
 /* Self-test of the failure path: launches one convolution whose tensor-core completion barrier
  * is never signalled (no MMA is issued). Every wait on such a barrier gives up after 0.5 s, records
  * the failure and frees the block's tensor memory, so the call returns HOMG_ECUDA with a timeout

@@ -2,21 +2,27 @@
 //
 // A 4-layer 3x3 convolutional network (2 -> 32 -> 32 -> 32 -> 1 channels) in bfloat16 with binary32
 // accumulation. Every convolution is an implicit GEMM on the tcgen05 tensor cores: a CTA stages a
-// band of input rows (with a one-pixel halo) in shared memory, and the A operand of each of the
-// nine taps is the same band read through a shifted shared-memory descriptor -- no im2col copy.
-// Rows of A are 128 consecutive output pixels of one image row (M = 128), columns are input
-// channels (K = 16 per instruction), B holds the packed weights of the tap (N = output channels),
-// and the accumulators of a CTA's four output rows live in tensor memory (TMEM) until an
-// epilogue reads them back with tcgen05.ld. One thread issues the MMAs; completion is signalled
-// through an mbarrier whose wait is bounded (the kernel records an error and frees its TMEM
-// rather than spin forever).
+// band of input rows (with a one-pixel halo) in shared memory, and the A operand of each product
+// is one band row read through a shifted shared-memory descriptor -- no im2col copy. Rows of A are
+// 128 consecutive pixels of one band row (M = 128), columns are input channels (K = 16 per
+// instruction). The accumulators of a CTA's R output rows (R x COUT TMEM columns, row r at columns
+// r COUT ..) live in tensor memory (TMEM) until an epilogue reads them back with tcgen05.ld.
+// Band row rho at column shift dx feeds output rows rho - dy for the three vertical taps dy, so
+// one instruction covers all of them: B stacks the weights of taps (2, dx), (1, dx), (0, dx) (3
+// COUT rows) and the instruction takes the contiguous slice of that stack whose output rows exist,
+// N = COUT, 2 COUT or 3 COUT wide, writing the adjacent accumulators of those rows. That makes
+// about a third as many instructions as one per tap and output row, each up to three times wider.
+// One thread issues the MMAs; completion is signalled through an mbarrier whose wait is bounded
+// (the kernel records an error and frees its TMEM rather than spin forever).
 //
 // Activations use a row-chunked layout: element (b, c, y, x) of a [B, C, H, W] tensor at
 // ((b*H + y)*(C/8) + c/8)*W*8 + x*8 + c%8, so that, for a fixed row and group of 8 channels, the
 // pixels' 16-byte chunks are contiguous -- exactly the core-matrix rows of the no-swizzle
-// K-major operand layout. A CTA's input band arrives by one TMA tensor copy: the layout is a 5-D
-// tensor (8 channels, W pixels, C/8 groups, H rows, B images) whose box (8 x 130 x C/8 x 6 x 1)
-// lands in shared memory in exactly the band's order, zero-filled outside the image.
+// K-major operand layout. Input rows arrive by TMA tensor copies: the layout is a 5-D tensor
+// (8 channels, W pixels, C/8 groups, H rows, B images) whose box (8 x 130 x C/8 x 1 x 1) -- one
+// input row with a one-pixel halo, zero-filled outside the image -- lands in a slot of a ring of
+// staged rows in exactly the operand's order. A CTA walks down a column of tiles, so each tile
+// loads only its R new rows, ahead of time (see k_conv3x3).
 //
 // Training kernels: weight packing (forward and transposed/flipped for the data gradient), the
 // MSE loss and its gradient, the weight gradient (CUDA cores, binary32), Adam. Solver-side
@@ -42,7 +48,6 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int TW = 128;           // output pixels per accumulator row (MMA M)
-constexpr int TR = 4;             // output rows per CTA tile (one accumulator each)
 constexpr int BANDW = TW + 2;     // staged pixels per band row (one-pixel halo each side)
 constexpr int NT = 128;           // threads per conv CTA: one per TMEM lane
 constexpr long long kWaitNs = 500000000ll;  // a barrier wait gives up after 0.5 s
@@ -167,7 +172,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&t);
 }
-
 // ---- the convolution ------------------------------------------------------------------------
 enum ConvMode { CONV_RELU = 0, CONV_LAST = 1, CONV_MASK = 2 };
 
@@ -182,34 +186,45 @@ struct ConvArgs {
     int B, H, W;
     int* err;
     int unsignalled;    // self-test of the bounded wait: issue no MMA, so the barrier never completes
+    int rows;           // output rows per CTA tile: 4 or 8
 };
 
-template <int CIN, int COUT>
+// R output rows per CTA tile (R + 2 staged band rows, one accumulator per output row).
+template <int CIN, int COUT, int R>
 struct ConvShape {
     static constexpr int GI = CIN / 8, GO = COUT / 8, KS = CIN / 16;
-    static constexpr int BAND = (TR + 2) * GI * BANDW * 16;
+    static constexpr int BOXB = GI * BANDW * 16;  // one staged input row (all channel groups)
+    // ring slot of a row, padded so every slot starts on the 128-byte boundary that a TMA tensor
+    // copy's shared-memory destination needs
+    static constexpr int ROWB = (BOXB + 127) / 128 * 128;
+    static constexpr int NRING = 2 * R + 2;         // staged rows: this tile's R + 2 and the next tile's R
+    static constexpr int RING = NRING * ROWB;
     static constexpr int WB = 9 * GI * COUT * 16;
-    static constexpr uint32_t NCOLS = TR * COUT;
+    static constexpr uint32_t NCOLS = R * COUT;
     // Shared memory requested per CTA: at least enough that no more CTAs fit on one SM (228 KB)
     // than its 512 TMEM columns can hold at once, so no CTA ever waits in tcgen05.alloc.
-    static constexpr int SMEM_USED = BAND + WB + 32;
+    static constexpr int SMEM_USED = RING + WB + 32;
     static constexpr int SMEM_FLOOR = 233472 / (int)(512 / NCOLS + 1) + 1024;
     static constexpr int SMEM = SMEM_USED > SMEM_FLOOR ? SMEM_USED : SMEM_FLOOR;
-    static constexpr uint32_t IDESC = idesc_bf16(TW, COUT);
+    // instruction shapes of a slice of one, two or three stacked taps
+    static constexpr uint32_t IDESC1 = idesc_bf16(TW, COUT), IDESC2 = idesc_bf16(TW, 2 * COUT),
+                              IDESC3 = idesc_bf16(TW, 3 * COUT);
     static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "shape");
+    static_assert(R == 4 || R == 8, "rows per tile");
+    static_assert(ROWB % 128 == 0 && RING % 128 == 0 && WB % 16 == 0, "TMA and descriptor alignment");
     static_assert(NCOLS >= 32 && (NCOLS & (NCOLS - 1)) == 0, "TMEM allocation must be a power of two >= 32");
 };
 
-template <int CIN, int COUT, int MODE>
+template <int CIN, int COUT, int MODE, int R>
 __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constant__ CUtensorMap tmap) {
-    using S = ConvShape<CIN, COUT>;
-    constexpr int GI = S::GI, GO = S::GO;
+    using S = ConvShape<CIN, COUT, R>;
+    constexpr int GI = S::GI, GO = S::GO, NRING = S::NRING, ROWB = S::ROWB;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* band = smem;
-    unsigned char* wsm = smem + S::BAND;
+    unsigned char* ring = smem;
+    unsigned char* wsm = smem + S::RING;
     uint64_t* bar = reinterpret_cast<uint64_t*>(wsm + S::WB);  // MMA completion
-    uint64_t* tbar = bar + 1;                                     // band arrival (TMA)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    uint64_t* tbar = bar + 1;                                     // row arrival (TMA), two alternating
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
     __shared__ float sbias[COUT];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int H = a.H, W = a.W;
@@ -220,6 +235,7 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constan
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_init(tbar, 1);
+        mbar_init(tbar + 1, 1);
     }
     if (warp == 0) tmem_alloc(tslot, S::NCOLS);
     cp_async_wait_all();
@@ -229,42 +245,97 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constan
     tc_fence_after();
     const uint32_t tbase = *tslot;
 
-    const int tx = (W + TW - 1) / TW, ty = (H + TR - 1) / TR;
+    // Tiles in column-major order (image, tile column, tile row); each CTA walks one contiguous
+    // chunk, so consecutive tiles of a column share two input rows. Input row y (-1 .. H) lives in
+    // ring slot (y + 1) mod NRING: a tile needs R + 2 consecutive slots, and the next tile of the
+    // same column adds R rows in slots only the previous tile used. Thread 0 loads those rows (one
+    // TMA copy per row, zero-filled outside the image) at the start of a tile, so they arrive while
+    // the tile's products and epilogue run; at a column change the ring is reloaded once the
+    // current tile's products have completed.
+    const int tx = (W + TW - 1) / TW, ty = (H + R - 1) / R;
     const long long tiles = (long long)a.B * ty * tx;
-    uint32_t parity = 0, tparity = 0;
-    bool ok = true, copy_pending = false, mma_pending = false;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int b = (int)(t / ((long long)ty * tx));
-        const int rem = (int)(t % ((long long)ty * tx));
-        const int y0 = (rem / tx) * TR, x0 = (rem % tx) * TW;
-        // input rows y0-1 .. y0+TR and pixels x0-1 .. x0+TW (zero outside the image): one TMA copy
-        if (tid == 0) {
-            mbar_expect_tx(tbar, (uint32_t)S::BAND);
-            tma_load_5d(band, &tmap, 0, x0 - 1, 0, y0 - 1, b, tbar);
+    const long long chunk = (tiles + gridDim.x - 1) / gridDim.x;
+    const long long u0 = (long long)blockIdx.x * chunk;
+    const long long u1 = u0 + chunk < tiles ? u0 + chunk : tiles;
+    auto coords = [&](long long u, int& b, int& xt, int& yt) {
+        yt = (int)(u % ty);
+        const long long c = u / ty;
+        xt = (int)(c % tx);
+        b = (int)(c / tx);
+    };
+    // rows [ya, yb] of tile u's column, arriving on tbar[k & 1]
+    auto load_rows = [&](long long u, int ya, int yb, int k) {
+        int b, xt, yt;
+        coords(u, b, xt, yt);
+        mbar_expect_tx(tbar + (k & 1), (uint32_t)((yb - ya + 1) * S::BOXB));
+        for (int y = ya; y <= yb; ++y)
+            tma_load_5d(ring + ((y + 1) % NRING) * ROWB, &tmap, 0, xt * TW - 1, 0, y, b, tbar + (k & 1));
+    };
+    auto same_column = [&](long long u, long long v) { return u / ty == v / ty; };
+    uint32_t parity = 0, tph = 0;  // tph bit j: phase of tbar[j]
+    bool ok = true, mma_pending = false;
+    int pending = 0;               // bit j: a copy on tbar[j] was issued and not yet waited for
+    if (tid == 0 && u0 < u1) {
+        const int yt = (int)(u0 % ty);
+        load_rows(u0, yt * R - 1, yt * R + R, 0);
+    }
+    pending = u0 < u1 ? 1 : 0;
+    int k = 0;
+    for (long long u = u0; u < u1; ++u, ++k) {
+        int b, xt, yt;
+        coords(u, b, xt, yt);
+        const int y0 = yt * R, x0 = xt * TW;
+        const bool next = u + 1 < u1, cont = next && same_column(u, u + 1);
+        if (cont) {  // the next tile's R new rows go to slots only the previous tile read
+            if (tid == 0) load_rows(u + 1, y0 + R + 1, y0 + 2 * R, k + 1);
+            pending |= 1 << ((k + 1) & 1);
         }
-        const bool arrived = mbar_wait(tbar, tparity);
-        tparity ^= 1u;
+        const int j = k & 1;
+        const bool arrived = mbar_wait(tbar + j, (tph >> j) & 1u);
+        tph ^= 1u << j;
+        pending &= ~(1 << j);
         if (!__syncthreads_and(arrived)) {
             ok = false;
-            copy_pending = true;
+            pending |= 1 << j;  // still to be waited for (its phase bit is flipped back below)
+            tph ^= 1u << j;
             break;
         }
         if (tid == 0 && !a.unsignalled) {
             tc_fence_after();
-            const uint32_t bb = smem_u32(band), wb = smem_u32(wsm);
-#pragma unroll 1
-            for (int r = 0; r < TR; ++r)
-#pragma unroll 1
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = tap / 3, dx = tap % 3;
+            // Descriptors advance in 16-byte units, so every operand address below is a base
+            // descriptor plus a compile-time offset (the loops are unrolled): a few instructions
+            // per MMA, where one thread has to keep the tensor pipe fed.
+            constexpr uint32_t LBO_B = 3 * COUT * 16;  // between the 8-channel groups of a tap stack
+            const uint64_t bdesc = sdesc(smem_u32(wsm), LBO_B, 128);
+            const uint32_t rb = smem_u32(ring);
+            int slot = y0 % NRING;  // ring slot of band row 0 (input row y0 - 1)
+            // Band row rho (input row y0 - 1 + rho) feeds output rows rf..rl (dy = rho - r in 0..2);
+            // the stack slice starts at the tap of the largest dy, rho - rf. Output row rho (dy = 0)
+            // gets its first product at dx = 0, s = 0: that instruction is split so the row starts
+            // from zero while the rows above it keep accumulating.
+#pragma unroll
+            for (int rho = 0; rho < R + 2; ++rho) {
+                const int rf = rho > 2 ? rho - 2 : 0, rl = rho < R - 1 ? rho : R - 1;
+                const int nr = rl - rf + 1;
+                const uint32_t dcol = tbase + (uint32_t)(rf * COUT);
+                const uint64_t arow = sdesc(rb + (uint32_t)(slot * ROWB), BANDW * 16, 128);
+                slot = slot + 1 == NRING ? 0 : slot + 1;
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                     for (int s = 0; s < S::KS; ++s) {
-                        const uint32_t aa = bb + (uint32_t)((((r + dy) * GI + 2 * s) * BANDW + dx) * 16);
-                        const uint32_t ba = wb + (uint32_t)(((tap * GI + 2 * s) * COUT) * 16);
-                        tc_mma(tbase + (uint32_t)(r * COUT), sdesc(aa, BANDW * 16, 128), sdesc(ba, COUT * 16, 128),
-                               S::IDESC, (tap | s) != 0);
+                        const uint64_t ad = arow + (uint64_t)((2 * s) * BANDW + dx);
+                        const uint64_t bs = bdesc + (uint64_t)((dx * GI + 2 * s) * 3 * COUT);
+                        const uint64_t bd = bs + (uint64_t)((2 - (rho - rf)) * COUT);
+                        if (rho < R && dx == 0 && s == 0) {
+                            if (nr > 1) tc_mma(dcol, ad, bd, nr == 3 ? S::IDESC2 : S::IDESC1, 1u);
+                            tc_mma(tbase + (uint32_t)(rho * COUT), ad, bs + (uint64_t)(2 * COUT), S::IDESC1, 0u);
+                        } else {
+                            tc_mma(dcol, ad, bd, nr == 3 ? S::IDESC3 : (nr == 2 ? S::IDESC2 : S::IDESC1), 1u);
+                        }
                     }
                 }
+            }
             tc_commit(bar);
         }
         const bool done = mbar_wait(bar, parity);
@@ -275,9 +346,15 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constan
             mma_pending = !a.unsignalled;
             break;
         }
+        if (next && !cont) {  // a new column: every slot is free once the products have completed
+            int b1, xt1, yt1;
+            coords(u + 1, b1, xt1, yt1);
+            if (tid == 0) load_rows(u + 1, yt1 * R - 1, yt1 * R + R, k + 1);
+            pending |= 1 << ((k + 1) & 1);
+        }
         // epilogue: thread tid holds pixel x0 + tid of each accumulator row
 #pragma unroll 1
-        for (int r = 0; r < TR; ++r) {
+        for (int r = 0; r < R; ++r) {
             float v[COUT];
             const uint32_t ta = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * COUT);
             if (COUT == 32) tmem_ld32(ta, v);
@@ -320,11 +397,13 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constan
         __syncthreads();
     }
     if (!ok) {
-        // a band copy or an MMA batch did not report completion in time: record it, give it one
-        // more bounded wait (on the phase it was issued in) before shared and tensor memory are
-        // released, and leave (the self-test issues no MMA, so there is nothing to wait for)
+        // a row copy or an MMA batch did not report completion in time: record it, give every copy
+        // still in flight and the MMA batch one more bounded wait (on the phase each was issued in)
+        // before shared and tensor memory are released, and leave (the self-test issues no MMA, so
+        // there is no batch to wait for)
         if (tid == 0) atomicExch(a.err, 1);
-        if (copy_pending) mbar_wait(tbar, tparity ^ 1u);
+        for (int j = 0; j < 2; ++j)
+            if (pending & (1 << j)) mbar_wait(tbar + j, (tph >> j) & 1u);
         if (mma_pending) mbar_wait(bar, parity ^ 1u);
         __syncthreads();
     }
@@ -335,16 +414,19 @@ __global__ void __launch_bounds__(NT) k_conv3x3(ConvArgs a, const __grid_constan
 }
 
 // ---- weight packing -------------------------------------------------------------------------
-// Forward: packed[((tap*GI + ci/8)*COUTP + co)*8 + ci%8] = bf16(W[co][ci][p][q]), tap = 3p + q.
+// Taps (p, q) = (row, column) offsets, stacked per column offset q in the order p = 2, 1, 0:
+// Forward: packed[((q*GI + ci/8)*3*COUTP + (2-p)*COUTP + co)*8 + ci%8] = bf16(W[co][ci][p][q]).
 // Transposed (the data gradient of the layer is a convolution from its O outputs back to its C
-// inputs with the kernel flipped in space): packed'[((tap*GI' + o/8)*COUTP' + c)*8 + o%8] =
+// inputs with the kernel flipped in space): the same layout with O and C exchanged holding
 // bf16(W[o][c][2-p][2-q]). Zero for padded channels.
 __global__ void k_pack(const float* W, int O, int C, int cinp, int coutp, int transposed, bf16* out) {
     const int total = 9 * cinp * coutp;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int e = idx % 8, n = (idx / 8) % coutp, g = (idx / (8 * coutp)) % (cinp / 8), tap = idx / (8 * coutp * (cinp / 8));
-    const int k = 8 * g + e, p = tap / 3, q = tap % 3;
+    const int e = idx % 8, row = (idx / 8) % (3 * coutp), g = (idx / (8 * 3 * coutp)) % (cinp / 8),
+              q = idx / (8 * 3 * coutp * (cinp / 8));
+    const int n = row % coutp, p = 2 - row / coutp;
+    const int k = 8 * g + e;
     float v = 0.f;
     if (!transposed) {
         if (n < O && k < C) v = W[((n * C + k) * 3 + p) * 3 + q];
@@ -659,14 +741,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// The band tensor map of a row-chunked [B, 8 G, H, W] bf16 tensor: dims (8, W, G, H, B), box
-// (8, 130, G, TR + 2, 1), zero fill outside.
+// The row tensor map of a row-chunked [B, 8 G, H, W] bf16 tensor: dims (8, W, G, H, B), box
+// (8, 130, G, 1, 1) -- one staged input row --, zero fill outside.
 cudaError_t band_tensor_map(CUtensorMap* map, const bf16* base, int B, int H, int W, int G) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)G, (cuuint64_t)H, (cuuint64_t)B};
     const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)G * W * 16, (cuuint64_t)H * G * W * 16};
-    const cuuint32_t box[5] = {8, BANDW, (cuuint32_t)G, TR + 2, 1};
+    const cuuint32_t box[5] = {8, BANDW, (cuuint32_t)G, 1, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -674,14 +756,14 @@ cudaError_t band_tensor_map(CUtensorMap* map, const bf16* base, int B, int H, in
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int CIN, int COUT, int MODE>
-cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
-    using S = ConvShape<CIN, COUT>;
+template <int CIN, int COUT, int MODE, int R>
+cudaError_t launch_conv_r(const ConvArgs& a, cudaStream_t s) {
+    using S = ConvShape<CIN, COUT, R>;
     static int per_sm = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         // CTAs per SM: as many as the 228 KB of shared memory hold (1 KB reserved per CTA), never
@@ -690,14 +772,19 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
         per_sm = per_sm < (int)(512 / S::NCOLS) ? per_sm : (int)(512 / S::NCOLS);
         if (per_sm < 1) per_sm = 1;
     }
-    const long long tiles = (long long)a.B * ((a.H + TR - 1) / TR) * ((a.W + TW - 1) / TW);
+    const long long tiles = (long long)a.B * ((a.H + R - 1) / R) * ((a.W + TW - 1) / TW);
     const long long cap = (long long)num_sms() * per_sm;
     const int grid = (int)(tiles < cap ? tiles : cap);
     CUtensorMap map;
     cudaError_t e = band_tensor_map(&map, a.in, a.B, a.H, a.W, CIN / 8);
     if (e != cudaSuccess) return e;
-    k_conv3x3<CIN, COUT, MODE><<<grid, NT, S::SMEM, s>>>(a, map);
+    k_conv3x3<CIN, COUT, MODE, R><<<grid, NT, S::SMEM, s>>>(a, map);
     return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int MODE>
+cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
+    return a.rows == 8 ? launch_conv_r<CIN, COUT, MODE, 8>(a, s) : launch_conv_r<CIN, COUT, MODE, 4>(a, s);
 }
 
 }  // namespace
@@ -738,6 +825,7 @@ struct homg_net {
     float* y = nullptr;  // training output
     float* lres = nullptr;  // residual loss: [res, w_W, w_E, w_S, w_N] per pixel
     int loss_kind = HOMG_NET_LOSS_ERROR;
+    int tile_rows = 4;  // output rows per convolution tile (4 or 8)
     double* part = nullptr;
     double* dloss = nullptr;
     int* derr = nullptr;
@@ -813,6 +901,7 @@ ConvArgs conv_args(homg_net* n, const bf16* in, int l, bf16* out, float* outf, i
     a.H = H;
     a.W = W;
     a.err = n->derr;
+    a.rows = n->tile_rows;
     return a;
 }
 
@@ -1026,6 +1115,7 @@ int homg_net_train_step(homg_net_handle net, const void* xv, const float* t, int
     c.H = H;
     c.W = W;
     c.err = net->derr;
+    c.rows = net->tile_rows;
     c.in = net->g4;
     c.w = net->wt[3];
     c.out = net->gA;
@@ -1065,6 +1155,13 @@ int homg_net_set_loss(homg_net_handle net, int kind) {
     if (kind != HOMG_NET_LOSS_ERROR && kind != HOMG_NET_LOSS_RESIDUAL)
         return net_fail(net, HOMG_EINVAL, "homg_net_set_loss: kind must be HOMG_NET_LOSS_ERROR or HOMG_NET_LOSS_RESIDUAL");
     net->loss_kind = kind;
+    return HOMG_OK;
+}
+
+int homg_net_set_tile_rows(homg_net_handle net, int rows) {
+    if (!net) return HOMG_EINVAL;
+    if (rows != 4 && rows != 8) return net_fail(net, HOMG_EINVAL, "homg_net_set_tile_rows: rows must be 4 or 8");
+    net->tile_rows = rows;
     return HOMG_OK;
 }
 

@@ -64,6 +64,7 @@ EXPORTS = [
     "homg_solve_learned",
     "homg_net_set_loss",
     "homg_set_learned_judge",
+    "homg_net_set_tile_rows",
 ]
 
 HOMG_BATCH_MAX_GROUPS = 16
@@ -161,6 +162,7 @@ def load(path=LIB_PATH):
     lib.homg_features.argtypes = [vp, vp, vp, vp, vp, vp, dp]
     lib.homg_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ip, dp, ip]
     lib.homg_net_set_loss.argtypes = [vp, ctypes.c_int]
+    lib.homg_net_set_tile_rows.argtypes = [vp, ctypes.c_int]
     lib.homg_set_learned_judge.argtypes = [vp, ctypes.c_int]
     lib.homg_get_history.argtypes = [vp, dp, ctypes.c_int]
     lib.homg_get_stats.argtypes = [vp, ctypes.POINTER(homg_stats)]
@@ -620,6 +622,10 @@ class Net:
         """Training loss: "error" (mean squared error against the scaled error target) or "residual"
         (the residual the proposal leaves on each patch; the target is then not used)."""
         _net_check(load().homg_net_set_loss(self.handle, NET_LOSSES[kind] if isinstance(kind, str) else kind), self.handle)
+
+    def set_tile_rows(self, rows):
+        """Output rows per convolution tile (4 or 8); results do not depend on it."""
+        _net_check(load().homg_net_set_tile_rows(self.handle, int(rows)), self.handle)
 
     def train_step(self, x, t, lr):
         B, H, _, W, _ = x.shape

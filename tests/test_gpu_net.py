@@ -52,13 +52,15 @@ def to_device_images(homg, xs):
     return torch.from_numpy(arr).to(torch.bfloat16).cuda()
 
 
-def gpu_forward(homg, params, xs):
+def gpu_forward(homg, params, xs, rows=None):
     import torch
 
     x = to_device_images(homg, xs)
     B, H, _, W, _ = x.shape
     y = torch.empty(B, H, W, dtype=torch.float32, device="cuda")
     with homg.Net() as net:
+        if rows is not None:
+            net.set_tile_rows(rows)
         net.set_params(flat(params))
         net.forward(x, y)
     return y.cpu().numpy().astype(np.float64)
@@ -77,8 +79,10 @@ def integer_network(seed):
     return params
 
 
-def test_integer_network_is_exact(homg):
-    # B = 2 images of 37 x 150 pixels: two tiles across, a ragged last row band
+@pytest.mark.parametrize("rows", [4, 8])
+def test_integer_network_is_exact(homg, rows):
+    # B = 2 images of 37 x 150 pixels: two tiles across, a ragged last row band (for tiles of 4 and
+    # of 8 output rows)
     rng = np.random.default_rng(1)
     params = integer_network(2)
     xs = [rng.integers(-2, 3, size=(2, 37, 150)).astype(np.float64) for _ in range(2)]
@@ -87,8 +91,20 @@ def test_integer_network_is_exact(homg):
         for a in acts[1:]:
             assert np.all(a == np.round(a)) and np.abs(a).max() <= 256
     ref = np.stack([cnn.forward(params, x)[0] for x in xs])
-    got = gpu_forward(homg, params, xs)
+    got = gpu_forward(homg, params, xs, rows)
     np.testing.assert_array_equal(got, ref)
+
+
+def test_tile_rows_do_not_change_the_result(homg):
+    # every output row accumulates its products in the same order (vertical taps 0, 1, 2, then column
+    # taps, then channel groups) whatever the tile height: bit-identical outputs
+    rng = np.random.default_rng(40)
+    params = [(w, cnn.f32(rng.standard_normal(b.shape) * 0.1)) for w, b in cnn.init_weights(41)]
+    xs = [cnn.bf16(rng.standard_normal((2, 29, 300))) for _ in range(3)]
+    np.testing.assert_array_equal(gpu_forward(homg, params, xs, 4), gpu_forward(homg, params, xs, 8))
+    with homg.Net() as net:
+        with pytest.raises(homg.HomgError):
+            net.set_tile_rows(6)
 
 
 @pytest.mark.parametrize("H,W", [(20, 130), (9, 64), (5, 7)])
@@ -103,7 +119,8 @@ def test_random_network_matches_oracle(homg, H, W):
     assert np.mean(np.abs(got - ref) <= 2e-2 * np.abs(ref).max()) >= 0.99
 
 
-def test_train_step_gradients_match_oracle(homg):
+@pytest.mark.parametrize("rows", [4, 8])
+def test_train_step_gradients_match_oracle(homg, rows):
     import torch
 
     rng = np.random.default_rng(5)
@@ -117,6 +134,7 @@ def test_train_step_gradients_match_oracle(homg):
     t = torch.from_numpy(np.stack(ts).astype(np.float32)).cuda()
     lr = 1e-3
     with homg.Net() as net:
+        net.set_tile_rows(rows)
         net.set_params(flat(params))
         loss = net.train_step(x, t, lr)
         grads = unflat(net.get_grads())
