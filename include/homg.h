@@ -120,6 +120,15 @@ typedef struct homg_options {
      * (one hat stencil per node). HOMG cycles in the whole-grid form only (the default exec mode
      * selects it), levels <= K, not with strict_fp, the V-cycle, batches or coefficients. */
     int geometry;
+    /* Lattice form of binary32 / bfloat16 HOMG cycles in 2-D (not strict_fp, not with
+     * coefficients): every level run on a lattice of at most run_max_n intervals per side after
+     * the coarsest ones -- the level change from the coarser lattice and all of the level's
+     * sweeps (Sec. 2, MFMG: n_m iterations per level) -- is one launch of one block per problem
+     * that keeps the lattice and its source in shared memory between sweeps, instead of a launch
+     * per sweep or pair. 0 selects 128 (the largest, limited by shared memory), a negative value
+     * turns it off; at most 128. The iterates are bit-identical either way. Persistent batches
+     * never use it. */
+    int run_max_n;
 } homg_options;
 
 #define HOMG_GEOM_NESTED 0

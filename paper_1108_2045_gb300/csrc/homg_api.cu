@@ -60,8 +60,8 @@ struct SolveGraph {
 constexpr int kStagesPerGraph = 12;  // even: keeps the ping-pong parity of the solution buffers
 
 struct Op {  // one kernel launch of a cycle part
-    enum Kind { ITER, ITER2, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD, POW2_ITER, POW2_RESTRICT } kind;
-    int sweeps = 1;  // ITER2: plain sweeps fused into the launch (2 or 4)
+    enum Kind { ITER, ITER2, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD, POW2_ITER, POW2_RESTRICT, RUN } kind;
+    int sweeps = 1;  // ITER2: plain sweeps fused into the launch (2 or 4); RUN: sweeps of the level run
     IterArgs it;
     Pow2IterArgs p2;
     Pow2RestrictArgs p2r;
@@ -269,6 +269,7 @@ void apply_batch(homg_ctx* h) {
         for (Op& op : *part) {
             if (op.kind == Op::ITER || op.kind == Op::ITER2) fix_it(op.it);
             else if (op.kind == Op::PROLONG) fix_pr(op.pr);
+            else if (op.kind == Op::RUN) { fix_it(op.it); fix_pr(op.pr); }
             else if (op.kind == Op::RESTRICT) fix_rs(op.rs);
         }
     for (BlockOp& b : h->block_ops) {
@@ -569,10 +570,55 @@ void plan_cycle(homg_ctx* h) {
     }
 }
 
+// Lattice form, binary32 cycles (2-D): each level run after the coarsest ones -- a stride-1 level
+// change, then the level's sweeps, the first with the pending stride-2 interpolation -- on a lattice
+// of at most opt.run_max_n intervals per side becomes one RUN op (k_level_run2: one block per
+// problem, the lattice in shared memory). Level 0's sweeps (part B) stay separate launches.
+void group_level_runs(homg_ctx* h) {
+    if (h->opt.run_max_n <= 0 || h->strict || h->exec != HOMG_EXEC_LATTICE ||
+        h->opt.cycle == HOMG_CYCLE_V || h->vc || h->ndim != 2 || h->geometry != HOMG_GEOM_NESTED ||
+        h->prec == PREC_FP64)
+        return;
+    std::vector<Op> out;
+    const std::vector<Op>& A = h->partA;
+    for (size_t q = 0; q < A.size();) {
+        const Op& op = A[q];
+        const int n = (op.kind == Op::PROLONG) ? op.pr.G.n : 0;
+        size_t r = q + 1;
+        int sweeps = 0;
+        if (op.kind == Op::PROLONG && op.pr.s == 1 && n >= 2 && n <= h->opt.run_max_n) {
+            while (r < A.size() && (A[r].kind == Op::ITER || A[r].kind == Op::ITER2) && A[r].it.e_new.n == n) {
+                sweeps += A[r].kind == Op::ITER2 ? A[r].sweeps : 1;
+                ++r;
+            }
+        }
+        const bool fuse = sweeps >= 1 && A[q + 1].kind == Op::ITER && A[q + 1].it.mp == 1 &&
+                          A[q + 1].it.dprev.p == op.pr.dl.p;
+        if (!fuse) {
+            out.push_back(op);
+            ++q;
+            continue;
+        }
+        Op run{};
+        run.kind = Op::RUN;
+        run.sweeps = sweeps;
+        run.pr = op.pr;
+        run.it = A[r - 1].it;              // the last sweep's output: the run's final buffer and variation
+        run.it.e_old = A[q + 1].it.e_old;  // not read (the level change fills shared memory)
+        run.it.g = A[q + 1].it.g;
+        run.it.mp = 1;
+        run.it.dprev = A[q + 1].it.dprev;
+        out.push_back(run);
+        q = r;
+    }
+    h->partA = out;
+}
+
 // Fast lattice form: the restrictions to, and the leading runs on, the coarsest lattices (at most
 // 16 intervals per side in 2-D, 8 in 3-D: a few hundred nodes, less than one per thread of the
-// block) become one single-block launch. Larger lattices run faster as separate launches.
-void group_coarse_block(homg_ctx* h) {
+// block) become one single-block launch. Larger lattices run faster as separate launches (or, in
+// binary32 cycles, as one shared-memory launch per level run: group_level_runs).
+void group_block_ops(homg_ctx* h) {
     h->block_ops.clear();
     if (h->strict || h->exec != HOMG_EXEC_LATTICE || h->opt.cycle == HOMG_CYCLE_V || h->vc) return;
     const int nb = (h->ndim == 2) ? 16 : 8;
@@ -613,6 +659,11 @@ void group_coarse_block(homg_ctx* h) {
     h->block_ops = blk;
 }
 
+void group_coarse_block(homg_ctx* h) {
+    group_block_ops(h);
+    group_level_runs(h);
+}
+
 cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s) {
     for (const Op& op : ops) {
         cudaError_t e = cudaSuccess;
@@ -630,6 +681,7 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
             case Op::BLOCK:
                 e = launch_coarse_block(h->ndim, h->prec, h->dblock_ops + op.block_first, op.block_count, h->nbatch, s);
                 break;
+            case Op::RUN: e = launch_level_run(h->prec, op.pr, op.it, op.sweeps, h->nbatch, s); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -893,6 +945,7 @@ int grid_exponent(int ndim, int64_t side, const char* who) {
 int check_options(int ndim, homg_options& o) {
     if (o.omega_j == 0.0) o.omega_j = (ndim == 2) ? 4.0 / 5.0 : 6.0 / 7.0;
     if (o.max_i == 0) o.max_i = 32;
+    if (o.run_max_n == 0) o.run_max_n = RUN_MAX_N;
     if (o.diverge_factor == 0.0) o.diverge_factor = 1e3;
     if (o.v_pre == 0) o.v_pre = 2;
     if (o.v_post == 0) o.v_post = 2;
@@ -903,7 +956,7 @@ int check_options(int ndim, homg_options& o) {
         (o.precision != HOMG_PREC_FP64 && o.precision != HOMG_PREC_FP32 && o.precision != HOMG_PREC_BF16) ||
         (o.cycle != HOMG_CYCLE_HOMG && o.cycle != HOMG_CYCLE_V) || o.v_pre < 0 || o.v_post < 0 || o.v_pre > 64 ||
         o.v_post > 64 || (o.cycle == HOMG_CYCLE_V && (o.n_schedule > 0 || o.exec_mode == HOMG_EXEC_WHOLEGRID)) ||
-        (o.geometry != HOMG_GEOM_NESTED && o.geometry != HOMG_GEOM_POW2))
+        (o.geometry != HOMG_GEOM_NESTED && o.geometry != HOMG_GEOM_POW2) || o.run_max_n > RUN_MAX_N)
         return fail(nullptr, HOMG_EINVAL, "homg_create: invalid options%s%s");
     if (o.geometry == HOMG_GEOM_POW2 &&
         (ndim != 2 || o.cycle != HOMG_CYCLE_HOMG || o.strict_fp || o.exec_mode == HOMG_EXEC_LATTICE))
@@ -985,6 +1038,12 @@ int create_ctx(int ndim, int64_t n, int K, int levels, int stencil, const homg_o
     plan_cycle(h);
     group_coarse_block(h);
     apply_batch(h);
+    ce = prepare_level_run(h->prec);
+    if (ce != cudaSuccess) {
+        int rc = cuda_fail(nullptr, ce, "setting the level-run kernel's shared memory");
+        homg_destroy(h);
+        return rc;
+    }
     if (!h->block_ops.empty()) {
         ce = cudaMemcpy(h->dblock_ops, h->block_ops.data(), h->block_ops.size() * sizeof(BlockOp), cudaMemcpyHostToDevice);
         if (ce != cudaSuccess) {
@@ -1353,6 +1412,7 @@ int homg_batch_create(int nprob, const int64_t* sides, const homg_options* opt, 
                     "homg_batch_create: batches use fast arithmetic, the lattice form, MFMG and graph or persistent launches%s%s");
     const bool persistent = o.launch_mode == HOMG_LAUNCH_PERSISTENT;
     o.launch_mode = HOMG_LAUNCH_GRAPH;  // the groups themselves are planned as for graph launches
+    if (persistent) o.run_max_n = -1;   // its kernel runs every op as work items: no level runs
     std::vector<int64_t> distinct;
     std::vector<int> group_of(nprob), index_in_group(nprob);
     std::vector<int> counts;

@@ -303,6 +303,12 @@ cudaError_t launch_residual(int ndim, int prec, bool strict, const ResidArgs& a,
 int residual_blocks(int ndim, bool strict, int n);  // partial sums written by launch_residual
 cudaError_t launch_restrict(int ndim, int prec, bool strict, const RestrictArgs& a, cudaStream_t s);
 cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, int nb, cudaStream_t s);
+// Lattice form, binary32 cycles (2-D): a level change and the whole run of `sweeps` sweeps on a
+// lattice of at most RUN_MAX_N intervals per side, in one block per problem (shared memory).
+constexpr int RUN_MAX_N = 128;
+cudaError_t launch_level_run(int prec, const ProlongArgs& pr, const IterArgs& it, int sweeps, int nb, cudaStream_t s);
+// Raises the level-run kernel's shared-memory limit on the current device (before any capture).
+cudaError_t prepare_level_run(int prec);
 cudaError_t launch_vresid(int ndim, int prec, bool strict, const VResidArgs& a, cudaStream_t s);
 cudaError_t launch_prolong_add(int ndim, int prec, bool strict, const ProlongAddArgs& a, cudaStream_t s);
 cudaError_t launch_pow2_iterate(int prec, const Pow2IterArgs& a, cudaStream_t s);

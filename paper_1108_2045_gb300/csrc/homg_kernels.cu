@@ -1251,6 +1251,119 @@ __global__ void __launch_bounds__(JX) k_prolong2_s1(ProlongArgs a, int rows) {
     prolong2_s1_body<T, BATCH, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// Lattice form, binary32 cycles (2-D): one level's whole run on a small lattice (at most
+// RUN_MAX_N intervals per side) in one block of n x RUN_Y threads, the level's iterate, source
+// and pending variation held in shared memory between sweeps instead of one launch per sweep (or
+// pair). Steps, in the arithmetic of the separate kernels: the level change from the coarser
+// lattice's final iterate Gc and variation dl (k_prolong2_s1), then `sweeps` damped-Jacobi sweeps
+// (k_jacobi2), the first adding the pending stride-2 interpolation of dl off the lattice, every
+// sweep's values rounded to the storage type as a stored sweep is; the last sweep also writes the
+// iterate (e_new) and, when requested, its variation (dnew). The results are bit-identical to the
+// separate launches. Batches: one block per problem (blockIdx.z).
+constexpr int RUN_Y = 8;  // thread rows of a level-run block (its columns: one per lattice column)
+
+// One sweep of a level run: each thread marches down its column through its band of rows.
+template <typename T, bool FIRST, bool LAST>
+__device__ __forceinline__ void run_sweep(const T* __restrict__ src, T* __restrict__ dst, const T* __restrict__ SG,
+                                          const T* __restrict__ SD, int n, int j0, int j1, typename St<T>::C c1,
+                                          typename St<T>::C om, const IterArgs& it) {
+    using C = typename St<T>::C;
+    const int np = n + 1, nc = (n >> 1) + 1;  // row lengths of the lattice and of the coarse variation
+    const int i = 1 + threadIdx.x;
+    if (i >= n || j0 >= j1) return;
+    const C hx = (i & 1) ? (C)0.5 : (C)0;
+    auto X = [&](int JJ) -> C {  // x-interpolant of compact row JJ of dl at this column
+        const C a = as_c<T>(SD[JJ * nc + (i >> 1)]), b = as_c<T>(SD[JJ * nc + (i >> 1) + 1]);
+        return fma(hx, b - a, a);
+    };
+    C vs = as_c<T>(src[(j0 - 1) * np + i]), vc = as_c<T>(src[j0 * np + i]);
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const C vn = as_c<T>(src[(j + 1) * np + i]);
+        const C w = as_c<T>(src[j * np + i - 1]), e = as_c<T>(src[j * np + i + 1]);
+        C v = jacobi_update(c1, om, vc, as_c<T>(SG[j * np + i]), w, e, vs, vn);
+        if (LAST && it.dnew.p) wp<T>(it.dnew)[(int64_t)j * it.dnew.pitch + i] = St<T>::put(v - vc);
+        if (FIRST) {
+            const C sv = (j & 1) ? (C)0.5 * (X(j >> 1) + X((j >> 1) + 1)) : X(j >> 1);
+            v += ((i | j) & 1) ? sv : (C)0;
+        }
+        const T out = St<T>::put(v);
+        dst[j * np + i] = out;
+        if (LAST) wp<T>(it.e_new)[(int64_t)j * it.e_new.pitch + i] = out;
+        vs = vc;
+        vc = vn;
+    }
+}
+
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(RUN_MAX_N * RUN_Y) k_level_run2(ProlongArgs pr, IterArgs it, int sweeps) {
+    pdl_begin();
+    if (BATCH) {
+        if (!batch_view<T>(pr, blockIdx.z)) return;  // this problem has converged (uniform over the block)
+        batch_view<T>(it, blockIdx.z);
+    }
+    using C = typename St<T>::C;
+    const int n = it.e_new.n, np = n + 1, nc = (n >> 1) + 1;
+    extern __shared__ __align__(16) unsigned char run_smem[];
+    T* S0 = reinterpret_cast<T*>(run_smem);  // iterate, ping
+    T* S1 = S0 + np * np;                     // iterate, pong (holds Gc until the first sweep)
+    T* SG = S1 + np * np;                     // source
+    T* SD = SG + np * np;                     // the coarser lattice's variation dl (compact)
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * RUN_Y;
+    // stage the source, Gc (into S1) and dl; zero the boundary of S0
+    for (int q = tid; q < np * np; q += nt) {
+        const int i = q % np, j = q / np;
+        SG[q] = cp<T>(it.g)[(int64_t)j * it.g.pitch + i];
+        if (i == 0 || j == 0 || i == n || j == n) S0[q] = St<T>::put((C)0);
+    }
+    for (int q = tid; q < nc * nc; q += nt) {
+        const int I = q % nc, J = q / nc;
+        S1[q] = cp<T>(pr.Gc)[(int64_t)J * pr.Gc.pitch + I];
+        SD[q] = cp<T>(pr.dl)[(int64_t)J * pr.dl.pitch + I];
+    }
+    __syncthreads();
+    // level change: lattice nodes copy Gc, the others take the stride-2 interpolant of Gc - dl
+    for (int j = 1 + threadIdx.y; j < n; j += RUN_Y)
+        for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const int I = i >> 1, J = j >> 1;
+            const C hx = (i & 1) ? (C)0.5 : (C)0;
+            auto X = [&](int JJ) -> C {
+                C a = as_c<T>(S1[JJ * nc + I]), b = as_c<T>(S1[JJ * nc + I + 1]);
+                a -= as_c<T>(SD[JJ * nc + I]);
+                b -= as_c<T>(SD[JJ * nc + I + 1]);
+                return fma(hx, b - a, a);
+            };
+            C v = (j & 1) ? (C)0.5 * (X(J) + X(J + 1)) : X(J);
+            if (!(j & 1) && !(i & 1)) v = as_c<T>(S1[J * nc + I]);
+            S0[j * np + i] = St<T>::put(v);
+        }
+    __syncthreads();
+    // the boundary of S1 (the first sweep writes its interior)
+    for (int q = tid; q < np * np; q += nt) {
+        const int i = q % np, j = q / np;
+        if (i == 0 || j == 0 || i == n || j == n) S1[q] = St<T>::put((C)0);
+    }
+    const C om = pick<C>(it.omega, it.omega_f), c1 = pick<C>(it.c1, it.c1_f);
+    const int band = (n - 1 + RUN_Y - 1) / RUN_Y;
+    const int j0 = 1 + threadIdx.y * band, j1 = min(j0 + band, n);
+    if (sweeps == 1) {
+        run_sweep<T, true, true>(S0, S1, SG, SD, n, j0, j1, c1, om, it);
+        return;
+    }
+    run_sweep<T, true, false>(S0, S1, SG, SD, n, j0, j1, c1, om, it);
+    __syncthreads();
+    T* src = S1;
+    T* dst = S0;
+    for (int s = 1; s + 1 < sweeps; ++s) {
+        run_sweep<T, false, false>(src, dst, SG, SD, n, j0, j1, c1, om, it);
+        __syncthreads();
+        T* t = src;
+        src = dst;
+        dst = t;
+    }
+    run_sweep<T, false, true>(src, dst, SG, SD, n, j0, j1, c1, om, it);
+}
+
 // Fast V-cycle kernels (2-D, column marching): level residual rho = g + omega (sum - 4 v) in 5
 // instructions per node, and the stride-2 prolongation-add e += P ec with the x-interpolant shared
 // down each column (lattice nodes take the coarse value itself, which ColumnInterp2 returns there).
@@ -2368,6 +2481,56 @@ cudaError_t launch_vc_setup(const double* k, int n, int m, bool dbl, void* kx, v
     if (dbl) k_vc_setup<double><<<g, b, 0, s>>>(k, n, m, (double*)kx, (double*)ky, (double*)wd, pitch, omega_j, bad);
     else k_vc_setup<float><<<g, b, 0, s>>>(k, n, m, (float*)kx, (float*)ky, (float*)wd, pitch, omega_j, bad);
     return cudaGetLastError();
+}
+
+// Shared memory of the largest level run (set once per device context, outside stream capture).
+// Shared memory of a level run on n intervals: iterate (two buffers) and source on the lattice,
+// the coarser variation on the coarse lattice.
+template <typename T> constexpr size_t run_smem_bytes(int n) {
+    return (3 * (size_t)(n + 1) * (size_t)(n + 1) + (size_t)(n / 2 + 1) * (size_t)(n / 2 + 1)) * sizeof(T);
+}
+static_assert(run_smem_bytes<float>(RUN_MAX_N) <= 232448, "a level run must fit one block's shared memory");
+
+template <typename T> cudaError_t level_run_setup() {
+    const int mx = (int)run_smem_bytes<T>(RUN_MAX_N);
+    cudaError_t e = cudaFuncSetAttribute(k_level_run2<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_level_run2<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+
+cudaError_t prepare_level_run(int prec) {
+    switch (prec) {
+        case PREC_FP32: return level_run_setup<float>();
+        case PREC_BF16: return level_run_setup<__nv_bfloat16>();
+        default: return cudaSuccess;
+    }
+}
+
+template <typename T>
+cudaError_t level_run_t(const ProlongArgs& pr, const IterArgs& it, int sweeps, int nb, cudaStream_t s) {
+    const int n = it.e_new.n;
+    if (n > RUN_MAX_N || n < 2 || sweeps < 1) return cudaErrorInvalidValue;
+    const size_t smem = run_smem_bytes<T>(n);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, 1, (unsigned)nb);
+    cfg.blockDim = dim3((unsigned)n, RUN_Y);  // thread (x, y): column x + 1, band y of rows
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return it.bst ? cudaLaunchKernelEx(&cfg, k_level_run2<T, true>, pr, it, sweeps)
+                  : cudaLaunchKernelEx(&cfg, k_level_run2<T, false>, pr, it, sweeps);
+}
+
+cudaError_t launch_level_run(int prec, const ProlongArgs& pr, const IterArgs& it, int sweeps, int nb, cudaStream_t s) {
+    switch (prec) {
+        case PREC_FP32: return level_run_t<float>(pr, it, sweeps, nb, s);
+        case PREC_BF16: return level_run_t<__nv_bfloat16>(pr, it, sweeps, nb, s);
+        default: return cudaErrorInvalidValue;  // FP64 sweeps are FP64-bound: one SM is too slow for them
+    }
 }
 
 cudaError_t launch_coarse_block(int ndim, int prec, const BlockOp* ops, int nops, int nb, cudaStream_t s) {
