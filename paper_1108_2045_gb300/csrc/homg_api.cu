@@ -700,6 +700,7 @@ ResidArgs resid_args(homg_ctx* h, int stage) {
         a.ky = h->ky0;
         a.kpitch = h->pitch0;
     }
+    a.scale_f = (float)a.scale;
     a.part_r = h->part_r;
     a.part_f = nullptr;
     a.g0 = grid(h->L[0].g, h->L[0].pitch, h->n);

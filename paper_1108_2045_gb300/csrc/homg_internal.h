@@ -117,6 +117,7 @@ struct ResidArgs {
     DGrid u_out;    // p == nullptr: not written
     Grid g0;        // p == nullptr: not written
     double scale;   // h^2 (strict) or omega h^2
+    float scale_f;  // the same, rounded to binary32 (binary32 and bfloat16 sources of the fast forms)
     double inv_h2;
     double* part_r;
     double* part_f; // nullptr: not accumulated

@@ -121,6 +121,19 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_d_store<__nv_bfloat16>
     return __float2bfloat16_rn(narrow_rn(x));
 }
 
+// The cycle's source scale * r stored from the FP64 residual r (fast forms). FP64 cycles form the
+// product in binary64; binary32 and bfloat16 cycles narrow r first and multiply in binary32 (one
+// rounding more than the binary64 product, within the cycle's own precision), which keeps the
+// multiply off the FP64 pipe that bounds the residual kernels.
+template <typename T> __device__ __forceinline__ T source_store(double r, double scale, float scale_f);
+template <> __device__ __forceinline__ double source_store<double>(double r, double scale, float) { return scale * r; }
+template <> __device__ __forceinline__ float source_store<float>(double r, double, float scale_f) {
+    return narrow_rn(r) * scale_f;
+}
+template <> __device__ __forceinline__ __nv_bfloat16 source_store<__nv_bfloat16>(double r, double, float scale_f) {
+    return __float2bfloat16_rn(narrow_rn(r) * scale_f);
+}
+
 // ---- arithmetic in the canonical order (S) or freely contracted ------------------------------
 template <bool S> __device__ __forceinline__ double add(double a, double b) { return S ? __dadd_rn(a, b) : a + b; }
 template <bool S> __device__ __forceinline__ double sub(double a, double b) { return S ? __dsub_rn(a, b) : a - b; }
@@ -1599,7 +1612,7 @@ __global__ void __launch_bounds__(J3X * J3Y) k_residual3_fast(ResidArgs a, int n
             const double sum = ((uval(i - 1, j, k) + uval(i + 1, j, k)) + (uval(i, j - 1, k) + uval(i, j + 1, k))) + (vb + vt);
             const double fv = __ldg(F + (int64_t)k * plf + (int64_t)j * pf + i);
             const double r = fma(a.inv_h2, fma(-6.0, vc, sum), fv);
-            if (a.g0.p) wp<T>(a.g0)[at(a.g0.pitch, n, i, j, k)] = from_d_store<T>(a.scale * r);
+            if (a.g0.p) wp<T>(a.g0)[at(a.g0.pitch, n, i, j, k)] = source_store<T>(r, a.scale, a.scale_f);
             rr = fma(r, r, rr);
             if (a.part_f) ff = fma(fv, fv, ff);
             vb = vc;
@@ -1735,9 +1748,10 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
 // u_new = u_in + e once per node of its column, the 30 inner lanes own their nodes and take the west
 // and east neighbours' updated values by shuffle, the two edge lanes only supply theirs. Every
 // instruction is issued once per warp and row for 30 nodes, none for an edge lane alone: 8 FP64
-// instructions per node (9 with the norm of f on the initial residual). Widening e and rounding the
-// source to the cycle's storage use the integer conversions above. Results are bit-identical to
-// forming every neighbour locally.
+// instructions per node in FP64 cycles, 7 in binary32 and bfloat16 cycles (the source's multiply in
+// binary32, source_store), one more for the norm of f on the initial residual. Widening e and
+// rounding the source to the cycle's storage use the integer conversions above. Results are
+// bit-identical to forming every neighbour locally.
 constexpr int RS_OUT = 30;  // nodes per warp strip
 template <typename T, bool VC, bool BATCH, bool P>
 __device__ __forceinline__ void residual2_fast_body(ResidArgs a, int n, int bx, int by, int bz, int gx) {
@@ -1791,7 +1805,7 @@ __device__ __forceinline__ void residual2_fast_body(ResidArgs a, int n, int bx, 
                 r = fma(a.inv_h2, fma(-4.0, vc, sum), fv);
             }
             if (a.u_out.p) a.u_out.p[(int64_t)j * a.u_out.pitch + i] = vc;
-            if (a.g0.p) wp<T>(a.g0)[(int64_t)j * a.g0.pitch + i] = from_d_store<T>(a.scale * r);
+            if (a.g0.p) wp<T>(a.g0)[(int64_t)j * a.g0.pitch + i] = source_store<T>(r, a.scale, a.scale_f);
             rr = fma(r, r, rr);
             if (want_f) ff = fma(fv, fv, ff);
         }
