@@ -702,12 +702,19 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL,
-                       "step": "one oracle MFMG cycle", "cycles_to_tol": converged_after},
+            "config": workload_config("fp64", args.gpus),
+            "run": {"step": "one oracle MFMG cycle", "cycles_to_tol": converged_after},
             "impl": "reference", "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def workload_config(precision, n_gpus):
+    """The benchmarked workload, identical in both arms (the run's own results go under "run")."""
+    return {"workload": WORKLOAD, "precision": precision, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I,
+            "tol": TOL, "l2": "working set ~0.8 GB > 126 MB L2; no flush",
+            "parallelism": "replicas" if n_gpus > 1 else "single GPU"}
 
 
 def legs_digest(line):
@@ -716,7 +723,7 @@ def legs_digest(line):
     def r3(x):
         return None if x is None else float("%.4g" % x)
 
-    d = {"fp64_ms": r3(line["ms_per_step"]), "fp64_cyc": line["config"]["cycles"],
+    d = {"fp64_ms": r3(line["ms_per_step"]), "fp64_cyc": line["run"]["cycles"],
          "roof_hbm": r3(line["roofline"]["frac"])}
     alu = line["roofline"].get("alu", {})
     if "frac" in alu:
@@ -976,12 +983,10 @@ def run(args):
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32 cycles, f64 residual/update", "bf16": "bf16 cycles, f64 residual/update"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "grid": N_SIDE + 1, "levels": LEVELS, "max_i": MAX_I, "tol": TOL,
-                   "exec": args.exec, "exec_used": {1: "wholegrid", 2: "lattice"}[stats[0]["exec_mode"]],
-                   "cycles": stats[-1]["cycles"], "final_relres": relres,
-                   "iterations_per_cycle": stats[0]["iterations_per_cycle"],
-                   "l2": "working set ~0.8 GB > 126 MB L2; no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "launch": args.launch},
+        "config": workload_config(args.precision, world),
+        "run": {"exec": args.exec, "exec_used": {1: "wholegrid", 2: "lattice"}[stats[0]["exec_mode"]],
+                "cycles": stats[-1]["cycles"], "final_relres": relres,
+                "iterations_per_cycle": stats[0]["iterations_per_cycle"], "launch": args.launch},
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * grid_bytes, "d2h_bytes_per_step": grid_bytes},

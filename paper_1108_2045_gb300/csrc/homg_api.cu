@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/homg.h"
 #include "../../include/homg_net.h"
 #include "homg_internal.h"
@@ -58,6 +60,16 @@ struct SolveGraph {
 // (their conditional nodes evaluate false), so the graph stays short and a solve that needs more
 // cycles relaunches the continuation graph (one host synchronisation per kStagesPerGraph cycles).
 constexpr int kStagesPerGraph = 12;  // even: keeps the ping-pong parity of the solution buffers
+
+// NVTX range over a host scope (a solve, a graph launch, a cycle in stream mode): profilers that
+// record NVTX (ncu --nvtx) can select a solve's kernels by it; without a tool attached it costs a
+// function call.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct Op {  // one kernel launch of a cycle part
     enum Kind { ITER, ITER2, PROLONG, RESTRICT, BLOCK, VRESID, PROLONG_ADD, POW2_ITER, POW2_RESTRICT, RUN } kind;
@@ -1506,6 +1518,7 @@ int homg_batch_solve(homg_batch_handle b, const double* const* f, double* const*
     for (int p = 0; p < b->nprob; ++p)
         if (!f[p] || !u[p]) return fail(nullptr, HOMG_EINVAL, "homg_batch_solve: null problem array%s%s");
     const int G = (int)b->groups.size();
+    NvtxRange batch_range("homg_batch_solve");
     auto cfail = [&](cudaError_t e, const char* where) { return cuda_fail(nullptr, e, where); };
     cudaError_t e = cudaEventRecord(b->t0, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
@@ -1680,6 +1693,7 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     if (max_cycles < 0 || max_cycles > HOMG_MAX_CYCLES)
         return fail(h, HOMG_EINVAL, "homg_solve: max_cycles must be in [0, HOMG_MAX_CYCLES]%s%s");
     CK(h, cudaSetDevice(h->device), "cudaSetDevice");
+    NvtxRange solve_range("homg_solve");
     State* s = h->hstate;
     memset(s, 0, sizeof(*s));
     s->f = f;
@@ -1699,6 +1713,7 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
         }
         s->stages = h->gfirst.stages;
         s->stage_base = 0;
+        NvtxRange graph_range("homg_solve: graph launches");
         CK(h, cudaMemcpyAsync(h->dstate, s, sizeof(State), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(state)");
         CK(h, cudaGraphLaunch(h->gfirst.exec, h->stream), "cudaGraphLaunch");
         CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(state)");
@@ -1711,6 +1726,7 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
                 if (rc != HOMG_OK) return rc;
             }
             const int base = s->cycle;
+            NvtxRange cont_range("homg_solve: continuation cycles (graph)");
             State* d = h->dstate;
             s->stage_base = base;
             s->stages = h->gcont.stages;
@@ -1738,6 +1754,7 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
         CK(h, cudaMemcpyAsync(s, h->dstate, sizeof(State), cudaMemcpyDeviceToHost, sm), "cudaMemcpyAsync(state)");
         CK(h, cudaStreamSynchronize(sm), "cudaStreamSynchronize");
         for (int k = 1; !s->done && k <= max_cycles; ++k) {
+            NvtxRange cycle_range("homg cycle");
             CK(h, enqueue_ops(h, h->partA, sm), "cycle kernels");
             CK(h, cudaEventRecord(h->sev[3 * k - 1], sm), "cudaEventRecord");
             CK(h, enqueue_ops(h, h->partB, sm), "cycle kernels");
@@ -1959,6 +1976,7 @@ int homg_solve_learned(homg_handle h, homg_net_handle net, const double* f, doub
     memset(&h->stats, 0, sizeof(h->stats));
     if (!net || !f || !u) return fail(h, HOMG_EINVAL, "homg_solve_learned: null argument%s%s");
     if (!h->vc) return fail(h, HOMG_EINVAL, "homg_solve_learned: the handle has no coefficient (homg_set_coefficient)%s%s");
+    NvtxRange learned_range("homg_solve_learned");
     if (!(tol >= 0.0) || !std::isfinite(tol) || max_cycles < 0 || max_cycles > HOMG_MAX_CYCLES)
         return fail(h, HOMG_EINVAL, "homg_solve_learned: invalid tol or max_cycles%s%s");
     CK(h, cudaSetDevice(h->device), "cudaSetDevice");
