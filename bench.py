@@ -723,7 +723,8 @@ def legs_digest(line):
     def r3(x):
         return None if x is None else float("%.4g" % x)
 
-    d = {"fp64_ms": r3(line["ms_per_step"]), "fp64_cyc": line["run"]["cycles"],
+    prec = line["config"]["precision"]  # the headline leg's cycle precision (fp64 by default)
+    d = {prec + "_ms": r3(line["ms_per_step"]), prec + "_cyc": line["run"]["cycles"],
          "roof_hbm": r3(line["roofline"]["frac"])}
     alu = line["roofline"].get("alu", {})
     if "frac" in alu:
