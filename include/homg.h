@@ -129,7 +129,16 @@ typedef struct homg_options {
      * turns it off; at most 128. The iterates are bit-identical either way. Persistent batches
      * never use it. */
     int run_max_n;
+    /* Lattice form of binary32 / bfloat16 HOMG cycles in 2-D (not strict_fp, one problem per
+     * handle or batch group): pairs of plain sweeps on lattices of at least tma_min_n intervals per
+     * side run as one launch whose blocks stage their tile of the iterate and the source (with a
+     * two-node halo) in shared memory by TMA tensor copies, then run both sweeps from there.
+     * 0 selects the default threshold (HOMG_TMA_MIN_N_DEFAULT), a negative value turns it off;
+     * values below 256 are raised to 256. The iterates are bit-identical either way. */
+    int tma_min_n;
 } homg_options;
+
+#define HOMG_TMA_MIN_N_DEFAULT 256
 
 #define HOMG_GEOM_NESTED 0
 #define HOMG_GEOM_POW2 1

@@ -82,6 +82,8 @@ struct Op {  // one kernel launch of a cycle part
     VResidArgs vr;
     ProlongAddArgs pa;
     int block_first = 0, block_count = 0;  // BLOCK: range of the device op list
+    bool tma = false;                       // ITER2: the TMA-staged two-sweep kernel, with these maps
+    TmaSweepMaps maps;
 };
 
 // Capacity of the coarse-lattice block's op list in the level buffer.
@@ -544,6 +546,10 @@ void plan_cycle(homg_ctx* h) {
                     set_weights(h, a);
                     a.mp = -1;
                     a.dnew = grid(nullptr, 0, 0);
+                    // large single-problem lattices: the two sweeps with the tile staged by TMA
+                    if (k == 2 && h->nbatch == 1 && h->opt.tma_min_n > 0 && lv.n >= h->opt.tma_min_n &&
+                        tma_sweep_maps(h->prec, a, &op.maps) == cudaSuccess)
+                        op.tma = true;
                     (m == 0 ? h->partB : h->partA).push_back(op);
                     cur ^= 1;
                     q += k - 1;
@@ -682,7 +688,9 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
         switch (op.kind) {
             case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
             case Op::ITER2:
-                e = (h->ndim == 3) ? launch_iterate3_2(h->prec, op.it, s) : launch_iterate2(h->prec, op.sweeps, op.it, s);
+                e = (h->ndim == 3) ? launch_iterate3_2(h->prec, op.it, s)
+                    : op.tma       ? launch_iterate2_tma(h->prec, op.it, op.maps, &h->dstate->fault, s)
+                                   : launch_iterate2(h->prec, op.sweeps, op.it, s);
                 break;
             case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;
@@ -959,6 +967,8 @@ int check_options(int ndim, homg_options& o) {
     if (o.omega_j == 0.0) o.omega_j = (ndim == 2) ? 4.0 / 5.0 : 6.0 / 7.0;
     if (o.max_i == 0) o.max_i = 32;
     if (o.run_max_n == 0) o.run_max_n = RUN_MAX_N;
+    if (o.tma_min_n == 0) o.tma_min_n = HOMG_TMA_MIN_N_DEFAULT;
+    if (o.tma_min_n > 0 && o.tma_min_n < XT_MIN_N) o.tma_min_n = XT_MIN_N;
     if (o.diverge_factor == 0.0) o.diverge_factor = 1e3;
     if (o.v_pre == 0) o.v_pre = 2;
     if (o.v_post == 0) o.v_post = 2;
@@ -1169,7 +1179,7 @@ int autotune_rows(homg_ctx* h, cudaStream_t st, int* best_rows, double* best_us,
     for (auto* part : {&h->partA, &h->partB})
         for (const Op& op : *part) {
             const bool single = op.kind == Op::ITER && op.it.e_old.p;
-            if ((!single && op.kind != Op::ITER2) || op.it.m != 0) continue;
+            if ((!single && op.kind != Op::ITER2) || op.it.m != 0 || op.tma) continue;
             const double nodes = (double)h->nbatch * (double)(op.it.e_new.n - 1) * (double)(op.it.e_new.n - 1);
             if (nodes < min_nodes) continue;
             bool seen = false;
@@ -1426,6 +1436,7 @@ int homg_batch_create(int nprob, const int64_t* sides, const homg_options* opt, 
     const bool persistent = o.launch_mode == HOMG_LAUNCH_PERSISTENT;
     o.launch_mode = HOMG_LAUNCH_GRAPH;  // the groups themselves are planned as for graph launches
     if (persistent) o.run_max_n = -1;   // its kernel runs every op as work items: no level runs
+    o.tma_min_n = -1;                   // batch groups keep the per-problem views of the marching kernels
     std::vector<int64_t> distinct;
     std::vector<int> group_of(nprob), index_in_group(nprob);
     std::vector<int> counts;
@@ -1774,6 +1785,8 @@ int homg_solve(homg_handle h, const double* f, double* u, double tol, int max_cy
     CK(h, cudaMemcpyAsync(h->hhist, h->dhist, (max_cycles + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
        "cudaMemcpyAsync(hist)");
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (s->fault)
+        return fail(h, HOMG_ECUDA, "homg_solve: a two-sweep launch's TMA copy did not complete within its bound%s%s");
     const int cycles = s->cycle;
     if (cycles_out) *cycles_out = cycles;
     if (relres_out) *relres_out = s->relres;

@@ -1,6 +1,7 @@
 // Private declarations shared by the HOMG kernels and the host-side C ABI implementation.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime's entry-point query)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,6 +32,7 @@ struct State {
     double fnorm;
     double rr0;
     double relres;
+    int fault;         // set by a kernel whose bounded wait gave up (a TMA copy that never arrived)
 };
 
 // A grid array of the cycle's storage type: `n` intervals per side, rows of `pitch` elements,
@@ -297,6 +299,16 @@ cudaError_t launch_check_conversions(const double* d_in, float* f_out, const flo
 // `sweeps` (2 or 4) plain lattice-form sweeps in one launch (2-D, FP32 / bfloat16 storage, no
 // pending interpolation, no variation output): e_new = sweep(...sweep(e_old)).
 cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_t s);
+// Two fused plain sweeps with the tile staged by TMA (binary32 / bfloat16, 2-D, one problem):
+// me = tensor map of e_old, mg = of g (tma_sweep_maps); fault = where a copy that never arrives is
+// reported (State::fault).
+struct TmaSweepMaps {
+    CUtensorMap me;
+    CUtensorMap mg;
+};
+constexpr int XT_MIN_N = 256;  // smallest lattice the TMA two-sweep kernel is planned for
+cudaError_t tma_sweep_maps(int prec, const IterArgs& a, TmaSweepMaps* maps);
+cudaError_t launch_iterate2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s);
 // Two plain 3-D lattice-form sweeps in one launch (FP32 / bfloat16 storage).
 cudaError_t launch_iterate3_2(int prec, const IterArgs& a, cudaStream_t s);
 cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a, cudaStream_t s);

@@ -9,6 +9,7 @@
 // round-to-nearest intrinsics (no FMA contraction), storing through the same rounding as the
 // oracle. The fast kernels reassociate to issue fewer floating-point instructions.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 
 #include <type_traits>
@@ -1065,6 +1066,17 @@ template <> __device__ __forceinline__ void st2<float>(float* p, float2 v) { *re
 template <> __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16* p, float2 v) {
     *reinterpret_cast<unsigned*>(p) = pack_bf16x2_rn(v);
 }
+// Pairs in shared memory (the staged tiles of k_jacobi2_x2t): an aligned pair load and store.
+template <typename T> __device__ __forceinline__ float2 ld2s(const T* p);
+template <> __device__ __forceinline__ float2 ld2s<float>(const float* p) { return *reinterpret_cast<const float2*>(p); }
+template <> __device__ __forceinline__ float2 ld2s<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return unpack_bf16x2(*reinterpret_cast<const unsigned*>(p));
+}
+template <typename T> __device__ __forceinline__ void st2s(T* p, float2 v);
+template <> __device__ __forceinline__ void st2s<float>(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+template <> __device__ __forceinline__ void st2s<__nv_bfloat16>(__nv_bfloat16* p, float2 v) {
+    *reinterpret_cast<unsigned*>(p) = pack_bf16x2_rn(v);
+}
 template <typename T> __device__ __forceinline__ float2 round2(float2 v) { return v; }
 template <> __device__ __forceinline__ float2 round2<__nv_bfloat16>(float2 v) { return unpack_bf16x2(pack_bf16x2_rn(v)); }
 
@@ -1231,6 +1243,150 @@ template <typename T, bool BATCH, int K>
 __global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
     pdl_begin();
     jacobi2_xk_body<T, BATCH, K, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Two plain damped-Jacobi sweeps of a large single-problem lattice with the tile staged by TMA
+// (binary32 and bfloat16 storage, 2-D lattice form). A block owns XT_OUT output columns c0 ..
+// c0 + XT_OUT - 1 (c0 = XT_OUT * blockIdx.x) and RT output rows r0 .. r0 + RT - 1. One thread
+// issues two TMA tensor copies: the input iterate's rows r0 - 2 .. r0 + RT + 1 and the source's
+// rows r0 - 1 .. r0 + RT, XT_W columns from c0 - 8 each (a multiple of 8: the copy's innermost
+// coordinate must sit on a 16-byte boundary; zero outside the lattice), into shared memory. Thread t
+// owns staged columns 2t and 2t + 1: it computes the first sweep on rows r0 - 1 .. r0 + RT into a
+// shared buffer (rounded to the storage type as a stored sweep is, 0 outside the interior), then,
+// after a block barrier, the second sweep on the output rows, stored to global memory. Both
+// sweeps run as packed binary32 pairs in the per-column kernel's operation order, so the result is
+// bit-identical to two single sweeps. The copy's completion barrier is waited on with a bound: on
+// expiry the block records State::fault, waits once more (bounded) so no copy lands after it
+// leaves, and returns without storing.
+constexpr int XT_W = 256;    // staged columns (the TMA box width)
+constexpr int XT_OUT = 240;  // output columns per block (staged columns 8 .. 247)
+constexpr long long kXtWaitNs = 1000000000ll;
+
+__device__ __forceinline__ bool xt_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool xt_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = device_clock_ns();
+    for (;;) {
+        if (xt_try_wait(bar, parity)) return true;
+        if (device_clock_ns() - t0 > kXtWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void xt_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"((uint32_t)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+
+// The two sweeps of k_jacobi2_x2t from its staged tiles (MASK: the tile touches the lattice's
+// boundary, so first-sweep values outside the interior are replaced by 0 and stores are masked).
+template <typename T, int RT, bool MASK>
+__device__ __forceinline__ void x2t_sweeps(const IterArgs& a, const T* SE, const T* SG, T* S1, int x, int r0) {
+    constexpr int GR = RT + 2;
+    const int t = threadIdx.x;
+    const int n = a.e_new.n;
+    const float2 om = make_float2(a.omega_f, a.omega_f), c1 = make_float2(a.c1_f, a.c1_f);
+    const bool m0 = !MASK || (x >= 1 && x <= n - 1), m1 = !MASK || (x + 1 >= 1 && x + 1 <= n - 1);  // interior columns
+    // first sweep, rows r0 - 1 .. r0 + RT (shared rows 0 .. GR - 1), staged columns 2 .. 253
+    if (t >= 1 && t < XT_W / 2 - 1) {
+        const T* col = SE + 2 * t;
+        float2 em = ld2s<T>(col), ec = ld2s<T>(col + XT_W);
+#pragma unroll 4
+        for (int p = 0; p < GR; ++p) {
+            const T* row = col + (p + 1) * XT_W;  // iterate row r0 - 1 + p
+            const float2 ep = ld2s<T>(row + XT_W);
+            const float left = as_c<T>(row[-1]), right = as_c<T>(row[2]);
+            const float2 g = ld2s<T>(SG + p * XT_W + 2 * t);
+            const float2 sum = add2(make_float2(left + ec.y, ec.x + right), add2(em, ep));  // (w + e) + (s + n)
+            float2 v = round2<T>(fma2(c1, ec, fma2(om, sum, g)));
+            if (MASK) {
+                const int r = r0 - 1 + p;
+                const bool rin = r >= 1 && r <= n - 1;
+                v.x = (rin && m0) ? v.x : 0.f;
+                v.y = (rin && m1) ? v.y : 0.f;
+            }
+            st2s<T>(S1 + p * XT_W + 2 * t, v);
+            em = ec;
+            ec = ep;
+        }
+    }
+    __syncthreads();
+    // second sweep, output rows r0 .. r0 + RT - 1 (shared rows 1 .. RT), staged columns 8 .. 247
+    if (t >= 4 && t < 4 + XT_OUT / 2) {
+        T* __restrict__ O = wp<T>(a.e_new);
+        const int64_t po = a.e_new.pitch;
+        const T* col = S1 + 2 * t;
+        float2 sp = ld2s<T>(col), sc = ld2s<T>(col + XT_W);
+        const int pe = MASK ? min(RT, n - r0) : RT;  // output rows inside the lattice
+#pragma unroll 4
+        for (int p = 1; p <= pe; ++p) {
+            const T* row = col + p * XT_W;
+            const float2 sn = ld2s<T>(row + XT_W);
+            const float left = as_c<T>(row[-1]), right = as_c<T>(row[2]);
+            const float2 g = ld2s<T>(SG + p * XT_W + 2 * t);
+            const float2 sum = add2(make_float2(left + sc.y, sc.x + right), add2(sp, sn));
+            const float2 o = fma2(c1, sc, fma2(om, sum, g));
+            T* dst = O + (int64_t)(r0 - 1 + p) * po + x;
+            if (m0 && m1) st2<T>(dst, o);
+            else {
+                if (m0) dst[0] = St<T>::put(o.x);
+                if (m1) dst[1] = St<T>::put(o.y);
+            }
+            sp = sc;
+            sc = sn;
+        }
+    }
+}
+
+template <typename T, int RT>
+__global__ void __launch_bounds__(XT_W / 2) k_jacobi2_x2t(IterArgs a, const __grid_constant__ CUtensorMap me,
+                                                          const __grid_constant__ CUtensorMap mg, int* fault) {
+    pdl_begin();
+    constexpr int ER = RT + 4, GR = RT + 2;  // staged rows of the iterate and of the source
+    extern __shared__ __align__(128) unsigned char xt_smem[];
+    T* SE = reinterpret_cast<T*>(xt_smem);  // [ER][XT_W]: iterate rows r0 - 2 ..
+    T* SG = SE + ER * XT_W;                  // [GR][XT_W]: source rows r0 - 1 ..
+    T* S1 = SG + GR * XT_W;                  // [GR][XT_W]: first sweep, rows r0 - 1 ..
+    uint64_t* bar = reinterpret_cast<uint64_t*>(S1 + GR * XT_W);
+    const int t = threadIdx.x;
+    const int n = a.e_new.n;
+    const int c0 = blockIdx.x * XT_OUT, r0 = blockIdx.y * RT + 1;
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
+                     "r"((uint32_t)((ER + GR) * XT_W * sizeof(T)))
+                     : "memory");
+        xt_load_2d(SE, &me, c0 - 8, r0 - 2, bar);
+        xt_load_2d(SG, &mg, c0 - 8, r0 - 1, bar);
+    }
+    if (!__syncthreads_and(xt_wait(bar, 0))) {
+        if (t == 0) atomicExch(fault, 1);
+        xt_wait(bar, 0);  // one more bounded wait before the block's shared memory is released
+        return;
+    }
+    const int x = c0 - 8 + 2 * t;  // this thread's first column
+    // A tile whose first-sweep area (staged columns 2 .. 253, rows r0 - 1 .. r0 + RT) lies inside the
+    // lattice's interior needs no masking. Measured at 4097² (same box, A/B): the bfloat16 kernel,
+    // bound by instruction issue, runs a level-0 pair in 23.4 us with the unmasked interior path
+    // against 26.0 us without; the binary32 one, bound by memory latency, in 39.4 against 38.3 us,
+    // so it keeps the masked path everywhere.
+    const bool inner = c0 - 6 >= 1 && c0 + 245 <= n - 1 && r0 - 1 >= 1 && r0 + RT <= n - 1;
+    if (sizeof(T) == 2 && inner) x2t_sweeps<T, RT, false>(a, SE, SG, S1, x, r0);
+    else x2t_sweeps<T, RT, true>(a, SE, SG, S1, x, r0);
 }
 
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
@@ -2401,6 +2557,95 @@ cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_
             return a.bst ? launch_k(k_jacobi2_x2<__nv_bfloat16, true>, g, b, s, a, rows)
                          : launch_k(k_jacobi2_x2<__nv_bfloat16, false>, g, b, s, a, rows);
         default: return cudaErrorInvalidValue;  // FP64 sweeps are FP64-bound: never paired
+    }
+}
+
+// TMA two-sweep kernel: RT output rows per block. Measured at 4097² (graph solves, RT from 4 to 32):
+// short tiles win, many small blocks per SM overlapping each other's copy with their sweeps;
+// bfloat16 8 rows (16 KB of shared memory, 24.9-25.5 us per level-0 pair against 28.3 at 32 rows),
+// binary32 4 rows (20 KB, 38.4 us against 45.0 at 32 rows).
+template <typename T> constexpr int xt_rows() { return sizeof(T) == 2 ? 8 : 4; }
+template <typename T> constexpr size_t xt_smem_bytes() {
+    return (size_t)((xt_rows<T>() + 4) + 2 * (xt_rows<T>() + 2)) * XT_W * sizeof(T) + 16;
+}
+
+// cuTensorMapEncodeTiled, obtained once through the runtime's driver entry-point query.
+PFN_cuTensorMapEncodeTiled_v12000 xt_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// A lattice array of (n + 1) x (n + 1) nodes, rows of `pitch` elements, as a 2-D tensor whose box
+// is XT_W columns x `rows` rows; zero outside the lattice.
+template <typename T>
+cudaError_t xt_map(CUtensorMap* map, const void* base, int n, int64_t pitch, int rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = xt_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)(n + 1), (cuuint64_t)(n + 1)};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(T)};
+    const cuuint32_t box[2] = {(cuuint32_t)XT_W, (cuuint32_t)rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename T> cudaError_t tma_sweep_maps_t(const IterArgs& a, TmaSweepMaps* maps) {
+    const int n = a.e_new.n;
+    if (!a.e_old.p || !a.g.p || a.bst || n < XT_MIN_N || (a.e_old.pitch * sizeof(T)) % 16 || (a.g.pitch * sizeof(T)) % 16 ||
+        reinterpret_cast<uintptr_t>(a.e_old.p) % 16 || reinterpret_cast<uintptr_t>(a.g.p) % 16 || a.e_new.pitch % 2 ||
+        reinterpret_cast<uintptr_t>(a.e_new.p) % (2 * sizeof(T)))
+        return cudaErrorInvalidValue;
+    cudaError_t e = xt_map<T>(&maps->me, a.e_old.p, n, a.e_old.pitch, xt_rows<T>() + 4);
+    if (e == cudaSuccess) e = xt_map<T>(&maps->mg, a.g.p, n, a.g.pitch, xt_rows<T>() + 2);
+    return e;
+}
+
+cudaError_t tma_sweep_maps(int prec, const IterArgs& a, TmaSweepMaps* maps) {
+    switch (prec) {
+        case PREC_FP32: return tma_sweep_maps_t<float>(a, maps);
+        case PREC_BF16: return tma_sweep_maps_t<__nv_bfloat16>(a, maps);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t iterate2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
+    constexpr int RT = xt_rows<T>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi2_x2t<T, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)xt_smem_bytes<T>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int n = a.e_new.n;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((n - 1) / XT_OUT + 1), (unsigned)((n - 1 + RT - 1) / RT));
+    cfg.blockDim = dim3(XT_W / 2);
+    cfg.dynamicSmemBytes = xt_smem_bytes<T>();
+    cfg.stream = s;
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_jacobi2_x2t<T, RT>, a, maps.me, maps.mg, fault);
+}
+
+cudaError_t launch_iterate2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
+    switch (prec) {
+        case PREC_FP32: return iterate2_tma_t<float>(a, maps, fault, s);
+        case PREC_BF16: return iterate2_tma_t<__nv_bfloat16>(a, maps, fault, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -86,6 +86,7 @@ class homg_options(ctypes.Structure):
         ("v_post", ctypes.c_int),
         ("geometry", ctypes.c_int),
         ("run_max_n", ctypes.c_int),
+        ("tma_min_n", ctypes.c_int),
     ]
 
 
@@ -221,7 +222,8 @@ HOMG_GEOM_NESTED, HOMG_GEOM_POW2 = 0, 1
 
 
 def _options(omega_j=0.0, max_i=32, schedule=None, exec_mode="auto", strict_fp=False, diverge_factor=0.0,
-             launch_mode="graph", precision="fp64", cycle="homg", v_pre=0, v_post=0, geometry="nested", run_max_n=0):
+             launch_mode="graph", precision="fp64", cycle="homg", v_pre=0, v_post=0, geometry="nested", run_max_n=0,
+             tma_min_n=0):
     o = homg_default_options()
     o.omega_j = omega_j
     o.max_i = max_i
@@ -235,6 +237,7 @@ def _options(omega_j=0.0, max_i=32, schedule=None, exec_mode="auto", strict_fp=F
     o.v_post = v_post
     o.geometry = GEOMETRIES[geometry] if isinstance(geometry, str) else int(geometry)
     o.run_max_n = int(run_max_n)
+    o.tma_min_n = int(tma_min_n)
     keep = None
     if schedule is not None:
         keep = (ctypes.c_int * len(schedule))(*schedule)
@@ -321,7 +324,7 @@ class BatchSolver:
 def homg_create(ndim, n_nodes, levels, stencil=None, **opts):
     """Create a handle for an (n_nodes)^ndim grid; returns an opaque handle (int). Options as in
     homg_options (omega_j, max_i, schedule, exec_mode, strict_fp, diverge_factor, launch_mode,
-    precision, cycle, v_pre, v_post, geometry, run_max_n)."""
+    precision, cycle, v_pre, v_post, geometry, run_max_n, tma_min_n)."""
     lib = load()
     o, _keep = _options(**opts)
     dims = (ctypes.c_int64 * ndim)(*([n_nodes] * ndim))
