@@ -110,17 +110,10 @@ __device__ __forceinline__ float narrow_rn(double d) {
     return __uint_as_float((sg | ((unsigned)e << 23) | m) + up);
 }
 
-// Stored value -> binary64, and binary64 -> stored value (via binary32 for bfloat16, the oracle's
-// storage rounding), with the conversions above.
+// Stored value -> binary64, with the conversions above.
 template <typename T> __device__ __forceinline__ double to_d(T x);
 template <> __device__ __forceinline__ double to_d<double>(double x) { return x; }
 template <> __device__ __forceinline__ double to_d<float>(float x) { return widen_f32(x); }
-template <typename T> __device__ __forceinline__ T from_d_store(double x);
-template <> __device__ __forceinline__ double from_d_store<double>(double x) { return x; }
-template <> __device__ __forceinline__ float from_d_store<float>(double x) { return narrow_rn(x); }
-template <> __device__ __forceinline__ __nv_bfloat16 from_d_store<__nv_bfloat16>(double x) {
-    return __float2bfloat16_rn(narrow_rn(x));
-}
 
 // The cycle's source scale * r stored from the FP64 residual r (fast forms). FP64 cycles form the
 // product in binary64; binary32 and bfloat16 cycles narrow r first and multiply in binary32 (one
@@ -1066,17 +1059,16 @@ template <> __device__ __forceinline__ void st2<float>(float* p, float2 v) { *re
 template <> __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16* p, float2 v) {
     *reinterpret_cast<unsigned*>(p) = pack_bf16x2_rn(v);
 }
-// Pairs in shared memory (the staged tiles of k_jacobi2_x2t): an aligned pair load and store.
-template <typename T> __device__ __forceinline__ float2 ld2s(const T* p);
-template <> __device__ __forceinline__ float2 ld2s<float>(const float* p) { return *reinterpret_cast<const float2*>(p); }
-template <> __device__ __forceinline__ float2 ld2s<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return unpack_bf16x2(*reinterpret_cast<const unsigned*>(p));
+// Binary32 pairs in shared memory (the staged tiles of k_jacobi2_x2t): an aligned pair load and store.
+__device__ __forceinline__ float2 ld2s(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2s(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+// Four adjacent bfloat16 values in shared memory (8-byte aligned) as two binary32 pairs, and back.
+__device__ __forceinline__ void ld4s(const __nv_bfloat16* p, float2& lo, float2& hi) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    lo = unpack_bf16x2(w.x);
+    hi = unpack_bf16x2(w.y);
 }
-template <typename T> __device__ __forceinline__ void st2s(T* p, float2 v);
-template <> __device__ __forceinline__ void st2s<float>(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
-template <> __device__ __forceinline__ void st2s<__nv_bfloat16>(__nv_bfloat16* p, float2 v) {
-    *reinterpret_cast<unsigned*>(p) = pack_bf16x2_rn(v);
-}
+__device__ __forceinline__ uint2 pack4(float2 lo, float2 hi) { return make_uint2(pack_bf16x2_rn(lo), pack_bf16x2_rn(hi)); }
 template <typename T> __device__ __forceinline__ float2 round2(float2 v) { return v; }
 template <> __device__ __forceinline__ float2 round2<__nv_bfloat16>(float2 v) { return unpack_bf16x2(pack_bf16x2_rn(v)); }
 
@@ -1251,7 +1243,8 @@ __global__ void __launch_bounds__(JX) k_jacobi2_xk(IterArgs a, int rows) {
 // issues two TMA tensor copies: the input iterate's rows r0 - 2 .. r0 + RT + 1 and the source's
 // rows r0 - 1 .. r0 + RT, XT_W columns from c0 - 8 each (a multiple of 8: the copy's innermost
 // coordinate must sit on a 16-byte boundary; zero outside the lattice), into shared memory. Thread t
-// owns staged columns 2t and 2t + 1: it computes the first sweep on rows r0 - 1 .. r0 + RT into a
+// owns Q adjacent staged columns from Q t (Q = 2 for binary32, 4 for bfloat16; XT_W / Q threads):
+// it computes the first sweep on rows r0 - 1 .. r0 + RT into a
 // shared buffer (rounded to the storage type as a stored sweep is, 0 outside the interior), then,
 // after a block barrier, the second sweep on the output rows, stored to global memory. Both
 // sweeps run as packed binary32 pairs in the per-column kernel's operation order, so the result is
@@ -1288,10 +1281,12 @@ __device__ __forceinline__ void xt_load_2d(void* dst, const CUtensorMap* map, in
         : "memory");
 }
 
-// The two sweeps of k_jacobi2_x2t from its staged tiles (MASK: the tile touches the lattice's
-// boundary, so first-sweep values outside the interior are replaced by 0 and stores are masked).
-template <typename T, int RT, bool MASK>
-__device__ __forceinline__ void x2t_sweeps(const IterArgs& a, const T* SE, const T* SG, T* S1, int x, int r0) {
+// The two sweeps of k_jacobi2_x2t from its staged tiles, two columns per thread (binary32 storage):
+// first-sweep values outside the interior are replaced by 0 and stores are masked.
+template <int RT>
+__device__ __forceinline__ void x2t_sweeps(const IterArgs& a, const float* SE, const float* SG, float* S1, int x, int r0) {
+    using T = float;
+    constexpr bool MASK = true;
     constexpr int GR = RT + 2;
     const int t = threadIdx.x;
     const int n = a.e_new.n;
@@ -1300,22 +1295,22 @@ __device__ __forceinline__ void x2t_sweeps(const IterArgs& a, const T* SE, const
     // first sweep, rows r0 - 1 .. r0 + RT (shared rows 0 .. GR - 1), staged columns 2 .. 253
     if (t >= 1 && t < XT_W / 2 - 1) {
         const T* col = SE + 2 * t;
-        float2 em = ld2s<T>(col), ec = ld2s<T>(col + XT_W);
+        float2 em = ld2s(col), ec = ld2s(col + XT_W);
 #pragma unroll 4
         for (int p = 0; p < GR; ++p) {
             const T* row = col + (p + 1) * XT_W;  // iterate row r0 - 1 + p
-            const float2 ep = ld2s<T>(row + XT_W);
+            const float2 ep = ld2s(row + XT_W);
             const float left = as_c<T>(row[-1]), right = as_c<T>(row[2]);
-            const float2 g = ld2s<T>(SG + p * XT_W + 2 * t);
+            const float2 g = ld2s(SG + p * XT_W + 2 * t);
             const float2 sum = add2(make_float2(left + ec.y, ec.x + right), add2(em, ep));  // (w + e) + (s + n)
-            float2 v = round2<T>(fma2(c1, ec, fma2(om, sum, g)));
+            float2 v = fma2(c1, ec, fma2(om, sum, g));
             if (MASK) {
                 const int r = r0 - 1 + p;
                 const bool rin = r >= 1 && r <= n - 1;
                 v.x = (rin && m0) ? v.x : 0.f;
                 v.y = (rin && m1) ? v.y : 0.f;
             }
-            st2s<T>(S1 + p * XT_W + 2 * t, v);
+            st2s(S1 + p * XT_W + 2 * t, v);
             em = ec;
             ec = ep;
         }
@@ -1326,14 +1321,14 @@ __device__ __forceinline__ void x2t_sweeps(const IterArgs& a, const T* SE, const
         T* __restrict__ O = wp<T>(a.e_new);
         const int64_t po = a.e_new.pitch;
         const T* col = S1 + 2 * t;
-        float2 sp = ld2s<T>(col), sc = ld2s<T>(col + XT_W);
+        float2 sp = ld2s(col), sc = ld2s(col + XT_W);
         const int pe = MASK ? min(RT, n - r0) : RT;  // output rows inside the lattice
 #pragma unroll 4
         for (int p = 1; p <= pe; ++p) {
             const T* row = col + p * XT_W;
-            const float2 sn = ld2s<T>(row + XT_W);
+            const float2 sn = ld2s(row + XT_W);
             const float left = as_c<T>(row[-1]), right = as_c<T>(row[2]);
-            const float2 g = ld2s<T>(SG + p * XT_W + 2 * t);
+            const float2 g = ld2s(SG + p * XT_W + 2 * t);
             const float2 sum = add2(make_float2(left + sc.y, sc.x + right), add2(sp, sn));
             const float2 o = fma2(c1, sc, fma2(om, sum, g));
             T* dst = O + (int64_t)(r0 - 1 + p) * po + x;
@@ -1348,8 +1343,91 @@ __device__ __forceinline__ void x2t_sweeps(const IterArgs& a, const T* SE, const
     }
 }
 
-template <typename T, int RT>
-__global__ void __launch_bounds__(XT_W / 2) k_jacobi2_x2t(IterArgs a, const __grid_constant__ CUtensorMap me,
+// The two sweeps of k_jacobi2_x2t with four adjacent columns per thread (bfloat16 storage, whose
+// kernel is bound by instruction issue): one 8-byte shared load per row for four columns, and the
+// side neighbours of the outer two; the same per-column operations as two pairs.
+template <int RT, bool MASK>
+__device__ __forceinline__ void x2t_sweeps4(const IterArgs& a, const __nv_bfloat16* SE, const __nv_bfloat16* SG,
+                                            __nv_bfloat16* S1, int x, int r0) {
+    using T = __nv_bfloat16;
+    constexpr int GR = RT + 2;
+    const int t = threadIdx.x;
+    const int n = a.e_new.n;
+    const float2 om = make_float2(a.omega_f, a.omega_f), c1 = make_float2(a.c1_f, a.c1_f);
+    bool m[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m[k] = !MASK || (x + k >= 1 && x + k <= n - 1);  // interior columns
+    // first sweep, rows r0 - 1 .. r0 + RT (shared rows 0 .. GR - 1), staged columns 4 .. 251
+    if (t >= 1 && t < XT_W / 4 - 1) {
+        const T* col = SE + 4 * t;
+        float2 emL, emH, ecL, ecH;
+        ld4s(col, emL, emH);
+        ld4s(col + XT_W, ecL, ecH);
+#pragma unroll 4
+        for (int p = 0; p < GR; ++p) {
+            const T* row = col + (p + 1) * XT_W;  // iterate row r0 - 1 + p
+            float2 epL, epH, gL, gH;
+            ld4s(row + XT_W, epL, epH);
+            ld4s(SG + p * XT_W + 4 * t, gL, gH);
+            const float left = as_c<T>(row[-1]), right = as_c<T>(row[4]);
+            // (w + e) + (s + n) per column
+            const float2 sL = add2(make_float2(left + ecL.y, ecL.x + ecH.x), add2(emL, epL));
+            const float2 sH = add2(make_float2(ecL.y + ecH.y, ecH.x + right), add2(emH, epH));
+            float2 vL = fma2(c1, ecL, fma2(om, sL, gL)), vH = fma2(c1, ecH, fma2(om, sH, gH));
+            if (MASK) {
+                const int r = r0 - 1 + p;
+                const bool rin = r >= 1 && r <= n - 1;
+                vL.x = (rin && m[0]) ? vL.x : 0.f;
+                vL.y = (rin && m[1]) ? vL.y : 0.f;
+                vH.x = (rin && m[2]) ? vH.x : 0.f;
+                vH.y = (rin && m[3]) ? vH.y : 0.f;
+            }
+            *reinterpret_cast<uint2*>(S1 + p * XT_W + 4 * t) = pack4(vL, vH);  // rounded to bfloat16 (0 stays 0)
+            emL = ecL;
+            emH = ecH;
+            ecL = epL;
+            ecH = epH;
+        }
+    }
+    __syncthreads();
+    // second sweep, output rows r0 .. r0 + RT - 1 (shared rows 1 .. RT), staged columns 8 .. 247
+    if (t >= 2 && t < 2 + XT_OUT / 4) {
+        T* __restrict__ O = wp<T>(a.e_new);
+        const int64_t po = a.e_new.pitch;
+        const T* col = S1 + 4 * t;
+        float2 spL, spH, scL, scH;
+        ld4s(col, spL, spH);
+        ld4s(col + XT_W, scL, scH);
+        const int pe = MASK ? min(RT, n - r0) : RT;  // output rows inside the lattice
+        const bool all = m[0] && m[1] && m[2] && m[3];
+#pragma unroll 4
+        for (int p = 1; p <= pe; ++p) {
+            const T* row = col + p * XT_W;
+            float2 snL, snH, gL, gH;
+            ld4s(row + XT_W, snL, snH);
+            ld4s(SG + p * XT_W + 4 * t, gL, gH);
+            const float left = as_c<T>(row[-1]), right = as_c<T>(row[4]);
+            const float2 sL = add2(make_float2(left + scL.y, scL.x + scH.x), add2(spL, snL));
+            const float2 sH = add2(make_float2(scL.y + scH.y, scH.x + right), add2(spH, snH));
+            const float2 oL = fma2(c1, scL, fma2(om, sL, gL)), oH = fma2(c1, scH, fma2(om, sH, gH));
+            T* dst = O + (int64_t)(r0 - 1 + p) * po + x;
+            if (all) *reinterpret_cast<uint2*>(dst) = pack4(oL, oH);
+            else {
+                const float o[4] = {oL.x, oL.y, oH.x, oH.y};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (m[k]) dst[k] = St<T>::put(o[k]);
+            }
+            spL = scL;
+            spH = scH;
+            scL = snL;
+            scH = snH;
+        }
+    }
+}
+
+template <typename T, int RT, int Q>
+__global__ void __launch_bounds__(XT_W / Q) k_jacobi2_x2t(IterArgs a, const __grid_constant__ CUtensorMap me,
                                                           const __grid_constant__ CUtensorMap mg, int* fault) {
     pdl_begin();
     constexpr int ER = RT + 4, GR = RT + 2;  // staged rows of the iterate and of the source
@@ -1378,15 +1456,19 @@ __global__ void __launch_bounds__(XT_W / 2) k_jacobi2_x2t(IterArgs a, const __gr
         xt_wait(bar, 0);  // one more bounded wait before the block's shared memory is released
         return;
     }
-    const int x = c0 - 8 + 2 * t;  // this thread's first column
-    // A tile whose first-sweep area (staged columns 2 .. 253, rows r0 - 1 .. r0 + RT) lies inside the
-    // lattice's interior needs no masking. Measured at 4097² (same box, A/B): the bfloat16 kernel,
-    // bound by instruction issue, runs a level-0 pair in 23.4 us with the unmasked interior path
-    // against 26.0 us without; the binary32 one, bound by memory latency, in 39.4 against 38.3 us,
-    // so it keeps the masked path everywhere.
+    const int x = c0 - 8 + Q * t;  // this thread's first column
+    // A tile whose first-sweep area (at most staged columns 2 .. 253, rows r0 - 1 .. r0 + RT) lies
+    // inside the lattice's interior needs no masking. Measured at 4097² (same box, A/B, two columns
+    // per thread): the bfloat16 kernel, bound by instruction issue, ran a level-0 pair in 23.4 us with
+    // the unmasked interior path against 26.0 us without (20.9 us with four columns per thread); the
+    // binary32 one, bound by memory latency, in 39.4 against 38.3 us, so it keeps the masked path.
     const bool inner = c0 - 6 >= 1 && c0 + 245 <= n - 1 && r0 - 1 >= 1 && r0 + RT <= n - 1;
-    if (sizeof(T) == 2 && inner) x2t_sweeps<T, RT, false>(a, SE, SG, S1, x, r0);
-    else x2t_sweeps<T, RT, true>(a, SE, SG, S1, x, r0);
+    if constexpr (Q == 4) {
+        if (inner) x2t_sweeps4<RT, false>(a, SE, SG, S1, x, r0);
+        else x2t_sweeps4<RT, true>(a, SE, SG, S1, x, r0);
+    } else {
+        x2t_sweeps<RT>(a, SE, SG, S1, x, r0);
+    }
 }
 
 // Fast lattice-form level change at stride 2 (2-D): lattice nodes copy Gc; the others take the
@@ -2562,9 +2644,11 @@ cudaError_t launch_iterate2(int prec, int sweeps, const IterArgs& a, cudaStream_
 
 // TMA two-sweep kernel: RT output rows per block. Measured at 4097² (graph solves, RT from 4 to 32):
 // short tiles win, many small blocks per SM overlapping each other's copy with their sweeps;
-// bfloat16 8 rows (16 KB of shared memory, 24.9-25.5 us per level-0 pair against 28.3 at 32 rows),
-// binary32 4 rows (20 KB, 38.4 us against 45.0 at 32 rows).
-template <typename T> constexpr int xt_rows() { return sizeof(T) == 2 ? 8 : 4; }
+// bfloat16 8 rows (16 KB of shared memory; four columns per thread: 20.9 us per level-0 pair, 23.0
+// at 4 rows, 21.4 at 12), binary32 6 rows (26 KB; 36.8 us, 38.4 at 4 and 8 rows, 45.0 at 32).
+template <typename T> constexpr int xt_rows() { return sizeof(T) == 2 ? 8 : 6; }
+// Columns per thread: four for bfloat16 (fewer instructions per node), two for binary32.
+template <typename T> constexpr int xt_cols() { return sizeof(T) == 2 ? 4 : 2; }
 template <typename T> constexpr size_t xt_smem_bytes() {
     return (size_t)((xt_rows<T>() + 4) + 2 * (xt_rows<T>() + 2)) * XT_W * sizeof(T) + 16;
 }
@@ -2620,9 +2704,10 @@ cudaError_t tma_sweep_maps(int prec, const IterArgs& a, TmaSweepMaps* maps) {
 template <typename T>
 cudaError_t iterate2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
     constexpr int RT = xt_rows<T>();
+    constexpr int Q = xt_cols<T>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_jacobi2_x2t<T, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi2_x2t<T, RT, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)xt_smem_bytes<T>());
         if (e != cudaSuccess) return e;
         attr = true;
@@ -2630,7 +2715,7 @@ cudaError_t iterate2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fau
     const int n = a.e_new.n;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((n - 1) / XT_OUT + 1), (unsigned)((n - 1 + RT - 1) / RT));
-    cfg.blockDim = dim3(XT_W / 2);
+    cfg.blockDim = dim3(XT_W / Q);
     cfg.dynamicSmemBytes = xt_smem_bytes<T>();
     cfg.stream = s;
     cudaLaunchAttribute attrs[1];
@@ -2638,7 +2723,7 @@ cudaError_t iterate2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fau
     attrs[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attrs;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_jacobi2_x2t<T, RT>, a, maps.me, maps.mg, fault);
+    return cudaLaunchKernelEx(&cfg, k_jacobi2_x2t<T, RT, Q>, a, maps.me, maps.mg, fault);
 }
 
 cudaError_t launch_iterate2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
