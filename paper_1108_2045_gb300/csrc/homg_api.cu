@@ -548,7 +548,8 @@ void plan_cycle(homg_ctx* h) {
                     a.dnew = grid(nullptr, 0, 0);
                     // large single-problem lattices: the two sweeps with the tile staged by TMA
                     if (k == 2 && h->nbatch == 1 && h->opt.tma_min_n > 0 && lv.n >= h->opt.tma_min_n &&
-                        tma_sweep_maps(h->prec, a, &op.maps) == cudaSuccess)
+                        (h->ndim == 2 ? tma_sweep_maps(h->prec, a, &op.maps) : tma_sweep_maps3(h->prec, a, &op.maps)) ==
+                            cudaSuccess)
                         op.tma = true;
                     (m == 0 ? h->partB : h->partA).push_back(op);
                     cur ^= 1;
@@ -688,9 +689,10 @@ cudaError_t enqueue_ops(homg_ctx* h, const std::vector<Op>& ops, cudaStream_t s)
         switch (op.kind) {
             case Op::ITER: e = launch_iterate(h->ndim, h->prec, h->strict, op.it, s); break;
             case Op::ITER2:
-                e = (h->ndim == 3) ? launch_iterate3_2(h->prec, op.it, s)
-                    : op.tma       ? launch_iterate2_tma(h->prec, op.it, op.maps, &h->dstate->fault, s)
-                                   : launch_iterate2(h->prec, op.sweeps, op.it, s);
+                e = op.tma ? (h->ndim == 3 ? launch_iterate3_2_tma(h->prec, op.it, op.maps, &h->dstate->fault, s)
+                                           : launch_iterate2_tma(h->prec, op.it, op.maps, &h->dstate->fault, s))
+                    : (h->ndim == 3) ? launch_iterate3_2(h->prec, op.it, s)
+                                     : launch_iterate2(h->prec, op.sweeps, op.it, s);
                 break;
             case Op::PROLONG: e = launch_prolong(h->ndim, h->prec, h->strict, op.pr, s); break;
             case Op::RESTRICT: e = launch_restrict(h->ndim, h->prec, h->strict, op.rs, s); break;

@@ -309,6 +309,9 @@ struct TmaSweepMaps {
 constexpr int XT_MIN_N = 256;  // smallest lattice the TMA two-sweep kernel is planned for
 cudaError_t tma_sweep_maps(int prec, const IterArgs& a, TmaSweepMaps* maps);
 cudaError_t launch_iterate2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s);
+// The same for 3-D lattices (planes staged by TMA, the block marching down z).
+cudaError_t tma_sweep_maps3(int prec, const IterArgs& a, TmaSweepMaps* maps);
+cudaError_t launch_iterate3_2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s);
 // Two plain 3-D lattice-form sweeps in one launch (FP32 / bfloat16 storage).
 cudaError_t launch_iterate3_2(int prec, const IterArgs& a, cudaStream_t s);
 cudaError_t launch_prolong(int ndim, int prec, bool strict, const ProlongArgs& a, cudaStream_t s);

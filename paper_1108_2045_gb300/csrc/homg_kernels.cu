@@ -1791,6 +1791,202 @@ __global__ void __launch_bounds__(J3X * J3Y2) k_jacobi3_x2(IterArgs a, int rows)
     }
 }
 
+// Two plain 3-D damped-Jacobi sweeps with the planes staged by TMA (binary32 and bfloat16 storage,
+// lattice form, one problem). A block owns XT_OUT output columns c0 .., RY output rows y0 .. and RZ
+// output planes z0 .. and marches down z. Its shared memory holds three rings of planes, each 256
+// columns from c0 - 8 wide: the input iterate (4 slots, rows y0 - 2 .. y0 + RY + 1), the source (3
+// slots, rows y0 - 1 .. y0 + RY) and the first sweep (3 slots, rows y0 - 1 .. y0 + RY). Step zf
+// (first-sweep plane, z0 - 1 .. z0 + RZ): thread 0 copies iterate plane zf + 2 and source plane
+// zf + 1 by TMA (zero outside the lattice) for the next step; all threads wait (bounded) for this
+// step's planes, run the first sweep at plane zf over RY + 2 rows into the first-sweep ring, pass a
+// block barrier, run the second sweep at plane zf - 1 over the output rows to global memory, and
+// pass another. Thread t owns Q adjacent columns from Q t and marches down its rows, keeping the
+// y neighbours in registers. Per node: the sums (w + e), (s + n) along y, (b + t) along z, added in
+// the single-sweep kernel's order, as packed binary32 pairs; bit-identical to two single sweeps.
+// tests/test_tma3_ring_model.py replays the ring schedule on the CPU.
+template <typename T> __device__ __forceinline__ void ldq(const T* p, float2* v, int np);
+template <> __device__ __forceinline__ void ldq<float>(const float* p, float2* v, int np) {
+    if (np == 1) v[0] = *reinterpret_cast<const float2*>(p);
+    else {
+        const float4 w = *reinterpret_cast<const float4*>(p);
+        v[0] = make_float2(w.x, w.y);
+        v[1] = make_float2(w.z, w.w);
+    }
+}
+template <> __device__ __forceinline__ void ldq<__nv_bfloat16>(const __nv_bfloat16* p, float2* v, int np) {
+    if (np == 1) v[0] = unpack_bf16x2(*reinterpret_cast<const unsigned*>(p));
+    else ld4s(p, v[0], v[1]);
+}
+template <typename T> __device__ __forceinline__ void stq(T* p, const float2* v, int np);
+template <> __device__ __forceinline__ void stq<float>(float* p, const float2* v, int np) {
+    if (np == 1) *reinterpret_cast<float2*>(p) = v[0];
+    else *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+}
+template <> __device__ __forceinline__ void stq<__nv_bfloat16>(__nv_bfloat16* p, const float2* v, int np) {
+    if (np == 1) *reinterpret_cast<unsigned*>(p) = pack_bf16x2_rn(v[0]);
+    else *reinterpret_cast<uint2*>(p) = pack4(v[0], v[1]);
+}
+__device__ __forceinline__ void xt_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"((uint32_t)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+__device__ __forceinline__ void xt_arm(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One row of a thread's Q = 2 NP columns of a 3-D sweep from staged planes: c the row in its plane,
+// y neighbours in vm / vp (registers), z neighbours at b / t, source at g.
+template <typename T, int NP>
+__device__ __forceinline__ void sweep3_row(const T* c, const float2* vm, const float2* vc, const float2* vp, const T* b,
+                                           const T* t, const T* g, float2 om, float2 c1, float2* o) {
+    constexpr int Q = 2 * NP;
+    float2 vb[NP], vt[NP], gv[NP];
+    ldq<T>(b, vb, NP);
+    ldq<T>(t, vt, NP);
+    ldq<T>(g, gv, NP);
+    const float left = as_c<T>(c[-1]), right = as_c<T>(c[Q]);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const float w0 = k == 0 ? left : vc[k - 1].y, e1 = k == NP - 1 ? right : vc[k + 1].x;
+        const float2 we = make_float2(w0 + vc[k].y, vc[k].x + e1);                  // (w + e)
+        const float2 sum = add2(add2(we, add2(vm[k], vp[k])), add2(vb[k], vt[k]));  // + (s + n), + (b + t)
+        o[k] = fma2(c1, vc[k], fma2(om, sum, gv[k]));
+    }
+}
+
+template <typename T, int RY, int RZ, int NP>
+__global__ void __launch_bounds__(XT_W / (2 * NP)) k_jacobi3_x2t(IterArgs a, const __grid_constant__ CUtensorMap me,
+                                                                 const __grid_constant__ CUtensorMap mg, int* fault) {
+    pdl_begin();
+    constexpr int Q = 2 * NP, ER = RY + 4, GR = RY + 2;
+    constexpr int EP = ER * XT_W, GP = GR * XT_W;  // elements of one staged plane
+    extern __shared__ __align__(128) unsigned char x3_smem[];
+    T* E = reinterpret_cast<T*>(x3_smem);  // 4 slots, iterate plane p in slot (p + 2) mod 4, rows y0 - 2 ..
+    T* G = E + 4 * EP;                     // 3 slots, source plane p in slot (p + 1) mod 3, rows y0 - 1 ..
+    T* S = G + 3 * GP;                     // 3 slots, first sweep at plane p in slot (p + 1) mod 3, rows y0 - 1 ..
+    uint64_t* bar = reinterpret_cast<uint64_t*>(S + 3 * GP);  // bar[0..3]: per-step copies, bar[4]: set-up
+    const int t = threadIdx.x;
+    const int n = a.e_new.n;
+    const int c0 = blockIdx.x * XT_OUT, y0 = blockIdx.y * RY + 1, z0 = blockIdx.z * RZ + 1;
+    const int zlast = min(z0 + RZ, n);  // last first-sweep plane (the plane past the block's last output)
+    const int zout = min(z0 + RZ - 1, n - 1);
+    auto eslot = [&](int p) { return E + ((p + 2) & 3) * EP; };
+    auto gslot = [&](int p) { return G + ((p + 1) % 3) * GP; };
+    auto sslot = [&](int p) { return S + ((p + 1) % 3) * GP; };
+    if (t == 0) {
+        for (int k = 0; k < 5; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar + k)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0) {
+        xt_arm(bar + 4, (uint32_t)((3 * EP + GP) * sizeof(T)));
+        for (int p = z0 - 2; p <= z0; ++p) xt_load_3d(eslot(p), &me, c0 - 8, y0 - 2, p, bar + 4);
+        xt_load_3d(gslot(z0 - 1), &mg, c0 - 8, y0 - 1, z0 - 1, bar + 4);
+    }
+    const float2 om = make_float2(a.omega_f, a.omega_f), c1 = make_float2(a.c1_f, a.c1_f);
+    const int x = c0 - 8 + Q * t;  // this thread's first column
+    bool mcol[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) mcol[k] = x + k >= 1 && x + k <= n - 1;
+    const bool first_cols = t >= 1 && t < XT_W / Q - 1;      // staged columns Q .. 255 - Q (7 .. 248 needed)
+    const bool out_cols = t >= 8 / Q && t < (8 + XT_OUT) / Q;                                 // staged columns 8 .. 247
+    uint32_t phases = 0;  // bit k: phase of bar[k] to wait for next
+    for (int zf = z0 - 1; zf <= zlast; ++zf) {
+        // (a) next step's planes, into slots the previous step's barriers freed
+        if (t == 0 && zf + 2 <= zlast + 1) {
+            uint64_t* b = bar + ((zf + 4) & 3);
+            const bool gnext = zf + 1 <= zlast;
+            xt_arm(b, (uint32_t)((EP + (gnext ? GP : 0)) * sizeof(T)));
+            xt_load_3d(eslot(zf + 2), &me, c0 - 8, y0 - 2, zf + 2, b);
+            if (gnext) xt_load_3d(gslot(zf + 1), &mg, c0 - 8, y0 - 1, zf + 1, b);
+        }
+        // (b) this step's planes
+        const int wb = zf == z0 - 1 ? 4 : ((zf + 3) & 3);
+        const bool arrived = xt_wait(bar + wb, (phases >> wb) & 1u);
+        phases ^= 1u << wb;
+        if (!__syncthreads_and(arrived)) {
+            // record the failure, give every copy still in flight one more bounded wait, and leave
+            if (t == 0) atomicExch(fault, 1);
+            for (int k = 0; k < 5; ++k) xt_wait(bar + k, (phases >> k) & 1u);
+            return;
+        }
+        // (c) first sweep at plane zf, rows y0 - 1 .. y0 + RY (0 off the interior)
+        if (first_cols) {
+            const T* ec = eslot(zf) + Q * t;
+            const T* eb = eslot(zf - 1) + Q * t;
+            const T* et = eslot(zf + 1) + Q * t;
+            const T* gp = gslot(zf) + Q * t;
+            T* sp = sslot(zf) + Q * t;
+            const bool pin = zf >= 1 && zf <= n - 1;
+            float2 vm[NP], vc[NP], vp[NP];
+            ldq<T>(ec, vm, NP);            // iterate row y0 - 2
+            ldq<T>(ec + XT_W, vc, NP);     // iterate row y0 - 1
+#pragma unroll 2
+            for (int r = 0; r < GR; ++r) {  // first-sweep row y0 - 1 + r = staged iterate row r + 1
+                const int q = r + 1;
+                ldq<T>(ec + (q + 1) * XT_W, vp, NP);
+                float2 o[NP];
+                sweep3_row<T, NP>(ec + q * XT_W, vm, vc, vp, eb + q * XT_W, et + q * XT_W, gp + r * XT_W, om, c1, o);
+                const int ra = y0 - 1 + r;
+                const bool in = pin && ra >= 1 && ra <= n - 1;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    o[k].x = (in && mcol[2 * k]) ? o[k].x : 0.f;
+                    o[k].y = (in && mcol[2 * k + 1]) ? o[k].y : 0.f;
+                }
+                stq<T>(sp + r * XT_W, o, NP);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    vm[k] = vc[k];
+                    vc[k] = vp[k];
+                }
+            }
+        }
+        __syncthreads();
+        // (e) second sweep at plane zs = zf - 1, rows y0 .. y0 + RY - 1, to global memory
+        const int zs = zf - 1;
+        if (zs >= z0 && zs <= zout && out_cols) {
+            const T* sc = sslot(zs) + Q * t;
+            const T* sb = sslot(zs - 1) + Q * t;
+            const T* st = sslot(zs + 1) + Q * t;
+            const T* gp = gslot(zs) + Q * t;
+            T* O = wp<T>(a.e_new) + ((int64_t)zs * (n + 1) + y0) * a.e_new.pitch + x;
+            const int pe = min(RY, n - y0);
+            const bool all = mcol[0] && mcol[Q - 1];
+            float2 vm[NP], vc[NP], vp[NP];
+            ldq<T>(sc, vm, NP);          // first-sweep row y0 - 1
+            ldq<T>(sc + XT_W, vc, NP);   // first-sweep row y0
+#pragma unroll 2
+            for (int r = 1; r <= pe; ++r) {
+                ldq<T>(sc + (r + 1) * XT_W, vp, NP);
+                float2 o[NP];
+                sweep3_row<T, NP>(sc + r * XT_W, vm, vc, vp, sb + r * XT_W, st + r * XT_W, gp + r * XT_W, om, c1, o);
+                T* d = O + (int64_t)(r - 1) * a.e_new.pitch;
+                if (all) stq<T>(d, o, NP);
+                else {
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        if (mcol[2 * k]) d[2 * k] = St<T>::put(o[k].x);
+                        if (mcol[2 * k + 1]) d[2 * k + 1] = St<T>::put(o[k].y);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    vm[k] = vc[k];
+                    vc[k] = vp[k];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Fast 3-D update + residual in two passes: k_update3 forms u_out = u_in + e (one FP64 add per
 // node), then k_residual3_fast marches each (i, j) column along z over the updated iterate with the
@@ -2724,6 +2920,85 @@ cudaError_t iterate2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fau
     cfg.attrs = attrs;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_jacobi2_x2t<T, RT, Q>, a, maps.me, maps.mg, fault);
+}
+
+// 3-D TMA two-sweep kernel: RY output rows, RZ output planes per block, Q = 2 NP columns per thread.
+// Measured at 513³ (level-0 pair inside the solve; RY 2 / 4 / 8, NP 1 / 2): bfloat16 8 rows, four
+// columns per thread (414 us against 576 us for the marching k_jacobi3_x2; 409 at 4 rows, 471-569
+// at 2), binary32 8 rows, two columns (567 against 598 us; 578 at 4 rows, 666 at 2).
+template <typename T> constexpr int x3_rows() { return 8; }
+constexpr int X3_PLANES = 32;
+template <typename T> constexpr int x3_pairs() { return sizeof(T) == 2 ? 2 : 1; }
+template <typename T> constexpr size_t x3_smem_bytes() {
+    return (size_t)(4 * (x3_rows<T>() + 4) + 6 * (x3_rows<T>() + 2)) * XT_W * sizeof(T) + 64;
+}
+
+// A 3-D lattice array of (n + 1)^3 nodes, rows of `pitch` elements, (n + 1) rows per plane, as a 3-D
+// tensor whose box is XT_W columns x `rows` rows x 1 plane; zero outside the lattice.
+template <typename T>
+cudaError_t xt_map3(CUtensorMap* map, const void* base, int n, int64_t pitch, int rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = xt_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)(n + 1), (cuuint64_t)(n + 1), (cuuint64_t)(n + 1)};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(T), (cuuint64_t)pitch * (cuuint64_t)(n + 1) * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)XT_W, (cuuint32_t)rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename T> cudaError_t tma_sweep_maps3_t(const IterArgs& a, TmaSweepMaps* maps) {
+    const int n = a.e_new.n;
+    if (!a.e_old.p || !a.g.p || a.bst || n < XT_MIN_N || (a.e_old.pitch * sizeof(T)) % 16 || (a.g.pitch * sizeof(T)) % 16 ||
+        reinterpret_cast<uintptr_t>(a.e_old.p) % 16 || reinterpret_cast<uintptr_t>(a.g.p) % 16 || a.e_new.pitch % 4 ||
+        reinterpret_cast<uintptr_t>(a.e_new.p) % 16)
+        return cudaErrorInvalidValue;
+    cudaError_t e = xt_map3<T>(&maps->me, a.e_old.p, n, a.e_old.pitch, x3_rows<T>() + 4);
+    if (e == cudaSuccess) e = xt_map3<T>(&maps->mg, a.g.p, n, a.g.pitch, x3_rows<T>() + 2);
+    return e;
+}
+
+cudaError_t tma_sweep_maps3(int prec, const IterArgs& a, TmaSweepMaps* maps) {
+    switch (prec) {
+        case PREC_FP32: return tma_sweep_maps3_t<float>(a, maps);
+        case PREC_BF16: return tma_sweep_maps3_t<__nv_bfloat16>(a, maps);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t iterate3_2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
+    constexpr int RY = x3_rows<T>(), NP = x3_pairs<T>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi3_x2t<T, RY, X3_PLANES, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)x3_smem_bytes<T>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int n = a.e_new.n;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((n - 1) / XT_OUT + 1), (unsigned)((n - 1 + RY - 1) / RY),
+                       (unsigned)((n - 1 + X3_PLANES - 1) / X3_PLANES));
+    cfg.blockDim = dim3(XT_W / (2 * NP));
+    cfg.dynamicSmemBytes = x3_smem_bytes<T>();
+    cfg.stream = s;
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_jacobi3_x2t<T, RY, X3_PLANES, NP>, a, maps.me, maps.mg, fault);
+}
+
+cudaError_t launch_iterate3_2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
+    switch (prec) {
+        case PREC_FP32: return iterate3_2_tma_t<float>(a, maps, fault, s);
+        case PREC_BF16: return iterate3_2_tma_t<__nv_bfloat16>(a, maps, fault, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_iterate2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {

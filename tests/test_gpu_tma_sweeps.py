@@ -62,3 +62,23 @@ def test_tma_sweeps_converge_to_the_oracle_residual(homg, precision):
     assert st == homg.HOMG_OK and rr <= 1e-10
     got = u.cpu().numpy()
     assert oracle.norm_interior(oracle.residual(f_np, got)) / oracle.norm_interior(f_np) <= 1.0001e-10
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_3d_tma_sweeps_are_bit_identical_to_marching_sweeps(homg, precision):
+    # 3-D: the planes staged by TMA in rings, the block marching down z (k_jacobi3_x2t); 257^3 nodes:
+    # the level-0 lattice of 256 intervals is not a multiple of the blocks' 240 columns, 4 rows or
+    # 32 planes
+    import torch
+
+    n, levels = 256, 8
+    f_np = inputs.normal_rhs(n, 3, seed=71)
+    out = {}
+    for tma in (256, -1):
+        with homg.Solver(3, n + 1, levels, exec_mode="lattice", precision=precision, tma_min_n=tma) as s:
+            f = torch.from_numpy(f_np).cuda()
+            u = torch.zeros_like(f)
+            st, cyc, rr = s.solve(f, u, tol=0.0, max_cycles=2)
+            out[tma] = (u, cyc, rr, s.history())
+    assert out[256][1:] == out[-1][1:]
+    assert torch.equal(out[256][0], out[-1][0])
