@@ -129,12 +129,13 @@ typedef struct homg_options {
      * turns it off; at most 128. The iterates are bit-identical either way. Persistent batches
      * never use it. */
     int run_max_n;
-    /* Lattice form of binary32 / bfloat16 HOMG cycles in 2-D (not strict_fp, one problem per
-     * handle or batch group): pairs of plain sweeps on lattices of at least tma_min_n intervals per
+    /* Lattice form of binary32 / bfloat16 HOMG cycles (not strict_fp, one problem per handle;
+     * batches never use it): pairs of plain sweeps on lattices of at least tma_min_n intervals per
      * side run as one launch whose blocks stage their tile of the iterate and the source (with a
-     * two-node halo) in shared memory by TMA tensor copies, then run both sweeps from there.
-     * 0 selects the default threshold (HOMG_TMA_MIN_N_DEFAULT), a negative value turns it off;
-     * values below 256 are raised to 256. The iterates are bit-identical either way. */
+     * two-node halo) in shared memory by TMA tensor copies, then run both sweeps from there (3-D:
+     * rings of planes, each block marching down z). 0 selects the default threshold
+     * (HOMG_TMA_MIN_N_DEFAULT), a negative value turns it off; values below 256 are raised to 256.
+     * The iterates are bit-identical either way. */
     int tma_min_n;
 } homg_options;
 
