@@ -1859,35 +1859,49 @@ __device__ __forceinline__ void sweep3_row(const T* c, const float2* vm, const f
     }
 }
 
-template <typename T, int RY, int RZ, int NP>
+template <typename T, int RY, int RZ, int NP, int D>
 __global__ void __launch_bounds__(XT_W / (2 * NP)) k_jacobi3_x2t(IterArgs a, const __grid_constant__ CUtensorMap me,
                                                                  const __grid_constant__ CUtensorMap mg, int* fault) {
     pdl_begin();
     constexpr int Q = 2 * NP, ER = RY + 4, GR = RY + 2;
     constexpr int EP = ER * XT_W, GP = GR * XT_W;  // elements of one staged plane
+    constexpr int NE = D + 3, NG = D + 2, NB = D + 1;  // ring slots; per-step barriers (bar[NB]: set-up)
     extern __shared__ __align__(128) unsigned char x3_smem[];
-    T* E = reinterpret_cast<T*>(x3_smem);  // 4 slots, iterate plane p in slot (p + 2) mod 4, rows y0 - 2 ..
-    T* G = E + 4 * EP;                     // 3 slots, source plane p in slot (p + 1) mod 3, rows y0 - 1 ..
-    T* S = G + 3 * GP;                     // 3 slots, first sweep at plane p in slot (p + 1) mod 3, rows y0 - 1 ..
-    uint64_t* bar = reinterpret_cast<uint64_t*>(S + 3 * GP);  // bar[0..3]: per-step copies, bar[4]: set-up
+    T* E = reinterpret_cast<T*>(x3_smem);  // iterate plane p in slot (p + 2) mod NE, rows y0 - 2 ..
+    T* G = E + NE * EP;                    // source plane p in slot (p + 1) mod NG, rows y0 - 1 ..
+    T* S = G + NG * GP;                    // first sweep at plane p in slot (p + 1) mod 3, rows y0 - 1 ..
+    uint64_t* bar = reinterpret_cast<uint64_t*>(S + 3 * GP);
     const int t = threadIdx.x;
     const int n = a.e_new.n;
     const int c0 = blockIdx.x * XT_OUT, y0 = blockIdx.y * RY + 1, z0 = blockIdx.z * RZ + 1;
     const int zlast = min(z0 + RZ, n);  // last first-sweep plane (the plane past the block's last output)
     const int zout = min(z0 + RZ - 1, n - 1);
-    auto eslot = [&](int p) { return E + ((p + 2) & 3) * EP; };
-    auto gslot = [&](int p) { return G + ((p + 1) % 3) * GP; };
+    auto eslot = [&](int p) { return E + ((p + 2) % NE) * EP; };
+    auto gslot = [&](int p) { return G + ((p + 1) % NG) * GP; };
     auto sslot = [&](int p) { return S + ((p + 1) % 3) * GP; };
+    // step s's planes (iterate s + 1, source s) on bar[s mod NB]; step z0 - 1's on bar[NB]
+    auto load_step = [&](int st) {
+        uint64_t* b = bar + st % NB;
+        xt_arm(b, (uint32_t)((EP + GP) * sizeof(T)));
+        xt_load_3d(eslot(st + 1), &me, c0 - 8, y0 - 2, st + 1, b);
+        xt_load_3d(gslot(st), &mg, c0 - 8, y0 - 1, st, b);
+    };
     if (t == 0) {
-        for (int k = 0; k < 5; ++k)
+        for (int k = 0; k <= NB; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar + k)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    uint32_t pend = 0;  // bit k: bar[k] has a phase armed and not yet waited for (same on every thread)
     if (t == 0) {
-        xt_arm(bar + 4, (uint32_t)((3 * EP + GP) * sizeof(T)));
-        for (int p = z0 - 2; p <= z0; ++p) xt_load_3d(eslot(p), &me, c0 - 8, y0 - 2, p, bar + 4);
-        xt_load_3d(gslot(z0 - 1), &mg, c0 - 8, y0 - 1, z0 - 1, bar + 4);
+        xt_arm(bar + NB, (uint32_t)((3 * EP + GP) * sizeof(T)));
+        for (int p = z0 - 2; p <= z0; ++p) xt_load_3d(eslot(p), &me, c0 - 8, y0 - 2, p, bar + NB);
+        xt_load_3d(gslot(z0 - 1), &mg, c0 - 8, y0 - 1, z0 - 1, bar + NB);
+    }
+    pend |= 1u << NB;
+    for (int st = z0; st <= min(z0 + D - 2, zlast); ++st) {
+        if (t == 0) load_step(st);
+        pend |= 1u << (st % NB);
     }
     const float2 om = make_float2(a.omega_f, a.omega_f), c1 = make_float2(a.c1_f, a.c1_f);
     const int x = c0 - 8 + Q * t;  // this thread's first column
@@ -1895,25 +1909,26 @@ __global__ void __launch_bounds__(XT_W / (2 * NP)) k_jacobi3_x2t(IterArgs a, con
 #pragma unroll
     for (int k = 0; k < Q; ++k) mcol[k] = x + k >= 1 && x + k <= n - 1;
     const bool first_cols = t >= 1 && t < XT_W / Q - 1;      // staged columns Q .. 255 - Q (7 .. 248 needed)
-    const bool out_cols = t >= 8 / Q && t < (8 + XT_OUT) / Q;                                 // staged columns 8 .. 247
+    const bool out_cols = t >= 8 / Q && t < (8 + XT_OUT) / Q;  // staged columns 8 .. 247
     uint32_t phases = 0;  // bit k: phase of bar[k] to wait for next
     for (int zf = z0 - 1; zf <= zlast; ++zf) {
-        // (a) next step's planes, into slots the previous step's barriers freed
-        if (t == 0 && zf + 2 <= zlast + 1) {
-            uint64_t* b = bar + ((zf + 4) & 3);
-            const bool gnext = zf + 1 <= zlast;
-            xt_arm(b, (uint32_t)((EP + (gnext ? GP : 0)) * sizeof(T)));
-            xt_load_3d(eslot(zf + 2), &me, c0 - 8, y0 - 2, zf + 2, b);
-            if (gnext) xt_load_3d(gslot(zf + 1), &mg, c0 - 8, y0 - 1, zf + 1, b);
+        // (a) the planes of step zf + D, into slots the previous steps' barriers freed
+        if (zf + D <= zlast) {
+            if (t == 0) load_step(zf + D);
+            pend |= 1u << ((zf + D) % NB);
         }
         // (b) this step's planes
-        const int wb = zf == z0 - 1 ? 4 : ((zf + 3) & 3);
+        const int wb = zf == z0 - 1 ? NB : zf % NB;
         const bool arrived = xt_wait(bar + wb, (phases >> wb) & 1u);
         phases ^= 1u << wb;
+        pend &= ~(1u << wb);
         if (!__syncthreads_and(arrived)) {
             // record the failure, give every copy still in flight one more bounded wait, and leave
             if (t == 0) atomicExch(fault, 1);
-            for (int k = 0; k < 5; ++k) xt_wait(bar + k, (phases >> k) & 1u);
+            phases ^= 1u << wb;
+            pend |= 1u << wb;
+            for (int k = 0; k <= NB; ++k)
+                if (pend & (1u << k)) xt_wait(bar + k, (phases >> k) & 1u);
             return;
         }
         // (c) first sweep at plane zf, rows y0 - 1 .. y0 + RY (0 off the interior)
@@ -2929,8 +2944,8 @@ cudaError_t iterate2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fau
 template <typename T> constexpr int x3_rows() { return 8; }
 constexpr int X3_PLANES = 32;
 template <typename T> constexpr int x3_pairs() { return sizeof(T) == 2 ? 2 : 1; }
-template <typename T> constexpr size_t x3_smem_bytes() {
-    return (size_t)(4 * (x3_rows<T>() + 4) + 6 * (x3_rows<T>() + 2)) * XT_W * sizeof(T) + 64;
+template <typename T, int D> constexpr size_t x3_smem_bytes() {
+    return (size_t)((D + 3) * (x3_rows<T>() + 4) + (D + 5) * (x3_rows<T>() + 2)) * XT_W * sizeof(T) + 64;
 }
 
 // A 3-D lattice array of (n + 1)^3 nodes, rows of `pitch` elements, (n + 1) rows per plane, as a 3-D
@@ -2968,13 +2983,13 @@ cudaError_t tma_sweep_maps3(int prec, const IterArgs& a, TmaSweepMaps* maps) {
     }
 }
 
-template <typename T>
-cudaError_t iterate3_2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
+template <typename T, int D>
+cudaError_t iterate3_2_tma_d(const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
     constexpr int RY = x3_rows<T>(), NP = x3_pairs<T>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_jacobi3_x2t<T, RY, X3_PLANES, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)x3_smem_bytes<T>());
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi3_x2t<T, RY, X3_PLANES, NP, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)x3_smem_bytes<T, D>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -2983,14 +2998,21 @@ cudaError_t iterate3_2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* f
     cfg.gridDim = dim3((unsigned)((n - 1) / XT_OUT + 1), (unsigned)((n - 1 + RY - 1) / RY),
                        (unsigned)((n - 1 + X3_PLANES - 1) / X3_PLANES));
     cfg.blockDim = dim3(XT_W / (2 * NP));
-    cfg.dynamicSmemBytes = x3_smem_bytes<T>();
+    cfg.dynamicSmemBytes = x3_smem_bytes<T, D>();
     cfg.stream = s;
     cudaLaunchAttribute attrs[1];
     attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attrs[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attrs;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_jacobi3_x2t<T, RY, X3_PLANES, NP>, a, maps.me, maps.mg, fault);
+    return cudaLaunchKernelEx(&cfg, k_jacobi3_x2t<T, RY, X3_PLANES, NP, D>, a, maps.me, maps.mg, fault);
+}
+
+// Prefetch distance 1: at 513³ distances 2 and 3 measured slower (binary32 934 / 927 us per level-0
+// pair against 588, bfloat16 492 / 611 against 425): their larger rings cost resident blocks per SM.
+template <typename T>
+cudaError_t iterate3_2_tma_t(const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
+    return iterate3_2_tma_d<T, 1>(a, maps, fault, s);
 }
 
 cudaError_t launch_iterate3_2_tma(int prec, const IterArgs& a, const TmaSweepMaps& maps, int* fault, cudaStream_t s) {
