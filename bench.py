@@ -39,7 +39,7 @@ FP64_NOMINAL_OPS = 0.625e12
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
-LEVEL0_FP64_DRAM_BYTES = 384.69e6  # k_jacobi2<0, 0, double> on 4097^2 (FMA-chain form), launch at 16 rows per thread
+LEVEL0_FP64_DRAM_BYTES = None  # k_jacobi2d2<0, 0> on 4097^2: not yet captured
 # k_jacobi2_x2<float> (two fused sweeps) on 4097^2, one captured launch: 134.8 MB read + 38.2 MB written
 LEVEL0_FP32_DRAM_BYTES = 173.01e6
 
@@ -949,21 +949,28 @@ def run(args):
     alu_achieved = ops / per_launch_s / 1e12
     hbm_achieved = bts / per_launch_s / 1e9
     clk = clocks.summary()
-    kname = ("k_jacobi2 (level-0 HOMG iteration: damped Jacobi on every interior node)" if sweeps_per_launch == 1 else
+    # FP64 instructions the level-0 sweep issues per interior node: one shared neighbour pair and
+    # three FMAs per node, on warps of 63 output columns out of 64 (k_jacobi2d2)
+    fp64_issued_per_node = 4.0 * 64 / 63
+    kname = ("k_jacobi2d2 (level-0 HOMG iteration: damped Jacobi on every interior node, shared neighbour pairs)"
+             if args.precision == "fp64" else
+             "k_jacobi2 (level-0 HOMG iteration: damped Jacobi on every interior node)" if sweeps_per_launch == 1 else
              "k_jacobi2_x2 / k_jacobi2 (level-0 HOMG iterations, consecutive plain sweeps fused two per launch; "
              "average over the level's launches)")
     # DRAM bytes (read + write) per launch of this kernel from ncu: the FP64 sweep
-    # (profiles/k_jacobi2_fp64_4097.md) and the fused FP32 pair (profiles/k_jacobi2_x2_fp32_4097.md;
+    # (profiles/k_jacobi2d2_fp64_4097.md) and the fused FP32 pair (profiles/k_jacobi2_x2_fp32_4097.md;
     # the level's two single FP32 sweeps move the same bytes); the bfloat16 build was not captured
-    traffic, traffic_src = {"fp64": (LEVEL0_FP64_DRAM_BYTES, "profiles/k_jacobi2_fp64_4097.md"),
+    traffic, traffic_src = {"fp64": (LEVEL0_FP64_DRAM_BYTES, "profiles/k_jacobi2d2_fp64_4097.md"),
                             "fp32": (LEVEL0_FP32_DRAM_BYTES, "profiles/k_jacobi2_x2_fp32_4097.md")}.get(
         args.precision, (None, None))
     common = {"kernel": kname, "launch_us": per_launch_s * 1e6, "launches": launches,
               "algorithmic_flops_per_launch": ops, "algorithmic_bytes_per_launch": bts, "traffic": traffic,
               "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + traffic_src if traffic else None}
     # The roofline is the HBM one (algorithmic bytes per launch / launch time / measured copy
-    # bandwidth). An FP64 sweep is bound on GB300 by the FP64 pipe instead (5 FP64 instructions per
-    # 24 bytes): its ALU fraction, against the issue rate measured in this run, is carried beside it.
+    # bandwidth). An FP64 sweep is bound on GB300 by the FP64 pipe instead (4.06 FP64 instructions
+    # issued per 24 bytes): its ALU fraction, against the issue rate measured in this run, is carried
+    # beside it, counted in the instructions the kernel issues (the method's own count, 5 per node
+    # as one FMA per neighbour, centre and source, is given as well).
     roofline = dict(common, bound="hbm", achieved=hbm_achieved, peak=hbm_peak, unit="GB/s",
                     frac=hbm_achieved / hbm_peak, peak_source=peak_src + " (MEASURED_PEAKS.json hbm_gbs)")
     if fp64_peak:
@@ -972,7 +979,11 @@ def run(args):
         roofline["alu"] = {"binding": args.precision == "fp64", "achieved": alu_achieved, "unit": instr_unit,
                            "instructions_per_launch": ops}
         if args.precision == "fp64":
-            roofline["alu"].update(peak=p_meas, frac=alu_achieved / p_meas,
+            issued = ops / 5.0 * fp64_issued_per_node
+            alu_achieved = issued / per_launch_s / 1e12
+            roofline["alu"].update(achieved=alu_achieved, instructions_per_launch=issued,
+                                   instructions_per_node=fp64_issued_per_node, method_instructions_per_launch=ops,
+                                   peak=p_meas, frac=alu_achieved / p_meas,
                                    peak_source="measured in this run: homg_fp64_issue_probe, mean of 20 back-to-back "
                                                "launches (FMA %.3f, ADD %.3f T instr/s; SM clock median %s MHz)" % (
                                                    fp64_peak["fma"]["mean_tinstr_per_s"],

@@ -818,6 +818,144 @@ __global__ void __launch_bounds__(JX) k_jacobi2(IterArgs a, int rows) {
     jacobi2_body<PEND, WD, T, BATCH, false>(a, rows, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// FP64 level iteration of a single problem with shared neighbour pairs. The pair
+// D(i, j) = v(i+1, j) + v(i, j+1) is the east + north sum of node (i, j) and the west + south sum
+// of node (i+1, j+1), so with one pair formed per node the update
+//   v' = c1 v + om (D(i, j) + D(i-1, j-1)) + g
+// costs one FP64 addition (written as an FMA by a run-time 1) and three FMAs: 4 FP64 instructions
+// per node instead of the 5 of jacobi_update. A warp's lanes march 32 adjacent columns down the
+// rows; D(i-1, j-1) is the left lane's pair from the row before (a shuffle). Lane 0 holds the
+// column left of the warp's 31 output columns and only forms its pair, so the warp issues 4 x 32 / 31
+// = 4.13 FP64 instructions per output node. Same values as jacobi2_body up to the order of the
+// additions.
+constexpr int JD_COLS = 31;  // output columns per warp
+template <int PEND, bool WD>
+__global__ void __launch_bounds__(JX) k_jacobi2d(IterArgs a, int rows) {
+    pdl_begin();
+    const int n = a.e_new.n;
+    const int lane = threadIdx.x & 31;
+    const int i0 = (blockIdx.x * (JX / 32) + (threadIdx.x >> 5)) * JD_COLS;  // the warp's left column
+    if (i0 + 1 > n - 1) return;                                              // warp-uniform: no output
+    const int iu = i0 + lane;
+    const int i = min(iu, n - 1);  // lanes past the last interior column load inside the lattice
+    const bool out = lane > 0 && iu <= n - 1;
+    const int j0 = blockIdx.y * rows + 1;
+    const int j1 = min(j0 + rows, n);
+    const double* __restrict__ E = cp<double>(a.e_old);
+    const int64_t pe = a.e_old.pitch;
+    double* __restrict__ O = wp<double>(a.e_new);
+    const int64_t po = a.e_new.pitch;
+    const double* __restrict__ G = cp<double>(a.g);
+    const int64_t pg = a.g.pitch;
+    const double om = a.omega, c1 = a.c1, one = a.one;
+    const int lpm = PEND ? (1 << a.mp) - 1 : 0;
+    ColumnInterp2<double, false> ci;
+    if (PEND == 1) {
+        ci.d = cp<double>(a.dprev) + (i >> 1);
+        ci.d2 = nullptr;
+        ci.pitch = a.dprev.pitch;
+        ci.pitch2 = 0;
+        ci.hx = (i & 1) ? 0.5 : 0.0;
+    }
+    double vc = __ldg(E + (int64_t)j0 * pe + i);
+    double dp = fma(one, __ldg(E + (int64_t)(j0 - 1) * pe + i + 1), vc);  // D(i, j0 - 1)
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const double* row = E + (int64_t)j * pe + i;
+        const double vn = __ldg(row + pe), e = __ldg(row + 1);
+        const double g = __ldg(G + (int64_t)j * pg + i);
+        const double dw = __shfl_up_sync(0xffffffffu, dp, 1);  // D(i-1, j-1): west + south
+        const double dh = fma(one, e, vn);                       // D(i, j): east + north
+        double v = fma(om, dh, fma(om, dw, fma(c1, vc, g)));
+        if (WD && out) wp<double>(a.dnew)[(int64_t)j * a.dnew.pitch + i] = v - vc;
+        if (PEND == 1) {
+            const double sv = ci.at(j);
+            v += ((i | j) & 1) ? sv : 0.0;
+        }
+        if (PEND == 2 && out && ((i | j) & lpm)) v += interp<2, false, false, double>(a.dprev, a.dprev, a.mp, i, j, 0);
+        if (out) O[(int64_t)j * po + i] = v;
+        dp = dh;
+        vc = vn;
+    }
+}
+
+// The same with two adjacent columns per lane (cA = i0 + 2 lane, cB = cA + 1; lane 0's cA is the
+// helper column): 63 output columns per warp, 4 x 64 / 63 = 4.06 FP64 instructions per output node,
+// one shuffle per two nodes. East of cA is cB's centre; west + south of cB is cA's pair from the row
+// before. Lanes past the lattice clamp their columns to n (the boundary column); PEND reads clamp
+// to n - 1.
+constexpr int JD2_COLS = 63;
+// Two columns per lane from this lattice size on. Measured in the 4097² FP64 solve: level-0 sweep
+// 148.1 -> 145.9 us, but the smaller lattices slower (levels >= 1: 17.2 -> 18.0 ms per solve).
+constexpr int JD2_MIN_N = 4096;
+template <int PEND, bool WD>
+__global__ void __launch_bounds__(JX) k_jacobi2d2(IterArgs a, int rows) {
+    pdl_begin();
+    const int n = a.e_new.n;
+    const int lane = threadIdx.x & 31;
+    const int i0 = (blockIdx.x * (JX / 32) + (threadIdx.x >> 5)) * JD2_COLS;
+    if (i0 + 1 > n - 1) return;  // warp-uniform
+    const int cA = i0 + 2 * lane, cB = cA + 1;
+    const int iA = min(cA, n), iB = min(cB, n), iE = min(cB + 1, n);
+    const bool outA = lane > 0 && cA <= n - 1, outB = cB <= n - 1;
+    const int j0 = blockIdx.y * rows + 1;
+    const int j1 = min(j0 + rows, n);
+    const double* __restrict__ E = cp<double>(a.e_old);
+    const int64_t pe = a.e_old.pitch;
+    double* __restrict__ O = wp<double>(a.e_new);
+    const int64_t po = a.e_new.pitch;
+    const double* __restrict__ G = cp<double>(a.g);
+    const int64_t pg = a.g.pitch;
+    const double om = a.omega, c1 = a.c1, one = a.one;
+    const int lpm = PEND ? (1 << a.mp) - 1 : 0;
+    const int pA = min(cA, n - 1), pB = min(cB, n - 1);
+    ColumnInterp2<double, false> ciA, ciB;
+    if (PEND == 1) {
+        ciA.d = cp<double>(a.dprev) + (pA >> 1);
+        ciB.d = cp<double>(a.dprev) + (pB >> 1);
+        ciA.d2 = ciB.d2 = nullptr;
+        ciA.pitch = ciB.pitch = a.dprev.pitch;
+        ciA.pitch2 = ciB.pitch2 = 0;
+        ciA.hx = (pA & 1) ? 0.5 : 0.0;
+        ciB.hx = (pB & 1) ? 0.5 : 0.0;
+    }
+    double vcA = __ldg(E + (int64_t)j0 * pe + iA), vcB = __ldg(E + (int64_t)j0 * pe + iB);
+    double dpA = fma(one, __ldg(E + (int64_t)(j0 - 1) * pe + iB), vcA);  // D(cA, j0 - 1)
+    double dpB = fma(one, __ldg(E + (int64_t)(j0 - 1) * pe + iE), vcB);  // D(cB, j0 - 1)
+#pragma unroll 2
+    for (int j = j0; j < j1; ++j) {
+        const double* row = E + (int64_t)j * pe;
+        const double vnA = __ldg(row + pe + iA), vnB = __ldg(row + pe + iB), eB = __ldg(row + iE);
+        const double* grow = G + (int64_t)j * pg;
+        const double gA = __ldg(grow + iA), gB = __ldg(grow + iB);
+        const double dwA = __shfl_up_sync(0xffffffffu, dpB, 1);  // D(cA-1, j-1)
+        const double dhA = fma(one, vcB, vnA), dhB = fma(one, eB, vnB);
+        double vA = fma(om, dhA, fma(om, dwA, fma(c1, vcA, gA)));
+        double vB = fma(om, dhB, fma(om, dpA, fma(c1, vcB, gB)));
+        if (WD) {
+            double* D = wp<double>(a.dnew) + (int64_t)j * a.dnew.pitch;
+            if (outA) D[cA] = vA - vcA;
+            if (outB) D[cB] = vB - vcB;
+        }
+        if (PEND == 1) {
+            const double sA = ciA.at(j), sB = ciB.at(j);
+            vA += ((pA | j) & 1) ? sA : 0.0;
+            vB += ((pB | j) & 1) ? sB : 0.0;
+        }
+        if (PEND == 2) {
+            if (outA && ((cA | j) & lpm)) vA += interp<2, false, false, double>(a.dprev, a.dprev, a.mp, cA, j, 0);
+            if (outB && ((cB | j) & lpm)) vB += interp<2, false, false, double>(a.dprev, a.dprev, a.mp, cB, j, 0);
+        }
+        double* orow = O + (int64_t)j * po;
+        if (outA) orow[cA] = vA;
+        if (outB) orow[cB] = vB;
+        dpA = dhA;
+        dpB = dhB;
+        vcA = vnA;
+        vcB = vnB;
+    }
+}
+
 // Coefficient storage of the variable-coefficient kernels: double for FP64 cycles, float otherwise.
 template <typename T> struct KT { using type = float; };
 template <> struct KT<double> { using type = double; };
@@ -2479,7 +2617,25 @@ cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) 
     if (!strict && a.m == 0 && a.e_old.p != nullptr) {
         const bool wd = a.dnew.p != nullptr;
         const int rows = a.rows > 0 ? a.rows : march_rows(ndim, n, a.nb);
-        if (ndim == 2) {
+        if (ndim == 2 && std::is_same<T, double>::value && !a.bst && n >= JD2_MIN_N) {
+            constexpr int per_block = JX / 32 * JD2_COLS;
+            const dim3 g((unsigned)((n - 1 + per_block - 1) / per_block), (unsigned)((n - 1 + rows - 1) / rows)), b(JX);
+            const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
+#define JAC2D(P, W) launch_k(k_jacobi2d2<P, W>, g, b, s, a, rows)
+            if (pend == 0) { if (wd) JAC2D(0, true); else JAC2D(0, false); }
+            else if (pend == 1) { if (wd) JAC2D(1, true); else JAC2D(1, false); }
+            else { if (wd) JAC2D(2, true); else JAC2D(2, false); }
+#undef JAC2D
+        } else if (ndim == 2 && std::is_same<T, double>::value && !a.bst) {
+            constexpr int per_block = JX / 32 * JD_COLS;
+            const dim3 g((unsigned)((n - 1 + per_block - 1) / per_block), (unsigned)((n - 1 + rows - 1) / rows)), b(JX);
+            const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
+#define JAC2D(P, W) launch_k(k_jacobi2d<P, W>, g, b, s, a, rows)
+            if (pend == 0) { if (wd) JAC2D(0, true); else JAC2D(0, false); }
+            else if (pend == 1) { if (wd) JAC2D(1, true); else JAC2D(1, false); }
+            else { if (wd) JAC2D(2, true); else JAC2D(2, false); }
+#undef JAC2D
+        } else if (ndim == 2) {
             const dim3 g((unsigned)((n - 1 + JX - 1) / JX), (unsigned)((n - 1 + rows - 1) / rows), (unsigned)a.nb), b(JX);
             const int pend = a.mp < 0 ? 0 : (a.mp == 1 ? 1 : 2);
 #define JAC2(P, W) (a.bst ? launch_k(k_jacobi2<P, W, T, true>, g, b, s, a, rows) : launch_k(k_jacobi2<P, W, T, false>, g, b, s, a, rows))
