@@ -167,15 +167,13 @@ template <> __device__ __forceinline__ float dyadic<float>(int f, int e) {
 
 // One damped-Jacobi update v' = c1 v + om (sum of the 2d neighbours) + g (g pre-scaled by om).
 // FP64 (the FP64 pipe bounds these kernels on GB300, and it issues fused multiply-adds at 0.627
-// against 0.528 T instr/s for additions, measured): a chain of 2d + 1 FMAs, every neighbour scaled
-// by om on its own. Binary32 (DRAM bound): the neighbour sum, then two FMAs.
-__device__ __forceinline__ double jacobi_update(double c1, double om, double vc, double g, double n0, double n1,
-                                                double n2, double n3) {
-    double t = fma(om, n0, g);
-    t = fma(om, n1, t);
-    t = fma(om, n2, t);
-    t = fma(om, n3, t);
-    return fma(c1, vc, t);
+// against 0.528 T instr/s for additions, measured). 2-D: the neighbour pairs e + n and s + w, then
+// three FMAs, in the order of the shared-pair sweeps (k_jacobi2d, k_jacobi2d2), which form each
+// pair once for two nodes; the additions are FMAs by the run-time 1. 3-D: a chain of 7 FMAs, every
+// neighbour scaled by om on its own. Binary32 (DRAM bound): the neighbour sum, then two FMAs.
+__device__ __forceinline__ double jacobi_pairs(double c1, double om, double one, double vc, double g, double w,
+                                               double e, double s, double n) {
+    return fma(om, fma(one, e, n), fma(om, fma(one, s, w), fma(c1, vc, g)));
 }
 __device__ __forceinline__ float jacobi_update(float c1, float om, float vc, float g, float n0, float n1, float n2,
                                                float n3) {
@@ -799,7 +797,9 @@ __device__ __forceinline__ void jacobi2_body(IterArgs a, int rows, int bx, int b
         const C vn = ldv<T, P>(row + pe);
         const C w = ldv<T, P>(row - 1), e = ldv<T, P>(row + 1);
         const C g = ldv<T, P>(G + (int64_t)j * pg + i);
-        C v = jacobi_update(c1, om, vc, g, w, e, vs, vn);
+        C v;
+        if constexpr (std::is_same<C, double>::value) v = jacobi_pairs(c1, om, a.one, vc, g, w, e, vs, vn);
+        else v = jacobi_update(c1, om, vc, g, w, e, vs, vn);
         if (WD) wp<T>(a.dnew)[(int64_t)j * a.dnew.pitch + i] = St<T>::put(v - vc);
         if (PEND == 1) {
             const C sv = ci.at(j);
