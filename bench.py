@@ -39,7 +39,7 @@ FP64_NOMINAL_OPS = 0.625e12
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
-LEVEL0_FP64_DRAM_BYTES = None  # k_jacobi2d2<0, 0> on 4097^2: not yet captured
+LEVEL0_FP64_DRAM_BYTES = 384.30e6  # k_jacobi2d2<0, 0> on 4097^2, one launch at 16 rows per thread
 # k_jacobi2_x2<float> (two fused sweeps) on 4097^2, one captured launch: 134.8 MB read + 38.2 MB written
 LEVEL0_FP32_DRAM_BYTES = 173.01e6
 
