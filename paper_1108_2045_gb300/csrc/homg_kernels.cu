@@ -1842,6 +1842,51 @@ __global__ void __launch_bounds__(J3X * J3Y) k_jacobi3(IterArgs a, int rows) {
     }
 }
 
+// FP64 3-D iteration with a shared neighbour pair: D(i, j, k) = v(i+1, j, k) + v(i, j, k+1) is the
+// east + top sum of node (i, j, k) and the west + bottom sum of node (i+1, j, k+1), the left lane's
+// pair from the step before. With the south + north sum that leaves 6 FP64 instructions per node
+// instead of the 7 of the FMA chain; lane 0 of each warp holds the column left of the warp's 31
+// output columns and only forms its pair (6 x 32 / 31 = 6.19 per output node).
+template <bool PEND, bool WD>
+__global__ void __launch_bounds__(J3X * J3Y) k_jacobi3d(IterArgs a, int rows) {
+    pdl_begin();
+    const int n = a.e_new.n;
+    const int j = blockIdx.y * J3Y + threadIdx.y + 1;
+    if (j >= n) return;  // uniform over the warp (one thread row)
+    const int iu = blockIdx.x * JD_COLS + threadIdx.x;
+    if (blockIdx.x * JD_COLS + 1 > n - 1) return;
+    const int i = min(iu, n - 1);
+    const bool out = threadIdx.x > 0 && iu <= n - 1;
+    const int k0 = blockIdx.z * rows + 1;
+    const int k1 = min(k0 + rows, n);
+    const double* __restrict__ E = cp<double>(a.e_old);
+    const int64_t pe = a.e_old.pitch, ple = (int64_t)(n + 1) * pe;
+    double* __restrict__ O = wp<double>(a.e_new);
+    const int64_t po = a.e_new.pitch, plo = (int64_t)(n + 1) * po;
+    const double* __restrict__ G = cp<double>(a.g);
+    const int64_t pg = a.g.pitch, plg = (int64_t)(n + 1) * pg;
+    const double om = a.omega, c1 = a.c1, one = a.one;
+    const int lpm = PEND ? (1 << a.mp) - 1 : 0;
+    const double* col = E + (int64_t)j * pe + i;
+    double vc = __ldg(col + (int64_t)k0 * ple);
+    double dp = fma(one, __ldg(col + (int64_t)(k0 - 1) * ple + 1), vc);  // D(i, j, k0 - 1)
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) {
+        const double* p = col + (int64_t)k * ple;
+        const double vt = __ldg(p + ple);
+        const double e = __ldg(p + 1), sn = __ldg(p - pe), nn = __ldg(p + pe);
+        const double g = __ldg(G + (int64_t)k * plg + (int64_t)j * pg + i);
+        const double dw = __shfl_up_sync(0xffffffffu, dp, 1);  // D(i-1, j, k-1): west + bottom
+        const double dh = fma(one, e, vt);                       // D(i, j, k): east + top
+        double v = fma(om, dh, fma(om, dw, fma(om, fma(one, sn, nn), fma(c1, vc, g))));
+        if (WD && out) wp<double>(a.dnew)[(int64_t)k * (n + 1) * a.dnew.pitch + (int64_t)j * a.dnew.pitch + i] = v - vc;
+        if (PEND && out && ((i | j | k) & lpm)) v += interp<3, false, false, double>(a.dprev, a.dprev, a.mp, i, j, k);
+        if (out) O[(int64_t)k * plo + (int64_t)j * po + i] = v;
+        dp = dh;
+        vc = vt;
+    }
+}
+
 
 // Two plain sweeps of the 3-D lattice form in one pass (binary32 arithmetic: FP32 and bfloat16
 // cycles, where a sweep is DRAM bound). A block of 32 x J3Y2 threads owns a tile of columns
@@ -2334,11 +2379,12 @@ __global__ void __launch_bounds__(JX) k_wholegrid2(IterArgs a) {
 // Fast update + residual (2-D): each warp marches a strip of 32 columns along y; every lane forms
 // u_new = u_in + e once per node of its column, the 30 inner lanes own their nodes and take the west
 // and east neighbours' updated values by shuffle, the two edge lanes only supply theirs. Every
-// instruction is issued once per warp and row for 30 nodes, none for an edge lane alone: 8 FP64
-// instructions per node in FP64 cycles, 7 in binary32 and bfloat16 cycles (the source's multiply in
-// binary32, source_store), one more for the norm of f on the initial residual. Widening e and
-// rounding the source to the cycle's storage use the integer conversions above. Results are
-// bit-identical to forming every neighbour locally.
+// instruction is issued once per warp and row for 30 nodes, none for an edge lane alone. The
+// neighbour sum is formed from shared pairs (one addition per node for the pair, one to join two
+// pairs, as in k_jacobi2d): 7 FP64 instructions per node in FP64 cycles, 6 in binary32 and bfloat16
+// cycles (the source's multiply in binary32, source_store), one more for the norm of f on the
+// initial residual. Widening e and rounding the source to the cycle's storage use the integer
+// conversions above. Results are bit-identical to forming every pair locally.
 constexpr int RS_OUT = 30;  // nodes per warp strip
 template <typename T, bool VC, bool BATCH, bool P>
 __device__ __forceinline__ void residual2_fast_body(ResidArgs a, int n, int bx, int by, int bz, int gx) {
@@ -2371,9 +2417,19 @@ __device__ __forceinline__ void residual2_fast_body(ResidArgs a, int n, int bx, 
     double rr = 0.0, ff = 0.0;
     double vs = un(j0 - 1), vc = un(j0);
     double ks = (VC && active) ? __ldg(a.ky + (int64_t)(j0 - 1) * a.kpitch + i) : 0.0;
+    // Poisson: the neighbour pair D(i, j) = v(i+1, j) + v(i, j+1) of every lane, east + north here
+    // and west + south of the node (i+1, j+1), taken from the left lane's previous row
+    double dp = VC ? 0.0 : fma(one, __shfl_down_sync(0xffffffffu, vs, 1), vc);  // D(i, j0 - 1)
     for (int j = j0; j < j1; ++j) {
         const double vn = un(j + 1);
-        const double w = __shfl_up_sync(0xffffffffu, vc, 1), e = __shfl_down_sync(0xffffffffu, vc, 1);
+        const double e = __shfl_down_sync(0xffffffffu, vc, 1);
+        const double w = VC ? __shfl_up_sync(0xffffffffu, vc, 1) : 0.0;
+        double dh = 0.0, dw = 0.0;
+        if constexpr (!VC) {
+            dw = __shfl_up_sync(0xffffffffu, dp, 1);  // D(i-1, j-1)
+            dh = fma(one, e, vn);                     // D(i, j)
+            dp = dh;
+        }
         if (active) {
             const double fv = __ldg(F + (int64_t)j * pf + i);
             double r;
@@ -2388,8 +2444,7 @@ __device__ __forceinline__ void residual2_fast_body(ResidArgs a, int n, int bx, 
                 r = fma(-a.inv_h2, fma(d, vc, -t), fv);
                 ks = kn;
             } else {
-                const double sum = fma(one, fma(one, w, e), fma(one, vs, vn));
-                r = fma(a.inv_h2, fma(-4.0, vc, sum), fv);
+                r = fma(a.inv_h2, fma(-4.0, vc, fma(one, dh, dw)), fv);
             }
             if (a.u_out.p) a.u_out.p[(int64_t)j * a.u_out.pitch + i] = vc;
             if (a.g0.p) wp<T>(a.g0)[(int64_t)j * a.g0.pitch + i] = source_store<T>(r, a.scale, a.scale_f);
@@ -2643,6 +2698,15 @@ cudaError_t iterate_t(int ndim, bool strict, const IterArgs& a, cudaStream_t s) 
             else if (pend == 1) { if (wd) JAC2(1, true); else JAC2(1, false); }
             else { if (wd) JAC2(2, true); else JAC2(2, false); }
 #undef JAC2
+        } else if (std::is_same<T, double>::value) {
+            const bool pend = a.mp >= 0;
+            const dim3 g((unsigned)((n - 1 + JD_COLS - 1) / JD_COLS), (unsigned)((n - 1 + J3Y - 1) / J3Y),
+                         (unsigned)((n - 1 + rows - 1) / rows)),
+                b(J3X, J3Y);
+            if (pend && wd) launch_k(k_jacobi3d<true, true>, g, b, s, a, rows);
+            else if (pend) launch_k(k_jacobi3d<true, false>, g, b, s, a, rows);
+            else if (wd) launch_k(k_jacobi3d<false, true>, g, b, s, a, rows);
+            else launch_k(k_jacobi3d<false, false>, g, b, s, a, rows);
         } else {
             const bool pend = a.mp >= 0;
             const dim3 g((unsigned)((n - 1 + J3X - 1) / J3X), (unsigned)((n - 1 + J3Y - 1) / J3Y),

@@ -1,8 +1,8 @@
-"""A CPU model of k_jacobi2d, the FP64 level iteration with shared neighbour pairs, restated as the
-kernel runs: blocks of four warps, each warp's 32 lanes on adjacent columns with lane 0 on the
-column left of the warp's 31 output columns, lanes past the last interior column clamped to it,
-each lane marching `rows` rows and taking the west + south pair from the left lane's previous row
-(a shuffle up by one, lane 0 keeping its own value).
+"""A CPU model of k_jacobi2d and k_jacobi2d2 (and of k_jacobi3d in 3-D), the FP64 level iterations
+with shared neighbour pairs, restated as the kernels run: blocks of four warps, each warp's 32 lanes
+on adjacent columns with lane 0 on the column left of the warp's 31 output columns, lanes past the
+last interior column clamped to it, each lane marching `rows` rows and taking the west + south pair
+from the left lane's previous row (a shuffle up by one, lane 0 keeping its own value).
 
 For every launch shape it checks:
 - every load stays inside the (n+1)^2 array;
@@ -157,3 +157,77 @@ def test_model_catches_a_wrong_shuffle():
             dh = fma(1.0, float(E[j, i + 1]), float(E[j + 1, i]))
             wrong[j, i] = fma(0.2, dh, fma(0.2, own, fma(0.2, float(E[j, i]), float(G[j, i]))))
     assert not np.array_equal(wrong[1:n, 1:n], ref[1:n, 1:n])
+
+
+J3Y = 4  # thread rows of a 3-D block; each row of 32 lanes is one warp
+
+
+def model3(E, G, n, rows, om, c1):
+    """k_jacobi3d: the pair D(i, j, k) = v(i+1, j, k) + v(i, j, k+1) handed to the right lane at the
+    next plane; arrays indexed [k, j, i]."""
+    O = np.zeros_like(E)
+    written = np.zeros(E.shape, dtype=int)
+
+    def ld(A, i, j, k):
+        assert 0 <= i <= n and 0 <= j <= n and 0 <= k <= n, (i, j, k)
+        return float(A[k, j, i])
+
+    for bx in range((n - 1 + COLS - 1) // COLS):
+        if bx * COLS + 1 > n - 1:
+            continue
+        for by in range((n - 1 + J3Y - 1) // J3Y):
+            for bz in range((n - 1 + rows - 1) // rows):
+                for ty in range(J3Y):
+                    j = by * J3Y + ty + 1
+                    if j >= n:
+                        continue
+                    lanes = range(32)
+                    col = [min(bx * COLS + l, n - 1) for l in lanes]
+                    out = [l > 0 and bx * COLS + l <= n - 1 for l in lanes]
+                    k0 = bz * rows + 1
+                    k1 = min(k0 + rows, n)
+                    vc = [ld(E, col[l], j, k0) for l in lanes]
+                    dp = [fma(1.0, ld(E, col[l] + 1, j, k0 - 1), vc[l]) for l in lanes]
+                    for k in range(k0, k1):
+                        dw = [dp[l - 1] if l > 0 else dp[0] for l in lanes]
+                        for l in lanes:
+                            i = col[l]
+                            vt = ld(E, i, j, k + 1)
+                            e, sn, nn = ld(E, i + 1, j, k), ld(E, i, j - 1, k), ld(E, i, j + 1, k)
+                            g = ld(G, i, j, k)
+                            dh = fma(1.0, e, vt)
+                            v = fma(om, dh, fma(om, dw[l], fma(om, fma(1.0, sn, nn), fma(c1, vc[l], g))))
+                            if out[l]:
+                                O[k, j, i] = v
+                                written[k, j, i] += 1
+                            dp[l] = dh
+                            vc[l] = vt
+    return O, written
+
+
+@pytest.mark.parametrize("n,rows", [(4, 2), (16, 5), (33, 8)])
+def test_pair_sweep_3d_geometry_and_values(n, rows):
+    rng = np.random.default_rng(n + rows)
+    E = rng.standard_normal((n + 1,) * 3)
+    for ax in range(3):
+        idx = [slice(None)] * 3
+        for b in (0, n):
+            idx[ax] = b
+            E[tuple(idx)] = 0.0
+    G = rng.standard_normal((n + 1,) * 3)
+    om, c1 = 0.8 / 6, 1.0 - 0.8
+    O, written = model3(E, G, n, rows, om, c1)
+    inner = (slice(1, n),) * 3
+    assert (written[inner] == 1).all() and written.sum() == (n - 1) ** 3
+    ref = np.zeros_like(E)
+    for k in range(1, n):
+        for j in range(1, n):
+            for i in range(1, n):
+                dh = fma(1.0, float(E[k, j, i + 1]), float(E[k + 1, j, i]))
+                dw = fma(1.0, float(E[k - 1, j, i]), float(E[k, j, i - 1]))
+                sn = fma(1.0, float(E[k, j - 1, i]), float(E[k, j + 1, i]))
+                ref[k, j, i] = fma(om, dh, fma(om, dw, fma(om, sn, fma(c1, float(E[k, j, i]), float(G[k, j, i])))))
+    assert np.array_equal(O[inner], ref[inner])
+    jac = c1 * E[inner] + om * (E[1:n, 1:n, :n - 1] + E[1:n, 1:n, 2:] + E[1:n, :n - 1, 1:n] + E[1:n, 2:, 1:n]
+                                + E[:n - 1, 1:n, 1:n] + E[2:, 1:n, 1:n]) + G[inner]
+    assert np.max(np.abs(O[inner] - jac)) <= 1e-14 * np.max(np.abs(jac))
